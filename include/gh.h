@@ -1,0 +1,247 @@
+/*
+ * gh.h - C-ABI of the GB300 grid-hopping library (libgh.so).
+ *
+ * Implements the hot path of "Grid Hopping: Accelerating Direct Estimation
+ * Algorithms for Multistatic FMCW Radar" (Monnoyer, Feuillen, Drouguet,
+ * Jacques, Vandendorpe): range-Doppler maps, the grid-hopping score over a 4D
+ * location-velocity grid, its argmax, a BOMP detect-and-deflate loop, and the
+ * exact direct decision function.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Problem statement (Sec. II): one TX at tx[0..1] (metres, 2D ground plane),
+ * Q receivers at rx[2q], rx[2q+1]; chirps of carrier f0 [Hz], bandwidth B [Hz]
+ * and duration Tc [s]; a frame of Mc chirps x Ms samples per receiver.
+ *
+ * Measurement Y: complex float32, interleaved (re, im), layout [Q][Mc][Ms]
+ * (row mc is chirp mc; Sec. II). Range-Doppler maps: layout [Q][Nr][Nd]
+ * (range bin major, Doppler bin contiguous), Nr = pad*Ms, Nd = pad*Mc.
+ *
+ * Sensing functions (Eq. 1, read as cycles per sample / per chirp):
+ *   r_q(x)    = B * d_q(x) / (c * Ms),  d_q = |x - tx| + |x - rx_q|
+ *   u_q(x, v) = (f0 * Tc / c) * <w_q(x), v>,
+ *   w_q = (x - tx)/|x - tx| + (x - rx_q)/|x - rx_q|   (a length < 1e-9 m gives 0)
+ * with c = 299792458 m/s. Atoms a_m(r) = exp(j 2 pi r m), b_mc(u) = exp(j 2 pi u mc).
+ *
+ * Grid (gh_grid): axes x, y, vx, vy; point i of axis a is
+ * lo[a] + (i + 1/2) * step[a], i < n[a]. Linear cell index
+ * ((ix * ny + iy) * nvx + ivx) * nvy + ivy (int64).
+ *
+ * Pointers: "_dev" arguments are device memory of the context's device;
+ * "_host" arguments are host memory. Arguments documented as "host or device"
+ * are classified with cudaPointerGetAttributes. The caller owns every buffer it
+ * passes; the context owns its workspace and frees it in gh_destroy.
+ *
+ * Errors: every int-returning call returns GH_OK (0) or a negative GH_E* code
+ * and never throws. GH_EINVAL is returned before any GPU work for bad
+ * arguments; GH_ECUDA keeps the CUDA error text, readable with gh_last_error.
+ * Calls are ordered on the context's stream; calls that return host results
+ * synchronise that stream before returning. A context is not thread safe.
+ */
+#ifndef GH_H
+#define GH_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GH_API __attribute__((visibility("default")))
+#else
+#define GH_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define GH_OK        0
+#define GH_EINVAL   (-1)  /* bad argument (NULL, size out of range, ...)       */
+#define GH_ENOMEM   (-2)  /* device or pinned-host allocation failed           */
+#define GH_ECUDA    (-3)  /* a CUDA runtime call or kernel launch failed       */
+#define GH_ETIMEOUT (-4)  /* a bounded device-side wait gave up                */
+#define GH_ENOTSUP  (-5)  /* valid but unsupported combination                 */
+
+/* Map storage types (gh_make_maps, gh_score_grid). */
+#define GH_C64      0     /* complex float32 (8 bytes per bin)                 */
+
+/* Scoring methods (gh_detect). */
+#define GH_HOP      0     /* grid hopping (Sec. IV)                            */
+#define GH_EXACT    1     /* exact direct decision function (Sec. III)        */
+
+/* Kernel classes for gh_kernel_stats. */
+#define GH_K_RANGE_FFT   0
+#define GH_K_DOPPLER_FFT 1
+#define GH_K_COORD       2
+#define GH_K_HOP_SCORE   3
+#define GH_K_ARGMAX      4
+#define GH_K_BOMP        5
+#define GH_K_EXACT_S1    6
+#define GH_K_EXACT_S2    7
+#define GH_K_SYNTH       8
+#define GH_K_COUNT       9
+
+/* Size limits checked by every entry point (GH_EINVAL beyond them). */
+#define GH_MAX_Q        64
+#define GH_MIN_M        4       /* Ms, Mc: powers of two in [GH_MIN_M, GH_MAX_M] */
+#define GH_MAX_M        4096
+#define GH_MAX_NFFT     8192    /* pad*Ms and pad*Mc at most this               */
+#define GH_MAX_K        16      /* BOMP iterations                              */
+
+/* FMCW frame parameters (Sec. II). pad: zero-padding factor of both FFT axes,
+ * a power of two in [1, 16]. */
+typedef struct gh_radar {
+    double  f0;        /* carrier frequency [Hz]          */
+    double  B;         /* chirp bandwidth [Hz]            */
+    double  Tc;        /* chirp duration [s]              */
+    int32_t Ms;        /* samples per chirp               */
+    int32_t Mc;        /* chirps per frame                */
+    int32_t pad;       /* zero-padding factor             */
+    int32_t reserved;  /* must be 0                       */
+} gh_radar;
+
+/* Cell-centred 4D grid (x [m], y [m], vx [m/s], vy [m/s]); step > 0, n >= 1,
+ * total cells < 2^62. */
+typedef struct gh_grid {
+    double  lo[4];
+    double  step[4];
+    int32_t n[4];
+} gh_grid;
+
+typedef struct gh_ctx gh_ctx;
+
+/* Create a context on CUDA device `device`. `stream` is a cudaStream_t to run
+ * on (NULL: the context creates and owns a non-blocking stream). */
+GH_API int gh_create(gh_ctx** ctx, int32_t device, void* stream);
+/* Free the context, its workspace and (if owned) its stream. NULL is a no-op. */
+GH_API void gh_destroy(gh_ctx* ctx);
+/* Static text for a status code. */
+GH_API const char* gh_status_str(int32_t status);
+/* Text of the last error recorded in the context ("" if none). */
+GH_API const char* gh_last_error(const gh_ctx* ctx);
+
+/*
+ * gh_make_maps - zero-padded 2D DFT range-Doppler maps of every receiver
+ * (Sec. III: the 2D FFT of Y_q; Sec. IV: bin i is the correlation with the
+ * atom at the FFT's i-th grid frequency).
+ *   maps[q][i][j] = exp(j pi (i/Nr)(Ms-1)) *
+ *                   sum_mc sum_m Y[q][mc][m] exp(-j 2 pi (j mc/Nd + i m/Nr))
+ * The range-centring factor makes bin (i, j) the correlation with the centred
+ * atom exp(j 2 pi r (m - (Ms-1)/2)), whose Gram is real (used by the polar
+ * interpolation of gh_score_grid).
+ *   Y_dev    : device, complex float32 [Q][Mc][Ms]
+ *   maps_dev : device, complex float32 [Q][Nr][Nd] (written; map_dtype GH_C64)
+ * No host synchronisation.
+ */
+GH_API int gh_make_maps(gh_ctx* ctx, const gh_radar* radar, int32_t Q,
+                 const void* Y_dev, void* maps_dev, int32_t map_dtype);
+
+/*
+ * gh_score_grid - grid-hopping score of every cell and its argmax (Sec. IV,
+ * Eq. 5, with the sum over receivers of Eq. 3):
+ *   S(x, v) = sum_q | sum_{k=-1,0,1} c_k(tau_q) maps[q][(i_q+k) mod Nr][j_q] |^2
+ * where rho_q = Nr * r_q(x), i_q = floor(rho_q + 1/2), tau_q = rho_q - i_q,
+ * c_k are the three-bin polar interpolation coefficients (range axis) and
+ * j_q = floor(Nd * u_q(x, v) + 1/2) mod Nd is the nearest Doppler bin (single
+ * index, Sec. IV). Bin decisions i_q and j_q are taken in float64; scores
+ * accumulate in float32. Range reads that wrap around the map carry the
+ * centring phase of the unwrapped index.
+ *   tx_host      : host, double[2]
+ *   rx_host      : host, double[2*Q]
+ *   maps_dev     : device, from gh_make_maps
+ *   scores_dev   : device float[ncells] or NULL (argmax only)
+ *   best_cell    : host int64, argmax (ties: smallest index); may be NULL
+ *   best_score   : host float, its score; may be NULL
+ * Synchronises the stream when best_cell or best_score is non-NULL.
+ */
+GH_API int gh_score_grid(gh_ctx* ctx, const gh_radar* radar, const double* tx_host,
+                  const double* rx_host, int32_t Q, const void* maps_dev,
+                  int32_t map_dtype, const gh_grid* grid, float* scores_dev,
+                  int64_t* best_cell, float* best_score);
+
+/*
+ * gh_direct_exact - exact direct decision function of every cell (Sec. III,
+ * the joint location-velocity form behind Eqs. 3-4):
+ *   S(x, v) = sum_q | <Y_q, b(u_q(x, v)) (x) a(r_q(x))> |^2,  <y, a> = sum y conj(a)
+ * computed as two contractions: P_q[x][mc] = sum_m Y[q][mc][m] conj(a_m(r_q(x)))
+ * (the g_q of Eq. 4), then per (x, q) the Doppler correlation of P_q with the
+ * separable atom b_mc(u) = exp(j2pi k wx vx mc) exp(j2pi k wy vy mc), k = f0 Tc/c.
+ *   Y_host_or_dev: complex float32 [Q][Mc][Ms], host or device
+ *   scores_dev   : device float[ncells] or NULL
+ *   best_cell, best_score: as gh_score_grid
+ */
+GH_API int gh_direct_exact(gh_ctx* ctx, const gh_radar* radar, const double* tx_host,
+                    const double* rx_host, int32_t Q, const void* Y_host_or_dev,
+                    const gh_grid* grid, float* scores_dev, int64_t* best_cell,
+                    float* best_score);
+
+/*
+ * gh_detect - K iterations of block orthogonal matching pursuit (BOMP, named
+ * in the paper's acronym list; multi-target iterative direct detection is its
+ * stated future work, Sec. VI). A block is the Q per-receiver atoms of one grid
+ * cell with independent amplitudes. Iteration k:
+ *   1. score the residual on the grid (method GH_HOP: maps + gh_score_grid;
+ *      GH_EXACT: gh_direct_exact), cells already selected excluded;
+ *   2. append the argmax cell;
+ *   3. per receiver, solve the float64 least-squares problem for the
+ *      amplitudes of all selected atoms (at their exact r, u) against Y;
+ *   4. residual R_q = Y_q - sum_t alpha_{t,q} b(u_{t,q}) (x) a(r_{t,q}).
+ *   Y_host_or_dev : complex float32 [Q][Mc][Ms], host or device
+ *   cells_host    : host int64[K], selected cells in order
+ *   scores_host   : host float[K], residual score at each selected cell (may be NULL)
+ *   alpha_host    : host double[K][Q][2] (re, im) amplitudes multiplying the
+ *                   atoms b(u) (x) a(r) of Sec. II, from the last solve (may be NULL)
+ * All K iterations run on the device without host round trips; the stream is
+ * synchronised once at the end. 1 <= K <= min(GH_MAX_K, ncells).
+ */
+GH_API int gh_detect(gh_ctx* ctx, int32_t method, const gh_radar* radar,
+              const double* tx_host, const double* rx_host, int32_t Q,
+              const void* Y_host_or_dev, const gh_grid* grid, int32_t K,
+              int64_t* cells_host, float* scores_host, double* alpha_host);
+
+/*
+ * gh_synth - synthetic measurement from the signal model (Sec. II, Eq.
+ * general-model): Y_q = sum_t alpha_{t,q} b(u_q(x_t, v_t)) (x) a(r_q(x_t)) + W_q.
+ *   targets_host : host double[T][4] (x, y, vx, vy)
+ *   alpha_host   : host double[T][Q][2] (re, im)
+ *   noise_dev    : device complex float32 [Q][Mc][Ms] added to Y, or NULL
+ *   Y_dev        : device complex float32 [Q][Mc][Ms] (written)
+ * Phases are reduced in float64 before a float32 sincos. 0 <= T <= 64.
+ */
+GH_API int gh_synth(gh_ctx* ctx, const gh_radar* radar, const double* tx_host,
+             const double* rx_host, int32_t Q, int32_t T,
+             const double* targets_host, const double* alpha_host,
+             const void* noise_dev, void* Y_dev);
+
+/*
+ * gh_coord_table - the coordinate mapping of the hopping scorer for every
+ * (ix, iy, q), copied to the host (diagnostic; Eq. 1 and the polar
+ * coefficients of Sec. IV):
+ *   ibin_host  : host int32[nx][ny][Q]   nearest range bin i_q (unwrapped)
+ *   tau_host   : host double[nx][ny][Q]  fractional offset tau_q
+ *   coef_host  : host float[nx][ny][Q][3] polar coefficients c_{-1}, c_0, c_{+1}
+ *   w_host     : host double[nx][ny][Q][2] bistatic gradient w_q (may be NULL)
+ */
+GH_API int gh_coord_table(gh_ctx* ctx, const gh_radar* radar, const double* tx_host,
+                   const double* rx_host, int32_t Q, const gh_grid* grid,
+                   int32_t* ibin_host, double* tau_host, float* coef_host,
+                   double* w_host);
+
+/*
+ * Instrumentation. gh_set_timing(ctx, mask) brackets every launch of the
+ * kernel classes whose bit (1 << GH_K_*) is set in `mask` with CUDA events on
+ * the context's stream (mask 0: off; -1: all classes). gh_kernel_stats
+ * returns, for kernel class `kind`, the summed device time of the timed
+ * launches [ms] and their count (it synchronises the stream).
+ * gh_reset_stats clears both. gh_launch_count returns the number of kernels
+ * the context has launched.
+ */
+GH_API int     gh_set_timing(gh_ctx* ctx, int32_t mask);
+GH_API int     gh_kernel_stats(gh_ctx* ctx, int32_t kind, double* ms_total, int64_t* launches);
+GH_API int     gh_reset_stats(gh_ctx* ctx);
+GH_API int64_t gh_launch_count(const gh_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GH_H */

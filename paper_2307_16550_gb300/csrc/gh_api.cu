@@ -1,0 +1,569 @@
+// C-ABI entry points of libgh: argument validation, context and workspace
+// management, launch bookkeeping and the orchestration of the kernels.
+#include <math.h>
+#include <stdarg.h>
+#include <string.h>
+
+#include "gh_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+int gh_fail(gh_ctx* ctx, int status, const char* fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return status;
+}
+
+int gh_fail_cuda(gh_ctx* ctx, cudaError_t e, const char* what, const char* file, int line) {
+    const char* base = strrchr(file, '/');
+    gh_fail(ctx, GH_ECUDA, "%s: %s (%s:%d)", what, cudaGetErrorString(e), base ? base + 1 : file, line);
+    return e == cudaErrorMemoryAllocation ? GH_ENOMEM : GH_ECUDA;
+}
+
+extern "C" const char* gh_status_str(int32_t status) {
+    switch (status) {
+        case GH_OK: return "ok";
+        case GH_EINVAL: return "invalid argument";
+        case GH_ENOMEM: return "out of memory";
+        case GH_ECUDA: return "CUDA error";
+        case GH_ETIMEOUT: return "device wait timed out";
+        case GH_ENOTSUP: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char* gh_last_error(const gh_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+// ---------------------------------------------------------------------------
+// Device guard: makes the context's device current for the duration of a call.
+// ---------------------------------------------------------------------------
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+extern "C" int gh_create(gh_ctx** out, int32_t device, void* stream) {
+    if (!out) return GH_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return GH_ECUDA;
+    if (device < 0 || device >= ndev) return GH_EINVAL;
+    gh_ctx* ctx = new (std::nothrow) gh_ctx();
+    if (!ctx) return GH_ENOMEM;
+    ctx->device = device;
+    DeviceGuard g(device);
+    if (!g.ok) {
+        delete ctx;
+        return GH_ECUDA;
+    }
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete ctx;
+        return GH_ECUDA;
+    }
+    ctx->num_sms = v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
+        delete ctx;
+        return GH_ECUDA;
+    }
+    ctx->smem_optin = (size_t)v;
+    if (stream) {
+        ctx->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return GH_ECUDA;
+        }
+        ctx->own_stream = true;
+    }
+    *out = ctx;
+    return GH_OK;
+}
+
+extern "C" void gh_destroy(gh_ctx* ctx) {
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& t : ctx->pending) {
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
+    for (auto ev : ctx->event_pool) cudaEventDestroy(ev);
+    for (int i = 0; i < WS_COUNT; ++i)
+        if (ctx->ws[i]) cudaFree(ctx->ws[i]);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+int gh_ws(gh_ctx* ctx, WsSlot slot, size_t bytes, void** p) {
+    if (bytes == 0) bytes = 256;
+    if (ctx->ws_bytes[slot] < bytes) {
+        if (ctx->ws[slot]) {
+            GH_CUDA(cudaStreamSynchronize(ctx->stream));
+            GH_CUDA(cudaFree(ctx->ws[slot]));
+            ctx->ws[slot] = nullptr;
+            ctx->ws_bytes[slot] = 0;
+        }
+        size_t want = (bytes + 4095) & ~(size_t)4095;
+        GH_CUDA(cudaMalloc(&ctx->ws[slot], want));
+        ctx->ws_bytes[slot] = want;
+        if (slot == WS_TWIDDLE) ctx->tw_n[0] = ctx->tw_n[1] = 0;
+    }
+    *p = ctx->ws[slot];
+    return GH_OK;
+}
+
+int gh_pinned(gh_ctx* ctx, size_t bytes, void** p) {
+    if (ctx->pinned_bytes < bytes) {
+        if (ctx->pinned) {
+            GH_CUDA(cudaStreamSynchronize(ctx->stream));
+            cudaFreeHost(ctx->pinned);
+            ctx->pinned = nullptr;
+            ctx->pinned_bytes = 0;
+        }
+        size_t want = (bytes + 4095) & ~(size_t)4095;
+        GH_CUDA(cudaMallocHost(&ctx->pinned, want));
+        ctx->pinned_bytes = want;
+    }
+    *p = ctx->pinned;
+    return GH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Launch bookkeeping
+// ---------------------------------------------------------------------------
+static cudaEvent_t take_event(gh_ctx* ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t ev = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return ev;
+    }
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+    return ev;
+}
+
+void gh_launch_begin(gh_ctx* ctx, int kind, cudaEvent_t* start) {
+    *start = nullptr;
+    if (!((ctx->timing >> kind) & 1u)) return;
+    *start = take_event(ctx);
+    if (*start) cudaEventRecord(*start, ctx->stream);
+}
+
+int gh_launch_end(gh_ctx* ctx, int kind, cudaEvent_t start, const char* name) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        if (start) ctx->event_pool.push_back(start);
+        return gh_fail_cuda(ctx, e, name, __FILE__, __LINE__);
+    }
+    ctx->launches++;
+    if (start) {
+        cudaEvent_t stop = take_event(ctx);
+        if (stop) {
+            cudaEventRecord(stop, ctx->stream);
+            ctx->pending.push_back({kind, start, stop});
+        } else {
+            ctx->event_pool.push_back(start);
+        }
+    }
+    return GH_OK;
+}
+
+static int drain_timing(gh_ctx* ctx) {
+    if (ctx->pending.empty()) return GH_OK;
+    GH_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (auto& t : ctx->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess) {
+            ctx->ms[t.kind] += ms;
+            ctx->nlaunch[t.kind] += 1;
+        }
+        ctx->event_pool.push_back(t.start);
+        ctx->event_pool.push_back(t.stop);
+    }
+    ctx->pending.clear();
+    return GH_OK;
+}
+
+extern "C" int gh_set_timing(gh_ctx* ctx, int32_t mask) {
+    if (!ctx) return GH_EINVAL;
+    ctx->timing = (uint32_t)mask;
+    return GH_OK;
+}
+
+extern "C" int gh_kernel_stats(gh_ctx* ctx, int32_t kind, double* ms_total, int64_t* launches) {
+    if (!ctx || kind < 0 || kind >= GH_K_COUNT) return GH_EINVAL;
+    DeviceGuard g(ctx->device);
+    GH_TRY(drain_timing(ctx));
+    if (ms_total) *ms_total = ctx->ms[kind];
+    if (launches) *launches = ctx->nlaunch[kind];
+    return GH_OK;
+}
+
+extern "C" int gh_reset_stats(gh_ctx* ctx) {
+    if (!ctx) return GH_EINVAL;
+    DeviceGuard g(ctx->device);
+    GH_TRY(drain_timing(ctx));
+    for (int i = 0; i < GH_K_COUNT; ++i) {
+        ctx->ms[i] = 0;
+        ctx->nlaunch[i] = 0;
+    }
+    return GH_OK;
+}
+
+extern "C" int64_t gh_launch_count(const gh_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+// ---------------------------------------------------------------------------
+// Validation
+// ---------------------------------------------------------------------------
+static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int gh_check_radar(gh_ctx* ctx, const gh_radar* r, int32_t Q, Dims* d) {
+    if (!r) return gh_fail(ctx, GH_EINVAL, "radar is NULL");
+    if (Q < 1 || Q > GH_MAX_Q) return gh_fail(ctx, GH_EINVAL, "Q=%d outside [1, %d]", Q, GH_MAX_Q);
+    if (!is_pow2(r->Ms) || r->Ms < GH_MIN_M || r->Ms > GH_MAX_M)
+        return gh_fail(ctx, GH_EINVAL, "Ms=%d must be a power of two in [%d, %d]", r->Ms, GH_MIN_M, GH_MAX_M);
+    if (!is_pow2(r->Mc) || r->Mc < GH_MIN_M || r->Mc > GH_MAX_M)
+        return gh_fail(ctx, GH_EINVAL, "Mc=%d must be a power of two in [%d, %d]", r->Mc, GH_MIN_M, GH_MAX_M);
+    if (!is_pow2(r->pad) || r->pad > 16)
+        return gh_fail(ctx, GH_EINVAL, "pad=%d must be a power of two in [1, 16]", r->pad);
+    if ((int64_t)r->pad * r->Ms > GH_MAX_NFFT || (int64_t)r->pad * r->Mc > GH_MAX_NFFT)
+        return gh_fail(ctx, GH_EINVAL, "pad*Ms and pad*Mc must be at most %d", GH_MAX_NFFT);
+    if (r->reserved != 0) return gh_fail(ctx, GH_EINVAL, "radar.reserved must be 0");
+    if (!(r->f0 > 0) || !(r->B > 0) || !(r->Tc > 0) || !isfinite(r->f0) || !isfinite(r->B) || !isfinite(r->Tc))
+        return gh_fail(ctx, GH_EINVAL, "f0, B, Tc must be finite and positive");
+    d->Q = Q;
+    d->Ms = r->Ms;
+    d->Mc = r->Mc;
+    d->pad = r->pad;
+    d->Nr = r->pad * r->Ms;
+    d->Nd = r->pad * r->Mc;
+    return GH_OK;
+}
+
+int gh_check_grid(gh_ctx* ctx, const gh_grid* g, Dims* d) {
+    if (!g) return gh_fail(ctx, GH_EINVAL, "grid is NULL");
+    int64_t cells = 1;
+    for (int a = 0; a < 4; ++a) {
+        if (g->n[a] < 1) return gh_fail(ctx, GH_EINVAL, "grid.n[%d]=%d must be >= 1", a, g->n[a]);
+        if (!(g->step[a] > 0) || !isfinite(g->step[a]) || !isfinite(g->lo[a]))
+            return gh_fail(ctx, GH_EINVAL, "grid.step[%d] must be finite and > 0, lo finite", a);
+        if (cells > ((int64_t)1 << 62) / g->n[a]) return gh_fail(ctx, GH_EINVAL, "grid has >= 2^62 cells");
+        cells *= g->n[a];
+    }
+    d->nx = g->n[0];
+    d->ny = g->n[1];
+    d->nvx = g->n[2];
+    d->nvy = g->n[3];
+    d->nxy = (int64_t)g->n[0] * g->n[1];
+    d->nv = (int64_t)g->n[2] * g->n[3];
+    d->ncells = cells;
+    return GH_OK;
+}
+
+int gh_check_positions(gh_ctx* ctx, const double* tx, const double* rx, int32_t Q) {
+    if (!tx || !rx) return gh_fail(ctx, GH_EINVAL, "tx or rx is NULL");
+    for (int i = 0; i < 2; ++i)
+        if (!isfinite(tx[i])) return gh_fail(ctx, GH_EINVAL, "tx not finite");
+    for (int i = 0; i < 2 * Q; ++i)
+        if (!isfinite(rx[i])) return gh_fail(ctx, GH_EINVAL, "rx not finite");
+    return GH_OK;
+}
+
+int gh_is_device_ptr(gh_ctx* ctx, const void* p) {
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return gh_fail(ctx, GH_EINVAL, "cannot classify pointer %p: %s", p, cudaGetErrorString(e));
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+        if (at.device != ctx->device && at.type == cudaMemoryTypeDevice)
+            return gh_fail(ctx, GH_EINVAL, "device pointer belongs to device %d, context is on %d", at.device,
+                           ctx->device);
+        return 1;
+    }
+    return 0;
+}
+
+void gh_fill_geo(GeoParams* g, const gh_radar* radar, const double* tx, const double* rx, int32_t Q,
+                 const gh_grid* grid) {
+    memset(g, 0, sizeof(*g));
+    g->tx[0] = tx[0];
+    g->tx[1] = tx[1];
+    for (int i = 0; i < 2 * Q; ++i) g->rx[i] = rx[i];
+    volatile double c = GH_C_LIGHT;  // keep the two roundings of (B*d)/(c*Ms) and (f0*Tc)/c
+    g->B = radar->B;
+    g->cMs = c * (double)radar->Ms;
+    double f0Tc = radar->f0 * radar->Tc;
+    g->kappa = f0Tc / c;
+    if (grid) {
+        for (int a = 0; a < 4; ++a) {
+            g->lo[a] = grid->lo[a];
+            g->step[a] = grid->step[a];
+            g->n[a] = grid->n[a];
+        }
+    }
+    g->Q = Q;
+    g->Ms = radar->Ms;
+    g->Mc = radar->Mc;
+    g->Nr = radar->pad * radar->Ms;
+    g->Nd = radar->pad * radar->Mc;
+}
+
+// Stages a host-or-device measurement in device memory.
+static int stage_Y(gh_ctx* ctx, const Dims& d, const void* Y, const float2** Ydev) {
+    if (!Y) return gh_fail(ctx, GH_EINVAL, "Y is NULL");
+    int dev = gh_is_device_ptr(ctx, Y);
+    if (dev < 0) return dev;
+    if (dev) {
+        *Ydev = (const float2*)Y;
+        return GH_OK;
+    }
+    size_t bytes = (size_t)d.Q * d.Mc * d.Ms * sizeof(float2);
+    void* p;
+    GH_TRY(gh_ws(ctx, WS_Y, bytes, &p));
+    GH_CUDA(cudaMemcpyAsync(p, Y, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    *Ydev = (const float2*)p;
+    return GH_OK;
+}
+
+static int read_result(gh_ctx* ctx, const ArgResult* res, int64_t* best_cell, float* best_score) {
+    if (!best_cell && !best_score) return GH_OK;
+    void* h;
+    GH_TRY(gh_pinned(ctx, sizeof(ArgResult), &h));
+    GH_CUDA(cudaMemcpyAsync(h, res, sizeof(ArgResult), cudaMemcpyDeviceToHost, ctx->stream));
+    GH_CUDA(cudaStreamSynchronize(ctx->stream));
+    const ArgResult* r = (const ArgResult*)h;
+    if (best_cell) *best_cell = r->cell;
+    if (best_score) *best_score = r->score;
+    return GH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Entry points
+// ---------------------------------------------------------------------------
+extern "C" int gh_make_maps(gh_ctx* ctx, const gh_radar* radar, int32_t Q, const void* Y_dev, void* maps_dev,
+                            int32_t map_dtype) {
+    if (!ctx) return GH_EINVAL;
+    Dims d = {};
+    GH_TRY(gh_check_radar(ctx, radar, Q, &d));
+    if (!Y_dev || !maps_dev) return gh_fail(ctx, GH_EINVAL, "Y_dev or maps_dev is NULL");
+    if (map_dtype != GH_C64) return gh_fail(ctx, GH_ENOTSUP, "map_dtype %d not supported", map_dtype);
+    DeviceGuard g(ctx->device);
+    int dv = gh_is_device_ptr(ctx, Y_dev);
+    if (dv < 0) return dv;
+    int dm = gh_is_device_ptr(ctx, maps_dev);
+    if (dm < 0) return dm;
+    if (!dv || !dm) return gh_fail(ctx, GH_EINVAL, "Y_dev and maps_dev must be device memory");
+    return gh_launch_maps(ctx, d, (const float2*)Y_dev, (float2*)maps_dev);
+}
+
+static int build_table(gh_ctx* ctx, const Dims& d, const GeoParams& geo, void** table) {
+    GH_TRY(gh_ws(ctx, WS_TABLE, gh_hop_table_bytes(d), table));
+    return gh_launch_coord(ctx, d, geo, *table, nullptr, nullptr, nullptr, nullptr);
+}
+
+extern "C" int gh_score_grid(gh_ctx* ctx, const gh_radar* radar, const double* tx_host, const double* rx_host,
+                             int32_t Q, const void* maps_dev, int32_t map_dtype, const gh_grid* grid,
+                             float* scores_dev, int64_t* best_cell, float* best_score) {
+    if (!ctx) return GH_EINVAL;
+    Dims d = {};
+    GH_TRY(gh_check_radar(ctx, radar, Q, &d));
+    GH_TRY(gh_check_grid(ctx, grid, &d));
+    GH_TRY(gh_check_positions(ctx, tx_host, rx_host, Q));
+    if (!maps_dev) return gh_fail(ctx, GH_EINVAL, "maps_dev is NULL");
+    if (map_dtype != GH_C64) return gh_fail(ctx, GH_ENOTSUP, "map_dtype %d not supported", map_dtype);
+    DeviceGuard dg(ctx->device);
+    int dm = gh_is_device_ptr(ctx, maps_dev);
+    if (dm < 0) return dm;
+    if (!dm) return gh_fail(ctx, GH_EINVAL, "maps_dev must be device memory");
+    if (scores_dev) {
+        int ds = gh_is_device_ptr(ctx, scores_dev);
+        if (ds < 0) return ds;
+        if (!ds) return gh_fail(ctx, GH_EINVAL, "scores_dev must be device memory");
+    }
+    GeoParams geo;
+    gh_fill_geo(&geo, radar, tx_host, rx_host, Q, grid);
+    void* table;
+    GH_TRY(build_table(ctx, d, geo, &table));
+    void* res;
+    GH_TRY(gh_ws(ctx, WS_RESULT, 64 * sizeof(ArgResult), &res));
+    GH_TRY(gh_launch_hop(ctx, d, geo, (const float2*)maps_dev, table, scores_dev, nullptr, 0, (ArgResult*)res));
+    return read_result(ctx, (const ArgResult*)res, best_cell, best_score);
+}
+
+extern "C" int gh_direct_exact(gh_ctx* ctx, const gh_radar* radar, const double* tx_host, const double* rx_host,
+                               int32_t Q, const void* Y, const gh_grid* grid, float* scores_dev,
+                               int64_t* best_cell, float* best_score) {
+    if (!ctx) return GH_EINVAL;
+    Dims d = {};
+    GH_TRY(gh_check_radar(ctx, radar, Q, &d));
+    GH_TRY(gh_check_grid(ctx, grid, &d));
+    GH_TRY(gh_check_positions(ctx, tx_host, rx_host, Q));
+    DeviceGuard dg(ctx->device);
+    if (scores_dev) {
+        int ds = gh_is_device_ptr(ctx, scores_dev);
+        if (ds < 0) return ds;
+        if (!ds) return gh_fail(ctx, GH_EINVAL, "scores_dev must be device memory");
+    }
+    const float2* Yd;
+    GH_TRY(stage_Y(ctx, d, Y, &Yd));
+    GeoParams geo;
+    gh_fill_geo(&geo, radar, tx_host, rx_host, Q, grid);
+    void* res;
+    GH_TRY(gh_ws(ctx, WS_RESULT, 64 * sizeof(ArgResult), &res));
+    GH_TRY(gh_launch_exact(ctx, d, geo, Yd, scores_dev, nullptr, 0, (ArgResult*)res));
+    return read_result(ctx, (const ArgResult*)res, best_cell, best_score);
+}
+
+extern "C" int gh_detect(gh_ctx* ctx, int32_t method, const gh_radar* radar, const double* tx_host,
+                         const double* rx_host, int32_t Q, const void* Y, const gh_grid* grid, int32_t K,
+                         int64_t* cells_host, float* scores_host, double* alpha_host) {
+    if (!ctx) return GH_EINVAL;
+    Dims d = {};
+    GH_TRY(gh_check_radar(ctx, radar, Q, &d));
+    GH_TRY(gh_check_grid(ctx, grid, &d));
+    GH_TRY(gh_check_positions(ctx, tx_host, rx_host, Q));
+    if (method != GH_HOP && method != GH_EXACT) return gh_fail(ctx, GH_EINVAL, "method %d unknown", method);
+    if (K < 1 || K > GH_MAX_K || K > d.ncells)
+        return gh_fail(ctx, GH_EINVAL, "K=%d outside [1, min(%d, ncells)]", K, GH_MAX_K);
+    if (!cells_host) return gh_fail(ctx, GH_EINVAL, "cells_host is NULL");
+    DeviceGuard dg(ctx->device);
+    const float2* Yd;
+    GH_TRY(stage_Y(ctx, d, Y, &Yd));
+    GeoParams geo;
+    gh_fill_geo(&geo, radar, tx_host, rx_host, Q, grid);
+
+    size_t ybytes = (size_t)d.Q * d.Mc * d.Ms * sizeof(float2);
+    size_t mbytes = (size_t)d.Q * d.Nr * d.Nd * sizeof(float2);
+    void *R, *maps = nullptr, *table = nullptr, *res, *bws;
+    GH_TRY(gh_ws(ctx, WS_R, ybytes, &R));
+    GH_TRY(gh_ws(ctx, WS_RESULT, 64 * sizeof(ArgResult), &res));
+    GH_TRY(gh_ws(ctx, WS_BOMP, gh_bomp_ws_bytes(d, K), &bws));
+    if (method == GH_HOP) {
+        GH_TRY(gh_ws(ctx, WS_MAPS, mbytes, &maps));
+        GH_TRY(build_table(ctx, d, geo, &table));
+    }
+    ArgResult* sel = (ArgResult*)res;  // sel[k] = selection of iteration k
+    // The scorer masks the selected cells: it reads sel[0..k).cell through
+    // this view (ArgResult starts with the int64 cell; stride handled below).
+    int64_t* mask;
+    GH_TRY(gh_ws(ctx, WS_DIAG, (size_t)GH_MAX_K * sizeof(int64_t) + 256, (void**)&mask));
+    const float2* cur = Yd;
+    for (int k = 0; k < K; ++k) {
+        if (method == GH_HOP) {
+            GH_TRY(gh_launch_maps(ctx, d, cur, (float2*)maps));
+            GH_TRY(gh_launch_hop(ctx, d, geo, (const float2*)maps, table, nullptr, mask, k, sel + k));
+        } else {
+            GH_TRY(gh_launch_exact(ctx, d, geo, cur, nullptr, mask, k, sel + k));
+        }
+        GH_TRY(gh_launch_bomp_iter(ctx, d, geo, Yd, (float2*)R, k, K, sel, bws));
+        // append the selected cell to the mask list (device to device)
+        GH_CUDA(cudaMemcpyAsync(mask + k, &sel[k].cell, sizeof(int64_t), cudaMemcpyDeviceToDevice, ctx->stream));
+        cur = (const float2*)R;
+    }
+    // results: selections and the final amplitudes
+    size_t sel_bytes = (size_t)K * sizeof(ArgResult);
+    size_t alpha_bytes = (size_t)K * d.Q * 2 * sizeof(double);
+    void* h;
+    GH_TRY(gh_pinned(ctx, sel_bytes + alpha_bytes, &h));
+    GH_CUDA(cudaMemcpyAsync(h, sel, sel_bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    // amplitudes live at the start of the BOMP workspace as double2 [K][Q]
+    GH_CUDA(cudaMemcpyAsync((char*)h + sel_bytes, bws, alpha_bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    GH_CUDA(cudaStreamSynchronize(ctx->stream));
+    const ArgResult* hs = (const ArgResult*)h;
+    for (int k = 0; k < K; ++k) {
+        cells_host[k] = hs[k].cell;
+        if (scores_host) scores_host[k] = hs[k].score;
+    }
+    if (alpha_host) memcpy(alpha_host, (char*)h + sel_bytes, alpha_bytes);
+    return GH_OK;
+}
+
+extern "C" int gh_synth(gh_ctx* ctx, const gh_radar* radar, const double* tx_host, const double* rx_host,
+                        int32_t Q, int32_t T, const double* targets_host, const double* alpha_host,
+                        const void* noise_dev, void* Y_dev) {
+    if (!ctx) return GH_EINVAL;
+    Dims d = {};
+    GH_TRY(gh_check_radar(ctx, radar, Q, &d));
+    GH_TRY(gh_check_positions(ctx, tx_host, rx_host, Q));
+    if (T < 0 || T > 64) return gh_fail(ctx, GH_EINVAL, "T=%d outside [0, 64]", T);
+    if (T > 0 && (!targets_host || !alpha_host)) return gh_fail(ctx, GH_EINVAL, "targets or alpha is NULL");
+    if (!Y_dev) return gh_fail(ctx, GH_EINVAL, "Y_dev is NULL");
+    for (int i = 0; i < 4 * T; ++i)
+        if (!isfinite(targets_host[i])) return gh_fail(ctx, GH_EINVAL, "targets not finite");
+    DeviceGuard dg(ctx->device);
+    int dy = gh_is_device_ptr(ctx, Y_dev);
+    if (dy < 0) return dy;
+    if (!dy) return gh_fail(ctx, GH_EINVAL, "Y_dev must be device memory");
+    if (noise_dev) {
+        int dn = gh_is_device_ptr(ctx, noise_dev);
+        if (dn < 0) return dn;
+        if (!dn) return gh_fail(ctx, GH_EINVAL, "noise_dev must be device memory");
+    }
+    GeoParams geo;
+    gh_fill_geo(&geo, radar, tx_host, rx_host, Q, nullptr);
+    size_t tb = (size_t)T * 4 * sizeof(double), ab = (size_t)T * Q * 2 * sizeof(double);
+    void* buf;
+    GH_TRY(gh_ws(ctx, WS_DIAG, tb + ab + 256, &buf));
+    if (T > 0) {
+        void* h;
+        GH_TRY(gh_pinned(ctx, tb + ab, &h));
+        GH_CUDA(cudaStreamSynchronize(ctx->stream));  // pinned buffer may be in use by an earlier copy
+        memcpy(h, targets_host, tb);
+        memcpy((char*)h + tb, alpha_host, ab);
+        GH_CUDA(cudaMemcpyAsync(buf, h, tb + ab, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    return gh_launch_synth(ctx, d, geo, T, (const double*)buf, (const float2*)noise_dev, (float2*)Y_dev);
+}
+
+extern "C" int gh_coord_table(gh_ctx* ctx, const gh_radar* radar, const double* tx_host, const double* rx_host,
+                              int32_t Q, const gh_grid* grid, int32_t* ibin_host, double* tau_host,
+                              float* coef_host, double* w_host) {
+    if (!ctx) return GH_EINVAL;
+    Dims d = {};
+    GH_TRY(gh_check_radar(ctx, radar, Q, &d));
+    GH_TRY(gh_check_grid(ctx, grid, &d));
+    GH_TRY(gh_check_positions(ctx, tx_host, rx_host, Q));
+    if (!ibin_host || !tau_host || !coef_host) return gh_fail(ctx, GH_EINVAL, "output is NULL");
+    if (d.nxy * d.Q > ((int64_t)1 << 28)) return gh_fail(ctx, GH_EINVAL, "table too large for diagnostics");
+    DeviceGuard dg(ctx->device);
+    GeoParams geo;
+    gh_fill_geo(&geo, radar, tx_host, rx_host, Q, grid);
+    size_t n = (size_t)d.nxy * d.Q;
+    size_t bytes = n * (sizeof(int32_t) + sizeof(double) + 3 * sizeof(float) + 2 * sizeof(double)) + 1024;
+    void *table, *diag;
+    GH_TRY(gh_ws(ctx, WS_TABLE, gh_hop_table_bytes(d), &table));
+    GH_TRY(gh_ws(ctx, WS_DIAG, bytes, &diag));
+    char* p = (char*)diag;
+    double* dtau = (double*)p;
+    double* dw = dtau + n;
+    int32_t* di = (int32_t*)(dw + 2 * n);
+    float* dc = (float*)(di + n);
+    GH_TRY(gh_launch_coord(ctx, d, geo, table, di, dtau, dc, dw));
+    GH_CUDA(cudaMemcpyAsync(ibin_host, di, n * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    GH_CUDA(cudaMemcpyAsync(tau_host, dtau, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    GH_CUDA(cudaMemcpyAsync(coef_host, dc, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    if (w_host) GH_CUDA(cudaMemcpyAsync(w_host, dw, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    GH_CUDA(cudaStreamSynchronize(ctx->stream));
+    return GH_OK;
+}

@@ -1,0 +1,218 @@
+// Internal declarations of libgh: context, workspace, launch bookkeeping and
+// the float64 geometry (Eq. 1) shared by the coordinate, exact-direct, BOMP
+// and synthesis kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <vector>
+
+#include "../../include/gh.h"
+
+#define GH_C_LIGHT 299792458.0
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+enum WsSlot {
+    WS_RANGE = 0,   // range-FFT intermediate [Q][Mc][Nr] complex64
+    WS_TABLE,       // hopping coordinate table
+    WS_PART,        // per-CTA argmax partials
+    WS_RESULT,      // small device results (argmax, BOMP selections)
+    WS_Y,           // staged measurement (host input) [Q][Mc][Ms]
+    WS_R,           // BOMP residual [Q][Mc][Ms]
+    WS_MAPS,        // maps of the residual [Q][Nr][Nd]
+    WS_BOMP,        // BOMP atoms, correlations, amplitudes
+    WS_EXACT_P,     // exact stage 1 output [Q][nxy][Mc] complex64
+    WS_DIAG,        // coordinate-table diagnostics
+    WS_TWIDDLE,     // FFT twiddle tables
+    WS_COUNT
+};
+
+struct TimedLaunch {
+    int kind;
+    cudaEvent_t start, stop;
+};
+
+struct gh_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    char err[512] = {0};
+
+    void* ws[WS_COUNT] = {nullptr};
+    size_t ws_bytes[WS_COUNT] = {0};
+    void* pinned = nullptr;
+    size_t pinned_bytes = 0;
+
+    // twiddle table currently in WS_TWIDDLE: sizes it holds
+    int tw_n[2] = {0, 0};
+
+    uint32_t timing = 0;  // bit mask over GH_K_* classes
+    std::vector<TimedLaunch> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double ms[GH_K_COUNT] = {0};
+    int64_t nlaunch[GH_K_COUNT] = {0};
+    int64_t launches = 0;
+};
+
+// Records a failed CUDA call in the context and returns GH_ECUDA.
+int gh_fail_cuda(gh_ctx* ctx, cudaError_t e, const char* what, const char* file, int line);
+int gh_fail(gh_ctx* ctx, int status, const char* fmt, ...);
+
+#define GH_CUDA(call)                                                              \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) return gh_fail_cuda(ctx, e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define GH_TRY(expr)                 \
+    do {                             \
+        int s_ = (expr);             \
+        if (s_ != GH_OK) return s_;  \
+    } while (0)
+
+// Grow-only workspace slot; returns GH_OK and sets *p.
+int gh_ws(gh_ctx* ctx, WsSlot slot, size_t bytes, void** p);
+int gh_pinned(gh_ctx* ctx, size_t bytes, void** p);
+
+// Launch bookkeeping: call gh_launch_begin before a kernel launch and
+// gh_launch_end right after it (checks the launch error, records events).
+void gh_launch_begin(gh_ctx* ctx, int kind, cudaEvent_t* start);
+int gh_launch_end(gh_ctx* ctx, int kind, cudaEvent_t start, const char* name);
+
+// ---------------------------------------------------------------------------
+// Argument validation shared by the entry points
+// ---------------------------------------------------------------------------
+struct Dims {
+    int Q, Ms, Mc, pad, Nr, Nd;
+    int nx, ny, nvx, nvy;
+    int64_t nxy, nv, ncells;
+};
+
+int gh_check_radar(gh_ctx* ctx, const gh_radar* radar, int32_t Q, Dims* d);
+int gh_check_grid(gh_ctx* ctx, const gh_grid* grid, Dims* d);
+int gh_check_positions(gh_ctx* ctx, const double* tx, const double* rx, int32_t Q);
+
+// Classifies a pointer: 1 = device-accessible, 0 = host, <0 = error status.
+int gh_is_device_ptr(gh_ctx* ctx, const void* p);
+
+// ---------------------------------------------------------------------------
+// Geometry parameters passed by value to kernels
+// ---------------------------------------------------------------------------
+struct GeoParams {
+    double tx[2];
+    double rx[2 * GH_MAX_Q];
+    double B, cMs;        // bandwidth and c*Ms (range: r = (B*d)/(c*Ms))
+    double kappa;         // (f0*Tc)/c (speed: u = kappa*(wx*vx + wy*vy))
+    double lo[4], step[4];
+    int32_t n[4];
+    int32_t Q, Ms, Mc, Nr, Nd;
+};
+
+void gh_fill_geo(GeoParams* g, const gh_radar* radar, const double* tx, const double* rx,
+                 int32_t Q, const gh_grid* grid);
+
+// float64 helpers with no contraction, so that every rounding matches the
+// documented expression order (bin decisions must agree with a plain float64
+// evaluation of the same expressions).
+__device__ __forceinline__ double gh_axis(double lo, double step, int i) {
+    return __dadd_rn(lo, __dmul_rn((double)i + 0.5, step));
+}
+
+__device__ __forceinline__ void gh_unit(double dx, double dy, double* n, double* ux, double* uy) {
+    double nn = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+    *n = nn;
+    if (nn < 1e-9) {
+        *ux = 0.0;
+        *uy = 0.0;
+    } else {
+        *ux = __ddiv_rn(dx, nn);
+        *uy = __ddiv_rn(dy, nn);
+    }
+}
+
+// Bistatic path d = |x - tx| + |x - rx| and gradient w (Eq. 1).
+__device__ __forceinline__ void gh_bistatic(const GeoParams& g, int q, double x, double y,
+                                            double* d, double* wx, double* wy) {
+    double n1, ux1, uy1, n2, ux2, uy2;
+    gh_unit(__dsub_rn(x, g.tx[0]), __dsub_rn(y, g.tx[1]), &n1, &ux1, &uy1);
+    gh_unit(__dsub_rn(x, g.rx[2 * q]), __dsub_rn(y, g.rx[2 * q + 1]), &n2, &ux2, &uy2);
+    *d = __dadd_rn(n1, n2);
+    *wx = __dadd_rn(ux1, ux2);
+    *wy = __dadd_rn(uy1, uy2);
+}
+
+// r = (B*d)/(c*Ms), cycles per sample.
+__device__ __forceinline__ double gh_range(const GeoParams& g, double d) {
+    return __ddiv_rn(__dmul_rn(g.B, d), g.cMs);
+}
+
+// u = kappa*(wx*vx + wy*vy), cycles per chirp.
+__device__ __forceinline__ double gh_speed(const GeoParams& g, double wx, double wy, double vx, double vy) {
+    return __dmul_rn(g.kappa, __dadd_rn(__dmul_rn(wx, vx), __dmul_rn(wy, vy)));
+}
+
+// Fraction of x (cycles) as an unsigned 64-bit fixed-point phase (2^64 = one
+// cycle). Integer products of such phases with sample indices wrap modulo one
+// cycle exactly, so large phase arguments are reduced without rounding.
+__device__ __forceinline__ uint64_t gh_phase_fix(double x) {
+    double f = x - floor(x);                       // [0, 1)
+    double s = f * 18446744073709551616.0;         // * 2^64
+    if (s >= 18446744073709551615.0) return 0ull;  // f rounded up to one cycle
+    return __double2ull_rz(s);
+}
+
+// sin/cos of 2*pi*phase for a fixed-point phase (top 32 bits used).
+__device__ __forceinline__ float2 gh_cis_fix(uint64_t ph) {
+    float t = (float)(uint32_t)(ph >> 32) * 4.656612873077392578125e-10f;  // 2^-31: turns * 2
+    float s, c;
+    sincospif(t, &s, &c);
+    return make_float2(c, s);
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
+// ---------------------------------------------------------------------------
+// Per-kernel launchers (one per .cu file)
+// ---------------------------------------------------------------------------
+struct ArgPartial {
+    float score;
+    int32_t pad;
+    int64_t cell;
+};
+
+// Result slot of an argmax: best cell and score.
+struct ArgResult {
+    int64_t cell;
+    float score;
+    int32_t valid;
+};
+
+int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, float2* maps);
+int gh_launch_coord(gh_ctx* ctx, const Dims& d, const GeoParams& g, void* table,
+                    int32_t* diag_i, double* diag_tau, float* diag_c, double* diag_w);
+size_t gh_hop_table_bytes(const Dims& d);
+int gh_launch_hop(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* maps,
+                  const void* table, float* scores, const int64_t* mask, int nmask,
+                  ArgResult* result);
+int gh_launch_argmax_finalize(gh_ctx* ctx, const ArgPartial* parts, int nparts, ArgResult* out);
+int gh_launch_exact(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y,
+                    float* scores, const int64_t* mask, int nmask, ArgResult* result);
+int gh_launch_synth(gh_ctx* ctx, const Dims& d, const GeoParams& g, int T,
+                    const double* targets_alpha_dev, const float2* noise, float2* Y);
+
+// BOMP iteration k of K (workspace of gh_bomp_ws_bytes(d, K) bytes; the
+// amplitudes, double2 [K][Q], sit at its start).
+int gh_launch_bomp_iter(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y,
+                        float2* R, int k, int K, const ArgResult* sel, void* bomp_ws);
+size_t gh_bomp_ws_bytes(const Dims& d, int K);

@@ -1,0 +1,291 @@
+"""Thin ctypes binding of libgh.so (include/gh.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels. Functions named ``gh_*`` mirror the C entry points one to one;
+``Context`` wraps them for convenience and allocates device buffers with
+PyTorch (plumbing only). There is no fallback: if the library is missing the
+first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libgh.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "gh.h")
+
+GH_OK, GH_EINVAL, GH_ENOMEM, GH_ECUDA, GH_ETIMEOUT, GH_ENOTSUP = 0, -1, -2, -3, -4, -5
+GH_C64 = 0
+GH_HOP, GH_EXACT = 0, 1
+(GH_K_RANGE_FFT, GH_K_DOPPLER_FFT, GH_K_COORD, GH_K_HOP_SCORE, GH_K_ARGMAX, GH_K_BOMP,
+ GH_K_EXACT_S1, GH_K_EXACT_S2, GH_K_SYNTH) = range(9)
+KERNEL_KINDS = {"range_fft": 0, "doppler_fft": 1, "coord": 2, "hop_score": 3, "argmax": 4,
+                "bomp": 5, "exact_s1": 6, "exact_s2": 7, "synth": 8}
+
+
+class GhRadar(ctypes.Structure):
+    _fields_ = [("f0", ctypes.c_double), ("B", ctypes.c_double), ("Tc", ctypes.c_double),
+                ("Ms", ctypes.c_int32), ("Mc", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class GhGrid(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 4), ("step", ctypes.c_double * 4), ("n", ctypes.c_int32 * 4)]
+
+
+class GhError(RuntimeError):
+    def __init__(self, func, status, detail):
+        super().__init__(f"{func} failed: {status} ({gh_status_str(status)}): {detail}")
+        self.status = status
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_PD = ctypes.POINTER(ctypes.c_double)
+
+_SIGNATURES = {
+    "gh_create": (_I32, [ctypes.POINTER(_P), _I32, _P]),
+    "gh_destroy": (None, [_P]),
+    "gh_status_str": (ctypes.c_char_p, [_I32]),
+    "gh_last_error": (ctypes.c_char_p, [_P]),
+    "gh_make_maps": (_I32, [_P, ctypes.POINTER(GhRadar), _I32, _P, _P, _I32]),
+    "gh_score_grid": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, _I32, ctypes.POINTER(GhGrid),
+                             _P, _P, _P]),
+    "gh_direct_exact": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, ctypes.POINTER(GhGrid), _P, _P, _P]),
+    "gh_detect": (_I32, [_P, _I32, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, ctypes.POINTER(GhGrid), _I32,
+                         _P, _P, _P]),
+    "gh_synth": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _I32, _P, _P, _P, _P]),
+    "gh_coord_table": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, ctypes.POINTER(GhGrid), _P, _P, _P, _P]),
+    "gh_set_timing": (_I32, [_P, _I32]),
+    "gh_kernel_stats": (_I32, [_P, _I32, _PD, ctypes.POINTER(ctypes.c_int64)]),
+    "gh_reset_stats": (_I32, [_P]),
+    "gh_launch_count": (ctypes.c_int64, [_P]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libgh.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgh.so not found at {path}: build it with "
+                           "`python -m paper_2307_16550_gb300.build` (there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def header_functions(path: str = HEADER):
+    """Names of the entry points include/gh.h declares."""
+    text = open(path).read()
+    return re.findall(r"^GH_API\s+[\w\s\*]+?\b(gh_\w+)\s*\(", text, flags=re.M)
+
+
+def gh_status_str(status: int) -> str:
+    return load().gh_status_str(status).decode()
+
+
+def _ptr(x):
+    """Raw address of a torch tensor, numpy array or None."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(x.ctypes.data)
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def radar_struct(radar) -> GhRadar:
+    return GhRadar(float(radar.f0), float(radar.B), float(radar.Tc), int(radar.Ms), int(radar.Mc),
+                   int(getattr(radar, "pad", 4)), 0)
+
+
+def grid_struct(grid) -> GhGrid:
+    g = GhGrid()
+    for a in range(4):
+        g.lo[a] = float(grid.lo[a])
+        g.step[a] = float(grid.step[a])
+        g.n[a] = int(grid.n[a])
+    return g
+
+
+def _f64(a, shape=None):
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None:
+        arr = arr.reshape(shape)
+    return arr
+
+
+class Context:
+    """A libgh context on one CUDA device (owns the library workspace)."""
+
+    def __init__(self, device: int = 0, stream="torch"):
+        """stream: "torch" (default) runs on PyTorch's current stream of the
+        device, so results are ordered with torch ops; None lets the library
+        create its own stream; or a torch.cuda.Stream / raw cudaStream_t."""
+        lib = load()
+        self._lib = lib
+        h = ctypes.c_void_p()
+        if isinstance(stream, str) and stream == "torch":
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        if stream is None:
+            s = None
+        else:
+            handle = int(getattr(stream, "cuda_stream", stream))
+            s = ctypes.c_void_p(handle if handle != 0 else 1)  # 0x1: cudaStreamLegacy
+        st = lib.gh_create(ctypes.byref(h), int(device), s)
+        if st != GH_OK:
+            raise GhError("gh_create", st, "")
+        self.handle = h
+        self.device = int(device)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self._lib.gh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, name, st):
+        if st != GH_OK:
+            raise GhError(name, st, self._lib.gh_last_error(self.handle).decode())
+
+    # -- entry points -----------------------------------------------------
+    def gh_make_maps(self, radar, Q, Y, maps, map_dtype=GH_C64):
+        self._check("gh_make_maps", self._lib.gh_make_maps(self.handle, ctypes.byref(radar_struct(radar)), int(Q),
+                                                           _ptr(Y), _ptr(maps), int(map_dtype)))
+
+    def gh_score_grid(self, radar, tx, rx, Q, maps, grid, scores=None, map_dtype=GH_C64):
+        txa, rxa = _f64(tx, (2,)), _f64(rx, (-1,))
+        cell = ctypes.c_int64(-1)
+        score = ctypes.c_float(0.0)
+        self._check("gh_score_grid", self._lib.gh_score_grid(
+            self.handle, ctypes.byref(radar_struct(radar)), _ptr(txa), _ptr(rxa), int(Q), _ptr(maps),
+            int(map_dtype), ctypes.byref(grid_struct(grid)), _ptr(scores), ctypes.byref(cell), ctypes.byref(score)))
+        return cell.value, score.value
+
+    def gh_direct_exact(self, radar, tx, rx, Q, Y, grid, scores=None):
+        txa, rxa = _f64(tx, (2,)), _f64(rx, (-1,))
+        cell = ctypes.c_int64(-1)
+        score = ctypes.c_float(0.0)
+        self._check("gh_direct_exact", self._lib.gh_direct_exact(
+            self.handle, ctypes.byref(radar_struct(radar)), _ptr(txa), _ptr(rxa), int(Q), _ptr(Y),
+            ctypes.byref(grid_struct(grid)), _ptr(scores), ctypes.byref(cell), ctypes.byref(score)))
+        return cell.value, score.value
+
+    def gh_detect(self, method, radar, tx, rx, Q, Y, grid, K):
+        txa, rxa = _f64(tx, (2,)), _f64(rx, (-1,))
+        cells = np.zeros(K, np.int64)
+        scores = np.zeros(K, np.float32)
+        alpha = np.zeros((K, Q, 2), np.float64)
+        self._check("gh_detect", self._lib.gh_detect(
+            self.handle, int(method), ctypes.byref(radar_struct(radar)), _ptr(txa), _ptr(rxa), int(Q), _ptr(Y),
+            ctypes.byref(grid_struct(grid)), int(K), _ptr(cells), _ptr(scores), _ptr(alpha)))
+        return cells, scores, alpha[..., 0] + 1j * alpha[..., 1]
+
+    def gh_synth(self, radar, tx, rx, Q, targets, alpha, noise, Y):
+        txa, rxa = _f64(tx, (2,)), _f64(rx, (-1,))
+        tg = _f64(targets, (-1, 4))
+        T = tg.shape[0]
+        al = np.ascontiguousarray(np.stack([np.real(alpha), np.imag(alpha)], axis=-1).astype(np.float64))
+        self._check("gh_synth", self._lib.gh_synth(
+            self.handle, ctypes.byref(radar_struct(radar)), _ptr(txa), _ptr(rxa), int(Q), int(T),
+            _ptr(tg) if T else None, _ptr(al) if T else None, _ptr(noise), _ptr(Y)))
+
+    def gh_coord_table(self, radar, tx, rx, Q, grid):
+        txa, rxa = _f64(tx, (2,)), _f64(rx, (-1,))
+        nx, ny = int(grid.n[0]), int(grid.n[1])
+        ib = np.zeros((nx, ny, Q), np.int32)
+        tau = np.zeros((nx, ny, Q), np.float64)
+        coef = np.zeros((nx, ny, Q, 3), np.float32)
+        w = np.zeros((nx, ny, Q, 2), np.float64)
+        self._check("gh_coord_table", self._lib.gh_coord_table(
+            self.handle, ctypes.byref(radar_struct(radar)), _ptr(txa), _ptr(rxa), int(Q),
+            ctypes.byref(grid_struct(grid)), _ptr(ib), _ptr(tau), _ptr(coef), _ptr(w)))
+        return ib, tau, coef, w
+
+    def gh_set_timing(self, enable):
+        """True: time every kernel class; False: none; a kind name, an int mask
+        or an iterable of kind names: only those classes."""
+        if enable is True:
+            mask = -1
+        elif enable is False or enable is None:
+            mask = 0
+        elif isinstance(enable, str):
+            mask = 1 << KERNEL_KINDS[enable]
+        elif isinstance(enable, int):
+            mask = enable
+        else:
+            mask = 0
+            for k in enable:
+                mask |= 1 << KERNEL_KINDS[k]
+        self._check("gh_set_timing", self._lib.gh_set_timing(self.handle, int(mask)))
+
+    def gh_kernel_stats(self, kind):
+        ms = ctypes.c_double(0)
+        n = ctypes.c_int64(0)
+        k = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
+        self._check("gh_kernel_stats", self._lib.gh_kernel_stats(self.handle, k, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def gh_reset_stats(self):
+        self._check("gh_reset_stats", self._lib.gh_reset_stats(self.handle))
+
+    def gh_launch_count(self) -> int:
+        return int(self._lib.gh_launch_count(self.handle))
+
+    # -- conveniences (allocate outputs with torch) -------------------------
+    def _torch(self):
+        import torch
+        return torch
+
+    def maps(self, radar, Y):
+        """Range-Doppler maps of a device measurement Y (complex64 [Q][Mc][Ms])."""
+        torch = self._torch()
+        Q = Y.shape[0]
+        out = torch.empty((Q, radar.pad * radar.Ms, radar.pad * radar.Mc), dtype=torch.complex64, device=Y.device)
+        self.gh_make_maps(radar, Q, Y, out)
+        return out
+
+    def scores(self, radar, tx, rx, maps, grid):
+        """Hopping scores of every cell (float32 [nx][ny][nvx][nvy]) and the argmax."""
+        torch = self._torch()
+        out = torch.empty(tuple(int(v) for v in grid.n), dtype=torch.float32, device=maps.device)
+        cell, score = self.gh_score_grid(radar, tx, rx, maps.shape[0], maps, grid, out)
+        return out, cell, score
+
+    def exact_scores(self, radar, tx, rx, Y, grid):
+        torch = self._torch()
+        out = torch.empty(tuple(int(v) for v in grid.n), dtype=torch.float32, device="cuda:%d" % self.device)
+        cell, score = self.gh_direct_exact(radar, tx, rx, Y.shape[0], Y, grid, out)
+        return out, cell, score
+
+    def synth(self, radar, tx, rx, targets, alpha, noise=None):
+        """Measurement of the signal model on the device (complex64 [Q][Mc][Ms])."""
+        torch = self._torch()
+        Q = np.asarray(rx).reshape(-1, 2).shape[0]
+        Y = torch.empty((Q, radar.Mc, radar.Ms), dtype=torch.complex64, device="cuda:%d" % self.device)
+        self.gh_synth(radar, tx, rx, Q, targets, alpha, noise, Y)
+        return Y

@@ -1,0 +1,62 @@
+"""GPU parity of the exact direct decision function (gh_direct_exact) against
+the FP64 oracle: full small and ragged grids, sampled (x, y) cells of the
+paper-shaped frame, host and device inputs."""
+import numpy as np
+import pytest
+
+from oracle import direct, hopping
+from paper_2307_16550_gb300 import scenes
+from tests.helpers import measurement64, rel_err, to_dev, top2_margin
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.mark.parametrize("seed", [1, 4])
+def test_tiny_full_grid(ctx, torch_cuda, seed):
+    sc = scenes.tiny_scene(seed)
+    Y32, Y = measurement64(sc)
+    ref = direct.scores_full(Y, sc.radar, sc.tx, sc.rx, sc.grid)
+    got, cell, score = ctx.exact_scores(sc.radar, sc.tx, sc.rx, to_dev(torch_cuda, Y32), sc.grid)
+    got = got.cpu().numpy()
+    assert rel_err(got, ref) < TOL
+    if top2_margin(ref) > 10 * TOL:
+        assert cell == hopping.argmax_cell(ref)
+
+
+def test_ragged_grid_host_input(ctx, torch_cuda):
+    radar = scenes.Radar(24e9, 250e6, 128e-6, 32, 64, 4)
+    grid = scenes.Grid.from_bounds((2, -1, -7, -13), (33, 27, 15, 9), (19, 23, 9, 14))
+    sc = scenes.custom_scene(8, radar, grid, Q=3, T=2, snr_db=0.0)
+    Y32, Y = measurement64(sc)
+    ref = direct.scores_full(Y, sc.radar, sc.tx, sc.rx, sc.grid)
+    out = torch_cuda.empty(tuple(grid.n), dtype=torch_cuda.float32, device="cuda:0")
+    cell, _ = ctx.gh_direct_exact(sc.radar, sc.tx, sc.rx, sc.Q, Y32, sc.grid, out)  # host Y
+    assert rel_err(out.cpu().numpy(), ref) < TOL
+    if top2_margin(ref) > 10 * TOL:
+        assert cell == hopping.argmax_cell(ref)
+
+
+def test_paper_frame_sampled_xy(ctx, torch_cuda):
+    sc = scenes.paper_frame(2)
+    Y32, Y = measurement64(sc)
+    got, cell, score = ctx.exact_scores(sc.radar, sc.tx, sc.rx, to_dev(torch_cuda, Y32), sc.grid)
+    got = got.cpu().numpy()
+    ix, iy, _, _ = sc.grid.unravel(cell)
+    xy = [(0, 0), (127, 127), (5, 90), (64, 3), (ix, iy)]
+    ref = direct.factored(Y, sc.radar, sc.tx, sc.rx, sc.grid, xy)
+    g = np.stack([got[a, b] for a, b in xy])
+    assert np.abs(g - ref).max() / ref.max() < TOL
+    # the picked cell is the best of its (x, y) cell in the oracle too
+    assert sc.grid.cell_index(ix, iy, *np.unravel_index(np.argmax(ref[-1]), ref[-1].shape)) == cell
+
+
+def test_exact_on_grid_noiseless_peak_value(ctx, torch_cuda):
+    """Cauchy-Schwarz equality at the true cell: S = (Ms Mc)^2 sum_q |alpha_q|^2."""
+    sc = scenes.tiny_scene(2, snr_db=None, on_grid=True)
+    Y32, _ = measurement64(sc)
+    cell, score = ctx.gh_direct_exact(sc.radar, sc.tx, sc.rx, sc.Q, to_dev(torch_cuda, Y32), sc.grid, None)
+    assert cell == sc.target_cells[0]
+    peak = (sc.radar.Ms * sc.radar.Mc) ** 2 * np.sum(np.abs(sc.alpha[0]) ** 2)
+    assert score == pytest.approx(peak, rel=1e-4)

@@ -1,0 +1,109 @@
+"""GPU parity of the grid-hopping scorer (gh_score_grid) and its coordinate
+mapping (gh_coord_table) against the FP64 oracle, from oracle-made maps and
+through the GPU's own maps, on full small grids, ragged grids and sampled
+rows of the paper-shaped frame."""
+import numpy as np
+import pytest
+
+from oracle import hopping, maps as omaps
+from paper_2307_16550_gb300 import scenes
+from tests.helpers import measurement64, rel_err, to_dev, top2_margin
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4  # max |S_gpu - S_oracle| / max S_oracle, float32 scores
+
+
+def _ragged():
+    radar = scenes.Radar(24e9, 250e6, 128e-6, 64, 32, 4)
+    grid = scenes.Grid.from_bounds((-3, 1, -12, -9), (37, 29, 14, 11), (41, 29, 13, 11))
+    return scenes.custom_scene(11, radar, grid, Q=5, T=2, snr_db=5.0, rx_box=((-5, 30), (-4, 2)))
+
+
+def _oracle_maps_dev(torch, Y, pad):
+    return to_dev(torch, omaps.centred_maps(Y, pad).astype(np.complex64))
+
+
+@pytest.mark.parametrize("make", [lambda: scenes.tiny_scene(1), lambda: scenes.paper_frame(2), _ragged])
+def test_coord_table_bit_exact(ctx, make):
+    sc = make()
+    ib, tau, coef, w = ctx.gh_coord_table(sc.radar, sc.tx, sc.rx, sc.Q, sc.grid)
+    ref = hopping.coord_table(sc.radar, sc.tx, sc.rx, sc.grid)
+    np.testing.assert_array_equal(ib, ref["i"])
+    np.testing.assert_array_equal(tau, ref["tau"])
+    np.testing.assert_array_equal(w[..., 0], ref["wx"])
+    np.testing.assert_array_equal(w[..., 1], ref["wy"])
+    np.testing.assert_allclose(coef, ref["c"], atol=2e-7)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_tiny_full_grid_from_oracle_maps(ctx, torch_cuda, seed):
+    sc = scenes.tiny_scene(seed)
+    Y32, Y = measurement64(sc)
+    ref = hopping.hop_scores(omaps.rd_maps(Y, 4), sc.radar, sc.tx, sc.rx, sc.grid)
+    got, cell, score = ctx.scores(sc.radar, sc.tx, sc.rx, _oracle_maps_dev(torch_cuda, Y, 4), sc.grid)
+    got = got.cpu().numpy()
+    assert rel_err(got, ref) < TOL
+    if top2_margin(ref) > 10 * TOL:
+        assert cell == hopping.argmax_cell(ref)
+    assert score == pytest.approx(got.reshape(-1)[cell])
+
+
+def test_ragged_grid_through_gpu_maps(ctx, torch_cuda):
+    sc = _ragged()
+    Y32, Y = measurement64(sc)
+    ref = hopping.hop_scores(omaps.rd_maps(Y, 4), sc.radar, sc.tx, sc.rx, sc.grid)
+    maps = ctx.maps(sc.radar, to_dev(torch_cuda, Y32))
+    got, cell, _ = ctx.scores(sc.radar, sc.tx, sc.rx, maps, sc.grid)
+    assert rel_err(got.cpu().numpy(), ref) < TOL
+    if top2_margin(ref) > 10 * TOL:
+        assert cell == hopping.argmax_cell(ref)
+
+
+def test_paper_frame_full_grid_bench_launch(ctx, torch_cuda):
+    """The paper-shaped frame (128 x 128 x 32 x 32 cells, Q = 4, Ms = 256,
+    Mc = 128) in the benchmark's launch configuration: every score and the
+    argmax against the oracle's full grid."""
+    sc = scenes.paper_frame(1)
+    Y32, Y = measurement64(sc)
+    ref = hopping.hop_scores(omaps.rd_maps(Y, 4), sc.radar, sc.tx, sc.rx, sc.grid)
+    maps = ctx.maps(sc.radar, to_dev(torch_cuda, Y32))
+    got, cell, score = ctx.scores(sc.radar, sc.tx, sc.rx, maps, sc.grid)
+    got = got.cpu().numpy()
+    assert rel_err(got, ref) < TOL
+    assert top2_margin(ref) > 10 * TOL
+    assert cell == hopping.argmax_cell(ref)
+    assert score == pytest.approx(ref.max(), rel=TOL)
+
+
+def test_argmax_without_scores_matches(ctx, torch_cuda):
+    sc = scenes.tiny_scene(5)
+    Y32, _ = measurement64(sc)
+    maps = ctx.maps(sc.radar, to_dev(torch_cuda, Y32))
+    _, c1, s1 = ctx.scores(sc.radar, sc.tx, sc.rx, maps, sc.grid)
+    c2, s2 = ctx.gh_score_grid(sc.radar, sc.tx, sc.rx, sc.Q, maps, sc.grid, None)
+    assert (c1, s1) == (c2, s2)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_noiseless_on_grid_target_peaks_on_true_cell(ctx, torch_cuda, seed):
+    sc = scenes.tiny_scene(seed, snr_db=None, on_grid=True)
+    Y32, _ = measurement64(sc)
+    maps = ctx.maps(sc.radar, to_dev(torch_cuda, Y32))
+    cell, _ = ctx.gh_score_grid(sc.radar, sc.tx, sc.rx, sc.Q, maps, sc.grid, None)
+    assert cell == sc.target_cells[0]
+
+
+def test_aliased_ranges_wrap_with_centring_sign(ctx, torch_cuda):
+    """Ms = 8 makes r exceed one cycle per sample for d > 9.6 m, so range rows
+    wrap around the map (several times); the wrapped reads carry the sign of
+    the centring phase. Pad 2 and an odd-sized velocity grid."""
+    radar = scenes.Radar(24e9, 250e6, 128e-6, 8, 16, 2)
+    grid = scenes.Grid.from_bounds((0, 0, -10, -10), (30, 30, 10, 10), (24, 24, 5, 7))
+    sc = scenes.custom_scene(4, radar, grid, Q=3, T=2, snr_db=10.0)
+    Y32, Y = measurement64(sc)
+    ref = hopping.hop_scores(omaps.rd_maps(Y, 2), sc.radar, sc.tx, sc.rx, sc.grid)
+    table = hopping.coord_table(sc.radar, sc.tx, sc.rx, sc.grid)
+    assert table["i"].max() > 2 * 16  # really wraps
+    got, _, _ = ctx.scores(sc.radar, sc.tx, sc.rx, ctx.maps(sc.radar, to_dev(torch_cuda, Y32)), sc.grid)
+    assert rel_err(got.cpu().numpy(), ref) < TOL
