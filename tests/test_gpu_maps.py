@@ -54,8 +54,7 @@ def test_synth_matches_oracle_measurement(ctx, torch_cuda, kind):
     ref = model.measurement(sc)
     noise = to_dev(torch_cuda, sc.noise.astype(np.complex64))
     got = ctx.synth(sc.radar, sc.tx, sc.rx, sc.targets, sc.alpha, noise).cpu().numpy()
-    assert rel_err(np.abs(got - ref), np.abs(ref)) < 1e-5
-    assert np.abs(got - ref).max() < 1e-5 * np.abs(sc.alpha).max() * sc.targets.shape[0] + 1e-6
+    assert np.abs(got - ref).max() < 1e-5 * np.abs(ref).max()
 
 
 def test_synth_without_noise_or_targets(ctx, torch_cuda):
