@@ -227,6 +227,41 @@ GH_API int gh_coord_table(gh_ctx* ctx, const gh_radar* radar, const double* tx_h
                    double* w_host);
 
 /*
+ * gh_score_grid_noalloc - the same scores and argmax as gh_score_grid, for
+ * callers that must not allocate device memory. The paper has no counterpart:
+ * this entry point exists for the software around it. Typical such callers are
+ * a real-time radar pipeline with a deadline per frame, where cudaMalloc and
+ * cudaFree may block on or synchronise with work already queued on the GPU,
+ * and a plug-in inside a host framework that owns the device memory budget
+ * and forbids allocations outside its own pool.
+ *
+ * It needs no context and calls no cudaMalloc, cudaFree, cudaMallocHost or
+ * other allocating routine. Its scratch (coordinate table, argmax partials,
+ * result slot) is one fixed 8 MiB array in device memory, reserved on every
+ * GPU that loads the library until the process exits; problems with
+ * nx * ny * Q > GH_NOALLOC_MAX_XYQ return GH_EINVAL. The array's device
+ * address is looked up on the first call made on each device (with that device
+ * current); make that first call before any stream capture. All calls share
+ * the array and leave their contents in it: calls whose GPU work overlaps (on
+ * two streams or from two host threads) race and must be serialised by the
+ * caller.
+ *   stream       : cudaStream_t to run on (NULL: the legacy default stream); the
+ *                  current device must own maps_dev and scores_dev
+ *   maps_dev     : device, complex float32 [Q][Nr][Nd] from gh_make_maps
+ *   scores_dev   : device float[ncells] or NULL
+ *   best_cell, best_score: host, may be NULL; when either is given the call
+ *                  copies the result with cudaMemcpyAsync and synchronises the stream
+ * Errors: GH_EINVAL for bad arguments or a problem beyond the scratch size,
+ * GH_ENOTSUP when shared memory is too small, GH_ECUDA for CUDA failures (no
+ * error text is kept: there is no context).
+ */
+#define GH_NOALLOC_MAX_XYQ 98304   /* max nx * ny * Q of gh_score_grid_noalloc */
+GH_API int gh_score_grid_noalloc(void* stream, const gh_radar* radar,
+                                 const double* tx_host, const double* rx_host,
+                                 int32_t Q, const void* maps_dev, const gh_grid* grid,
+                                 float* scores_dev, int64_t* best_cell, float* best_score);
+
+/*
  * Instrumentation. gh_set_timing(ctx, mask) brackets every launch of the
  * kernel classes whose bit (1 << GH_K_*) is set in `mask` with CUDA events on
  * the context's stream (mask 0: off; -1: all classes). gh_kernel_stats

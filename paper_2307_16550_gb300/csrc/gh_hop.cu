@@ -372,3 +372,147 @@ int gh_launch_hop(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* 
     if (need <= 16) return launch_hop_t<16>(ctx, d, hp, maps, t, scores, mask, nmask, result);
     return launch_hop_t<32>(ctx, d, hp, maps, t, scores, mask, nmask, result);
 }
+
+// ---------------------------------------------------------------------------
+// gh_score_grid_noalloc: the hopping score and argmax of gh_score_grid for
+// callers that cannot allocate device memory. The paper has no counterpart.
+//
+// Its scratch (coordinate table, per-CTA argmax partials, result slot) is the
+// file-scope array below, which every GPU that loads the library holds until
+// the process exits. Host code only ever passes the array's device address,
+// obtained per device with cudaGetSymbolAddress on the first call made with
+// that device current (the array's name in host code is a host-side stand-in,
+// not a device address). Nothing in the array needs to start at zero: every
+// call writes each scratch word it reads. All calls share the array, so calls
+// whose GPU work overlaps (two streams, two host threads) race on it.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoAllocTableBytes = (size_t)GH_NOALLOC_MAX_XYQ * sizeof(HopEntry);
+constexpr int kNoAllocMaxCtas = 4096;
+constexpr size_t kNoAllocPartsBytes = (size_t)kNoAllocMaxCtas * sizeof(ArgPartial);
+constexpr size_t kNoAllocBytes = kNoAllocTableBytes + kNoAllocPartsBytes + 256;
+static_assert(kNoAllocBytes <= ((size_t)8 << 20), "scratch must stay at or below 8 MiB");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};  // device address of the scratch, per device ordinal
+
+int noalloc_scratch(int dev, unsigned char** p) {
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return GH_ENOTSUP;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* addr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+        if (e != cudaSuccess || !addr) return GH_ECUDA;
+        g_noalloc_addr[dev] = addr;
+    }
+    *p = (unsigned char*)g_noalloc_addr[dev];
+    return GH_OK;
+}
+
+template <int AMAX>
+int noalloc_score(cudaStream_t stream, const Dims& d, const HopParams& hp0, const float2* maps,
+                  const HopEntry* table, float* scores, ArgPartial* parts, ArgResult* result, int num_sms,
+                  int smem_optin) {
+    HopParams hp = hp0;
+    const size_t smem = (size_t)2 * d.Q * d.Nd * sizeof(float) + (size_t)2 * d.Q * sizeof(HopEntry);
+    if (smem > (size_t)smem_optin) return GH_ENOTSUP;
+    if (cudaFuncSetAttribute(hop_score_kernel<AMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return GH_ECUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_score_kernel<AMAX>, 256, smem) != cudaSuccess)
+        return GH_ECUDA;
+    if (per_sm < 1) per_sm = 1;
+    long long ctas = (long long)num_sms * per_sm;
+    if (ctas > kNoAllocMaxCtas) ctas = kNoAllocMaxCtas;
+    if (ctas > d.nxy) ctas = d.nxy;
+    hp.xy_per_cta = (d.nxy + ctas - 1) / ctas;
+    ctas = (d.nxy + hp.xy_per_cta - 1) / hp.xy_per_cta;
+    hop_score_kernel<AMAX><<<(unsigned)ctas, 256, smem, stream>>>(maps, table, hp, scores, nullptr, 0, parts);
+    if (cudaGetLastError() != cudaSuccess) return GH_ECUDA;
+    argmax_finalize_kernel<<<1, 1024, 0, stream>>>(parts, (int)ctas, result);
+    return cudaGetLastError() == cudaSuccess ? GH_OK : GH_ECUDA;
+}
+
+}  // namespace
+
+extern "C" int gh_score_grid_noalloc(void* stream_ptr, const gh_radar* radar, const double* tx_host,
+                                     const double* rx_host, int32_t Q, const void* maps_dev, const gh_grid* grid,
+                                     float* scores_dev, int64_t* best_cell, float* best_score) {
+    Dims d = {};
+    GH_TRY(gh_check_radar(nullptr, radar, Q, &d));
+    GH_TRY(gh_check_grid(nullptr, grid, &d));
+    GH_TRY(gh_check_positions(nullptr, tx_host, rx_host, Q));
+    if (!maps_dev) return GH_EINVAL;
+    if (d.nxy * d.Q > (int64_t)GH_NOALLOC_MAX_XYQ) return GH_EINVAL;  // beyond the fixed scratch
+    cudaStream_t stream = (cudaStream_t)stream_ptr;
+    int dev = 0, num_sms = 0, smem_optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GH_ECUDA;
+    if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GH_ECUDA;
+    if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return GH_ECUDA;
+    unsigned char* scratch;
+    GH_TRY(noalloc_scratch(dev, &scratch));
+    HopEntry* table = (HopEntry*)scratch;
+    ArgPartial* parts = (ArgPartial*)(scratch + kNoAllocTableBytes);
+    ArgResult* result = (ArgResult*)(scratch + kNoAllocTableBytes + kNoAllocPartsBytes);
+
+    GeoParams g;
+    gh_fill_geo(&g, radar, tx_host, rx_host, Q, grid);
+    CoordParams cp;
+    const double D1 = dirichlet_closed(1.0 / d.Nr, d.Ms), D2 = dirichlet_closed(2.0 / d.Nr, d.Ms);
+    cp.theta = 2.0 * acos(0.5 * sqrt((d.Ms - D2) / (d.Ms - D1)));
+    cp.cos_t = cos(cp.theta);
+    cp.sin_t = sin(cp.theta);
+    cp.Ms_odd_sign = ((d.Ms - 1) & 1) ? 1 : 0;
+    const long long n = d.nxy * d.Q;
+    coord_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(g, cp, table, nullptr, nullptr, nullptr, nullptr);
+    if (cudaGetLastError() != cudaSuccess) return GH_ECUDA;
+
+    HopParams hp;
+    hp.Q = d.Q;
+    hp.Nr = d.Nr;
+    hp.Nd = d.Nd;
+    hp.nvx = d.nvx;
+    hp.nvy = d.nvy;
+    hp.NB = d.nvy < 256 ? d.nvy : 256;
+    hp.SA = 256 / hp.NB;
+    hp.nxy = d.nxy;
+    hp.nv = d.nv;
+    hp.xy_per_cta = 1;
+    hp.lo2 = g.lo[2];
+    hp.step2 = g.step[2];
+    hp.lo3 = g.lo[3];
+    hp.step3 = g.step[3];
+    hp.kappa = g.kappa;
+    const int need = (d.nvx + hp.SA - 1) / hp.SA;
+    const float2* maps = (const float2*)maps_dev;
+    int st;
+    if (need <= 1)
+        st = noalloc_score<1>(stream, d, hp, maps, table, scores_dev, parts, result, num_sms, smem_optin);
+    else if (need <= 2)
+        st = noalloc_score<2>(stream, d, hp, maps, table, scores_dev, parts, result, num_sms, smem_optin);
+    else if (need <= 4)
+        st = noalloc_score<4>(stream, d, hp, maps, table, scores_dev, parts, result, num_sms, smem_optin);
+    else if (need <= 8)
+        st = noalloc_score<8>(stream, d, hp, maps, table, scores_dev, parts, result, num_sms, smem_optin);
+    else if (need <= 16)
+        st = noalloc_score<16>(stream, d, hp, maps, table, scores_dev, parts, result, num_sms, smem_optin);
+    else
+        st = noalloc_score<32>(stream, d, hp, maps, table, scores_dev, parts, result, num_sms, smem_optin);
+    if (st != GH_OK) return st;
+    if (best_cell || best_score) {
+        ArgResult h;
+        if (cudaMemcpyAsync(&h, result, sizeof(h), cudaMemcpyDeviceToHost, stream) != cudaSuccess) return GH_ECUDA;
+        if (cudaStreamSynchronize(stream) != cudaSuccess) return GH_ECUDA;
+        if (best_cell) *best_cell = h.cell;
+        if (best_score) *best_score = h.score;
+    }
+    return GH_OK;
+}

@@ -61,6 +61,8 @@ _SIGNATURES = {
                          _P, _P, _P]),
     "gh_synth": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _I32, _P, _P, _P, _P]),
     "gh_coord_table": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, ctypes.POINTER(GhGrid), _P, _P, _P, _P]),
+    "gh_score_grid_noalloc": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, ctypes.POINTER(GhGrid),
+                                     _P, _P, _P]),
     "gh_set_timing": (_I32, [_P, _I32]),
     "gh_kernel_stats": (_I32, [_P, _I32, _PD, ctypes.POINTER(ctypes.c_int64)]),
     "gh_reset_stats": (_I32, [_P]),
@@ -131,6 +133,23 @@ def _f64(a, shape=None):
     if shape is not None:
         arr = arr.reshape(shape)
     return arr
+
+
+def gh_score_grid_noalloc(stream, radar, tx, rx, Q, maps, grid, scores=None):
+    """Allocation-free hopping score and argmax (see include/gh.h); runs on
+    `stream` (a torch.cuda.Stream, a raw cudaStream_t or None for the legacy
+    default stream) on the current device. Returns (cell, score)."""
+    lib = load()
+    txa, rxa = _f64(tx, (2,)), _f64(rx, (-1,))
+    cell = ctypes.c_int64(-1)
+    score = ctypes.c_float(0.0)
+    h = None if stream is None else ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)) or None)
+    st = lib.gh_score_grid_noalloc(h, ctypes.byref(radar_struct(radar)), _ptr(txa), _ptr(rxa), int(Q), _ptr(maps),
+                                   ctypes.byref(grid_struct(grid)), _ptr(scores), ctypes.byref(cell),
+                                   ctypes.byref(score))
+    if st != GH_OK:
+        raise GhError("gh_score_grid_noalloc", st, "no context: see the status code")
+    return cell.value, score.value
 
 
 class Context:
