@@ -20,8 +20,11 @@
 
 namespace {
 
+constexpr int kCorrRows = 8;  // chirps per correlation CTA (one per warp)
+
 struct BompLayout {
-    size_t alpha, corr, ru, atoms_a, atoms_b, total;
+    size_t alpha, corr, ru, phase, gram, corrp, atoms_a, atoms_b, total;
+    int chunks;
 };
 
 BompLayout bomp_layout(const Dims& d, int K) {
@@ -32,19 +35,37 @@ BompLayout bomp_layout(const Dims& d, int K) {
         o += (bytes + 255) & ~(size_t)255;
         return at;
     };
+    L.chunks = (d.Mc + kCorrRows - 1) / kCorrRows;
     L.alpha = take((size_t)K * d.Q * 2 * sizeof(double));    // double2 [K][Q]  (must stay at offset 0)
-    L.corr = take((size_t)K * d.Q * 2 * sizeof(double));     // double2 [K][Q]
+    L.corr = take((size_t)K * d.Q * 2 * sizeof(double));     // double2 [K][Q]  <Y_q, atom>
     L.ru = take((size_t)K * d.Q * 2 * sizeof(double));       // (r, u) [K][Q]
+    L.phase = take((size_t)K * d.Q * 2 * sizeof(double));    // (cos, sin)(pi (r (Ms-1) + u (Mc-1))) [K][Q]
+    L.gram = take((size_t)d.Q * K * K * sizeof(double));      // [Q][K][K]
+    L.corrp = take((size_t)K * d.Q * L.chunks * 2 * sizeof(double));  // double2 [K][Q][chunks]
     L.atoms_a = take((size_t)K * d.Q * d.Ms * sizeof(float2));
     L.atoms_b = take((size_t)K * d.Q * d.Mc * sizeof(float2));
     L.total = o;
     return L;
 }
 
-__global__ void bomp_atoms_kernel(GeoParams g, const ArgResult* __restrict__ sel, int k, double2* __restrict__ ru,
+__device__ double dirichlet(double f, int M) {
+    const double s = sinpi(f);
+    if (fabs(s) < 1e-13) {
+        // f is (numerically) an integer n: D_M(n) = M (-1)^(n (M - 1))
+        const double n = rint(f);
+        return M * cospi(n * (double)(M - 1));
+    }
+    return sinpi((double)M * f) / s;
+}
+
+// One CTA per receiver: (r, u) of the cell selected in iteration k, its
+// centring phase, row k of the real Gram matrix, and the atoms a(r), b(u).
+__global__ void bomp_atoms_kernel(GeoParams g, const ArgResult* __restrict__ sel, int k, int K,
+                                  double2* __restrict__ ru, double2* __restrict__ phase, double* __restrict__ gram,
                                   float2* __restrict__ atoms_a, float2* __restrict__ atoms_b) {
     const int q = blockIdx.x;
     __shared__ unsigned long long s_rf, s_uf;
+    __shared__ double s_r, s_u;
     if (threadIdx.x == 0) {
         long long cell = sel[k].cell;
         const int nvy = g.n[3], nvx = g.n[2], ny = g.n[1];
@@ -59,30 +80,47 @@ __global__ void bomp_atoms_kernel(GeoParams g, const ArgResult* __restrict__ sel
         const double r = gh_range(g, d);
         const double u = gh_speed(g, wx, wy, gh_axis(g.lo[2], g.step[2], ivx), gh_axis(g.lo[3], g.step[3], ivy));
         ru[(size_t)k * g.Q + q] = make_double2(r, u);
+        double sn, cs;
+        sincospi(r * (g.Ms - 1) + u * (g.Mc - 1), &sn, &cs);
+        phase[(size_t)k * g.Q + q] = make_double2(cs, sn);
+        s_r = r;
+        s_u = u;
         s_rf = gh_phase_fix(r);
         s_uf = gh_phase_fix(u);
     }
     __syncthreads();
+    if (threadIdx.x <= k) {
+        const int t = threadIdx.x;
+        const double2 rut = t == k ? make_double2(s_r, s_u) : ru[(size_t)t * g.Q + q];
+        const double v = dirichlet(s_r - rut.x, g.Ms) * dirichlet(s_u - rut.y, g.Mc);
+        double* G = gram + (size_t)q * K * K;
+        G[k * K + t] = v;
+        G[t * K + k] = v;
+    }
     float2* a = atoms_a + ((size_t)k * g.Q + q) * g.Ms;
     float2* b = atoms_b + ((size_t)k * g.Q + q) * g.Mc;
     for (int m = threadIdx.x; m < g.Ms; m += blockDim.x) a[m] = gh_cis_fix(s_rf * (unsigned long long)m);
     for (int m = threadIdx.x; m < g.Mc; m += blockDim.x) b[m] = gh_cis_fix(s_uf * (unsigned long long)m);
 }
 
-__global__ void __launch_bounds__(256) bomp_corr_kernel(const float2* __restrict__ Y, GeoParams g, int k,
+// CTA (chunk, q): partial <Y_q, b(u) (x) a(r)> over kCorrRows chirps; each warp
+// sums one chirp in float32 and the chirps are added in float64.
+__global__ void __launch_bounds__(256) bomp_corr_kernel(const float2* __restrict__ Y, GeoParams g, int k, int chunks,
                                                         const float2* __restrict__ atoms_a,
                                                         const float2* __restrict__ atoms_b,
-                                                        double2* __restrict__ corr) {
-    const int q = blockIdx.x;
+                                                        double2* __restrict__ corrp) {
+    const int ch = blockIdx.x, q = blockIdx.y;
     const float2* a = atoms_a + ((size_t)k * g.Q + q) * g.Ms;
     const float2* b = atoms_b + ((size_t)k * g.Q + q) * g.Mc;
-    const float2* Yq = Y + (size_t)q * g.Mc * g.Ms;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mc = ch * kCorrRows + warp;
+    __shared__ double rx[kCorrRows], ry[kCorrRows];
     double sx = 0.0, sy = 0.0;
-    for (int mc = warp; mc < g.Mc; mc += nw) {
+    if (warp < kCorrRows && mc < g.Mc) {
+        const float2* row = Y + ((size_t)q * g.Mc + mc) * g.Ms;
         float2 s = make_float2(0.f, 0.f);
         for (int m = lane; m < g.Ms; m += 32) {
-            const float2 y = Yq[(size_t)mc * g.Ms + m];
+            const float2 y = row[m];
             const float2 w = a[m];
             s.x += y.x * w.x + y.y * w.y;  // y * conj(a)
             s.y += y.y * w.x - y.x * w.y;
@@ -91,72 +129,68 @@ __global__ void __launch_bounds__(256) bomp_corr_kernel(const float2* __restrict
             s.x += __shfl_down_sync(0xffffffffu, s.x, off);
             s.y += __shfl_down_sync(0xffffffffu, s.y, off);
         }
-        if (lane == 0) {
-            const double bx = b[mc].x, by = b[mc].y;  // s * conj(b)
-            sx += (double)s.x * bx + (double)s.y * by;
-            sy += (double)s.y * bx - (double)s.x * by;
-        }
+        const double bx = b[mc].x, by = b[mc].y;  // s * conj(b)
+        sx = (double)s.x * bx + (double)s.y * by;
+        sy = (double)s.y * bx - (double)s.x * by;
     }
-    __shared__ double rx[32], ry[32];
-    if (lane == 0) {
+    if (lane == 0 && warp < kCorrRows) {
         rx[warp] = sx;
         ry[warp] = sy;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double tx = 0, ty = 0;
-        for (int w = 0; w < nw; ++w) {
+        for (int w = 0; w < kCorrRows; ++w) {
             tx += rx[w];
             ty += ry[w];
         }
-        corr[(size_t)k * g.Q + q] = make_double2(tx, ty);
+        corrp[((size_t)k * g.Q + q) * chunks + ch] = make_double2(tx, ty);
     }
 }
 
-__device__ double dirichlet(double f, int M) {
-    const double s = sinpi(f);
-    if (fabs(s) < 1e-13) {
-        // f is (numerically) an integer n: D_M(n) = M (-1)^(n (M - 1))
-        const double n = rint(f);
-        return M * cospi(n * (double)(M - 1));
-    }
-    return sinpi((double)M * f) / s;
-}
-
-// One thread per receiver: n = k + 1 atoms, n <= GH_MAX_K.
-__global__ void bomp_solve_kernel(GeoParams g, int n, const double2* __restrict__ ru,
-                                  const double2* __restrict__ corr, double2* __restrict__ alpha) {
+// One thread per receiver: sums the correlation partials of atom k, then
+// solves the normal equations of atoms 0..k with the stored Gram matrix
+// (Cholesky, dependent atoms dropped) and rotates the amplitudes back to the
+// atoms of the signal model. Float64 arithmetic only.
+__global__ void bomp_solve_kernel(int Q, int Ms, int Mc, int k, int K, int chunks,
+                                  const double2* __restrict__ corrp, double2* __restrict__ corr,
+                                  const double2* __restrict__ phase, const double* __restrict__ gram,
+                                  double2* __restrict__ alpha) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= g.Q) return;
+    if (q >= Q) return;
+    const int n = k + 1;
+    {
+        double cx = 0.0, cy = 0.0;
+        const double2* pp = corrp + ((size_t)k * Q + q) * chunks;
+        for (int c = 0; c < chunks; ++c) {
+            cx += pp[c].x;
+            cy += pp[c].y;
+        }
+        corr[(size_t)k * Q + q] = make_double2(cx, cy);
+    }
     double L[GH_MAX_K][GH_MAX_K];
-    double zr[GH_MAX_K], zi[GH_MAX_K], ph[GH_MAX_K];
+    double zr[GH_MAX_K], zi[GH_MAX_K];
     bool dep[GH_MAX_K];
     for (int t = 0; t < n; ++t) {
-        const double2 rut = ru[(size_t)t * g.Q + q];
-        ph[t] = rut.x * (g.Ms - 1) + rut.y * (g.Mc - 1);
-        // centred right-hand side: exp(+j pi ph) * <Y, atom>
-        double s, c;
-        sincospi(ph[t], &s, &c);
-        const double2 ct = corr[(size_t)t * g.Q + q];
-        zr[t] = c * ct.x - s * ct.y;
-        zi[t] = c * ct.y + s * ct.x;
+        const double2 ph = phase[(size_t)t * Q + q];
+        const double2 ct = corr[(size_t)t * Q + q];
+        zr[t] = ph.x * ct.x - ph.y * ct.y;  // exp(+j pi ph) <Y, atom>
+        zi[t] = ph.x * ct.y + ph.y * ct.x;
     }
-    // Cholesky of the real Gram matrix, dependent atoms dropped
+    const double* G = gram + (size_t)q * K * K;
+    const double floor_v = 1e-9 * (double)Ms * (double)Mc;
     for (int j = 0; j < n; ++j) {
-        const double2 ruj = ru[(size_t)j * g.Q + q];
         for (int i = j; i < n; ++i) {
-            const double2 rui = ru[(size_t)i * g.Q + q];
-            double v = dirichlet(rui.x - ruj.x, g.Ms) * dirichlet(rui.y - ruj.y, g.Mc);
+            double v = G[i * K + j];
             for (int t = 0; t < j; ++t) v -= L[i][t] * L[j][t];
             if (i == j) {
-                dep[j] = !(v > 1e-9 * (double)g.Ms * (double)g.Mc);
+                dep[j] = !(v > floor_v);
                 L[j][j] = dep[j] ? 0.0 : sqrt(v);
             } else {
                 L[i][j] = dep[j] ? 0.0 : v / L[j][j];
             }
         }
     }
-    // forward then backward substitution (complex right-hand side)
     for (int i = 0; i < n; ++i) {
         if (dep[i]) {
             zr[i] = zi[i] = 0.0;
@@ -181,11 +215,9 @@ __global__ void bomp_solve_kernel(GeoParams g, int n, const double2* __restrict_
         zr[i] /= L[i][i];
         zi[i] /= L[i][i];
     }
-    // back to the atoms of the signal model: alpha = alpha~ exp(-j pi ph)
     for (int t = 0; t < n; ++t) {
-        double s, c;
-        sincospi(ph[t], &s, &c);
-        alpha[(size_t)t * g.Q + q] = make_double2(c * zr[t] + s * zi[t], c * zi[t] - s * zr[t]);
+        const double2 ph = phase[(size_t)t * Q + q];  // alpha = alpha~ exp(-j pi ph)
+        alpha[(size_t)t * Q + q] = make_double2(ph.x * zr[t] + ph.y * zi[t], ph.x * zi[t] - ph.y * zr[t]);
     }
 }
 
@@ -248,23 +280,27 @@ __global__ void __launch_bounds__(256) synth_kernel(GeoParams g, int T, const do
 size_t gh_bomp_ws_bytes(const Dims& d, int K) { return bomp_layout(d, K).total; }
 
 int gh_launch_bomp_iter(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y, float2* R, int k, int K,
-                          const ArgResult* sel, void* ws) {
+                        const ArgResult* sel, void* ws) {
     const BompLayout L = bomp_layout(d, K);
     char* base = (char*)ws;
     double2* alpha = (double2*)(base + L.alpha);
     double2* corr = (double2*)(base + L.corr);
     double2* ru = (double2*)(base + L.ru);
+    double2* phase = (double2*)(base + L.phase);
+    double* gram = (double*)(base + L.gram);
+    double2* corrp = (double2*)(base + L.corrp);
     float2* aa = (float2*)(base + L.atoms_a);
     float2* ab = (float2*)(base + L.atoms_b);
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_BOMP, &ev);
-    bomp_atoms_kernel<<<d.Q, 256, 0, ctx->stream>>>(g, sel, k, ru, aa, ab);
+    bomp_atoms_kernel<<<d.Q, 256, 0, ctx->stream>>>(g, sel, k, K, ru, phase, gram, aa, ab);
     GH_TRY(gh_launch_end(ctx, GH_K_BOMP, ev, "bomp_atoms_kernel"));
     gh_launch_begin(ctx, GH_K_BOMP, &ev);
-    bomp_corr_kernel<<<d.Q, 256, 0, ctx->stream>>>(Y, g, k, aa, ab, corr);
+    bomp_corr_kernel<<<dim3(L.chunks, d.Q), 32 * kCorrRows, 0, ctx->stream>>>(Y, g, k, L.chunks, aa, ab, corrp);
     GH_TRY(gh_launch_end(ctx, GH_K_BOMP, ev, "bomp_corr_kernel"));
     gh_launch_begin(ctx, GH_K_BOMP, &ev);
-    bomp_solve_kernel<<<(d.Q + 31) / 32, 32, 0, ctx->stream>>>(g, k + 1, ru, corr, alpha);
+    bomp_solve_kernel<<<(d.Q + 31) / 32, 32, 0, ctx->stream>>>(d.Q, d.Ms, d.Mc, k, K, L.chunks, corrp, corr, phase,
+                                                              gram, alpha);
     GH_TRY(gh_launch_end(ctx, GH_K_BOMP, ev, "bomp_solve_kernel"));
     const size_t total = (size_t)d.Q * d.Mc * d.Ms;
     unsigned blocks = (unsigned)((total + 255) / 256);

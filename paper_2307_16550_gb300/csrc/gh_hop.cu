@@ -9,42 +9,52 @@
 //   indices (a, b), so eta * 2^32 = base + a * ax + b * by exactly up to the
 //   rounding of three integers (error <= (1 + a + b) * 2^-33 bins).
 //
-// hop_score_kernel (one CTA per run of (x, y) cells):
+// hop_score_kernel (one warp per (x, y) cell at a time, no block barriers):
 //   For a fixed (x, y, q) the hopping value at Doppler bin j is
 //   T_q[j] = sum_k c_k Z~_q[i+k][j], and the cell's contribution is |T_q[j_q]|^2.
-//   The CTA first evaluates P_q[j] = |T_q[j]|^2 for the Doppler bins that the
-//   velocity grid reaches (coalesced reads of three map rows), then every
-//   velocity cell sums P_q over q with one shared-memory read per receiver.
-//   The bin j_q = floor(eta + 1/2) comes from the fixed-point value; when its
-//   fraction lies within 2^-20 of a rounding boundary the bin is recomputed
-//   with the float64 expression floor(Nd * (kappa * (wx*vx + wy*vy)) + 1/2),
+//   The warp first evaluates P_q[j] = |T_q[j]|^2 into its own shared-memory
+//   rows (indexed by absolute Doppler bin) for the bins the velocity grid
+//   reaches, reading the three map rows with 16-byte loads; then each lane
+//   scores up to 32 velocity cells, one shared-memory read per receiver.
+//   The bin j_q = floor(eta + 1/2) is the high word of the fixed-point value;
+//   when its fraction lies within `tol` of a rounding boundary the bin is
+//   recomputed with the float64 expression floor(Nd * (kappa * (wx*vx + wy*vy)) + 1/2),
 //   so every bin decision equals a plain float64 evaluation.
-//   P rows are double buffered: one barrier per (x, y) cell.
-//   Scores (optional) are written coalesced; the CTA's best (score, cell) is
-//   reduced with warp shuffles (ties: smallest cell index).
+//   The warps of a CTA work on neighbouring y cells at the same time, so their
+//   map rows overlap in L1. Scores (optional) are written coalesced; the best
+//   (score, cell) is reduced per lane, then with warp shuffles and once per
+//   CTA (ties: smallest cell index).
 #include <math.h>
 
 #include "gh_internal.cuh"
 
 namespace {
 
-constexpr uint32_t kTol = 4096u;  // 2^-20 of a bin, in 2^-32 units
+// Fixed-point tolerance (2^-32 bin units) of the Doppler bin decision: at least
+// 2^-20 of a bin and four times the rounding bound (1 + nvx + nvy) * 2^-33.
+inline uint32_t hop_tol(int nvx, int nvy) {
+    const long long t = 4LL * (nvx + nvy + 2);
+    return (uint32_t)(t > 4096 ? t : 4096);
+}
 
 struct __align__(16) HopEntry {
-    long long base;  // (eta(0,0) - j_lo + 1/2) * 2^32 + kTol
+    long long base;  // (eta(0,0) + 1/2) * 2^32 + tol
     long long ax;    // d eta / d ivx * 2^32
     long long by;    // d eta / d ivy * 2^32
     double wx, wy;   // bistatic gradient (float64 bin decisions)
     int row[3];      // map rows (i + k) mod Nr, k = -1, 0, 1
     float cs[3];     // polar coefficients times the wrap sign
-    int j_lo;        // Doppler bin of P[0]
-    int nP;          // number of P entries (<= Nd)
+    int j_lo;        // first Doppler bin the velocity grid reaches (minus one)
+    int nP;          // number of bins from j_lo on that it reaches (<= Nd)
 };
 static_assert(sizeof(HopEntry) == 80, "HopEntry layout");
 
 struct CoordParams {
-    double theta, cos_t, sin_t;  // polar half-arc angle
+    float theta_f;               // polar half-arc angle theta
+    float inv_sin2_half;         // 1 / sin^2(theta / 2)
+    float inv_sin_t;             // 1 / sin(theta)
     int Ms_odd_sign;             // 1 if (Ms - 1) is odd (wrap flips the sign)
+    uint32_t tol;                // hop_tol(nvx, nvy)
 };
 
 __global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__ table, int32_t* diag_i,
@@ -66,10 +76,14 @@ __global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__
     const double tau = __dsub_rn(rho, fi);
     const long long i = (long long)fi;
 
-    // polar coefficients on the arc through bins i-1, i, i+1
-    const double kap = (1.0 - cos(cp.theta * tau)) / (1.0 - cp.cos_t);
-    const double sig = sin(cp.theta * tau) / cp.sin_t;
-    const double c[3] = {0.5 * (kap - sig), 1.0 - kap, 0.5 * (kap + sig)};
+    // polar coefficients on the arc through bins i-1, i, i+1 (float32: they are
+    // stored in float32; 1 - cos(theta tau) = 2 sin^2(theta tau / 2) avoids cancellation)
+    float sh, ch, sf, cf;
+    sincosf(0.5f * cp.theta_f * (float)tau, &sh, &ch);
+    sincosf(cp.theta_f * (float)tau, &sf, &cf);
+    const float kap = sh * sh * cp.inv_sin2_half;
+    const float sig = sf * cp.inv_sin_t;
+    const float c[3] = {0.5f * (kap - sig), 1.0f - kap, 0.5f * (kap + sig)};
 
     HopEntry e;
     for (int k = 0; k < 3; ++k) {
@@ -78,7 +92,7 @@ __global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__
         if (n < 0 && w * g.Nr != n) --w;  // floor division
         e.row[k] = (int)(n - w * g.Nr);
         const bool flip = cp.Ms_odd_sign && (w & 1);
-        e.cs[k] = (float)(flip ? -c[k] : c[k]);
+        e.cs[k] = flip ? -c[k] : c[k];
     }
 
     // Doppler bin position, affine in (ivx, ivy)
@@ -94,7 +108,7 @@ __global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__
     const long long j_hi = (long long)floor(emax + 0.5) + 1;
     const long long span = j_hi - j_lo + 1;
     const double two32 = 4294967296.0;
-    e.base = llrint((eta00 - (double)j_lo + 0.5) * two32) + (long long)kTol;
+    e.base = llrint((eta00 + 0.5) * two32) + (long long)cp.tol;
     e.ax = llrint(ax * two32);
     e.by = llrint(by * two32);
     e.wx = wx;
@@ -106,7 +120,7 @@ __global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__
     if (diag_i) {
         diag_i[idx] = (int32_t)i;
         diag_tau[idx] = tau;
-        for (int k = 0; k < 3; ++k) diag_c[3 * idx + k] = (float)c[k];
+        for (int k = 0; k < 3; ++k) diag_c[3 * idx + k] = c[k];
         diag_w[2 * idx] = wx;
         diag_w[2 * idx + 1] = wy;
     }
@@ -114,19 +128,21 @@ __global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__
 
 struct HopParams {
     int Q, Nr, Nd, nvx, nvy;
-    int NB, SA;           // thread mapping: b = tid % NB (stride NB), a = tid / NB (stride SA)
+    int NB, SA;           // lane mapping: b = lane % NB (stride NB), a = lane / NB (stride SA)
+    uint32_t tol2;        // 2 * tol
     long long nxy, nv;
     long long xy_per_cta;
     double lo2, step2, lo3, step3, kappa;
 };
 
-// Exact float64 Doppler bin for cell (a, b), as an index into the P row.
-__device__ __noinline__ int slow_bin(const HopParams& p, double wx, double wy, int j_lo, int a, int b) {
-    const double vx = gh_axis(p.lo2, p.step2, a);
-    const double vy = gh_axis(p.lo3, p.step3, b);
-    const double u = __dmul_rn(p.kappa, __dadd_rn(__dmul_rn(wx, vx), __dmul_rn(wy, vy)));
-    const long long j = (long long)floor(__dadd_rn(__dmul_rn((double)p.Nd, u), 0.5));
-    return (int)((j - j_lo) & (p.Nd - 1));
+// Exact float64 Doppler bin (mod Nd) of cell (a, b).
+__device__ __noinline__ int slow_bin(double wx, double wy, int a, int b, double lo2, double step2, double lo3,
+                                     double step3, double kappa, int Nd) {
+    const double vx = gh_axis(lo2, step2, a);
+    const double vy = gh_axis(lo3, step3, b);
+    const double u = __dmul_rn(kappa, __dadd_rn(__dmul_rn(wx, vx), __dmul_rn(wy, vy)));
+    const long long j = (long long)floor(__dadd_rn(__dmul_rn((double)Nd, u), 0.5));
+    return (int)(j & (Nd - 1));
 }
 
 __device__ __forceinline__ void better(float s, long long c, float& bs, long long& bc) {
@@ -136,126 +152,159 @@ __device__ __forceinline__ void better(float s, long long c, float& bs, long lon
     }
 }
 
-template <int AMAX>
-__global__ void __launch_bounds__(256) hop_score_kernel(const float2* __restrict__ maps,
-                                                        const HopEntry* __restrict__ table, HopParams p,
-                                                        float* __restrict__ scores, const int64_t* __restrict__ mask,
-                                                        int nmask, ArgPartial* __restrict__ parts) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* P = (float*)smem_raw;                                        // [2][Q][Nd]
-    HopEntry* tab = (HopEntry*)(smem_raw + (size_t)2 * p.Q * p.Nd * 4);  // [2][Q]
-    __shared__ int s_mask[2];
+// AC: velocity cells per lane per pass (along vx, stride SA).
+template <int AC>
+__global__ void __launch_bounds__(256, 2) hop_score_kernel(const float2* __restrict__ maps,
+                                                           const HopEntry* __restrict__ table, HopParams p,
+                                                           float* __restrict__ scores,
+                                                           const int64_t* __restrict__ mask, int nmask,
+                                                           ArgPartial* __restrict__ parts) {
+    extern __shared__ __align__(16) unsigned char smem_hop[];  // [warps] x ([Q][Nd] floats + [Q] entries)
     __shared__ float s_bs[8];
     __shared__ long long s_bc[8];
-
-    const int tid = threadIdx.x;
-    const long long xy0 = (long long)blockIdx.x * p.xy_per_cta;
-    long long xy1 = xy0 + p.xy_per_cta;
-    if (xy1 > p.nxy) xy1 = p.nxy;
-    const int cnt = (int)(xy1 - xy0);
-    const int tb = tid % p.NB;
-    const int ta = tid / p.NB;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int W = blockDim.x >> 5;
+    const int ndm = p.Nd - 1;
+    const size_t warp_bytes =
+        (size_t)p.Q * p.Nd * sizeof(float) + (size_t)p.Q * sizeof(HopEntry) + (size_t)32 * AC * sizeof(float);
+    float* P = (float*)(smem_hop + warp * warp_bytes);
+    HopEntry* E = (HopEntry*)(P + (size_t)p.Q * p.Nd);
+    float* fix = (float*)(E + p.Q) + lane * AC;  // per-lane corrections of the float64 path
+    const int tb = lane % p.NB, ta = lane / p.NB;
+    const bool active = ta < p.SA;
     float best = -INFINITY;
     long long bestc = 0x7fffffffffffffffLL;
 
-    auto build = [&](long long xy, int buf) {
-        const HopEntry* e = table + xy * p.Q;
-        const long long* src = (const long long*)e;
-        long long* dst = (long long*)(tab + buf * p.Q);
-        const int words = p.Q * (int)(sizeof(HopEntry) / 8);
-        for (int t = tid; t < words; t += blockDim.x) dst[t] = __ldg(src + t);
-        if (tid == 0) {
-            int f = 0;
-            for (int m = 0; m < nmask; ++m) f |= (mask[m] / p.nv == xy);
-            s_mask[buf] = f;
+    const long long xy0 = (long long)blockIdx.x * p.xy_per_cta;
+    long long xy1 = xy0 + p.xy_per_cta;
+    if (xy1 > p.nxy) xy1 = p.nxy;
+    const int ewords = p.Q * (int)(sizeof(HopEntry) / 8);
+    for (long long xy = xy0 + warp; xy < xy1; xy += W) {
+        __syncwarp();  // the previous cell's reads of P and E are done
+        {
+            const long long* src = (const long long*)(table + xy * p.Q);
+            long long* dst = (long long*)E;
+            for (int w = lane; w < ewords; w += 32) dst[w] = __ldg(src + w);
         }
+        __syncwarp();
         for (int q = 0; q < p.Q; ++q) {
-            const int nP = __ldg(&e[q].nP);
-            const int j_lo = __ldg(&e[q].j_lo);
-            const float2* r0 = maps + ((size_t)q * p.Nr + __ldg(&e[q].row[0])) * p.Nd;
-            const float2* r1 = maps + ((size_t)q * p.Nr + __ldg(&e[q].row[1])) * p.Nd;
-            const float2* r2 = maps + ((size_t)q * p.Nr + __ldg(&e[q].row[2])) * p.Nd;
-            const float c0 = __ldg(&e[q].cs[0]), c1 = __ldg(&e[q].cs[1]), c2 = __ldg(&e[q].cs[2]);
-            const int js = j_lo & (p.Nd - 1);
-            float* Pq = P + ((size_t)buf * p.Q + q) * p.Nd;
-            for (int t = tid; t < nP; t += blockDim.x) {
-                const int j = (js + t) & (p.Nd - 1);
-                const float2 z0 = __ldg(r0 + j), z1 = __ldg(r1 + j), z2 = __ldg(r2 + j);
-                const float re = c0 * z0.x + c1 * z1.x + c2 * z2.x;
-                const float im = c0 * z0.y + c1 * z1.y + c2 * z2.y;
-                Pq[t] = re * re + im * im;
+            const HopEntry& eq = E[q];
+            const int j_lo = eq.j_lo, nP = eq.nP;
+            const float c0 = eq.cs[0], c1 = eq.cs[1], c2 = eq.cs[2];
+            const size_t qb = (size_t)q * p.Nr;
+            const float4* r0 = (const float4*)(maps + (qb + eq.row[0]) * p.Nd);
+            const float4* r1 = (const float4*)(maps + (qb + eq.row[1]) * p.Nd);
+            const float4* r2 = (const float4*)(maps + (qb + eq.row[2]) * p.Nd);
+            const int jbeg = j_lo & ~1;
+            int npair = (nP + (j_lo - jbeg) + 1) >> 1;
+            if (npair > (p.Nd >> 1)) npair = p.Nd >> 1;
+            float* Pq = P + (size_t)q * p.Nd;
+            constexpr int U = 4;  // row loads in flight per lane
+            for (int pp0 = 0; pp0 < npair; pp0 += 32 * U) {
+                float4 z0[U], z1[U], z2[U];
+                int jj[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int pp = pp0 + lane + 32 * u;
+                    jj[u] = (jbeg + 2 * pp) & ndm;
+                    if (pp < npair) {
+                        z0[u] = __ldg(r0 + (jj[u] >> 1));
+                        z1[u] = __ldg(r1 + (jj[u] >> 1));
+                        z2[u] = __ldg(r2 + (jj[u] >> 1));
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (pp0 + lane + 32 * u < npair) {
+                        const float re0 = c0 * z0[u].x + c1 * z1[u].x + c2 * z2[u].x;
+                        const float im0 = c0 * z0[u].y + c1 * z1[u].y + c2 * z2[u].y;
+                        const float re1 = c0 * z0[u].z + c1 * z1[u].z + c2 * z2[u].z;
+                        const float im1 = c0 * z0[u].w + c1 * z1[u].w + c2 * z2[u].w;
+                        *(float2*)(Pq + jj[u]) = make_float2(re0 * re0 + im0 * im0, re1 * re1 + im1 * im1);
+                    }
+                }
             }
         }
-    };
-
-    auto gather = [&](long long xy, int buf) {
-        if (ta >= p.SA) return;
-        const HopEntry* E = tab + buf * p.Q;
-        const bool hm = s_mask[buf] != 0;
+        bool hm = false;
+        for (int m = 0; m < nmask; ++m) hm |= (__ldg(&mask[m]) / p.nv == xy);
+        __syncwarp();  // P rows complete
+        if (!active) continue;
         const long long cbase = xy * p.nv;
-        const float* Pb = P + (size_t)buf * p.Q * p.Nd;
         for (int b = tb; b < p.nvy; b += p.NB) {
-            for (int a0 = 0; a0 < p.nvx; a0 += p.SA * AMAX) {
-                float acc[AMAX];
+            for (int a0 = ta; a0 < p.nvx; a0 += p.SA * AC) {
+                float acc[AC];
 #pragma unroll
-                for (int i = 0; i < AMAX; ++i) acc[i] = 0.f;
+                for (int i = 0; i < AC; ++i) acc[i] = 0.f;
                 for (int q = 0; q < p.Q; ++q) {
-                    const long long ax = E[q].ax;
-                    long long t = E[q].base + (long long)b * E[q].by + (long long)(a0 + ta) * ax;
-                    const long long st = (long long)p.SA * ax;
-                    const float* Pq = Pb + (size_t)q * p.Nd;
+                    const HopEntry& eq = E[q];
+                    const long long t0 = eq.base + (long long)b * eq.by + (long long)a0 * eq.ax;
+                    const long long st = (long long)p.SA * eq.ax;
+                    const float* Pq = P + (size_t)q * p.Nd;
+                    long long t = t0;
+                    bool amb = false;
 #pragma unroll
-                    for (int i = 0; i < AMAX; ++i) {
-                        const int a = a0 + ta + i * p.SA;
-                        if (a < p.nvx) {
-                            const uint32_t lo = (uint32_t)t;
-                            int idx = (int)(t >> 32) & (p.Nd - 1);
-                            if (lo < 2u * kTol) idx = slow_bin(p, E[q].wx, E[q].wy, E[q].j_lo, a, b);
-                            acc[i] += Pq[idx];
-                        }
+                    for (int i = 0; i < AC; ++i) {
+                        amb |= (uint32_t)t < p.tol2;
+                        acc[i] += Pq[(int)(t >> 32) & ndm];
                         t += st;
                     }
-                }
+                    if (amb) {
+                        // rare: a bin decision within tol of a rounding boundary;
+                        // replace the fast bin by the float64 one for those cells
+                        // (corrections go through shared memory so that the
+                        // float64 path keeps the accumulators in registers)
+                        t = t0;
+#pragma unroll 1
+                        for (int i = 0; i < AC; ++i) {
+                            float dlt = 0.f;
+                            if ((uint32_t)t < p.tol2) {
+                                const int fast = (int)(t >> 32) & ndm;
+                                const int exact = slow_bin(eq.wx, eq.wy, a0 + i * p.SA, b, p.lo2, p.step2, p.lo3,
+                                                           p.step3, p.kappa, p.Nd);
+                                if (exact != fast) dlt = Pq[exact] - Pq[fast];
+                            }
+                            fix[i] = dlt;
+                            t += st;
+                        }
 #pragma unroll
-                for (int i = 0; i < AMAX; ++i) {
-                    const int a = a0 + ta + i * p.SA;
-                    if (a < p.nvx) {
-                        const long long cell = cbase + (long long)a * p.nvy + b;
-                        const float s = acc[i];
-                        if (scores) scores[cell] = s;
-                        bool masked = false;
-                        if (hm)
-                            for (int m = 0; m < nmask; ++m) masked |= (mask[m] == cell);
-                        if (!masked) better(s, cell, best, bestc);
+                        for (int i = 0; i < AC; ++i) acc[i] += fix[i];
                     }
                 }
+                // best of this run (cells in increasing index order), then merge
+                float rb = -INFINITY;
+                int ri = -1;
+                const bool full = a0 + (AC - 1) * p.SA < p.nvx;
+#pragma unroll
+                for (int i = 0; i < AC; ++i) {
+                    if (full || a0 + i * p.SA < p.nvx) {
+                        const long long cell = cbase + (long long)(a0 + i * p.SA) * p.nvy + b;
+                        if (scores) scores[cell] = acc[i];
+                        bool masked = false;
+                        if (hm)
+                            for (int m = 0; m < nmask; ++m) masked |= (__ldg(&mask[m]) == cell);
+                        if (!masked && acc[i] > rb) {
+                            rb = acc[i];
+                            ri = i;
+                        }
+                    }
+                }
+                if (ri >= 0) better(rb, cbase + (long long)(a0 + ri * p.SA) * p.nvy + b, best, bestc);
             }
-        }
-    };
-
-    if (cnt > 0) {
-        build(xy0, 0);
-        for (int n = 0; n < cnt; ++n) {
-            __syncthreads();
-            if (n + 1 < cnt) build(xy0 + n + 1, (n + 1) & 1);
-            gather(xy0 + n, n & 1);
         }
     }
 
-    // block argmax
     for (int off = 16; off > 0; off >>= 1) {
         const float os = __shfl_down_sync(0xffffffffu, best, off);
         const long long oc = __shfl_down_sync(0xffffffffu, bestc, off);
         better(os, oc, best, bestc);
     }
-    const int warp = tid >> 5, lane = tid & 31;
     if (lane == 0) {
         s_bs[warp] = best;
         s_bc[warp] = bestc;
     }
     __syncthreads();
-    if (tid == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) better(s_bs[w], s_bc[w], best, bestc);
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < W; ++w) better(s_bs[w], s_bc[w], best, bestc);
         parts[blockIdx.x].score = best;
         parts[blockIdx.x].cell = bestc;
     }
@@ -287,33 +336,95 @@ __global__ void __launch_bounds__(1024) argmax_finalize_kernel(const ArgPartial*
     }
 }
 
-template <int AMAX>
-int launch_hop_t(gh_ctx* ctx, const Dims& d, const HopParams& hp0, const float2* maps, const HopEntry* table,
-                 float* scores, const int64_t* mask, int nmask, ArgResult* result) {
-    HopParams hp = hp0;
-    const size_t smem = (size_t)2 * d.Q * d.Nd * sizeof(float) + (size_t)2 * d.Q * sizeof(HopEntry);
-    if (smem > ctx->smem_optin) return gh_fail(ctx, GH_ENOTSUP, "hop scorer needs %zu B shared memory", smem);
-    GH_CUDA(cudaFuncSetAttribute(hop_score_kernel<AMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+HopParams hop_params(const Dims& d, const GeoParams& g) {
+    HopParams hp;
+    hp.Q = d.Q;
+    hp.Nr = d.Nr;
+    hp.Nd = d.Nd;
+    hp.nvx = d.nvx;
+    hp.nvy = d.nvy;
+    hp.NB = d.nvy < 32 ? d.nvy : 32;
+    hp.SA = 32 / hp.NB;
+    hp.tol2 = 2u * hop_tol(d.nvx, d.nvy);
+    hp.nxy = d.nxy;
+    hp.nv = d.nv;
+    hp.xy_per_cta = 1;
+    hp.lo2 = g.lo[2];
+    hp.step2 = g.step[2];
+    hp.lo3 = g.lo[3];
+    hp.step3 = g.step[3];
+    hp.kappa = g.kappa;
+    return hp;
+}
+
+CoordParams coord_params(const Dims& d);
+
+// Launch of the scorer (shared by the context path and the allocation-free
+// entry point). Returns the number of CTAs (partials) in *nparts.
+template <int AC>
+int hop_launch_t(cudaStream_t stream, const Dims& d, HopParams hp, const float2* maps, const HopEntry* table,
+                 float* scores, const int64_t* mask, int nmask, ArgPartial* parts, long long max_ctas, int num_sms,
+                 size_t smem_optin, long long* nparts) {
+    const size_t per_warp =
+        (size_t)d.Q * d.Nd * sizeof(float) + (size_t)d.Q * sizeof(HopEntry) + (size_t)32 * AC * sizeof(float);
+    if (per_warp > smem_optin) return GH_ENOTSUP;
+    int W = (int)((size_t)(100 << 10) / per_warp);
+    if (W > 8) W = 8;
+    if (W < 1) W = 1;
+    const size_t smem = per_warp * W;
+    if (cudaFuncSetAttribute(hop_score_kernel<AC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return GH_ECUDA;
     int per_sm = 0;
-    GH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_score_kernel<AMAX>, 256, smem));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_score_kernel<AC>, 32 * W, smem) != cudaSuccess)
+        return GH_ECUDA;
     if (per_sm < 1) per_sm = 1;
-    long long ctas = (long long)ctx->num_sms * per_sm;
+    long long ctas = (long long)num_sms * per_sm;
+    if (ctas > max_ctas) ctas = max_ctas;
     if (ctas > d.nxy) ctas = d.nxy;
     hp.xy_per_cta = (d.nxy + ctas - 1) / ctas;
     ctas = (d.nxy + hp.xy_per_cta - 1) / hp.xy_per_cta;
-    void* parts;
-    GH_TRY(gh_ws(ctx, WS_PART, (size_t)ctas * sizeof(ArgPartial), &parts));
-    cudaEvent_t ev;
-    gh_launch_begin(ctx, GH_K_HOP_SCORE, &ev);
-    hop_score_kernel<AMAX><<<(unsigned)ctas, 256, smem, ctx->stream>>>(maps, table, hp, scores, mask, nmask,
-                                                                        (ArgPartial*)parts);
-    GH_TRY(gh_launch_end(ctx, GH_K_HOP_SCORE, ev, "hop_score_kernel"));
-    return gh_launch_argmax_finalize(ctx, (const ArgPartial*)parts, (int)ctas, result);
+    hop_score_kernel<AC><<<(unsigned)ctas, 32 * W, smem, stream>>>(maps, table, hp, scores, mask, nmask, parts);
+    *nparts = ctas;
+    return cudaGetLastError() == cudaSuccess ? GH_OK : GH_ECUDA;
+}
+
+int hop_launch(cudaStream_t stream, const Dims& d, const HopParams& hp, const float2* maps, const HopEntry* table,
+               float* scores, const int64_t* mask, int nmask, ArgPartial* parts, long long max_ctas, int num_sms,
+               size_t smem_optin, long long* nparts) {
+    const int need = (d.nvx + hp.SA - 1) / hp.SA;
+#define GH_HOP_CASE(N)                                                                                       \
+    if (need <= N)                                                                                           \
+        return hop_launch_t<N>(stream, d, hp, maps, table, scores, mask, nmask, parts, max_ctas, num_sms, \
+                               smem_optin, nparts);
+    GH_HOP_CASE(1)
+    GH_HOP_CASE(2)
+    GH_HOP_CASE(4)
+    GH_HOP_CASE(8)
+    GH_HOP_CASE(16)
+#undef GH_HOP_CASE
+    return hop_launch_t<32>(stream, d, hp, maps, table, scores, mask, nmask, parts, max_ctas, num_sms, smem_optin,
+                            nparts);
 }
 
 double dirichlet_closed(double f, int M) {
     const double pi = 3.14159265358979323846264338327950288;
     return sin(pi * M * f) / sin(pi * f);
+}
+
+CoordParams coord_params(const Dims& d) {
+    CoordParams cp;
+    // Half-arc angle of the three-bin polar model, from the Gram of centred
+    // atoms: cos(theta/2) = 1/2 sqrt((Ms - D(2/Nr)) / (Ms - D(1/Nr))).
+    const double D1 = dirichlet_closed(1.0 / d.Nr, d.Ms), D2 = dirichlet_closed(2.0 / d.Nr, d.Ms);
+    const double theta = 2.0 * acos(0.5 * sqrt((d.Ms - D2) / (d.Ms - D1)));
+    const double sh = sin(0.5 * theta);
+    cp.theta_f = (float)theta;
+    cp.inv_sin2_half = (float)(1.0 / (sh * sh));
+    cp.inv_sin_t = (float)(1.0 / sin(theta));
+    cp.Ms_odd_sign = ((d.Ms - 1) & 1) ? 1 : 0;
+    cp.tol = hop_tol(d.nvx, d.nvy);
+    return cp;
 }
 
 }  // namespace
@@ -322,14 +433,7 @@ size_t gh_hop_table_bytes(const Dims& d) { return (size_t)d.nxy * d.Q * sizeof(H
 
 int gh_launch_coord(gh_ctx* ctx, const Dims& d, const GeoParams& g, void* table, int32_t* diag_i,
                     double* diag_tau, float* diag_c, double* diag_w) {
-    CoordParams cp;
-    // Half-arc angle of the three-bin polar model, from the Gram of centred
-    // atoms: cos(theta/2) = 1/2 sqrt((Ms - D(2/Nr)) / (Ms - D(1/Nr))).
-    const double D1 = dirichlet_closed(1.0 / d.Nr, d.Ms), D2 = dirichlet_closed(2.0 / d.Nr, d.Ms);
-    cp.theta = 2.0 * acos(0.5 * sqrt((d.Ms - D2) / (d.Ms - D1)));
-    cp.cos_t = cos(cp.theta);
-    cp.sin_t = sin(cp.theta);
-    cp.Ms_odd_sign = ((d.Ms - 1) & 1) ? 1 : 0;
+    const CoordParams cp = coord_params(d);
     const long long n = d.nxy * d.Q;
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_COORD, &ev);
@@ -347,30 +451,19 @@ int gh_launch_argmax_finalize(gh_ctx* ctx, const ArgPartial* parts, int nparts, 
 
 int gh_launch_hop(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* maps, const void* table,
                   float* scores, const int64_t* mask, int nmask, ArgResult* result) {
-    HopParams hp;
-    hp.Q = d.Q;
-    hp.Nr = d.Nr;
-    hp.Nd = d.Nd;
-    hp.nvx = d.nvx;
-    hp.nvy = d.nvy;
-    hp.NB = d.nvy < 256 ? d.nvy : 256;
-    hp.SA = 256 / hp.NB;
-    hp.nxy = d.nxy;
-    hp.nv = d.nv;
-    hp.xy_per_cta = 1;
-    hp.lo2 = g.lo[2];
-    hp.step2 = g.step[2];
-    hp.lo3 = g.lo[3];
-    hp.step3 = g.step[3];
-    hp.kappa = g.kappa;
-    const int need = (d.nvx + hp.SA - 1) / hp.SA;
-    const HopEntry* t = (const HopEntry*)table;
-    if (need <= 1) return launch_hop_t<1>(ctx, d, hp, maps, t, scores, mask, nmask, result);
-    if (need <= 2) return launch_hop_t<2>(ctx, d, hp, maps, t, scores, mask, nmask, result);
-    if (need <= 4) return launch_hop_t<4>(ctx, d, hp, maps, t, scores, mask, nmask, result);
-    if (need <= 8) return launch_hop_t<8>(ctx, d, hp, maps, t, scores, mask, nmask, result);
-    if (need <= 16) return launch_hop_t<16>(ctx, d, hp, maps, t, scores, mask, nmask, result);
-    return launch_hop_t<32>(ctx, d, hp, maps, t, scores, mask, nmask, result);
+    const HopParams hp = hop_params(d, g);
+    const long long max_ctas = (long long)ctx->num_sms * 32;
+    void* parts;
+    GH_TRY(gh_ws(ctx, WS_PART, (size_t)max_ctas * sizeof(ArgPartial), &parts));
+    cudaEvent_t ev;
+    long long nparts = 0;
+    gh_launch_begin(ctx, GH_K_HOP_SCORE, &ev);
+    const int st = hop_launch(ctx->stream, d, hp, maps, (const HopEntry*)table, scores, mask, nmask,
+                              (ArgPartial*)parts, max_ctas, ctx->num_sms, ctx->smem_optin, &nparts);
+    if (st == GH_ENOTSUP) return gh_fail(ctx, GH_ENOTSUP, "hop scorer: Q*Nd*4 bytes exceed shared memory");
+    GH_TRY(gh_launch_end(ctx, GH_K_HOP_SCORE, ev, "hop_score_kernel"));
+    if (st != GH_OK) return gh_fail(ctx, st, "hop scorer launch failed");
+    return gh_launch_argmax_finalize(ctx, (const ArgPartial*)parts, (int)nparts, result);
 }
 
 // ---------------------------------------------------------------------------
@@ -415,31 +508,6 @@ int noalloc_scratch(int dev, unsigned char** p) {
     return GH_OK;
 }
 
-template <int AMAX>
-int noalloc_score(cudaStream_t stream, const Dims& d, const HopParams& hp0, const float2* maps,
-                  const HopEntry* table, float* scores, ArgPartial* parts, ArgResult* result, int num_sms,
-                  int smem_optin) {
-    HopParams hp = hp0;
-    const size_t smem = (size_t)2 * d.Q * d.Nd * sizeof(float) + (size_t)2 * d.Q * sizeof(HopEntry);
-    if (smem > (size_t)smem_optin) return GH_ENOTSUP;
-    if (cudaFuncSetAttribute(hop_score_kernel<AMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return GH_ECUDA;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_score_kernel<AMAX>, 256, smem) != cudaSuccess)
-        return GH_ECUDA;
-    if (per_sm < 1) per_sm = 1;
-    long long ctas = (long long)num_sms * per_sm;
-    if (ctas > kNoAllocMaxCtas) ctas = kNoAllocMaxCtas;
-    if (ctas > d.nxy) ctas = d.nxy;
-    hp.xy_per_cta = (d.nxy + ctas - 1) / ctas;
-    ctas = (d.nxy + hp.xy_per_cta - 1) / hp.xy_per_cta;
-    hop_score_kernel<AMAX><<<(unsigned)ctas, 256, smem, stream>>>(maps, table, hp, scores, nullptr, 0, parts);
-    if (cudaGetLastError() != cudaSuccess) return GH_ECUDA;
-    argmax_finalize_kernel<<<1, 1024, 0, stream>>>(parts, (int)ctas, result);
-    return cudaGetLastError() == cudaSuccess ? GH_OK : GH_ECUDA;
-}
-
 }  // namespace
 
 extern "C" int gh_score_grid_noalloc(void* stream_ptr, const gh_radar* radar, const double* tx_host,
@@ -465,48 +533,17 @@ extern "C" int gh_score_grid_noalloc(void* stream_ptr, const gh_radar* radar, co
 
     GeoParams g;
     gh_fill_geo(&g, radar, tx_host, rx_host, Q, grid);
-    CoordParams cp;
-    const double D1 = dirichlet_closed(1.0 / d.Nr, d.Ms), D2 = dirichlet_closed(2.0 / d.Nr, d.Ms);
-    cp.theta = 2.0 * acos(0.5 * sqrt((d.Ms - D2) / (d.Ms - D1)));
-    cp.cos_t = cos(cp.theta);
-    cp.sin_t = sin(cp.theta);
-    cp.Ms_odd_sign = ((d.Ms - 1) & 1) ? 1 : 0;
+    const CoordParams cp = coord_params(d);
     const long long n = d.nxy * d.Q;
     coord_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(g, cp, table, nullptr, nullptr, nullptr, nullptr);
     if (cudaGetLastError() != cudaSuccess) return GH_ECUDA;
-
-    HopParams hp;
-    hp.Q = d.Q;
-    hp.Nr = d.Nr;
-    hp.Nd = d.Nd;
-    hp.nvx = d.nvx;
-    hp.nvy = d.nvy;
-    hp.NB = d.nvy < 256 ? d.nvy : 256;
-    hp.SA = 256 / hp.NB;
-    hp.nxy = d.nxy;
-    hp.nv = d.nv;
-    hp.xy_per_cta = 1;
-    hp.lo2 = g.lo[2];
-    hp.step2 = g.step[2];
-    hp.lo3 = g.lo[3];
-    hp.step3 = g.step[3];
-    hp.kappa = g.kappa;
-    const int need = (d.nvx + hp.SA - 1) / hp.SA;
-    const float2* maps = (const float2*)maps_dev;
-    int st;
-    if (need <= 1)
-        st = noalloc_score<1>(stream, d, hp, maps, table, scores_dev, parts, result, num_sms, smem_optin);
-    else if (need <= 2)
-        st = noalloc_score<2>(stream, d, hp, maps, table, scores_dev, parts, result, num_sms, smem_optin);
-    else if (need <= 4)
-        st = noalloc_score<4>(stream, d, hp, maps, table, scores_dev, parts, result, num_sms, smem_optin);
-    else if (need <= 8)
-        st = noalloc_score<8>(stream, d, hp, maps, table, scores_dev, parts, result, num_sms, smem_optin);
-    else if (need <= 16)
-        st = noalloc_score<16>(stream, d, hp, maps, table, scores_dev, parts, result, num_sms, smem_optin);
-    else
-        st = noalloc_score<32>(stream, d, hp, maps, table, scores_dev, parts, result, num_sms, smem_optin);
+    const HopParams hp = hop_params(d, g);
+    long long nparts = 0;
+    int st = hop_launch(stream, d, hp, (const float2*)maps_dev, table, scores_dev, nullptr, 0, parts,
+                        kNoAllocMaxCtas, num_sms, (size_t)smem_optin, &nparts);
     if (st != GH_OK) return st;
+    argmax_finalize_kernel<<<1, 1024, 0, stream>>>(parts, (int)nparts, result);
+    if (cudaGetLastError() != cudaSuccess) return GH_ECUDA;
     if (best_cell || best_score) {
         ArgResult h;
         if (cudaMemcpyAsync(&h, result, sizeof(h), cudaMemcpyDeviceToHost, stream) != cudaSuccess) return GH_ECUDA;

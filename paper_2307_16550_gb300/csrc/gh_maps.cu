@@ -1,8 +1,9 @@
 // Range-Doppler maps (Sec. III: the 2D FFT of each Y_q; Sec. IV: the FFT bins
 // are correlations with the atoms on the FFT's frequency grid).
 //
-// Two kernels, both radix-2 Stockham FFTs in shared memory with float32 data
-// and twiddles rounded from float64:
+// Two kernels, both Stockham FFTs in shared memory (radix-4 passes, one
+// radix-2 pass for odd log2 sizes) with float32 data and a twiddle table
+// rounded from float64 and staged in shared memory:
 //   range_fft   : per (q, mc) row, the Ms samples zero-padded to Nr = pad*Ms,
 //                 written [Q][Mc][Nr];
 //   doppler_fft : per (q, block of IB range bins), the Mc chirps zero-padded to
@@ -20,23 +21,58 @@ namespace {
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
-// In-place (ping-pong) radix-2 Stockham FFT of `ncol` columns of length
-// N = 2^logN stored at x + c*ld. tw[t] = exp(-j 2 pi t / N), t < N/2.
-// Returns the buffer holding the transform (x or y).
-__device__ float2* fft_columns(float2* x, float2* y, int logN, int ncol, int ld, const float2* __restrict__ tw) {
-    const int half = 1 << (logN - 1);
-    const int total = ncol << (logN - 1);
-    for (int s = 0; s < logN; ++s) {
-        const int Ns = 1 << s;
-        const int twshift = logN - 1 - s;
+// Ping-pong Stockham FFT of `ncol` columns of length N = 2^logN stored at
+// x + c*ld: radix-4 passes, then one radix-2 pass when logN is odd.
+// tw[t] = exp(-j 2 pi t / N), t < 3N/4 (in shared memory). Returns the buffer
+// holding the transform (x or y).
+__device__ float2* fft_columns(float2* x, float2* y, int logN, int ncol, int ld, const float2* tw) {
+    const int N = 1 << logN;
+    int Ns = 1, rem = logN;
+    while (rem >= 2) {
+        const int lq = logN - 2, q4 = 1 << lq;
+        const int total = ncol << lq;
+        const int tstep = N / (4 * Ns);
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int c = idx >> (logN - 1);
+            const int c = idx >> lq;
+            const int j = idx & (q4 - 1);
+            const int k = j & (Ns - 1);
+            const float2* xc = x + c * ld;
+            float2* yc = y + c * ld;
+            float2 v0 = xc[j], v1 = xc[j + q4], v2 = xc[j + 2 * q4], v3 = xc[j + 3 * q4];
+            if (Ns > 1) {
+                const int s = tstep * k;
+                v1 = cmul(v1, tw[s]);
+                v2 = cmul(v2, tw[2 * s]);
+                v3 = cmul(v3, tw[3 * s]);
+            }
+            const float2 a = f2add(v0, v2), b = f2sub(v0, v2), cc = f2add(v1, v3);
+            const float2 dd = f2sub(v1, v3);
+            const float2 d = make_float2(dd.y, -dd.x);  // (v1 - v3) * (-j)
+            const int o = ((j - k) << 2) + k;
+            yc[o] = f2add(a, cc);
+            yc[o + Ns] = f2add(b, d);
+            yc[o + 2 * Ns] = f2sub(a, cc);
+            yc[o + 3 * Ns] = f2sub(b, d);
+        }
+        __syncthreads();
+        float2* t = x;
+        x = y;
+        y = t;
+        Ns <<= 2;
+        rem -= 2;
+    }
+    if (rem == 1) {
+        const int lh = logN - 1, half = 1 << lh;
+        const int total = ncol << lh;
+        const int tstep = N / (2 * Ns);
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int c = idx >> lh;
             const int j = idx & (half - 1);
             const int k = j & (Ns - 1);
             const float2* xc = x + c * ld;
             float2* yc = y + c * ld;
-            float2 a = xc[j];
-            float2 b = cmul(xc[j + half], __ldg(&tw[k << twshift]));
+            const float2 a = xc[j];
+            const float2 b = cmul(xc[j + half], tw[tstep * k]);
             const int o = ((j - k) << 1) + k;
             yc[o] = f2add(a, b);
             yc[o + Ns] = f2sub(a, b);
@@ -49,6 +85,10 @@ __device__ float2* fft_columns(float2* x, float2* y, int logN, int ncol, int ld,
     return x;
 }
 
+__device__ void load_twiddles(float2* dst, const float2* __restrict__ src, int n) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = __ldg(src + t);
+}
+
 __global__ void __launch_bounds__(256) range_fft_kernel(const float2* __restrict__ Y, float2* __restrict__ out,
                                                         int Ms, int logNr, int rows, int rows_per_cta,
                                                         const float2* __restrict__ tw) {
@@ -58,13 +98,15 @@ __global__ void __launch_bounds__(256) range_fft_kernel(const float2* __restrict
     const int nrow = min(rows_per_cta, rows - r0);
     float2* x = smem;
     float2* y = smem + rows_per_cta * Nr;
+    float2* twS = y + rows_per_cta * Nr;
+    load_twiddles(twS, tw, 3 * Nr / 4);
     for (int idx = threadIdx.x; idx < nrow * Nr; idx += blockDim.x) {
         const int c = idx >> logNr;
         const int n = idx & (Nr - 1);
         x[idx] = n < Ms ? Y[(size_t)(r0 + c) * Ms + n] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    float2* res = fft_columns(x, y, logNr, nrow, Nr, tw);
+    float2* res = fft_columns(x, y, logNr, nrow, Nr, twS);
     for (int idx = threadIdx.x; idx < nrow * Nr; idx += blockDim.x) out[(size_t)r0 * Nr + idx] = res[idx];
 }
 
@@ -80,6 +122,8 @@ __global__ void __launch_bounds__(256) doppler_fft_kernel(const float2* __restri
     float2* x = smem;
     float2* y = smem + IB * ld;
     float2* ramp = y + IB * ld;
+    float2* twS = ramp + IB;
+    load_twiddles(twS, tw, 3 * Nd / 4);
     const float2* src = Zr + (size_t)q * Mc * Nr + i0;
     for (int idx = threadIdx.x; idx < Mc * IB; idx += blockDim.x) {
         const int mc = idx / IB;
@@ -99,7 +143,7 @@ __global__ void __launch_bounds__(256) doppler_fft_kernel(const float2* __restri
         ramp[threadIdx.x] = make_float2(c, s);
     }
     __syncthreads();
-    float2* res = fft_columns(x, y, logNd, IB, ld, tw);
+    float2* res = fft_columns(x, y, logNd, IB, ld, twS);
     float2* dst = maps + ((size_t)q * Nr + i0) * Nd;
     for (int idx = threadIdx.x; idx < IB * Nd; idx += blockDim.x) {
         const int c = idx >> logNd;
@@ -114,28 +158,30 @@ int ilog2(int v) {
     return l;
 }
 
-// Uploads exp(-j 2 pi t / N), t < N/2, for N = Nr then N = Nd (float64 -> float32).
+// Uploads exp(-j 2 pi t / N), t < 3N/4, for N = Nr then N = Nd (float64 -> float32).
 int ensure_twiddles(gh_ctx* ctx, int Nr, int Nd, const float2** twr, const float2** twd) {
-    size_t bytes = (size_t)(Nr / 2 + Nd / 2) * sizeof(float2);
+    const int nr = 3 * Nr / 4, nd = 3 * Nd / 4;
+    size_t bytes = (size_t)(nr + nd) * sizeof(float2);
     void* p;
     GH_TRY(gh_ws(ctx, WS_TWIDDLE, bytes, &p));
     if (ctx->tw_n[0] != Nr || ctx->tw_n[1] != Nd) {
-        std::vector<float2> h(Nr / 2 + Nd / 2);
+        std::vector<float2> h(nr + nd);
         const double two_pi = 6.283185307179586476925286766559;
-        for (int t = 0; t < Nr / 2; ++t) {
+        for (int t = 0; t < nr; ++t) {
             double a = -two_pi * (double)t / (double)Nr;
             h[t] = make_float2((float)cos(a), (float)sin(a));
         }
-        for (int t = 0; t < Nd / 2; ++t) {
+        for (int t = 0; t < nd; ++t) {
             double a = -two_pi * (double)t / (double)Nd;
-            h[Nr / 2 + t] = make_float2((float)cos(a), (float)sin(a));
+            h[nr + t] = make_float2((float)cos(a), (float)sin(a));
         }
         GH_CUDA(cudaMemcpyAsync(p, h.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
+        GH_CUDA(cudaStreamSynchronize(ctx->stream));  // h goes out of scope
         ctx->tw_n[0] = Nr;
         ctx->tw_n[1] = Nd;
     }
     *twr = (const float2*)p;
-    *twd = (const float2*)p + Nr / 2;
+    *twd = (const float2*)p + nr;
     return GH_OK;
 }
 
@@ -152,7 +198,7 @@ int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, float2* maps) {
     int rpc = 2048 / d.Nr;
     if (rpc < 1) rpc = 1;
     const int rows = d.Q * d.Mc;
-    size_t smem1 = (size_t)2 * rpc * d.Nr * sizeof(float2);
+    size_t smem1 = ((size_t)2 * rpc * d.Nr + 3 * d.Nr / 4) * sizeof(float2);
     GH_CUDA(cudaFuncSetAttribute(range_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_RANGE_FFT, &ev);
@@ -165,7 +211,7 @@ int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, float2* maps) {
     if (IB < 1) IB = 1;
     if (IB > 16) IB = 16;
     if (IB > d.Nr) IB = d.Nr;
-    size_t smem2 = ((size_t)2 * IB * (d.Nd + 1) + IB) * sizeof(float2);
+    size_t smem2 = ((size_t)2 * IB * (d.Nd + 1) + IB + 3 * d.Nd / 4) * sizeof(float2);
     GH_CUDA(cudaFuncSetAttribute(doppler_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
     gh_launch_begin(ctx, GH_K_DOPPLER_FFT, &ev);
     doppler_fft_kernel<<<dim3(d.Nr / IB, d.Q), 256, smem2, ctx->stream>>>((const float2*)zr, maps, d.Ms, d.Mc,

@@ -33,7 +33,7 @@ def test_coord_table_bit_exact(ctx, make):
     np.testing.assert_array_equal(tau, ref["tau"])
     np.testing.assert_array_equal(w[..., 0], ref["wx"])
     np.testing.assert_array_equal(w[..., 1], ref["wy"])
-    np.testing.assert_allclose(coef, ref["c"], atol=2e-7)
+    np.testing.assert_allclose(coef, ref["c"], atol=1e-6)  # stored in float32
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
