@@ -262,6 +262,17 @@ GH_API int gh_score_grid_noalloc(void* stream, const gh_radar* radar,
                                  float* scores_dev, int64_t* best_cell, float* best_score);
 
 /*
+ * gh_selftest_tcgen05 - diagnostic of the tensor-core plumbing the exact
+ * direct path uses (no counterpart in the paper): D = A * B^T with M = 128,
+ * A and B rounded to BF16, FP32 accumulation in tensor memory.
+ *   A_host : host float[128][K]; B_host : host float[N][K]; D_host : host float[128][N]
+ *   N a multiple of 32 in [32, 256]; K a multiple of 16 in [16, 256].
+ * GH_ETIMEOUT if the completion barrier does not arrive within its wait limit.
+ */
+GH_API int gh_selftest_tcgen05(gh_ctx* ctx, const float* A_host, const float* B_host,
+                               float* D_host, int32_t N, int32_t K);
+
+/*
  * Instrumentation. gh_set_timing(ctx, mask) brackets every launch of the
  * kernel classes whose bit (1 << GH_K_*) is set in `mask` with CUDA events on
  * the context's stream (mask 0: off; -1: all classes). gh_kernel_stats

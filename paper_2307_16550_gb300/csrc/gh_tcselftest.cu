@@ -1,0 +1,96 @@
+// Self-test of the tensor-core plumbing used by the exact direct path:
+// D = A * B^T for M = 128, one CTA, BF16 operands in shared memory (no-swizzle
+// K-major layout), FP32 accumulation in tensor memory, mbarrier completion.
+#include "gh_internal.cuh"
+#include "gh_tc.cuh"
+
+namespace {
+
+constexpr uint32_t kWaitIters = 1u << 22;
+
+__global__ void __launch_bounds__(128) tc_selftest_kernel(const float* __restrict__ A, const float* __restrict__ B,
+                                                          float* __restrict__ D, int N, int K, int* status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_holder;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t lboA = (128 / 8) * 128, lboB = (uint32_t)(N / 8) * 128, sbo = 128;
+    unsigned char* sA = smem;
+    unsigned char* sB = smem + (size_t)128 * K * 2;
+    for (int idx = tid; idx < 128 * K; idx += blockDim.x) {
+        const int r = idx / K, k = idx % K;
+        *(__nv_bfloat16*)(sA + gh_tc::kmajor_off(r, k, lboA, sbo)) = __float2bfloat16_rn(A[idx]);
+    }
+    for (int idx = tid; idx < N * K; idx += blockDim.x) {
+        const int r = idx / K, k = idx % K;
+        *(__nv_bfloat16*)(sB + gh_tc::kmajor_off(r, k, lboB, sbo)) = __float2bfloat16_rn(B[idx]);
+    }
+    gh_tc::fence_smem_to_async();
+    if (tid == 0) {
+        gh_tc::mbar_init(&bar, 1);
+        gh_tc::mbar_fence_init();
+    }
+    if (warp == 0) gh_tc::tmem_alloc(&tmem_holder, 256);
+    gh_tc::fence_before_sync();
+    __syncthreads();
+    gh_tc::fence_after_sync();
+    const uint32_t tmem = tmem_holder;
+    if (tid == 0) {
+        const uint32_t idesc = gh_tc::idesc_bf16_f32(128, (uint32_t)N);
+        const uint32_t a0 = gh_tc::smem_u32(sA), b0 = gh_tc::smem_u32(sB);
+        for (int kk = 0; kk < K / 16; ++kk) {
+            const uint64_t ad = gh_tc::smem_desc(a0 + 2 * kk * lboA, lboA, sbo);
+            const uint64_t bd = gh_tc::smem_desc(b0 + 2 * kk * lboB, lboB, sbo);
+            gh_tc::mma_bf16(tmem, ad, bd, idesc, kk > 0);
+        }
+        gh_tc::mma_commit(&bar);
+    }
+    const bool ok = gh_tc::mbar_wait_bounded(&bar, 0, kWaitIters);
+    if (!ok && lane == 0) atomicExch(status, GH_ETIMEOUT);
+    gh_tc::fence_after_sync();
+    if (ok) {
+        for (int c0 = 0; c0 < N; c0 += 32) {
+            float v[32];
+            gh_tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+            const int row = 32 * warp + lane;
+            for (int i = 0; i < 32 && c0 + i < N; ++i) D[(size_t)row * N + c0 + i] = v[i];
+        }
+    }
+    gh_tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) gh_tc::tmem_dealloc(tmem, 256);
+}
+
+}  // namespace
+
+extern "C" int gh_selftest_tcgen05(gh_ctx* ctx, const float* A_host, const float* B_host, float* D_host, int32_t N,
+                                   int32_t K) {
+    if (!ctx) return GH_EINVAL;
+    if (!A_host || !B_host || !D_host) return gh_fail(ctx, GH_EINVAL, "NULL argument");
+    if (N < 32 || N > 256 || N % 32 != 0 || K < 16 || K > 256 || K % 16 != 0)
+        return gh_fail(ctx, GH_EINVAL, "N must be a multiple of 32 in [32, 256], K a multiple of 16 in [16, 256]");
+    cudaSetDevice(ctx->device);
+    const size_t a = (size_t)128 * K, b = (size_t)N * K, dsz = (size_t)128 * N;
+    void* buf;
+    GH_TRY(gh_ws(ctx, WS_DIAG, (a + b + dsz) * sizeof(float) + 256, &buf));
+    float* dA = (float*)buf;
+    float* dB = dA + a;
+    float* dD = dB + b;
+    int* status = (int*)(dD + dsz);
+    GH_CUDA(cudaMemcpyAsync(dA, A_host, a * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    GH_CUDA(cudaMemcpyAsync(dB, B_host, b * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    GH_CUDA(cudaMemsetAsync(status, 0, sizeof(int), ctx->stream));
+    GH_CUDA(cudaMemsetAsync(dD, 0, dsz * sizeof(float), ctx->stream));
+    const size_t smem = (a + b) * 2;
+    GH_CUDA(cudaFuncSetAttribute(tc_selftest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaEvent_t ev;
+    gh_launch_begin(ctx, GH_K_EXACT_S2, &ev);
+    tc_selftest_kernel<<<1, 128, smem, ctx->stream>>>(dA, dB, dD, N, K, status);
+    GH_TRY(gh_launch_end(ctx, GH_K_EXACT_S2, ev, "tc_selftest_kernel"));
+    int st = 0;
+    GH_CUDA(cudaMemcpyAsync(D_host, dD, dsz * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    GH_CUDA(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    GH_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (st != 0) return gh_fail(ctx, GH_ETIMEOUT, "tensor-core self-test: mbarrier wait timed out");
+    return GH_OK;
+}

@@ -63,6 +63,7 @@ _SIGNATURES = {
     "gh_coord_table": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, ctypes.POINTER(GhGrid), _P, _P, _P, _P]),
     "gh_score_grid_noalloc": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, ctypes.POINTER(GhGrid),
                                      _P, _P, _P]),
+    "gh_selftest_tcgen05": (_I32, [_P, _P, _P, _P, _I32, _I32]),
     "gh_set_timing": (_I32, [_P, _I32]),
     "gh_kernel_stats": (_I32, [_P, _I32, _PD, ctypes.POINTER(ctypes.c_int64)]),
     "gh_reset_stats": (_I32, [_P]),
@@ -244,6 +245,16 @@ class Context:
             self.handle, ctypes.byref(radar_struct(radar)), _ptr(txa), _ptr(rxa), int(Q),
             ctypes.byref(grid_struct(grid)), _ptr(ib), _ptr(tau), _ptr(coef), _ptr(w)))
         return ib, tau, coef, w
+
+    def gh_selftest_tcgen05(self, A, B):
+        """D = A @ B.T on the tensor cores (A: 128 x K, B: N x K, rounded to BF16)."""
+        A = np.ascontiguousarray(A, dtype=np.float32)
+        B = np.ascontiguousarray(B, dtype=np.float32)
+        N, K = B.shape
+        D = np.zeros((128, N), np.float32)
+        self._check("gh_selftest_tcgen05", self._lib.gh_selftest_tcgen05(self.handle, _ptr(A), _ptr(B), _ptr(D),
+                                                                         int(N), int(K)))
+        return D
 
     def gh_set_timing(self, enable):
         """True: time every kernel class; False: none; a kind name, an int mask
