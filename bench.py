@@ -314,7 +314,8 @@ def run_ours(args):
     nxy = sc.grid.n[0] * sc.grid.n[1]
     nv = sc.grid.n[2] * sc.grid.n[3]
     flops = 8.0 * sc.Q * nxy * sc.radar.Mc * (sc.radar.Ms + nv)
-    ex_kernel_s = (s1_ms + s2_ms) * 1e-3 / max(s1_n, 1)
+    # one exact scoring pass = stage 1 (+ its phase table) and one stage-2 launch
+    ex_kernel_s = (s1_ms + s2_ms) * 1e-3 / max(s2_n, 1)
     out = None
     if rank == 0:
         Y_np = Yd.cpu().numpy().astype(np.complex128)

@@ -346,13 +346,32 @@ static int stage_Y(gh_ctx* ctx, const Dims& d, const void* Y, const float2** Yde
     return GH_OK;
 }
 
+// The result workspace holds kResultSlots ArgResults; the last slot's first
+// int is the device status word written by kernels with bounded waits.
+constexpr int kResultSlots = 64;
+
+int* gh_status_dev(gh_ctx* ctx) { return (int*)((ArgResult*)ctx->ws[WS_RESULT] + (kResultSlots - 1)); }
+
+int gh_status_reset(gh_ctx* ctx) {
+    GH_CUDA(cudaMemsetAsync(gh_status_dev(ctx), 0, sizeof(int), ctx->stream));
+    return GH_OK;
+}
+
+static int check_status(gh_ctx* ctx, const ArgResult* host_slots) {
+    const int st = *(const int*)(host_slots + (kResultSlots - 1));
+    if (st != 0) return gh_fail(ctx, st, "a device-side wait gave up (status %d)", st);
+    return GH_OK;
+}
+
+// Copies the whole result block (results and status word) to pinned memory.
 static int read_result(gh_ctx* ctx, const ArgResult* res, int64_t* best_cell, float* best_score) {
-    if (!best_cell && !best_score) return GH_OK;
     void* h;
-    GH_TRY(gh_pinned(ctx, sizeof(ArgResult), &h));
-    GH_CUDA(cudaMemcpyAsync(h, res, sizeof(ArgResult), cudaMemcpyDeviceToHost, ctx->stream));
+    GH_TRY(gh_pinned(ctx, kResultSlots * sizeof(ArgResult), &h));
+    GH_CUDA(cudaMemcpyAsync(h, ctx->ws[WS_RESULT], kResultSlots * sizeof(ArgResult), cudaMemcpyDeviceToHost,
+                            ctx->stream));
     GH_CUDA(cudaStreamSynchronize(ctx->stream));
-    const ArgResult* r = (const ArgResult*)h;
+    GH_TRY(check_status(ctx, (const ArgResult*)h));
+    const ArgResult* r = (const ArgResult*)h + (res - (const ArgResult*)ctx->ws[WS_RESULT]);
     if (best_cell) *best_cell = r->cell;
     if (best_score) *best_score = r->score;
     return GH_OK;
@@ -406,8 +425,10 @@ extern "C" int gh_score_grid(gh_ctx* ctx, const gh_radar* radar, const double* t
     void* table;
     GH_TRY(build_table(ctx, d, geo, &table));
     void* res;
-    GH_TRY(gh_ws(ctx, WS_RESULT, 64 * sizeof(ArgResult), &res));
+    GH_TRY(gh_ws(ctx, WS_RESULT, kResultSlots * sizeof(ArgResult), &res));
+    GH_TRY(gh_status_reset(ctx));
     GH_TRY(gh_launch_hop(ctx, d, geo, (const float2*)maps_dev, table, scores_dev, nullptr, 0, (ArgResult*)res));
+    if (!best_cell && !best_score) return GH_OK;
     return read_result(ctx, (const ArgResult*)res, best_cell, best_score);
 }
 
@@ -430,7 +451,8 @@ extern "C" int gh_direct_exact(gh_ctx* ctx, const gh_radar* radar, const double*
     GeoParams geo;
     gh_fill_geo(&geo, radar, tx_host, rx_host, Q, grid);
     void* res;
-    GH_TRY(gh_ws(ctx, WS_RESULT, 64 * sizeof(ArgResult), &res));
+    GH_TRY(gh_ws(ctx, WS_RESULT, kResultSlots * sizeof(ArgResult), &res));
+    GH_TRY(gh_status_reset(ctx));
     GH_TRY(gh_launch_exact(ctx, d, geo, Yd, scores_dev, nullptr, 0, (ArgResult*)res));
     return read_result(ctx, (const ArgResult*)res, best_cell, best_score);
 }
@@ -457,7 +479,8 @@ extern "C" int gh_detect(gh_ctx* ctx, int32_t method, const gh_radar* radar, con
     size_t mbytes = (size_t)d.Q * d.Nr * d.Nd * sizeof(float2);
     void *R, *maps = nullptr, *table = nullptr, *res, *bws;
     GH_TRY(gh_ws(ctx, WS_R, ybytes, &R));
-    GH_TRY(gh_ws(ctx, WS_RESULT, 64 * sizeof(ArgResult), &res));
+    GH_TRY(gh_ws(ctx, WS_RESULT, kResultSlots * sizeof(ArgResult), &res));
+    GH_TRY(gh_status_reset(ctx));
     GH_TRY(gh_ws(ctx, WS_BOMP, gh_bomp_ws_bytes(d, K), &bws));
     if (method == GH_HOP) {
         GH_TRY(gh_ws(ctx, WS_MAPS, mbytes, &maps));
@@ -481,8 +504,8 @@ extern "C" int gh_detect(gh_ctx* ctx, int32_t method, const gh_radar* radar, con
         GH_CUDA(cudaMemcpyAsync(mask + k, &sel[k].cell, sizeof(int64_t), cudaMemcpyDeviceToDevice, ctx->stream));
         cur = (const float2*)R;
     }
-    // results: selections and the final amplitudes
-    size_t sel_bytes = (size_t)K * sizeof(ArgResult);
+    // results: selections, status word and the final amplitudes
+    size_t sel_bytes = (size_t)kResultSlots * sizeof(ArgResult);
     size_t alpha_bytes = (size_t)K * d.Q * 2 * sizeof(double);
     void* h;
     GH_TRY(gh_pinned(ctx, sel_bytes + alpha_bytes, &h));
@@ -491,6 +514,7 @@ extern "C" int gh_detect(gh_ctx* ctx, int32_t method, const gh_radar* radar, con
     GH_CUDA(cudaMemcpyAsync((char*)h + sel_bytes, bws, alpha_bytes, cudaMemcpyDeviceToHost, ctx->stream));
     GH_CUDA(cudaStreamSynchronize(ctx->stream));
     const ArgResult* hs = (const ArgResult*)h;
+    GH_TRY(check_status(ctx, hs));
     for (int k = 0; k < K; ++k) {
         cells_host[k] = hs[k].cell;
         if (scores_host) scores_host[k] = hs[k].score;

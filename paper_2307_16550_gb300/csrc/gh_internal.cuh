@@ -28,6 +28,7 @@ enum WsSlot {
     WS_EXACT_P,     // exact stage 1 output [Q][nxy][Mc] complex64
     WS_DIAG,        // coordinate-table diagnostics
     WS_TWIDDLE,     // FFT twiddle tables
+    WS_EXACT_TAB,   // exact-path phase table [nxy][Q]
     WS_COUNT
 };
 
@@ -79,6 +80,11 @@ int gh_fail(gh_ctx* ctx, int status, const char* fmt, ...);
 // Grow-only workspace slot; returns GH_OK and sets *p.
 int gh_ws(gh_ctx* ctx, WsSlot slot, size_t bytes, void** p);
 int gh_pinned(gh_ctx* ctx, size_t bytes, void** p);
+
+// Device status word (0 = ok, else a GH_E* code written by a kernel), kept in
+// the result workspace; gh_status_reset zeroes it on the context's stream.
+int* gh_status_dev(gh_ctx* ctx);
+int gh_status_reset(gh_ctx* ctx);
 
 // Launch bookkeeping: call gh_launch_begin before a kernel launch and
 // gh_launch_end right after it (checks the launch error, records events).
