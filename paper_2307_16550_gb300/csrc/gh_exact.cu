@@ -22,7 +22,7 @@ constexpr int S1_MT = 64;   // chirps per stage-1 CTA
 constexpr int S1_KT = 32;   // samples per k-step
 
 __global__ void __launch_bounds__(256) exact_stage1_kernel(const float2* __restrict__ Y, GeoParams g,
-                                                           float2* __restrict__ P) {
+                                                           float* __restrict__ P) {
     __shared__ float2 As[S1_XT][S1_KT + 1];
     __shared__ float2 Bs[S1_MT][S1_KT + 1];
     __shared__ unsigned long long rfix[S1_XT];
@@ -86,7 +86,11 @@ __global__ void __launch_bounds__(256) exact_stage1_kernel(const float2* __restr
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int mc = mc0 + tx + 16 * j;
-            if (mc < g.Mc) P[((size_t)q * nxy + xy) * g.Mc + mc] = acc[i][j];
+            if (mc < g.Mc) {
+                float* row = P + ((size_t)q * nxy + xy) * 2 * g.Mc;  // planar: Re row, then Im row
+                row[mc] = acc[i][j].x;
+                row[g.Mc + mc] = acc[i][j].y;
+            }
         }
     }
 }
@@ -102,7 +106,7 @@ constexpr int S2_MCC = 64;  // chirps per stage-2 chunk
 
 // One CTA per (x, y) cell; CPT velocity cells per thread.
 template <int CPT>
-__global__ void __launch_bounds__(256) exact_stage2_kernel(const float2* __restrict__ P, GeoParams g,
+__global__ void __launch_bounds__(256) exact_stage2_kernel(const float* __restrict__ P, GeoParams g,
                                                            float* __restrict__ scores,
                                                            const int64_t* __restrict__ mask, int nmask,
                                                            ArgPartial* __restrict__ parts) {
@@ -137,7 +141,7 @@ __global__ void __launch_bounds__(256) exact_stage2_kernel(const float2* __restr
         float2 F[CPT];
 #pragma unroll
         for (int c = 0; c < CPT; ++c) F[c] = make_float2(0.f, 0.f);
-        const float2* Pq = P + ((size_t)q * nxy + xy) * g.Mc;
+        const float* Pq = P + ((size_t)q * nxy + xy) * 2 * g.Mc;  // planar: Re row, then Im row
         for (int mc0 = 0; mc0 < g.Mc; mc0 += S2_MCC) {
             __syncthreads();
             for (int idx = tid; idx < nvx * S2_MCC; idx += blockDim.x) {
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(256) exact_stage2_kernel(const float2* __restr
             for (int idx = tid; idx < nvy * S2_MCC; idx += blockDim.x) {
                 const int b = idx / S2_MCC, k = idx - b * S2_MCC;
                 const int mc = mc0 + k;
-                const float2 pv = mc < g.Mc ? Pq[mc] : make_float2(0.f, 0.f);
+                const float2 pv = mc < g.Mc ? make_float2(Pq[mc], Pq[g.Mc + mc]) : make_float2(0.f, 0.f);
                 const float2 e = gh_cis_fix(phy[b] * (unsigned long long)mc);
                 Ey[idx] = cmulc(pv, e);  // P[mc] * conj(e)
             }
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(256) exact_stage2_kernel(const float2* __restr
 }
 
 template <int CPT>
-int launch_s2(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* P, float* scores, const int64_t* mask,
+int launch_s2(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float* P, float* scores, const int64_t* mask,
               int nmask, ArgPartial* parts) {
     const size_t smem = (size_t)(d.nvx + d.nvy) * S2_MCC * sizeof(float2) + (size_t)(d.nvx + d.nvy) * 8;
     if (smem > ctx->smem_optin) return gh_fail(ctx, GH_ENOTSUP, "exact stage 2 needs %zu B shared memory", smem);
@@ -270,52 +274,69 @@ struct ExactTcParams {
 
 constexpr uint32_t kTcWaitIters = 1u << 22;
 
-// z[k] = exp(-j 2 pi ph (m0 + k)), k < 32, reseeded exactly every 8 chirps.
-__device__ __forceinline__ void atoms32(unsigned long long ph, int m0, float2* z) {
+// z[k] = exp(-j 2 pi ph (m0 + k)), k < 16: an exact seed at k = 0, the other
+// entries by repeated multiplication with exp(-j 2 pi ph).
+__device__ __forceinline__ void atoms16(unsigned long long ph, int m0, float2* z) {
     const float2 w = gh_cis_fix(0ull - ph);
+    float2 v = gh_cis_fix(0ull - ph * (unsigned long long)m0);
+    z[0] = v;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        float2 v = gh_cis_fix(0ull - ph * (unsigned long long)(m0 + 8 * j));
-        z[8 * j] = v;
-#pragma unroll
-        for (int i = 1; i < 8; ++i) {
-            v = cmul(v, w);
-            z[8 * j + i] = v;
-        }
+    for (int i = 1; i < 16; ++i) {
+        v = cmul(v, w);
+        z[i] = v;
     }
 }
 
-__device__ __forceinline__ void store_chunk(unsigned char* hi, unsigned char* lo, uint32_t off, const float* v) {
-    uint4 h, l;
-    gh_tc::split_bf16x2(v[0], v[1], &h.x, &l.x);
-    gh_tc::split_bf16x2(v[2], v[3], &h.y, &l.y);
-    gh_tc::split_bf16x2(v[4], v[5], &h.z, &l.z);
-    gh_tc::split_bf16x2(v[6], v[7], &h.w, &l.w);
-    *(uint4*)(hi + off) = h;
-    *(uint4*)(lo + off) = l;
+// BF16 high/low parts of the real and imaginary parts of z[0..15], packed in
+// pairs of consecutive entries.
+__device__ __forceinline__ void split16(const float2* z, uint32_t* reH, uint32_t* reL, uint32_t* imH,
+                                        uint32_t* imL) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        gh_tc::split_bf16x2(z[2 * i].x, z[2 * i + 1].x, &reH[i], &reL[i]);
+        gh_tc::split_bf16x2(z[2 * i].y, z[2 * i + 1].y, &imH[i], &imL[i]);
+    }
 }
 
+__device__ __forceinline__ void st16(unsigned char* p, const uint32_t* w, uint32_t flip) {
+    *(uint4*)p = make_uint4(w[0] ^ flip, w[1] ^ flip, w[2] ^ flip, w[3] ^ flip);
+}
+
+// 256 threads, 8 warps. Generation: warp w < 4 writes A rows, w >= 4 B rows;
+// receiver half h = (w & 3) >> 1; chirp half kh = w & 1 (chirps 16 kh .. 16 kh + 15
+// of the 32-chirp stage). An A lane a writes both the Re F row (h*64 + a) and the
+// Im F row (h*64 + 32 + a) from one set of atoms. Epilogue: warp w reads TMEM
+// lanes 32 (w % 4) .. +31 (quarter: Re/Im F of receiver half) and column half w / 4.
 template <int NV32>
-__global__ void __launch_bounds__(128) exact_tc_kernel(const float2* __restrict__ P, const ExEntry* __restrict__ tab,
-                                                       ExactTcParams p, float* __restrict__ scores,
-                                                       const int64_t* __restrict__ mask, int nmask,
-                                                       ArgPartial* __restrict__ parts, int* __restrict__ status) {
+__global__ void __launch_bounds__(256, 2) exact_tc_kernel(const float* __restrict__ P, const ExEntry* __restrict__ tab,
+                                                          ExactTcParams p, float* __restrict__ scores,
+                                                          const int64_t* __restrict__ mask, int nmask,
+                                                          ArgPartial* __restrict__ parts, int* __restrict__ status) {
     constexpr int NVP = 32 * NV32;           // padded nvy
     constexpr int N = 2 * NVP;               // MMA N
+    constexpr int NH = NVP / 2;              // columns per epilogue warp
     constexpr uint32_t SBO = 128, LBO_A = 16 * 128, LBO_B = (N / 8) * 128;
     constexpr uint32_t A_BYTES = 128 * 64 * 2, B_BYTES = N * 64 * 2;
     constexpr uint32_t BUF_BYTES = 2 * A_BYTES + 2 * B_BYTES;
     constexpr uint32_t TM_COLS = 2 * N <= 32 ? 32 : (2 * N <= 64 ? 64 : (2 * N <= 128 ? 128 : (2 * N <= 256 ? 256 : 512)));
+    constexpr uint32_t FLIP = 0x80008000u;  // sign bits of a BF16 pair
     extern __shared__ __align__(1024) unsigned char smem[];
-    float* xfer = (float*)(smem + 2 * BUF_BYTES);  // [32][NVP]
+    // [6][32][NH] cross-warp sums; reuses the operand buffers, which are idle
+    // between the last epilogue of one (x, y) cell and the first stage of the next
+    float* xfer = (float*)smem;
+    static_assert(6 * 32 * NH * 4 <= 2 * BUF_BYTES, "cross-warp buffer must fit in the operand buffers");
     __shared__ uint64_t bar[2];
     __shared__ uint32_t tmem_holder;
-    __shared__ float s_bs[4];
-    __shared__ long long s_bc[4];
+    __shared__ float s_bs[8];
+    __shared__ long long s_bc[8];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int h = tid >> 6, a = (tid & 63) >> 1, part = tid & 1;
-    const int kh = tid & 1;
+    const bool a_role = warp < 4;
+    const int h = (warp & 3) >> 1;      // receiver of the pair (generation)
+    const int kh = warp & 1;            // chirp half of a stage (generation)
+    const int quarter = warp & 3;       // TMEM lane quarter (epilogue)
+    const int eh = quarter >> 1;        // receiver of the pair (epilogue)
+    const int chalf = warp >> 2;        // column half (epilogue)
     const int npairs = (p.Q + 1) >> 1;
 
     if (tid == 0) {
@@ -329,6 +350,8 @@ __global__ void __launch_bounds__(128) exact_tc_kernel(const float2* __restrict_
     gh_tc::fence_after_sync();
     const uint32_t tmem = tmem_holder;
     const uint32_t idesc = gh_tc::idesc_bf16_f32(128, N);
+    const uint32_t offA_re = gh_tc::kmajor_off((uint32_t)(h * 64 + lane), 0, LBO_A, SBO);
+    const uint32_t offA_im = gh_tc::kmajor_off((uint32_t)(h * 64 + 32 + lane), 0, LBO_A, SBO);
 
     float best = -INFINITY;
     long long bestc = 0x7fffffffffffffffLL;
@@ -337,16 +360,34 @@ __global__ void __launch_bounds__(128) exact_tc_kernel(const float2* __restrict_
     bool aborted = false;
 
     for (long long xy = blockIdx.x; xy < p.nxy && !aborted; xy += gridDim.x) {
-        float acc[NVP];
+        float acc[NH];
 #pragma unroll
-        for (int i = 0; i < NVP; ++i) acc[i] = 0.f;
+        for (int i = 0; i < NH; ++i) acc[i] = 0.f;
         for (int pp = 0; pp < npairs && !aborted; ++pp) {
-            const int qa = 2 * pp + h;
-            const bool va = qa < p.Q && a < p.nvx;
-            unsigned long long phx = 0;
-            if (va) {
-                const ExEntry& e = tab[xy * p.Q + qa];
-                phx = e.phx0 + (unsigned long long)a * e.dphx;
+            const int q = 2 * pp + h;
+            const bool vq = q < p.Q;
+            unsigned long long ph[NV32];
+            bool vrow[NV32];
+            const float* Pq = nullptr;  // planar Re row, then Im row
+            if (a_role) {
+                vrow[0] = vq && lane < p.nvx;
+                ph[0] = 0;
+                if (vrow[0]) {
+                    const ExEntry& e = tab[xy * p.Q + q];
+                    ph[0] = e.phx0 + (unsigned long long)lane * e.dphx;
+                }
+            } else {
+#pragma unroll
+                for (int g = 0; g < NV32; ++g) {
+                    const int b = lane + 32 * g;
+                    vrow[g] = vq && b < p.nvy;
+                    ph[g] = 0;
+                    if (vrow[g]) {
+                        const ExEntry& e = tab[xy * p.Q + q];
+                        ph[g] = e.phy0 + (unsigned long long)b * e.dphy;
+                    }
+                }
+                if (vq) Pq = P + ((size_t)q * p.nxy + xy) * 2 * p.Mc;
             }
             const uint32_t dcol = (uint32_t)(pair_ctr & 1) * N;
             for (int s = 0; s < p.nstages; ++s) {
@@ -362,66 +403,79 @@ __global__ void __launch_bounds__(128) exact_tc_kernel(const float2* __restrict_
                 unsigned char* Al = Ah + A_BYTES;
                 unsigned char* Bh = Al + A_BYTES;
                 unsigned char* Bl = Bh + B_BYTES;
-                const int m0 = 32 * s;
-                // ---- A: this thread's row ----
-                {
-                    float2 z[32];
-                    if (va) {
-                        atoms32(phx, m0, z);
+                const int m0 = 32 * s + 16 * kh;
+                // K positions of this chirp half: chunks 2kh, 2kh+1 (first half of K) and 4+2kh, 5+2kh
+                const uint32_t c0 = 2 * kh, c1 = 4 + 2 * kh;
+                if (a_role) {
+                    float2 z[16];
+                    if (vrow[0]) {
+                        atoms16(ph[0], m0, z);
                     } else {
 #pragma unroll
-                        for (int k = 0; k < 32; ++k) z[k] = make_float2(0.f, 0.f);
+                        for (int k = 0; k < 16; ++k) z[k] = make_float2(0.f, 0.f);
                     }
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        float v[8];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const float2 zz = z[(c & 3) * 8 + i];
-                            // chunks 0-3: [Re | Im] of the first half; 4-7: [-Im | Re]
-                            v[i] = part == 0 ? (c < 4 ? zz.x : -zz.y) : (c < 4 ? zz.y : zz.x);
-                        }
-                        store_chunk(Ah, Al, gh_tc::kmajor_off((uint32_t)tid, (uint32_t)(8 * c), LBO_A, SBO), v);
-                    }
-                }
-                // ---- B: rows n = tid/2 + 64 g, chirps m0 + 16 kh .. +15 ----
-#pragma unroll
-                for (int g = 0; g < N / 64; ++g) {
-                    const int n = (tid >> 1) + 64 * g;
-                    const int hb = n / NVP, b = n - hb * NVP;
-                    const int qb = 2 * pp + hb;
-                    const bool vb = qb < p.Q && b < p.nvy;
-                    float gr[16], gi[16];
-                    if (vb) {
-                        const ExEntry& e = tab[xy * p.Q + qb];
-                        const unsigned long long phy = e.phy0 + (unsigned long long)b * e.dphy;
-                        const float2* Pq = P + ((size_t)qb * p.nxy + xy) * p.Mc;
-                        const int mb = m0 + 16 * kh;
-                        const float2 w = gh_cis_fix(0ull - phy);
-#pragma unroll
-                        for (int j = 0; j < 2; ++j) {
-                            float2 at = gh_cis_fix(0ull - phy * (unsigned long long)(mb + 8 * j));
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                const int mc = mb + 8 * j + i;
-                                const float2 pv = mc < p.Mc ? __ldg(Pq + mc) : make_float2(0.f, 0.f);
-                                const float2 gv = cmul(pv, at);
-                                gr[8 * j + i] = gv.x;
-                                gi[8 * j + i] = gv.y;
-                                at = cmul(at, w);
-                            }
-                        }
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) gr[i] = gi[i] = 0.f;
-                    }
+                    uint32_t reH[8], reL[8], imH[8], imL[8];
+                    split16(z, reH, reL, imH, imL);
 #pragma unroll
                     for (int j = 0; j < 2; ++j) {
-                        store_chunk(Bh, Bl, gh_tc::kmajor_off((uint32_t)n, (uint32_t)(16 * kh + 8 * j), LBO_B, SBO),
-                                    gr + 8 * j);
-                        store_chunk(Bh, Bl,
-                                    gh_tc::kmajor_off((uint32_t)n, (uint32_t)(32 + 16 * kh + 8 * j), LBO_B, SBO),
-                                    gi + 8 * j);
+                        // Re F row: [Re z | -Im z]; Im F row: [Im z | Re z]
+                        st16(Ah + offA_re + (c0 + j) * LBO_A, reH + 4 * j, 0u);
+                        st16(Al + offA_re + (c0 + j) * LBO_A, reL + 4 * j, 0u);
+                        st16(Ah + offA_re + (c1 + j) * LBO_A, imH + 4 * j, FLIP);
+                        st16(Al + offA_re + (c1 + j) * LBO_A, imL + 4 * j, FLIP);
+                        st16(Ah + offA_im + (c0 + j) * LBO_A, imH + 4 * j, 0u);
+                        st16(Al + offA_im + (c0 + j) * LBO_A, imL + 4 * j, 0u);
+                        st16(Ah + offA_im + (c1 + j) * LBO_A, reH + 4 * j, 0u);
+                        st16(Al + offA_im + (c1 + j) * LBO_A, reL + 4 * j, 0u);
+                    }
+                } else {
+                    float2 pv[16];
+                    if (vq) {
+#pragma unroll
+                        for (int k = 0; k < 16; k += 4) {
+                            const int mc = m0 + k;
+                            float4 re = make_float4(0.f, 0.f, 0.f, 0.f), im = re;
+                            if (mc + 3 < p.Mc) {
+                                re = __ldg((const float4*)(Pq + mc));
+                                im = __ldg((const float4*)(Pq + p.Mc + mc));
+                            } else {
+                                float* rr = &re.x;
+                                float* ii = &im.x;
+#pragma unroll
+                                for (int t = 0; t < 4; ++t)
+                                    if (mc + t < p.Mc) {
+                                        rr[t] = __ldg(Pq + mc + t);
+                                        ii[t] = __ldg(Pq + p.Mc + mc + t);
+                                    }
+                            }
+                            pv[k] = make_float2(re.x, im.x);
+                            pv[k + 1] = make_float2(re.y, im.y);
+                            pv[k + 2] = make_float2(re.z, im.z);
+                            pv[k + 3] = make_float2(re.w, im.w);
+                        }
+                    }
+#pragma unroll
+                    for (int g = 0; g < NV32; ++g) {
+                        float2 z[16];
+                        if (vrow[g]) {
+                            atoms16(ph[g], m0, z);
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) z[k] = cmul(pv[k], z[k]);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) z[k] = make_float2(0.f, 0.f);
+                        }
+                        uint32_t reH[8], reL[8], imH[8], imL[8];
+                        split16(z, reH, reL, imH, imL);
+                        const uint32_t offB =
+                            gh_tc::kmajor_off((uint32_t)(h * NVP + lane + 32 * g), 0, LBO_B, SBO);
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            st16(Bh + offB + (c0 + j) * LBO_B, reH + 4 * j, 0u);
+                            st16(Bl + offB + (c0 + j) * LBO_B, reL + 4 * j, 0u);
+                            st16(Bh + offB + (c1 + j) * LBO_B, imH + 4 * j, 0u);
+                            st16(Bl + offB + (c1 + j) * LBO_B, imL + 4 * j, 0u);
+                        }
                     }
                 }
                 gh_tc::fence_smem_to_async();
@@ -446,7 +500,7 @@ __global__ void __launch_bounds__(128) exact_tc_kernel(const float2* __restrict_
                 ++gs;
             }
             if (aborted) break;
-            // epilogue of the pair: |F|^2 of this half's block of D
+            // epilogue of the pair: (Re F)^2 or (Im F)^2 of this warp's rows and columns
             {
                 const uint32_t last = gs - 1;
                 const bool ok = gh_tc::mbar_wait_bounded(&bar[last & 1], (last >> 1) & 1, kTcWaitIters);
@@ -456,37 +510,45 @@ __global__ void __launch_bounds__(128) exact_tc_kernel(const float2* __restrict_
                 }
                 gh_tc::fence_after_sync();
 #pragma unroll
-                for (int c = 0; c < NV32; ++c) {
-                    float v[32];
-                    gh_tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + dcol + (uint32_t)(h * NVP + 32 * c), v);
+                for (int c = 0; c < NH / 16; ++c) {
+                    float v[16];
+                    gh_tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + dcol +
+                                         (uint32_t)(eh * NVP + chalf * NH + 16 * c),
+                                     v);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const float o = __shfl_xor_sync(0xffffffffu, v[i], 1);
-                        acc[32 * c + i] += v[i] * v[i] + o * o;
-                    }
+                    for (int i = 0; i < 16; ++i) acc[16 * c + i] += v[i] * v[i];
                 }
                 gh_tc::fence_before_sync();
             }
             ++pair_ctr;
         }
         if (aborted) break;
-        // sum over receivers: rows 64-127 (odd q) hand their sums to rows 0-63
+        // S = sum over the four quarters (Re/Im F of both receiver halves): the
+        // warps of quarters 1-3 hand their sums to the quarter-0 warp of their
+        // column half. Every MMA of this cell has completed, so the operand
+        // buffers are free.
         __syncthreads();
-        if (h == 1 && part == 0 && a < p.nvx) {
+        if (quarter > 0) {
+            float* dst = xfer + ((size_t)((chalf * 3 + quarter - 1) * 32 + lane)) * NH;
 #pragma unroll
-            for (int b = 0; b < NVP; ++b) xfer[a * NVP + b] = acc[b];
+            for (int b = 0; b < NH; ++b) dst[b] = acc[b];
         }
         __syncthreads();
-        if (h == 0 && part == 0 && a < p.nvx) {
-            const long long cbase = xy * p.nv + (long long)a * p.nvy;
+        if (quarter == 0 && lane < p.nvx) {
+            const int b0 = chalf * NH;
+            const long long cbase = xy * p.nv + (long long)lane * p.nvy;
             bool hm = false;
             for (int m = 0; m < nmask; ++m) hm |= (__ldg(&mask[m]) / p.nv == xy);
+            const float* x1 = xfer + ((size_t)((chalf * 3 + 0) * 32 + lane)) * NH;
+            const float* x2 = xfer + ((size_t)((chalf * 3 + 1) * 32 + lane)) * NH;
+            const float* x3 = xfer + ((size_t)((chalf * 3 + 2) * 32 + lane)) * NH;
             float rb = -INFINITY;
             int ri = -1;
 #pragma unroll
-            for (int b = 0; b < NVP; ++b) {
+            for (int i = 0; i < NH; ++i) {
+                const int b = b0 + i;
                 if (b < p.nvy) {
-                    const float sc = acc[b] + xfer[a * NVP + b];
+                    const float sc = acc[i] + x1[i] + x2[i] + x3[i];
                     if (scores) scores[cbase + b] = sc;
                     bool masked = false;
                     if (hm)
@@ -499,6 +561,7 @@ __global__ void __launch_bounds__(128) exact_tc_kernel(const float2* __restrict_
             }
             if (ri >= 0) better(rb, cbase + ri, best, bestc);
         }
+        __syncthreads();  // the next cell's operands overwrite the cross-warp sums
     }
 
     if (aborted) {
@@ -521,22 +584,262 @@ __global__ void __launch_bounds__(128) exact_tc_kernel(const float2* __restrict_
     }
     __syncthreads();
     if (tid == 0) {
-        for (int w = 1; w < 4; ++w) better(s_bs[w], s_bc[w], best, bestc);
+        for (int w = 1; w < 8; ++w) better(s_bs[w], s_bc[w], best, bestc);
         parts[blockIdx.x].score = best;
         parts[blockIdx.x].cell = bestc;
     }
 }
 
+// ---------------------------------------------------------------------------
+// Stage 1 on the tensor cores: P_q[x][mc] = sum_m Y_q[mc][m] conj(a_m(r_q(x))).
+// Real form per receiver: A rows [Re ca | -Im ca] and [Im ca | Re ca] with
+// ca_m = exp(-j 2 pi r m) for a tile of 64 (x, y) cells (M = 128), B rows
+// [Re Y | Im Y] of the Mc chirps (N = Mc), K = 2 Ms in stages of 32 samples.
+// Y is split into BF16 high/low tiles once per call, already in the canonical
+// shared-memory layout, and each stage's B tiles arrive with one bulk copy
+// (TMA) that completes on an mbarrier. Split-BF16, three MMAs per K step.
+// ---------------------------------------------------------------------------
+// Splits 8 floats into BF16 high/low parts and stores one 16-byte chunk of each.
+__device__ __forceinline__ void store_chunk(unsigned char* hi, unsigned char* lo, uint32_t off, const float* v) {
+    uint4 a, b;
+    gh_tc::split_bf16x2(v[0], v[1], &a.x, &b.x);
+    gh_tc::split_bf16x2(v[2], v[3], &a.y, &b.y);
+    gh_tc::split_bf16x2(v[4], v[5], &a.z, &b.z);
+    gh_tc::split_bf16x2(v[6], v[7], &a.w, &b.w);
+    *(uint4*)(hi + off) = a;
+    *(uint4*)(lo + off) = b;
+}
+
+// Y -> per (q, stage) B tiles [hi | lo], rows mc, K = [Re Y[mc][32s..] | Im Y[mc][32s..]].
+__global__ void y_split_kernel(const float2* __restrict__ Y, int Q, int Ms, int Mc, unsigned char* __restrict__ out) {
+    const int nst = Ms / 32;
+    const long long total = (long long)Q * nst * Mc * 8;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int c = (int)(idx & 7);
+    long long t = idx >> 3;
+    const int mc = (int)(t % Mc);
+    t /= Mc;
+    const int s = (int)(t % nst);
+    const int q = (int)(t / nst);
+    const uint32_t tile = (uint32_t)Mc * 64 * 2, lbo = (uint32_t)(Mc / 8) * 128;
+    unsigned char* hi = out + ((size_t)(q * nst + s) * 2) * tile;
+    unsigned char* lo = hi + tile;
+    const float2* row = Y + ((size_t)q * Mc + mc) * Ms + 32 * s + 8 * (c & 3);
+    float v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = c < 4 ? row[i].x : row[i].y;
+    const uint32_t off = gh_tc::kmajor_off((uint32_t)mc, (uint32_t)(8 * c), lbo, 128);
+    store_chunk(hi, lo, off, v);
+}
+
+// z[k] = exp(-j 2 pi ph (m0 + k)), k < 8.
+__device__ __forceinline__ void atoms8(unsigned long long ph, int m0, float2* z) {
+    const float2 w = gh_cis_fix(0ull - ph);
+    float2 v = gh_cis_fix(0ull - ph * (unsigned long long)m0);
+    z[0] = v;
+#pragma unroll
+    for (int i = 1; i < 8; ++i) {
+        v = cmul(v, w);
+        z[i] = v;
+    }
+}
+
+struct S1Params {
+    int Q, Ms, nstages, ntiles_xy;
+    long long nxy;
+};
+
+template <int NMC>
+__global__ void __launch_bounds__(256, 1) exact_s1_tc_kernel(const unsigned char* __restrict__ Bt,
+                                                             const ExEntry* __restrict__ tab, S1Params p,
+                                                             float* __restrict__ Pout, int* __restrict__ status) {
+    constexpr int N = NMC;
+    constexpr uint32_t SBO = 128, LBO_A = 16 * 128, LBO_B = (N / 8) * 128;
+    constexpr uint32_t A_BYTES = 128 * 64 * 2, B_BYTES = N * 64 * 2;
+    constexpr uint32_t BUF_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+    constexpr uint32_t TM_COLS = 2 * N <= 64 ? 64 : (2 * N <= 128 ? 128 : (2 * N <= 256 ? 256 : 512));
+    constexpr uint32_t FLIP = 0x80008000u;
+    constexpr int CH = N / 2;  // columns per epilogue warp
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t mbar[2], tbar[2];
+    __shared__ uint32_t tmem_holder;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int h = warp >> 2;        // xy half of the tile (generation)
+    const int kq = warp & 3;        // 8-sample quarter of a stage (generation)
+    const int quarter = warp & 3;   // TMEM lane quarter (epilogue)
+    const int chalf = warp >> 2;    // column half (epilogue)
+    if (tid == 0) {
+        gh_tc::mbar_init(&mbar[0], 1);
+        gh_tc::mbar_init(&mbar[1], 1);
+        gh_tc::mbar_init(&tbar[0], 1);
+        gh_tc::mbar_init(&tbar[1], 1);
+        gh_tc::mbar_fence_init();
+    }
+    if (warp == 0) gh_tc::tmem_alloc(&tmem_holder, TM_COLS);
+    gh_tc::fence_before_sync();
+    __syncthreads();
+    gh_tc::fence_after_sync();
+    const uint32_t tmem = tmem_holder;
+    const uint32_t idesc = gh_tc::idesc_bf16_f32(128, N);
+    const uint32_t offA_re = gh_tc::kmajor_off((uint32_t)(h * 64 + lane), 0, LBO_A, SBO);
+    const uint32_t offA_im = gh_tc::kmajor_off((uint32_t)(h * 64 + 32 + lane), 0, LBO_A, SBO);
+
+    uint32_t gs = 0;
+    int tile_ctr = 0;
+    bool aborted = false;
+    const long long ntiles = (long long)p.Q * p.ntiles_xy;
+    for (long long tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
+        const int q = (int)(tile / p.ntiles_xy);
+        const long long xy0 = (tile - (long long)q * p.ntiles_xy) * 64;
+        const long long xy = xy0 + h * 32 + lane;
+        const unsigned long long rf = xy < p.nxy ? tab[xy * p.Q + q].rfix : 0ull;
+        const bool vx = xy < p.nxy;
+        const uint32_t dcol = (uint32_t)(tile_ctr & 1) * N;
+        for (int s = 0; s < p.nstages; ++s) {
+            const int buf = gs & 1;
+            if (gs >= 2) {
+                const bool ok = gh_tc::mbar_wait_bounded(&mbar[buf], ((gs - 2) >> 1) & 1, kTcWaitIters);
+                if (__syncthreads_or(!ok)) {
+                    aborted = true;
+                    break;
+                }
+            }
+            unsigned char* Ah = smem + buf * BUF_BYTES;
+            unsigned char* Al = Ah + A_BYTES;
+            unsigned char* Bh = Al + A_BYTES;
+            if (tid == 0) {
+                gh_tc::mbar_arrive_expect_tx(&tbar[buf], 2 * B_BYTES);
+                gh_tc::bulk_g2s(Bh, Bt + ((size_t)(q * p.nstages + s) * 2) * B_BYTES, 2 * B_BYTES, &tbar[buf]);
+            }
+            {
+                float2 z[8];
+                if (vx) {
+                    atoms8(rf, 32 * s + 8 * kq, z);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) z[k] = make_float2(0.f, 0.f);
+                }
+                uint32_t reH[4], reL[4], imH[4], imL[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    gh_tc::split_bf16x2(z[2 * i].x, z[2 * i + 1].x, &reH[i], &reL[i]);
+                    gh_tc::split_bf16x2(z[2 * i].y, z[2 * i + 1].y, &imH[i], &imL[i]);
+                }
+                // Re row: [Re ca | -Im ca]; Im row: [Im ca | Re ca]
+                st16(Ah + offA_re + kq * LBO_A, reH, 0u);
+                st16(Al + offA_re + kq * LBO_A, reL, 0u);
+                st16(Ah + offA_re + (4 + kq) * LBO_A, imH, FLIP);
+                st16(Al + offA_re + (4 + kq) * LBO_A, imL, FLIP);
+                st16(Ah + offA_im + kq * LBO_A, imH, 0u);
+                st16(Al + offA_im + kq * LBO_A, imL, 0u);
+                st16(Ah + offA_im + (4 + kq) * LBO_A, reH, 0u);
+                st16(Al + offA_im + (4 + kq) * LBO_A, reL, 0u);
+            }
+            gh_tc::fence_smem_to_async();
+            const bool tok = gh_tc::mbar_wait_bounded(&tbar[buf], (gs >> 1) & 1, kTcWaitIters);
+            gh_tc::fence_before_sync();
+            if (__syncthreads_or(!tok)) {
+                aborted = true;
+                break;
+            }
+            if (tid == 0) {
+                gh_tc::fence_after_sync();
+                const uint32_t ah = gh_tc::smem_u32(Ah), al = gh_tc::smem_u32(Al);
+                const uint32_t bh = gh_tc::smem_u32(Bh), bl = bh + B_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t dah = gh_tc::smem_desc(ah + 2 * kk * LBO_A, LBO_A, SBO);
+                    const uint64_t dal = gh_tc::smem_desc(al + 2 * kk * LBO_A, LBO_A, SBO);
+                    const uint64_t dbh = gh_tc::smem_desc(bh + 2 * kk * LBO_B, LBO_B, SBO);
+                    const uint64_t dbl = gh_tc::smem_desc(bl + 2 * kk * LBO_B, LBO_B, SBO);
+                    gh_tc::mma_bf16(tmem + dcol, dah, dbh, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+                    gh_tc::mma_bf16(tmem + dcol, dah, dbl, idesc, 1u);
+                    gh_tc::mma_bf16(tmem + dcol, dal, dbh, idesc, 1u);
+                }
+                gh_tc::mma_commit(&mbar[buf]);
+            }
+            ++gs;
+        }
+        if (aborted) break;
+        // epilogue: this warp's quarter holds Re P or Im P of 32 cells; write its column half
+        {
+            const uint32_t last = gs - 1;
+            const bool ok = gh_tc::mbar_wait_bounded(&mbar[last & 1], (last >> 1) & 1, kTcWaitIters);
+            if (__syncthreads_or(!ok)) {
+                aborted = true;
+                break;
+            }
+            gh_tc::fence_after_sync();
+            const int eh = quarter >> 1, part = quarter & 1;
+            const long long exy = xy0 + eh * 32 + lane;
+            float* dst = Pout + ((size_t)q * p.nxy + exy) * 2 * N + (size_t)part * N + chalf * CH;
+#pragma unroll
+            for (int c = 0; c < CH / 16; ++c) {
+                float v[16];
+                gh_tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + dcol + (uint32_t)(chalf * CH + 16 * c), v);
+                if (exy < p.nxy) {
+#pragma unroll
+                    for (int i = 0; i < 16; i += 4)
+                        *(float4*)(dst + 16 * c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                }
+            }
+            gh_tc::fence_before_sync();
+        }
+        ++tile_ctr;
+    }
+    if (aborted) {
+        if (tid == 0) atomicExch(status, GH_ETIMEOUT);
+        if (gs > 0) gh_tc::mbar_wait_bounded(&mbar[(gs - 1) & 1], ((gs - 1) >> 1) & 1, kTcWaitIters);
+    }
+    gh_tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) gh_tc::tmem_dealloc(tmem, TM_COLS);
+}
+
+template <int NMC>
+int launch_s1_tc(gh_ctx* ctx, const Dims& d, const float2* Y, const ExEntry* tab, float* P, int* status) {
+    constexpr uint32_t B_BYTES = NMC * 64 * 2;
+    const size_t smem = (size_t)2 * (2 * 128 * 64 * 2 + 2 * B_BYTES);
+    if (smem > ctx->smem_optin) return gh_fail(ctx, GH_ENOTSUP, "stage-1 tensor-core path needs %zu B", smem);
+    const int nst = d.Ms / 32;
+    void* bt;
+    GH_TRY(gh_ws(ctx, WS_EXACT_B, (size_t)d.Q * nst * 2 * B_BYTES, &bt));
+    cudaEvent_t ev;
+    const long long nsplit = (long long)d.Q * nst * d.Mc * 8;
+    gh_launch_begin(ctx, GH_K_EXACT_S1, &ev);
+    y_split_kernel<<<(unsigned)((nsplit + 255) / 256), 256, 0, ctx->stream>>>(Y, d.Q, d.Ms, d.Mc, (unsigned char*)bt);
+    GH_TRY(gh_launch_end(ctx, GH_K_EXACT_S1, ev, "y_split_kernel"));
+    GH_CUDA(cudaFuncSetAttribute(exact_s1_tc_kernel<NMC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GH_CUDA(cudaFuncSetAttribute(exact_s1_tc_kernel<NMC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
+    S1Params p;
+    p.Q = d.Q;
+    p.Ms = d.Ms;
+    p.nstages = nst;
+    p.ntiles_xy = (int)((d.nxy + 63) / 64);
+    p.nxy = d.nxy;
+    long long ctas = (long long)ctx->num_sms;
+    const long long ntiles = (long long)d.Q * p.ntiles_xy;
+    if (ctas > ntiles) ctas = ntiles;
+    gh_launch_begin(ctx, GH_K_EXACT_S1, &ev);
+    exact_s1_tc_kernel<NMC><<<(unsigned)ctas, 256, smem, ctx->stream>>>((const unsigned char*)bt, tab, p, P, status);
+    return gh_launch_end(ctx, GH_K_EXACT_S1, ev, "exact_s1_tc_kernel");
+}
+
 template <int NV32>
-int launch_tc(gh_ctx* ctx, const Dims& d, const float2* P, const ExEntry* tab, float* scores, const int64_t* mask,
+int launch_tc(gh_ctx* ctx, const Dims& d, const float* P, const ExEntry* tab, float* scores, const int64_t* mask,
               int nmask, ArgPartial* parts, int* status, long long* nparts) {
     constexpr int NVP = 32 * NV32, N = 2 * NVP;
-    const size_t smem = (size_t)2 * (2 * 128 * 64 * 2 + 2 * N * 64 * 2) + (size_t)32 * NVP * 4;
+    const size_t smem = (size_t)2 * (2 * 128 * 64 * 2 + 2 * N * 64 * 2);
     if (smem > ctx->smem_optin) return gh_fail(ctx, GH_ENOTSUP, "exact tensor-core path needs %zu B", smem);
     GH_CUDA(cudaFuncSetAttribute(exact_tc_kernel<NV32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GH_CUDA(cudaFuncSetAttribute(exact_tc_kernel<NV32>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
     int per_sm = 0;
-    GH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, exact_tc_kernel<NV32>, 128, smem));
-    if (per_sm < 1) per_sm = 1;
+    GH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, exact_tc_kernel<NV32>, 256, smem));
+    if (per_sm < 2) per_sm = 2;  // persistent grid-stride kernel: a second wave costs nothing extra
     long long ctas = (long long)ctx->num_sms * per_sm;
     if (ctas > d.nxy) ctas = d.nxy;
     ExactTcParams p;
@@ -549,7 +852,7 @@ int launch_tc(gh_ctx* ctx, const Dims& d, const float2* P, const ExEntry* tab, f
     p.nv = d.nv;
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_EXACT_S2, &ev);
-    exact_tc_kernel<NV32><<<(unsigned)ctas, 128, smem, ctx->stream>>>(P, tab, p, scores, mask, nmask, parts, status);
+    exact_tc_kernel<NV32><<<(unsigned)ctas, 256, smem, ctx->stream>>>(P, tab, p, scores, mask, nmask, parts, status);
     GH_TRY(gh_launch_end(ctx, GH_K_EXACT_S2, ev, "exact_tc_kernel"));
     *nparts = ctas;
     return GH_OK;
@@ -561,45 +864,57 @@ int gh_launch_exact(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2
                     const int64_t* mask, int nmask, ArgResult* result) {
     if (d.nxy > 0x7fffffffLL) return gh_fail(ctx, GH_ENOTSUP, "exact path supports < 2^31 (x, y) cells");
     if (d.nv > 256 * 16) return gh_fail(ctx, GH_ENOTSUP, "exact path supports at most 4096 velocity cells");
-    void* P;
-    GH_TRY(gh_ws(ctx, WS_EXACT_P, (size_t)d.Q * d.nxy * d.Mc * sizeof(float2), &P));
+    void* P;  // planar [Q][nxy][Re row | Im row][Mc]
+    GH_TRY(gh_ws(ctx, WS_EXACT_P, (size_t)d.Q * d.nxy * 2 * d.Mc * sizeof(float), &P));
+    const bool tc1 = d.Ms % 32 == 0 && (d.Mc == 32 || d.Mc == 64 || d.Mc == 128 || d.Mc == 256);
+    const bool tc2 = d.nvx <= 32 && d.nvy <= 64;
+    int* status = gh_status_dev(ctx);
     cudaEvent_t ev;
-    gh_launch_begin(ctx, GH_K_EXACT_S1, &ev);
-    dim3 grid1((unsigned)((d.nxy + S1_XT - 1) / S1_XT), (unsigned)((d.Mc + S1_MT - 1) / S1_MT), (unsigned)d.Q);
-    exact_stage1_kernel<<<grid1, 256, 0, ctx->stream>>>(Y, g, (float2*)P);
-    GH_TRY(gh_launch_end(ctx, GH_K_EXACT_S1, ev, "exact_stage1_kernel"));
-    void* parts;
-    GH_TRY(gh_ws(ctx, WS_PART, (size_t)d.nxy * sizeof(ArgPartial), &parts));
-    if (d.nvx <= 32 && d.nvy <= 64) {
-        // tensor-core stage 2
-        void* tab;
+    void* tab = nullptr;
+    if (tc1 || tc2) {
         GH_TRY(gh_ws(ctx, WS_EXACT_TAB, (size_t)d.nxy * d.Q * sizeof(ExEntry), &tab));
         const long long n = d.nxy * d.Q;
         gh_launch_begin(ctx, GH_K_EXACT_S1, &ev);
         exact_coord_kernel<<<(unsigned)((n + 127) / 128), 128, 0, ctx->stream>>>(g, (ExEntry*)tab);
         GH_TRY(gh_launch_end(ctx, GH_K_EXACT_S1, ev, "exact_coord_kernel"));
+    }
+    if (tc1) {
+        const ExEntry* t = (const ExEntry*)tab;
+        float* Pf = (float*)P;
+        if (d.Mc == 32) GH_TRY(launch_s1_tc<32>(ctx, d, Y, t, Pf, status));
+        else if (d.Mc == 64) GH_TRY(launch_s1_tc<64>(ctx, d, Y, t, Pf, status));
+        else if (d.Mc == 128) GH_TRY(launch_s1_tc<128>(ctx, d, Y, t, Pf, status));
+        else GH_TRY(launch_s1_tc<256>(ctx, d, Y, t, Pf, status));
+    } else {
+        gh_launch_begin(ctx, GH_K_EXACT_S1, &ev);
+        dim3 grid1((unsigned)((d.nxy + S1_XT - 1) / S1_XT), (unsigned)((d.Mc + S1_MT - 1) / S1_MT), (unsigned)d.Q);
+        exact_stage1_kernel<<<grid1, 256, 0, ctx->stream>>>(Y, g, (float*)P);
+        GH_TRY(gh_launch_end(ctx, GH_K_EXACT_S1, ev, "exact_stage1_kernel"));
+    }
+    void* parts;
+    GH_TRY(gh_ws(ctx, WS_PART, (size_t)d.nxy * sizeof(ArgPartial), &parts));
+    if (tc2) {
         long long nparts = 0;
-        int* status = gh_status_dev(ctx);
         if (d.nvy <= 32)
-            GH_TRY(launch_tc<1>(ctx, d, (const float2*)P, (const ExEntry*)tab, scores, mask, nmask,
+            GH_TRY(launch_tc<1>(ctx, d, (const float*)P, (const ExEntry*)tab, scores, mask, nmask,
                                 (ArgPartial*)parts, status, &nparts));
         else
-            GH_TRY(launch_tc<2>(ctx, d, (const float2*)P, (const ExEntry*)tab, scores, mask, nmask,
+            GH_TRY(launch_tc<2>(ctx, d, (const float*)P, (const ExEntry*)tab, scores, mask, nmask,
                                 (ArgPartial*)parts, status, &nparts));
         return gh_launch_argmax_finalize(ctx, (const ArgPartial*)parts, (int)nparts, result);
     }
     const int cpt = (int)((d.nv + 255) / 256);
     int st;
     if (cpt <= 1)
-        st = launch_s2<1>(ctx, d, g, (const float2*)P, scores, mask, nmask, (ArgPartial*)parts);
+        st = launch_s2<1>(ctx, d, g, (const float*)P, scores, mask, nmask, (ArgPartial*)parts);
     else if (cpt <= 2)
-        st = launch_s2<2>(ctx, d, g, (const float2*)P, scores, mask, nmask, (ArgPartial*)parts);
+        st = launch_s2<2>(ctx, d, g, (const float*)P, scores, mask, nmask, (ArgPartial*)parts);
     else if (cpt <= 4)
-        st = launch_s2<4>(ctx, d, g, (const float2*)P, scores, mask, nmask, (ArgPartial*)parts);
+        st = launch_s2<4>(ctx, d, g, (const float*)P, scores, mask, nmask, (ArgPartial*)parts);
     else if (cpt <= 8)
-        st = launch_s2<8>(ctx, d, g, (const float2*)P, scores, mask, nmask, (ArgPartial*)parts);
+        st = launch_s2<8>(ctx, d, g, (const float*)P, scores, mask, nmask, (ArgPartial*)parts);
     else
-        st = launch_s2<16>(ctx, d, g, (const float2*)P, scores, mask, nmask, (ArgPartial*)parts);
+        st = launch_s2<16>(ctx, d, g, (const float*)P, scores, mask, nmask, (ArgPartial*)parts);
     GH_TRY(st);
     return gh_launch_argmax_finalize(ctx, (const ArgPartial*)parts, (int)d.nxy, result);
 }

@@ -373,7 +373,9 @@ int hop_launch_t(cudaStream_t stream, const Dims& d, HopParams hp, const float2*
     if (W < 1) W = 1;
     const size_t smem = per_warp * W;
     if (cudaFuncSetAttribute(hop_score_kernel<AC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+            cudaSuccess ||
+        cudaFuncSetAttribute(hop_score_kernel<AC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
         return GH_ECUDA;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_score_kernel<AC>, 32 * W, smem) != cudaSuccess)

@@ -29,6 +29,7 @@ enum WsSlot {
     WS_DIAG,        // coordinate-table diagnostics
     WS_TWIDDLE,     // FFT twiddle tables
     WS_EXACT_TAB,   // exact-path phase table [nxy][Q]
+    WS_EXACT_B,     // stage-1 split-BF16 tiles of Y
     WS_COUNT
 };
 
