@@ -273,6 +273,15 @@ GH_API int gh_selftest_tcgen05(gh_ctx* ctx, const float* A_host, const float* B_
                                float* D_host, int32_t N, int32_t K);
 
 /*
+ * gh_probe_read_bandwidth - diagnostic read-bandwidth probe (no counterpart in
+ * the paper): streams 16-byte loads over a device buffer of `bytes` bytes
+ * (1 MiB .. 64 GiB), `reps` times (1 .. 1000), and returns GB/s in *gbs. A
+ * buffer well below the L2 size measures L2-to-SM bandwidth; one well above it
+ * measures DRAM read bandwidth. Allocates its buffer in the context workspace.
+ */
+GH_API int gh_probe_read_bandwidth(gh_ctx* ctx, int64_t bytes, int32_t reps, double* gbs);
+
+/*
  * Instrumentation. gh_set_timing(ctx, mask) brackets every launch of the
  * kernel classes whose bit (1 << GH_K_*) is set in `mask` with CUDA events on
  * the context's stream (mask 0: off; -1: all classes). gh_kernel_stats

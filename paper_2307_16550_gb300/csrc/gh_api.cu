@@ -393,7 +393,7 @@ extern "C" int gh_make_maps(gh_ctx* ctx, const gh_radar* radar, int32_t Q, const
     int dm = gh_is_device_ptr(ctx, maps_dev);
     if (dm < 0) return dm;
     if (!dv || !dm) return gh_fail(ctx, GH_EINVAL, "Y_dev and maps_dev must be device memory");
-    return gh_launch_maps(ctx, d, (const float2*)Y_dev, (float2*)maps_dev);
+    return gh_launch_maps(ctx, d, (const float2*)Y_dev, nullptr, (float2*)maps_dev);
 }
 
 static int build_table(gh_ctx* ctx, const Dims& d, const GeoParams& geo, void** table) {
@@ -475,34 +475,32 @@ extern "C" int gh_detect(gh_ctx* ctx, int32_t method, const gh_radar* radar, con
     GeoParams geo;
     gh_fill_geo(&geo, radar, tx_host, rx_host, Q, grid);
 
-    size_t ybytes = (size_t)d.Q * d.Mc * d.Ms * sizeof(float2);
     size_t mbytes = (size_t)d.Q * d.Nr * d.Nd * sizeof(float2);
-    void *R, *maps = nullptr, *table = nullptr, *res, *bws;
-    GH_TRY(gh_ws(ctx, WS_R, ybytes, &R));
+    void *maps = nullptr, *table = nullptr, *res, *bws;
     GH_TRY(gh_ws(ctx, WS_RESULT, kResultSlots * sizeof(ArgResult), &res));
     GH_TRY(gh_status_reset(ctx));
     GH_TRY(gh_ws(ctx, WS_BOMP, gh_bomp_ws_bytes(d, K), &bws));
+    GH_TRY(gh_bomp_reset(ctx, d, K, bws));
     if (method == GH_HOP) {
         GH_TRY(gh_ws(ctx, WS_MAPS, mbytes, &maps));
         GH_TRY(build_table(ctx, d, geo, &table));
     }
     ArgResult* sel = (ArgResult*)res;  // sel[k] = selection of iteration k
-    // The scorer masks the selected cells: it reads sel[0..k).cell through
-    // this view (ArgResult starts with the int64 cell; stride handled below).
-    int64_t* mask;
+    int64_t* mask;                      // selected cells, excluded from later argmaxes
     GH_TRY(gh_ws(ctx, WS_DIAG, (size_t)GH_MAX_K * sizeof(int64_t) + 256, (void**)&mask));
-    const float2* cur = Yd;
     for (int k = 0; k < K; ++k) {
+        // the residual of iteration k subtracts atoms 0..k-1 (amplitudes of the last solve)
+        const Deflate df = gh_bomp_deflate(bws, d, K, k);
+        ArgPartial* parts;
+        int nparts;
         if (method == GH_HOP) {
-            GH_TRY(gh_launch_maps(ctx, d, cur, (float2*)maps));
-            GH_TRY(gh_launch_hop(ctx, d, geo, (const float2*)maps, table, nullptr, mask, k, sel + k));
+            GH_TRY(gh_launch_maps(ctx, d, Yd, &df, (float2*)maps));
+            GH_TRY(gh_launch_hop_parts(ctx, d, geo, (const float2*)maps, table, nullptr, mask, k, &parts, &nparts));
         } else {
-            GH_TRY(gh_launch_exact(ctx, d, geo, cur, nullptr, mask, k, sel + k));
+            GH_TRY(gh_launch_exact_parts(ctx, d, geo, Yd, &df, nullptr, mask, k, &parts, &nparts));
         }
-        GH_TRY(gh_launch_bomp_iter(ctx, d, geo, Yd, (float2*)R, k, K, sel, bws));
-        // append the selected cell to the mask list (device to device)
-        GH_CUDA(cudaMemcpyAsync(mask + k, &sel[k].cell, sizeof(int64_t), cudaMemcpyDeviceToDevice, ctx->stream));
-        cur = (const float2*)R;
+        GH_TRY(gh_launch_bomp_select(ctx, d, geo, parts, nparts, sel, mask, k, K, bws));
+        GH_TRY(gh_launch_bomp_corr(ctx, d, geo, Yd, k, K, bws));
     }
     // results: selections, status word and the final amplitudes
     size_t sel_bytes = (size_t)kResultSlots * sizeof(ArgResult);

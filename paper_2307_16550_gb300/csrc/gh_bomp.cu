@@ -2,18 +2,23 @@
 // targets by iterative direct detection, Sec. VI) and the measurement
 // synthesiser of the signal model (Sec. II).
 //
-// One BOMP iteration k, after the scorer has written the selected cell to
-// sel[k] on the device (no host round trip):
-//   bomp_atoms    : (r, u) of the selected cell at every receiver (float64) and
-//                   its atoms a(r) (Ms) and b(u) (Mc), phases reduced exactly;
-//   bomp_corr     : c_{k,q} = <Y_q, b(u) (x) a(r)>, float32 row sums added in float64;
-//   bomp_solve    : per receiver, the normal equations of all k+1 selected
-//                   atoms, in float64. With centred atoms (phase
-//                   exp(-j pi (r (Ms-1) + u (Mc-1)))) the Gram matrix is real,
-//                   G[s][t] = D_Ms(r_t - r_s) D_Mc(u_t - u_s),
-//                   D_M(f) = sin(pi M f) / sin(pi f); Cholesky solve, then the
-//                   amplitudes are rotated back to the atoms of Sec. II;
-//   bomp_residual : R_q = Y_q - sum_t alpha_{t,q} b(u_t) (x) a(r_t).
+// BOMP iteration k, after the scorer has written its per-CTA argmax partials
+// (no host round trip):
+//   bomp_select : reduces the partials to the selected cell sel[k] (ties: the
+//                 smallest index), appends it to the mask, and prepares the new
+//                 atom at every receiver q: (r, u) in float64, its centring
+//                 phase exp(j pi (r (Ms-1) + u (Mc-1))), row k of the real Gram
+//                 matrix G[s][t] = D_Ms(r_t - r_s) D_Mc(u_t - u_s) with
+//                 D_M(f) = sin(pi M f) / sin(pi f), and the atoms a(r), b(u).
+//                 Trigonometric arguments are reduced exactly in float64 before
+//                 a float32 sincos.
+//   bomp_corr   : c_{k,q} = <Y_q, b(u) (x) a(r)> (float32 row sums added in
+//                 float64); the last CTA to finish solves, per receiver, the
+//                 float64 normal equations of atoms 0..k (Cholesky, dependent
+//                 atoms dropped) and rotates the amplitudes back to the atoms of
+//                 the signal model (Sec. II).
+// The residual Y - sum_t alpha_t atom_t is never stored on the hopping path:
+// the next map-making pass subtracts it while loading Y (gh_deflate).
 #include <math.h>
 
 #include "gh_internal.cuh"
@@ -23,7 +28,7 @@ namespace {
 constexpr int kCorrRows = 8;  // chirps per correlation CTA (one per warp)
 
 struct BompLayout {
-    size_t alpha, corr, ru, phase, gram, corrp, atoms_a, atoms_b, total;
+    size_t alpha, corr, ru, phase, gram, corrp, atoms_a, atoms_b, counter, total;
     int chunks;
 };
 
@@ -44,30 +49,93 @@ BompLayout bomp_layout(const Dims& d, int K) {
     L.corrp = take((size_t)K * d.Q * L.chunks * 2 * sizeof(double));  // double2 [K][Q][chunks]
     L.atoms_a = take((size_t)K * d.Q * d.Ms * sizeof(float2));
     L.atoms_b = take((size_t)K * d.Q * d.Mc * sizeof(float2));
+    L.counter = take(sizeof(unsigned int));
     L.total = o;
     return L;
 }
 
-__device__ double dirichlet(double f, int M) {
-    const double s = sinpi(f);
-    if (fabs(s) < 1e-13) {
-        // f is (numerically) an integer n: D_M(n) = M (-1)^(n (M - 1))
-        const double n = rint(f);
-        return M * cospi(n * (double)(M - 1));
-    }
-    return sinpi((double)M * f) / s;
+struct BompPtrs {
+    double2 *alpha, *corr, *ru, *phase, *corrp;
+    double* gram;
+    float2 *atoms_a, *atoms_b;
+    unsigned int* counter;
+    int chunks;
+};
+
+BompPtrs bomp_ptrs(void* ws, const Dims& d, int K) {
+    const BompLayout L = bomp_layout(d, K);
+    char* b = (char*)ws;
+    BompPtrs w;
+    w.alpha = (double2*)(b + L.alpha);
+    w.corr = (double2*)(b + L.corr);
+    w.ru = (double2*)(b + L.ru);
+    w.phase = (double2*)(b + L.phase);
+    w.gram = (double*)(b + L.gram);
+    w.corrp = (double2*)(b + L.corrp);
+    w.atoms_a = (float2*)(b + L.atoms_a);
+    w.atoms_b = (float2*)(b + L.atoms_b);
+    w.counter = (unsigned int*)(b + L.counter);
+    w.chunks = L.chunks;
+    return w;
 }
 
-// One CTA per receiver: (r, u) of the cell selected in iteration k, its
-// centring phase, row k of the real Gram matrix, and the atoms a(r), b(u).
-__global__ void bomp_atoms_kernel(GeoParams g, const ArgResult* __restrict__ sel, int k, int K,
-                                  double2* __restrict__ ru, double2* __restrict__ phase, double* __restrict__ gram,
-                                  float2* __restrict__ atoms_a, float2* __restrict__ atoms_b) {
-    const int q = blockIdx.x;
-    __shared__ unsigned long long s_rf, s_uf;
-    __shared__ double s_r, s_u;
+// x mod 2, exactly, as a float (argument of sinpif / cospif).
+__device__ __forceinline__ float mod2f(double x) { return (float)(x - 2.0 * floor(0.5 * x)); }
+
+// D_M(f) = sin(pi M f) / sin(pi f) (M a power of two, so M f is exact).
+__device__ double dirichlet(double f, int M) {
+    const float s = sinpif(mod2f(f));
+    if (fabsf(s) < 1e-6f) {
+        // f is (numerically) an integer n: D_M(n) = M (-1)^(n (M - 1))
+        const long long n = llrint(f);
+        return ((n * (long long)(M - 1)) & 1) ? -(double)M : (double)M;
+    }
+    return (double)(sinpif(mod2f((double)M * f)) / s);
+}
+
+__device__ __forceinline__ void better(float s, long long c, float& bs, long long& bc) {
+    if (s > bs || (s == bs && c < bc)) {
+        bs = s;
+        bc = c;
+    }
+}
+
+// One CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) bomp_select_kernel(const ArgPartial* __restrict__ parts, int nparts,
+                                                           ArgResult* __restrict__ sel, int64_t* __restrict__ mask,
+                                                           int k, int K, GeoParams g, BompPtrs w) {
+    __shared__ float s_bs[32];
+    __shared__ long long s_bc[32];
+    __shared__ long long s_cell;
+    __shared__ unsigned long long s_rf[GH_MAX_Q], s_uf[GH_MAX_Q];
+    __shared__ double s_r[GH_MAX_Q], s_u[GH_MAX_Q];
+    float best = -INFINITY;
+    long long bestc = 0x7fffffffffffffffLL;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) better(parts[i].score, parts[i].cell, best, bestc);
+    for (int off = 16; off > 0; off >>= 1) {
+        const float os = __shfl_down_sync(0xffffffffu, best, off);
+        const long long oc = __shfl_down_sync(0xffffffffu, bestc, off);
+        better(os, oc, best, bestc);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s_bs[warp] = best;
+        s_bc[warp] = bestc;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        long long cell = sel[k].cell;
+        for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) better(s_bs[ww], s_bc[ww], best, bestc);
+        const bool valid = bestc != 0x7fffffffffffffffLL;
+        sel[k].cell = bestc;
+        sel[k].score = best;
+        sel[k].valid = valid;
+        mask[k] = bestc;
+        s_cell = valid ? bestc : 0;
+    }
+    __syncthreads();
+    const int q = threadIdx.x;
+    if (q < g.Q) {
+        long long cell = s_cell;
         const int nvy = g.n[3], nvx = g.n[2], ny = g.n[1];
         const int ivy = (int)(cell % nvy);
         cell /= nvy;
@@ -79,95 +147,39 @@ __global__ void bomp_atoms_kernel(GeoParams g, const ArgResult* __restrict__ sel
         gh_bistatic(g, q, gh_axis(g.lo[0], g.step[0], ix), gh_axis(g.lo[1], g.step[1], iy), &d, &wx, &wy);
         const double r = gh_range(g, d);
         const double u = gh_speed(g, wx, wy, gh_axis(g.lo[2], g.step[2], ivx), gh_axis(g.lo[3], g.step[3], ivy));
-        ru[(size_t)k * g.Q + q] = make_double2(r, u);
-        double sn, cs;
-        sincospi(r * (g.Ms - 1) + u * (g.Mc - 1), &sn, &cs);
-        phase[(size_t)k * g.Q + q] = make_double2(cs, sn);
-        s_r = r;
-        s_u = u;
-        s_rf = gh_phase_fix(r);
-        s_uf = gh_phase_fix(u);
+        w.ru[(size_t)k * g.Q + q] = make_double2(r, u);
+        float sn, cs;
+        sincospif(mod2f(r * (g.Ms - 1) + u * (g.Mc - 1)), &sn, &cs);
+        w.phase[(size_t)k * g.Q + q] = make_double2(cs, sn);
+        s_r[q] = r;
+        s_u[q] = u;
+        s_rf[q] = gh_phase_fix(r);
+        s_uf[q] = gh_phase_fix(u);
     }
     __syncthreads();
-    if (threadIdx.x <= k) {
-        const int t = threadIdx.x;
-        const double2 rut = t == k ? make_double2(s_r, s_u) : ru[(size_t)t * g.Q + q];
-        const double v = dirichlet(s_r - rut.x, g.Ms) * dirichlet(s_u - rut.y, g.Mc);
-        double* G = gram + (size_t)q * K * K;
+    // row k of the Gram matrix of every receiver
+    for (int idx = threadIdx.x; idx < g.Q * (k + 1); idx += blockDim.x) {
+        const int qq = idx / (k + 1), t = idx - qq * (k + 1);
+        const double2 rut = t == k ? make_double2(s_r[qq], s_u[qq]) : w.ru[(size_t)t * g.Q + qq];
+        const double v = dirichlet(s_r[qq] - rut.x, g.Ms) * dirichlet(s_u[qq] - rut.y, g.Mc);
+        double* G = w.gram + (size_t)qq * K * K;
         G[k * K + t] = v;
         G[t * K + k] = v;
     }
-    float2* a = atoms_a + ((size_t)k * g.Q + q) * g.Ms;
-    float2* b = atoms_b + ((size_t)k * g.Q + q) * g.Mc;
-    for (int m = threadIdx.x; m < g.Ms; m += blockDim.x) a[m] = gh_cis_fix(s_rf * (unsigned long long)m);
-    for (int m = threadIdx.x; m < g.Mc; m += blockDim.x) b[m] = gh_cis_fix(s_uf * (unsigned long long)m);
-}
-
-// CTA (chunk, q): partial <Y_q, b(u) (x) a(r)> over kCorrRows chirps; each warp
-// sums one chirp in float32 and the chirps are added in float64.
-__global__ void __launch_bounds__(256) bomp_corr_kernel(const float2* __restrict__ Y, GeoParams g, int k, int chunks,
-                                                        const float2* __restrict__ atoms_a,
-                                                        const float2* __restrict__ atoms_b,
-                                                        double2* __restrict__ corrp) {
-    const int ch = blockIdx.x, q = blockIdx.y;
-    const float2* a = atoms_a + ((size_t)k * g.Q + q) * g.Ms;
-    const float2* b = atoms_b + ((size_t)k * g.Q + q) * g.Mc;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mc = ch * kCorrRows + warp;
-    __shared__ double rx[kCorrRows], ry[kCorrRows];
-    double sx = 0.0, sy = 0.0;
-    if (warp < kCorrRows && mc < g.Mc) {
-        const float2* row = Y + ((size_t)q * g.Mc + mc) * g.Ms;
-        float2 s = make_float2(0.f, 0.f);
-        for (int m = lane; m < g.Ms; m += 32) {
-            const float2 y = row[m];
-            const float2 w = a[m];
-            s.x += y.x * w.x + y.y * w.y;  // y * conj(a)
-            s.y += y.y * w.x - y.x * w.y;
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-            s.x += __shfl_down_sync(0xffffffffu, s.x, off);
-            s.y += __shfl_down_sync(0xffffffffu, s.y, off);
-        }
-        const double bx = b[mc].x, by = b[mc].y;  // s * conj(b)
-        sx = (double)s.x * bx + (double)s.y * by;
-        sy = (double)s.y * bx - (double)s.x * by;
+    for (int idx = threadIdx.x; idx < g.Q * g.Ms; idx += blockDim.x) {
+        const int qq = idx / g.Ms, m = idx - qq * g.Ms;
+        w.atoms_a[((size_t)k * g.Q + qq) * g.Ms + m] = gh_cis_fix(s_rf[qq] * (unsigned long long)m);
     }
-    if (lane == 0 && warp < kCorrRows) {
-        rx[warp] = sx;
-        ry[warp] = sy;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double tx = 0, ty = 0;
-        for (int w = 0; w < kCorrRows; ++w) {
-            tx += rx[w];
-            ty += ry[w];
-        }
-        corrp[((size_t)k * g.Q + q) * chunks + ch] = make_double2(tx, ty);
+    for (int idx = threadIdx.x; idx < g.Q * g.Mc; idx += blockDim.x) {
+        const int qq = idx / g.Mc, m = idx - qq * g.Mc;
+        w.atoms_b[((size_t)k * g.Q + qq) * g.Mc + m] = gh_cis_fix(s_uf[qq] * (unsigned long long)m);
     }
 }
 
-// One thread per receiver: sums the correlation partials of atom k, then
-// solves the normal equations of atoms 0..k with the stored Gram matrix
-// (Cholesky, dependent atoms dropped) and rotates the amplitudes back to the
-// atoms of the signal model. Float64 arithmetic only.
-__global__ void bomp_solve_kernel(int Q, int Ms, int Mc, int k, int K, int chunks,
-                                  const double2* __restrict__ corrp, double2* __restrict__ corr,
-                                  const double2* __restrict__ phase, const double* __restrict__ gram,
-                                  double2* __restrict__ alpha) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= Q) return;
-    const int n = k + 1;
-    {
-        double cx = 0.0, cy = 0.0;
-        const double2* pp = corrp + ((size_t)k * Q + q) * chunks;
-        for (int c = 0; c < chunks; ++c) {
-            cx += pp[c].x;
-            cy += pp[c].y;
-        }
-        corr[(size_t)k * Q + q] = make_double2(cx, cy);
-    }
+// Float64 normal equations of atoms 0..n-1 of receiver q (Cholesky, dependent
+// atoms dropped), amplitudes rotated back to the atoms of the signal model.
+__device__ void bomp_solve_q(int q, int Q, int Ms, int Mc, int n, int K, const double2* corr, const double2* phase,
+                             const double* gram, double2* alpha) {
     double L[GH_MAX_K][GH_MAX_K];
     double zr[GH_MAX_K], zi[GH_MAX_K];
     bool dep[GH_MAX_K];
@@ -221,27 +233,79 @@ __global__ void bomp_solve_kernel(int Q, int Ms, int Mc, int k, int K, int chunk
     }
 }
 
-__global__ void __launch_bounds__(256) bomp_residual_kernel(const float2* __restrict__ Y, GeoParams g, int n,
-                                                            const double2* __restrict__ alpha,
-                                                            const float2* __restrict__ atoms_a,
-                                                            const float2* __restrict__ atoms_b,
-                                                            float2* __restrict__ R) {
-    const size_t per_q = (size_t)g.Mc * g.Ms;
-    const size_t total = per_q * g.Q;
+// CTA (chunk, q): partial <Y_q, b(u) (x) a(r)> over kCorrRows chirps. The last
+// CTA to finish sums the partials and solves every receiver's least squares.
+__global__ void __launch_bounds__(256) bomp_corr_kernel(const float2* __restrict__ Y, GeoParams g, int k, int K,
+                                                        BompPtrs w) {
+    const int ch = blockIdx.x, q = blockIdx.y;
+    const float2* a = w.atoms_a + ((size_t)k * g.Q + q) * g.Ms;
+    const float2* b = w.atoms_b + ((size_t)k * g.Q + q) * g.Mc;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mc = ch * kCorrRows + warp;
+    __shared__ double rx[kCorrRows], ry[kCorrRows];
+    __shared__ bool s_last;
+    double sx = 0.0, sy = 0.0;
+    if (warp < kCorrRows && mc < g.Mc) {
+        const float2* row = Y + ((size_t)q * g.Mc + mc) * g.Ms;
+        float2 s = make_float2(0.f, 0.f);
+        for (int m = lane; m < g.Ms; m += 32) {
+            const float2 y = row[m];
+            const float2 v = a[m];
+            s.x += y.x * v.x + y.y * v.y;  // y * conj(a)
+            s.y += y.y * v.x - y.x * v.y;
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            s.x += __shfl_down_sync(0xffffffffu, s.x, off);
+            s.y += __shfl_down_sync(0xffffffffu, s.y, off);
+        }
+        const double bx = b[mc].x, by = b[mc].y;  // s * conj(b)
+        sx = (double)s.x * bx + (double)s.y * by;
+        sy = (double)s.y * bx - (double)s.x * by;
+    }
+    if (lane == 0 && warp < kCorrRows) {
+        rx[warp] = sx;
+        ry[warp] = sy;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tx = 0, ty = 0;
+        for (int ww = 0; ww < kCorrRows; ++ww) {
+            tx += rx[ww];
+            ty += ry[ww];
+        }
+        w.corrp[((size_t)k * g.Q + q) * w.chunks + ch] = make_double2(tx, ty);
+        __threadfence();
+        const unsigned int total = gridDim.x * gridDim.y;
+        s_last = atomicAdd(w.counter, 1u) == total - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int qq = threadIdx.x;
+    if (qq < g.Q) {
+        double cx = 0.0, cy = 0.0;
+        const double2* pp = w.corrp + ((size_t)k * g.Q + qq) * w.chunks;
+        for (int c = 0; c < w.chunks; ++c) {
+            const double2 v = __ldcg(pp + c);
+            cx += v.x;
+            cy += v.y;
+        }
+        w.corr[(size_t)k * g.Q + qq] = make_double2(cx, cy);
+        bomp_solve_q(qq, g.Q, g.Ms, g.Mc, k + 1, K, w.corr, w.phase, w.gram, w.alpha);
+    }
+    if (threadIdx.x == 0) *w.counter = 0u;  // ready for the next iteration
+}
+
+__global__ void __launch_bounds__(256) residual_kernel(const float2* __restrict__ Y, int Q, int Ms, int Mc,
+                                                       Deflate df, float2* __restrict__ R) {
+    const size_t per_q = (size_t)Mc * Ms;
+    const size_t total = per_q * Q;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const int q = (int)(idx / per_q);
         const size_t e = idx - (size_t)q * per_q;
-        const int mc = (int)(e / g.Ms), m = (int)(e - (size_t)mc * g.Ms);
-        float2 v = Y[idx];
-        for (int t = 0; t < n; ++t) {
-            const double2 al = alpha[(size_t)t * g.Q + q];
-            const float2 ab = cmul(atoms_b[((size_t)t * g.Q + q) * g.Mc + mc], atoms_a[((size_t)t * g.Q + q) * g.Ms + m]);
-            const float2 c = cmul(make_float2((float)al.x, (float)al.y), ab);
-            v.x -= c.x;
-            v.y -= c.y;
-        }
-        R[idx] = v;
+        const int mc = (int)(e / Ms), m = (int)(e - (size_t)mc * Ms);
+        R[idx] = gh_deflate(df, Q, Ms, Mc, q, mc, m, Y[idx]);
     }
 }
 
@@ -279,35 +343,47 @@ __global__ void __launch_bounds__(256) synth_kernel(GeoParams g, int T, const do
 
 size_t gh_bomp_ws_bytes(const Dims& d, int K) { return bomp_layout(d, K).total; }
 
-int gh_launch_bomp_iter(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y, float2* R, int k, int K,
-                        const ArgResult* sel, void* ws) {
-    const BompLayout L = bomp_layout(d, K);
-    char* base = (char*)ws;
-    double2* alpha = (double2*)(base + L.alpha);
-    double2* corr = (double2*)(base + L.corr);
-    double2* ru = (double2*)(base + L.ru);
-    double2* phase = (double2*)(base + L.phase);
-    double* gram = (double*)(base + L.gram);
-    double2* corrp = (double2*)(base + L.corrp);
-    float2* aa = (float2*)(base + L.atoms_a);
-    float2* ab = (float2*)(base + L.atoms_b);
+Deflate gh_bomp_deflate(void* ws, const Dims& d, int K, int n) {
+    const BompPtrs w = bomp_ptrs(ws, d, K);
+    Deflate f;
+    f.alpha = w.alpha;
+    f.atoms_a = w.atoms_a;
+    f.atoms_b = w.atoms_b;
+    f.n = n;
+    return f;
+}
+
+int gh_bomp_reset(gh_ctx* ctx, const Dims& d, int K, void* ws) {
+    const BompPtrs w = bomp_ptrs(ws, d, K);
+    GH_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned int), ctx->stream));
+    return GH_OK;
+}
+
+int gh_launch_bomp_select(gh_ctx* ctx, const Dims& d, const GeoParams& g, const ArgPartial* parts, int nparts,
+                          ArgResult* sel, int64_t* mask, int k, int K, void* ws) {
+    const BompPtrs w = bomp_ptrs(ws, d, K);
+    cudaEvent_t ev;
+    gh_launch_begin(ctx, GH_K_ARGMAX, &ev);
+    bomp_select_kernel<<<1, 1024, 0, ctx->stream>>>(parts, nparts, sel, mask, k, K, g, w);
+    return gh_launch_end(ctx, GH_K_ARGMAX, ev, "bomp_select_kernel");
+}
+
+int gh_launch_bomp_corr(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y, int k, int K, void* ws) {
+    const BompPtrs w = bomp_ptrs(ws, d, K);
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_BOMP, &ev);
-    bomp_atoms_kernel<<<d.Q, 256, 0, ctx->stream>>>(g, sel, k, K, ru, phase, gram, aa, ab);
-    GH_TRY(gh_launch_end(ctx, GH_K_BOMP, ev, "bomp_atoms_kernel"));
-    gh_launch_begin(ctx, GH_K_BOMP, &ev);
-    bomp_corr_kernel<<<dim3(L.chunks, d.Q), 32 * kCorrRows, 0, ctx->stream>>>(Y, g, k, L.chunks, aa, ab, corrp);
-    GH_TRY(gh_launch_end(ctx, GH_K_BOMP, ev, "bomp_corr_kernel"));
-    gh_launch_begin(ctx, GH_K_BOMP, &ev);
-    bomp_solve_kernel<<<(d.Q + 31) / 32, 32, 0, ctx->stream>>>(d.Q, d.Ms, d.Mc, k, K, L.chunks, corrp, corr, phase,
-                                                              gram, alpha);
-    GH_TRY(gh_launch_end(ctx, GH_K_BOMP, ev, "bomp_solve_kernel"));
+    bomp_corr_kernel<<<dim3(w.chunks, d.Q), 32 * kCorrRows, 0, ctx->stream>>>(Y, g, k, K, w);
+    return gh_launch_end(ctx, GH_K_BOMP, ev, "bomp_corr_kernel");
+}
+
+int gh_launch_residual(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate& df, float2* R) {
     const size_t total = (size_t)d.Q * d.Mc * d.Ms;
     unsigned blocks = (unsigned)((total + 255) / 256);
     if (blocks > (unsigned)ctx->num_sms * 8) blocks = (unsigned)ctx->num_sms * 8;
+    cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_BOMP, &ev);
-    bomp_residual_kernel<<<blocks, 256, 0, ctx->stream>>>(Y, g, k + 1, alpha, aa, ab, R);
-    return gh_launch_end(ctx, GH_K_BOMP, ev, "bomp_residual_kernel");
+    residual_kernel<<<blocks, 256, 0, ctx->stream>>>(Y, d.Q, d.Ms, d.Mc, df, R);
+    return gh_launch_end(ctx, GH_K_BOMP, ev, "residual_kernel");
 }
 
 int gh_launch_synth(gh_ctx* ctx, const Dims& d, const GeoParams& g, int T, const double* tgt, const float2* noise,

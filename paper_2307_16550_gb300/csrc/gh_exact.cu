@@ -611,7 +611,8 @@ __device__ __forceinline__ void store_chunk(unsigned char* hi, unsigned char* lo
 }
 
 // Y -> per (q, stage) B tiles [hi | lo], rows mc, K = [Re Y[mc][32s..] | Im Y[mc][32s..]].
-__global__ void y_split_kernel(const float2* __restrict__ Y, int Q, int Ms, int Mc, unsigned char* __restrict__ out) {
+__global__ void y_split_kernel(const float2* __restrict__ Y, int Q, int Ms, int Mc, Deflate df,
+                               unsigned char* __restrict__ out) {
     const int nst = Ms / 32;
     const long long total = (long long)Q * nst * Mc * 8;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -625,10 +626,15 @@ __global__ void y_split_kernel(const float2* __restrict__ Y, int Q, int Ms, int 
     const uint32_t tile = (uint32_t)Mc * 64 * 2, lbo = (uint32_t)(Mc / 8) * 128;
     unsigned char* hi = out + ((size_t)(q * nst + s) * 2) * tile;
     unsigned char* lo = hi + tile;
-    const float2* row = Y + ((size_t)q * Mc + mc) * Ms + 32 * s + 8 * (c & 3);
+    const int m0 = 32 * s + 8 * (c & 3);
+    const float2* row = Y + ((size_t)q * Mc + mc) * Ms + m0;
     float v[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = c < 4 ? row[i].x : row[i].y;
+    for (int i = 0; i < 8; ++i) {
+        float2 y = row[i];
+        if (df.n > 0) y = gh_deflate(df, Q, Ms, Mc, q, mc, m0 + i, y);
+        v[i] = c < 4 ? y.x : y.y;
+    }
     const uint32_t off = gh_tc::kmajor_off((uint32_t)mc, (uint32_t)(8 * c), lbo, 128);
     store_chunk(hi, lo, off, v);
 }
@@ -799,7 +805,8 @@ __global__ void __launch_bounds__(256, 1) exact_s1_tc_kernel(const unsigned char
 }
 
 template <int NMC>
-int launch_s1_tc(gh_ctx* ctx, const Dims& d, const float2* Y, const ExEntry* tab, float* P, int* status) {
+int launch_s1_tc(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate& df, const ExEntry* tab, float* P,
+                 int* status) {
     constexpr uint32_t B_BYTES = NMC * 64 * 2;
     const size_t smem = (size_t)2 * (2 * 128 * 64 * 2 + 2 * B_BYTES);
     if (smem > ctx->smem_optin) return gh_fail(ctx, GH_ENOTSUP, "stage-1 tensor-core path needs %zu B", smem);
@@ -809,7 +816,8 @@ int launch_s1_tc(gh_ctx* ctx, const Dims& d, const float2* Y, const ExEntry* tab
     cudaEvent_t ev;
     const long long nsplit = (long long)d.Q * nst * d.Mc * 8;
     gh_launch_begin(ctx, GH_K_EXACT_S1, &ev);
-    y_split_kernel<<<(unsigned)((nsplit + 255) / 256), 256, 0, ctx->stream>>>(Y, d.Q, d.Ms, d.Mc, (unsigned char*)bt);
+    y_split_kernel<<<(unsigned)((nsplit + 255) / 256), 256, 0, ctx->stream>>>(Y, d.Q, d.Ms, d.Mc, df,
+                                                                               (unsigned char*)bt);
     GH_TRY(gh_launch_end(ctx, GH_K_EXACT_S1, ev, "y_split_kernel"));
     GH_CUDA(cudaFuncSetAttribute(exact_s1_tc_kernel<NMC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     GH_CUDA(cudaFuncSetAttribute(exact_s1_tc_kernel<NMC>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -860,10 +868,11 @@ int launch_tc(gh_ctx* ctx, const Dims& d, const float* P, const ExEntry* tab, fl
 
 }  // namespace
 
-int gh_launch_exact(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y, float* scores,
-                    const int64_t* mask, int nmask, ArgResult* result) {
+int gh_launch_exact_parts(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y, const Deflate* dfp,
+                          float* scores, const int64_t* mask, int nmask, ArgPartial** parts_out, int* nparts_out) {
     if (d.nxy > 0x7fffffffLL) return gh_fail(ctx, GH_ENOTSUP, "exact path supports < 2^31 (x, y) cells");
     if (d.nv > 256 * 16) return gh_fail(ctx, GH_ENOTSUP, "exact path supports at most 4096 velocity cells");
+    const Deflate df = dfp ? *dfp : Deflate{nullptr, nullptr, nullptr, 0};
     void* P;  // planar [Q][nxy][Re row | Im row][Mc]
     GH_TRY(gh_ws(ctx, WS_EXACT_P, (size_t)d.Q * d.nxy * 2 * d.Mc * sizeof(float), &P));
     const bool tc1 = d.Ms % 32 == 0 && (d.Mc == 32 || d.Mc == 64 || d.Mc == 128 || d.Mc == 256);
@@ -881,18 +890,26 @@ int gh_launch_exact(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2
     if (tc1) {
         const ExEntry* t = (const ExEntry*)tab;
         float* Pf = (float*)P;
-        if (d.Mc == 32) GH_TRY(launch_s1_tc<32>(ctx, d, Y, t, Pf, status));
-        else if (d.Mc == 64) GH_TRY(launch_s1_tc<64>(ctx, d, Y, t, Pf, status));
-        else if (d.Mc == 128) GH_TRY(launch_s1_tc<128>(ctx, d, Y, t, Pf, status));
-        else GH_TRY(launch_s1_tc<256>(ctx, d, Y, t, Pf, status));
+        if (d.Mc == 32) GH_TRY(launch_s1_tc<32>(ctx, d, Y, df, t, Pf, status));
+        else if (d.Mc == 64) GH_TRY(launch_s1_tc<64>(ctx, d, Y, df, t, Pf, status));
+        else if (d.Mc == 128) GH_TRY(launch_s1_tc<128>(ctx, d, Y, df, t, Pf, status));
+        else GH_TRY(launch_s1_tc<256>(ctx, d, Y, df, t, Pf, status));
     } else {
+        const float2* Ys = Y;
+        if (df.n > 0) {  // the CUDA-core stage 1 reads a stored residual
+            void* R;
+            GH_TRY(gh_ws(ctx, WS_R, (size_t)d.Q * d.Mc * d.Ms * sizeof(float2), &R));
+            GH_TRY(gh_launch_residual(ctx, d, Y, df, (float2*)R));
+            Ys = (const float2*)R;
+        }
         gh_launch_begin(ctx, GH_K_EXACT_S1, &ev);
         dim3 grid1((unsigned)((d.nxy + S1_XT - 1) / S1_XT), (unsigned)((d.Mc + S1_MT - 1) / S1_MT), (unsigned)d.Q);
-        exact_stage1_kernel<<<grid1, 256, 0, ctx->stream>>>(Y, g, (float*)P);
+        exact_stage1_kernel<<<grid1, 256, 0, ctx->stream>>>(Ys, g, (float*)P);
         GH_TRY(gh_launch_end(ctx, GH_K_EXACT_S1, ev, "exact_stage1_kernel"));
     }
     void* parts;
     GH_TRY(gh_ws(ctx, WS_PART, (size_t)d.nxy * sizeof(ArgPartial), &parts));
+    *parts_out = (ArgPartial*)parts;
     if (tc2) {
         long long nparts = 0;
         if (d.nvy <= 32)
@@ -901,7 +918,8 @@ int gh_launch_exact(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2
         else
             GH_TRY(launch_tc<2>(ctx, d, (const float*)P, (const ExEntry*)tab, scores, mask, nmask,
                                 (ArgPartial*)parts, status, &nparts));
-        return gh_launch_argmax_finalize(ctx, (const ArgPartial*)parts, (int)nparts, result);
+        *nparts_out = (int)nparts;
+        return GH_OK;
     }
     const int cpt = (int)((d.nv + 255) / 256);
     int st;
@@ -916,5 +934,14 @@ int gh_launch_exact(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2
     else
         st = launch_s2<16>(ctx, d, g, (const float*)P, scores, mask, nmask, (ArgPartial*)parts);
     GH_TRY(st);
-    return gh_launch_argmax_finalize(ctx, (const ArgPartial*)parts, (int)d.nxy, result);
+    *nparts_out = (int)d.nxy;
+    return GH_OK;
+}
+
+int gh_launch_exact(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y, float* scores,
+                    const int64_t* mask, int nmask, ArgResult* result) {
+    ArgPartial* parts;
+    int nparts;
+    GH_TRY(gh_launch_exact_parts(ctx, d, g, Y, nullptr, scores, mask, nmask, &parts, &nparts));
+    return gh_launch_argmax_finalize(ctx, parts, nparts, result);
 }

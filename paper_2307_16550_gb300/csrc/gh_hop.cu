@@ -37,15 +37,23 @@ inline uint32_t hop_tol(int nvx, int nvy) {
     return (uint32_t)(t > 4096 ? t : 4096);
 }
 
+#ifndef GH_HOP_U
+#define GH_HOP_U 4  // map-row loads in flight per lane in the power-row build
+#endif
+#ifndef GH_HOP_MINB
+#define GH_HOP_MINB 2  // CTAs per SM the scorer's register budget targets
+#endif
+
 struct __align__(16) HopEntry {
-    long long base;  // (eta(0,0) + 1/2) * 2^32 + tol
+    long long base;  // (eta(0,0) - j_ref + 1/2) * 2^32 + tol
     long long ax;    // d eta / d ivx * 2^32
     long long by;    // d eta / d ivy * 2^32
     double wx, wy;   // bistatic gradient (float64 bin decisions)
     int row[3];      // map rows (i + k) mod Nr, k = -1, 0, 1
     float cs[3];     // polar coefficients times the wrap sign
-    int j_lo;        // first Doppler bin the velocity grid reaches (minus one)
-    int nP;          // number of bins from j_lo on that it reaches (<= Nd)
+    int j_ref;       // even Doppler bin of power-row entry 0 (entry u is bin (j_ref + u) mod Nd)
+    int npair;       // power-row entries to build, in pairs
+    int wrap;        // 1 if the velocity grid reaches more than Nd - 1 bins (entries wrap mod Nd)
 };
 static_assert(sizeof(HopEntry) == 80, "HopEntry layout");
 
@@ -106,15 +114,18 @@ __global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__
     const double emax = eta00 + fmax(0.0, ex) + fmax(0.0, ey);
     const long long j_lo = (long long)floor(emin + 0.5) - 1;
     const long long j_hi = (long long)floor(emax + 0.5) + 1;
-    const long long span = j_hi - j_lo + 1;
+    const long long j_ref = j_lo & ~1LL;  // even, <= j_lo
+    const long long nu = j_hi - j_ref + 1;
+    const bool wrap = nu > g.Nd;
     const double two32 = 4294967296.0;
-    e.base = llrint((eta00 + 0.5) * two32) + (long long)cp.tol;
+    e.base = llrint((eta00 - (double)j_ref + 0.5) * two32) + (long long)cp.tol;
     e.ax = llrint(ax * two32);
     e.by = llrint(by * two32);
     e.wx = wx;
     e.wy = wy;
-    e.j_lo = (int)j_lo;
-    e.nP = (int)(span < g.Nd ? span : g.Nd);
+    e.j_ref = (int)j_ref;
+    e.npair = wrap ? g.Nd / 2 : (int)((nu + 1) >> 1);
+    e.wrap = wrap ? 1 : 0;
     table[idx] = e;
 
     if (diag_i) {
@@ -135,14 +146,13 @@ struct HopParams {
     double lo2, step2, lo3, step3, kappa;
 };
 
-// Exact float64 Doppler bin (mod Nd) of cell (a, b).
-__device__ __noinline__ int slow_bin(double wx, double wy, int a, int b, double lo2, double step2, double lo3,
-                                     double step3, double kappa, int Nd) {
+// Exact float64 Doppler bin of cell (a, b), unwrapped.
+__device__ __noinline__ long long slow_bin(double wx, double wy, int a, int b, double lo2, double step2, double lo3,
+                                           double step3, double kappa, int Nd) {
     const double vx = gh_axis(lo2, step2, a);
     const double vy = gh_axis(lo3, step3, b);
     const double u = __dmul_rn(kappa, __dadd_rn(__dmul_rn(wx, vx), __dmul_rn(wy, vy)));
-    const long long j = (long long)floor(__dadd_rn(__dmul_rn((double)Nd, u), 0.5));
-    return (int)(j & (Nd - 1));
+    return (long long)floor(__dadd_rn(__dmul_rn((double)Nd, u), 0.5));
 }
 
 __device__ __forceinline__ void better(float s, long long c, float& bs, long long& bc) {
@@ -154,7 +164,7 @@ __device__ __forceinline__ void better(float s, long long c, float& bs, long lon
 
 // AC: velocity cells per lane per pass (along vx, stride SA).
 template <int AC>
-__global__ void __launch_bounds__(256, 2) hop_score_kernel(const float2* __restrict__ maps,
+__global__ void __launch_bounds__(256, GH_HOP_MINB) hop_score_kernel(const float2* __restrict__ maps,
                                                            const HopEntry* __restrict__ table, HopParams p,
                                                            float* __restrict__ scores,
                                                            const int64_t* __restrict__ mask, int nmask,
@@ -189,38 +199,35 @@ __global__ void __launch_bounds__(256, 2) hop_score_kernel(const float2* __restr
         __syncwarp();
         for (int q = 0; q < p.Q; ++q) {
             const HopEntry& eq = E[q];
-            const int j_lo = eq.j_lo, nP = eq.nP;
+            const int j_ref = eq.j_ref, npair = eq.npair;
             const float c0 = eq.cs[0], c1 = eq.cs[1], c2 = eq.cs[2];
             const size_t qb = (size_t)q * p.Nr;
             const float4* r0 = (const float4*)(maps + (qb + eq.row[0]) * p.Nd);
             const float4* r1 = (const float4*)(maps + (qb + eq.row[1]) * p.Nd);
             const float4* r2 = (const float4*)(maps + (qb + eq.row[2]) * p.Nd);
-            const int jbeg = j_lo & ~1;
-            int npair = (nP + (j_lo - jbeg) + 1) >> 1;
-            if (npair > (p.Nd >> 1)) npair = p.Nd >> 1;
             float* Pq = P + (size_t)q * p.Nd;
-            constexpr int U = 4;  // row loads in flight per lane
+            constexpr int U = GH_HOP_U;  // row loads in flight per lane
             for (int pp0 = 0; pp0 < npair; pp0 += 32 * U) {
                 float4 z0[U], z1[U], z2[U];
-                int jj[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int pp = pp0 + lane + 32 * u;
-                    jj[u] = (jbeg + 2 * pp) & ndm;
                     if (pp < npair) {
-                        z0[u] = __ldg(r0 + (jj[u] >> 1));
-                        z1[u] = __ldg(r1 + (jj[u] >> 1));
-                        z2[u] = __ldg(r2 + (jj[u] >> 1));
+                        const int jh = ((j_ref + 2 * pp) & ndm) >> 1;  // pair of absolute bins
+                        z0[u] = __ldg(r0 + jh);
+                        z1[u] = __ldg(r1 + jh);
+                        z2[u] = __ldg(r2 + jh);
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    if (pp0 + lane + 32 * u < npair) {
+                    const int pp = pp0 + lane + 32 * u;
+                    if (pp < npair) {
                         const float re0 = c0 * z0[u].x + c1 * z1[u].x + c2 * z2[u].x;
                         const float im0 = c0 * z0[u].y + c1 * z1[u].y + c2 * z2[u].y;
                         const float re1 = c0 * z0[u].z + c1 * z1[u].z + c2 * z2[u].z;
                         const float im1 = c0 * z0[u].w + c1 * z1[u].w + c2 * z2[u].w;
-                        *(float2*)(Pq + jj[u]) = make_float2(re0 * re0 + im0 * im0, re1 * re1 + im1 * im1);
+                        *(float2*)(Pq + 2 * pp) = make_float2(re0 * re0 + im0 * im0, re1 * re1 + im1 * im1);
                     }
                 }
             }
@@ -240,13 +247,17 @@ __global__ void __launch_bounds__(256, 2) hop_score_kernel(const float2* __restr
                     const long long t0 = eq.base + (long long)b * eq.by + (long long)a0 * eq.ax;
                     const long long st = (long long)p.SA * eq.ax;
                     const float* Pq = P + (size_t)q * p.Nd;
+                    // entries wrap mod Nd only in the rare case of a grid reaching >= Nd bins
+                    const int imask = eq.wrap ? ndm : -1;
                     long long t = t0;
                     bool amb = false;
+                    {
 #pragma unroll
-                    for (int i = 0; i < AC; ++i) {
-                        amb |= (uint32_t)t < p.tol2;
-                        acc[i] += Pq[(int)(t >> 32) & ndm];
-                        t += st;
+                        for (int i = 0; i < AC; ++i) {
+                            amb |= (uint32_t)t < p.tol2;
+                            acc[i] += Pq[(int)(t >> 32) & imask];
+                            t += st;
+                        }
                     }
                     if (amb) {
                         // rare: a bin decision within tol of a rounding boundary;
@@ -258,9 +269,10 @@ __global__ void __launch_bounds__(256, 2) hop_score_kernel(const float2* __restr
                         for (int i = 0; i < AC; ++i) {
                             float dlt = 0.f;
                             if ((uint32_t)t < p.tol2) {
-                                const int fast = (int)(t >> 32) & ndm;
-                                const int exact = slow_bin(eq.wx, eq.wy, a0 + i * p.SA, b, p.lo2, p.step2, p.lo3,
-                                                           p.step3, p.kappa, p.Nd);
+                                const int fast = (int)(t >> 32) & imask;
+                                const long long j = slow_bin(eq.wx, eq.wy, a0 + i * p.SA, b, p.lo2, p.step2, p.lo3,
+                                                             p.step3, p.kappa, p.Nd);
+                                const int exact = (int)(j - eq.j_ref) & imask;
                                 if (exact != fast) dlt = Pq[exact] - Pq[fast];
                             }
                             fix[i] = dlt;
@@ -451,8 +463,8 @@ int gh_launch_argmax_finalize(gh_ctx* ctx, const ArgPartial* parts, int nparts, 
     return gh_launch_end(ctx, GH_K_ARGMAX, ev, "argmax_finalize_kernel");
 }
 
-int gh_launch_hop(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* maps, const void* table,
-                  float* scores, const int64_t* mask, int nmask, ArgResult* result) {
+int gh_launch_hop_parts(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* maps, const void* table,
+                        float* scores, const int64_t* mask, int nmask, ArgPartial** parts_out, int* nparts_out) {
     const HopParams hp = hop_params(d, g);
     const long long max_ctas = (long long)ctx->num_sms * 32;
     void* parts;
@@ -465,7 +477,17 @@ int gh_launch_hop(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* 
     if (st == GH_ENOTSUP) return gh_fail(ctx, GH_ENOTSUP, "hop scorer: Q*Nd*4 bytes exceed shared memory");
     GH_TRY(gh_launch_end(ctx, GH_K_HOP_SCORE, ev, "hop_score_kernel"));
     if (st != GH_OK) return gh_fail(ctx, st, "hop scorer launch failed");
-    return gh_launch_argmax_finalize(ctx, (const ArgPartial*)parts, (int)nparts, result);
+    *parts_out = (ArgPartial*)parts;
+    *nparts_out = (int)nparts;
+    return GH_OK;
+}
+
+int gh_launch_hop(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* maps, const void* table,
+                  float* scores, const int64_t* mask, int nmask, ArgResult* result) {
+    ArgPartial* parts;
+    int nparts;
+    GH_TRY(gh_launch_hop_parts(ctx, d, g, maps, table, scores, mask, nmask, &parts, &nparts));
+    return gh_launch_argmax_finalize(ctx, parts, nparts, result);
 }
 
 // ---------------------------------------------------------------------------

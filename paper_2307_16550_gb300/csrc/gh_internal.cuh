@@ -190,6 +190,31 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
 }
 
 // ---------------------------------------------------------------------------
+// On-the-fly deflation of a measurement (BOMP residual):
+//   R_q[mc][m] = Y_q[mc][m] - sum_{t < n} alpha[t][q] b_t,q[mc] a_t,q[m]
+// ---------------------------------------------------------------------------
+struct Deflate {
+    const double2* alpha;    // [K][Q] amplitudes
+    const float2* atoms_a;   // [K][Q][Ms] a(r_t,q)
+    const float2* atoms_b;   // [K][Q][Mc] b(u_t,q)
+    int n;                   // atoms to subtract (0: Y unchanged)
+};
+
+__device__ __forceinline__ float2 gh_deflate(const Deflate& f, int Q, int Ms, int Mc, int q, int mc, int m,
+                                             float2 y) {
+    for (int t = 0; t < f.n; ++t) {
+        const double2 al = f.alpha[(size_t)t * Q + q];
+        const float2 b = f.atoms_b[((size_t)t * Q + q) * Mc + mc];
+        const float2 a = f.atoms_a[((size_t)t * Q + q) * Ms + m];
+        const float2 ab = make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+        const float ax = (float)al.x, ay = (float)al.y;
+        y.x -= ax * ab.x - ay * ab.y;
+        y.y -= ax * ab.y + ay * ab.x;
+    }
+    return y;
+}
+
+// ---------------------------------------------------------------------------
 // Per-kernel launchers (one per .cu file)
 // ---------------------------------------------------------------------------
 struct ArgPartial {
@@ -205,21 +230,38 @@ struct ArgResult {
     int32_t valid;
 };
 
-int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, float2* maps);
+int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* df, float2* maps);
 int gh_launch_coord(gh_ctx* ctx, const Dims& d, const GeoParams& g, void* table,
                     int32_t* diag_i, double* diag_tau, float* diag_c, double* diag_w);
 size_t gh_hop_table_bytes(const Dims& d);
+// Scorer: per-CTA argmax partials into the context workspace (*parts, *nparts);
+// gh_launch_hop also reduces them into *result.
+int gh_launch_hop_parts(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* maps,
+                        const void* table, float* scores, const int64_t* mask, int nmask,
+                        ArgPartial** parts, int* nparts);
 int gh_launch_hop(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* maps,
                   const void* table, float* scores, const int64_t* mask, int nmask,
                   ArgResult* result);
 int gh_launch_argmax_finalize(gh_ctx* ctx, const ArgPartial* parts, int nparts, ArgResult* out);
+// Exact direct scores of the (deflated) measurement; partials as gh_launch_hop_parts.
+int gh_launch_exact_parts(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y,
+                          const Deflate* df, float* scores, const int64_t* mask, int nmask,
+                          ArgPartial** parts, int* nparts);
 int gh_launch_exact(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y,
                     float* scores, const int64_t* mask, int nmask, ArgResult* result);
 int gh_launch_synth(gh_ctx* ctx, const Dims& d, const GeoParams& g, int T,
                     const double* targets_alpha_dev, const float2* noise, float2* Y);
+int gh_launch_residual(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate& df, float2* R);
 
-// BOMP iteration k of K (workspace of gh_bomp_ws_bytes(d, K) bytes; the
-// amplitudes, double2 [K][Q], sit at its start).
-int gh_launch_bomp_iter(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y,
-                        float2* R, int k, int K, const ArgResult* sel, void* bomp_ws);
+// BOMP (workspace of gh_bomp_ws_bytes(d, K) bytes; the amplitudes, double2
+// [K][Q], sit at its start). Iteration k: gh_launch_bomp_select reduces the
+// scorer's partials into sel[k] (and mask[k]) and prepares the new atom;
+// gh_launch_bomp_corr correlates it with Y and solves the least squares of
+// atoms 0..k. gh_bomp_reset zeroes the workspace's completion counter.
 size_t gh_bomp_ws_bytes(const Dims& d, int K);
+Deflate gh_bomp_deflate(void* bomp_ws, const Dims& d, int K, int n);
+int gh_bomp_reset(gh_ctx* ctx, const Dims& d, int K, void* bomp_ws);
+int gh_launch_bomp_select(gh_ctx* ctx, const Dims& d, const GeoParams& g, const ArgPartial* parts,
+                          int nparts, ArgResult* sel, int64_t* mask, int k, int K, void* bomp_ws);
+int gh_launch_bomp_corr(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y, int k, int K,
+                        void* bomp_ws);

@@ -5,7 +5,8 @@
 // radix-2 pass for odd log2 sizes) with float32 data and a twiddle table
 // rounded from float64 and staged in shared memory:
 //   range_fft   : per (q, mc) row, the Ms samples zero-padded to Nr = pad*Ms,
-//                 written [Q][Mc][Nr];
+//                 written [Q][Mc][Nr]; a BOMP residual is subtracted from the
+//                 samples as they are loaded;
 //   doppler_fft : per (q, block of IB range bins), the Mc chirps zero-padded to
 //                 Nd = pad*Mc, times the range-centring factor
 //                 exp(j pi (i/Nr)(Ms-1)), written [Q][Nr][Nd] so that one
@@ -90,7 +91,8 @@ __device__ void load_twiddles(float2* dst, const float2* __restrict__ src, int n
 }
 
 __global__ void __launch_bounds__(256) range_fft_kernel(const float2* __restrict__ Y, float2* __restrict__ out,
-                                                        int Ms, int logNr, int rows, int rows_per_cta,
+                                                        int Q, int Ms, int Mc, int logNr, int rows,
+                                                        int rows_per_cta, Deflate df,
                                                         const float2* __restrict__ tw) {
     extern __shared__ float2 smem[];
     const int Nr = 1 << logNr;
@@ -103,7 +105,13 @@ __global__ void __launch_bounds__(256) range_fft_kernel(const float2* __restrict
     for (int idx = threadIdx.x; idx < nrow * Nr; idx += blockDim.x) {
         const int c = idx >> logNr;
         const int n = idx & (Nr - 1);
-        x[idx] = n < Ms ? Y[(size_t)(r0 + c) * Ms + n] : make_float2(0.f, 0.f);
+        float2 v = make_float2(0.f, 0.f);
+        if (n < Ms) {
+            const int row = r0 + c;  // q * Mc + mc
+            v = Y[(size_t)row * Ms + n];
+            if (df.n > 0) v = gh_deflate(df, Q, Ms, Mc, row / Mc, row % Mc, n, v);
+        }
+        x[idx] = v;
     }
     __syncthreads();
     float2* res = fft_columns(x, y, logNr, nrow, Nr, twS);
@@ -187,7 +195,8 @@ int ensure_twiddles(gh_ctx* ctx, int Nr, int Nd, const float2** twr, const float
 
 }  // namespace
 
-int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, float2* maps) {
+int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* df, float2* maps) {
+    Deflate none = {nullptr, nullptr, nullptr, 0};
     const float2 *twr, *twd;
     GH_TRY(ensure_twiddles(ctx, d.Nr, d.Nd, &twr, &twd));
     void* zr;
@@ -202,8 +211,8 @@ int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, float2* maps) {
     GH_CUDA(cudaFuncSetAttribute(range_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_RANGE_FFT, &ev);
-    range_fft_kernel<<<(rows + rpc - 1) / rpc, 256, smem1, ctx->stream>>>(Y, (float2*)zr, d.Ms, logNr, rows, rpc,
-                                                                          twr);
+    range_fft_kernel<<<(rows + rpc - 1) / rpc, 256, smem1, ctx->stream>>>(Y, (float2*)zr, d.Q, d.Ms, d.Mc, logNr,
+                                                                          rows, rpc, df ? *df : none, twr);
     GH_TRY(gh_launch_end(ctx, GH_K_RANGE_FFT, ev, "range_fft_kernel"));
 
     // Doppler FFT: IB range bins per CTA

@@ -94,3 +94,59 @@ extern "C" int gh_selftest_tcgen05(gh_ctx* ctx, const float* A_host, const float
     if (st != 0) return gh_fail(ctx, GH_ETIMEOUT, "tensor-core self-test: mbarrier wait timed out");
     return GH_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Read-bandwidth probe: every thread streams 16-byte loads over a buffer of
+// `bytes` bytes, `reps` times; a buffer much smaller than L2 measures the
+// L2-to-SM bandwidth, a buffer much larger measures DRAM read bandwidth.
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void __launch_bounds__(512) probe_read_kernel(const float4* __restrict__ buf, long long n4, int reps,
+                                                         float* __restrict__ sink) {
+    float acc = 0.f;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (int r = 0; r < reps; ++r) {
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += 4 * stride) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long j = i + u * stride;
+                v[u] = j < n4 ? __ldcg(buf + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc += v[u].x + v[u].y + v[u].z + v[u].w;
+        }
+    }
+    if (acc == 1.234567e-30f) sink[0] = acc;  // keeps the loads alive
+}
+}  // namespace
+
+extern "C" int gh_probe_read_bandwidth(gh_ctx* ctx, int64_t bytes, int32_t reps, double* gbs) {
+    if (!ctx || !gbs) return GH_EINVAL;
+    if (bytes < (1 << 20) || bytes > ((int64_t)64 << 30) || reps < 1 || reps > 1000)
+        return gh_fail(ctx, GH_EINVAL, "bytes must be in [1 MiB, 64 GiB], reps in [1, 1000]");
+    cudaSetDevice(ctx->device);
+    void* buf;
+    GH_TRY(gh_ws(ctx, WS_DIAG, (size_t)bytes + 256, &buf));
+    GH_CUDA(cudaMemsetAsync(buf, 0, (size_t)bytes + 256, ctx->stream));
+    const long long n4 = bytes / 16;
+    float* sink = (float*)((char*)buf + bytes);
+    const unsigned blocks = (unsigned)ctx->num_sms * 4;
+    probe_read_kernel<<<blocks, 512, 0, ctx->stream>>>((const float4*)buf, n4, 1, sink);  // warm
+    GH_CUDA(cudaGetLastError());
+    cudaEvent_t a, b;
+    GH_CUDA(cudaEventCreate(&a));
+    GH_CUDA(cudaEventCreate(&b));
+    GH_CUDA(cudaEventRecord(a, ctx->stream));
+    probe_read_kernel<<<blocks, 512, 0, ctx->stream>>>((const float4*)buf, n4, reps, sink);
+    GH_CUDA(cudaGetLastError());
+    GH_CUDA(cudaEventRecord(b, ctx->stream));
+    GH_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    GH_CUDA(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->launches += 2;
+    *gbs = (double)(n4 * 16) * reps / (ms * 1e-3) / 1e9;
+    return GH_OK;
+}

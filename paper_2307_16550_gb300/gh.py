@@ -64,6 +64,7 @@ _SIGNATURES = {
     "gh_score_grid_noalloc": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, ctypes.POINTER(GhGrid),
                                      _P, _P, _P]),
     "gh_selftest_tcgen05": (_I32, [_P, _P, _P, _P, _I32, _I32]),
+    "gh_probe_read_bandwidth": (_I32, [_P, ctypes.c_int64, _I32, _PD]),
     "gh_set_timing": (_I32, [_P, _I32]),
     "gh_kernel_stats": (_I32, [_P, _I32, _PD, ctypes.POINTER(ctypes.c_int64)]),
     "gh_reset_stats": (_I32, [_P]),
@@ -255,6 +256,13 @@ class Context:
         self._check("gh_selftest_tcgen05", self._lib.gh_selftest_tcgen05(self.handle, _ptr(A), _ptr(B), _ptr(D),
                                                                          int(N), int(K)))
         return D
+
+    def gh_probe_read_bandwidth(self, nbytes, reps=20):
+        """Read bandwidth in GB/s over a device buffer of nbytes (L2 if small, DRAM if large)."""
+        g = ctypes.c_double(0)
+        self._check("gh_probe_read_bandwidth",
+                    self._lib.gh_probe_read_bandwidth(self.handle, int(nbytes), int(reps), ctypes.byref(g)))
+        return g.value
 
     def gh_set_timing(self, enable):
         """True: time every kernel class; False: none; a kind name, an int mask

@@ -104,5 +104,6 @@ def test_timing_and_launch_counts(ctx, torch_cuda):
     ms, launches = ctx.gh_kernel_stats("hop_score")
     ctx.gh_set_timing(False)
     assert launches == 2 and ms > 0
-    # per iteration: range FFT, Doppler FFT, scorer, argmax, 4 BOMP kernels; plus the table once
-    assert n1 - n0 == 1 + 2 * 8
+    # per iteration: range FFT (residual applied on load), Doppler FFT, scorer,
+    # selection (argmax + new atom), correlation (+ least squares); plus the table once
+    assert n1 - n0 == 1 + 2 * 5
