@@ -291,6 +291,12 @@ GH_API int gh_probe_read_bandwidth(gh_ctx* ctx, int64_t bytes, int32_t reps, dou
  * the context has launched.
  */
 GH_API int     gh_set_timing(gh_ctx* ctx, int32_t mask);
+/* gh_set_graphs(ctx, 1) (the default) lets gh_detect record its launch
+ * sequence into a CUDA graph on the second call with an unchanged
+ * configuration (method, radar, grid, positions, Q, K, measurement address,
+ * timing mask; device or pinned-host measurement) and replay it afterwards.
+ * The graph is dropped when any workspace buffer is reallocated. 0 disables. */
+GH_API int     gh_set_graphs(gh_ctx* ctx, int32_t enable);
 GH_API int     gh_kernel_stats(gh_ctx* ctx, int32_t kind, double* ms_total, int64_t* launches);
 GH_API int     gh_reset_stats(gh_ctx* ctx);
 GH_API int64_t gh_launch_count(const gh_ctx* ctx);

@@ -101,6 +101,8 @@ extern "C" void gh_destroy(gh_ctx* ctx) {
     if (!ctx) return;
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    gh_graph_invalidate(ctx);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     for (auto& t : ctx->pending) {
         cudaEventDestroy(t.start);
         cudaEventDestroy(t.stop);
@@ -113,9 +115,27 @@ extern "C" void gh_destroy(gh_ctx* ctx) {
     delete ctx;
 }
 
+static void graph_entry_free(GraphEntry& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    for (auto& t : g.events) {
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
+    g.events.clear();
+}
+
+void gh_graph_invalidate(gh_ctx* ctx) {
+    for (auto& g : ctx->graph_cache) graph_entry_free(g);
+    ctx->graph_cache.clear();
+    ctx->seen_keys.clear();
+}
+
 int gh_ws(gh_ctx* ctx, WsSlot slot, size_t bytes, void** p) {
     if (bytes == 0) bytes = 256;
     if (ctx->ws_bytes[slot] < bytes) {
+        if (ctx->capturing) return gh_fail(ctx, GH_ECUDA, "workspace growth during graph capture");
+        gh_graph_invalidate(ctx);
         if (ctx->ws[slot]) {
             GH_CUDA(cudaStreamSynchronize(ctx->stream));
             GH_CUDA(cudaFree(ctx->ws[slot]));
@@ -133,6 +153,8 @@ int gh_ws(gh_ctx* ctx, WsSlot slot, size_t bytes, void** p) {
 
 int gh_pinned(gh_ctx* ctx, size_t bytes, void** p) {
     if (ctx->pinned_bytes < bytes) {
+        if (ctx->capturing) return gh_fail(ctx, GH_ECUDA, "pinned buffer growth during graph capture");
+        gh_graph_invalidate(ctx);
         if (ctx->pinned) {
             GH_CUDA(cudaStreamSynchronize(ctx->stream));
             cudaFreeHost(ctx->pinned);
@@ -161,11 +183,17 @@ static cudaEvent_t take_event(gh_ctx* ctx) {
     return ev;
 }
 
+// While a graph is being captured the timing events become event-record
+// nodes of the graph (external records), so every replay times its kernels.
+static void record_event(gh_ctx* ctx, cudaEvent_t ev) {
+    cudaEventRecordWithFlags(ev, ctx->stream, ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+}
+
 void gh_launch_begin(gh_ctx* ctx, int kind, cudaEvent_t* start) {
     *start = nullptr;
     if (!((ctx->timing >> kind) & 1u)) return;
     *start = take_event(ctx);
-    if (*start) cudaEventRecord(*start, ctx->stream);
+    if (*start) record_event(ctx, *start);
 }
 
 int gh_launch_end(gh_ctx* ctx, int kind, cudaEvent_t start, const char* name) {
@@ -178,7 +206,7 @@ int gh_launch_end(gh_ctx* ctx, int kind, cudaEvent_t start, const char* name) {
     if (start) {
         cudaEvent_t stop = take_event(ctx);
         if (stop) {
-            cudaEventRecord(stop, ctx->stream);
+            record_event(ctx, stop);
             ctx->pending.push_back({kind, start, stop});
         } else {
             ctx->event_pool.push_back(start);
@@ -206,6 +234,17 @@ static int drain_timing(gh_ctx* ctx) {
 extern "C" int gh_set_timing(gh_ctx* ctx, int32_t mask) {
     if (!ctx) return GH_EINVAL;
     ctx->timing = (uint32_t)mask;
+    return GH_OK;
+}
+
+extern "C" int gh_set_graphs(gh_ctx* ctx, int32_t enable) {
+    if (!ctx) return GH_EINVAL;
+    ctx->graphs = enable != 0;
+    if (!ctx->graphs) {
+        DeviceGuard g(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        gh_graph_invalidate(ctx);
+    }
     return GH_OK;
 }
 
@@ -457,37 +496,35 @@ extern "C" int gh_direct_exact(gh_ctx* ctx, const gh_radar* radar, const double*
     return read_result(ctx, (const ArgResult*)res, best_cell, best_score);
 }
 
-extern "C" int gh_detect(gh_ctx* ctx, int32_t method, const gh_radar* radar, const double* tx_host,
-                         const double* rx_host, int32_t Q, const void* Y, const gh_grid* grid, int32_t K,
-                         int64_t* cells_host, float* scores_host, double* alpha_host) {
-    if (!ctx) return GH_EINVAL;
-    Dims d = {};
-    GH_TRY(gh_check_radar(ctx, radar, Q, &d));
-    GH_TRY(gh_check_grid(ctx, grid, &d));
-    GH_TRY(gh_check_positions(ctx, tx_host, rx_host, Q));
-    if (method != GH_HOP && method != GH_EXACT) return gh_fail(ctx, GH_EINVAL, "method %d unknown", method);
-    if (K < 1 || K > GH_MAX_K || K > d.ncells)
-        return gh_fail(ctx, GH_EINVAL, "K=%d outside [1, min(%d, ncells)]", K, GH_MAX_K);
-    if (!cells_host) return gh_fail(ctx, GH_EINVAL, "cells_host is NULL");
-    DeviceGuard dg(ctx->device);
+// The gh_detect launch sequence (from the staged measurement to the results
+// copied into pinned host memory); recorded into a CUDA graph when capturing.
+static int detect_sequence(gh_ctx* ctx, int32_t method, const Dims& d, const GeoParams& geo, const void* Y,
+                           int Ydev, int K, void** host_out) {
     const float2* Yd;
-    GH_TRY(stage_Y(ctx, d, Y, &Yd));
-    GeoParams geo;
-    gh_fill_geo(&geo, radar, tx_host, rx_host, Q, grid);
-
+    if (Ydev) {
+        Yd = (const float2*)Y;
+    } else {
+        size_t bytes = (size_t)d.Q * d.Mc * d.Ms * sizeof(float2);
+        void* p;
+        GH_TRY(gh_ws(ctx, WS_Y, bytes, &p));
+        GH_CUDA(cudaMemcpyAsync(p, Y, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        Yd = (const float2*)p;
+    }
     size_t mbytes = (size_t)d.Q * d.Nr * d.Nd * sizeof(float2);
     void *maps = nullptr, *table = nullptr, *res, *bws;
     GH_TRY(gh_ws(ctx, WS_RESULT, kResultSlots * sizeof(ArgResult), &res));
-    GH_TRY(gh_status_reset(ctx));
     GH_TRY(gh_ws(ctx, WS_BOMP, gh_bomp_ws_bytes(d, K), &bws));
-    GH_TRY(gh_bomp_reset(ctx, d, K, bws));
-    if (method == GH_HOP) {
-        GH_TRY(gh_ws(ctx, WS_MAPS, mbytes, &maps));
-        GH_TRY(build_table(ctx, d, geo, &table));
-    }
-    ArgResult* sel = (ArgResult*)res;  // sel[k] = selection of iteration k
-    int64_t* mask;                      // selected cells, excluded from later argmaxes
+    int64_t* mask;  // selected cells, excluded from later argmaxes
     GH_TRY(gh_ws(ctx, WS_DIAG, (size_t)GH_MAX_K * sizeof(int64_t) + 256, (void**)&mask));
+    if (method == GH_HOP) GH_TRY(gh_ws(ctx, WS_MAPS, mbytes, &maps));
+    size_t sel_bytes = (size_t)kResultSlots * sizeof(ArgResult);
+    size_t alpha_bytes = (size_t)K * d.Q * 2 * sizeof(double);
+    void* h;
+    GH_TRY(gh_pinned(ctx, sel_bytes + alpha_bytes, &h));
+    GH_TRY(gh_status_reset(ctx));
+    GH_TRY(gh_bomp_reset(ctx, d, K, bws));
+    if (method == GH_HOP) GH_TRY(build_table(ctx, d, geo, &table));
+    ArgResult* sel = (ArgResult*)res;  // sel[k] = selection of iteration k
     for (int k = 0; k < K; ++k) {
         // the residual of iteration k subtracts atoms 0..k-1 (amplitudes of the last solve)
         const Deflate df = gh_bomp_deflate(bws, d, K, k);
@@ -502,22 +539,162 @@ extern "C" int gh_detect(gh_ctx* ctx, int32_t method, const gh_radar* radar, con
         GH_TRY(gh_launch_bomp_select(ctx, d, geo, parts, nparts, sel, mask, k, K, bws));
         GH_TRY(gh_launch_bomp_corr(ctx, d, geo, Yd, k, K, bws));
     }
-    // results: selections, status word and the final amplitudes
-    size_t sel_bytes = (size_t)kResultSlots * sizeof(ArgResult);
-    size_t alpha_bytes = (size_t)K * d.Q * 2 * sizeof(double);
-    void* h;
-    GH_TRY(gh_pinned(ctx, sel_bytes + alpha_bytes, &h));
+    // results: selections, status word and the final amplitudes (double2 [K][Q]
+    // at the start of the BOMP workspace)
     GH_CUDA(cudaMemcpyAsync(h, sel, sel_bytes, cudaMemcpyDeviceToHost, ctx->stream));
-    // amplitudes live at the start of the BOMP workspace as double2 [K][Q]
     GH_CUDA(cudaMemcpyAsync((char*)h + sel_bytes, bws, alpha_bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    *host_out = h;
+    return GH_OK;
+}
+
+static void key_append(std::vector<unsigned char>& k, const void* p, size_t n) {
+    const unsigned char* b = (const unsigned char*)p;
+    k.insert(k.end(), b, b + n);
+}
+
+static GraphEntry* find_graph(gh_ctx* ctx, const std::vector<unsigned char>& key) {
+    for (auto& g : ctx->graph_cache)
+        if (g.key == key) {
+            g.used = ++ctx->graph_tick;
+            return &g;
+        }
+    return nullptr;
+}
+
+static bool seen_before(gh_ctx* ctx, const std::vector<unsigned char>& key) {
+    for (auto& k : ctx->seen_keys)
+        if (k == key) return true;
+    return false;
+}
+
+// Runs the launch sequence of one configuration (this call's results), then
+// records it into a new cache entry without running it again (evicting the
+// least recently used entry when the cache is full).
+static int record_graph(gh_ctx* ctx, const std::vector<unsigned char>& key, int32_t method, const Dims& d,
+                        const GeoParams& geo, const void* Y, int ydev, int K, void** h, GraphEntry** out) {
+    // the plain run makes sure every buffer of this configuration exists, so
+    // that the capture allocates nothing (a growth would drop all graphs)
+    GH_TRY(detect_sequence(ctx, method, d, geo, Y, ydev, K, h));
     GH_CUDA(cudaStreamSynchronize(ctx->stream));
+    if ((int)ctx->graph_cache.size() >= kMaxGraphs) {
+        size_t lru = 0;
+        for (size_t i = 1; i < ctx->graph_cache.size(); ++i)
+            if (ctx->graph_cache[i].used < ctx->graph_cache[lru].used) lru = i;
+        graph_entry_free(ctx->graph_cache[lru]);
+        ctx->graph_cache.erase(ctx->graph_cache.begin() + lru);
+    }
+    if (!ctx->capture_stream) GH_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+    const int64_t n0 = ctx->launches;
+    const size_t p0 = ctx->pending.size();
+    // recorded on a private stream, launched on the context's stream
+    cudaStream_t user_stream = ctx->stream;
+    GH_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeRelaxed));
+    ctx->stream = ctx->capture_stream;
+    ctx->capturing = true;
+    const int st = detect_sequence(ctx, method, d, geo, Y, ydev, K, h);
+    ctx->capturing = false;
+    ctx->stream = user_stream;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(ctx->capture_stream, &graph);
+    GraphEntry e;
+    e.key = key;
+    // events recorded while capturing are nodes of the graph now
+    e.events.assign(ctx->pending.begin() + p0, ctx->pending.end());
+    ctx->pending.resize(p0);
+    e.launches = ctx->launches - n0;
+    ctx->launches = n0;  // the capture ran nothing; replays count their kernels
+    int rc = st;
+    if (rc == GH_OK && ec != cudaSuccess) rc = gh_fail_cuda(ctx, ec, "cudaStreamEndCapture", __FILE__, __LINE__);
+    if (rc == GH_OK) {
+        const cudaError_t ei = cudaGraphInstantiate(&e.exec, graph, 0);
+        if (ei != cudaSuccess) {
+            e.exec = nullptr;
+            rc = gh_fail_cuda(ctx, ei, "cudaGraphInstantiate", __FILE__, __LINE__);
+        }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != GH_OK) {
+        graph_entry_free(e);
+        return rc;
+    }
+    e.used = ++ctx->graph_tick;
+    ctx->graph_cache.push_back(std::move(e));
+    *out = &ctx->graph_cache.back();
+    return GH_OK;
+}
+
+extern "C" int gh_detect(gh_ctx* ctx, int32_t method, const gh_radar* radar, const double* tx_host,
+                         const double* rx_host, int32_t Q, const void* Y, const gh_grid* grid, int32_t K,
+                         int64_t* cells_host, float* scores_host, double* alpha_host) {
+    if (!ctx) return GH_EINVAL;
+    Dims d = {};
+    GH_TRY(gh_check_radar(ctx, radar, Q, &d));
+    GH_TRY(gh_check_grid(ctx, grid, &d));
+    GH_TRY(gh_check_positions(ctx, tx_host, rx_host, Q));
+    if (method != GH_HOP && method != GH_EXACT) return gh_fail(ctx, GH_EINVAL, "method %d unknown", method);
+    if (K < 1 || K > GH_MAX_K || K > d.ncells)
+        return gh_fail(ctx, GH_EINVAL, "K=%d outside [1, min(%d, ncells)]", K, GH_MAX_K);
+    if (!cells_host) return gh_fail(ctx, GH_EINVAL, "cells_host is NULL");
+    if (!Y) return gh_fail(ctx, GH_EINVAL, "Y is NULL");
+    DeviceGuard dg(ctx->device);
+    GeoParams geo;
+    gh_fill_geo(&geo, radar, tx_host, rx_host, Q, grid);
+    const int ydev = gh_is_device_ptr(ctx, Y);
+    if (ydev < 0) return ydev;
+    bool pinned_host = false;
+    if (!ydev) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, Y) == cudaSuccess) pinned_host = at.type == cudaMemoryTypeHost;
+        cudaGetLastError();
+    }
+    // graphs replay fixed addresses: device or pinned-host measurements only
+    const bool graphable = ctx->graphs && (ydev || pinned_host);
+    std::vector<unsigned char> key;
+    if (graphable) {
+        key_append(key, &method, sizeof(method));
+        key_append(key, radar, sizeof(*radar));
+        key_append(key, grid, sizeof(*grid));
+        key_append(key, tx_host, 2 * sizeof(double));
+        key_append(key, rx_host, 2 * (size_t)Q * sizeof(double));
+        key_append(key, &Q, sizeof(Q));
+        key_append(key, &K, sizeof(K));
+        key_append(key, &Y, sizeof(Y));
+        key_append(key, &ctx->timing, sizeof(ctx->timing));
+    }
+    void* h = nullptr;
+    GraphEntry* g = graphable ? find_graph(ctx, key) : nullptr;
+    if (g) {
+        GH_CUDA(cudaGraphLaunch(g->exec, ctx->stream));
+        ctx->launches += g->launches;
+        h = ctx->pinned;
+    } else if (graphable && seen_before(ctx, key)) {
+        GraphEntry* rec;
+        GH_TRY(record_graph(ctx, key, method, d, geo, Y, ydev, K, &h, &rec));
+    } else {
+        GH_TRY(detect_sequence(ctx, method, d, geo, Y, ydev, K, &h));
+        if (graphable) {
+            if (ctx->seen_keys.size() >= 4 * kMaxGraphs) ctx->seen_keys.erase(ctx->seen_keys.begin());
+            ctx->seen_keys.push_back(key);
+        }
+    }
+    GH_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (g) {
+        for (auto& t : g->events) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess) {
+                ctx->ms[t.kind] += ms;
+                ctx->nlaunch[t.kind] += 1;
+            }
+        }
+    }
+    const size_t sel_bytes = (size_t)kResultSlots * sizeof(ArgResult);
     const ArgResult* hs = (const ArgResult*)h;
     GH_TRY(check_status(ctx, hs));
     for (int k = 0; k < K; ++k) {
         cells_host[k] = hs[k].cell;
         if (scores_host) scores_host[k] = hs[k].score;
     }
-    if (alpha_host) memcpy(alpha_host, (char*)h + sel_bytes, alpha_bytes);
+    if (alpha_host) memcpy(alpha_host, (char*)h + sel_bytes, (size_t)K * d.Q * 2 * sizeof(double));
     return GH_OK;
 }
 

@@ -38,6 +38,15 @@ struct TimedLaunch {
     cudaEvent_t start, stop;
 };
 
+struct GraphEntry {
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;             // kernels per replay
+    std::vector<TimedLaunch> events;  // timing event pairs recorded by each replay
+    uint64_t used = 0;                // last use, for eviction
+};
+constexpr int kMaxGraphs = 8;
+
 struct gh_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -55,6 +64,17 @@ struct gh_ctx {
     int tw_n[2] = {0, 0};
 
     uint32_t timing = 0;  // bit mask over GH_K_* classes
+
+    // CUDA graphs of the gh_detect launch sequence, one per configuration
+    // (recorded on the second call with that configuration, replayed
+    // afterwards; all dropped whenever a workspace buffer moves or the
+    // twiddle tables change).
+    bool graphs = true;
+    bool capturing = false;
+    cudaStream_t capture_stream = nullptr;  // records graphs (the legacy stream cannot be captured)
+    std::vector<GraphEntry> graph_cache;
+    std::vector<std::vector<unsigned char>> seen_keys;  // configurations met once
+    uint64_t graph_tick = 0;
     std::vector<TimedLaunch> pending;
     std::vector<cudaEvent_t> event_pool;
     double ms[GH_K_COUNT] = {0};
@@ -77,6 +97,9 @@ int gh_fail(gh_ctx* ctx, int status, const char* fmt, ...);
         int s_ = (expr);             \
         if (s_ != GH_OK) return s_;  \
     } while (0)
+
+// Drops the cached gh_detect graph (its kernels hold workspace pointers).
+void gh_graph_invalidate(gh_ctx* ctx);
 
 // Grow-only workspace slot; returns GH_OK and sets *p.
 int gh_ws(gh_ctx* ctx, WsSlot slot, size_t bytes, void** p);

@@ -173,6 +173,8 @@ int ensure_twiddles(gh_ctx* ctx, int Nr, int Nd, const float2** twr, const float
     void* p;
     GH_TRY(gh_ws(ctx, WS_TWIDDLE, bytes, &p));
     if (ctx->tw_n[0] != Nr || ctx->tw_n[1] != Nd) {
+        if (ctx->capturing) return gh_fail(ctx, GH_ECUDA, "twiddle upload during graph capture");
+        gh_graph_invalidate(ctx);  // cached graphs read the old tables
         std::vector<float2> h(nr + nd);
         const double two_pi = 6.283185307179586476925286766559;
         for (int t = 0; t < nr; ++t) {

@@ -66,6 +66,7 @@ _SIGNATURES = {
     "gh_selftest_tcgen05": (_I32, [_P, _P, _P, _P, _I32, _I32]),
     "gh_probe_read_bandwidth": (_I32, [_P, ctypes.c_int64, _I32, _PD]),
     "gh_set_timing": (_I32, [_P, _I32]),
+    "gh_set_graphs": (_I32, [_P, _I32]),
     "gh_kernel_stats": (_I32, [_P, _I32, _PD, ctypes.POINTER(ctypes.c_int64)]),
     "gh_reset_stats": (_I32, [_P]),
     "gh_launch_count": (ctypes.c_int64, [_P]),
@@ -280,6 +281,9 @@ class Context:
             for k in enable:
                 mask |= 1 << KERNEL_KINDS[k]
         self._check("gh_set_timing", self._lib.gh_set_timing(self.handle, int(mask)))
+
+    def gh_set_graphs(self, enable: bool):
+        self._check("gh_set_graphs", self._lib.gh_set_graphs(self.handle, int(bool(enable))))
 
     def gh_kernel_stats(self, kind):
         ms = ctypes.c_double(0)
