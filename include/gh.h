@@ -277,7 +277,8 @@ GH_API int gh_selftest_tcgen05(gh_ctx* ctx, const float* A_host, const float* B_
  * the paper): streams 16-byte loads over a device buffer of `bytes` bytes
  * (1 MiB .. 64 GiB), `reps` times (1 .. 1000), and returns GB/s in *gbs. A
  * buffer well below the L2 size measures L2-to-SM bandwidth; one well above it
- * measures DRAM read bandwidth. Allocates its buffer in the context workspace.
+ * measures DRAM read bandwidth. Allocates its buffer in the context workspace
+ * (a growth drops the context's recorded gh_detect graphs).
  */
 GH_API int gh_probe_read_bandwidth(gh_ctx* ctx, int64_t bytes, int32_t reps, double* gbs);
 
