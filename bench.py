@@ -253,6 +253,62 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def precision_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args):
+    """Precision-at-scale frame (Q = 8, Ms = 512 x Mc = 256, five targets at
+    SNR 5 dB, grid 256 x 256 x 64 x 64 = 268M cells, K = 5): hopping detection
+    with float32, float16 and bfloat16 maps, and the exact direct scores of a
+    64 x 64 x 32 x 32 sub-grid around the first target. Device-resident frame,
+    L2 flushed before every step."""
+    sc = scenes.precision_scene(1 + rank)
+    K = 5
+    noise = torch.from_numpy(sc.noise.astype(np.complex64)).to(device)
+    Y = ctx.synth(sc.radar, sc.tx, sc.rx, sc.targets, sc.alpha, noise)
+    evals = K * sc.grid.ncells * sc.Q
+
+    def timed(fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        out = None
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            out = fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(device)
+        return sum(a.elapsed_time(b) for a, b in ev) / steps, out
+
+    res = {"workload": "precision-at-scale frame: Q=8 RX, Ms=512 x Mc=256, 5 Rayleigh targets at SNR 5 dB, "
+                       "grid 256x256x64x64 (268M cells), 4x-padded maps, BOMP K=5",
+           "unit": UNIT, "maps": {}}
+    cells64 = None
+    for name, mt in (("c64", gh.GH_C64), ("c16", gh.GH_C16), ("bf16", gh.GH_CBF16)):
+        ctx.gh_set_detect_maps(mt)
+        ctx.gh_set_timing("hop_score")
+        det = lambda: ctx.gh_detect(gh.GH_HOP, sc.radar, sc.tx, sc.rx, sc.Q, Y, sc.grid, K)
+        for _ in range(args.warmup):
+            det()
+        ctx.gh_reset_stats()
+        ms, (cells, scores, _) = timed(det, args.steps)
+        hs_ms, hs_n = ctx.gh_kernel_stats("hop_score")
+        ctx.gh_set_timing(False)
+        if cells64 is None:
+            cells64 = cells
+        res["maps"][name] = {"value": evals / (ms * 1e-3), "ms_per_step": ms,
+                             "hop_score_ms": hs_ms / max(hs_n, 1), "cells": cells.tolist(),
+                             "cells_equal_c64": bool(np.array_equal(cells, cells64))}
+    ctx.gh_set_detect_maps(gh.GH_C64)
+    t = sc.targets[0]
+    sub = scenes.Grid.from_bounds((t[0] - 6.4, t[1] - 6.4, -15.0, -15.0), (t[0] + 6.4, t[1] + 6.4, 15.0, 15.0),
+                                  (64, 64, 32, 32))
+    ex = lambda: ctx.gh_direct_exact(sc.radar, sc.tx, sc.rx, sc.Q, Y, sub)
+    for _ in range(args.warmup):
+        ex()
+    ms, _ = timed(ex, args.steps)
+    res["exact_subgrid"] = {"value": sub.ncells * sc.Q / (ms * 1e-3), "ms_per_step": ms,
+                            "grid": list(sub.n)}
+    res["error_vs_oracle"] = "tests/test_gpu_precision.py (per score and per detected cell, printed with -s)"
+    return res
+
+
 def run_ours(args):
     import torch
 
@@ -328,6 +384,7 @@ def run_ours(args):
     torch.cuda.synchronize(device)
     _barrier(world)
     wall = time.perf_counter() - t_wall
+    prec = None if args.no_precision else precision_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args)
     clk = clocks.stop()
 
     value, hop_ms, _ = aggregate(world, hop_ms, evals * args.steps, device)
@@ -388,7 +445,7 @@ def run_ours(args):
                "gpu_launches": int(hop_launches + ex_launches + e2e_launches),
                "gpu_launches_per_step": {"hop": hop_launches // args.steps, "exact": ex_launches // args.steps},
                "launch": "CUDA graph of the detect sequence, replayed every step",
-               "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+               "roofline": roof, "cpu_baseline": cpu, "precision": prec, "clocks": clk,
                "wall_s_timed_region": wall}
         print(json.dumps(out), flush=True)
     ctx.close()
@@ -405,6 +462,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true", help="skip the precision-at-scale leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -61,8 +61,13 @@ extern "C" {
 #define GH_ETIMEOUT (-4)  /* a bounded device-side wait gave up                */
 #define GH_ENOTSUP  (-5)  /* valid but unsupported combination                 */
 
-/* Map storage types (gh_make_maps, gh_score_grid). */
+/* Map storage types (gh_make_maps, gh_score_grid, gh_set_detect_maps).
+ * The reduced-precision types store 2^-s times each map value, with
+ * s = log2(Ms) + log2(Mc) (a unit-amplitude on-bin tone becomes 1), so that
+ * the float16 range holds every map; gh_score_grid undoes the scale exactly. */
 #define GH_C64      0     /* complex float32 (8 bytes per bin)                 */
+#define GH_C16      1     /* complex float16, (re, im) pair (4 bytes per bin)  */
+#define GH_CBF16    2     /* complex bfloat16, (re, im) pair (4 bytes per bin) */
 
 /* Scoring methods (gh_detect). */
 #define GH_HOP      0     /* grid hopping (Sec. IV)                            */
@@ -129,7 +134,10 @@ GH_API const char* gh_last_error(const gh_ctx* ctx);
  * atom exp(j 2 pi r (m - (Ms-1)/2)), whose Gram is real (used by the polar
  * interpolation of gh_score_grid).
  *   Y_dev    : device, complex float32 [Q][Mc][Ms]
- *   maps_dev : device, complex float32 [Q][Nr][Nd] (written; map_dtype GH_C64)
+ *   maps_dev : device, [Q][Nr][Nd] bins of type map_dtype (written): complex
+ *              float32 (GH_C64), or 2^-s times the values rounded to
+ *              nearest-even complex float16 (GH_C16) / bfloat16 (GH_CBF16)
+ *              from the float32 transform
  * No host synchronisation.
  */
 GH_API int gh_make_maps(gh_ctx* ctx, const gh_radar* radar, int32_t Q,
@@ -147,7 +155,9 @@ GH_API int gh_make_maps(gh_ctx* ctx, const gh_radar* radar, int32_t Q,
  * centring phase of the unwrapped index.
  *   tx_host      : host, double[2]
  *   rx_host      : host, double[2*Q]
- *   maps_dev     : device, from gh_make_maps
+ *   maps_dev     : device, from gh_make_maps with the same map_dtype
+ *                  (reduced-precision maps are read as float32 values and
+ *                  accumulated in float32)
  *   scores_dev   : device float[ncells] or NULL (argmax only)
  *   best_cell    : host int64, argmax (ties: smallest index); may be NULL
  *   best_score   : host float, its score; may be NULL
@@ -193,6 +203,12 @@ GH_API int gh_direct_exact(gh_ctx* ctx, const gh_radar* radar, const double* tx_
  * All K iterations run on the device without host round trips; the stream is
  * synchronised once at the end. 1 <= K <= min(GH_MAX_K, ncells).
  */
+/*
+ * gh_set_detect_maps - storage type (GH_C64 default, GH_C16, GH_CBF16) of the
+ * range-Doppler maps gh_detect makes on the context for method GH_HOP.
+ */
+GH_API int gh_set_detect_maps(gh_ctx* ctx, int32_t map_dtype);
+
 GH_API int gh_detect(gh_ctx* ctx, int32_t method, const gh_radar* radar,
               const double* tx_host, const double* rx_host, int32_t Q,
               const void* Y_host_or_dev, const gh_grid* grid, int32_t K,

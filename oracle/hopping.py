@@ -146,3 +146,37 @@ def argmax_cell(scores):
     """Linear index of the largest score; ties go to the smallest index."""
     flat = np.asarray(scores).reshape(-1)
     return int(np.argmax(flat))
+
+
+def hop_quantization_bound(Z, radar, tx, rx, grid, kind, xy_rows=None):
+    """Bound on |S_q - S| per cell when every map part is stored in the
+    reduced-precision format ``kind`` (``maps.quantize_maps``) instead of exactly.
+
+    Each stored part is within u |x| + eta of its exact value
+    (``maps.quantization_error_bound``), so a complex bin moves by at most
+    e_bin = u |Z| + sqrt(2) eta (Minkowski) and the interpolated correlation by
+    e_q = sum_k |c_k| e_bin(k); then | |s + d|^2 - |s|^2 | <= (2|s| + e_q) e_q,
+    summed over the receivers. Returns float64 of the shape of ``hop_scores``."""
+    from .maps import map_scale_log2, quantization_error_bound
+    u, eta = quantization_error_bound(kind, map_scale_log2(radar.Ms, radar.Mc))
+    table = coord_table(radar, tx, rx, grid)
+    _, _, VX, VY = grid_axes(grid)
+    Q, Nd, Nr = Z.shape
+    nx, ny, nvx, nvy = grid.n
+    rows = range(nx) if xy_rows is None else xy_rows
+    out = np.zeros((len(rows), ny, nvx, nvy))
+    A = np.abs(Z)
+    iy = np.arange(ny)
+    for r, ixv in enumerate(rows):
+        ix = np.full(ny, ixv)
+        s = hop_correlations(Z, radar, tx, rx, grid, ix, iy, table)
+        for q in range(Q):
+            i0 = table["i"][ix, iy, q]
+            c = np.abs(table["c"][ix, iy, q])
+            j = doppler_bin(table["wx"][ix, iy, q][:, None, None], table["wy"][ix, iy, q][:, None, None],
+                            VX[None, :, None], VY[None, None, :], radar)
+            e = np.zeros((ny, nvx, nvy))
+            for kk, k in enumerate((-1, 0, 1)):
+                e += c[:, kk][:, None, None] * (u * A[q][j, np.mod(i0 + k, Nr)[:, None, None]] + np.sqrt(2.0) * eta)
+            out[r] += (2.0 * np.abs(s[:, q]) + e) * e
+    return out

@@ -52,3 +52,55 @@ def centred_maps(Y, pad):
     Z = rd_maps(Y, pad)  # (Q, Nd, Nr)
     ph = centring_phase(np.arange(Nr), Nr, Ms)
     return np.ascontiguousarray(np.transpose(Z * ph[None, None, :], (0, 2, 1)))
+
+
+# ---------------------------------------------------------------------------
+# Reduced-precision map storage (the precision mode of the CUDA path; no
+# counterpart in the paper). A stored bin is 2^-s times the centred map value,
+# s = log2(Ms) + log2(Mc), with its real and imaginary parts each rounded to
+# nearest, ties to even, in IEEE binary16 ("f16": 11 significant bits,
+# exponents -14..15, subnormal spacing 2^-24) or bfloat16 ("bf16": 8
+# significant bits, the binary32 exponent range).
+# ---------------------------------------------------------------------------
+FORMATS = {"f16": (11, -14, 15), "bf16": (8, -126, 127)}  # significant bits, min / max exponent
+
+
+def map_scale_log2(Ms, Mc):
+    """s with 2^s = Ms * Mc (both powers of two)."""
+    return int(round(np.log2(Ms))) + int(round(np.log2(Mc)))
+
+
+def round_format(x, kind):
+    """Round float64 values to the nearest value of the format, ties to even.
+
+    A finite value x = m 2^e (1 <= |m| < 2) keeps p significant bits for
+    e >= emin, i.e. x is rounded to a multiple of 2^(max(e, emin) - p + 1);
+    below 2^emin the spacing stays 2^(emin - p + 1) (subnormals). Values
+    beyond the largest finite value are an error here (the storage scale is
+    chosen so that maps never reach it)."""
+    p, emin, emax = FORMATS[kind]
+    x = np.asarray(x, dtype=np.float64)
+    mant, ex = np.frexp(x)                 # x = mant * 2^ex, 0.5 <= |mant| < 1
+    e = np.maximum(ex - 1, emin)           # exponent of the leading bit, clamped
+    quantum = np.ldexp(1.0, e - p + 1)
+    y = np.rint(x / quantum) * quantum     # np.rint rounds half to even; x / quantum is exact
+    big = np.ldexp(2.0 - 2.0 ** (1 - p), emax)
+    if np.any(np.abs(y) > big):
+        raise OverflowError(f"value beyond the {kind} range")
+    return y
+
+
+def quantize_maps(Zc, kind, s):
+    """Centred maps as stored and read back: 2^s * round(2^-s Zc), parts rounded separately."""
+    scale = np.ldexp(1.0, -s)
+    re = round_format(Zc.real * scale, kind)
+    im = round_format(Zc.imag * scale, kind)
+    return (re + 1j * im) / scale
+
+
+def quantization_error_bound(kind, s):
+    """(u, eta) with |q(x) - x| <= u |x| + eta for every stored part x (before
+    the 2^s scale-back): u = 2^-p (half an ulp relative), eta = half the
+    subnormal spacing, times 2^s."""
+    p, emin, _ = FORMATS[kind]
+    return 2.0 ** -p, np.ldexp(1.0, emin - p) * np.ldexp(1.0, s)

@@ -237,6 +237,13 @@ extern "C" int gh_set_timing(gh_ctx* ctx, int32_t mask) {
     return GH_OK;
 }
 
+extern "C" int gh_set_detect_maps(gh_ctx* ctx, int32_t map_dtype) {
+    if (!ctx) return GH_EINVAL;
+    if (!gh_map_dtype_ok(map_dtype)) return gh_fail(ctx, GH_EINVAL, "map_dtype %d unknown", map_dtype);
+    ctx->detect_maps = map_dtype;
+    return GH_OK;
+}
+
 extern "C" int gh_set_graphs(gh_ctx* ctx, int32_t enable) {
     if (!ctx) return GH_EINVAL;
     ctx->graphs = enable != 0;
@@ -425,14 +432,14 @@ extern "C" int gh_make_maps(gh_ctx* ctx, const gh_radar* radar, int32_t Q, const
     Dims d = {};
     GH_TRY(gh_check_radar(ctx, radar, Q, &d));
     if (!Y_dev || !maps_dev) return gh_fail(ctx, GH_EINVAL, "Y_dev or maps_dev is NULL");
-    if (map_dtype != GH_C64) return gh_fail(ctx, GH_ENOTSUP, "map_dtype %d not supported", map_dtype);
+    if (!gh_map_dtype_ok(map_dtype)) return gh_fail(ctx, GH_EINVAL, "map_dtype %d unknown", map_dtype);
     DeviceGuard g(ctx->device);
     int dv = gh_is_device_ptr(ctx, Y_dev);
     if (dv < 0) return dv;
     int dm = gh_is_device_ptr(ctx, maps_dev);
     if (dm < 0) return dm;
     if (!dv || !dm) return gh_fail(ctx, GH_EINVAL, "Y_dev and maps_dev must be device memory");
-    return gh_launch_maps(ctx, d, (const float2*)Y_dev, nullptr, (float2*)maps_dev);
+    return gh_launch_maps(ctx, d, (const float2*)Y_dev, nullptr, maps_dev, map_dtype);
 }
 
 static int build_table(gh_ctx* ctx, const Dims& d, const GeoParams& geo, void** table) {
@@ -449,7 +456,7 @@ extern "C" int gh_score_grid(gh_ctx* ctx, const gh_radar* radar, const double* t
     GH_TRY(gh_check_grid(ctx, grid, &d));
     GH_TRY(gh_check_positions(ctx, tx_host, rx_host, Q));
     if (!maps_dev) return gh_fail(ctx, GH_EINVAL, "maps_dev is NULL");
-    if (map_dtype != GH_C64) return gh_fail(ctx, GH_ENOTSUP, "map_dtype %d not supported", map_dtype);
+    if (!gh_map_dtype_ok(map_dtype)) return gh_fail(ctx, GH_EINVAL, "map_dtype %d unknown", map_dtype);
     DeviceGuard dg(ctx->device);
     int dm = gh_is_device_ptr(ctx, maps_dev);
     if (dm < 0) return dm;
@@ -466,7 +473,7 @@ extern "C" int gh_score_grid(gh_ctx* ctx, const gh_radar* radar, const double* t
     void* res;
     GH_TRY(gh_ws(ctx, WS_RESULT, kResultSlots * sizeof(ArgResult), &res));
     GH_TRY(gh_status_reset(ctx));
-    GH_TRY(gh_launch_hop(ctx, d, geo, (const float2*)maps_dev, table, scores_dev, nullptr, 0, (ArgResult*)res));
+    GH_TRY(gh_launch_hop(ctx, d, geo, maps_dev, map_dtype, table, scores_dev, nullptr, 0, (ArgResult*)res));
     if (!best_cell && !best_score) return GH_OK;
     return read_result(ctx, (const ArgResult*)res, best_cell, best_score);
 }
@@ -510,7 +517,7 @@ static int detect_sequence(gh_ctx* ctx, int32_t method, const Dims& d, const Geo
         GH_CUDA(cudaMemcpyAsync(p, Y, bytes, cudaMemcpyHostToDevice, ctx->stream));
         Yd = (const float2*)p;
     }
-    size_t mbytes = (size_t)d.Q * d.Nr * d.Nd * sizeof(float2);
+    size_t mbytes = (size_t)d.Q * d.Nr * d.Nd * gh_map_bin_bytes(ctx->detect_maps);
     void *maps = nullptr, *table = nullptr, *res, *bws;
     GH_TRY(gh_ws(ctx, WS_RESULT, kResultSlots * sizeof(ArgResult), &res));
     GH_TRY(gh_ws(ctx, WS_BOMP, gh_bomp_ws_bytes(d, K), &bws));
@@ -531,8 +538,9 @@ static int detect_sequence(gh_ctx* ctx, int32_t method, const Dims& d, const Geo
         ArgPartial* parts;
         int nparts;
         if (method == GH_HOP) {
-            GH_TRY(gh_launch_maps(ctx, d, Yd, &df, (float2*)maps));
-            GH_TRY(gh_launch_hop_parts(ctx, d, geo, (const float2*)maps, table, nullptr, mask, k, &parts, &nparts));
+            GH_TRY(gh_launch_maps(ctx, d, Yd, &df, maps, ctx->detect_maps));
+            GH_TRY(gh_launch_hop_parts(ctx, d, geo, maps, ctx->detect_maps, table, nullptr, mask, k, &parts,
+                                       &nparts));
         } else {
             GH_TRY(gh_launch_exact_parts(ctx, d, geo, Yd, &df, nullptr, mask, k, &parts, &nparts));
         }
@@ -660,6 +668,7 @@ extern "C" int gh_detect(gh_ctx* ctx, int32_t method, const gh_radar* radar, con
         key_append(key, &K, sizeof(K));
         key_append(key, &Y, sizeof(Y));
         key_append(key, &ctx->timing, sizeof(ctx->timing));
+        key_append(key, &ctx->detect_maps, sizeof(ctx->detect_maps));
     }
     void* h = nullptr;
     GraphEntry* g = graphable ? find_graph(ctx, key) : nullptr;

@@ -24,6 +24,8 @@
 //   map rows overlap in L1. Scores (optional) are written coalesced; the best
 //   (score, cell) is reduced per lane, then with warp shuffles and once per
 //   CTA (ties: smallest cell index).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "gh_internal.cuh"
@@ -139,6 +141,7 @@ __global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__
 
 struct HopParams {
     int Q, Nr, Nd, nvx, nvy;
+    float cscale;         // 2^s of reduced-precision maps (folded into the polar coefficients)
     int NB, SA;           // lane mapping: b = lane % NB (stride NB), a = lane / NB (stride SA)
     uint32_t tol2;        // 2 * tol
     long long nxy, nv;
@@ -162,9 +165,29 @@ __device__ __forceinline__ void better(float s, long long c, float& bs, long lon
     }
 }
 
-// AC: velocity cells per lane per pass (along vx, stride SA).
-template <int AC>
-__global__ void __launch_bounds__(256, GH_HOP_MINB) hop_score_kernel(const float2* __restrict__ maps,
+// Two consecutive map bins (an even bin and the next) of a map row, as float32
+// (re0, im0, re1, im1), from storage type MT.
+template <int MT>
+__device__ __forceinline__ float4 load_pair(const void* row, int jh) {
+    if constexpr (MT == GH_C64) {
+        return __ldg((const float4*)row + jh);
+    } else {
+        const uint2 w = __ldg((const uint2*)row + jh);
+        float2 a, b;
+        if constexpr (MT == GH_C16) {
+            a = __half22float2(*reinterpret_cast<const __half2*>(&w.x));
+            b = __half22float2(*reinterpret_cast<const __half2*>(&w.y));
+        } else {
+            a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w.x));
+            b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w.y));
+        }
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+
+// AC: velocity cells per lane per pass (along vx, stride SA); MT: map storage type.
+template <int AC, int MT>
+__global__ void __launch_bounds__(256, GH_HOP_MINB) hop_score_kernel(const void* __restrict__ maps,
                                                            const HopEntry* __restrict__ table, HopParams p,
                                                            float* __restrict__ scores,
                                                            const int64_t* __restrict__ mask, int nmask,
@@ -200,11 +223,12 @@ __global__ void __launch_bounds__(256, GH_HOP_MINB) hop_score_kernel(const float
         for (int q = 0; q < p.Q; ++q) {
             const HopEntry& eq = E[q];
             const int j_ref = eq.j_ref, npair = eq.npair;
-            const float c0 = eq.cs[0], c1 = eq.cs[1], c2 = eq.cs[2];
+            const float c0 = eq.cs[0] * p.cscale, c1 = eq.cs[1] * p.cscale, c2 = eq.cs[2] * p.cscale;
             const size_t qb = (size_t)q * p.Nr;
-            const float4* r0 = (const float4*)(maps + (qb + eq.row[0]) * p.Nd);
-            const float4* r1 = (const float4*)(maps + (qb + eq.row[1]) * p.Nd);
-            const float4* r2 = (const float4*)(maps + (qb + eq.row[2]) * p.Nd);
+            constexpr size_t BB = MT == GH_C64 ? 8 : 4;  // bytes per bin
+            const char* r0 = (const char*)maps + (qb + eq.row[0]) * p.Nd * BB;
+            const char* r1 = (const char*)maps + (qb + eq.row[1]) * p.Nd * BB;
+            const char* r2 = (const char*)maps + (qb + eq.row[2]) * p.Nd * BB;
             float* Pq = P + (size_t)q * p.Nd;
             constexpr int U = GH_HOP_U;  // row loads in flight per lane
             for (int pp0 = 0; pp0 < npair; pp0 += 32 * U) {
@@ -214,9 +238,9 @@ __global__ void __launch_bounds__(256, GH_HOP_MINB) hop_score_kernel(const float
                     const int pp = pp0 + lane + 32 * u;
                     if (pp < npair) {
                         const int jh = ((j_ref + 2 * pp) & ndm) >> 1;  // pair of absolute bins
-                        z0[u] = __ldg(r0 + jh);
-                        z1[u] = __ldg(r1 + jh);
-                        z2[u] = __ldg(r2 + jh);
+                        z0[u] = load_pair<MT>(r0, jh);
+                        z1[u] = load_pair<MT>(r1, jh);
+                        z2[u] = load_pair<MT>(r2, jh);
                     }
                 }
 #pragma unroll
@@ -355,6 +379,7 @@ HopParams hop_params(const Dims& d, const GeoParams& g) {
     hp.Nd = d.Nd;
     hp.nvx = d.nvx;
     hp.nvy = d.nvy;
+    hp.cscale = 1.0f;
     hp.NB = d.nvy < 32 ? d.nvy : 32;
     hp.SA = 32 / hp.NB;
     hp.tol2 = 2u * hop_tol(d.nvx, d.nvy);
@@ -373,8 +398,8 @@ CoordParams coord_params(const Dims& d);
 
 // Launch of the scorer (shared by the context path and the allocation-free
 // entry point). Returns the number of CTAs (partials) in *nparts.
-template <int AC>
-int hop_launch_t(cudaStream_t stream, const Dims& d, HopParams hp, const float2* maps, const HopEntry* table,
+template <int AC, int MT>
+int hop_launch_t(cudaStream_t stream, const Dims& d, HopParams hp, const void* maps, const HopEntry* table,
                  float* scores, const int64_t* mask, int nmask, ArgPartial* parts, long long max_ctas, int num_sms,
                  size_t smem_optin, long long* nparts) {
     const size_t per_warp =
@@ -384,13 +409,13 @@ int hop_launch_t(cudaStream_t stream, const Dims& d, HopParams hp, const float2*
     if (W > 8) W = 8;
     if (W < 1) W = 1;
     const size_t smem = per_warp * W;
-    if (cudaFuncSetAttribute(hop_score_kernel<AC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (cudaFuncSetAttribute(hop_score_kernel<AC, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||
-        cudaFuncSetAttribute(hop_score_kernel<AC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(hop_score_kernel<AC, MT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
         return GH_ECUDA;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_score_kernel<AC>, 32 * W, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_score_kernel<AC, MT>, 32 * W, smem) != cudaSuccess)
         return GH_ECUDA;
     if (per_sm < 1) per_sm = 1;
     long long ctas = (long long)num_sms * per_sm;
@@ -398,27 +423,42 @@ int hop_launch_t(cudaStream_t stream, const Dims& d, HopParams hp, const float2*
     if (ctas > d.nxy) ctas = d.nxy;
     hp.xy_per_cta = (d.nxy + ctas - 1) / ctas;
     ctas = (d.nxy + hp.xy_per_cta - 1) / hp.xy_per_cta;
-    hop_score_kernel<AC><<<(unsigned)ctas, 32 * W, smem, stream>>>(maps, table, hp, scores, mask, nmask, parts);
+    hop_score_kernel<AC, MT><<<(unsigned)ctas, 32 * W, smem, stream>>>(maps, table, hp, scores, mask, nmask, parts);
     *nparts = ctas;
     return cudaGetLastError() == cudaSuccess ? GH_OK : GH_ECUDA;
 }
 
-int hop_launch(cudaStream_t stream, const Dims& d, const HopParams& hp, const float2* maps, const HopEntry* table,
-               float* scores, const int64_t* mask, int nmask, ArgPartial* parts, long long max_ctas, int num_sms,
-               size_t smem_optin, long long* nparts) {
+template <int MT>
+int hop_launch_mt(cudaStream_t stream, const Dims& d, const HopParams& hp, const void* maps, const HopEntry* table,
+                  float* scores, const int64_t* mask, int nmask, ArgPartial* parts, long long max_ctas, int num_sms,
+                  size_t smem_optin, long long* nparts) {
     const int need = (d.nvx + hp.SA - 1) / hp.SA;
-#define GH_HOP_CASE(N)                                                                                       \
-    if (need <= N)                                                                                           \
-        return hop_launch_t<N>(stream, d, hp, maps, table, scores, mask, nmask, parts, max_ctas, num_sms, \
-                               smem_optin, nparts);
+#define GH_HOP_CASE(N)                                                                                           \
+    if (need <= N)                                                                                               \
+        return hop_launch_t<N, MT>(stream, d, hp, maps, table, scores, mask, nmask, parts, max_ctas, num_sms, \
+                                   smem_optin, nparts);
     GH_HOP_CASE(1)
     GH_HOP_CASE(2)
     GH_HOP_CASE(4)
     GH_HOP_CASE(8)
     GH_HOP_CASE(16)
 #undef GH_HOP_CASE
-    return hop_launch_t<32>(stream, d, hp, maps, table, scores, mask, nmask, parts, max_ctas, num_sms, smem_optin,
-                            nparts);
+    return hop_launch_t<32, MT>(stream, d, hp, maps, table, scores, mask, nmask, parts, max_ctas, num_sms,
+                                smem_optin, nparts);
+}
+
+int hop_launch(cudaStream_t stream, const Dims& d, HopParams hp, const void* maps, int map_dtype,
+               const HopEntry* table, float* scores, const int64_t* mask, int nmask, ArgPartial* parts,
+               long long max_ctas, int num_sms, size_t smem_optin, long long* nparts) {
+    hp.cscale = ldexpf(1.0f, gh_map_scale_log2(d, map_dtype));
+    if (map_dtype == GH_C16)
+        return hop_launch_mt<GH_C16>(stream, d, hp, maps, table, scores, mask, nmask, parts, max_ctas, num_sms,
+                                     smem_optin, nparts);
+    if (map_dtype == GH_CBF16)
+        return hop_launch_mt<GH_CBF16>(stream, d, hp, maps, table, scores, mask, nmask, parts, max_ctas, num_sms,
+                                       smem_optin, nparts);
+    return hop_launch_mt<GH_C64>(stream, d, hp, maps, table, scores, mask, nmask, parts, max_ctas, num_sms,
+                                 smem_optin, nparts);
 }
 
 double dirichlet_closed(double f, int M) {
@@ -463,8 +503,9 @@ int gh_launch_argmax_finalize(gh_ctx* ctx, const ArgPartial* parts, int nparts, 
     return gh_launch_end(ctx, GH_K_ARGMAX, ev, "argmax_finalize_kernel");
 }
 
-int gh_launch_hop_parts(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* maps, const void* table,
-                        float* scores, const int64_t* mask, int nmask, ArgPartial** parts_out, int* nparts_out) {
+int gh_launch_hop_parts(gh_ctx* ctx, const Dims& d, const GeoParams& g, const void* maps, int map_dtype,
+                        const void* table, float* scores, const int64_t* mask, int nmask, ArgPartial** parts_out,
+                        int* nparts_out) {
     const HopParams hp = hop_params(d, g);
     const long long max_ctas = (long long)ctx->num_sms * 32;
     void* parts;
@@ -472,7 +513,7 @@ int gh_launch_hop_parts(gh_ctx* ctx, const Dims& d, const GeoParams& g, const fl
     cudaEvent_t ev;
     long long nparts = 0;
     gh_launch_begin(ctx, GH_K_HOP_SCORE, &ev);
-    const int st = hop_launch(ctx->stream, d, hp, maps, (const HopEntry*)table, scores, mask, nmask,
+    const int st = hop_launch(ctx->stream, d, hp, maps, map_dtype, (const HopEntry*)table, scores, mask, nmask,
                               (ArgPartial*)parts, max_ctas, ctx->num_sms, ctx->smem_optin, &nparts);
     if (st == GH_ENOTSUP) return gh_fail(ctx, GH_ENOTSUP, "hop scorer: Q*Nd*4 bytes exceed shared memory");
     GH_TRY(gh_launch_end(ctx, GH_K_HOP_SCORE, ev, "hop_score_kernel"));
@@ -482,11 +523,11 @@ int gh_launch_hop_parts(gh_ctx* ctx, const Dims& d, const GeoParams& g, const fl
     return GH_OK;
 }
 
-int gh_launch_hop(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* maps, const void* table,
-                  float* scores, const int64_t* mask, int nmask, ArgResult* result) {
+int gh_launch_hop(gh_ctx* ctx, const Dims& d, const GeoParams& g, const void* maps, int map_dtype,
+                  const void* table, float* scores, const int64_t* mask, int nmask, ArgResult* result) {
     ArgPartial* parts;
     int nparts;
-    GH_TRY(gh_launch_hop_parts(ctx, d, g, maps, table, scores, mask, nmask, &parts, &nparts));
+    GH_TRY(gh_launch_hop_parts(ctx, d, g, maps, map_dtype, table, scores, mask, nmask, &parts, &nparts));
     return gh_launch_argmax_finalize(ctx, parts, nparts, result);
 }
 
@@ -563,7 +604,7 @@ extern "C" int gh_score_grid_noalloc(void* stream_ptr, const gh_radar* radar, co
     if (cudaGetLastError() != cudaSuccess) return GH_ECUDA;
     const HopParams hp = hop_params(d, g);
     long long nparts = 0;
-    int st = hop_launch(stream, d, hp, (const float2*)maps_dev, table, scores_dev, nullptr, 0, parts,
+    int st = hop_launch(stream, d, hp, maps_dev, GH_C64, table, scores_dev, nullptr, 0, parts,
                         kNoAllocMaxCtas, num_sms, (size_t)smem_optin, &nparts);
     if (st != GH_OK) return st;
     argmax_finalize_kernel<<<1, 1024, 0, stream>>>(parts, (int)nparts, result);

@@ -69,6 +69,7 @@ struct gh_ctx {
     // (recorded on the second call with that configuration, replayed
     // afterwards; all dropped whenever a workspace buffer moves or the
     // twiddle tables change).
+    int detect_maps = GH_C64;  // map storage type of gh_detect (GH_HOP)
     bool graphs = true;
     bool capturing = false;
     cudaStream_t capture_stream = nullptr;  // records graphs (the legacy stream cannot be captured)
@@ -123,6 +124,19 @@ struct Dims {
     int nx, ny, nvx, nvy;
     int64_t nxy, nv, ncells;
 };
+
+// Map storage: bytes per bin and the power-of-two scale exponent s of the
+// reduced-precision types (stored value = 2^-s * map value).
+inline size_t gh_map_bin_bytes(int map_dtype) { return map_dtype == GH_C64 ? 8 : 4; }
+inline int gh_map_scale_log2(const Dims& d, int map_dtype) {
+    if (map_dtype == GH_C64) return 0;
+    int s = 0;
+    while ((1LL << s) < (long long)d.Ms * d.Mc) ++s;
+    return s;
+}
+inline bool gh_map_dtype_ok(int map_dtype) {
+    return map_dtype == GH_C64 || map_dtype == GH_C16 || map_dtype == GH_CBF16;
+}
 
 int gh_check_radar(gh_ctx* ctx, const gh_radar* radar, int32_t Q, Dims* d);
 int gh_check_grid(gh_ctx* ctx, const gh_grid* grid, Dims* d);
@@ -253,16 +267,16 @@ struct ArgResult {
     int32_t valid;
 };
 
-int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* df, float2* maps);
+int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* df, void* maps, int map_dtype);
 int gh_launch_coord(gh_ctx* ctx, const Dims& d, const GeoParams& g, void* table,
                     int32_t* diag_i, double* diag_tau, float* diag_c, double* diag_w);
 size_t gh_hop_table_bytes(const Dims& d);
 // Scorer: per-CTA argmax partials into the context workspace (*parts, *nparts);
 // gh_launch_hop also reduces them into *result.
-int gh_launch_hop_parts(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* maps,
+int gh_launch_hop_parts(gh_ctx* ctx, const Dims& d, const GeoParams& g, const void* maps, int map_dtype,
                         const void* table, float* scores, const int64_t* mask, int nmask,
                         ArgPartial** parts, int* nparts);
-int gh_launch_hop(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* maps,
+int gh_launch_hop(gh_ctx* ctx, const Dims& d, const GeoParams& g, const void* maps, int map_dtype,
                   const void* table, float* scores, const int64_t* mask, int nmask,
                   ArgResult* result);
 int gh_launch_argmax_finalize(gh_ctx* ctx, const ArgPartial* parts, int nparts, ArgResult* out);

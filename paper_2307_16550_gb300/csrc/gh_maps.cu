@@ -11,6 +11,8 @@
 //                 Nd = pad*Mc, times the range-centring factor
 //                 exp(j pi (i/Nr)(Ms-1)), written [Q][Nr][Nd] so that one
 //                 range bin's Doppler row is contiguous for the scorer.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include <vector>
@@ -118,9 +120,23 @@ __global__ void __launch_bounds__(256) range_fft_kernel(const float2* __restrict
     for (int idx = threadIdx.x; idx < nrow * Nr; idx += blockDim.x) out[(size_t)r0 * Nr + idx] = res[idx];
 }
 
-__global__ void __launch_bounds__(256) doppler_fft_kernel(const float2* __restrict__ Zr, float2* __restrict__ maps,
+// One map bin in storage type MT (float32 pair, or 2^-s times the value
+// rounded to nearest-even float16 / bfloat16).
+template <int MT>
+__device__ __forceinline__ void store_bin(void* maps, size_t idx, float2 v, float oscale) {
+    if constexpr (MT == GH_C64) {
+        ((float2*)maps)[idx] = v;
+    } else if constexpr (MT == GH_C16) {
+        ((__half2*)maps)[idx] = __floats2half2_rn(v.x * oscale, v.y * oscale);
+    } else {
+        ((__nv_bfloat162*)maps)[idx] = __floats2bfloat162_rn(v.x * oscale, v.y * oscale);
+    }
+}
+
+template <int MT>
+__global__ void __launch_bounds__(256) doppler_fft_kernel(const float2* __restrict__ Zr, void* __restrict__ maps,
                                                           int Ms, int Mc, int logNr, int logNd, int IB,
-                                                          const float2* __restrict__ tw) {
+                                                          const float2* __restrict__ tw, float oscale) {
     extern __shared__ float2 smem[];
     const int Nr = 1 << logNr;
     const int Nd = 1 << logNd;
@@ -152,11 +168,11 @@ __global__ void __launch_bounds__(256) doppler_fft_kernel(const float2* __restri
     }
     __syncthreads();
     float2* res = fft_columns(x, y, logNd, IB, ld, twS);
-    float2* dst = maps + ((size_t)q * Nr + i0) * Nd;
+    const size_t dst = ((size_t)q * Nr + i0) * Nd;
     for (int idx = threadIdx.x; idx < IB * Nd; idx += blockDim.x) {
         const int c = idx >> logNd;
         const int j = idx & (Nd - 1);
-        dst[idx] = cmul(res[c * ld + j], ramp[c]);
+        store_bin<MT>(maps, dst + idx, cmul(res[c * ld + j], ramp[c]), oscale);
     }
 }
 
@@ -197,7 +213,7 @@ int ensure_twiddles(gh_ctx* ctx, int Nr, int Nd, const float2** twr, const float
 
 }  // namespace
 
-int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* df, float2* maps) {
+int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* df, void* maps, int map_dtype) {
     Deflate none = {nullptr, nullptr, nullptr, 0};
     const float2 *twr, *twd;
     GH_TRY(ensure_twiddles(ctx, d.Nr, d.Nd, &twr, &twd));
@@ -223,9 +239,12 @@ int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* d
     if (IB > 16) IB = 16;
     if (IB > d.Nr) IB = d.Nr;
     size_t smem2 = ((size_t)2 * IB * (d.Nd + 1) + IB + 3 * d.Nd / 4) * sizeof(float2);
-    GH_CUDA(cudaFuncSetAttribute(doppler_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+    const float oscale = ldexpf(1.0f, -gh_map_scale_log2(d, map_dtype));
+    auto kern = map_dtype == GH_C16 ? doppler_fft_kernel<GH_C16>
+              : map_dtype == GH_CBF16 ? doppler_fft_kernel<GH_CBF16> : doppler_fft_kernel<GH_C64>;
+    GH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
     gh_launch_begin(ctx, GH_K_DOPPLER_FFT, &ev);
-    doppler_fft_kernel<<<dim3(d.Nr / IB, d.Q), 256, smem2, ctx->stream>>>((const float2*)zr, maps, d.Ms, d.Mc,
-                                                                          logNr, logNd, IB, twd);
+    kern<<<dim3(d.Nr / IB, d.Q), 256, smem2, ctx->stream>>>((const float2*)zr, maps, d.Ms, d.Mc, logNr, logNd, IB,
+                                                            twd, oscale);
     return gh_launch_end(ctx, GH_K_DOPPLER_FFT, ev, "doppler_fft_kernel");
 }

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libgh.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "gh.h")
 
 GH_OK, GH_EINVAL, GH_ENOMEM, GH_ECUDA, GH_ETIMEOUT, GH_ENOTSUP = 0, -1, -2, -3, -4, -5
-GH_C64 = 0
+GH_C64, GH_C16, GH_CBF16 = 0, 1, 2
 GH_HOP, GH_EXACT = 0, 1
 (GH_K_RANGE_FFT, GH_K_DOPPLER_FFT, GH_K_COORD, GH_K_HOP_SCORE, GH_K_ARGMAX, GH_K_BOMP,
  GH_K_EXACT_S1, GH_K_EXACT_S2, GH_K_SYNTH) = range(9)
@@ -67,6 +67,7 @@ _SIGNATURES = {
     "gh_probe_read_bandwidth": (_I32, [_P, ctypes.c_int64, _I32, _PD]),
     "gh_set_timing": (_I32, [_P, _I32]),
     "gh_set_graphs": (_I32, [_P, _I32]),
+    "gh_set_detect_maps": (_I32, [_P, _I32]),
     "gh_kernel_stats": (_I32, [_P, _I32, _PD, ctypes.POINTER(ctypes.c_int64)]),
     "gh_reset_stats": (_I32, [_P]),
     "gh_launch_count": (ctypes.c_int64, [_P]),
@@ -282,6 +283,10 @@ class Context:
                 mask |= 1 << KERNEL_KINDS[k]
         self._check("gh_set_timing", self._lib.gh_set_timing(self.handle, int(mask)))
 
+    def gh_set_detect_maps(self, map_dtype):
+        """Storage type of the maps gh_detect makes for GH_HOP (GH_C64, GH_C16, GH_CBF16)."""
+        self._check("gh_set_detect_maps", self._lib.gh_set_detect_maps(self.handle, int(map_dtype)))
+
     def gh_set_graphs(self, enable: bool):
         self._check("gh_set_graphs", self._lib.gh_set_graphs(self.handle, int(bool(enable))))
 
@@ -303,19 +308,32 @@ class Context:
         import torch
         return torch
 
-    def maps(self, radar, Y):
-        """Range-Doppler maps of a device measurement Y (complex64 [Q][Mc][Ms])."""
+    def maps(self, radar, Y, map_dtype=GH_C64):
+        """Range-Doppler maps of a device measurement Y (complex64 [Q][Mc][Ms]):
+        complex64 [Q][Nr][Nd] for GH_C64, float16 / bfloat16 [Q][Nr][Nd][2]
+        (2^-s times the values, s = log2(Ms Mc)) for GH_C16 / GH_CBF16."""
         torch = self._torch()
         Q = Y.shape[0]
-        out = torch.empty((Q, radar.pad * radar.Ms, radar.pad * radar.Mc), dtype=torch.complex64, device=Y.device)
-        self.gh_make_maps(radar, Q, Y, out)
+        shape = (Q, radar.pad * radar.Ms, radar.pad * radar.Mc)
+        if map_dtype == GH_C64:
+            out = torch.empty(shape, dtype=torch.complex64, device=Y.device)
+        else:
+            dt = torch.float16 if map_dtype == GH_C16 else torch.bfloat16
+            out = torch.empty(shape + (2,), dtype=dt, device=Y.device)
+        self.gh_make_maps(radar, Q, Y, out, map_dtype)
         return out
+
+    @staticmethod
+    def map_dtype_of(maps):
+        import torch
+        return {torch.complex64: GH_C64, torch.float16: GH_C16, torch.bfloat16: GH_CBF16}[maps.dtype]
 
     def scores(self, radar, tx, rx, maps, grid):
         """Hopping scores of every cell (float32 [nx][ny][nvx][nvy]) and the argmax."""
         torch = self._torch()
         out = torch.empty(tuple(int(v) for v in grid.n), dtype=torch.float32, device=maps.device)
-        cell, score = self.gh_score_grid(radar, tx, rx, maps.shape[0], maps, grid, out)
+        cell, score = self.gh_score_grid(radar, tx, rx, maps.shape[0], maps, grid, out,
+                                         map_dtype=self.map_dtype_of(maps))
         return out, cell, score
 
     def exact_scores(self, radar, tx, rx, Y, grid):

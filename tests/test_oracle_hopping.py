@@ -144,3 +144,26 @@ def test_argmax_ties_take_smallest_index():
     s = np.zeros((2, 2, 2, 2))
     s.reshape(-1)[[5, 9, 3]] = 7.0
     assert hopping.argmax_cell(s) == 3
+
+
+@pytest.mark.parametrize("kind", ["f16", "bf16"])
+def test_quantization_bound_covers_stored_maps(kind):
+    """Hopping scores from maps stored in a reduced-precision format stay
+    within the per-cell bound, which is not vacuous."""
+    sc = scenes.tiny_scene(4)
+    Y = model.measurement(sc)
+    Z = maps.rd_maps(Y, sc.radar.pad)
+    s = maps.map_scale_log2(sc.radar.Ms, sc.radar.Mc)
+    # the stored maps are the centred ones; quantize those, then undo the centring
+    Nr = Z.shape[2]
+    ph = maps.centring_phase(np.arange(Nr), Nr, sc.radar.Ms)
+    Zq = maps.quantize_maps(Z * ph[None, None, :], kind, s) / ph[None, None, :]
+    ref = hopping.hop_scores(Z, sc.radar, sc.tx, sc.rx, sc.grid)
+    got = hopping.hop_scores(Zq, sc.radar, sc.tx, sc.rx, sc.grid)
+    bound = hopping.hop_quantization_bound(Z, sc.radar, sc.tx, sc.rx, sc.grid, kind)
+    slack = 1e-9 * ref.max()  # float64 rounding of the centring round trip
+    assert np.all(np.abs(got - ref) <= bound + slack)
+    ratio = np.abs(got - ref).max() / bound.max()
+    assert 1e-3 < ratio <= 1.0
+    u = {"f16": 2.0 ** -11, "bf16": 2.0 ** -8}[kind]
+    assert bound.max() / ref.max() < 8 * u  # a few units of the format's rounding

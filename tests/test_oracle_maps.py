@@ -66,3 +66,49 @@ def test_centred_map_is_centred_atom_correlation():
         r, u = i / (pad * Ms), j / (pad * Mc)
         atom = np.outer(np.exp(2j * np.pi * u * np.arange(Mc)), np.exp(2j * np.pi * r * m))
         assert abs(Zc[q, i, j] - np.vdot(atom, Y[q])) < 1e-10
+
+
+# --- reduced-precision storage -------------------------------------------------
+def _values():
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(200000) * np.exp(rng.uniform(-25, 10, 200000))
+    return np.concatenate([x, [0.0, -0.0, 1.0, 65504.0, 2.0 ** -24, 3 * 2.0 ** -25, 1 + 2.0 ** -11]])
+
+
+def test_round_f16_equals_numpy_half_cast():
+    """numpy's float16 cast is an independent IEEE binary16 rounding (incl.
+    subnormals and ties to even)."""
+    x = _values()
+    x = x[np.abs(x) < 65000]
+    np.testing.assert_array_equal(maps.round_format(x, "f16"), x.astype(np.float16).astype(np.float64))
+    with pytest.raises(OverflowError):
+        maps.round_format(np.array([70000.0]), "f16")
+
+
+def _bf16_by_bits(x32):
+    """bfloat16 round-to-nearest-even on the binary32 bit pattern: add
+    0x7fff plus the lowest kept bit, clear the low 16 bits."""
+    b = x32.view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_round_bf16_equals_bit_rounding():
+    x32 = _values().astype(np.float32)
+    x32 = x32[np.abs(x32) < 3e38]
+    np.testing.assert_array_equal(maps.round_format(x32.astype(np.float64), "bf16"), _bf16_by_bits(x32))
+    # ties go to even: 1 + 2^-8 lies halfway between 1 and 1 + 2^-7
+    assert maps.round_format(np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8]), "bf16").tolist() == [1.0, 1 + 2.0 ** -6]
+
+
+@pytest.mark.parametrize("kind", ["f16", "bf16"])
+def test_quantization_error_bound_holds_and_is_attained(kind):
+    s = maps.map_scale_log2(256, 128)
+    assert s == 15
+    x = _values()
+    x = x[np.abs(x) < 6e4] * 2.0 ** s
+    u, eta = maps.quantization_error_bound(kind, s)
+    q = maps.quantize_maps(x + 0j, kind, s).real
+    err = np.abs(q - x)
+    assert np.all(err <= u * np.abs(x) + eta)
+    assert np.max(err / (u * np.abs(x) + eta)) > 0.9  # the bound is tight
