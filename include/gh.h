@@ -83,7 +83,8 @@ extern "C" {
 #define GH_K_EXACT_S1    6
 #define GH_K_EXACT_S2    7
 #define GH_K_SYNTH       8
-#define GH_K_COUNT       9
+#define GH_K_POINTS      9   /* continuous-point scores, adjoint, refinement */
+#define GH_K_COUNT       10
 
 /* Size limits checked by every entry point (GH_EINVAL beyond them). */
 #define GH_MAX_Q        64
@@ -203,6 +204,65 @@ GH_API int gh_direct_exact(gh_ctx* ctx, const gh_radar* radar, const double* tx_
  * All K iterations run on the device without host round trips; the stream is
  * synchronised once at the end. 1 <= K <= min(GH_MAX_K, ncells).
  */
+/*
+ * gh_score_points - differentiable hopping score at P continuous points
+ * (x, y, vx, vy), for off-grid refinement of detections and calibration of
+ * receiver positions (Sec. VI names refined estimation as future work). Both
+ * map axes are interpolated with the three-bin polar model of Sec. IV (range:
+ * c_k(tau) as in gh_score_grid; Doppler: the same construction on centred
+ * Doppler atoms, coefficients d_l(sigma), in place of the nearest bin, so that
+ * the score varies smoothly with v):
+ *   S(p) = sum_q | sum_{k,l} c_k(tau_q) d_l(sigma_q) V_q(i_q+k, j_q+l) |^2
+ *   V_q(n, m) = maps[q][n mod Nr][m mod Nd] (-1)^((Ms-1) floor(n/Nr)) exp(j pi m (Mc-1)/Nd)
+ * with i_q, tau_q from Nr r_q and j_q, sigma_q from Nd u_q (float64, Eq. 1).
+ *   tx_host    : host double[2]
+ *   rx_dev     : device double[Q][2] receiver positions (device memory so that
+ *                their gradient can be taken)
+ *   maps_dev   : device, from gh_make_maps with map_dtype
+ *   points_dev : device double[P][4] (x, y, vx, vy); P >= 0
+ *   scores_dev : device float[P] (written)
+ * Non-finite positions give non-finite scores. No host synchronisation.
+ */
+GH_API int gh_score_points(gh_ctx* ctx, const gh_radar* radar, const double* tx_host,
+                    const double* rx_dev, int32_t Q, const void* maps_dev, int32_t map_dtype,
+                    const double* points_dev, int64_t P, float* scores_dev);
+
+/*
+ * gh_score_points_adjoint - gradients of L = sum_p g_p S(p) (gh_score_points)
+ * for upstream weights g = dscores_dev (device float[P]):
+ *   dpoints_dev : device double[P][4], written with dL/d(x, y, vx, vy), or NULL
+ *   drx_dev     : device double[Q][2], dL/drx ADDED to its contents, or NULL
+ *   dmaps_dev   : device complex float32 [Q][Nr][Nd], dL/dRe + j dL/dIm of each
+ *                 map bin ADDED to its contents (scatter-add), or NULL; needs
+ *                 map_dtype GH_C64
+ * The score is differentiated between bin switches (tau, sigma = +-1/2, where
+ * the three-bin stencil moves by one bin). Uses atomics (the summation order
+ * of drx and dmaps is not deterministic).
+ */
+GH_API int gh_score_points_adjoint(gh_ctx* ctx, const gh_radar* radar, const double* tx_host,
+                    const double* rx_dev, int32_t Q, const void* maps_dev, int32_t map_dtype,
+                    const double* points_dev, int64_t P, const float* dscores_dev,
+                    double* dpoints_dev, double* drx_dev, void* dmaps_dev);
+
+/*
+ * gh_refine_points - off-grid refinement of P points by damped Newton
+ * (Levenberg-Marquardt) ascent of gh_score_points, all iterations in one
+ * launch (one warp per point). Per iteration: the Hessian from central
+ * differences of the analytic gradient (steps of 1e-3 scale units), then
+ * steps d solving (-H + lambda D) d = grad, D = diag(1/scale^2) with scales
+ * (scale_xy, scale_xy, scale_v, scale_v); an improving step is taken and
+ * lambda shrinks by 3, otherwise lambda grows by 4 (at most 40 trials; no
+ * improving step ends the iterations). The first lambda makes the first step
+ * about `step` scale units long.
+ *   points_dev : device double[P][4], read and overwritten with the refined points
+ *   scores_dev : device float[P], their scores (may be NULL)
+ *   iters in [0, 100000]; scale_xy, scale_v, step > 0.
+ */
+GH_API int gh_refine_points(gh_ctx* ctx, const gh_radar* radar, const double* tx_host,
+                    const double* rx_dev, int32_t Q, const void* maps_dev, int32_t map_dtype,
+                    double* points_dev, int64_t P, int32_t iters, double scale_xy,
+                    double scale_v, double step, float* scores_dev);
+
 /*
  * gh_set_detect_maps - storage type (GH_C64 default, GH_C16, GH_CBF16) of the
  * range-Doppler maps gh_detect makes on the context for method GH_HOP.

@@ -4,6 +4,8 @@
 #include <stdarg.h>
 #include <string.h>
 
+#include <cmath>
+
 #include "gh_internal.cuh"
 
 // ---------------------------------------------------------------------------
@@ -235,6 +237,72 @@ extern "C" int gh_set_timing(gh_ctx* ctx, int32_t mask) {
     if (!ctx) return GH_EINVAL;
     ctx->timing = (uint32_t)mask;
     return GH_OK;
+}
+
+// Common checks of the continuous-point entry points.
+static int points_prologue(gh_ctx* ctx, const gh_radar* radar, const double* tx_host, const double* rx_dev,
+                           int32_t Q, const void* maps_dev, int32_t map_dtype, const double* points_dev, int64_t P,
+                           Dims* d, GeoParams* geo) {
+    GH_TRY(gh_check_radar(ctx, radar, Q, d));
+    if (!tx_host || !std::isfinite(tx_host[0]) || !std::isfinite(tx_host[1]))
+        return gh_fail(ctx, GH_EINVAL, "tx_host must hold two finite values");
+    if (!gh_map_dtype_ok(map_dtype)) return gh_fail(ctx, GH_EINVAL, "map_dtype %d unknown", map_dtype);
+    if (P < 0) return gh_fail(ctx, GH_EINVAL, "P must be >= 0");
+    if (!rx_dev || !maps_dev || (P > 0 && !points_dev))
+        return gh_fail(ctx, GH_EINVAL, "rx_dev, maps_dev and points_dev must be non-NULL");
+    for (const void* ptr : {(const void*)rx_dev, maps_dev, (const void*)points_dev}) {
+        if (!ptr) continue;
+        const int dv = gh_is_device_ptr(ctx, ptr);
+        if (dv < 0) return dv;
+        if (!dv) return gh_fail(ctx, GH_EINVAL, "rx_dev, maps_dev and points_dev must be device memory");
+    }
+    double rx0[2 * GH_MAX_Q] = {0};
+    gh_fill_geo(geo, radar, tx_host, rx0, Q, nullptr);
+    return GH_OK;
+}
+
+extern "C" int gh_score_points(gh_ctx* ctx, const gh_radar* radar, const double* tx_host, const double* rx_dev,
+                               int32_t Q, const void* maps_dev, int32_t map_dtype, const double* points_dev,
+                               int64_t P, float* scores_dev) {
+    if (!ctx) return GH_EINVAL;
+    DeviceGuard dg(ctx->device);
+    Dims d = {};
+    GeoParams geo;
+    GH_TRY(points_prologue(ctx, radar, tx_host, rx_dev, Q, maps_dev, map_dtype, points_dev, P, &d, &geo));
+    if (P > 0 && !scores_dev) return gh_fail(ctx, GH_EINVAL, "scores_dev is NULL");
+    return gh_launch_points(ctx, d, geo, maps_dev, map_dtype, rx_dev, points_dev, P, scores_dev);
+}
+
+extern "C" int gh_score_points_adjoint(gh_ctx* ctx, const gh_radar* radar, const double* tx_host,
+                                       const double* rx_dev, int32_t Q, const void* maps_dev, int32_t map_dtype,
+                                       const double* points_dev, int64_t P, const float* dscores_dev,
+                                       double* dpoints_dev, double* drx_dev, void* dmaps_dev) {
+    if (!ctx) return GH_EINVAL;
+    DeviceGuard dg(ctx->device);
+    Dims d = {};
+    GeoParams geo;
+    GH_TRY(points_prologue(ctx, radar, tx_host, rx_dev, Q, maps_dev, map_dtype, points_dev, P, &d, &geo));
+    if (P > 0 && !dscores_dev) return gh_fail(ctx, GH_EINVAL, "dscores_dev is NULL");
+    if (dmaps_dev && map_dtype != GH_C64)
+        return gh_fail(ctx, GH_ENOTSUP, "map gradients need complex float32 maps (GH_C64)");
+    return gh_launch_points_adjoint(ctx, d, geo, maps_dev, map_dtype, rx_dev, points_dev, P, dscores_dev,
+                                    dpoints_dev, drx_dev, (float2*)dmaps_dev);
+}
+
+extern "C" int gh_refine_points(gh_ctx* ctx, const gh_radar* radar, const double* tx_host, const double* rx_dev,
+                                int32_t Q, const void* maps_dev, int32_t map_dtype, double* points_dev, int64_t P,
+                                int32_t iters, double scale_xy, double scale_v, double step, float* scores_dev) {
+    if (!ctx) return GH_EINVAL;
+    DeviceGuard dg(ctx->device);
+    Dims d = {};
+    GeoParams geo;
+    GH_TRY(points_prologue(ctx, radar, tx_host, rx_dev, Q, maps_dev, map_dtype, points_dev, P, &d, &geo));
+    if (iters < 0 || iters > 100000) return gh_fail(ctx, GH_EINVAL, "iters must be in [0, 100000]");
+    if (!(scale_xy > 0.0) || !(scale_v > 0.0) || !(step > 0.0) || !std::isfinite(scale_xy) ||
+        !std::isfinite(scale_v) || !std::isfinite(step))
+        return gh_fail(ctx, GH_EINVAL, "scale_xy, scale_v and step must be finite and > 0");
+    return gh_launch_refine(ctx, d, geo, maps_dev, map_dtype, rx_dev, points_dev, P, iters, scale_xy, scale_v, step,
+                            scores_dev);
 }
 
 extern "C" int gh_set_detect_maps(gh_ctx* ctx, int32_t map_dtype) {

@@ -280,6 +280,15 @@ int gh_launch_hop(gh_ctx* ctx, const Dims& d, const GeoParams& g, const void* ma
                   const void* table, float* scores, const int64_t* mask, int nmask,
                   ArgResult* result);
 int gh_launch_argmax_finalize(gh_ctx* ctx, const ArgPartial* parts, int nparts, ArgResult* out);
+// Continuous-point scores, their adjoint and the refinement (gh_points.cu).
+int gh_launch_points(gh_ctx* ctx, const Dims& d, const GeoParams& g, const void* maps, int map_dtype,
+                     const double* rx_dev, const double* pts, long long P, float* S);
+int gh_launch_points_adjoint(gh_ctx* ctx, const Dims& d, const GeoParams& g, const void* maps, int map_dtype,
+                             const double* rx_dev, const double* pts, long long P, const float* gS, double* dpts,
+                             double* drx, float2* dmaps);
+int gh_launch_refine(gh_ctx* ctx, const Dims& d, const GeoParams& g, const void* maps, int map_dtype,
+                     const double* rx_dev, double* pts, long long P, int iters, double sx, double sv, double step,
+                     float* S);
 // Exact direct scores of the (deflated) measurement; partials as gh_launch_hop_parts.
 int gh_launch_exact_parts(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y,
                           const Deflate* df, float* scores, const int64_t* mask, int nmask,

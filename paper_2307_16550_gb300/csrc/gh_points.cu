@@ -1,0 +1,446 @@
+// Differentiable hopping score at continuous points, its adjoint, and an
+// on-device gradient-ascent refinement (off-grid estimates; Sec. VI names
+// refined estimation as future work).
+//
+// The score of a point (x, y, vx, vy) interpolates both map axes with the
+// three-bin polar model of Sec. IV: the range coefficients c_k(tau) as in the
+// grid scorer, and, because the nearest Doppler bin of the grid scorer makes
+// the score piecewise constant in v, the same construction on the Doppler axis
+// with centred Doppler atoms (coefficients d_l(sigma), half-angle from Mc, Nd):
+//   s_q = sum_{k,l} c_k(tau_q) d_l(sigma_q) V_q(i_q + k, j_q + l),  S = sum_q |s_q|^2,
+//   V_q(n, m) = maps[q][n mod Nr][m mod Nd] (-1)^((Ms-1) floor(n/Nr)) exp(j pi m (Mc-1)/Nd)
+// with rho = Nr r_q, i = floor(rho + 1/2), tau = rho - i, eta = Nd u_q,
+// j = floor(eta + 1/2), sigma = eta - j, all in float64 (Eq. 1).
+//
+// Adjoint (i, j fixed between bin switches): dS/drho_q = 2 Re(conj(s) sum c_k' d_l V),
+// dS/deta_q = 2 Re(conj(s) sum c_k d_l' V), chained through
+//   drho/dx = Nr B/(c Ms) w_q,   drho/drx_q = -Nr B/(c Ms) u_rx,
+//   deta/dv = Nd kappa w_q,      deta/dx = Nd kappa (J_tx + J_rx) v,   deta/drx_q = -Nd kappa J_rx v,
+// J_p = (I - u_p u_p^T)/|x - p|; and into the maps as d|s|^2/d(bin) = 2 s conj(weight).
+//
+// One warp per point, lanes over receivers, warp-shuffle sums over q.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include "gh_internal.cuh"
+
+namespace {
+
+struct PtParams {
+    double tx0, tx1;
+    double B, cMs, kappa;
+    double gr, ge;     // Nr B / (c Ms) and Nd kappa
+    int Q, Ms, Mc, Nr, Nd;
+    float thr, thd;    // polar half-angles (range, Doppler)
+    float mscale;      // 2^s of reduced-precision maps
+};
+
+struct Coef {
+    float c[3], dc[3];
+};
+
+// Polar coefficients (c_{-1}, c_0, c_{+1}) at offset t and their derivatives.
+__device__ __forceinline__ Coef polar(float theta, float t) {
+    float sh, ch, sf, cf;
+    sincosf(0.5f * theta * t, &sh, &ch);
+    sincosf(theta * t, &sf, &cf);
+    float s2, c2, st, ct;
+    sincosf(0.5f * theta, &s2, &c2);
+    sincosf(theta, &st, &ct);
+    const float inv_h = 1.0f / (s2 * s2);  // 1 / sin^2(theta/2) = 2 / (1 - cos theta)
+    const float kap = sh * sh * inv_h;
+    const float sig = sf / st;
+    const float dkap = 0.5f * theta * sf * inv_h;
+    const float dsig = theta * cf / st;
+    Coef r;
+    r.c[0] = 0.5f * (kap - sig);
+    r.c[1] = 1.0f - kap;
+    r.c[2] = 0.5f * (kap + sig);
+    r.dc[0] = 0.5f * (dkap - dsig);
+    r.dc[1] = -dkap;
+    r.dc[2] = 0.5f * (dkap + dsig);
+    return r;
+}
+
+template <int MT>
+__device__ __forceinline__ float2 load_bin(const void* maps, size_t idx) {
+    if constexpr (MT == GH_C64) {
+        return __ldg((const float2*)maps + idx);
+    } else if constexpr (MT == GH_C16) {
+        const unsigned w = __ldg((const unsigned*)maps + idx);
+        return __half22float2(*reinterpret_cast<const __half2*>(&w));
+    } else {
+        const unsigned w = __ldg((const unsigned*)maps + idx);
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+    }
+}
+
+// Geometry of one (point, receiver) in float64 and its stencil.
+struct PtGeo {
+    double ux1, uy1, n1, ux2, uy2, n2, wx, wy;
+    long long i, j;
+    float tau, sig;
+};
+
+__device__ __forceinline__ PtGeo pt_geo(const PtParams& p, double x, double y, double vx, double vy, double rxx,
+                                        double rxy) {
+    PtGeo g;
+    gh_unit(__dsub_rn(x, p.tx0), __dsub_rn(y, p.tx1), &g.n1, &g.ux1, &g.uy1);
+    gh_unit(__dsub_rn(x, rxx), __dsub_rn(y, rxy), &g.n2, &g.ux2, &g.uy2);
+    const double d = __dadd_rn(g.n1, g.n2);
+    g.wx = __dadd_rn(g.ux1, g.ux2);
+    g.wy = __dadd_rn(g.uy1, g.uy2);
+    const double rho = __dmul_rn((double)p.Nr, __ddiv_rn(__dmul_rn(p.B, d), p.cMs));
+    const double eta =
+        __dmul_rn((double)p.Nd, __dmul_rn(p.kappa, __dadd_rn(__dmul_rn(g.wx, vx), __dmul_rn(g.wy, vy))));
+    const double fi = floor(__dadd_rn(rho, 0.5)), fj = floor(__dadd_rn(eta, 0.5));
+    g.i = (long long)fi;
+    g.j = (long long)fj;
+    g.tau = (float)__dsub_rn(rho, fi);
+    g.sig = (float)__dsub_rn(eta, fj);
+    return g;
+}
+
+__device__ __forceinline__ long long floor_div(long long a, long long b) {
+    long long q = a / b;
+    if (a < 0 && q * b != a) --q;
+    return q;
+}
+
+// Stencil values V(i+k, j+l) of receiver q (range sign and Doppler centring applied).
+template <int MT>
+__device__ __forceinline__ void stencil(const void* maps, const PtParams& p, int q, long long i, long long j,
+                                        float2 V[3][3], size_t idx[3][3], float2 wph[3][3]) {
+    float2 ph[3];
+    long long mm[3];
+    for (int l = 0; l < 3; ++l) {
+        const long long m = j + (l - 1);
+        const long long w = floor_div(m, p.Nd);
+        mm[l] = m - w * p.Nd;
+        // exp(j pi m (Mc-1)/Nd), angle reduced exactly modulo 2 pi
+        long long t = (m % (2LL * p.Nd)) * (long long)(p.Mc - 1) % (2LL * p.Nd);
+        if (t < 0) t += 2LL * p.Nd;
+        float s, c;
+        sincospif((float)t / (float)p.Nd, &s, &c);
+        ph[l] = make_float2(c, s);
+    }
+    for (int k = 0; k < 3; ++k) {
+        const long long n = i + (k - 1);
+        const long long w = floor_div(n, p.Nr);
+        const long long nr = n - w * p.Nr;
+        const float sg = (((p.Ms - 1) & 1) && (w & 1)) ? -p.mscale : p.mscale;
+        for (int l = 0; l < 3; ++l) {
+            idx[k][l] = ((size_t)q * p.Nr + (size_t)nr) * p.Nd + (size_t)mm[l];
+            wph[k][l] = make_float2(sg * ph[l].x, sg * ph[l].y);
+            V[k][l] = cmul(load_bin<MT>(maps, idx[k][l]), wph[k][l]);
+        }
+    }
+}
+
+__device__ __forceinline__ float2 contract(const float* a, const float* b, float2 V[3][3]) {
+    float2 s = make_float2(0.f, 0.f);
+    for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) {
+            const float w = a[k] * b[l];
+            s.x += w * V[k][l].x;
+            s.y += w * V[k][l].y;
+        }
+    return s;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// S of one point (whole warp; every lane returns the sum over receivers).
+template <int MT>
+__device__ double point_score(const void* maps, const PtParams& p, const double* __restrict__ rx, double x, double y,
+                              double vx, double vy) {
+    const int lane = threadIdx.x & 31;
+    double acc = 0.0;
+    for (int q = lane; q < p.Q; q += 32) {
+        const PtGeo g = pt_geo(p, x, y, vx, vy, rx[2 * q], rx[2 * q + 1]);
+        const Coef cr = polar(p.thr, g.tau), cd = polar(p.thd, g.sig);
+        float2 V[3][3], wph[3][3];
+        size_t idx[3][3];
+        stencil<MT>(maps, p, q, g.i, g.j, V, idx, wph);
+        const float2 s = contract(cr.c, cd.c, V);
+        acc += (double)(s.x * s.x + s.y * s.y);
+    }
+    return warp_sum(acc);
+}
+
+// Gradient of S of one point: dS/d(x, y, vx, vy) summed over receivers (every
+// lane returns it); per-receiver RX gradients and map gradients, scaled by gs,
+// are accumulated when drx / dmaps are non-NULL.
+template <int MT>
+__device__ double point_grad(const void* maps, const PtParams& p, const double* __restrict__ rx, double x, double y,
+                             double vx, double vy, float gs, double* __restrict__ drx, float2* __restrict__ dmaps,
+                             double grad[4]) {
+    const int lane = threadIdx.x & 31;
+    double acc = 0.0, gx = 0.0, gy = 0.0, gvx = 0.0, gvy = 0.0;
+    for (int q = lane; q < p.Q; q += 32) {
+        const PtGeo g = pt_geo(p, x, y, vx, vy, rx[2 * q], rx[2 * q + 1]);
+        const Coef cr = polar(p.thr, g.tau), cd = polar(p.thd, g.sig);
+        float2 V[3][3], wph[3][3];
+        size_t idx[3][3];
+        stencil<MT>(maps, p, q, g.i, g.j, V, idx, wph);
+        const float2 s = contract(cr.c, cd.c, V);
+        const float2 ar = contract(cr.dc, cd.c, V);
+        const float2 ae = contract(cr.c, cd.dc, V);
+        acc += (double)(s.x * s.x + s.y * s.y);
+        const double dSr = 2.0 * (double)(s.x * ar.x + s.y * ar.y);  // 2 Re(conj(s) ar)
+        const double dSe = 2.0 * (double)(s.x * ae.x + s.y * ae.y);
+        // J_p v = (v - u (u.v)) / n (zero for a point on p)
+        double j1x = 0.0, j1y = 0.0, j2x = 0.0, j2y = 0.0;
+        if (g.n1 >= 1e-9) {
+            const double uv = g.ux1 * vx + g.uy1 * vy;
+            j1x = (vx - g.ux1 * uv) / g.n1;
+            j1y = (vy - g.uy1 * uv) / g.n1;
+        }
+        if (g.n2 >= 1e-9) {
+            const double uv = g.ux2 * vx + g.uy2 * vy;
+            j2x = (vx - g.ux2 * uv) / g.n2;
+            j2y = (vy - g.uy2 * uv) / g.n2;
+        }
+        const double fr = dSr * p.gr, fe = dSe * p.ge;
+        gx += fr * g.wx + fe * (j1x + j2x);
+        gy += fr * g.wy + fe * (j1y + j2y);
+        gvx += fe * g.wx;
+        gvy += fe * g.wy;
+        if (drx) {
+            atomicAdd(&drx[2 * q], (double)gs * (-fr * g.ux2 - fe * j2x));
+            atomicAdd(&drx[2 * q + 1], (double)gs * (-fr * g.uy2 - fe * j2y));
+        }
+        if (dmaps) {
+            // d|s|^2 / d(stored bin) = 2 s conj(c_k d_l wph) (stored bins are 2^-s times the values)
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) {
+                    const float w = 2.0f * gs * cr.c[k] * cd.c[l];
+                    const float2 t = cmulc(s, wph[k][l]);  // s conj(wph)
+                    atomicAdd(&dmaps[idx[k][l]].x, w * t.x);
+                    atomicAdd(&dmaps[idx[k][l]].y, w * t.y);
+                }
+        }
+    }
+    grad[0] = warp_sum(gx);
+    grad[1] = warp_sum(gy);
+    grad[2] = warp_sum(gvx);
+    grad[3] = warp_sum(gvy);
+    return warp_sum(acc);
+}
+
+template <int MT>
+__global__ void __launch_bounds__(128) points_fwd_kernel(const void* __restrict__ maps, PtParams p,
+                                                        const double* __restrict__ rx,
+                                                        const double* __restrict__ pts, long long P,
+                                                        float* __restrict__ S) {
+    const long long pt = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (pt >= P) return;  // whole warps leave together
+    const double* a = pts + 4 * pt;
+    const double v = point_score<MT>(maps, p, rx, a[0], a[1], a[2], a[3]);
+    if ((threadIdx.x & 31) == 0) S[pt] = (float)v;
+}
+
+template <int MT>
+__global__ void __launch_bounds__(128) points_adj_kernel(const void* __restrict__ maps, PtParams p,
+                                                        const double* __restrict__ rx,
+                                                        const double* __restrict__ pts, long long P,
+                                                        const float* __restrict__ gS, double* __restrict__ dpts,
+                                                        double* __restrict__ drx, float2* __restrict__ dmaps) {
+    const long long pt = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (pt >= P) return;
+    const double* a = pts + 4 * pt;
+    const float gs = gS[pt];
+    double grad[4];
+    point_grad<MT>(maps, p, rx, a[0], a[1], a[2], a[3], gs, drx, dmaps, grad);
+    if (dpts && (threadIdx.x & 31) == 0)
+        for (int c = 0; c < 4; ++c) dpts[4 * pt + c] = (double)gs * grad[c];
+}
+
+// Solves A x = b for a symmetric 4 x 4 A by Cholesky; false if A is not
+// positive definite.
+__device__ __forceinline__ bool chol4_solve(double A[4][4], const double b[4], double x[4]) {
+    double L[4][4] = {{0}};
+    for (int i = 0; i < 4; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double s = A[i][j];
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (!(s > 0.0)) return false;
+                L[i][i] = sqrt(s);
+            } else {
+                L[i][j] = s / L[j][j];
+            }
+        }
+    }
+    double y[4];
+    for (int i = 0; i < 4; ++i) {
+        double s = b[i];
+        for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
+        y[i] = s / L[i][i];
+    }
+    for (int i = 3; i >= 0; --i) {
+        double s = y[i];
+        for (int k = i + 1; k < 4; ++k) s -= L[k][i] * x[k];
+        x[i] = s / L[i][i];
+    }
+    return true;
+}
+
+// Damped Newton (Levenberg-Marquardt) ascent of every point for at most
+// `iters` iterations. The Hessian comes from central differences of the
+// analytic gradient (steps 1e-3 of the per-axis scales sc); a step solves
+// (-H + lambda D) d = g with D = diag(1 / sc^2); a step that raises S is
+// taken and lambda shrinks by 3, otherwise lambda grows by 4 (at most 40
+// trials). The first lambda makes the step about `step` scale units long.
+// Every lane of the warp holds the same values (the sums over receivers are
+// butterfly reductions), so control flow stays warp-uniform.
+template <int MT>
+__global__ void __launch_bounds__(128) refine_kernel(const void* __restrict__ maps, PtParams p,
+                                                    const double* __restrict__ rx, double* __restrict__ pts,
+                                                    long long P, int iters, double sx, double sv, double step,
+                                                    float* __restrict__ S) {
+    const long long pt = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (pt >= P) return;
+    double* a = pts + 4 * pt;
+    double x[4] = {a[0], a[1], a[2], a[3]};
+    const double sc[4] = {sx, sx, sv, sv};
+    double g[4];
+    double cur = point_grad<MT>(maps, p, rx, x[0], x[1], x[2], x[3], 0.f, nullptr, nullptr, g);
+    double lam = -1.0;
+    for (int it = 0; it < iters; ++it) {
+        double H[4][4];
+        for (int c = 0; c < 4; ++c) {
+            const double del = 1e-3 * sc[c];
+            double xp[4] = {x[0], x[1], x[2], x[3]}, xm[4] = {x[0], x[1], x[2], x[3]};
+            xp[c] += del;
+            xm[c] -= del;
+            double gp[4], gm[4];
+            point_grad<MT>(maps, p, rx, xp[0], xp[1], xp[2], xp[3], 0.f, nullptr, nullptr, gp);
+            point_grad<MT>(maps, p, rx, xm[0], xm[1], xm[2], xm[3], 0.f, nullptr, nullptr, gm);
+            for (int r = 0; r < 4; ++r) H[r][c] = (gp[r] - gm[r]) / (2.0 * del);
+        }
+        for (int r = 0; r < 4; ++r)
+            for (int c = r + 1; c < 4; ++c) H[r][c] = H[c][r] = 0.5 * (H[r][c] + H[c][r]);
+        if (lam < 0.0) {
+            double n = 0.0;
+            for (int c = 0; c < 4; ++c) n += (sc[c] * g[c]) * (sc[c] * g[c]);
+            lam = sqrt(n) / step;
+            if (!(lam > 0.0)) break;  // zero gradient: nothing to do
+        }
+        bool moved = false;
+        for (int trial = 0; trial < 40 && !moved; ++trial) {
+            double A[4][4], d[4];
+            for (int r = 0; r < 4; ++r)
+                for (int c = 0; c < 4; ++c) A[r][c] = -H[r][c] + (r == c ? lam / (sc[r] * sc[r]) : 0.0);
+            if (chol4_solve(A, g, d)) {
+                const double y0 = x[0] + d[0], y1 = x[1] + d[1], y2 = x[2] + d[2], y3 = x[3] + d[3];
+                double gy[4];
+                const double val = point_grad<MT>(maps, p, rx, y0, y1, y2, y3, 0.f, nullptr, nullptr, gy);
+                if (val > cur) {
+                    x[0] = y0;
+                    x[1] = y1;
+                    x[2] = y2;
+                    x[3] = y3;
+                    for (int c = 0; c < 4; ++c) g[c] = gy[c];
+                    cur = val;
+                    lam /= 3.0;
+                    moved = true;
+                    break;
+                }
+            }
+            lam *= 4.0;
+        }
+        if (!moved) break;  // no improving step at any damping: converged
+    }
+    if ((threadIdx.x & 31) == 0) {
+        for (int c = 0; c < 4; ++c) a[c] = x[c];
+        if (S) S[pt] = (float)cur;
+    }
+}
+
+double dirichlet_d(double f, int M) {
+    const double pi = 3.14159265358979323846264338327950288;
+    return sin(pi * M * f) / sin(pi * f);
+}
+
+double half_angle(int M, int N) {
+    const double D1 = dirichlet_d(1.0 / N, M), D2 = dirichlet_d(2.0 / N, M);
+    return 2.0 * acos(0.5 * sqrt((M - D2) / (M - D1)));
+}
+
+PtParams pt_params(const Dims& d, const GeoParams& g, int map_dtype) {
+    PtParams p;
+    p.tx0 = g.tx[0];
+    p.tx1 = g.tx[1];
+    p.B = g.B;
+    p.cMs = g.cMs;
+    p.kappa = g.kappa;
+    p.gr = (double)d.Nr * g.B / g.cMs;
+    p.ge = (double)d.Nd * g.kappa;
+    p.Q = d.Q;
+    p.Ms = d.Ms;
+    p.Mc = d.Mc;
+    p.Nr = d.Nr;
+    p.Nd = d.Nd;
+    p.thr = (float)half_angle(d.Ms, d.Nr);
+    p.thd = (float)half_angle(d.Mc, d.Nd);
+    p.mscale = ldexpf(1.0f, gh_map_scale_log2(d, map_dtype));
+    return p;
+}
+
+}  // namespace
+
+int gh_launch_points(gh_ctx* ctx, const Dims& d, const GeoParams& g, const void* maps, int map_dtype,
+                     const double* rx_dev, const double* pts, long long P, float* S) {
+    if (P == 0) return GH_OK;
+    const PtParams p = pt_params(d, g, map_dtype);
+    const unsigned blocks = (unsigned)((P * 32 + 127) / 128);
+    cudaEvent_t ev;
+    gh_launch_begin(ctx, GH_K_POINTS, &ev);
+    if (map_dtype == GH_C16)
+        points_fwd_kernel<GH_C16><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, S);
+    else if (map_dtype == GH_CBF16)
+        points_fwd_kernel<GH_CBF16><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, S);
+    else
+        points_fwd_kernel<GH_C64><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, S);
+    return gh_launch_end(ctx, GH_K_POINTS, ev, "points_fwd_kernel");
+}
+
+int gh_launch_points_adjoint(gh_ctx* ctx, const Dims& d, const GeoParams& g, const void* maps, int map_dtype,
+                             const double* rx_dev, const double* pts, long long P, const float* gS, double* dpts,
+                             double* drx, float2* dmaps) {
+    if (P == 0) return GH_OK;
+    const PtParams p = pt_params(d, g, map_dtype);
+    const unsigned blocks = (unsigned)((P * 32 + 127) / 128);
+    cudaEvent_t ev;
+    gh_launch_begin(ctx, GH_K_POINTS, &ev);
+    if (map_dtype == GH_C16)
+        points_adj_kernel<GH_C16><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, gS, dpts, drx, dmaps);
+    else if (map_dtype == GH_CBF16)
+        points_adj_kernel<GH_CBF16><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, gS, dpts, drx,
+                                                                      dmaps);
+    else
+        points_adj_kernel<GH_C64><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, gS, dpts, drx, dmaps);
+    return gh_launch_end(ctx, GH_K_POINTS, ev, "points_adj_kernel");
+}
+
+int gh_launch_refine(gh_ctx* ctx, const Dims& d, const GeoParams& g, const void* maps, int map_dtype,
+                     const double* rx_dev, double* pts, long long P, int iters, double sx, double sv, double step,
+                     float* S) {
+    if (P == 0) return GH_OK;
+    const PtParams p = pt_params(d, g, map_dtype);
+    const unsigned blocks = (unsigned)((P * 32 + 127) / 128);
+    cudaEvent_t ev;
+    gh_launch_begin(ctx, GH_K_POINTS, &ev);
+    if (map_dtype == GH_C16)
+        refine_kernel<GH_C16><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, iters, sx, sv, step, S);
+    else if (map_dtype == GH_CBF16)
+        refine_kernel<GH_CBF16><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, iters, sx, sv, step, S);
+    else
+        refine_kernel<GH_C64><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, iters, sx, sv, step, S);
+    return gh_launch_end(ctx, GH_K_POINTS, ev, "refine_kernel");
+}

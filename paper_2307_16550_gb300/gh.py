@@ -22,9 +22,9 @@ GH_OK, GH_EINVAL, GH_ENOMEM, GH_ECUDA, GH_ETIMEOUT, GH_ENOTSUP = 0, -1, -2, -3, 
 GH_C64, GH_C16, GH_CBF16 = 0, 1, 2
 GH_HOP, GH_EXACT = 0, 1
 (GH_K_RANGE_FFT, GH_K_DOPPLER_FFT, GH_K_COORD, GH_K_HOP_SCORE, GH_K_ARGMAX, GH_K_BOMP,
- GH_K_EXACT_S1, GH_K_EXACT_S2, GH_K_SYNTH) = range(9)
+ GH_K_EXACT_S1, GH_K_EXACT_S2, GH_K_SYNTH, GH_K_POINTS) = range(10)
 KERNEL_KINDS = {"range_fft": 0, "doppler_fft": 1, "coord": 2, "hop_score": 3, "argmax": 4,
-                "bomp": 5, "exact_s1": 6, "exact_s2": 7, "synth": 8}
+                "bomp": 5, "exact_s1": 6, "exact_s2": 7, "synth": 8, "points": 9}
 
 
 class GhRadar(ctypes.Structure):
@@ -68,6 +68,11 @@ _SIGNATURES = {
     "gh_set_timing": (_I32, [_P, _I32]),
     "gh_set_graphs": (_I32, [_P, _I32]),
     "gh_set_detect_maps": (_I32, [_P, _I32]),
+    "gh_score_points": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, _I32, _P, ctypes.c_int64, _P]),
+    "gh_score_points_adjoint": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, _I32, _P, ctypes.c_int64,
+                                       _P, _P, _P, _P]),
+    "gh_refine_points": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, _I32, _P, ctypes.c_int64, _I32,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_double, _P]),
     "gh_kernel_stats": (_I32, [_P, _I32, _PD, ctypes.POINTER(ctypes.c_int64)]),
     "gh_reset_stats": (_I32, [_P]),
     "gh_launch_count": (ctypes.c_int64, [_P]),
@@ -282,6 +287,27 @@ class Context:
             for k in enable:
                 mask |= 1 << KERNEL_KINDS[k]
         self._check("gh_set_timing", self._lib.gh_set_timing(self.handle, int(mask)))
+
+    def gh_score_points(self, radar, tx, rx_dev, Q, maps, points, P, scores, map_dtype=GH_C64):
+        txa = _f64(tx, (2,))
+        self._check("gh_score_points", self._lib.gh_score_points(
+            self.handle, ctypes.byref(radar_struct(radar)), _ptr(txa), _ptr(rx_dev), int(Q), _ptr(maps),
+            int(map_dtype), _ptr(points), int(P), _ptr(scores)))
+
+    def gh_score_points_adjoint(self, radar, tx, rx_dev, Q, maps, points, P, dscores, dpoints=None, drx=None,
+                                dmaps=None, map_dtype=GH_C64):
+        txa = _f64(tx, (2,))
+        self._check("gh_score_points_adjoint", self._lib.gh_score_points_adjoint(
+            self.handle, ctypes.byref(radar_struct(radar)), _ptr(txa), _ptr(rx_dev), int(Q), _ptr(maps),
+            int(map_dtype), _ptr(points), int(P), _ptr(dscores), _ptr(dpoints), _ptr(drx), _ptr(dmaps)))
+
+    def gh_refine_points(self, radar, tx, rx_dev, Q, maps, points, P, iters, scale_xy, scale_v, step=1.0,
+                         scores=None, map_dtype=GH_C64):
+        txa = _f64(tx, (2,))
+        self._check("gh_refine_points", self._lib.gh_refine_points(
+            self.handle, ctypes.byref(radar_struct(radar)), _ptr(txa), _ptr(rx_dev), int(Q), _ptr(maps),
+            int(map_dtype), _ptr(points), int(P), int(iters), float(scale_xy), float(scale_v), float(step),
+            _ptr(scores)))
 
     def gh_set_detect_maps(self, map_dtype):
         """Storage type of the maps gh_detect makes for GH_HOP (GH_C64, GH_C16, GH_CBF16)."""
