@@ -309,6 +309,70 @@ def precision_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args):
     return res
 
 
+def diff_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args):
+    """Differentiation workload on the paper-shaped frame: 64 seeded candidates
+    (+-1/2 grid step around the K = 3 detections) refined by damped Newton
+    ascent in one launch, and the forward / adjoint point kernels on 2^20
+    random points of the grid (gradients to points and receivers)."""
+    from paper_2307_16550_gb300 import autograd
+    sc = scenes.paper_frame(replica_seed(rank))
+    noise = torch.from_numpy(sc.noise.astype(np.complex64)).to(device)
+    Y = ctx.synth(sc.radar, sc.tx, sc.rx, sc.targets, sc.alpha, noise)
+    cells, _, _ = ctx.gh_detect(gh.GH_HOP, sc.radar, sc.tx, sc.rx, sc.Q, Y, sc.grid, K_DETECT)
+    maps = ctx.maps(sc.radar, Y)
+    step = np.array(sc.grid.step)
+    lo = np.array(sc.grid.lo)
+    centres = np.array([lo + (np.array(np.unravel_index(c, sc.grid.n)) + 0.5) * step for c in cells])
+    rng = np.random.default_rng(11 + rank)
+    cand = centres[np.arange(64) % K_DETECT] + rng.uniform(-0.5, 0.5, (64, 4)) * step
+    rx = torch.tensor(sc.rx, dtype=torch.float64, device=device)
+    p0 = torch.tensor(cand, device=device)
+
+    def timed(fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(device)
+        return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+    iters = 20
+    pts = p0.clone()
+    S = torch.empty(64, dtype=torch.float32, device=device)
+
+    def refine():
+        pts.copy_(p0)
+        ctx.gh_refine_points(sc.radar, sc.tx, rx, sc.Q, maps, pts, 64, iters, step[0], step[2], 0.5, S)
+
+    for _ in range(args.warmup):
+        refine()
+    refine_ms = timed(refine, args.steps)
+    S0 = autograd.score_points(ctx, sc.radar, sc.tx, rx, maps, p0)
+    P = 1 << 20
+    hi = lo + step * np.array(sc.grid.n)
+    big = torch.tensor(lo + np.random.default_rng(5).uniform(0, 1, (P, 4)) * (hi - lo), device=device)
+    Sb = torch.empty(P, dtype=torch.float32, device=device)
+    gS = torch.ones(P, dtype=torch.float32, device=device)
+    dp = torch.empty_like(big)
+    drx = torch.zeros_like(rx)
+    fwd = lambda: ctx.gh_score_points(sc.radar, sc.tx, rx, sc.Q, maps, big, P, Sb)
+    adj = lambda: ctx.gh_score_points_adjoint(sc.radar, sc.tx, rx, sc.Q, maps, big, P, gS, dp, drx)
+    for _ in range(args.warmup):
+        fwd()
+        adj()
+    fwd_ms = timed(fwd, args.steps)
+    adj_ms = timed(adj, args.steps)
+    return {"workload": "paper-shaped frame: 64 candidates (+-1/2 grid step around the 3 detections) refined by "
+                        "damped Newton ascent (20 iterations, one launch); forward / adjoint on 2^20 random points",
+            "refine_ms": refine_ms, "refine_iters": iters,
+            "score_gain_median": float(torch.median(S / S0).item()),
+            "forward": {"value": P * sc.Q / (fwd_ms * 1e-3), "unit": "point·RX evals/s", "ms": fwd_ms},
+            "adjoint": {"value": P * sc.Q / (adj_ms * 1e-3), "unit": "point·RX gradient evals/s", "ms": adj_ms,
+                        "grads": "points and receiver positions"}}
+
+
 def run_ours(args):
     import torch
 
@@ -385,6 +449,7 @@ def run_ours(args):
     _barrier(world)
     wall = time.perf_counter() - t_wall
     prec = None if args.no_precision else precision_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args)
+    diff = diff_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args)
     clk = clocks.stop()
 
     value, hop_ms, _ = aggregate(world, hop_ms, evals * args.steps, device)
@@ -445,7 +510,8 @@ def run_ours(args):
                "gpu_launches": int(hop_launches + ex_launches + e2e_launches),
                "gpu_launches_per_step": {"hop": hop_launches // args.steps, "exact": ex_launches // args.steps},
                "launch": "CUDA graph of the detect sequence, replayed every step",
-               "roofline": roof, "cpu_baseline": cpu, "precision": prec, "clocks": clk,
+               "roofline": roof, "cpu_baseline": cpu, "precision": prec,
+               "differentiation": diff, "clocks": clk,
                "wall_s_timed_region": wall}
         print(json.dumps(out), flush=True)
     ctx.close()

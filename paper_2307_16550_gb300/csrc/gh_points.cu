@@ -149,18 +149,21 @@ __device__ __forceinline__ float2 contract(const float* a, const float* b, float
     return s;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+// Sum over a group of G lanes (G a power of two <= 32; butterfly, so every
+// lane of the group gets the same bits). All 32 lanes must call it.
+__device__ __forceinline__ double group_sum(double v, int G) {
+    for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-// S of one point (whole warp; every lane returns the sum over receivers).
+// S of one point, evaluated by a group of G lanes (receivers strided over the
+// group); every lane of the group returns the sum over receivers.
 template <int MT>
 __device__ double point_score(const void* maps, const PtParams& p, const double* __restrict__ rx, double x, double y,
-                              double vx, double vy) {
-    const int lane = threadIdx.x & 31;
+                              double vx, double vy, int G) {
+    const int sub = threadIdx.x & (G - 1);
     double acc = 0.0;
-    for (int q = lane; q < p.Q; q += 32) {
+    for (int q = sub; q < p.Q; q += G) {
         const PtGeo g = pt_geo(p, x, y, vx, vy, rx[2 * q], rx[2 * q + 1]);
         const Coef cr = polar(p.thr, g.tau), cd = polar(p.thd, g.sig);
         float2 V[3][3], wph[3][3];
@@ -169,19 +172,20 @@ __device__ double point_score(const void* maps, const PtParams& p, const double*
         const float2 s = contract(cr.c, cd.c, V);
         acc += (double)(s.x * s.x + s.y * s.y);
     }
-    return warp_sum(acc);
+    return group_sum(acc, G);
 }
 
-// Gradient of S of one point: dS/d(x, y, vx, vy) summed over receivers (every
-// lane returns it); per-receiver RX gradients and map gradients, scaled by gs,
-// are accumulated when drx / dmaps are non-NULL.
+// Gradient of S of one point (group of G lanes as point_score): dS/d(x, y, vx, vy)
+// summed over receivers (every lane of the group returns it); per-receiver RX
+// gradients and map gradients, scaled by gs, are accumulated when drx / dmaps
+// are non-NULL and `live` is set.
 template <int MT>
 __device__ double point_grad(const void* maps, const PtParams& p, const double* __restrict__ rx, double x, double y,
                              double vx, double vy, float gs, double* __restrict__ drx, float2* __restrict__ dmaps,
-                             double grad[4]) {
-    const int lane = threadIdx.x & 31;
+                             double grad[4], int G, bool live = true) {
+    const int sub = threadIdx.x & (G - 1);
     double acc = 0.0, gx = 0.0, gy = 0.0, gvx = 0.0, gvy = 0.0;
-    for (int q = lane; q < p.Q; q += 32) {
+    for (int q = sub; q < p.Q; q += G) {
         const PtGeo g = pt_geo(p, x, y, vx, vy, rx[2 * q], rx[2 * q + 1]);
         const Coef cr = polar(p.thr, g.tau), cd = polar(p.thd, g.sig);
         float2 V[3][3], wph[3][3];
@@ -210,11 +214,11 @@ __device__ double point_grad(const void* maps, const PtParams& p, const double* 
         gy += fr * g.wy + fe * (j1y + j2y);
         gvx += fe * g.wx;
         gvy += fe * g.wy;
-        if (drx) {
+        if (drx && live) {
             atomicAdd(&drx[2 * q], (double)gs * (-fr * g.ux2 - fe * j2x));
             atomicAdd(&drx[2 * q + 1], (double)gs * (-fr * g.uy2 - fe * j2y));
         }
-        if (dmaps) {
+        if (dmaps && live) {
             // d|s|^2 / d(stored bin) = 2 s conj(c_k d_l wph) (stored bins are 2^-s times the values)
             for (int k = 0; k < 3; ++k)
                 for (int l = 0; l < 3; ++l) {
@@ -225,39 +229,54 @@ __device__ double point_grad(const void* maps, const PtParams& p, const double* 
                 }
         }
     }
-    grad[0] = warp_sum(gx);
-    grad[1] = warp_sum(gy);
-    grad[2] = warp_sum(gvx);
-    grad[3] = warp_sum(gvy);
-    return warp_sum(acc);
+    grad[0] = group_sum(gx, G);
+    grad[1] = group_sum(gy, G);
+    grad[2] = group_sum(gvx, G);
+    grad[3] = group_sum(gvy, G);
+    return group_sum(acc, G);
 }
 
+// One group of G lanes per point (G = the power of two >= Q, at most 32).
+// Groups past the last point evaluate the last point and write nothing, so
+// that every lane takes part in the shuffles.
 template <int MT>
 __global__ void __launch_bounds__(128) points_fwd_kernel(const void* __restrict__ maps, PtParams p,
                                                         const double* __restrict__ rx,
-                                                        const double* __restrict__ pts, long long P,
+                                                        const double* __restrict__ pts, long long P, int G,
                                                         float* __restrict__ S) {
-    const long long pt = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (pt >= P) return;  // whole warps leave together
+    const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    if ((gid - (threadIdx.x & 31) / G) >= P) return;  // the warp's first point is past the end: whole warp leaves
+    const long long pt = gid < P ? gid : P - 1;
     const double* a = pts + 4 * pt;
-    const double v = point_score<MT>(maps, p, rx, a[0], a[1], a[2], a[3]);
-    if ((threadIdx.x & 31) == 0) S[pt] = (float)v;
+    const double v = point_score<MT>(maps, p, rx, a[0], a[1], a[2], a[3], G);
+    if ((threadIdx.x & (G - 1)) == 0 && gid < P) S[pt] = (float)v;
 }
 
+// Receiver gradients are summed per CTA in shared memory first (one global
+// atomic per receiver coordinate and CTA instead of one per point).
 template <int MT>
 __global__ void __launch_bounds__(128) points_adj_kernel(const void* __restrict__ maps, PtParams p,
                                                         const double* __restrict__ rx,
-                                                        const double* __restrict__ pts, long long P,
+                                                        const double* __restrict__ pts, long long P, int G,
                                                         const float* __restrict__ gS, double* __restrict__ dpts,
                                                         double* __restrict__ drx, float2* __restrict__ dmaps) {
-    const long long pt = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (pt >= P) return;
-    const double* a = pts + 4 * pt;
-    const float gs = gS[pt];
-    double grad[4];
-    point_grad<MT>(maps, p, rx, a[0], a[1], a[2], a[3], gs, drx, dmaps, grad);
-    if (dpts && (threadIdx.x & 31) == 0)
-        for (int c = 0; c < 4; ++c) dpts[4 * pt + c] = (double)gs * grad[c];
+    __shared__ double sdrx[2 * GH_MAX_Q];
+    for (int i = threadIdx.x; i < 2 * p.Q; i += blockDim.x) sdrx[i] = 0.0;
+    __syncthreads();
+    const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    if ((gid - (threadIdx.x & 31) / G) < P) {  // warp-uniform
+        const bool live = gid < P;
+        const long long pt = live ? gid : P - 1;
+        const double* a = pts + 4 * pt;
+        const float gs = gS[pt];
+        double grad[4];
+        point_grad<MT>(maps, p, rx, a[0], a[1], a[2], a[3], gs, drx ? sdrx : nullptr, dmaps, grad, G, live);
+        if (dpts && live && (threadIdx.x & (G - 1)) == 0)
+            for (int c = 0; c < 4; ++c) dpts[4 * pt + c] = (double)gs * grad[c];
+    }
+    __syncthreads();
+    if (drx)
+        for (int i = threadIdx.x; i < 2 * p.Q; i += blockDim.x) atomicAdd(&drx[i], sdrx[i]);
 }
 
 // Solves A x = b for a symmetric 4 x 4 A by Cholesky; false if A is not
@@ -309,7 +328,7 @@ __global__ void __launch_bounds__(128) refine_kernel(const void* __restrict__ ma
     double x[4] = {a[0], a[1], a[2], a[3]};
     const double sc[4] = {sx, sx, sv, sv};
     double g[4];
-    double cur = point_grad<MT>(maps, p, rx, x[0], x[1], x[2], x[3], 0.f, nullptr, nullptr, g);
+    double cur = point_grad<MT>(maps, p, rx, x[0], x[1], x[2], x[3], 0.f, nullptr, nullptr, g, 32);
     double lam = -1.0;
     for (int it = 0; it < iters; ++it) {
         double H[4][4];
@@ -319,8 +338,8 @@ __global__ void __launch_bounds__(128) refine_kernel(const void* __restrict__ ma
             xp[c] += del;
             xm[c] -= del;
             double gp[4], gm[4];
-            point_grad<MT>(maps, p, rx, xp[0], xp[1], xp[2], xp[3], 0.f, nullptr, nullptr, gp);
-            point_grad<MT>(maps, p, rx, xm[0], xm[1], xm[2], xm[3], 0.f, nullptr, nullptr, gm);
+            point_grad<MT>(maps, p, rx, xp[0], xp[1], xp[2], xp[3], 0.f, nullptr, nullptr, gp, 32);
+            point_grad<MT>(maps, p, rx, xm[0], xm[1], xm[2], xm[3], 0.f, nullptr, nullptr, gm, 32);
             for (int r = 0; r < 4; ++r) H[r][c] = (gp[r] - gm[r]) / (2.0 * del);
         }
         for (int r = 0; r < 4; ++r)
@@ -339,7 +358,7 @@ __global__ void __launch_bounds__(128) refine_kernel(const void* __restrict__ ma
             if (chol4_solve(A, g, d)) {
                 const double y0 = x[0] + d[0], y1 = x[1] + d[1], y2 = x[2] + d[2], y3 = x[3] + d[3];
                 double gy[4];
-                const double val = point_grad<MT>(maps, p, rx, y0, y1, y2, y3, 0.f, nullptr, nullptr, gy);
+                const double val = point_grad<MT>(maps, p, rx, y0, y1, y2, y3, 0.f, nullptr, nullptr, gy, 32);
                 if (val > cur) {
                     x[0] = y0;
                     x[1] = y1;
@@ -392,21 +411,29 @@ PtParams pt_params(const Dims& d, const GeoParams& g, int map_dtype) {
     return p;
 }
 
+// Lanes per point: the power of two >= Q, at most 32.
+int group_width(int Q) {
+    int G = 1;
+    while (G < Q && G < 32) G <<= 1;
+    return G;
+}
+
 }  // namespace
 
 int gh_launch_points(gh_ctx* ctx, const Dims& d, const GeoParams& g, const void* maps, int map_dtype,
                      const double* rx_dev, const double* pts, long long P, float* S) {
     if (P == 0) return GH_OK;
     const PtParams p = pt_params(d, g, map_dtype);
-    const unsigned blocks = (unsigned)((P * 32 + 127) / 128);
+    const int G = group_width(d.Q);
+    const unsigned blocks = (unsigned)((P * G + 127) / 128);
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_POINTS, &ev);
     if (map_dtype == GH_C16)
-        points_fwd_kernel<GH_C16><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, S);
+        points_fwd_kernel<GH_C16><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, G, S);
     else if (map_dtype == GH_CBF16)
-        points_fwd_kernel<GH_CBF16><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, S);
+        points_fwd_kernel<GH_CBF16><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, G, S);
     else
-        points_fwd_kernel<GH_C64><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, S);
+        points_fwd_kernel<GH_C64><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, G, S);
     return gh_launch_end(ctx, GH_K_POINTS, ev, "points_fwd_kernel");
 }
 
@@ -415,16 +442,17 @@ int gh_launch_points_adjoint(gh_ctx* ctx, const Dims& d, const GeoParams& g, con
                              double* drx, float2* dmaps) {
     if (P == 0) return GH_OK;
     const PtParams p = pt_params(d, g, map_dtype);
-    const unsigned blocks = (unsigned)((P * 32 + 127) / 128);
+    const int G = group_width(d.Q);
+    const unsigned blocks = (unsigned)((P * G + 127) / 128);
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_POINTS, &ev);
     if (map_dtype == GH_C16)
-        points_adj_kernel<GH_C16><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, gS, dpts, drx, dmaps);
+        points_adj_kernel<GH_C16><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, G, gS, dpts, drx, dmaps);
     else if (map_dtype == GH_CBF16)
-        points_adj_kernel<GH_CBF16><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, gS, dpts, drx,
+        points_adj_kernel<GH_CBF16><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, G, gS, dpts, drx,
                                                                       dmaps);
     else
-        points_adj_kernel<GH_C64><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, gS, dpts, drx, dmaps);
+        points_adj_kernel<GH_C64><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, G, gS, dpts, drx, dmaps);
     return gh_launch_end(ctx, GH_K_POINTS, ev, "points_adj_kernel");
 }
 
