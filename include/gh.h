@@ -264,6 +264,44 @@ GH_API int gh_refine_points(gh_ctx* ctx, const gh_radar* radar, const double* tx
                     double scale_v, double step, float* scores_dev);
 
 /*
+ * One frame of a batch (gh_detect_batch): the arguments of gh_detect for one
+ * measurement, with the measurement in device memory.
+ */
+typedef struct {
+    gh_radar radar;
+    double tx[2];          /* TX position (m)                                  */
+    const double* rx;      /* host double[2*Q], RX positions (m)               */
+    int32_t Q;             /* receivers, 1..GH_MAX_Q                           */
+    int32_t K;             /* BOMP iterations, 1..min(GH_MAX_K, cells)         */
+    gh_grid grid;          /* at most 2^32 - 1 cells                           */
+    const void* Y;         /* device complex float32 [Q][Mc][Ms]               */
+} gh_frame;
+
+/*
+ * gh_detect_batch - gh_detect with grid hopping (GH_HOP, complex float32
+ * maps) for nframes independent frames of any sizes, each step launched once
+ * for the whole batch (coordinate tables, maps, a persistent scorer whose
+ * warps take (frame, cells) work items from a shared counter, BOMP selection
+ * and correlation); frames whose K is reached drop out of later iterations.
+ * Each frame's results equal those of gh_detect on that frame. Outputs are
+ * concatenated in frame order:
+ *   cells_host  : host int64[sum K]
+ *   scores_host : host float[sum K] (may be NULL)
+ *   alpha_host  : host double[sum K*Q][2] (may be NULL), per frame [K][Q][2]
+ * The scorer's cells per lane and warps per CTA are chosen by timing the
+ * candidates on the first iteration of a batch shape (cached in the context),
+ * unless fixed with gh_set_batch_tuning. From the second call with an
+ * unchanged batch on, the whole sequence is a replayed CUDA graph.
+ */
+GH_API int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* frames, int64_t* cells_host,
+                    float* scores_host, double* alpha_host);
+/* Fixes the batched scorer's configuration: cells per lane in {8, 16, 32},
+ * warps per CTA in {2, 4, 8}; (0, 0) returns to autotuning (the default). */
+GH_API int gh_set_batch_tuning(gh_ctx* ctx, int32_t cells_per_lane, int32_t warps);
+/* The configuration the last gh_detect_batch call used. */
+GH_API int gh_batch_tuning(gh_ctx* ctx, int32_t* cells_per_lane, int32_t* warps);
+
+/*
  * gh_set_detect_maps - storage type (GH_C64 default, GH_C16, GH_CBF16) of the
  * range-Doppler maps gh_detect makes on the context for method GH_HOP.
  */

@@ -44,18 +44,7 @@ extern "C" const char* gh_last_error(const gh_ctx* ctx) { return ctx ? ctx->err 
 // ---------------------------------------------------------------------------
 // Device guard: makes the context's device current for the duration of a call.
 // ---------------------------------------------------------------------------
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard() {
-        int cur;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
+
 
 // ---------------------------------------------------------------------------
 // Context
@@ -104,6 +93,7 @@ extern "C" void gh_destroy(gh_ctx* ctx) {
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     gh_graph_invalidate(ctx);
+    gh_batch_release(ctx);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     for (auto& t : ctx->pending) {
         cudaEventDestroy(t.start);
@@ -646,11 +636,10 @@ static bool seen_before(gh_ctx* ctx, const std::vector<unsigned char>& key) {
 // Runs the launch sequence of one configuration (this call's results), then
 // records it into a new cache entry without running it again (evicting the
 // least recently used entry when the cache is full).
-static int record_graph(gh_ctx* ctx, const std::vector<unsigned char>& key, int32_t method, const Dims& d,
-                        const GeoParams& geo, const void* Y, int ydev, int K, void** h, GraphEntry** out) {
+static int record_graph(gh_ctx* ctx, const std::vector<unsigned char>& key, const GhSequence& seq, void** h) {
     // the plain run makes sure every buffer of this configuration exists, so
     // that the capture allocates nothing (a growth would drop all graphs)
-    GH_TRY(detect_sequence(ctx, method, d, geo, Y, ydev, K, h));
+    GH_TRY(seq(h));
     GH_CUDA(cudaStreamSynchronize(ctx->stream));
     if ((int)ctx->graph_cache.size() >= kMaxGraphs) {
         size_t lru = 0;
@@ -667,7 +656,8 @@ static int record_graph(gh_ctx* ctx, const std::vector<unsigned char>& key, int3
     GH_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeRelaxed));
     ctx->stream = ctx->capture_stream;
     ctx->capturing = true;
-    const int st = detect_sequence(ctx, method, d, geo, Y, ydev, K, h);
+    void* h2 = nullptr;
+    const int st = seq(&h2);
     ctx->capturing = false;
     ctx->stream = user_stream;
     cudaGraph_t graph = nullptr;
@@ -681,6 +671,7 @@ static int record_graph(gh_ctx* ctx, const std::vector<unsigned char>& key, int3
     ctx->launches = n0;  // the capture ran nothing; replays count their kernels
     int rc = st;
     if (rc == GH_OK && ec != cudaSuccess) rc = gh_fail_cuda(ctx, ec, "cudaStreamEndCapture", __FILE__, __LINE__);
+    if (rc == GH_OK && h2 != *h) rc = gh_fail(ctx, GH_ECUDA, "graph capture moved the result buffer");
     if (rc == GH_OK) {
         const cudaError_t ei = cudaGraphInstantiate(&e.exec, graph, 0);
         if (ei != cudaSuccess) {
@@ -695,7 +686,34 @@ static int record_graph(gh_ctx* ctx, const std::vector<unsigned char>& key, int3
     }
     e.used = ++ctx->graph_tick;
     ctx->graph_cache.push_back(std::move(e));
-    *out = &ctx->graph_cache.back();
+    return GH_OK;
+}
+
+int gh_run_sequence(gh_ctx* ctx, const std::vector<unsigned char>* key, const GhSequence& seq, void** h) {
+    GraphEntry* g = key ? find_graph(ctx, *key) : nullptr;
+    if (g) {
+        GH_CUDA(cudaGraphLaunch(g->exec, ctx->stream));
+        ctx->launches += g->launches;
+        *h = ctx->pinned;
+    } else if (key && seen_before(ctx, *key)) {
+        GH_TRY(record_graph(ctx, *key, seq, h));
+    } else {
+        GH_TRY(seq(h));
+        if (key) {
+            if (ctx->seen_keys.size() >= 4 * kMaxGraphs) ctx->seen_keys.erase(ctx->seen_keys.begin());
+            ctx->seen_keys.push_back(*key);
+        }
+    }
+    GH_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (g) {
+        for (auto& t : g->events) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess) {
+                ctx->ms[t.kind] += ms;
+                ctx->nlaunch[t.kind] += 1;
+            }
+        }
+    }
     return GH_OK;
 }
 
@@ -739,31 +757,8 @@ extern "C" int gh_detect(gh_ctx* ctx, int32_t method, const gh_radar* radar, con
         key_append(key, &ctx->detect_maps, sizeof(ctx->detect_maps));
     }
     void* h = nullptr;
-    GraphEntry* g = graphable ? find_graph(ctx, key) : nullptr;
-    if (g) {
-        GH_CUDA(cudaGraphLaunch(g->exec, ctx->stream));
-        ctx->launches += g->launches;
-        h = ctx->pinned;
-    } else if (graphable && seen_before(ctx, key)) {
-        GraphEntry* rec;
-        GH_TRY(record_graph(ctx, key, method, d, geo, Y, ydev, K, &h, &rec));
-    } else {
-        GH_TRY(detect_sequence(ctx, method, d, geo, Y, ydev, K, &h));
-        if (graphable) {
-            if (ctx->seen_keys.size() >= 4 * kMaxGraphs) ctx->seen_keys.erase(ctx->seen_keys.begin());
-            ctx->seen_keys.push_back(key);
-        }
-    }
-    GH_CUDA(cudaStreamSynchronize(ctx->stream));
-    if (g) {
-        for (auto& t : g->events) {
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess) {
-                ctx->ms[t.kind] += ms;
-                ctx->nlaunch[t.kind] += 1;
-            }
-        }
-    }
+    const GhSequence seq = [&](void** out) { return detect_sequence(ctx, method, d, geo, Y, ydev, K, out); };
+    GH_TRY(gh_run_sequence(ctx, graphable ? &key : nullptr, seq, &h));
     const size_t sel_bytes = (size_t)kResultSlots * sizeof(ArgResult);
     const ArgResult* hs = (const ArgResult*)h;
     GH_TRY(check_status(ctx, hs));

@@ -1,0 +1,472 @@
+// gh_detect_batch: the grid-hopping detect-and-deflate loop of gh_detect
+// (Sec. IV scores, BOMP iterations) over many independent frames of uneven
+// size at once. Every step is one launch for the whole batch:
+//   coordinate tables         coord_batch_kernel       (once)
+//   per iteration k:
+//     maps of the residuals   range_fft_batch_kernel, doppler_fft_batch_kernel
+//     scores + argmax         hop_batch_kernel (persistent; warps take work
+//                             items from a counter; per-frame packed argmax)
+//     selection, new atom     bomp_select_batch_kernel (one CTA per frame)
+//     correlation + solve     bomp_corr_batch_kernel
+//   results                   batch_gather_kernel + one copy to the host
+// Frames whose K is reached drop out of later iterations. Every frame runs
+// the kernels of the single-frame path on the same data in the same order, so
+// its results are those of gh_detect bit for bit.
+//
+// The scorer's cells per lane and warps per CTA are picked by timing the
+// candidates on the batch's first iteration (once per batch shape, cached in
+// the context) unless set with gh_set_batch_tuning. The whole sequence is a
+// CUDA graph from the second call with an unchanged batch on (gh_run_sequence).
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "gh_internal.cuh"
+
+namespace {
+
+constexpr int kBatchXyPerItem = 8;      // (x, y) cells per scorer work item
+constexpr int kBatchMaxFrames = 65536;
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct Plan {
+    std::vector<unsigned char> key;    // whole batch (graph key)
+    std::vector<unsigned char> shape;  // sizes only (tuning key)
+    int nframes = 0, Kmax = 0, max_q = 0, max_q_nd = 0, max_chunks = 0;
+    std::vector<int> K;                      // per frame
+    std::vector<long long> out_off;          // byte offset of each frame in the packed results
+    size_t out_bytes = 0;
+    // device pointers (inside WS_BATCH / WS_BATCH_META)
+    BatchFrame* frames = nullptr;
+    BatchItem *coord_items = nullptr, *range_items = nullptr, *dop_items = nullptr;
+    std::vector<BatchItem*> score_items;     // per k
+    std::vector<int> n_score;                // per k
+    std::vector<int*> active;                // per k
+    std::vector<int> n_active;               // per k
+    int n_coord = 0, n_range = 0, n_dop = 0;
+    size_t smem_range = 0, smem_dop = 0;
+    unsigned long long* keys = nullptr;      // all frames' keys, contiguous
+    size_t keys_bytes = 0;
+    unsigned* counter = nullptr;
+    long long* out_off_dev = nullptr;
+    void* out_dev = nullptr;
+};
+
+struct Tuning {
+    int ac = 0, warps = 0;
+};
+
+// Context-side state of the batch path (one per context).
+struct BatchState {
+    Plan plan;
+    bool plan_valid = false;
+    int force_ac = 0, force_warps = 0;
+    Tuning last;
+    std::map<std::vector<unsigned char>, Tuning> tuned;  // per batch shape
+};
+
+std::mutex g_state_mu;
+std::map<const gh_ctx*, BatchState*> g_state;
+
+BatchState* state_of(gh_ctx* ctx) {
+    std::lock_guard<std::mutex> lk(g_state_mu);
+    auto it = g_state.find(ctx);
+    if (it != g_state.end()) return it->second;
+    BatchState* s = new BatchState();
+    g_state[ctx] = s;
+    return s;
+}
+
+template <class T>
+void append(std::vector<unsigned char>& k, const T& v) {
+    const unsigned char* b = (const unsigned char*)&v;
+    k.insert(k.end(), b, b + sizeof(T));
+}
+
+int validate(gh_ctx* ctx, int nframes, const gh_frame* frames) {
+    if (nframes < 1 || nframes > kBatchMaxFrames)
+        return gh_fail(ctx, GH_EINVAL, "nframes=%d outside [1, %d]", nframes, kBatchMaxFrames);
+    if (!frames) return gh_fail(ctx, GH_EINVAL, "frames is NULL");
+    for (int f = 0; f < nframes; ++f) {
+        const gh_frame& fr = frames[f];
+        Dims d = {};
+        int st = gh_check_radar(ctx, &fr.radar, fr.Q, &d);
+        if (st == GH_OK) st = gh_check_grid(ctx, &fr.grid, &d);
+        if (st == GH_OK) st = gh_check_positions(ctx, fr.tx, fr.rx, fr.Q);
+        if (st != GH_OK) return gh_fail(ctx, st, "frame %d: %s", f, gh_last_error(ctx));
+        if (fr.K < 1 || fr.K > GH_MAX_K || fr.K > d.ncells)
+            return gh_fail(ctx, GH_EINVAL, "frame %d: K=%d outside [1, min(%d, ncells)]", f, fr.K, GH_MAX_K);
+        if (d.ncells >= ((int64_t)1 << 32))
+            return gh_fail(ctx, GH_EINVAL, "frame %d: %lld cells (at most 2^32 - 1 per frame)", f,
+                           (long long)d.ncells);
+        if (!fr.Y) return gh_fail(ctx, GH_EINVAL, "frame %d: Y is NULL", f);
+        const int dv = gh_is_device_ptr(ctx, fr.Y);
+        if (dv < 0) return dv;
+        if (!dv) return gh_fail(ctx, GH_EINVAL, "frame %d: Y must be device memory", f);
+    }
+    return GH_OK;
+}
+
+// Builds the descriptors and work items of a batch and uploads them.
+int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
+    P = Plan();
+    P.nframes = nframes;
+    std::vector<Dims> dims(nframes);
+    std::vector<GeoParams> geos(nframes);
+    for (int f = 0; f < nframes; ++f) {
+        const gh_frame& fr = frames[f];
+        GH_TRY(gh_check_radar(ctx, &fr.radar, fr.Q, &dims[f]));
+        GH_TRY(gh_check_grid(ctx, &fr.grid, &dims[f]));
+        gh_fill_geo(&geos[f], &fr.radar, fr.tx, fr.rx, fr.Q, &fr.grid);
+        P.K.push_back(fr.K);
+        P.Kmax = std::max(P.Kmax, fr.K);
+        P.max_q = std::max(P.max_q, fr.Q);
+        P.max_q_nd = std::max(P.max_q_nd, fr.Q * dims[f].Nd);
+        P.max_chunks = std::max(P.max_chunks, gh_bomp_chunks(dims[f]));
+        // graph key: everything the sequence reads from the host
+        append(P.key, fr.radar);
+        append(P.key, fr.grid);
+        append(P.key, fr.Q);
+        append(P.key, fr.K);
+        append(P.key, fr.Y);
+        P.key.insert(P.key.end(), (const unsigned char*)fr.tx, (const unsigned char*)(fr.tx + 2));
+        P.key.insert(P.key.end(), (const unsigned char*)fr.rx, (const unsigned char*)(fr.rx + 2 * fr.Q));
+        append(P.shape, fr.radar.Ms);
+        append(P.shape, fr.radar.Mc);
+        append(P.shape, fr.radar.pad);
+        append(P.shape, fr.Q);
+        append(P.shape, fr.K);
+        P.shape.insert(P.shape.end(), (const unsigned char*)fr.grid.n, (const unsigned char*)(fr.grid.n + 4));
+    }
+    // per-frame device buffers
+    std::vector<size_t> off_zr(nframes), off_maps(nframes), off_tab(nframes), off_bomp(nframes), off_mask(nframes),
+        off_sel(nframes), off_key(nframes);
+    size_t o = 0, okeys = 0;
+    for (int f = 0; f < nframes; ++f) {
+        const Dims& d = dims[f];
+        const int K = P.K[f];
+        off_zr[f] = o;
+        o += align256((size_t)d.Q * d.Mc * d.Nr * sizeof(float2));
+        off_maps[f] = o;
+        o += align256((size_t)d.Q * d.Nr * d.Nd * sizeof(float2));
+        off_tab[f] = o;
+        o += align256(gh_hop_table_bytes(d));
+        off_bomp[f] = o;
+        o += align256(gh_bomp_ws_bytes(d, K));
+        off_mask[f] = o;
+        o += align256((size_t)K * sizeof(int64_t));
+        off_sel[f] = o;
+        o += align256((size_t)K * sizeof(ArgResult));
+        off_key[f] = okeys;
+        okeys += (size_t)K * sizeof(unsigned long long);
+    }
+    const size_t keys_off = o;
+    o += align256(okeys);
+    const size_t counter_off = o;
+    o += 256;
+    void* big;
+    GH_TRY(gh_ws(ctx, WS_BATCH, o, &big));
+    char* B = (char*)big;
+    P.keys = (unsigned long long*)(B + keys_off);
+    P.keys_bytes = okeys;
+    P.counter = (unsigned*)(B + counter_off);
+
+    // twiddle tables of every transform size of the batch
+    std::map<int, size_t> tw_off;
+    size_t ntw = 0;
+    for (int f = 0; f < nframes; ++f)
+        for (int N : {dims[f].Nr, dims[f].Nd})
+            if (!tw_off.count(N)) {
+                tw_off[N] = ntw;
+                ntw += (size_t)(3 * N / 4 + 1);
+            }
+    std::vector<float2> tw(ntw);
+    for (auto& kv : tw_off) gh_twiddles(kv.first, tw.data() + kv.second);
+
+    // work items
+    std::vector<BatchItem> coord, range, dop;
+    std::vector<std::vector<BatchItem>> score(P.Kmax);
+    std::vector<std::vector<int>> active(P.Kmax);
+    for (int f = 0; f < nframes; ++f) {
+        const Dims& d = dims[f];
+        const long long ne = d.nxy * d.Q;
+        for (long long s = 0; s < ne; s += 128) coord.push_back({f, 0, s, std::min(128LL, ne - s)});
+        const int rpc = std::max(1, 2048 / d.Nr);
+        const int rows = d.Q * d.Mc;
+        for (int r = 0; r < rows; r += rpc) {
+            const int c = std::min(rpc, rows - r);
+            range.push_back({f, 0, r, c});
+            P.smem_range = std::max(P.smem_range, ((size_t)2 * c * d.Nr + 3 * d.Nr / 4) * sizeof(float2));
+        }
+        const int IB = std::min(std::min(std::max(1, 4096 / d.Nd), 16), d.Nr);
+        for (int q = 0; q < d.Q; ++q)
+            for (int i0 = 0; i0 < d.Nr; i0 += IB) dop.push_back({f, q, i0, IB});
+        P.smem_dop = std::max(P.smem_dop, ((size_t)2 * IB * (d.Nd + 1) + IB + 3 * d.Nd / 4) * sizeof(float2));
+        for (int k = 0; k < P.K[f]; ++k) {
+            active[k].push_back(f);
+            for (long long s = 0; s < d.nxy; s += kBatchXyPerItem)
+                score[k].push_back({f, 0, s, std::min((long long)kBatchXyPerItem, d.nxy - s)});
+        }
+    }
+    // packed results: per frame ArgResult[K] then double2[K][Q]
+    for (int f = 0; f < nframes; ++f) {
+        P.out_off.push_back((long long)P.out_bytes);
+        P.out_bytes += (size_t)P.K[f] * sizeof(ArgResult) + (size_t)P.K[f] * dims[f].Q * 2 * sizeof(double);
+    }
+
+    // metadata buffer: frames, items, active lists, twiddles, result offsets, packed results
+    size_t m = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = m;
+        m += align256(bytes);
+        return at;
+    };
+    const size_t m_frames = take(nframes * sizeof(BatchFrame));
+    const size_t m_coord = take(coord.size() * sizeof(BatchItem));
+    const size_t m_range = take(range.size() * sizeof(BatchItem));
+    const size_t m_dop = take(dop.size() * sizeof(BatchItem));
+    std::vector<size_t> m_score(P.Kmax), m_active(P.Kmax);
+    for (int k = 0; k < P.Kmax; ++k) {
+        m_score[k] = take(score[k].size() * sizeof(BatchItem));
+        m_active[k] = take(active[k].size() * sizeof(int));
+    }
+    const size_t m_tw = take(ntw * sizeof(float2));
+    const size_t m_outoff = take(nframes * sizeof(long long));
+    const size_t m_out = take(P.out_bytes);
+    void* meta;
+    GH_TRY(gh_ws(ctx, WS_BATCH_META, m, &meta));
+    char* M = (char*)meta;
+    // workspace pointers are final now (both slots allocated)
+    B = (char*)ctx->ws[WS_BATCH];
+    P.keys = (unsigned long long*)(B + keys_off);
+    P.counter = (unsigned*)(B + counter_off);
+
+    std::vector<unsigned char> host(m, 0);
+    auto put = [&](size_t at, const void* src, size_t bytes) {
+        if (bytes) memcpy(host.data() + at, src, bytes);
+    };
+    std::vector<BatchFrame> bf(nframes);
+    const float2* twdev = (const float2*)(M + m_tw);
+    for (int f = 0; f < nframes; ++f) {
+        BatchFrame& F = bf[f];
+        memset(&F, 0, sizeof(F));
+        F.g = geos[f];
+        F.d = dims[f];
+        gh_hop_frame_params(dims[f], geos[f], &F.hp, &F.cp);
+        void* bomp = B + off_bomp[f];
+        F.bw = gh_bomp_ptrs(bomp, dims[f], P.K[f]);
+        F.df = gh_bomp_deflate(bomp, dims[f], P.K[f], 0);
+        F.K = P.K[f];
+        F.Y = (const float2*)frames[f].Y;
+        F.zr = (float2*)(B + off_zr[f]);
+        F.maps = (float2*)(B + off_maps[f]);
+        F.table = B + off_tab[f];
+        F.mask = (int64_t*)(B + off_mask[f]);
+        F.key = (unsigned long long*)((char*)P.keys + off_key[f]);
+        F.sel = (ArgResult*)(B + off_sel[f]);
+        F.twr = twdev + tw_off[dims[f].Nr];
+        F.twd = twdev + tw_off[dims[f].Nd];
+    }
+    put(m_frames, bf.data(), nframes * sizeof(BatchFrame));
+    put(m_coord, coord.data(), coord.size() * sizeof(BatchItem));
+    put(m_range, range.data(), range.size() * sizeof(BatchItem));
+    put(m_dop, dop.data(), dop.size() * sizeof(BatchItem));
+    for (int k = 0; k < P.Kmax; ++k) {
+        put(m_score[k], score[k].data(), score[k].size() * sizeof(BatchItem));
+        put(m_active[k], active[k].data(), active[k].size() * sizeof(int));
+    }
+    put(m_tw, tw.data(), ntw * sizeof(float2));
+    put(m_outoff, P.out_off.data(), nframes * sizeof(long long));
+    GH_CUDA(cudaMemcpyAsync(meta, host.data(), m, cudaMemcpyHostToDevice, ctx->stream));
+    GH_CUDA(cudaStreamSynchronize(ctx->stream));  // host staging goes out of scope
+
+    P.frames = (BatchFrame*)(M + m_frames);
+    P.coord_items = (BatchItem*)(M + m_coord);
+    P.range_items = (BatchItem*)(M + m_range);
+    P.dop_items = (BatchItem*)(M + m_dop);
+    P.n_coord = (int)coord.size();
+    P.n_range = (int)range.size();
+    P.n_dop = (int)dop.size();
+    for (int k = 0; k < P.Kmax; ++k) {
+        P.score_items.push_back((BatchItem*)(M + m_score[k]));
+        P.n_score.push_back((int)score[k].size());
+        P.active.push_back((int*)(M + m_active[k]));
+        P.n_active.push_back((int)active[k].size());
+    }
+    P.out_off_dev = (long long*)(M + m_outoff);
+    P.out_dev = M + m_out;
+    return GH_OK;
+}
+
+// Zeroes the argmax keys and the BOMP counters of every frame.
+int reset_frames(gh_ctx* ctx, const Plan& P) {
+    GH_CUDA(cudaMemsetAsync(P.keys, 0, P.keys_bytes, ctx->stream));
+    return gh_launch_batch_reset(ctx, P.frames, P.nframes);
+}
+
+int batch_sequence(gh_ctx* ctx, const Plan& P, const Tuning& t, void** h) {
+    GH_TRY(reset_frames(ctx, P));
+    GH_TRY(gh_launch_coord_batch(ctx, P.frames, P.coord_items, P.n_coord));
+    for (int k = 0; k < P.Kmax; ++k) {
+        GH_TRY(gh_launch_maps_batch(ctx, P.frames, P.range_items, P.n_range, 0, P.smem_range, P.dop_items, P.n_dop,
+                                    P.smem_dop, k));
+        GH_TRY(gh_launch_hop_batch(ctx, P.frames, P.score_items[k], P.n_score[k], P.counter, k, t.ac, t.warps,
+                                   P.max_q_nd, P.max_q));
+        GH_TRY(gh_launch_bomp_select_batch(ctx, P.frames, P.active[k], P.n_active[k], k));
+        GH_TRY(gh_launch_bomp_corr_batch(ctx, P.frames, P.active[k], P.n_active[k], k, P.max_chunks, P.max_q));
+    }
+    GH_TRY(gh_launch_batch_gather(ctx, P.frames, P.nframes, P.out_off_dev, P.out_dev));
+    void* hp;
+    GH_TRY(gh_pinned(ctx, P.out_bytes, &hp));
+    GH_CUDA(cudaMemcpyAsync(hp, P.out_dev, P.out_bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    *h = hp;
+    return GH_OK;
+}
+
+// Times every scorer configuration that fits in shared memory on the first
+// iteration of the batch and returns the fastest.
+int autotune(gh_ctx* ctx, const Plan& P, Tuning* best) {
+    GH_TRY(reset_frames(ctx, P));
+    GH_TRY(gh_launch_coord_batch(ctx, P.frames, P.coord_items, P.n_coord));
+    GH_TRY(gh_launch_maps_batch(ctx, P.frames, P.range_items, P.n_range, 0, P.smem_range, P.dop_items, P.n_dop,
+                                P.smem_dop, 0));
+    cudaEvent_t a, b;
+    GH_CUDA(cudaEventCreate(&a));
+    GH_CUDA(cudaEventCreate(&b));
+    float best_ms = 1e30f;
+    *best = Tuning();
+    int st = GH_OK;
+    for (int ac : {8, 16, 32})
+        for (int warps : {8, 4, 2}) {
+            if (gh_hop_batch_warp_bytes(ac, P.max_q_nd, P.max_q) * warps > ctx->smem_optin) continue;
+            for (int rep = 0; rep < 2 && st == GH_OK; ++rep) {  // first launch warms up
+                cudaEventRecord(a, ctx->stream);
+                st = gh_launch_hop_batch(ctx, P.frames, P.score_items[0], P.n_score[0], P.counter, 0, ac, warps,
+                                         P.max_q_nd, P.max_q);
+                cudaEventRecord(b, ctx->stream);
+            }
+            if (st != GH_OK) break;
+            float ms = 0.f;
+            if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+                st = gh_fail(ctx, GH_ECUDA, "autotune timing failed");
+                break;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best->ac = ac;
+                best->warps = warps;
+            }
+        }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st == GH_OK && best->ac == 0) st = gh_fail(ctx, GH_ENOTSUP, "batched scorer: frames too large for shared memory");
+    return st;
+}
+
+}  // namespace
+
+extern "C" int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* frames, int64_t* cells_host,
+                               float* scores_host, double* alpha_host) {
+    if (!ctx) return GH_EINVAL;
+    if (!cells_host) return gh_fail(ctx, GH_EINVAL, "cells_host is NULL");
+    DeviceGuard dg(ctx->device);
+    GH_TRY(validate(ctx, nframes, frames));
+    BatchState* S = state_of(ctx);
+    // the plan (descriptors, items) is rebuilt when the batch changes
+    std::vector<unsigned char> key;
+    for (int f = 0; f < nframes; ++f) {
+        const gh_frame& fr = frames[f];
+        append(key, fr.radar);
+        append(key, fr.grid);
+        append(key, fr.Q);
+        append(key, fr.K);
+        append(key, fr.Y);
+        key.insert(key.end(), (const unsigned char*)fr.tx, (const unsigned char*)(fr.tx + 2));
+        key.insert(key.end(), (const unsigned char*)fr.rx, (const unsigned char*)(fr.rx + 2 * fr.Q));
+    }
+    const bool same = S->plan_valid && S->plan.key == key && ctx->ws[WS_BATCH] && ctx->ws[WS_BATCH_META];
+    if (!same) {
+        S->plan_valid = false;
+        GH_TRY(build_plan(ctx, nframes, frames, S->plan));
+        S->plan_valid = true;
+    }
+    Plan& P = S->plan;
+    Tuning t;
+    if (S->force_ac) {
+        t.ac = S->force_ac;
+        t.warps = S->force_warps;
+    } else {
+        auto it = S->tuned.find(P.shape);
+        if (it == S->tuned.end()) {
+            GH_TRY(autotune(ctx, P, &t));
+            S->tuned[P.shape] = t;
+        } else {
+            t = it->second;
+        }
+    }
+    S->last = t;
+    // graph key: the batch, the scorer configuration and the timing mask
+    std::vector<unsigned char> gkey = P.key;
+    append(gkey, t.ac);
+    append(gkey, t.warps);
+    append(gkey, ctx->timing);
+    const char tag[] = "batch";
+    gkey.insert(gkey.begin(), tag, tag + sizeof(tag));
+    void* h = nullptr;
+    const GhSequence seq = [&](void** out) { return batch_sequence(ctx, P, t, out); };
+    GH_TRY(gh_run_sequence(ctx, ctx->graphs ? &gkey : nullptr, seq, &h));
+    // unpack: per frame ArgResult[K] then double2[K][Q]
+    size_t oc = 0, oa = 0;
+    for (int f = 0; f < nframes; ++f) {
+        const unsigned char* base = (const unsigned char*)h + P.out_off[f];
+        const ArgResult* sel = (const ArgResult*)base;
+        const double* al = (const double*)(sel + P.K[f]);
+        for (int k = 0; k < P.K[f]; ++k) {
+            if (!sel[k].valid) return gh_fail(ctx, GH_ECUDA, "frame %d: iteration %d selected no cell", f, k);
+            cells_host[oc + k] = sel[k].cell;
+            if (scores_host) scores_host[oc + k] = sel[k].score;
+        }
+        if (alpha_host) memcpy(alpha_host + oa, al, (size_t)P.K[f] * frames[f].Q * 2 * sizeof(double));
+        oc += P.K[f];
+        oa += (size_t)P.K[f] * frames[f].Q * 2;
+    }
+    return GH_OK;
+}
+
+extern "C" int gh_set_batch_tuning(gh_ctx* ctx, int32_t cells_per_lane, int32_t warps) {
+    if (!ctx) return GH_EINVAL;
+    if (cells_per_lane == 0 && warps == 0) {
+        state_of(ctx)->force_ac = 0;
+        return GH_OK;
+    }
+    if ((cells_per_lane != 8 && cells_per_lane != 16 && cells_per_lane != 32) ||
+        (warps != 2 && warps != 4 && warps != 8))
+        return gh_fail(ctx, GH_EINVAL, "tuning (%d, %d): cells per lane in {8, 16, 32}, warps in {2, 4, 8}",
+                       cells_per_lane, warps);
+    BatchState* S = state_of(ctx);
+    S->force_ac = cells_per_lane;
+    S->force_warps = warps;
+    return GH_OK;
+}
+
+extern "C" int gh_batch_tuning(gh_ctx* ctx, int32_t* cells_per_lane, int32_t* warps) {
+    if (!ctx || !cells_per_lane || !warps) return GH_EINVAL;
+    const BatchState* S = state_of(ctx);
+    *cells_per_lane = S->last.ac;
+    *warps = S->last.warps;
+    return GH_OK;
+}
+
+void gh_batch_release(gh_ctx* ctx) {
+    std::lock_guard<std::mutex> lk(g_state_mu);
+    auto it = g_state.find(ctx);
+    if (it != g_state.end()) {
+        delete it->second;
+        g_state.erase(it);
+    }
+}

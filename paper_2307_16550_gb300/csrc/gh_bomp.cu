@@ -54,13 +54,6 @@ BompLayout bomp_layout(const Dims& d, int K) {
     return L;
 }
 
-struct BompPtrs {
-    double2 *alpha, *corr, *ru, *phase, *corrp;
-    double* gram;
-    float2 *atoms_a, *atoms_b;
-    unsigned int* counter;
-    int chunks;
-};
 
 BompPtrs bomp_ptrs(void* ws, const Dims& d, int K) {
     const BompLayout L = bomp_layout(d, K);
@@ -100,31 +93,16 @@ __device__ __forceinline__ void better(float s, long long c, float& bs, long lon
     }
 }
 
-// One CTA of 1024 threads.
-__global__ void __launch_bounds__(1024) bomp_select_kernel(const ArgPartial* __restrict__ parts, int nparts,
-                                                           ArgResult* __restrict__ sel, int64_t* __restrict__ mask,
-                                                           int k, int K, GeoParams g, BompPtrs w) {
-    __shared__ float s_bs[32];
-    __shared__ long long s_bc[32];
+// Second half of a selection (one CTA of 1024 threads): thread 0 holds the
+// best (score, cell) of iteration k; writes sel[k] and mask[k] and prepares
+// the new atom at every receiver: (r, u) in float64, its centring phase, row
+// k of the Gram matrices and the atom tables.
+__device__ void bomp_select_body(float best, long long bestc, ArgResult* __restrict__ sel,
+                                 int64_t* __restrict__ mask, int k, int K, const GeoParams& g, const BompPtrs& w) {
     __shared__ long long s_cell;
     __shared__ unsigned long long s_rf[GH_MAX_Q], s_uf[GH_MAX_Q];
     __shared__ double s_r[GH_MAX_Q], s_u[GH_MAX_Q];
-    float best = -INFINITY;
-    long long bestc = 0x7fffffffffffffffLL;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) better(parts[i].score, parts[i].cell, best, bestc);
-    for (int off = 16; off > 0; off >>= 1) {
-        const float os = __shfl_down_sync(0xffffffffu, best, off);
-        const long long oc = __shfl_down_sync(0xffffffffu, bestc, off);
-        better(os, oc, best, bestc);
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        s_bs[warp] = best;
-        s_bc[warp] = bestc;
-    }
-    __syncthreads();
     if (threadIdx.x == 0) {
-        for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) better(s_bs[ww], s_bc[ww], best, bestc);
         const bool valid = bestc != 0x7fffffffffffffffLL;
         sel[k].cell = bestc;
         sel[k].score = best;
@@ -174,6 +152,46 @@ __global__ void __launch_bounds__(1024) bomp_select_kernel(const ArgPartial* __r
         const int qq = idx / g.Mc, m = idx - qq * g.Mc;
         w.atoms_b[((size_t)k * g.Q + qq) * g.Mc + m] = gh_cis_fix(s_uf[qq] * (unsigned long long)m);
     }
+}
+
+
+// One CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) bomp_select_kernel(const ArgPartial* __restrict__ parts, int nparts,
+                                                           ArgResult* __restrict__ sel, int64_t* __restrict__ mask,
+                                                           int k, int K, GeoParams g, BompPtrs w) {
+    __shared__ float s_bs[32];
+    __shared__ long long s_bc[32];
+    float best = -INFINITY;
+    long long bestc = 0x7fffffffffffffffLL;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) better(parts[i].score, parts[i].cell, best, bestc);
+    for (int off = 16; off > 0; off >>= 1) {
+        const float os = __shfl_down_sync(0xffffffffu, best, off);
+        const long long oc = __shfl_down_sync(0xffffffffu, bestc, off);
+        better(os, oc, best, bestc);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s_bs[warp] = best;
+        s_bc[warp] = bestc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) better(s_bs[ww], s_bc[ww], best, bestc);
+    bomp_select_body(best, bestc, sel, mask, k, K, g, w);
+}
+
+// Batched selection: one CTA per listed frame, best cell from the frame's key.
+__global__ void __launch_bounds__(1024) bomp_select_batch_kernel(const BatchFrame* __restrict__ frames,
+                                                                 const int* __restrict__ active, int k) {
+    const BatchFrame& F = frames[active[blockIdx.x]];
+    const unsigned long long key = F.key[k];
+    float best = -INFINITY;
+    long long bestc = 0x7fffffffffffffffLL;
+    if (key != 0ull) {
+        best = __uint_as_float((unsigned)(key >> 32));
+        bestc = (long long)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull));
+    }
+    bomp_select_body(best, bestc, F.sel, F.mask, k, F.K, F.g, F.bw);
 }
 
 // Float64 normal equations of atoms 0..n-1 of receiver q (Cholesky, dependent
@@ -234,10 +252,10 @@ __device__ void bomp_solve_q(int q, int Q, int Ms, int Mc, int n, int K, const d
 }
 
 // CTA (chunk, q): partial <Y_q, b(u) (x) a(r)> over kCorrRows chirps. The last
-// CTA to finish sums the partials and solves every receiver's least squares.
-__global__ void __launch_bounds__(256) bomp_corr_kernel(const float2* __restrict__ Y, GeoParams g, int k, int K,
-                                                        BompPtrs w) {
-    const int ch = blockIdx.x, q = blockIdx.y;
+// of the frame's `total` CTAs to finish sums the partials and solves every
+// receiver's least squares.
+__device__ void bomp_corr_body(const float2* __restrict__ Y, const GeoParams& g, int k, int K, const BompPtrs& w,
+                               int ch, int q, unsigned total) {
     const float2* a = w.atoms_a + ((size_t)k * g.Q + q) * g.Ms;
     const float2* b = w.atoms_b + ((size_t)k * g.Q + q) * g.Mc;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -275,7 +293,6 @@ __global__ void __launch_bounds__(256) bomp_corr_kernel(const float2* __restrict
         }
         w.corrp[((size_t)k * g.Q + q) * w.chunks + ch] = make_double2(tx, ty);
         __threadfence();
-        const unsigned int total = gridDim.x * gridDim.y;
         s_last = atomicAdd(w.counter, 1u) == total - 1;
     }
     __syncthreads();
@@ -294,6 +311,35 @@ __global__ void __launch_bounds__(256) bomp_corr_kernel(const float2* __restrict
         bomp_solve_q(qq, g.Q, g.Ms, g.Mc, k + 1, K, w.corr, w.phase, w.gram, w.alpha);
     }
     if (threadIdx.x == 0) *w.counter = 0u;  // ready for the next iteration
+}
+
+
+__global__ void __launch_bounds__(256) bomp_corr_kernel(const float2* __restrict__ Y, GeoParams g, int k, int K,
+                                                        BompPtrs w) {
+    bomp_corr_body(Y, g, k, K, w, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
+}
+
+// Batched correlations: grid (max chunks, max Q, listed frames).
+__global__ void __launch_bounds__(256) bomp_corr_batch_kernel(const BatchFrame* __restrict__ frames,
+                                                              const int* __restrict__ active, int k) {
+    const BatchFrame& F = frames[active[blockIdx.z]];
+    if ((int)blockIdx.x >= F.bw.chunks || (int)blockIdx.y >= F.g.Q) return;
+    bomp_corr_body(F.Y, F.g, k, F.K, F.bw, blockIdx.x, blockIdx.y, (unsigned)F.bw.chunks * (unsigned)F.g.Q);
+}
+
+__global__ void batch_reset_kernel(const BatchFrame* __restrict__ frames) {
+    if (threadIdx.x == 0) *frames[blockIdx.x].bw.counter = 0u;
+}
+
+// Packs frame f's selections (ArgResult [K]) and amplitudes (double2 [K][Q])
+// at byte offset offsets[f] of out; one CTA per frame.
+__global__ void batch_gather_kernel(const BatchFrame* __restrict__ frames, const long long* __restrict__ offsets,
+                                    unsigned char* __restrict__ out) {
+    const BatchFrame& F = frames[blockIdx.x];
+    ArgResult* s = (ArgResult*)(out + offsets[blockIdx.x]);
+    double2* a = (double2*)(s + F.K);
+    for (int i = threadIdx.x; i < F.K; i += blockDim.x) s[i] = F.sel[i];
+    for (int i = threadIdx.x; i < F.K * F.g.Q; i += blockDim.x) a[i] = F.bw.alpha[i];
 }
 
 __global__ void __launch_bounds__(256) residual_kernel(const float2* __restrict__ Y, int Q, int Ms, int Mc,
@@ -395,4 +441,38 @@ int gh_launch_synth(gh_ctx* ctx, const Dims& d, const GeoParams& g, int T, const
     gh_launch_begin(ctx, GH_K_SYNTH, &ev);
     synth_kernel<<<dim3(bx, d.Q), 256, 0, ctx->stream>>>(g, T, tgt, noise, Y);
     return gh_launch_end(ctx, GH_K_SYNTH, ev, "synth_kernel");
+}
+
+int gh_launch_bomp_select_batch(gh_ctx* ctx, const BatchFrame* frames, const int* active, int n, int k) {
+    if (n == 0) return GH_OK;
+    cudaEvent_t ev;
+    gh_launch_begin(ctx, GH_K_ARGMAX, &ev);
+    bomp_select_batch_kernel<<<n, 1024, 0, ctx->stream>>>(frames, active, k);
+    return gh_launch_end(ctx, GH_K_ARGMAX, ev, "bomp_select_batch_kernel");
+}
+
+int gh_launch_bomp_corr_batch(gh_ctx* ctx, const BatchFrame* frames, const int* active, int n, int k, int max_chunks,
+                              int max_q) {
+    if (n == 0) return GH_OK;
+    cudaEvent_t ev;
+    gh_launch_begin(ctx, GH_K_BOMP, &ev);
+    bomp_corr_batch_kernel<<<dim3(max_chunks, max_q, n), 32 * kCorrRows, 0, ctx->stream>>>(frames, active, k);
+    return gh_launch_end(ctx, GH_K_BOMP, ev, "bomp_corr_batch_kernel");
+}
+
+int gh_launch_batch_gather(gh_ctx* ctx, const BatchFrame* frames, int nframes, const long long* offsets, void* out) {
+    cudaEvent_t ev;
+    gh_launch_begin(ctx, GH_K_BOMP, &ev);
+    batch_gather_kernel<<<nframes, 128, 0, ctx->stream>>>(frames, offsets, (unsigned char*)out);
+    return gh_launch_end(ctx, GH_K_BOMP, ev, "batch_gather_kernel");
+}
+
+BompPtrs gh_bomp_ptrs(void* ws, const Dims& d, int K) { return bomp_ptrs(ws, d, K); }
+int gh_bomp_chunks(const Dims& d) { return (d.Mc + kCorrRows - 1) / kCorrRows; }
+
+int gh_launch_batch_reset(gh_ctx* ctx, const BatchFrame* frames, int nframes) {
+    cudaEvent_t ev;
+    gh_launch_begin(ctx, GH_K_BOMP, &ev);
+    batch_reset_kernel<<<nframes, 32, 0, ctx->stream>>>(frames);
+    return gh_launch_end(ctx, GH_K_BOMP, ev, "batch_reset_kernel");
 }

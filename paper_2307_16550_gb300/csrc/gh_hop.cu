@@ -59,19 +59,11 @@ struct __align__(16) HopEntry {
 };
 static_assert(sizeof(HopEntry) == 80, "HopEntry layout");
 
-struct CoordParams {
-    float theta_f;               // polar half-arc angle theta
-    float inv_sin2_half;         // 1 / sin^2(theta / 2)
-    float inv_sin_t;             // 1 / sin(theta)
-    int Ms_odd_sign;             // 1 if (Ms - 1) is odd (wrap flips the sign)
-    uint32_t tol;                // hop_tol(nvx, nvy)
-};
 
-__global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__ table, int32_t* diag_i,
-                             double* diag_tau, float* diag_c, double* diag_w) {
-    const long long nxy = (long long)g.n[0] * g.n[1];
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nxy * g.Q) return;
+// Entry idx = xy * Q + q of the coordinate table (diagnostics optional).
+__device__ __forceinline__ void coord_entry(const GeoParams& g, const CoordParams& cp, long long idx,
+                                            HopEntry* __restrict__ table, int32_t* diag_i, double* diag_tau,
+                                            float* diag_c, double* diag_w) {
     const int q = (int)(idx % g.Q);
     const long long xy = idx / g.Q;
     const int ix = (int)(xy / g.n[1]);
@@ -139,15 +131,22 @@ __global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__
     }
 }
 
-struct HopParams {
-    int Q, Nr, Nd, nvx, nvy;
-    float cscale;         // 2^s of reduced-precision maps (folded into the polar coefficients)
-    int NB, SA;           // lane mapping: b = lane % NB (stride NB), a = lane / NB (stride SA)
-    uint32_t tol2;        // 2 * tol
-    long long nxy, nv;
-    long long xy_per_cta;
-    double lo2, step2, lo3, step3, kappa;
-};
+__global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__ table, int32_t* diag_i,
+                             double* diag_tau, float* diag_c, double* diag_w) {
+    const long long nxy = (long long)g.n[0] * g.n[1];
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nxy * g.Q) return;
+    coord_entry(g, cp, idx, table, diag_i, diag_tau, diag_c, diag_w);
+}
+
+// Batched tables: item = (frame, first entry, count <= blockDim.x).
+__global__ void coord_batch_kernel(const BatchFrame* __restrict__ frames, const BatchItem* __restrict__ items) {
+    const BatchItem it = items[blockIdx.x];
+    if (threadIdx.x >= it.count) return;
+    const BatchFrame& F = frames[it.frame];
+    coord_entry(F.g, F.cp, it.start + threadIdx.x, (HopEntry*)F.table, nullptr, nullptr, nullptr, nullptr);
+}
+
 
 // Exact float64 Doppler bin of cell (a, b), unwrapped.
 __device__ __noinline__ long long slow_bin(double wx, double wy, int a, int b, double lo2, double step2, double lo3,
@@ -185,6 +184,137 @@ __device__ __forceinline__ float4 load_pair(const void* row, int jh) {
     }
 }
 
+// Scores every velocity cell of the (x, y) cell `xy` with one warp: builds the
+// Doppler power rows P_q of the receivers in the warp's shared memory, then
+// each lane sums the rows at its cells' Doppler bins; merges the best unmasked
+// cell into (best, bestc). P, E and fix are the warp's shared-memory areas.
+template <int AC, int MT>
+__device__ __forceinline__ void score_xy(const void* __restrict__ maps, const HopEntry* __restrict__ table,
+                                         const HopParams& p, float* __restrict__ scores,
+                                         const int64_t* __restrict__ mask, int nmask, long long xy, float* P,
+                                         HopEntry* E, float* fix, int lane, int tb, int ta, bool active, float& best,
+                                         long long& bestc) {
+    const int ndm = p.Nd - 1;
+    const int ewords = p.Q * (int)(sizeof(HopEntry) / 8);
+    __syncwarp();  // the previous cell's reads of P and E are done
+    {
+        const long long* src = (const long long*)(table + xy * p.Q);
+        long long* dst = (long long*)E;
+        for (int w = lane; w < ewords; w += 32) dst[w] = __ldg(src + w);
+    }
+    __syncwarp();
+    for (int q = 0; q < p.Q; ++q) {
+        const HopEntry& eq = E[q];
+        const int j_ref = eq.j_ref, npair = eq.npair;
+        const float c0 = eq.cs[0] * p.cscale, c1 = eq.cs[1] * p.cscale, c2 = eq.cs[2] * p.cscale;
+        const size_t qb = (size_t)q * p.Nr;
+        constexpr size_t BB = MT == GH_C64 ? 8 : 4;  // bytes per bin
+        const char* r0 = (const char*)maps + (qb + eq.row[0]) * p.Nd * BB;
+        const char* r1 = (const char*)maps + (qb + eq.row[1]) * p.Nd * BB;
+        const char* r2 = (const char*)maps + (qb + eq.row[2]) * p.Nd * BB;
+        float* Pq = P + (size_t)q * p.Nd;
+        constexpr int U = GH_HOP_U;  // row loads in flight per lane
+        for (int pp0 = 0; pp0 < npair; pp0 += 32 * U) {
+            float4 z0[U], z1[U], z2[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int pp = pp0 + lane + 32 * u;
+                if (pp < npair) {
+                    const int jh = ((j_ref + 2 * pp) & ndm) >> 1;  // pair of absolute bins
+                    z0[u] = load_pair<MT>(r0, jh);
+                    z1[u] = load_pair<MT>(r1, jh);
+                    z2[u] = load_pair<MT>(r2, jh);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int pp = pp0 + lane + 32 * u;
+                if (pp < npair) {
+                    const float re0 = c0 * z0[u].x + c1 * z1[u].x + c2 * z2[u].x;
+                    const float im0 = c0 * z0[u].y + c1 * z1[u].y + c2 * z2[u].y;
+                    const float re1 = c0 * z0[u].z + c1 * z1[u].z + c2 * z2[u].z;
+                    const float im1 = c0 * z0[u].w + c1 * z1[u].w + c2 * z2[u].w;
+                    *(float2*)(Pq + 2 * pp) = make_float2(re0 * re0 + im0 * im0, re1 * re1 + im1 * im1);
+                }
+            }
+        }
+    }
+    bool hm = false;
+    for (int m = 0; m < nmask; ++m) hm |= (__ldg(&mask[m]) / p.nv == xy);
+    __syncwarp();  // P rows complete
+    if (!active) return;
+    const long long cbase = xy * p.nv;
+    for (int b = tb; b < p.nvy; b += p.NB) {
+        for (int a0 = ta; a0 < p.nvx; a0 += p.SA * AC) {
+            float acc[AC];
+#pragma unroll
+            for (int i = 0; i < AC; ++i) acc[i] = 0.f;
+            for (int q = 0; q < p.Q; ++q) {
+                const HopEntry& eq = E[q];
+                const long long t0 = eq.base + (long long)b * eq.by + (long long)a0 * eq.ax;
+                const long long st = (long long)p.SA * eq.ax;
+                const float* Pq = P + (size_t)q * p.Nd;
+                // Entries of cells on the grid lie in [0, Nd) (wrapping mod Nd only
+                // when the grid reaches Nd or more bins). Cells of a partial run
+                // past the grid's edge are read and discarded; the mask keeps
+                // those reads inside the receiver's row as well.
+                const int imask = ndm;
+                long long t = t0;
+                bool amb = false;
+                {
+#pragma unroll
+                    for (int i = 0; i < AC; ++i) {
+                        amb |= (uint32_t)t < p.tol2;
+                        acc[i] += Pq[(int)(t >> 32) & imask];
+                        t += st;
+                    }
+                }
+                if (amb) {
+                    // rare: a bin decision within tol of a rounding boundary;
+                    // replace the fast bin by the float64 one for those cells
+                    // (corrections go through shared memory so that the
+                    // float64 path keeps the accumulators in registers)
+                    t = t0;
+#pragma unroll 1
+                    for (int i = 0; i < AC; ++i) {
+                        float dlt = 0.f;
+                        if ((uint32_t)t < p.tol2) {
+                            const int fast = (int)(t >> 32) & imask;
+                            const long long j = slow_bin(eq.wx, eq.wy, a0 + i * p.SA, b, p.lo2, p.step2, p.lo3,
+                                                         p.step3, p.kappa, p.Nd);
+                            const int exact = (int)(j - eq.j_ref) & imask;
+                            if (exact != fast) dlt = Pq[exact] - Pq[fast];
+                        }
+                        fix[i] = dlt;
+                        t += st;
+                    }
+#pragma unroll
+                    for (int i = 0; i < AC; ++i) acc[i] += fix[i];
+                }
+            }
+            // best of this run (cells in increasing index order), then merge
+            float rb = -INFINITY;
+            int ri = -1;
+            const bool full = a0 + (AC - 1) * p.SA < p.nvx;
+#pragma unroll
+            for (int i = 0; i < AC; ++i) {
+                if (full || a0 + i * p.SA < p.nvx) {
+                    const long long cell = cbase + (long long)(a0 + i * p.SA) * p.nvy + b;
+                    if (scores) scores[cell] = acc[i];
+                    bool masked = false;
+                    if (hm)
+                        for (int m = 0; m < nmask; ++m) masked |= (__ldg(&mask[m]) == cell);
+                    if (!masked && acc[i] > rb) {
+                        rb = acc[i];
+                        ri = i;
+                    }
+                }
+            }
+            if (ri >= 0) better(rb, cbase + (long long)(a0 + ri * p.SA) * p.nvy + b, best, bestc);
+        }
+    }
+}
+
 // AC: velocity cells per lane per pass (along vx, stride SA); MT: map storage type.
 template <int AC, int MT>
 __global__ void __launch_bounds__(256, GH_HOP_MINB) hop_score_kernel(const void* __restrict__ maps,
@@ -197,7 +327,6 @@ __global__ void __launch_bounds__(256, GH_HOP_MINB) hop_score_kernel(const void*
     __shared__ long long s_bc[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int W = blockDim.x >> 5;
-    const int ndm = p.Nd - 1;
     const size_t warp_bytes =
         (size_t)p.Q * p.Nd * sizeof(float) + (size_t)p.Q * sizeof(HopEntry) + (size_t)32 * AC * sizeof(float);
     float* P = (float*)(smem_hop + warp * warp_bytes);
@@ -211,123 +340,10 @@ __global__ void __launch_bounds__(256, GH_HOP_MINB) hop_score_kernel(const void*
     const long long xy0 = (long long)blockIdx.x * p.xy_per_cta;
     long long xy1 = xy0 + p.xy_per_cta;
     if (xy1 > p.nxy) xy1 = p.nxy;
-    const int ewords = p.Q * (int)(sizeof(HopEntry) / 8);
     for (long long xy = xy0 + warp; xy < xy1; xy += W) {
-        __syncwarp();  // the previous cell's reads of P and E are done
-        {
-            const long long* src = (const long long*)(table + xy * p.Q);
-            long long* dst = (long long*)E;
-            for (int w = lane; w < ewords; w += 32) dst[w] = __ldg(src + w);
-        }
-        __syncwarp();
-        for (int q = 0; q < p.Q; ++q) {
-            const HopEntry& eq = E[q];
-            const int j_ref = eq.j_ref, npair = eq.npair;
-            const float c0 = eq.cs[0] * p.cscale, c1 = eq.cs[1] * p.cscale, c2 = eq.cs[2] * p.cscale;
-            const size_t qb = (size_t)q * p.Nr;
-            constexpr size_t BB = MT == GH_C64 ? 8 : 4;  // bytes per bin
-            const char* r0 = (const char*)maps + (qb + eq.row[0]) * p.Nd * BB;
-            const char* r1 = (const char*)maps + (qb + eq.row[1]) * p.Nd * BB;
-            const char* r2 = (const char*)maps + (qb + eq.row[2]) * p.Nd * BB;
-            float* Pq = P + (size_t)q * p.Nd;
-            constexpr int U = GH_HOP_U;  // row loads in flight per lane
-            for (int pp0 = 0; pp0 < npair; pp0 += 32 * U) {
-                float4 z0[U], z1[U], z2[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int pp = pp0 + lane + 32 * u;
-                    if (pp < npair) {
-                        const int jh = ((j_ref + 2 * pp) & ndm) >> 1;  // pair of absolute bins
-                        z0[u] = load_pair<MT>(r0, jh);
-                        z1[u] = load_pair<MT>(r1, jh);
-                        z2[u] = load_pair<MT>(r2, jh);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int pp = pp0 + lane + 32 * u;
-                    if (pp < npair) {
-                        const float re0 = c0 * z0[u].x + c1 * z1[u].x + c2 * z2[u].x;
-                        const float im0 = c0 * z0[u].y + c1 * z1[u].y + c2 * z2[u].y;
-                        const float re1 = c0 * z0[u].z + c1 * z1[u].z + c2 * z2[u].z;
-                        const float im1 = c0 * z0[u].w + c1 * z1[u].w + c2 * z2[u].w;
-                        *(float2*)(Pq + 2 * pp) = make_float2(re0 * re0 + im0 * im0, re1 * re1 + im1 * im1);
-                    }
-                }
-            }
-        }
-        bool hm = false;
-        for (int m = 0; m < nmask; ++m) hm |= (__ldg(&mask[m]) / p.nv == xy);
-        __syncwarp();  // P rows complete
-        if (!active) continue;
-        const long long cbase = xy * p.nv;
-        for (int b = tb; b < p.nvy; b += p.NB) {
-            for (int a0 = ta; a0 < p.nvx; a0 += p.SA * AC) {
-                float acc[AC];
-#pragma unroll
-                for (int i = 0; i < AC; ++i) acc[i] = 0.f;
-                for (int q = 0; q < p.Q; ++q) {
-                    const HopEntry& eq = E[q];
-                    const long long t0 = eq.base + (long long)b * eq.by + (long long)a0 * eq.ax;
-                    const long long st = (long long)p.SA * eq.ax;
-                    const float* Pq = P + (size_t)q * p.Nd;
-                    // entries wrap mod Nd only in the rare case of a grid reaching >= Nd bins
-                    const int imask = eq.wrap ? ndm : -1;
-                    long long t = t0;
-                    bool amb = false;
-                    {
-#pragma unroll
-                        for (int i = 0; i < AC; ++i) {
-                            amb |= (uint32_t)t < p.tol2;
-                            acc[i] += Pq[(int)(t >> 32) & imask];
-                            t += st;
-                        }
-                    }
-                    if (amb) {
-                        // rare: a bin decision within tol of a rounding boundary;
-                        // replace the fast bin by the float64 one for those cells
-                        // (corrections go through shared memory so that the
-                        // float64 path keeps the accumulators in registers)
-                        t = t0;
-#pragma unroll 1
-                        for (int i = 0; i < AC; ++i) {
-                            float dlt = 0.f;
-                            if ((uint32_t)t < p.tol2) {
-                                const int fast = (int)(t >> 32) & imask;
-                                const long long j = slow_bin(eq.wx, eq.wy, a0 + i * p.SA, b, p.lo2, p.step2, p.lo3,
-                                                             p.step3, p.kappa, p.Nd);
-                                const int exact = (int)(j - eq.j_ref) & imask;
-                                if (exact != fast) dlt = Pq[exact] - Pq[fast];
-                            }
-                            fix[i] = dlt;
-                            t += st;
-                        }
-#pragma unroll
-                        for (int i = 0; i < AC; ++i) acc[i] += fix[i];
-                    }
-                }
-                // best of this run (cells in increasing index order), then merge
-                float rb = -INFINITY;
-                int ri = -1;
-                const bool full = a0 + (AC - 1) * p.SA < p.nvx;
-#pragma unroll
-                for (int i = 0; i < AC; ++i) {
-                    if (full || a0 + i * p.SA < p.nvx) {
-                        const long long cell = cbase + (long long)(a0 + i * p.SA) * p.nvy + b;
-                        if (scores) scores[cell] = acc[i];
-                        bool masked = false;
-                        if (hm)
-                            for (int m = 0; m < nmask; ++m) masked |= (__ldg(&mask[m]) == cell);
-                        if (!masked && acc[i] > rb) {
-                            rb = acc[i];
-                            ri = i;
-                        }
-                    }
-                }
-                if (ri >= 0) better(rb, cbase + (long long)(a0 + ri * p.SA) * p.nvy + b, best, bestc);
-            }
-        }
+        score_xy<AC, MT>(maps, table, p, scores, mask, nmask, xy, P, E, fix, lane, tb, ta, active, best, bestc);
     }
+
 
     for (int off = 16; off > 0; off >>= 1) {
         const float os = __shfl_down_sync(0xffffffffu, best, off);
@@ -459,6 +475,86 @@ int hop_launch(cudaStream_t stream, const Dims& d, HopParams hp, const void* map
                                        smem_optin, nparts);
     return hop_launch_mt<GH_C64>(stream, d, hp, maps, table, scores, mask, nmask, parts, max_ctas, num_sms,
                                  smem_optin, nparts);
+}
+
+// Persistent batched scorer (complex float32 maps): each warp takes work items
+// (frame, first (x, y) cell, count) from *counter until none is left, scores
+// the item's cells with score_xy and folds the item's best unmasked cell into
+// the frame's key[k] = score bits << 32 | (2^32 - 1 - cell) (largest key: best
+// score, then smallest cell). The warp's shared-memory area holds a copy of
+// the frame's scorer parameters, its power rows, entries and corrections.
+template <int AC>
+__global__ void __launch_bounds__(256, GH_HOP_MINB) hop_batch_kernel(const BatchFrame* __restrict__ frames,
+                                                          const BatchItem* __restrict__ items, int nitems,
+                                                          unsigned* __restrict__ counter, int k,
+                                                          int per_warp_bytes) {
+    extern __shared__ __align__(16) unsigned char smem_hop[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* base = smem_hop + (size_t)warp * per_warp_bytes;
+    HopParams& p = *(HopParams*)base;
+    constexpr int kParamBytes = (int)((sizeof(HopParams) + 15) & ~(size_t)15);
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = (int)atomicAdd(counter, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= nitems) break;
+        const BatchItem item = items[it];
+        const BatchFrame& F = frames[item.frame];
+        __syncwarp();  // the previous item's reads of p are done
+        {
+            const int* src = (const int*)&F.hp;
+            int* dst = (int*)&p;
+            for (int w = lane; w < (int)(sizeof(HopParams) / 4); w += 32) dst[w] = src[w];
+        }
+        __syncwarp();
+        float* P = (float*)(base + kParamBytes);
+        HopEntry* E = (HopEntry*)(P + (size_t)p.Q * p.Nd);
+        float* fix = (float*)(E + p.Q) + lane * AC;
+        const int tb = lane % p.NB, ta = lane / p.NB;
+        const bool active = ta < p.SA;
+        float best = -INFINITY;
+        long long bestc = 0x7fffffffffffffffLL;
+        for (long long xy = item.start; xy < item.start + item.count; ++xy)
+            score_xy<AC, GH_C64>(F.maps, (const HopEntry*)F.table, p, nullptr, F.mask, k, xy, P, E, fix, lane, tb, ta,
+                                 active, best, bestc);
+        for (int off = 16; off > 0; off >>= 1) {
+            const float os = __shfl_down_sync(0xffffffffu, best, off);
+            const long long oc = __shfl_down_sync(0xffffffffu, bestc, off);
+            better(os, oc, best, bestc);
+        }
+        if (lane == 0 && bestc != 0x7fffffffffffffffLL) {
+            const unsigned long long key =
+                ((unsigned long long)__float_as_uint(best) << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)bestc);
+            atomicMax(&F.key[k], key);
+        }
+    }
+}
+
+// Shared memory of one batched-scorer warp for frames with Q * Nd <= max_q_nd.
+size_t hop_batch_warp_bytes(int ac, int max_q_nd, int max_q) {
+    const size_t b = ((sizeof(HopParams) + 15) & ~(size_t)15) + (size_t)max_q_nd * sizeof(float) +
+                     (size_t)max_q * sizeof(HopEntry) + (size_t)32 * ac * sizeof(float);
+    return (b + 15) & ~(size_t)15;
+}
+
+template <int AC>
+int hop_batch_launch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* items, int n, unsigned* counter, int k,
+                     int warps, int max_q_nd, int max_q) {
+    const size_t per_warp = hop_batch_warp_bytes(AC, max_q_nd, max_q);
+    const size_t smem = per_warp * warps;
+    if (smem > ctx->smem_optin) return gh_fail(ctx, GH_ENOTSUP, "batched scorer: %zu bytes of shared memory", smem);
+    GH_CUDA(cudaFuncSetAttribute(hop_batch_kernel<AC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GH_CUDA(cudaFuncSetAttribute(hop_batch_kernel<AC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
+    int per_sm = 0;
+    GH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_batch_kernel<AC>, 32 * warps, smem));
+    if (per_sm < 1) per_sm = 1;
+    GH_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), ctx->stream));
+    cudaEvent_t ev;
+    gh_launch_begin(ctx, GH_K_HOP_SCORE, &ev);
+    hop_batch_kernel<AC><<<ctx->num_sms * per_sm, 32 * warps, smem, ctx->stream>>>(frames, items, n, counter, k,
+                                                                                  (int)per_warp);
+    return gh_launch_end(ctx, GH_K_HOP_SCORE, ev, "hop_batch_kernel");
 }
 
 double dirichlet_closed(double f, int M) {
@@ -618,3 +714,27 @@ extern "C" int gh_score_grid_noalloc(void* stream_ptr, const gh_radar* radar, co
     }
     return GH_OK;
 }
+
+void gh_hop_frame_params(const Dims& d, const GeoParams& g, HopParams* hp, CoordParams* cp) {
+    *hp = hop_params(d, g);
+    *cp = coord_params(d);
+}
+
+int gh_launch_coord_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* items, int n) {
+    if (n == 0) return GH_OK;
+    cudaEvent_t ev;
+    gh_launch_begin(ctx, GH_K_COORD, &ev);
+    coord_batch_kernel<<<n, 128, 0, ctx->stream>>>(frames, items);
+    return gh_launch_end(ctx, GH_K_COORD, ev, "coord_batch_kernel");
+}
+
+int gh_launch_hop_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* items, int n, unsigned* counter,
+                        int k, int ac, int warps, int max_q_nd, int max_q) {
+    if (n == 0) return GH_OK;
+    if (ac == 8) return hop_batch_launch<8>(ctx, frames, items, n, counter, k, warps, max_q_nd, max_q);
+    if (ac == 16) return hop_batch_launch<16>(ctx, frames, items, n, counter, k, warps, max_q_nd, max_q);
+    if (ac == 32) return hop_batch_launch<32>(ctx, frames, items, n, counter, k, warps, max_q_nd, max_q);
+    return gh_fail(ctx, GH_EINVAL, "batched scorer: cells per lane %d not in {8, 16, 32}", ac);
+}
+
+size_t gh_hop_batch_warp_bytes(int ac, int max_q_nd, int max_q) { return hop_batch_warp_bytes(ac, max_q_nd, max_q); }

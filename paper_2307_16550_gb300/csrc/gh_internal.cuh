@@ -7,6 +7,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <functional>
 #include <vector>
 
 #include "../../include/gh.h"
@@ -30,6 +31,8 @@ enum WsSlot {
     WS_TWIDDLE,     // FFT twiddle tables
     WS_EXACT_TAB,   // exact-path phase table [nxy][Q]
     WS_EXACT_B,     // stage-1 split-BF16 tiles of Y
+    WS_BATCH,       // per-frame buffers of gh_detect_batch
+    WS_BATCH_META,  // batch descriptors, work items, twiddles, packed results
     WS_COUNT
 };
 
@@ -99,8 +102,33 @@ int gh_fail(gh_ctx* ctx, int status, const char* fmt, ...);
         if (s_ != GH_OK) return s_;  \
     } while (0)
 
+// Makes a device current for the scope of an entry point.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Frees the batch planner state of a context (gh_batch.cu).
+void gh_batch_release(gh_ctx* ctx);
+
 // Drops the cached gh_detect graph (its kernels hold workspace pointers).
 void gh_graph_invalidate(gh_ctx* ctx);
+
+// A launch sequence on ctx->stream that ends with an asynchronous copy of its
+// results into the context's pinned buffer and sets *h to that buffer.
+using GhSequence = std::function<int(void**)>;
+// Runs seq eagerly, records it into a CUDA graph (second call with the same
+// key) or replays the recorded graph (later calls); key NULL: always eager.
+// Synchronises the stream and adds the replay's kernel timers.
+int gh_run_sequence(gh_ctx* ctx, const std::vector<unsigned char>* key, const GhSequence& seq, void** h);
 
 // Grow-only workspace slot; returns GH_OK and sets *p.
 int gh_ws(gh_ctx* ctx, WsSlot slot, size_t bytes, void** p);
@@ -123,6 +151,38 @@ struct Dims {
     int Q, Ms, Mc, pad, Nr, Nd;
     int nx, ny, nvx, nvy;
     int64_t nxy, nv, ncells;
+};
+
+// ---------------------------------------------------------------------------
+// Kernel parameter blocks shared by the single-frame and batched launches
+// ---------------------------------------------------------------------------
+// Hopping scorer (gh_hop.cu).
+struct HopParams {
+    int Q, Nr, Nd, nvx, nvy;
+    float cscale;         // 2^s of reduced-precision maps (folded into the polar coefficients)
+    int NB, SA;           // lane mapping: b = lane % NB (stride NB), a = lane / NB (stride SA)
+    uint32_t tol2;        // 2 * tol
+    long long nxy, nv;
+    long long xy_per_cta;
+    double lo2, step2, lo3, step3, kappa;
+};
+
+// Coordinate table (gh_hop.cu).
+struct CoordParams {
+    float theta_f;               // polar half-arc angle theta
+    float inv_sin2_half;         // 1 / sin^2(theta / 2)
+    float inv_sin_t;             // 1 / sin(theta)
+    int Ms_odd_sign;             // 1 if (Ms - 1) is odd (wrap flips the sign)
+    uint32_t tol;                // hop_tol(nvx, nvy)
+};
+
+// BOMP workspace pointers (gh_bomp.cu).
+struct BompPtrs {
+    double2 *alpha, *corr, *ru, *phase, *corrp;
+    double* gram;
+    float2 *atoms_a, *atoms_b;
+    unsigned int* counter;
+    int chunks;
 };
 
 // Map storage: bytes per bin and the power-of-two scale exponent s of the
@@ -251,6 +311,7 @@ __device__ __forceinline__ float2 gh_deflate(const Deflate& f, int Q, int Ms, in
     return y;
 }
 
+
 // ---------------------------------------------------------------------------
 // Per-kernel launchers (one per .cu file)
 // ---------------------------------------------------------------------------
@@ -267,7 +328,63 @@ struct ArgResult {
     int32_t valid;
 };
 
+// ---------------------------------------------------------------------------
+// Batches of frames (gh_detect_batch): one device-resident descriptor per frame
+// and work items that name a frame and a range of its rows, columns or cells.
+// ---------------------------------------------------------------------------
+struct BatchFrame {
+    GeoParams g;
+    Dims d;
+    HopParams hp;
+    CoordParams cp;
+    BompPtrs bw;
+    Deflate df;                 // atoms of the frame's BOMP workspace (n set per iteration)
+    int K;
+    const float2* Y;            // [Q][Mc][Ms]
+    float2* zr;                 // range-FFT intermediate [Q][Mc][Nr]
+    float2* maps;               // [Q][Nr][Nd]
+    void* table;                // hopping coordinate table [nxy][Q]
+    int64_t* mask;              // [K] selected cells
+    unsigned long long* key;    // [K] packed argmax: score bits << 32 | (2^32 - 1 - cell)
+    ArgResult* sel;             // [K]
+    const float2* twr;          // exp(-j 2 pi t / Nr), t < 3 Nr / 4
+    const float2* twd;          // exp(-j 2 pi t / Nd), t < 3 Nd / 4
+};
+
+struct BatchItem {
+    int frame;
+    int aux;          // FFT items: receiver q (Doppler) / unused
+    long long start;  // first row, range bin or (x, y) cell
+    long long count;
+};
+
 int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* df, void* maps, int map_dtype);
+// exp(-j 2 pi t / N), t < 3N/4, rounded from float64 (the FFT twiddle table).
+void gh_twiddles(int N, float2* out);
+// Batched maps (iteration k's residual applied on load); items as built by gh_batch.cu.
+int gh_launch_maps_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* range_items, int n_range,
+                         int rows_alloc, size_t smem_range, const BatchItem* dop_items, int n_dop, size_t smem_dop,
+                         int k);
+// Scorer and coordinate-table parameters of one frame.
+void gh_hop_frame_params(const Dims& d, const GeoParams& g, HopParams* hp, CoordParams* cp);
+size_t gh_hop_batch_warp_bytes(int ac, int max_q_nd, int max_q);
+// Batched coordinate tables (items: frame, first (x, y, q) entry, count <= 128).
+int gh_launch_coord_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* items, int n);
+// Persistent batched scorer: warps take items (frame, first (x, y) cell, count)
+// from *counter (zeroed here) and fold each frame's best cell into key[k].
+int gh_launch_hop_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* items, int n, unsigned* counter,
+                        int k, int ac, int warps, int max_q_nd, int max_q);
+// Batched BOMP selection and correlation of iteration k for the listed frames.
+int gh_launch_bomp_select_batch(gh_ctx* ctx, const BatchFrame* frames, const int* active, int n, int k);
+int gh_launch_bomp_corr_batch(gh_ctx* ctx, const BatchFrame* frames, const int* active, int n, int k, int max_chunks,
+                              int max_q);
+// BOMP workspace pointers of one frame and its correlation chunk count.
+BompPtrs gh_bomp_ptrs(void* ws, const Dims& d, int K);
+int gh_bomp_chunks(const Dims& d);
+// Zeroes every frame's BOMP counter (one CTA per frame).
+int gh_launch_batch_reset(gh_ctx* ctx, const BatchFrame* frames, int nframes);
+// Packs every frame's selections and amplitudes into out (see gh_batch.cu).
+int gh_launch_batch_gather(gh_ctx* ctx, const BatchFrame* frames, int nframes, const long long* offsets, void* out);
 int gh_launch_coord(gh_ctx* ctx, const Dims& d, const GeoParams& g, void* table,
                     int32_t* diag_i, double* diag_tau, float* diag_c, double* diag_w);
 size_t gh_hop_table_bytes(const Dims& d);

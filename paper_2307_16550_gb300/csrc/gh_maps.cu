@@ -92,17 +92,14 @@ __device__ void load_twiddles(float2* dst, const float2* __restrict__ src, int n
     for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = __ldg(src + t);
 }
 
-__global__ void __launch_bounds__(256) range_fft_kernel(const float2* __restrict__ Y, float2* __restrict__ out,
-                                                        int Q, int Ms, int Mc, int logNr, int rows,
-                                                        int rows_per_cta, Deflate df,
-                                                        const float2* __restrict__ tw) {
-    extern __shared__ float2 smem[];
+// Range FFTs of rows r0 .. r0 + nrow - 1 (row = q * Mc + mc) of one frame.
+__device__ __forceinline__ void range_rows(const float2* __restrict__ Y, float2* __restrict__ out, int Q, int Ms,
+                                           int Mc, int logNr, int r0, int nrow, int rows_alloc, const Deflate& df,
+                                           const float2* __restrict__ tw, float2* smem) {
     const int Nr = 1 << logNr;
-    const int r0 = blockIdx.x * rows_per_cta;
-    const int nrow = min(rows_per_cta, rows - r0);
     float2* x = smem;
-    float2* y = smem + rows_per_cta * Nr;
-    float2* twS = y + rows_per_cta * Nr;
+    float2* y = smem + rows_alloc * Nr;
+    float2* twS = y + rows_alloc * Nr;
     load_twiddles(twS, tw, 3 * Nr / 4);
     for (int idx = threadIdx.x; idx < nrow * Nr; idx += blockDim.x) {
         const int c = idx >> logNr;
@@ -120,6 +117,15 @@ __global__ void __launch_bounds__(256) range_fft_kernel(const float2* __restrict
     for (int idx = threadIdx.x; idx < nrow * Nr; idx += blockDim.x) out[(size_t)r0 * Nr + idx] = res[idx];
 }
 
+__global__ void __launch_bounds__(256) range_fft_kernel(const float2* __restrict__ Y, float2* __restrict__ out,
+                                                        int Q, int Ms, int Mc, int logNr, int rows,
+                                                        int rows_per_cta, Deflate df,
+                                                        const float2* __restrict__ tw) {
+    extern __shared__ float2 smem[];
+    const int r0 = blockIdx.x * rows_per_cta;
+    range_rows(Y, out, Q, Ms, Mc, logNr, r0, min(rows_per_cta, rows - r0), rows_per_cta, df, tw, smem);
+}
+
 // One map bin in storage type MT (float32 pair, or 2^-s times the value
 // rounded to nearest-even float16 / bfloat16).
 template <int MT>
@@ -133,16 +139,15 @@ __device__ __forceinline__ void store_bin(void* maps, size_t idx, float2 v, floa
     }
 }
 
+// Doppler FFTs of range bins i0 .. i0 + IB - 1 of receiver q of one frame,
+// times the range-centring factor, stored in type MT.
 template <int MT>
-__global__ void __launch_bounds__(256) doppler_fft_kernel(const float2* __restrict__ Zr, void* __restrict__ maps,
-                                                          int Ms, int Mc, int logNr, int logNd, int IB,
-                                                          const float2* __restrict__ tw, float oscale) {
-    extern __shared__ float2 smem[];
+__device__ __forceinline__ void doppler_cols(const float2* __restrict__ Zr, void* __restrict__ maps, int Ms, int Mc,
+                                             int logNr, int logNd, int IB, int q, int i0,
+                                             const float2* __restrict__ tw, float oscale, float2* smem) {
     const int Nr = 1 << logNr;
     const int Nd = 1 << logNd;
     const int ld = Nd + 1;
-    const int q = blockIdx.y;
-    const int i0 = blockIdx.x * IB;
     float2* x = smem;
     float2* y = smem + IB * ld;
     float2* ramp = y + IB * ld;
@@ -176,6 +181,55 @@ __global__ void __launch_bounds__(256) doppler_fft_kernel(const float2* __restri
     }
 }
 
+template <int MT>
+__global__ void __launch_bounds__(256) doppler_fft_kernel(const float2* __restrict__ Zr, void* __restrict__ maps,
+                                                          int Ms, int Mc, int logNr, int logNd, int IB,
+                                                          const float2* __restrict__ tw, float oscale) {
+    extern __shared__ float2 smem[];
+    doppler_cols<MT>(Zr, maps, Ms, Mc, logNr, logNd, IB, blockIdx.y, blockIdx.x * IB, tw, oscale, smem);
+}
+
+// Batched maps of several frames: one work item (frame, first row / range
+// bin, count) per CTA; the residual of iteration k is applied on load.
+__global__ void __launch_bounds__(256) range_fft_batch_kernel(const BatchFrame* __restrict__ frames,
+                                                              const BatchItem* __restrict__ items, int k,
+                                                              int rows_alloc) {
+    extern __shared__ float2 smem[];
+    const BatchItem it = items[blockIdx.x];
+    const BatchFrame& F = frames[it.frame];
+    Deflate df = F.df;
+    df.n = k;
+    int logNr = 0;
+    while ((1 << logNr) < F.d.Nr) ++logNr;
+    (void)rows_alloc;
+    range_rows(F.Y, F.zr, F.d.Q, F.d.Ms, F.d.Mc, logNr, (int)it.start, (int)it.count, (int)it.count, df, F.twr,
+               smem);
+}
+
+__global__ void __launch_bounds__(256) doppler_fft_batch_kernel(const BatchFrame* __restrict__ frames,
+                                                                const BatchItem* __restrict__ items) {
+    extern __shared__ float2 smem[];
+    const BatchItem it = items[blockIdx.x];
+    const BatchFrame& F = frames[it.frame];
+    int logNr = 0, logNd = 0;
+    while ((1 << logNr) < F.d.Nr) ++logNr;
+    while ((1 << logNd) < F.d.Nd) ++logNd;
+    doppler_cols<GH_C64>(F.zr, F.maps, F.d.Ms, F.d.Mc, logNr, logNd, (int)it.count, it.aux, (int)it.start, F.twd,
+                         1.0f, smem);
+}
+
+}  // namespace
+
+void gh_twiddles(int N, float2* out) {
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int t = 0; t < 3 * N / 4; ++t) {
+        const double a = -two_pi * (double)t / (double)N;
+        out[t] = make_float2((float)cos(a), (float)sin(a));
+    }
+}
+
+namespace {
+
 int ilog2(int v) {
     int l = 0;
     while ((1 << l) < v) ++l;
@@ -192,15 +246,8 @@ int ensure_twiddles(gh_ctx* ctx, int Nr, int Nd, const float2** twr, const float
         if (ctx->capturing) return gh_fail(ctx, GH_ECUDA, "twiddle upload during graph capture");
         gh_graph_invalidate(ctx);  // cached graphs read the old tables
         std::vector<float2> h(nr + nd);
-        const double two_pi = 6.283185307179586476925286766559;
-        for (int t = 0; t < nr; ++t) {
-            double a = -two_pi * (double)t / (double)Nr;
-            h[t] = make_float2((float)cos(a), (float)sin(a));
-        }
-        for (int t = 0; t < nd; ++t) {
-            double a = -two_pi * (double)t / (double)Nd;
-            h[nr + t] = make_float2((float)cos(a), (float)sin(a));
-        }
+        gh_twiddles(Nr, h.data());
+        gh_twiddles(Nd, h.data() + nr);
         GH_CUDA(cudaMemcpyAsync(p, h.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
         GH_CUDA(cudaStreamSynchronize(ctx->stream));  // h goes out of scope
         ctx->tw_n[0] = Nr;
@@ -247,4 +294,26 @@ int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* d
     kern<<<dim3(d.Nr / IB, d.Q), 256, smem2, ctx->stream>>>((const float2*)zr, maps, d.Ms, d.Mc, logNr, logNd, IB,
                                                             twd, oscale);
     return gh_launch_end(ctx, GH_K_DOPPLER_FFT, ev, "doppler_fft_kernel");
+}
+
+int gh_launch_maps_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* range_items, int n_range,
+                         int rows_alloc, size_t smem_range, const BatchItem* dop_items, int n_dop, size_t smem_dop,
+                         int k) {
+    if (n_range > 0) {
+        GH_CUDA(cudaFuncSetAttribute(range_fft_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_range));
+        cudaEvent_t ev;
+        gh_launch_begin(ctx, GH_K_RANGE_FFT, &ev);
+        range_fft_batch_kernel<<<n_range, 256, smem_range, ctx->stream>>>(frames, range_items, k, rows_alloc);
+        GH_TRY(gh_launch_end(ctx, GH_K_RANGE_FFT, ev, "range_fft_batch_kernel"));
+    }
+    if (n_dop > 0) {
+        GH_CUDA(cudaFuncSetAttribute(doppler_fft_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_dop));
+        cudaEvent_t ev;
+        gh_launch_begin(ctx, GH_K_DOPPLER_FFT, &ev);
+        doppler_fft_batch_kernel<<<n_dop, 256, smem_dop, ctx->stream>>>(frames, dop_items);
+        GH_TRY(gh_launch_end(ctx, GH_K_DOPPLER_FFT, ev, "doppler_fft_batch_kernel"));
+    }
+    return GH_OK;
 }

@@ -37,6 +37,11 @@ class GhGrid(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_double * 4), ("step", ctypes.c_double * 4), ("n", ctypes.c_int32 * 4)]
 
 
+class GhFrame(ctypes.Structure):
+    _fields_ = [("radar", GhRadar), ("tx", ctypes.c_double * 2), ("rx", ctypes.POINTER(ctypes.c_double)),
+                ("Q", ctypes.c_int32), ("K", ctypes.c_int32), ("grid", GhGrid), ("Y", ctypes.c_void_p)]
+
+
 class GhError(RuntimeError):
     def __init__(self, func, status, detail):
         super().__init__(f"{func} failed: {status} ({gh_status_str(status)}): {detail}")
@@ -68,6 +73,9 @@ _SIGNATURES = {
     "gh_set_timing": (_I32, [_P, _I32]),
     "gh_set_graphs": (_I32, [_P, _I32]),
     "gh_set_detect_maps": (_I32, [_P, _I32]),
+    "gh_detect_batch": (_I32, [_P, _I32, _P, _P, _P, _P]),
+    "gh_set_batch_tuning": (_I32, [_P, _I32, _I32]),
+    "gh_batch_tuning": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "gh_score_points": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, _I32, _P, ctypes.c_int64, _P]),
     "gh_score_points_adjoint": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, _I32, _P, ctypes.c_int64,
                                        _P, _P, _P, _P]),
@@ -308,6 +316,46 @@ class Context:
             self.handle, ctypes.byref(radar_struct(radar)), _ptr(txa), _ptr(rx_dev), int(Q), _ptr(maps),
             int(map_dtype), _ptr(points), int(P), int(iters), float(scale_xy), float(scale_v), float(step),
             _ptr(scores)))
+
+    def gh_detect_batch(self, frames):
+        """frames: list of (radar, tx, rx, Q, Y_dev, grid, K). Returns per frame
+        (cells int64[K], scores float32[K], alpha complex128[K][Q])."""
+        n = len(frames)
+        arr = (GhFrame * n)()
+        keep = []
+        total_k = sum(int(f[6]) for f in frames)
+        total_a = sum(int(f[6]) * int(f[3]) for f in frames)
+        for i, (radar, tx, rx, Q, Y, grid, K) in enumerate(frames):
+            rxa = _f64(rx, (-1,))
+            keep.append(rxa)
+            fr = arr[i]
+            fr.radar = radar_struct(radar)
+            fr.tx[0], fr.tx[1] = float(tx[0]), float(tx[1])
+            fr.rx = rxa.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            fr.Q = int(Q)
+            fr.K = int(K)
+            fr.grid = grid_struct(grid)
+            fr.Y = _ptr(Y)
+        cells = np.zeros(total_k, np.int64)
+        scores = np.zeros(total_k, np.float32)
+        alpha = np.zeros((total_a, 2), np.float64)
+        self._check("gh_detect_batch", self._lib.gh_detect_batch(self.handle, n, ctypes.cast(arr, _P), _ptr(cells),
+                                                                 _ptr(scores), _ptr(alpha)))
+        out, oc, oa = [], 0, 0
+        for (_, _, _, Q, _, _, K) in frames:
+            a = alpha[oa:oa + K * Q]
+            out.append((cells[oc:oc + K], scores[oc:oc + K], (a[:, 0] + 1j * a[:, 1]).reshape(K, Q)))
+            oc += K
+            oa += K * Q
+        return out
+
+    def gh_set_batch_tuning(self, cells_per_lane=0, warps=0):
+        self._check("gh_set_batch_tuning", self._lib.gh_set_batch_tuning(self.handle, int(cells_per_lane), int(warps)))
+
+    def gh_batch_tuning(self):
+        a, w = _I32(0), _I32(0)
+        self._check("gh_batch_tuning", self._lib.gh_batch_tuning(self.handle, ctypes.byref(a), ctypes.byref(w)))
+        return a.value, w.value
 
     def gh_set_detect_maps(self, map_dtype):
         """Storage type of the maps gh_detect makes for GH_HOP (GH_C64, GH_C16, GH_CBF16)."""

@@ -23,6 +23,10 @@ f0 = 24 GHz, B = 250 MHz, Tc = 128 us, Ms = Mc = 128, four receivers):
   [0, 40]^2 m x [-15, 15]^2 m/s, K = 3 detections.
 * ``precision_scene``: Q = 8, Ms = 512 x Mc = 256, five targets at SNR 5 dB,
   grid 256 x 256 x 64 x 64.
+* ``batch_scenes``: many frames of uneven size (Q in 3..8, Ms in
+  {128, 256, 512}, Mc in {64, 128, 256}, (x, y) sides in {64, 96, 128, 160},
+  velocity sides in {16, 24, 32, 40}, 1..5 targets at SNR 0..20 dB), or a
+  small variant with the same spread for the oracle.
 """
 from __future__ import annotations
 
@@ -36,7 +40,7 @@ _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 
 # Stream identifiers: one independent stream per kind of draw.
-_S_RX, _S_TGT_POS, _S_TGT_VEL, _S_AMP, _S_PHASE, _S_NOISE, _S_ONGRID = range(1, 8)
+_S_RX, _S_TGT_POS, _S_TGT_VEL, _S_AMP, _S_PHASE, _S_NOISE, _S_ONGRID, _S_BATCH = range(1, 9)
 
 
 def _mix64(z: np.ndarray) -> np.ndarray:
@@ -271,3 +275,28 @@ def custom_scene(seed: int, radar: Radar, grid: Grid, Q: int, T: int,
     alpha = _rayleigh_alpha(seed, T, Q)
     return Scene("custom", seed, radar, np.zeros(2), rx, tg, alpha,
                  _noise(seed, Q, radar, snr_db), grid, T, snr_db, cells)
+
+
+def batch_scenes(seed: int, n: int, small: bool = False):
+    """n frames of uneven size; frame i uses seed (seed * 100003 + i) for its
+    own draws. ``small`` scales the sizes down (Ms in {32, 64}, Mc in {16, 32},
+    (x, y) sides in {8, 12, 16}, velocity sides in {4, 6, 8}) so that the FP64
+    oracle can score every frame."""
+    u = uniform(seed, _S_BATCH, 8 * n).reshape(n, 8)
+    pick = lambda opts, v: opts[min(int(v * len(opts)), len(opts) - 1)]
+    frames = []
+    for i in range(n):
+        Q = 3 + min(int(u[i, 0] * 6), 5)
+        if small:
+            Ms, Mc = pick((32, 64), u[i, 1]), pick((16, 32), u[i, 2])
+            nxy, nv = pick((8, 12, 16), u[i, 3]), pick((4, 6, 8), u[i, 4])
+        else:
+            Ms, Mc = pick((128, 256, 512), u[i, 1]), pick((64, 128, 256), u[i, 2])
+            nxy, nv = pick((64, 96, 128, 160), u[i, 3]), pick((16, 24, 32, 40), u[i, 4])
+        T = 1 + min(int(u[i, 5] * 5), 4)
+        snr = 20.0 * u[i, 6]
+        radar = Radar(24e9, 250e6, 128e-6, Ms, Mc, 4)
+        grid = Grid.from_bounds((0, 0, -15, -15), (40, 40, 15, 15), (nxy, nxy, nv, nv))
+        sc = custom_scene(seed * 100003 + i, radar, grid, Q=Q, T=T, snr_db=snr)
+        frames.append(replace(sc, name="batch"))
+    return frames

@@ -42,6 +42,9 @@ def test_null_context_is_rejected(lib):
     assert lib.gh_set_timing(None, 1) == gh.GH_EINVAL
     assert lib.gh_reset_stats(None) == gh.GH_EINVAL
     assert lib.gh_launch_count(None) == -1
+    assert lib.gh_detect_batch(None, 1, None, None, None, None) == gh.GH_EINVAL
+    assert lib.gh_score_points(None, r, None, None, 1, None, 0, None, 0, None) == gh.GH_EINVAL
+    assert lib.gh_set_batch_tuning(None, 8, 4) == gh.GH_EINVAL
     lib.gh_destroy(None)
     assert lib.gh_create(None, 0, None) == gh.GH_EINVAL
 
@@ -49,3 +52,22 @@ def test_null_context_is_rejected(lib):
 def test_struct_layouts_match_header(lib):
     assert ctypes.sizeof(gh.GhRadar) == 3 * 8 + 4 * 4
     assert ctypes.sizeof(gh.GhGrid) == 8 * 8 + 4 * 4
+
+
+def test_struct_sizes_agree_with_the_c_compiler(tmp_path):
+    """sizeof of the ABI structs as gcc lays them out from include/gh.h."""
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include "gh.h"\n'
+                   'int main(void) { printf("%zu %zu %zu\\n", sizeof(gh_radar), sizeof(gh_grid), '
+                   'sizeof(gh_frame)); return 0; }\n')
+    exe = tmp_path / "sizes"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert [int(v) for v in out] == [ctypes.sizeof(gh.GhRadar), ctypes.sizeof(gh.GhGrid), ctypes.sizeof(gh.GhFrame)]
