@@ -373,6 +373,55 @@ def diff_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args):
                         "grads": "points and receiver positions"}}
 
 
+def batch_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args):
+    """Batching workload: 256 frames of uneven size (Q 3..8, Ms 128..512,
+    Mc 64..256, grids 64^2 x 16^2 .. 160^2 x 40^2, 1..5 targets at SNR
+    0..20 dB, K = targets) detected by one gh_detect_batch call per step (a
+    replayed CUDA graph of batched launches, persistent scorer), against the
+    same frames detected one gh_detect call after another."""
+    frames = scenes.batch_scenes(1 + rank, 256)
+    dev = []
+    for sc in frames:
+        noise = torch.from_numpy(sc.noise.astype(np.complex64)).to(device)
+        Y = ctx.synth(sc.radar, sc.tx, sc.rx, sc.targets, sc.alpha, noise)
+        dev.append((sc.radar, sc.tx, sc.rx, sc.Q, Y, sc.grid, sc.K))
+        sc.noise = None  # host copy no longer needed
+    units = sum(sc.K * sc.grid.ncells * sc.Q for sc in frames)
+
+    def timed(fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(device)
+        return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+    batched = lambda: ctx.gh_detect_batch(dev)
+    for _ in range(max(args.warmup, 3)):
+        batched()
+    ms_batch = timed(batched, args.steps)
+    tuning = ctx.gh_batch_tuning()
+
+    def one_by_one():
+        for (radar, tx, rx, Q, Y, grid, K) in dev:
+            ctx.gh_detect(gh.GH_HOP, radar, tx, rx, Q, Y, grid, K)
+
+    steps_seq = max(1, min(args.steps, 3))
+    for _ in range(2):
+        one_by_one()
+    ms_seq = timed(one_by_one, steps_seq)
+    maps_gb = sum(sc.Q * sc.radar.pad ** 2 * sc.radar.Ms * sc.radar.Mc * 8 for sc in frames) / 1e9
+    return {"workload": "256 frames of uneven size: Q 3..8, Ms 128..512, Mc 64..256, grids 64^2x16^2 .. "
+                        "160^2x40^2, 1..5 targets at SNR 0..20 dB, K = targets",
+            "value": units / (ms_batch * 1e-3), "unit": UNIT, "ms_per_step": ms_batch,
+            "evals_per_step": units, "maps_gb": maps_gb,
+            "tuning": {"cells_per_lane": tuning[0], "warps_per_cta": tuning[1]},
+            "one_by_one": {"value": units / (ms_seq * 1e-3), "ms_per_step": ms_seq,
+                           "how": "256 gh_detect calls (each a replayed graph)"}}
+
+
 def run_ours(args):
     import torch
 
@@ -450,6 +499,7 @@ def run_ours(args):
     wall = time.perf_counter() - t_wall
     prec = None if args.no_precision else precision_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args)
     diff = diff_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args)
+    batch = None if args.no_batch else batch_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args)
     clk = clocks.stop()
 
     value, hop_ms, _ = aggregate(world, hop_ms, evals * args.steps, device)
@@ -511,7 +561,7 @@ def run_ours(args):
                "gpu_launches_per_step": {"hop": hop_launches // args.steps, "exact": ex_launches // args.steps},
                "launch": "CUDA graph of the detect sequence, replayed every step",
                "roofline": roof, "cpu_baseline": cpu, "precision": prec,
-               "differentiation": diff, "clocks": clk,
+               "differentiation": diff, "batching": batch, "clocks": clk,
                "wall_s_timed_region": wall}
         print(json.dumps(out), flush=True)
     ctx.close()
@@ -529,6 +579,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the precision-at-scale leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-frame batching leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
