@@ -280,17 +280,18 @@ typedef struct {
 /*
  * gh_detect_batch - gh_detect with grid hopping (GH_HOP, complex float32
  * maps) for nframes independent frames of any sizes, each step launched once
- * for the whole batch (coordinate tables, maps, a persistent scorer whose
- * warps take (frame, cells) work items from a shared counter, BOMP selection
- * and correlation); frames whose K is reached drop out of later iterations.
+ * for the whole batch (coordinate tables, maps, persistent scorers whose
+ * warps take (frame, cells) work items from a shared counter, one per group
+ * of frames with the same shared-memory need, BOMP selection and
+ * correlation); frames whose K is reached drop out of later iterations.
  * Each frame's results equal those of gh_detect on that frame. Outputs are
  * concatenated in frame order:
  *   cells_host  : host int64[sum K]
  *   scores_host : host float[sum K] (may be NULL)
  *   alpha_host  : host double[sum K*Q][2] (may be NULL), per frame [K][Q][2]
- * The scorer's cells per lane and warps per CTA are chosen by timing the
- * candidates on the first iteration of a batch shape (cached in the context),
- * unless fixed with gh_set_batch_tuning. From the second call with an
+ * Each scorer group's cells per lane and warps per CTA are chosen by timing
+ * the candidates on the first iteration of a batch shape (cached in the
+ * context), unless fixed with gh_set_batch_tuning. From the second call with an
  * unchanged batch on, the whole sequence is a replayed CUDA graph.
  */
 GH_API int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* frames, int64_t* cells_host,
@@ -298,7 +299,8 @@ GH_API int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* frames,
 /* Fixes the batched scorer's configuration: cells per lane in {8, 16, 32},
  * warps per CTA in {2, 4, 8}; (0, 0) returns to autotuning (the default). */
 GH_API int gh_set_batch_tuning(gh_ctx* ctx, int32_t cells_per_lane, int32_t warps);
-/* The configuration the last gh_detect_batch call used. */
+/* The configuration the last gh_detect_batch call used for its scorer group
+ * with the most work. */
 GH_API int gh_batch_tuning(gh_ctx* ctx, int32_t* cells_per_lane, int32_t* warps);
 
 /*

@@ -13,9 +13,11 @@
 // the kernels of the single-frame path on the same data in the same order, so
 // its results are those of gh_detect bit for bit.
 //
-// The scorer's cells per lane and warps per CTA are picked by timing the
-// candidates on the batch's first iteration (once per batch shape, cached in
-// the context) unless set with gh_set_batch_tuning. The whole sequence is a
+// Frames are grouped by the shared memory a scorer warp needs (Q * Nd rounded
+// up to a power of two); each group has its own scorer launch per iteration,
+// whose cells per lane and warps per CTA are picked by timing the candidates
+// on the group's first iteration (once per batch shape, cached in the
+// context) unless set with gh_set_batch_tuning. The whole sequence is a
 // CUDA graph from the second call with an unchanged batch on (gh_run_sequence).
 #include <string.h>
 
@@ -37,15 +39,23 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 struct Plan {
     std::vector<unsigned char> key;    // whole batch (graph key)
     std::vector<unsigned char> shape;  // sizes only (tuning key)
-    int nframes = 0, Kmax = 0, max_q = 0, max_q_nd = 0, max_chunks = 0;
+    int nframes = 0, Kmax = 0, max_q = 0, max_chunks = 0;
     std::vector<int> K;                      // per frame
     std::vector<long long> out_off;          // byte offset of each frame in the packed results
     size_t out_bytes = 0;
     // device pointers (inside WS_BATCH / WS_BATCH_META)
     BatchFrame* frames = nullptr;
     BatchItem *coord_items = nullptr, *range_items = nullptr, *dop_items = nullptr;
-    std::vector<BatchItem*> score_items;     // per k
-    std::vector<int> n_score;                // per k
+    // frames grouped by the shared memory their scorer warps need (Q * Nd
+    // rounded up to a power of two, at least 1024 floats): one scorer launch
+    // per class and iteration, each sized and tuned for its class
+    struct ScoreClass {
+        int bound = 0, max_q = 0;
+        double work = 0.0;                    // cell * receiver * iteration evals
+        std::vector<BatchItem*> items;        // per k
+        std::vector<int> n;                   // per k
+    };
+    std::vector<ScoreClass> classes;
     std::vector<int*> active;                // per k
     std::vector<int> n_active;               // per k
     int n_coord = 0, n_range = 0, n_dop = 0;
@@ -61,13 +71,19 @@ struct Tuning {
     int ac = 0, warps = 0;
 };
 
+int class_bound(int q_nd) {
+    int b = 1024;
+    while (b < q_nd) b <<= 1;
+    return b;
+}
+
 // Context-side state of the batch path (one per context).
 struct BatchState {
     Plan plan;
     bool plan_valid = false;
     int force_ac = 0, force_warps = 0;
-    Tuning last;
-    std::map<std::vector<unsigned char>, Tuning> tuned;  // per batch shape
+    Tuning last;                                         // of the class with the most work
+    std::map<std::vector<unsigned char>, Tuning> tuned;  // per batch shape and class
 };
 
 std::mutex g_state_mu;
@@ -126,7 +142,6 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
         P.K.push_back(fr.K);
         P.Kmax = std::max(P.Kmax, fr.K);
         P.max_q = std::max(P.max_q, fr.Q);
-        P.max_q_nd = std::max(P.max_q_nd, fr.Q * dims[f].Nd);
         P.max_chunks = std::max(P.max_chunks, gh_bomp_chunks(dims[f]));
         // graph key: everything the sequence reads from the host
         append(P.key, fr.radar);
@@ -190,7 +205,19 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
 
     // work items
     std::vector<BatchItem> coord, range, dop;
-    std::vector<std::vector<BatchItem>> score(P.Kmax);
+    std::map<int, int> class_of_bound;
+    for (int f = 0; f < nframes; ++f) {
+        const int b = class_bound(dims[f].Q * dims[f].Nd);
+        if (!class_of_bound.count(b)) class_of_bound[b] = 0;
+    }
+    for (auto& kv : class_of_bound) {
+        kv.second = (int)P.classes.size();
+        Plan::ScoreClass c;
+        c.bound = kv.first;
+        P.classes.push_back(c);
+    }
+    std::vector<std::vector<std::vector<BatchItem>>> score(P.classes.size(),
+                                                          std::vector<std::vector<BatchItem>>(P.Kmax));
     std::vector<std::vector<int>> active(P.Kmax);
     for (int f = 0; f < nframes; ++f) {
         const Dims& d = dims[f];
@@ -207,10 +234,13 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
         for (int q = 0; q < d.Q; ++q)
             for (int i0 = 0; i0 < d.Nr; i0 += IB) dop.push_back({f, q, i0, IB});
         P.smem_dop = std::max(P.smem_dop, ((size_t)2 * IB * (d.Nd + 1) + IB + 3 * d.Nd / 4) * sizeof(float2));
+        const int cls = class_of_bound[class_bound(d.Q * d.Nd)];
+        P.classes[cls].max_q = std::max(P.classes[cls].max_q, d.Q);
+        P.classes[cls].work += (double)d.ncells * d.Q * P.K[f];
         for (int k = 0; k < P.K[f]; ++k) {
             active[k].push_back(f);
             for (long long s = 0; s < d.nxy; s += kBatchXyPerItem)
-                score[k].push_back({f, 0, s, std::min((long long)kBatchXyPerItem, d.nxy - s)});
+                score[cls][k].push_back({f, 0, s, std::min((long long)kBatchXyPerItem, d.nxy - s)});
         }
     }
     // packed results: per frame ArgResult[K] then double2[K][Q]
@@ -230,9 +260,10 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
     const size_t m_coord = take(coord.size() * sizeof(BatchItem));
     const size_t m_range = take(range.size() * sizeof(BatchItem));
     const size_t m_dop = take(dop.size() * sizeof(BatchItem));
-    std::vector<size_t> m_score(P.Kmax), m_active(P.Kmax);
+    std::vector<std::vector<size_t>> m_score(P.classes.size(), std::vector<size_t>(P.Kmax));
+    std::vector<size_t> m_active(P.Kmax);
     for (int k = 0; k < P.Kmax; ++k) {
-        m_score[k] = take(score[k].size() * sizeof(BatchItem));
+        for (size_t c = 0; c < P.classes.size(); ++c) m_score[c][k] = take(score[c][k].size() * sizeof(BatchItem));
         m_active[k] = take(active[k].size() * sizeof(int));
     }
     const size_t m_tw = take(ntw * sizeof(float2));
@@ -277,7 +308,8 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
     put(m_range, range.data(), range.size() * sizeof(BatchItem));
     put(m_dop, dop.data(), dop.size() * sizeof(BatchItem));
     for (int k = 0; k < P.Kmax; ++k) {
-        put(m_score[k], score[k].data(), score[k].size() * sizeof(BatchItem));
+        for (size_t c = 0; c < P.classes.size(); ++c)
+            put(m_score[c][k], score[c][k].data(), score[c][k].size() * sizeof(BatchItem));
         put(m_active[k], active[k].data(), active[k].size() * sizeof(int));
     }
     put(m_tw, tw.data(), ntw * sizeof(float2));
@@ -293,8 +325,10 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
     P.n_range = (int)range.size();
     P.n_dop = (int)dop.size();
     for (int k = 0; k < P.Kmax; ++k) {
-        P.score_items.push_back((BatchItem*)(M + m_score[k]));
-        P.n_score.push_back((int)score[k].size());
+        for (size_t c = 0; c < P.classes.size(); ++c) {
+            P.classes[c].items.push_back((BatchItem*)(M + m_score[c][k]));
+            P.classes[c].n.push_back((int)score[c][k].size());
+        }
         P.active.push_back((int*)(M + m_active[k]));
         P.n_active.push_back((int)active[k].size());
     }
@@ -309,14 +343,17 @@ int reset_frames(gh_ctx* ctx, const Plan& P) {
     return gh_launch_batch_reset(ctx, P.frames, P.nframes);
 }
 
-int batch_sequence(gh_ctx* ctx, const Plan& P, const Tuning& t, void** h) {
+int batch_sequence(gh_ctx* ctx, const Plan& P, const std::vector<Tuning>& t, void** h) {
     GH_TRY(reset_frames(ctx, P));
     GH_TRY(gh_launch_coord_batch(ctx, P.frames, P.coord_items, P.n_coord));
     for (int k = 0; k < P.Kmax; ++k) {
         GH_TRY(gh_launch_maps_batch(ctx, P.frames, P.range_items, P.n_range, 0, P.smem_range, P.dop_items, P.n_dop,
                                     P.smem_dop, k));
-        GH_TRY(gh_launch_hop_batch(ctx, P.frames, P.score_items[k], P.n_score[k], P.counter, k, t.ac, t.warps,
-                                   P.max_q_nd, P.max_q));
+        for (size_t c = 0; c < P.classes.size(); ++c) {
+            const Plan::ScoreClass& C = P.classes[c];
+            GH_TRY(gh_launch_hop_batch(ctx, P.frames, C.items[k], C.n[k], P.counter, k, t[c].ac, t[c].warps,
+                                       C.bound, C.max_q));
+        }
         GH_TRY(gh_launch_bomp_select_batch(ctx, P.frames, P.active[k], P.n_active[k], k));
         GH_TRY(gh_launch_bomp_corr_batch(ctx, P.frames, P.active[k], P.n_active[k], k, P.max_chunks, P.max_q));
     }
@@ -328,13 +365,17 @@ int batch_sequence(gh_ctx* ctx, const Plan& P, const Tuning& t, void** h) {
     return GH_OK;
 }
 
-// Times every scorer configuration that fits in shared memory on the first
-// iteration of the batch and returns the fastest.
-int autotune(gh_ctx* ctx, const Plan& P, Tuning* best) {
+// Maps of the batch's first iteration (what the autotuner scores).
+int autotune_prepare(gh_ctx* ctx, const Plan& P) {
     GH_TRY(reset_frames(ctx, P));
     GH_TRY(gh_launch_coord_batch(ctx, P.frames, P.coord_items, P.n_coord));
-    GH_TRY(gh_launch_maps_batch(ctx, P.frames, P.range_items, P.n_range, 0, P.smem_range, P.dop_items, P.n_dop,
-                                P.smem_dop, 0));
+    return gh_launch_maps_batch(ctx, P.frames, P.range_items, P.n_range, 0, P.smem_range, P.dop_items, P.n_dop,
+                                P.smem_dop, 0);
+}
+
+// Times every scorer configuration that fits in shared memory on the first
+// iteration of one class and returns the fastest.
+int autotune(gh_ctx* ctx, const Plan& P, const Plan::ScoreClass& C, Tuning* best) {
     cudaEvent_t a, b;
     GH_CUDA(cudaEventCreate(&a));
     GH_CUDA(cudaEventCreate(&b));
@@ -343,11 +384,11 @@ int autotune(gh_ctx* ctx, const Plan& P, Tuning* best) {
     int st = GH_OK;
     for (int ac : {8, 16, 32})
         for (int warps : {8, 4, 2}) {
-            if (gh_hop_batch_warp_bytes(ac, P.max_q_nd, P.max_q) * warps > ctx->smem_optin) continue;
+            if (gh_hop_batch_warp_bytes(ac, C.bound, C.max_q) * warps > ctx->smem_optin) continue;
             for (int rep = 0; rep < 2 && st == GH_OK; ++rep) {  // first launch warms up
                 cudaEventRecord(a, ctx->stream);
-                st = gh_launch_hop_batch(ctx, P.frames, P.score_items[0], P.n_score[0], P.counter, 0, ac, warps,
-                                         P.max_q_nd, P.max_q);
+                st = gh_launch_hop_batch(ctx, P.frames, C.items[0], C.n[0], P.counter, 0, ac, warps, C.bound,
+                                         C.max_q);
                 cudaEventRecord(b, ctx->stream);
             }
             if (st != GH_OK) break;
@@ -396,24 +437,37 @@ extern "C" int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* fra
         S->plan_valid = true;
     }
     Plan& P = S->plan;
-    Tuning t;
-    if (S->force_ac) {
-        t.ac = S->force_ac;
-        t.warps = S->force_warps;
-    } else {
-        auto it = S->tuned.find(P.shape);
-        if (it == S->tuned.end()) {
-            GH_TRY(autotune(ctx, P, &t));
-            S->tuned[P.shape] = t;
-        } else {
-            t = it->second;
+    std::vector<Tuning> t(P.classes.size());
+    bool prepared = false;
+    size_t heaviest = 0;
+    for (size_t c = 0; c < P.classes.size(); ++c) {
+        if (P.classes[c].work > P.classes[heaviest].work) heaviest = c;
+        if (S->force_ac) {
+            t[c].ac = S->force_ac;
+            t[c].warps = S->force_warps;
+            continue;
         }
+        std::vector<unsigned char> tkey = P.shape;
+        append(tkey, P.classes[c].bound);
+        auto it = S->tuned.find(tkey);
+        if (it != S->tuned.end()) {
+            t[c] = it->second;
+            continue;
+        }
+        if (!prepared) {
+            GH_TRY(autotune_prepare(ctx, P));
+            prepared = true;
+        }
+        GH_TRY(autotune(ctx, P, P.classes[c], &t[c]));
+        S->tuned[tkey] = t[c];
     }
-    S->last = t;
-    // graph key: the batch, the scorer configuration and the timing mask
+    S->last = t[heaviest];
+    // graph key: the batch, the scorer configurations and the timing mask
     std::vector<unsigned char> gkey = P.key;
-    append(gkey, t.ac);
-    append(gkey, t.warps);
+    for (const Tuning& tc : t) {
+        append(gkey, tc.ac);
+        append(gkey, tc.warps);
+    }
     append(gkey, ctx->timing);
     const char tag[] = "batch";
     gkey.insert(gkey.begin(), tag, tag + sizeof(tag));
