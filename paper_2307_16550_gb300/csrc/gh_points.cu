@@ -10,7 +10,10 @@
 //   s_q = sum_{k,l} c_k(tau_q) d_l(sigma_q) V_q(i_q + k, j_q + l),  S = sum_q |s_q|^2,
 //   V_q(n, m) = maps[q][n mod Nr][m mod Nd] (-1)^((Ms-1) floor(n/Nr)) exp(j pi m (Mc-1)/Nd)
 // with rho = Nr r_q, i = floor(rho + 1/2), tau = rho - i, eta = Nd u_q,
-// j = floor(eta + 1/2), sigma = eta - j, all in float64 (Eq. 1).
+// j = floor(eta + 1/2), sigma = eta - j, all in float64 (Eq. 1; one
+// reciprocal per distance, so bin choices may differ from a division-based
+// evaluation within a few ulps of a bin edge, where the score is continuous
+// to the interpolation error); derivatives in float32.
 //
 // Adjoint (i, j fixed between bin switches): dS/drho_q = 2 Re(conj(s) sum c_k' d_l V),
 // dS/deta_q = 2 Re(conj(s) sum c_k d_l' V), chained through
@@ -31,6 +34,7 @@ struct PtParams {
     double tx0, tx1;
     double B, cMs, kappa;
     double gr, ge;     // Nr B / (c Ms) and Nd kappa
+    float grf, gef;    // the same in float32 (derivative factors)
     int Q, Ms, Mc, Nr, Nd;
     float thr, thd;    // polar half-angles (range, Doppler)
     float mscale;      // 2^s of reduced-precision maps
@@ -78,27 +82,46 @@ __device__ __forceinline__ float2 load_bin(const void* maps, size_t idx) {
 
 // Geometry of one (point, receiver) in float64 and its stencil.
 struct PtGeo {
-    double ux1, uy1, n1, ux2, uy2, n2, wx, wy;
+    float ux1, uy1, r1, ux2, uy2, r2, wx, wy;  // unit vectors, 1/|x - p| (0 on p), gradient w (for derivatives)
     long long i, j;
     float tau, sig;
 };
 
+// Unit vector from p to x and 1/|x - p| in float64 with one division
+// (zero below 1e-9 m, as Eq. 1's gradient of a point on p).
+__device__ __forceinline__ void unit_recip(double dx, double dy, double* n, double* ux, double* uy, double* r) {
+    const double nn = sqrt(dx * dx + dy * dy);
+    *n = nn;
+    *r = nn < 1e-9 ? 0.0 : 1.0 / nn;
+    *ux = dx * *r;
+    *uy = dy * *r;
+}
+
+// Range and Doppler positions of a point at one receiver in float64 (bins
+// and offsets: rho = Nr B d / (c Ms), eta = Nd kappa <w, v>); derivative
+// factors in float32.
 __device__ __forceinline__ PtGeo pt_geo(const PtParams& p, double x, double y, double vx, double vy, double rxx,
                                         double rxy) {
+    double n1, ux1, uy1, r1, n2, ux2, uy2, r2;
+    unit_recip(x - p.tx0, y - p.tx1, &n1, &ux1, &uy1, &r1);
+    unit_recip(x - rxx, y - rxy, &n2, &ux2, &uy2, &r2);
+    const double wx = ux1 + ux2, wy = uy1 + uy2;
+    const double rho = p.gr * (n1 + n2);
+    const double eta = p.ge * (wx * vx + wy * vy);
+    const double fi = floor(rho + 0.5), fj = floor(eta + 0.5);
     PtGeo g;
-    gh_unit(__dsub_rn(x, p.tx0), __dsub_rn(y, p.tx1), &g.n1, &g.ux1, &g.uy1);
-    gh_unit(__dsub_rn(x, rxx), __dsub_rn(y, rxy), &g.n2, &g.ux2, &g.uy2);
-    const double d = __dadd_rn(g.n1, g.n2);
-    g.wx = __dadd_rn(g.ux1, g.ux2);
-    g.wy = __dadd_rn(g.uy1, g.uy2);
-    const double rho = __dmul_rn((double)p.Nr, __ddiv_rn(__dmul_rn(p.B, d), p.cMs));
-    const double eta =
-        __dmul_rn((double)p.Nd, __dmul_rn(p.kappa, __dadd_rn(__dmul_rn(g.wx, vx), __dmul_rn(g.wy, vy))));
-    const double fi = floor(__dadd_rn(rho, 0.5)), fj = floor(__dadd_rn(eta, 0.5));
+    g.ux1 = (float)ux1;
+    g.uy1 = (float)uy1;
+    g.r1 = (float)r1;
+    g.ux2 = (float)ux2;
+    g.uy2 = (float)uy2;
+    g.r2 = (float)r2;
+    g.wx = (float)wx;
+    g.wy = (float)wy;
     g.i = (long long)fi;
     g.j = (long long)fj;
-    g.tau = (float)__dsub_rn(rho, fi);
-    g.sig = (float)__dsub_rn(eta, fj);
+    g.tau = (float)(rho - fi);
+    g.sig = (float)(eta - fj);
     return g;
 }
 
@@ -184,7 +207,8 @@ __device__ double point_grad(const void* maps, const PtParams& p, const double* 
                              double vx, double vy, float gs, double* __restrict__ drx, float2* __restrict__ dmaps,
                              double grad[4], int G, bool live = true) {
     const int sub = threadIdx.x & (G - 1);
-    double acc = 0.0, gx = 0.0, gy = 0.0, gvx = 0.0, gvy = 0.0;
+    double acc = 0.0;
+    float gx = 0.f, gy = 0.f, gvx = 0.f, gvy = 0.f;
     for (int q = sub; q < p.Q; q += G) {
         const PtGeo g = pt_geo(p, x, y, vx, vy, rx[2 * q], rx[2 * q + 1]);
         const Coef cr = polar(p.thr, g.tau), cd = polar(p.thd, g.sig);
@@ -195,28 +219,21 @@ __device__ double point_grad(const void* maps, const PtParams& p, const double* 
         const float2 ar = contract(cr.dc, cd.c, V);
         const float2 ae = contract(cr.c, cd.dc, V);
         acc += (double)(s.x * s.x + s.y * s.y);
-        const double dSr = 2.0 * (double)(s.x * ar.x + s.y * ar.y);  // 2 Re(conj(s) ar)
-        const double dSe = 2.0 * (double)(s.x * ae.x + s.y * ae.y);
-        // J_p v = (v - u (u.v)) / n (zero for a point on p)
-        double j1x = 0.0, j1y = 0.0, j2x = 0.0, j2y = 0.0;
-        if (g.n1 >= 1e-9) {
-            const double uv = g.ux1 * vx + g.uy1 * vy;
-            j1x = (vx - g.ux1 * uv) / g.n1;
-            j1y = (vy - g.uy1 * uv) / g.n1;
-        }
-        if (g.n2 >= 1e-9) {
-            const double uv = g.ux2 * vx + g.uy2 * vy;
-            j2x = (vx - g.ux2 * uv) / g.n2;
-            j2y = (vy - g.uy2 * uv) / g.n2;
-        }
-        const double fr = dSr * p.gr, fe = dSe * p.ge;
+        const float dSr = 2.0f * (s.x * ar.x + s.y * ar.y);  // 2 Re(conj(s) ar)
+        const float dSe = 2.0f * (s.x * ae.x + s.y * ae.y);
+        // J_p v = (v - u (u.v)) / |x - p| (zero for a point on p: r = 0)
+        const float fvx = (float)vx, fvy = (float)vy;
+        const float uv1 = g.ux1 * fvx + g.uy1 * fvy, uv2 = g.ux2 * fvx + g.uy2 * fvy;
+        const float j1x = (fvx - g.ux1 * uv1) * g.r1, j1y = (fvy - g.uy1 * uv1) * g.r1;
+        const float j2x = (fvx - g.ux2 * uv2) * g.r2, j2y = (fvy - g.uy2 * uv2) * g.r2;
+        const float fr = dSr * p.grf, fe = dSe * p.gef;
         gx += fr * g.wx + fe * (j1x + j2x);
         gy += fr * g.wy + fe * (j1y + j2y);
         gvx += fe * g.wx;
         gvy += fe * g.wy;
         if (drx && live) {
-            atomicAdd(&drx[2 * q], (double)gs * (-fr * g.ux2 - fe * j2x));
-            atomicAdd(&drx[2 * q + 1], (double)gs * (-fr * g.uy2 - fe * j2y));
+            atomicAdd(&drx[2 * q], (double)(gs * (-fr * g.ux2 - fe * j2x)));
+            atomicAdd(&drx[2 * q + 1], (double)(gs * (-fr * g.uy2 - fe * j2y)));
         }
         if (dmaps && live) {
             // d|s|^2 / d(stored bin) = 2 s conj(c_k d_l wph) (stored bins are 2^-s times the values)
@@ -229,10 +246,10 @@ __device__ double point_grad(const void* maps, const PtParams& p, const double* 
                 }
         }
     }
-    grad[0] = group_sum(gx, G);
-    grad[1] = group_sum(gy, G);
-    grad[2] = group_sum(gvx, G);
-    grad[3] = group_sum(gvy, G);
+    grad[0] = group_sum((double)gx, G);
+    grad[1] = group_sum((double)gy, G);
+    grad[2] = group_sum((double)gvx, G);
+    grad[3] = group_sum((double)gvy, G);
     return group_sum(acc, G);
 }
 
@@ -400,6 +417,8 @@ PtParams pt_params(const Dims& d, const GeoParams& g, int map_dtype) {
     p.kappa = g.kappa;
     p.gr = (double)d.Nr * g.B / g.cMs;
     p.ge = (double)d.Nd * g.kappa;
+    p.grf = (float)p.gr;
+    p.gef = (float)p.ge;
     p.Q = d.Q;
     p.Ms = d.Ms;
     p.Mc = d.Mc;
