@@ -551,7 +551,7 @@ def run_ours(args):
                                 "speedup_hop_vs_exact": value / ex_value,
                                 "roofline": {"bound": "tensor", "achieved": ex_achieved, "peak": tc_peak,
                                              "unit": "TFLOP/s", "frac": ex_achieved / tc_peak, "traffic": None,
-                                             "kernel": "exact_s1_tc_kernel + exact_tc_kernel",
+                                             "kernel": "exact_s1_tc_kernel + exact_tc_ws_kernel",
                                              "flops_per_launch": flops, "kernel_ms": ex_kernel_s * 1e3,
                                              "peak_source": f"{peak_src} bf16 sustained / 3 (split-BF16)"}},
                "e2e": {"value": e2e_value, "unit": UNIT,

@@ -237,9 +237,7 @@ int launch_s2(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float* P, fl
 // rows side by side in N = 2 * nvy_pad; the cross blocks are discarded).
 // Operands are split into BF16 high and low parts and three MMAs per K step
 // (hi*hi + hi*lo + lo*hi) accumulate in FP32 in tensor memory.
-// The K loop runs over stages of 32 chirps (K = 64 per stage): the 128 threads
-// write a stage's operands to shared memory while the tensor core consumes the
-// previous stage (two buffers, completion through mbarriers, bounded waits).
+// The K loop runs over stages of 32 chirps (K = 64 per stage).
 // ---------------------------------------------------------------------------
 struct ExEntry {
     unsigned long long rfix;        // r_q(x): cycles per sample, 2^64 fixed point
@@ -274,319 +272,455 @@ struct ExactTcParams {
 
 constexpr uint32_t kTcWaitIters = 1u << 22;
 
-// z[k] = exp(-j 2 pi ph (m0 + k)), k < 16: an exact seed at k = 0, the other
-// entries by repeated multiplication with exp(-j 2 pi ph).
-__device__ __forceinline__ void atoms16(unsigned long long ph, int m0, float2* z) {
-    const float2 w = gh_cis_fix(0ull - ph);
-    float2 v = gh_cis_fix(0ull - ph * (unsigned long long)m0);
-    z[0] = v;
-#pragma unroll
-    for (int i = 1; i < 16; ++i) {
-        v = cmul(v, w);
-        z[i] = v;
-    }
+__device__ __forceinline__ void st16(unsigned char* p, const uint32_t* w, uint32_t flip) {
+    *(uint4*)p = make_uint4(w[0] ^ flip, w[1] ^ flip, w[2] ^ flip, w[3] ^ flip);
 }
 
-// BF16 high/low parts of the real and imaginary parts of z[0..15], packed in
-// pairs of consecutive entries.
-__device__ __forceinline__ void split16(const float2* z, uint32_t* reH, uint32_t* reL, uint32_t* imH,
-                                        uint32_t* imL) {
+// ---------------------------------------------------------------------------
+// Stage 2 kernel, warp-specialised: the warps of a CTA (one per SM,
+// persistent over the items (x, y, receiver pair)) have fixed roles and meet
+// only at mbarriers:
+//   warp 0       : TMEM owner; its lane 0 issues the MMAs of each stage and
+//                  the commits that free a stage slot (empty) and publish an
+//                  accumulator (accfull)
+//   warps 1..16  : producers; generate a stage's split-BF16 A and B operands
+//                  into a ring of shared-memory slots (full, count 16 warps):
+//                  8 warps per operand, (receiver of the pair, chirp quarter)
+//   warps 17..20 : epilogue, one per TMEM lane quarter; square their Re or
+//                  Im F rows, hand the accumulator back (accempty, count 4),
+//                  sum the four quarters in a fixed order through shared
+//                  memory and keep each cell's sum over receiver pairs; after
+//                  the last pair of a cell (x, y): scores, mask and argmax
+// Two accumulators in TMEM let the MMAs of one item run while the epilogue
+// reads the previous one. Every wait is bounded; a wait that gives up sets a
+// shared abort flag that ends every role's loop, and the kernel reports
+// GH_ETIMEOUT through the status word after freeing its tensor memory.
+// ---------------------------------------------------------------------------
+constexpr int kProdWarps = 16;
+constexpr int kEpiWarps = 4;
+constexpr int kThreadsWS = 32 * (1 + kProdWarps + kEpiWarps);
+
+template <int NV32>
+struct WsCfg {
+    static constexpr int NVP = 32 * NV32;
+    static constexpr int N = 2 * NVP;
+    static constexpr int STAGES = NV32 == 1 ? 4 : 3;
+    static constexpr uint32_t A_BYTES = 128 * 64 * 2, B_BYTES = N * 64 * 2;
+    static constexpr uint32_t SLOT = 2 * A_BYTES + 2 * B_BYTES;
+    static constexpr uint32_t XFER = kEpiWarps * 32 * (NVP + 1) * 4;  // rows padded by one word
+    static constexpr uint32_t SMEM = STAGES * SLOT + XFER;
+    static constexpr uint32_t TM_COLS = 2 * N <= 128 ? 128 : 256;
+};
+
+// Bounded wait of one thread, sleeping in the wait instruction (up to 20 us
+// per poll, at most kWsPolls polls: a few seconds); gives up when another role
+// has aborted.
+constexpr uint32_t kWsPolls = 1u << 17;
+__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    for (uint32_t i = 0; i < kWsPolls; ++i) {
+        if (gh_tc::mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+        if (*abort_flag) return false;
+    }
+    *abort_flag = 1;
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(gh_tc::smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Barrier of the 128 epilogue threads that also ANDs their predicates, so that
+// the four warps take the same decision after their bounded waits.
+__device__ __forceinline__ bool epi_all(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+
+// Atoms of one row for the 8 chirps m0 .. m0 + 7 of every stage (m0 = 32 s +
+// 8 kq): z[k] = exp(-j 2 pi ph (m0 + k)). The seed of stage 0 and the steps
+// w = exp(-j 2 pi ph), w^2, w^32 are exact (fixed-point phase, float32
+// sincos); within a stage two interleaved recurrences z[k + 2] = z[k] w^2,
+// and the next stage's seed is this seed times w^32.
+struct AtomRow {
+    float2 seed, w, w2, w32;
+};
+
+__device__ __forceinline__ AtomRow atom_row(unsigned long long ph, int m0) {
+    AtomRow r;
+    r.w = gh_cis_fix(0ull - ph);
+    r.w2 = cmul(r.w, r.w);
+    float2 t = cmul(r.w2, r.w2);  // w^4
+    t = cmul(t, t);               // w^8
+    t = cmul(t, t);               // w^16
+    r.w32 = cmul(t, t);
+    r.seed = gh_cis_fix(0ull - ph * (unsigned long long)m0);
+    return r;
+}
+
+__device__ __forceinline__ void atoms8_next(AtomRow& r, float2* z) {
+    z[0] = r.seed;
+    z[1] = cmul(z[0], r.w);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 2; i < 8; ++i) z[i] = cmul(z[i - 2], r.w2);
+    r.seed = cmul(r.seed, r.w32);
+}
+
+__device__ __forceinline__ void split8(const float2* z, uint32_t* reH, uint32_t* reL, uint32_t* imH,
+                                       uint32_t* imL) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
         gh_tc::split_bf16x2(z[2 * i].x, z[2 * i + 1].x, &reH[i], &reL[i]);
         gh_tc::split_bf16x2(z[2 * i].y, z[2 * i + 1].y, &imH[i], &imL[i]);
     }
 }
 
-__device__ __forceinline__ void st16(unsigned char* p, const uint32_t* w, uint32_t flip) {
-    *(uint4*)p = make_uint4(w[0] ^ flip, w[1] ^ flip, w[2] ^ flip, w[3] ^ flip);
-}
-
-// 256 threads, 8 warps. Generation: warp w < 4 writes A rows, w >= 4 B rows;
-// receiver half h = (w & 3) >> 1; chirp half kh = w & 1 (chirps 16 kh .. 16 kh + 15
-// of the 32-chirp stage). An A lane a writes both the Re F row (h*64 + a) and the
-// Im F row (h*64 + 32 + a) from one set of atoms. Epilogue: warp w reads TMEM
-// lanes 32 (w % 4) .. +31 (quarter: Re/Im F of receiver half) and column half w / 4.
 template <int NV32>
-__global__ void __launch_bounds__(256, 2) exact_tc_kernel(const float* __restrict__ P, const ExEntry* __restrict__ tab,
-                                                          ExactTcParams p, float* __restrict__ scores,
-                                                          const int64_t* __restrict__ mask, int nmask,
-                                                          ArgPartial* __restrict__ parts, int* __restrict__ status) {
-    constexpr int NVP = 32 * NV32;           // padded nvy
-    constexpr int N = 2 * NVP;               // MMA N
-    constexpr int NH = NVP / 2;              // columns per epilogue warp
+__global__ void __launch_bounds__(kThreadsWS, 1) exact_tc_ws_kernel(const float* __restrict__ P,
+                                                                    const ExEntry* __restrict__ tab, ExactTcParams p,
+                                                                    float* __restrict__ scores,
+                                                                    const int64_t* __restrict__ mask, int nmask,
+                                                                    ArgPartial* __restrict__ parts,
+                                                                    int* __restrict__ status) {
+    using C = WsCfg<NV32>;
+    constexpr int NVP = C::NVP, N = C::N, S = C::STAGES;
     constexpr uint32_t SBO = 128, LBO_A = 16 * 128, LBO_B = (N / 8) * 128;
-    constexpr uint32_t A_BYTES = 128 * 64 * 2, B_BYTES = N * 64 * 2;
-    constexpr uint32_t BUF_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-    constexpr uint32_t TM_COLS = 2 * N <= 32 ? 32 : (2 * N <= 64 ? 64 : (2 * N <= 128 ? 128 : (2 * N <= 256 ? 256 : 512)));
     constexpr uint32_t FLIP = 0x80008000u;  // sign bits of a BF16 pair
+    constexpr int CPT = NVP / 4;            // epilogue cells per thread and pair row
     extern __shared__ __align__(1024) unsigned char smem[];
-    // [6][32][NH] cross-warp sums; reuses the operand buffers, which are idle
-    // between the last epilogue of one (x, y) cell and the first stage of the next
-    float* xfer = (float*)smem;
-    static_assert(6 * 32 * NH * 4 <= 2 * BUF_BYTES, "cross-warp buffer must fit in the operand buffers");
-    __shared__ uint64_t bar[2];
+    float* xfer = (float*)(smem + S * C::SLOT);  // [4 quarters][32 lanes][NVP + 1]
+    constexpr int XS = NVP + 1;                  // row stride of xfer (bank-conflict free)
+    __shared__ uint64_t full[S], empty[S], accfull[2], accempty[2];
     __shared__ uint32_t tmem_holder;
-    __shared__ float s_bs[8];
-    __shared__ long long s_bc[8];
+    __shared__ int s_abort;
+    __shared__ int s_issued;  // stages issued by the MMA thread (for the abort drain)
+    __shared__ float s_bs[kEpiWarps];
+    __shared__ long long s_bc[kEpiWarps];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool a_role = warp < 4;
-    const int h = (warp & 3) >> 1;      // receiver of the pair (generation)
-    const int kh = warp & 1;            // chirp half of a stage (generation)
-    const int quarter = warp & 3;       // TMEM lane quarter (epilogue)
-    const int eh = quarter >> 1;        // receiver of the pair (epilogue)
-    const int chalf = warp >> 2;        // column half (epilogue)
     const int npairs = (p.Q + 1) >> 1;
-
+    volatile int* abort_flag = &s_abort;
     if (tid == 0) {
-        gh_tc::mbar_init(&bar[0], 1);
-        gh_tc::mbar_init(&bar[1], 1);
+        for (int i = 0; i < S; ++i) {
+            gh_tc::mbar_init(&full[i], kProdWarps);
+            gh_tc::mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            gh_tc::mbar_init(&accfull[i], 1);
+            gh_tc::mbar_init(&accempty[i], kEpiWarps);
+        }
+        s_abort = 0;
+        s_issued = 0;
         gh_tc::mbar_fence_init();
     }
-    if (warp == 0) gh_tc::tmem_alloc(&tmem_holder, TM_COLS);
+    if (warp == 0) gh_tc::tmem_alloc(&tmem_holder, C::TM_COLS);
     gh_tc::fence_before_sync();
     __syncthreads();
     gh_tc::fence_after_sync();
     const uint32_t tmem = tmem_holder;
-    const uint32_t idesc = gh_tc::idesc_bf16_f32(128, N);
-    const uint32_t offA_re = gh_tc::kmajor_off((uint32_t)(h * 64 + lane), 0, LBO_A, SBO);
-    const uint32_t offA_im = gh_tc::kmajor_off((uint32_t)(h * 64 + 32 + lane), 0, LBO_A, SBO);
 
     float best = -INFINITY;
     long long bestc = 0x7fffffffffffffffLL;
-    uint32_t gs = 0;
-    int pair_ctr = 0;
-    bool aborted = false;
 
-    for (long long xy = blockIdx.x; xy < p.nxy && !aborted; xy += gridDim.x) {
-        float acc[NH];
-#pragma unroll
-        for (int i = 0; i < NH; ++i) acc[i] = 0.f;
-        for (int pp = 0; pp < npairs && !aborted; ++pp) {
-            const int q = 2 * pp + h;
-            const bool vq = q < p.Q;
-            unsigned long long ph[NV32];
-            bool vrow[NV32];
-            const float* Pq = nullptr;  // planar Re row, then Im row
-            if (a_role) {
-                vrow[0] = vq && lane < p.nvx;
-                ph[0] = 0;
-                if (vrow[0]) {
-                    const ExEntry& e = tab[xy * p.Q + q];
-                    ph[0] = e.phx0 + (unsigned long long)lane * e.dphx;
-                }
-            } else {
-#pragma unroll
-                for (int g = 0; g < NV32; ++g) {
-                    const int b = lane + 32 * g;
-                    vrow[g] = vq && b < p.nvy;
-                    ph[g] = 0;
-                    if (vrow[g]) {
-                        const ExEntry& e = tab[xy * p.Q + q];
-                        ph[g] = e.phy0 + (unsigned long long)b * e.dphy;
-                    }
-                }
-                if (vq) Pq = P + ((size_t)q * p.nxy + xy) * 2 * p.Mc;
-            }
-            const uint32_t dcol = (uint32_t)(pair_ctr & 1) * N;
-            for (int s = 0; s < p.nstages; ++s) {
-                const int buf = gs & 1;
-                if (gs >= 2) {
-                    const bool ok = gh_tc::mbar_wait_bounded(&bar[buf], ((gs - 2) >> 1) & 1, kTcWaitIters);
-                    if (__syncthreads_or(!ok)) {
-                        aborted = true;
+    if (warp == 0) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = gh_tc::idesc_bf16_f32(128, N);
+            uint32_t g = 0, it = 0;
+            bool ok = true;
+            for (long long xy = blockIdx.x; xy < p.nxy && ok; xy += gridDim.x)
+                for (int pp = 0; pp < npairs && ok; ++pp, ++it) {
+                    const uint32_t buf = it & 1;
+                    if (!ws_wait(&accempty[buf], ((it >> 1) & 1) ^ 1, abort_flag)) {
+                        ok = false;
                         break;
                     }
-                }
-                unsigned char* Ah = smem + buf * BUF_BYTES;
-                unsigned char* Al = Ah + A_BYTES;
-                unsigned char* Bh = Al + A_BYTES;
-                unsigned char* Bl = Bh + B_BYTES;
-                const int m0 = 32 * s + 16 * kh;
-                // K positions of this chirp half: chunks 2kh, 2kh+1 (first half of K) and 4+2kh, 5+2kh
-                const uint32_t c0 = 2 * kh, c1 = 4 + 2 * kh;
-                if (a_role) {
-                    float2 z[16];
-                    if (vrow[0]) {
-                        atoms16(ph[0], m0, z);
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < 16; ++k) z[k] = make_float2(0.f, 0.f);
-                    }
-                    uint32_t reH[8], reL[8], imH[8], imL[8];
-                    split16(z, reH, reL, imH, imL);
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        // Re F row: [Re z | -Im z]; Im F row: [Im z | Re z]
-                        st16(Ah + offA_re + (c0 + j) * LBO_A, reH + 4 * j, 0u);
-                        st16(Al + offA_re + (c0 + j) * LBO_A, reL + 4 * j, 0u);
-                        st16(Ah + offA_re + (c1 + j) * LBO_A, imH + 4 * j, FLIP);
-                        st16(Al + offA_re + (c1 + j) * LBO_A, imL + 4 * j, FLIP);
-                        st16(Ah + offA_im + (c0 + j) * LBO_A, imH + 4 * j, 0u);
-                        st16(Al + offA_im + (c0 + j) * LBO_A, imL + 4 * j, 0u);
-                        st16(Ah + offA_im + (c1 + j) * LBO_A, reH + 4 * j, 0u);
-                        st16(Al + offA_im + (c1 + j) * LBO_A, reL + 4 * j, 0u);
-                    }
-                } else {
-                    float2 pv[16];
-                    if (vq) {
-#pragma unroll
-                        for (int k = 0; k < 16; k += 4) {
-                            const int mc = m0 + k;
-                            float4 re = make_float4(0.f, 0.f, 0.f, 0.f), im = re;
-                            if (mc + 3 < p.Mc) {
-                                re = __ldg((const float4*)(Pq + mc));
-                                im = __ldg((const float4*)(Pq + p.Mc + mc));
-                            } else {
-                                float* rr = &re.x;
-                                float* ii = &im.x;
-#pragma unroll
-                                for (int t = 0; t < 4; ++t)
-                                    if (mc + t < p.Mc) {
-                                        rr[t] = __ldg(Pq + mc + t);
-                                        ii[t] = __ldg(Pq + p.Mc + mc + t);
-                                    }
-                            }
-                            pv[k] = make_float2(re.x, im.x);
-                            pv[k + 1] = make_float2(re.y, im.y);
-                            pv[k + 2] = make_float2(re.z, im.z);
-                            pv[k + 3] = make_float2(re.w, im.w);
+                    gh_tc::fence_after_sync();
+                    const uint32_t dcol = buf * N;
+                    for (int s = 0; s < p.nstages; ++s, ++g) {
+                        const uint32_t slot = g % S;
+                        if (!ws_wait(&full[slot], (g / S) & 1, abort_flag)) {
+                            ok = false;
+                            break;
                         }
+                        gh_tc::fence_after_sync();
+                        unsigned char* Ah = smem + slot * C::SLOT;
+                        const uint32_t ah = gh_tc::smem_u32(Ah), al = ah + C::A_BYTES;
+                        const uint32_t bh = al + C::A_BYTES, bl = bh + C::B_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t dah = gh_tc::smem_desc(ah + 2 * kk * LBO_A, LBO_A, SBO);
+                            const uint64_t dal = gh_tc::smem_desc(al + 2 * kk * LBO_A, LBO_A, SBO);
+                            const uint64_t dbh = gh_tc::smem_desc(bh + 2 * kk * LBO_B, LBO_B, SBO);
+                            const uint64_t dbl = gh_tc::smem_desc(bl + 2 * kk * LBO_B, LBO_B, SBO);
+                            gh_tc::mma_bf16(tmem + dcol, dah, dbh, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+                            gh_tc::mma_bf16(tmem + dcol, dah, dbl, idesc, 1u);
+                            gh_tc::mma_bf16(tmem + dcol, dal, dbh, idesc, 1u);
+                        }
+                        gh_tc::mma_commit(&empty[slot]);  // the slot is free once these MMAs are done
+                        s_issued = (int)(g + 1);
                     }
+                    if (!ok) break;
+                    gh_tc::mma_commit(&accfull[buf]);  // the item's accumulator is complete
+                }
+        }
+    } else if (warp <= kProdWarps) {
+        // ---------------- producers ----------------
+        // The inputs of an item (its phase entry and, for B warps, its row of
+        // P) are loaded while the previous item is generated, so that no
+        // stage waits on a global load. P values depend on the chirp only:
+        // lane l of a B warp holds chirps 32 (l / 8 + 4 u) + 8 kq + l % 8,
+        // u = 0, 1, and a stage takes its 8 values by shuffles.
+        const int pw = warp - 1;
+        const bool a_role = pw < 8;
+        const int h = (pw & 7) >> 2;  // receiver of the pair
+        const int kq = pw & 3;        // chirp quarter of a stage (8 chirps)
+        const uint32_t offA_re = gh_tc::kmajor_off((uint32_t)(h * 64 + lane), 0, LBO_A, SBO);
+        const uint32_t offA_im = gh_tc::kmajor_off((uint32_t)(h * 64 + 32 + lane), 0, LBO_A, SBO);
+        auto fetch = [&](long long fxy, int fpp, unsigned long long& f0, unsigned long long& f1, float* fre,
+                         float* fim) {
+            const int fq = 2 * fpp + h;
+            f0 = f1 = 0ull;
+            fre[0] = fre[1] = fim[0] = fim[1] = 0.f;
+            if (fxy >= p.nxy || fq >= p.Q) return;
+            const ExEntry& e = tab[fxy * p.Q + fq];
+            if (a_role) {
+                f0 = e.phx0;
+                f1 = e.dphx;
+            } else {
+                f0 = e.phy0;
+                f1 = e.dphy;
+                const float* Pq = P + ((size_t)fq * p.nxy + fxy) * 2 * p.Mc;
 #pragma unroll
-                    for (int g = 0; g < NV32; ++g) {
-                        float2 z[16];
-                        if (vrow[g]) {
-                            atoms16(ph[g], m0, z);
+                for (int u = 0; u < 2; ++u) {
+                    const int mc = 32 * ((lane >> 3) + 4 * u) + 8 * kq + (lane & 7);
+                    if (mc < p.Mc) {
+                        fre[u] = __ldg(Pq + mc);
+                        fim[u] = __ldg(Pq + p.Mc + mc);
+                    }
+                }
+            }
+        };
+        uint32_t g = 0;
+        bool ok = true;
+        unsigned long long n0, n1;
+        float nre[2], nim[2];
+        fetch(blockIdx.x, 0, n0, n1, nre, nim);
+        for (long long xy = blockIdx.x; xy < p.nxy && ok; xy += gridDim.x)
+            for (int pp = 0; pp < npairs && ok; ++pp) {
+                const int q = 2 * pp + h;
+                const bool vq = q < p.Q;
+                const unsigned long long c0e = n0, c1e = n1;
+                const float cre[2] = {nre[0], nre[1]}, cim[2] = {nim[0], nim[1]};
+                {
+                    long long nxy = xy;
+                    int npp = pp + 1;
+                    if (npp == npairs) {
+                        npp = 0;
+                        nxy += gridDim.x;
+                    }
+                    fetch(nxy, npp, n0, n1, nre, nim);  // next item's inputs, in flight during this item
+                }
+                AtomRow ar[NV32];
+                bool vrow[NV32];
+                if (a_role) {
+                    vrow[0] = vq && lane < p.nvx;
+                    if (vrow[0]) ar[0] = atom_row(c0e + (unsigned long long)lane * c1e, 8 * kq);
+                } else {
 #pragma unroll
-                            for (int k = 0; k < 16; ++k) z[k] = cmul(pv[k], z[k]);
+                    for (int gg = 0; gg < NV32; ++gg) {
+                        const int b = lane + 32 * gg;
+                        vrow[gg] = vq && b < p.nvy;
+                        if (vrow[gg]) ar[gg] = atom_row(c0e + (unsigned long long)b * c1e, 8 * kq);
+                    }
+                }
+                for (int s = 0; s < p.nstages; ++s, ++g) {
+                    const uint32_t slot = g % S;
+                    // chirps 32 s + 8 kq .. + 7: K chunk kq (real parts) and 4 + kq (imaginary parts)
+                    float2 pv[8];
+                    if (!a_role) {
+                        const int src = ((s & 3) << 3);
+                        const float sre = (s < 4) ? cre[0] : cre[1];
+                        const float sim = (s < 4) ? cim[0] : cim[1];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k)
+                            pv[k] = make_float2(__shfl_sync(0xffffffffu, sre, src + k),
+                                                __shfl_sync(0xffffffffu, sim, src + k));
+                    }
+                    const bool w_ok = ws_wait(&empty[slot], ((g / S) & 1) ^ 1, abort_flag);
+                    if (!__all_sync(0xffffffffu, w_ok)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char* Ah = smem + slot * C::SLOT;
+                    unsigned char* Al = Ah + C::A_BYTES;
+                    unsigned char* Bh = Al + C::A_BYTES;
+                    unsigned char* Bl = Bh + C::B_BYTES;
+                    const uint32_t c0 = kq, c1 = 4 + kq;
+                    if (a_role) {
+                        float2 z[8];
+                        if (vrow[0]) {
+                            atoms8_next(ar[0], z);
                         } else {
 #pragma unroll
-                            for (int k = 0; k < 16; ++k) z[k] = make_float2(0.f, 0.f);
+                            for (int k = 0; k < 8; ++k) z[k] = make_float2(0.f, 0.f);
                         }
-                        uint32_t reH[8], reL[8], imH[8], imL[8];
-                        split16(z, reH, reL, imH, imL);
-                        const uint32_t offB =
-                            gh_tc::kmajor_off((uint32_t)(h * NVP + lane + 32 * g), 0, LBO_B, SBO);
+                        uint32_t reH[4], reL[4], imH[4], imL[4];
+                        split8(z, reH, reL, imH, imL);
+                        // Re F row: [Re z | -Im z]; Im F row: [Im z | Re z]
+                        st16(Ah + offA_re + c0 * LBO_A, reH, 0u);
+                        st16(Al + offA_re + c0 * LBO_A, reL, 0u);
+                        st16(Ah + offA_re + c1 * LBO_A, imH, FLIP);
+                        st16(Al + offA_re + c1 * LBO_A, imL, FLIP);
+                        st16(Ah + offA_im + c0 * LBO_A, imH, 0u);
+                        st16(Al + offA_im + c0 * LBO_A, imL, 0u);
+                        st16(Ah + offA_im + c1 * LBO_A, reH, 0u);
+                        st16(Al + offA_im + c1 * LBO_A, reL, 0u);
+                    } else {
 #pragma unroll
-                        for (int j = 0; j < 2; ++j) {
-                            st16(Bh + offB + (c0 + j) * LBO_B, reH + 4 * j, 0u);
-                            st16(Bl + offB + (c0 + j) * LBO_B, reL + 4 * j, 0u);
-                            st16(Bh + offB + (c1 + j) * LBO_B, imH + 4 * j, 0u);
-                            st16(Bl + offB + (c1 + j) * LBO_B, imL + 4 * j, 0u);
+                        for (int gg = 0; gg < NV32; ++gg) {
+                            float2 z[8];
+                            if (vrow[gg]) {
+                                atoms8_next(ar[gg], z);
+#pragma unroll
+                                for (int k = 0; k < 8; ++k) z[k] = cmul(pv[k], z[k]);
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < 8; ++k) z[k] = make_float2(0.f, 0.f);
+                            }
+                            uint32_t reH[4], reL[4], imH[4], imL[4];
+                            split8(z, reH, reL, imH, imL);
+                            const uint32_t offB =
+                                gh_tc::kmajor_off((uint32_t)(h * NVP + lane + 32 * gg), 0, LBO_B, SBO);
+                            st16(Bh + offB + c0 * LBO_B, reH, 0u);
+                            st16(Bl + offB + c0 * LBO_B, reL, 0u);
+                            st16(Bh + offB + c1 * LBO_B, imH, 0u);
+                            st16(Bl + offB + c1 * LBO_B, imL, 0u);
                         }
                     }
+                    gh_tc::fence_smem_to_async();  // generic stores -> tensor core
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&full[slot]);
                 }
-                gh_tc::fence_smem_to_async();
-                gh_tc::fence_before_sync();
-                __syncthreads();
-                if (tid == 0) {
-                    gh_tc::fence_after_sync();
-                    const uint32_t ah = gh_tc::smem_u32(Ah), al = gh_tc::smem_u32(Al);
-                    const uint32_t bh = gh_tc::smem_u32(Bh), bl = gh_tc::smem_u32(Bl);
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t dah = gh_tc::smem_desc(ah + 2 * kk * LBO_A, LBO_A, SBO);
-                        const uint64_t dal = gh_tc::smem_desc(al + 2 * kk * LBO_A, LBO_A, SBO);
-                        const uint64_t dbh = gh_tc::smem_desc(bh + 2 * kk * LBO_B, LBO_B, SBO);
-                        const uint64_t dbl = gh_tc::smem_desc(bl + 2 * kk * LBO_B, LBO_B, SBO);
-                        gh_tc::mma_bf16(tmem + dcol, dah, dbh, idesc, (s > 0 || kk > 0) ? 1u : 0u);
-                        gh_tc::mma_bf16(tmem + dcol, dah, dbl, idesc, 1u);
-                        gh_tc::mma_bf16(tmem + dcol, dal, dbh, idesc, 1u);
-                    }
-                    gh_tc::mma_commit(&bar[buf]);
-                }
-                ++gs;
             }
-            if (aborted) break;
-            // epilogue of the pair: (Re F)^2 or (Im F)^2 of this warp's rows and columns
-            {
-                const uint32_t last = gs - 1;
-                const bool ok = gh_tc::mbar_wait_bounded(&bar[last & 1], (last >> 1) & 1, kTcWaitIters);
-                if (__syncthreads_or(!ok)) {
-                    aborted = true;
+    } else {
+        // ---------------- epilogue ----------------
+        const int e = warp & 3;               // TMEM lane quarter this warp may access (warp % 4)
+        const int eh = e >> 1;                // receiver of the pair
+        const int et = tid - 32 * (1 + kProdWarps);  // 0..127
+        const int ca = et >> 2;               // cell row a of this thread
+        const int cb0 = (et & 3) * CPT;       // first column b
+        float sacc[CPT];
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) sacc[i] = 0.f;
+        uint32_t it = 0;
+        bool ok = true;
+        for (long long xy = blockIdx.x; xy < p.nxy && ok; xy += gridDim.x) {
+            for (int pp = 0; pp < npairs; ++pp, ++it) {
+                const uint32_t buf = it & 1;
+                const bool w_ok = ws_wait(&accfull[buf], (it >> 1) & 1, abort_flag);
+                if (!epi_all(w_ok)) {  // same decision in all four epilogue warps
+                    ok = false;
                     break;
                 }
                 gh_tc::fence_after_sync();
+                float* dst = xfer + ((size_t)e * 32 + lane) * XS;
 #pragma unroll
-                for (int c = 0; c < NH / 16; ++c) {
+                for (int c = 0; c < NVP / 16; ++c) {
                     float v[16];
-                    gh_tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + dcol +
-                                         (uint32_t)(eh * NVP + chalf * NH + 16 * c),
-                                     v);
+                    gh_tc::tmem_ld16(tmem + ((uint32_t)(32 * e) << 16) + buf * N + (uint32_t)(eh * NVP + 16 * c), v);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) acc[16 * c + i] += v[i] * v[i];
+                    for (int i = 0; i < 16; ++i) dst[16 * c + i] = v[i] * v[i];
                 }
                 gh_tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&accempty[buf]);
+                epi_barrier();  // the four quarters' squares are in xfer
+                // |F|^2 = (Re F)^2 + (Im F)^2 for both receivers, in a fixed order
+#pragma unroll
+                for (int i = 0; i < CPT; ++i) {
+                    const int b = cb0 + i;
+                    const float r0 = xfer[((size_t)0 * 32 + ca) * XS + b];
+                    const float i0 = xfer[((size_t)1 * 32 + ca) * XS + b];
+                    const float r1 = xfer[((size_t)2 * 32 + ca) * XS + b];
+                    const float i1 = xfer[((size_t)3 * 32 + ca) * XS + b];
+                    sacc[i] += (r0 + i0) + (r1 + i1);
+                }
+                epi_barrier();  // xfer is free for the next item
             }
-            ++pair_ctr;
-        }
-        if (aborted) break;
-        // S = sum over the four quarters (Re/Im F of both receiver halves): the
-        // warps of quarters 1-3 hand their sums to the quarter-0 warp of their
-        // column half. Every MMA of this cell has completed, so the operand
-        // buffers are free.
-        __syncthreads();
-        if (quarter > 0) {
-            float* dst = xfer + ((size_t)((chalf * 3 + quarter - 1) * 32 + lane)) * NH;
+            if (!ok) break;
+            // cell (x, y) complete: scores, mask, argmax
+            if (ca < p.nvx) {
+                const long long cbase = xy * p.nv + (long long)ca * p.nvy;
+                bool hm = false;
+                for (int m = 0; m < nmask; ++m) hm |= (__ldg(&mask[m]) / p.nv == xy);
+                float rb = -INFINITY;
+                int ri = -1;
 #pragma unroll
-            for (int b = 0; b < NH; ++b) dst[b] = acc[b];
-        }
-        __syncthreads();
-        if (quarter == 0 && lane < p.nvx) {
-            const int b0 = chalf * NH;
-            const long long cbase = xy * p.nv + (long long)lane * p.nvy;
-            bool hm = false;
-            for (int m = 0; m < nmask; ++m) hm |= (__ldg(&mask[m]) / p.nv == xy);
-            const float* x1 = xfer + ((size_t)((chalf * 3 + 0) * 32 + lane)) * NH;
-            const float* x2 = xfer + ((size_t)((chalf * 3 + 1) * 32 + lane)) * NH;
-            const float* x3 = xfer + ((size_t)((chalf * 3 + 2) * 32 + lane)) * NH;
-            float rb = -INFINITY;
-            int ri = -1;
-#pragma unroll
-            for (int i = 0; i < NH; ++i) {
-                const int b = b0 + i;
-                if (b < p.nvy) {
-                    const float sc = acc[i] + x1[i] + x2[i] + x3[i];
-                    if (scores) scores[cbase + b] = sc;
-                    bool masked = false;
-                    if (hm)
-                        for (int m = 0; m < nmask; ++m) masked |= (__ldg(&mask[m]) == cbase + b);
-                    if (!masked && sc > rb) {
-                        rb = sc;
-                        ri = b;
+                for (int i = 0; i < CPT; ++i) {
+                    const int b = cb0 + i;
+                    if (b < p.nvy) {
+                        if (scores) scores[cbase + b] = sacc[i];
+                        bool masked = false;
+                        if (hm)
+                            for (int m = 0; m < nmask; ++m) masked |= (__ldg(&mask[m]) == cbase + b);
+                        if (!masked && sacc[i] > rb) {
+                            rb = sacc[i];
+                            ri = b;
+                        }
                     }
                 }
+                if (ri >= 0) better(rb, cbase + ri, best, bestc);
             }
-            if (ri >= 0) better(rb, cbase + ri, best, bestc);
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) sacc[i] = 0.f;
         }
-        __syncthreads();  // the next cell's operands overwrite the cross-warp sums
     }
 
-    if (aborted) {
+    __syncthreads();
+    if (*abort_flag) {
         if (tid == 0) atomicExch(status, GH_ETIMEOUT);
-        // give in-flight tensor-core work a bounded chance to drain before freeing TMEM
-        if (gs > 0) gh_tc::mbar_wait_bounded(&bar[(gs - 1) & 1], ((gs - 1) >> 1) & 1, kTcWaitIters);
+        // give issued tensor-core work a bounded chance to drain before freeing TMEM
+        if (tid == 0 && s_issued > 0) {
+            const uint32_t last = (uint32_t)s_issued - 1;
+            gh_tc::mbar_wait_bounded(&empty[last % S], (last / S) & 1, kTcWaitIters);
+        }
     }
     gh_tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) gh_tc::tmem_dealloc(tmem, TM_COLS);
-
-    for (int off = 16; off > 0; off >>= 1) {
-        const float os = __shfl_down_sync(0xffffffffu, best, off);
-        const long long oc = __shfl_down_sync(0xffffffffu, bestc, off);
-        better(os, oc, best, bestc);
+    if (warp == 0) {
+        __syncwarp();
+        gh_tc::tmem_dealloc(tmem, C::TM_COLS);
     }
-    if (lane == 0) {
-        s_bs[warp] = best;
-        s_bc[warp] = bestc;
+
+    // argmax over the epilogue warps
+    if (warp > kProdWarps) {
+        for (int off = 16; off > 0; off >>= 1) {
+            const float os = __shfl_down_sync(0xffffffffu, best, off);
+            const long long oc = __shfl_down_sync(0xffffffffu, bestc, off);
+            better(os, oc, best, bestc);
+        }
+        if (lane == 0) {
+            s_bs[warp - 1 - kProdWarps] = best;
+            s_bc[warp - 1 - kProdWarps] = bestc;
+        }
     }
     __syncthreads();
     if (tid == 0) {
-        for (int w = 1; w < 8; ++w) better(s_bs[w], s_bc[w], best, bestc);
-        parts[blockIdx.x].score = best;
-        parts[blockIdx.x].cell = bestc;
+        float b = s_bs[0];
+        long long c = s_bc[0];
+        for (int w = 1; w < kEpiWarps; ++w) better(s_bs[w], s_bc[w], b, c);
+        parts[blockIdx.x].score = b;
+        parts[blockIdx.x].cell = c;
     }
 }
 
@@ -839,16 +973,11 @@ int launch_s1_tc(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate& df,
 template <int NV32>
 int launch_tc(gh_ctx* ctx, const Dims& d, const float* P, const ExEntry* tab, float* scores, const int64_t* mask,
               int nmask, ArgPartial* parts, int* status, long long* nparts) {
-    constexpr int NVP = 32 * NV32, N = 2 * NVP;
-    const size_t smem = (size_t)2 * (2 * 128 * 64 * 2 + 2 * N * 64 * 2);
+    using C = WsCfg<NV32>;
+    const size_t smem = C::SMEM;
     if (smem > ctx->smem_optin) return gh_fail(ctx, GH_ENOTSUP, "exact tensor-core path needs %zu B", smem);
-    GH_CUDA(cudaFuncSetAttribute(exact_tc_kernel<NV32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    GH_CUDA(cudaFuncSetAttribute(exact_tc_kernel<NV32>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared));
-    int per_sm = 0;
-    GH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, exact_tc_kernel<NV32>, 256, smem));
-    if (per_sm < 2) per_sm = 2;  // persistent grid-stride kernel: a second wave costs nothing extra
-    long long ctas = (long long)ctx->num_sms * per_sm;
+    GH_CUDA(cudaFuncSetAttribute(exact_tc_ws_kernel<NV32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    long long ctas = ctx->num_sms;  // one persistent CTA per SM
     if (ctas > d.nxy) ctas = d.nxy;
     ExactTcParams p;
     p.Q = d.Q;
@@ -860,8 +989,9 @@ int launch_tc(gh_ctx* ctx, const Dims& d, const float* P, const ExEntry* tab, fl
     p.nv = d.nv;
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_EXACT_S2, &ev);
-    exact_tc_kernel<NV32><<<(unsigned)ctas, 256, smem, ctx->stream>>>(P, tab, p, scores, mask, nmask, parts, status);
-    GH_TRY(gh_launch_end(ctx, GH_K_EXACT_S2, ev, "exact_tc_kernel"));
+    exact_tc_ws_kernel<NV32><<<(unsigned)ctas, kThreadsWS, smem, ctx->stream>>>(P, tab, p, scores, mask, nmask, parts,
+                                                                                status);
+    GH_TRY(gh_launch_end(ctx, GH_K_EXACT_S2, ev, "exact_tc_ws_kernel"));
     *nparts = ctas;
     return GH_OK;
 }
