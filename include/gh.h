@@ -72,6 +72,7 @@ extern "C" {
 /* Scoring methods (gh_detect). */
 #define GH_HOP      0     /* grid hopping (Sec. IV)                            */
 #define GH_EXACT    1     /* exact direct decision function (Sec. III)        */
+#define GH_INDIRECT 2     /* indirect method: map peaks + multilateration (Eq. 2), gh_factorized only */
 
 /* Kernel classes for gh_kernel_stats. */
 #define GH_K_RANGE_FFT   0
@@ -302,6 +303,32 @@ GH_API int gh_set_batch_tuning(gh_ctx* ctx, int32_t cells_per_lane, int32_t warp
 /* The configuration the last gh_detect_batch call used for its scorer group
  * with the most work. */
 GH_API int gh_batch_tuning(gh_ctx* ctx, int32_t* cells_per_lane, int32_t* warps);
+
+/*
+ * gh_factorized - the paper's factorised single-target estimators: location
+ * first over the (x, y) part of the grid, then velocity over its (vx, vy) part
+ * at that location (Sec. III, Eqs. 3-4), and the indirect method (Eq. 2).
+ *   GH_HOP      grid hopping (Sec. IV): Eq. 3 with the three-bin polar
+ *               interpolation of the zero-padded range FFT of every chirp;
+ *               Eq. 4 with g_q[mc] = <Y_q[mc], a(r_q(x^))> and the nearest bin
+ *               of its Doppler DFT zero-padded to Nd
+ *   GH_EXACT    the direct method: Eq. 3 exactly (the exact path's stage 1),
+ *               Eq. 4 exactly
+ *   GH_INDIRECT per receiver the peak (i, j) of |RD map|: r^ = i / Nr,
+ *               u^ = j / Nd in [-1/2, 1/2); x^ = argmin sum_q (r_q(x) - r^_q)^2,
+ *               then v^ = argmin sum_q (u_q(x^, v) - u^_q)^2, in float64
+ * Ties go to the smallest index.
+ *   Y_host_or_dev  : complex float32 [Q][Mc][Ms]
+ *   cell_host      : host int64, the 4D cell (ix, iy, ivx, ivy) of the estimate
+ *   values_host    : host double[2] (may be NULL): GH_HOP / GH_EXACT: S_loc at
+ *                    x^ and S_vel at v^; GH_INDIRECT: the two costs at x^, v^
+ *   loc_scores_dev : device float[nx*ny] location scores (may be NULL;
+ *                    GH_HOP and GH_EXACT)
+ * Synchronises the stream.
+ */
+GH_API int gh_factorized(gh_ctx* ctx, int32_t method, const gh_radar* radar, const double* tx_host,
+                  const double* rx_host, int32_t Q, const void* Y_host_or_dev, const gh_grid* grid,
+                  int64_t* cell_host, double* values_host, float* loc_scores_dev);
 
 /*
  * gh_set_detect_maps - storage type (GH_C64 default, GH_C16, GH_CBF16) of the

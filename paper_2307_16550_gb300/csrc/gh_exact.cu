@@ -998,19 +998,17 @@ int launch_tc(gh_ctx* ctx, const Dims& d, const float* P, const ExEntry* tab, fl
 
 }  // namespace
 
-int gh_launch_exact_parts(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y, const Deflate* dfp,
-                          float* scores, const int64_t* mask, int nmask, ArgPartial** parts_out, int* nparts_out) {
-    if (d.nxy > 0x7fffffffLL) return gh_fail(ctx, GH_ENOTSUP, "exact path supports < 2^31 (x, y) cells");
-    if (d.nv > 256 * 16) return gh_fail(ctx, GH_ENOTSUP, "exact path supports at most 4096 velocity cells");
-    const Deflate df = dfp ? *dfp : Deflate{nullptr, nullptr, nullptr, 0};
+// Stage 1 (and the phase table the tensor-core kernels read): P planar
+// [Q][nxy][Re row | Im row][Mc]; *tab_out is NULL when no table was made.
+static int exact_stage1(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y, const Deflate& df,
+                        bool need_tab, void** P_out, void** tab_out) {
     void* P;  // planar [Q][nxy][Re row | Im row][Mc]
     GH_TRY(gh_ws(ctx, WS_EXACT_P, (size_t)d.Q * d.nxy * 2 * d.Mc * sizeof(float), &P));
     const bool tc1 = d.Ms % 32 == 0 && (d.Mc == 32 || d.Mc == 64 || d.Mc == 128 || d.Mc == 256);
-    const bool tc2 = d.nvx <= 32 && d.nvy <= 64;
     int* status = gh_status_dev(ctx);
     cudaEvent_t ev;
     void* tab = nullptr;
-    if (tc1 || tc2) {
+    if (tc1 || need_tab) {
         GH_TRY(gh_ws(ctx, WS_EXACT_TAB, (size_t)d.nxy * d.Q * sizeof(ExEntry), &tab));
         const long long n = d.nxy * d.Q;
         gh_launch_begin(ctx, GH_K_EXACT_S1, &ev);
@@ -1037,6 +1035,28 @@ int gh_launch_exact_parts(gh_ctx* ctx, const Dims& d, const GeoParams& g, const 
         exact_stage1_kernel<<<grid1, 256, 0, ctx->stream>>>(Ys, g, (float*)P);
         GH_TRY(gh_launch_end(ctx, GH_K_EXACT_S1, ev, "exact_stage1_kernel"));
     }
+    *P_out = P;
+    *tab_out = tab;
+    return GH_OK;
+}
+
+int gh_launch_exact_stage1(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y, const float** P) {
+    if (d.nxy > 0x7fffffffLL) return gh_fail(ctx, GH_ENOTSUP, "exact path supports < 2^31 (x, y) cells");
+    void *Pv, *tab;
+    GH_TRY(exact_stage1(ctx, d, g, Y, Deflate{nullptr, nullptr, nullptr, 0}, false, &Pv, &tab));
+    *P = (const float*)Pv;
+    return GH_OK;
+}
+
+int gh_launch_exact_parts(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y, const Deflate* dfp,
+                          float* scores, const int64_t* mask, int nmask, ArgPartial** parts_out, int* nparts_out) {
+    if (d.nxy > 0x7fffffffLL) return gh_fail(ctx, GH_ENOTSUP, "exact path supports < 2^31 (x, y) cells");
+    if (d.nv > 256 * 16) return gh_fail(ctx, GH_ENOTSUP, "exact path supports at most 4096 velocity cells");
+    const Deflate df = dfp ? *dfp : Deflate{nullptr, nullptr, nullptr, 0};
+    const bool tc2 = d.nvx <= 32 && d.nvy <= 64;
+    int* status = gh_status_dev(ctx);
+    void *P, *tab;
+    GH_TRY(exact_stage1(ctx, d, g, Y, df, tc2, &P, &tab));
     void* parts;
     GH_TRY(gh_ws(ctx, WS_PART, (size_t)d.nxy * sizeof(ArgPartial), &parts));
     *parts_out = (ArgPartial*)parts;

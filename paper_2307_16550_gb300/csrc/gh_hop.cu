@@ -46,18 +46,7 @@ inline uint32_t hop_tol(int nvx, int nvy) {
 #define GH_HOP_MINB 2  // CTAs per SM the scorer's register budget targets
 #endif
 
-struct __align__(16) HopEntry {
-    long long base;  // (eta(0,0) - j_ref + 1/2) * 2^32 + tol
-    long long ax;    // d eta / d ivx * 2^32
-    long long by;    // d eta / d ivy * 2^32
-    double wx, wy;   // bistatic gradient (float64 bin decisions)
-    int row[3];      // map rows (i + k) mod Nr, k = -1, 0, 1
-    float cs[3];     // polar coefficients times the wrap sign
-    int j_ref;       // even Doppler bin of power-row entry 0 (entry u is bin (j_ref + u) mod Nd)
-    int npair;       // power-row entries to build, in pairs
-    int wrap;        // 1 if the velocity grid reaches more than Nd - 1 bins (entries wrap mod Nd)
-};
-static_assert(sizeof(HopEntry) == 80, "HopEntry layout");
+
 
 
 // Entry idx = xy * Q + q of the coordinate table (diagnostics optional).

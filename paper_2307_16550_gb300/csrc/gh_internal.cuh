@@ -156,6 +156,20 @@ struct Dims {
 // ---------------------------------------------------------------------------
 // Kernel parameter blocks shared by the single-frame and batched launches
 // ---------------------------------------------------------------------------
+// Coordinate-table entry of one (x, y, q) (gh_hop.cu).
+struct __align__(16) HopEntry {
+    long long base;  // (eta(0,0) - j_ref + 1/2) * 2^32 + tol
+    long long ax;    // d eta / d ivx * 2^32
+    long long by;    // d eta / d ivy * 2^32
+    double wx, wy;   // bistatic gradient (float64 bin decisions)
+    int row[3];      // map rows (i + k) mod Nr, k = -1, 0, 1
+    float cs[3];     // polar coefficients times the wrap sign
+    int j_ref;       // even Doppler bin of power-row entry 0 (entry u is bin (j_ref + u) mod Nd)
+    int npair;       // power-row entries to build, in pairs
+    int wrap;        // 1 if the velocity grid reaches more than Nd - 1 bins (entries wrap mod Nd)
+};
+static_assert(sizeof(HopEntry) == 80, "HopEntry layout");
+
 // Hopping scorer (gh_hop.cu).
 struct HopParams {
     int Q, Nr, Nd, nvx, nvy;
@@ -359,6 +373,8 @@ struct BatchItem {
 };
 
 int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* df, void* maps, int map_dtype);
+// Zero-padded range FFT of every chirp alone: *zr = [Q][Mc][Nr] complex64 (context workspace).
+int gh_launch_range_rows(gh_ctx* ctx, const Dims& d, const float2* Y, void** zr);
 // exp(-j 2 pi t / N), t < 3N/4, rounded from float64 (the FFT twiddle table).
 void gh_twiddles(int N, float2* out);
 // Batched maps (iteration k's residual applied on load); items as built by gh_batch.cu.
@@ -406,6 +422,9 @@ int gh_launch_points_adjoint(gh_ctx* ctx, const Dims& d, const GeoParams& g, con
 int gh_launch_refine(gh_ctx* ctx, const Dims& d, const GeoParams& g, const void* maps, int map_dtype,
                      const double* rx_dev, double* pts, long long P, int iters, double sx, double sv, double step,
                      float* S);
+// Stage 1 of the exact path alone (Eq. 4's g_q for every (x, y)): *P planar
+// [Q][nxy][Re row | Im row][Mc] float32 in the context workspace.
+int gh_launch_exact_stage1(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y, const float** P);
 // Exact direct scores of the (deflated) measurement; partials as gh_launch_hop_parts.
 int gh_launch_exact_parts(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y,
                           const Deflate* df, float* scores, const int64_t* mask, int nmask,

@@ -260,15 +260,13 @@ int ensure_twiddles(gh_ctx* ctx, int Nr, int Nd, const float2** twr, const float
 
 }  // namespace
 
-int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* df, void* maps, int map_dtype) {
+static int range_fft(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* df, const float2* twr,
+                     void** zr_out) {
     Deflate none = {nullptr, nullptr, nullptr, 0};
-    const float2 *twr, *twd;
-    GH_TRY(ensure_twiddles(ctx, d.Nr, d.Nd, &twr, &twd));
     void* zr;
     GH_TRY(gh_ws(ctx, WS_RANGE, (size_t)d.Q * d.Mc * d.Nr * sizeof(float2), &zr));
-
-    // range FFT: rows of Nr points, as many rows per CTA as fit in ~32 KB
-    const int logNr = ilog2(d.Nr), logNd = ilog2(d.Nd);
+    // rows of Nr points, as many rows per CTA as fit in ~32 KB
+    const int logNr = ilog2(d.Nr);
     int rpc = 2048 / d.Nr;
     if (rpc < 1) rpc = 1;
     const int rows = d.Q * d.Mc;
@@ -279,7 +277,23 @@ int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* d
     range_fft_kernel<<<(rows + rpc - 1) / rpc, 256, smem1, ctx->stream>>>(Y, (float2*)zr, d.Q, d.Ms, d.Mc, logNr,
                                                                           rows, rpc, df ? *df : none, twr);
     GH_TRY(gh_launch_end(ctx, GH_K_RANGE_FFT, ev, "range_fft_kernel"));
+    *zr_out = zr;
+    return GH_OK;
+}
 
+int gh_launch_range_rows(gh_ctx* ctx, const Dims& d, const float2* Y, void** zr) {
+    const float2 *twr, *twd;
+    GH_TRY(ensure_twiddles(ctx, d.Nr, d.Nd, &twr, &twd));
+    return range_fft(ctx, d, Y, nullptr, twr, zr);
+}
+
+int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* df, void* maps, int map_dtype) {
+    const float2 *twr, *twd;
+    GH_TRY(ensure_twiddles(ctx, d.Nr, d.Nd, &twr, &twd));
+    void* zr;
+    GH_TRY(range_fft(ctx, d, Y, df, twr, &zr));
+    const int logNr = ilog2(d.Nr), logNd = ilog2(d.Nd);
+    cudaEvent_t ev;
     // Doppler FFT: IB range bins per CTA
     int IB = 4096 / d.Nd;
     if (IB < 1) IB = 1;

@@ -20,7 +20,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "gh.h")
 
 GH_OK, GH_EINVAL, GH_ENOMEM, GH_ECUDA, GH_ETIMEOUT, GH_ENOTSUP = 0, -1, -2, -3, -4, -5
 GH_C64, GH_C16, GH_CBF16 = 0, 1, 2
-GH_HOP, GH_EXACT = 0, 1
+GH_HOP, GH_EXACT, GH_INDIRECT = 0, 1, 2
 (GH_K_RANGE_FFT, GH_K_DOPPLER_FFT, GH_K_COORD, GH_K_HOP_SCORE, GH_K_ARGMAX, GH_K_BOMP,
  GH_K_EXACT_S1, GH_K_EXACT_S2, GH_K_SYNTH, GH_K_POINTS) = range(10)
 KERNEL_KINDS = {"range_fft": 0, "doppler_fft": 1, "coord": 2, "hop_score": 3, "argmax": 4,
@@ -74,6 +74,8 @@ _SIGNATURES = {
     "gh_set_graphs": (_I32, [_P, _I32]),
     "gh_set_detect_maps": (_I32, [_P, _I32]),
     "gh_detect_batch": (_I32, [_P, _I32, _P, _P, _P, _P]),
+    "gh_factorized": (_I32, [_P, _I32, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, ctypes.POINTER(GhGrid), _P, _P,
+                             _P]),
     "gh_set_batch_tuning": (_I32, [_P, _I32, _I32]),
     "gh_batch_tuning": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "gh_score_points": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, _I32, _P, ctypes.c_int64, _P]),
@@ -348,6 +350,17 @@ class Context:
             oc += K
             oa += K * Q
         return out
+
+    def gh_factorized(self, method, radar, tx, rx, Q, Y, grid, loc_scores=None):
+        """The paper's factorised estimators (GH_HOP, GH_EXACT) or the indirect
+        method (GH_INDIRECT): (4D cell, (location value, velocity value))."""
+        txa, rxa = _f64(tx, (2,)), _f64(rx, (-1,))
+        cell = np.zeros(1, np.int64)
+        vals = np.zeros(2, np.float64)
+        self._check("gh_factorized", self._lib.gh_factorized(
+            self.handle, int(method), ctypes.byref(radar_struct(radar)), _ptr(txa), _ptr(rxa), int(Q), _ptr(Y),
+            ctypes.byref(grid_struct(grid)), _ptr(cell), _ptr(vals), _ptr(loc_scores)))
+        return int(cell[0]), (float(vals[0]), float(vals[1]))
 
     def gh_set_batch_tuning(self, cells_per_lane=0, warps=0):
         self._check("gh_set_batch_tuning", self._lib.gh_set_batch_tuning(self.handle, int(cells_per_lane), int(warps)))
