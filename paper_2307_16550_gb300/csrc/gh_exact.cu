@@ -974,6 +974,7 @@ template <int NV32>
 int launch_tc(gh_ctx* ctx, const Dims& d, const float* P, const ExEntry* tab, float* scores, const int64_t* mask,
               int nmask, ArgPartial* parts, int* status, long long* nparts) {
     using C = WsCfg<NV32>;
+    if (d.Mc > 256) return gh_fail(ctx, GH_ENOTSUP, "exact tensor-core stage 2 supports Mc <= 256");
     const size_t smem = C::SMEM;
     if (smem > ctx->smem_optin) return gh_fail(ctx, GH_ENOTSUP, "exact tensor-core path needs %zu B", smem);
     GH_CUDA(cudaFuncSetAttribute(exact_tc_ws_kernel<NV32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1053,7 +1054,8 @@ int gh_launch_exact_parts(gh_ctx* ctx, const Dims& d, const GeoParams& g, const 
     if (d.nxy > 0x7fffffffLL) return gh_fail(ctx, GH_ENOTSUP, "exact path supports < 2^31 (x, y) cells");
     if (d.nv > 256 * 16) return gh_fail(ctx, GH_ENOTSUP, "exact path supports at most 4096 velocity cells");
     const Deflate df = dfp ? *dfp : Deflate{nullptr, nullptr, nullptr, 0};
-    const bool tc2 = d.nvx <= 32 && d.nvy <= 64;
+    // the tensor-core stage 2 prefetches P for at most 8 stages of 32 chirps
+    const bool tc2 = d.nvx <= 32 && d.nvy <= 64 && d.Mc <= 256;
     int* status = gh_status_dev(ctx);
     void *P, *tab;
     GH_TRY(exact_stage1(ctx, d, g, Y, df, tc2, &P, &tab));

@@ -251,22 +251,16 @@ __global__ void __launch_bounds__(256) rd_peak_kernel(const float2* __restrict__
     block_best(best, bestc, parts + (size_t)q * gridDim.x + blockIdx.x);
 }
 
-// Multilateration (one CTA, float64): per-receiver peaks from the partials,
-// then the location and velocity argmins of Eq. 2.
-__global__ void __launch_bounds__(1024) multilat_kernel(GeoParams g, const ArgPartial* __restrict__ parts,
-                                                        int nchunks, FzResult* __restrict__ out) {
-    __shared__ double s_r[GH_MAX_Q], s_u[GH_MAX_Q], s_wx[GH_MAX_Q], s_wy[GH_MAX_Q];
-    __shared__ double s_bv[32];
-    __shared__ long long s_bi[32];
-    __shared__ long long s_loc;
-    __shared__ double s_locv;
+// Per-receiver map peaks from the rd_peak partials: r^_q = i / Nr and
+// u^_q = j / Nd in [-1/2, 1/2) (one warp per receiver; ties -> smallest index).
+__device__ void peaks_to_values(const GeoParams& g, const ArgPartial* __restrict__ parts, int nchunks, double* r,
+                                double* u) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    // peaks: one warp per receiver
     for (int q = warp; q < g.Q; q += nw) {
         float best = -INFINITY;
         long long bestc = 0x7fffffffffffffffLL;
-        for (int c = lane; c < nchunks; c += 32) better(parts[(size_t)q * nchunks + c].score,
-                                                      parts[(size_t)q * nchunks + c].cell, best, bestc);
+        for (int c = lane; c < nchunks; c += 32)
+            better(parts[(size_t)q * nchunks + c].score, parts[(size_t)q * nchunks + c].cell, best, bestc);
         for (int off = 16; off > 0; off >>= 1) {
             const float os = __shfl_down_sync(0xffffffffu, best, off);
             const long long oc = __shfl_down_sync(0xffffffffu, bestc, off);
@@ -274,64 +268,86 @@ __global__ void __launch_bounds__(1024) multilat_kernel(GeoParams g, const ArgPa
         }
         if (lane == 0) {
             const long long i = bestc / g.Nd, j = bestc - i * g.Nd;
-            s_r[q] = __ddiv_rn((double)i, (double)g.Nr);
-            s_u[q] = j < g.Nd / 2 ? __ddiv_rn((double)j, (double)g.Nd)
-                                  : __dsub_rn(__ddiv_rn((double)j, (double)g.Nd), 1.0);
+            r[q] = __ddiv_rn((double)i, (double)g.Nr);
+            u[q] = j < g.Nd / 2 ? __ddiv_rn((double)j, (double)g.Nd)
+                                : __dsub_rn(__ddiv_rn((double)j, (double)g.Nd), 1.0);
         }
     }
+}
+
+struct MinPartial {
+    double v;
+    long long i;
+};
+
+__device__ __forceinline__ void take_min(double v, long long i, double& bv, long long& bi) {
+    if (v < bv || (v == bv && i < bi)) {
+        bv = v;
+        bi = i;
+    }
+}
+
+// Block-wide argmin (float64, ties -> smallest index); thread 0 gets the result.
+__device__ void block_min(double& bv, long long& bi) {
+    __shared__ double s_bv[32];
+    __shared__ long long s_bi[32];
+    for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+        const long long oi = __shfl_down_sync(0xffffffffu, bi, off);
+        take_min(ov, oi, bv, bi);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s_bv[warp] = bv;
+        s_bi[warp] = bi;
+    }
     __syncthreads();
-    // argmin over a range of cells, float64 costs, ties -> smallest index
-    auto argmin = [&](long long n, auto cost, long long* where, double* value) {
-        double bv = INFINITY;
-        long long bi = 0x7fffffffffffffffLL;
-        for (long long c = threadIdx.x; c < n; c += blockDim.x) {
-            const double v = cost(c);
-            if (v < bv || (v == bv && c < bi)) {
-                bv = v;
-                bi = c;
-            }
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-            const double ov = __shfl_down_sync(0xffffffffu, bv, off);
-            const long long oi = __shfl_down_sync(0xffffffffu, bi, off);
-            if (ov < bv || (ov == bv && oi < bi)) {
-                bv = ov;
-                bi = oi;
-            }
-        }
-        if (lane == 0) {
-            s_bv[warp] = bv;
-            s_bi[warp] = bi;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < nw; ++w)
-                if (s_bv[w] < bv || (s_bv[w] == bv && s_bi[w] < bi)) {
-                    bv = s_bv[w];
-                    bi = s_bi[w];
-                }
-            *where = bi;
-            *value = bv;
-        }
-        __syncthreads();
-    };
+    if (threadIdx.x == 0)
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) take_min(s_bv[w], s_bi[w], bv, bi);
+}
+
+// Eq. 2 location cost sum_q (r_q(x) - r^_q)^2 of the (x, y) cells, float64;
+// per-CTA argmin partials.
+__global__ void __launch_bounds__(256) multilat_loc_kernel(GeoParams g, const ArgPartial* __restrict__ parts,
+                                                           int nchunks, MinPartial* __restrict__ out) {
+    __shared__ double s_r[GH_MAX_Q], s_u[GH_MAX_Q];
+    peaks_to_values(g, parts, nchunks, s_r, s_u);
+    __syncthreads();
     const long long nxy = (long long)g.n[0] * g.n[1];
-    argmin(
-        nxy,
-        [&](long long c) {
-            const int ix = (int)(c / g.n[1]), iy = (int)(c - (long long)ix * g.n[1]);
-            const double x = gh_axis(g.lo[0], g.step[0], ix), y = gh_axis(g.lo[1], g.step[1], iy);
-            double L = 0.0;
-            for (int q = 0; q < g.Q; ++q) {
-                double d, wx, wy;
-                gh_bistatic(g, q, x, y, &d, &wx, &wy);
-                const double e = __dsub_rn(gh_range(g, d), s_r[q]);
-                L = __dadd_rn(L, __dmul_rn(e, e));
-            }
-            return L;
-        },
-        &s_loc, &s_locv);
-    const long long xy = s_loc;
+    double bv = INFINITY;
+    long long bi = 0x7fffffffffffffffLL;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nxy;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(c / g.n[1]), iy = (int)(c - (long long)ix * g.n[1]);
+        const double x = gh_axis(g.lo[0], g.step[0], ix), y = gh_axis(g.lo[1], g.step[1], iy);
+        double L = 0.0;
+        for (int q = 0; q < g.Q; ++q) {
+            double d, wx, wy;
+            gh_bistatic(g, q, x, y, &d, &wx, &wy);
+            const double e = __dsub_rn(gh_range(g, d), s_r[q]);
+            L = __dadd_rn(L, __dmul_rn(e, e));
+        }
+        take_min(L, c, bv, bi);
+    }
+    block_min(bv, bi);
+    if (threadIdx.x == 0) out[blockIdx.x] = MinPartial{bv, bi};
+}
+
+// Location from the partials, then the velocity cost sum_q (u_q(x^, v) - u^_q)^2
+// over the (vx, vy) cells and its argmin (one CTA).
+__global__ void __launch_bounds__(1024) multilat_vel_kernel(GeoParams g, const ArgPartial* __restrict__ parts,
+                                                            int nchunks, const MinPartial* __restrict__ loc,
+                                                            int nloc, FzResult* __restrict__ out) {
+    __shared__ double s_r[GH_MAX_Q], s_u[GH_MAX_Q], s_wx[GH_MAX_Q], s_wy[GH_MAX_Q];
+    __shared__ MinPartial s_loc;
+    peaks_to_values(g, parts, nchunks, s_r, s_u);
+    double bv = INFINITY;
+    long long bi = 0x7fffffffffffffffLL;
+    for (int c = threadIdx.x; c < nloc; c += blockDim.x) take_min(loc[c].v, loc[c].i, bv, bi);
+    block_min(bv, bi);
+    if (threadIdx.x == 0) s_loc = MinPartial{bv, bi};
+    __syncthreads();
+    const long long xy = s_loc.i;
     const int ix = (int)(xy / g.n[1]), iy = (int)(xy - (long long)ix * g.n[1]);
     const double x = gh_axis(g.lo[0], g.step[0], ix), y = gh_axis(g.lo[1], g.step[1], iy);
     for (int q = threadIdx.x; q < g.Q; q += blockDim.x) {
@@ -341,27 +357,25 @@ __global__ void __launch_bounds__(1024) multilat_kernel(GeoParams g, const ArgPa
         s_wy[q] = wy;
     }
     __syncthreads();
-    __shared__ long long s_vel;
-    __shared__ double s_velv;
     const int nvy = g.n[3];
-    argmin(
-        (long long)g.n[2] * nvy,
-        [&](long long c) {
-            const int a = (int)(c / nvy), b = (int)(c - (long long)a * nvy);
-            const double vx = gh_axis(g.lo[2], g.step[2], a), vy = gh_axis(g.lo[3], g.step[3], b);
-            double V = 0.0;
-            for (int q = 0; q < g.Q; ++q) {
-                const double e = __dsub_rn(gh_speed(g, s_wx[q], s_wy[q], vx, vy), s_u[q]);
-                V = __dadd_rn(V, __dmul_rn(e, e));
-            }
-            return V;
-        },
-        &s_vel, &s_velv);
+    bv = INFINITY;
+    bi = 0x7fffffffffffffffLL;
+    for (long long c = threadIdx.x; c < (long long)g.n[2] * nvy; c += blockDim.x) {
+        const int a = (int)(c / nvy), b = (int)(c - (long long)a * nvy);
+        const double vx = gh_axis(g.lo[2], g.step[2], a), vy = gh_axis(g.lo[3], g.step[3], b);
+        double V = 0.0;
+        for (int q = 0; q < g.Q; ++q) {
+            const double e = __dsub_rn(gh_speed(g, s_wx[q], s_wy[q], vx, vy), s_u[q]);
+            V = __dadd_rn(V, __dmul_rn(e, e));
+        }
+        take_min(V, c, bv, bi);
+    }
+    block_min(bv, bi);
     if (threadIdx.x == 0) {
-        const long long a = s_vel / nvy, b = s_vel - a * nvy;
+        const long long a = bi / nvy, b = bi - a * nvy;
         out->cell = ((xy * g.n[2]) + a) * nvy + b;
-        out->loc = s_locv;
-        out->vel = s_velv;
+        out->loc = s_loc.v;
+        out->vel = bv;
         out->valid = 1;
     }
 }
@@ -417,9 +431,16 @@ extern "C" int gh_factorized(gh_ctx* ctx, int32_t method, const gh_radar* radar,
         gh_launch_begin(ctx, GH_K_ARGMAX, &ev);
         rd_peak_kernel<<<dim3(nch, Q), 256, 0, ctx->stream>>>((const float2*)maps, per_q, chunk, (ArgPartial*)parts);
         GH_TRY(gh_launch_end(ctx, GH_K_ARGMAX, ev, "rd_peak_kernel"));
+        void* mins;
+        const int nloc = (int)std::min<long long>(ctas, (d.nxy + 255) / 256);
+        GH_TRY(gh_ws(ctx, WS_DIAG, (size_t)nloc * sizeof(MinPartial), &mins));
         gh_launch_begin(ctx, GH_K_ARGMAX, &ev);
-        multilat_kernel<<<1, 1024, 0, ctx->stream>>>(geo, (const ArgPartial*)parts, nch, fres);
-        GH_TRY(gh_launch_end(ctx, GH_K_ARGMAX, ev, "multilat_kernel"));
+        multilat_loc_kernel<<<nloc, 256, 0, ctx->stream>>>(geo, (const ArgPartial*)parts, nch, (MinPartial*)mins);
+        GH_TRY(gh_launch_end(ctx, GH_K_ARGMAX, ev, "multilat_loc_kernel"));
+        gh_launch_begin(ctx, GH_K_ARGMAX, &ev);
+        multilat_vel_kernel<<<1, 1024, 0, ctx->stream>>>(geo, (const ArgPartial*)parts, nch, (const MinPartial*)mins,
+                                                          nloc, fres);
+        GH_TRY(gh_launch_end(ctx, GH_K_ARGMAX, ev, "multilat_vel_kernel"));
     } else {
         void* parts;
         GH_TRY(gh_ws(ctx, WS_PART, (size_t)ctas * sizeof(ArgPartial), &parts));

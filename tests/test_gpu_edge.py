@@ -107,3 +107,36 @@ def test_timing_and_launch_counts(ctx, torch_cuda):
     # per iteration: range FFT (residual applied on load), Doppler FFT, scorer,
     # selection (argmax + new atom), correlation (+ least squares); plus the table once
     assert n1 - n0 == 1 + 2 * 5
+
+
+@pytest.mark.parametrize("Q,Ms,Mc,pad,n", [
+    (64, 16, 8, 4, (3, 4, 2, 3)),      # GH_MAX_Q receivers
+    (2, 2048, 8, 4, (3, 2, 2, 2)),     # Nr = 8192 = GH_MAX_NFFT
+    (2, 8, 2048, 4, (2, 2, 3, 2)),     # Nd = 8192
+    (1, 4, 4, 1, (2, 2, 2, 2)),        # smallest transforms, no padding
+    (3, 4096, 4, 2, (2, 2, 2, 2)),     # Ms = GH_MAX_M
+])
+def test_maximum_and_minimum_sizes(ctx, torch_cuda, Q, Ms, Mc, pad, n):
+    radar = scenes.Radar(24e9, 250e6, 128e-6, Ms, Mc, pad)
+    grid = scenes.Grid.from_bounds((0, 0, -15, -15), (40, 40, 15, 15), n)
+    sc = scenes.custom_scene(5, radar, grid, Q=Q, T=1, snr_db=10.0)
+    Y32, Y = measurement64(sc)
+    Yd = to_dev(torch_cuda, Y32)
+    ref = hopping.hop_scores(omaps.rd_maps(Y, pad), sc.radar, sc.tx, sc.rx, sc.grid)
+    got, _, _ = ctx.scores(sc.radar, sc.tx, sc.rx, ctx.maps(sc.radar, Yd), sc.grid)
+    assert rel_err(got.cpu().numpy(), ref) < TOL
+    ex = direct.scores_full(Y, sc.radar, sc.tx, sc.rx, sc.grid)
+    got_e, _, _ = ctx.exact_scores(sc.radar, sc.tx, sc.rx, Yd, sc.grid)
+    assert rel_err(got_e.cpu().numpy(), ex) < TOL
+
+
+def test_sizes_beyond_the_limits_are_rejected(ctx, torch_cuda):
+    grid = scenes.Grid.from_bounds((0, 0, -1, -1), (1, 1, 1, 1), (2, 2, 2, 2))
+    Y = torch_cuda.zeros((1, 8, 8), dtype=torch_cuda.complex64, device="cuda:0")
+    for radar, Q in [(scenes.Radar(24e9, 250e6, 1e-4, 4096, 8, 4), 1),   # Nr = 16384 > GH_MAX_NFFT
+                     (scenes.Radar(24e9, 250e6, 1e-4, 8192, 8, 1), 1),   # Ms > GH_MAX_M
+                     (scenes.Radar(24e9, 250e6, 1e-4, 2, 8, 4), 1),      # Ms < GH_MIN_M
+                     (scenes.Radar(24e9, 250e6, 1e-4, 8, 8, 4), 65)]:    # Q > GH_MAX_Q
+        with pytest.raises(gh.GhError) as e:
+            ctx.gh_detect(gh.GH_HOP, radar, np.zeros(2), np.zeros((Q, 2)) + 1.0, Q, Y, grid, 1)
+        assert e.value.status == gh.GH_EINVAL
