@@ -602,8 +602,7 @@ static int detect_sequence(gh_ctx* ctx, int32_t method, const Dims& d, const Geo
         } else {
             GH_TRY(gh_launch_exact_parts(ctx, d, geo, Yd, &df, nullptr, mask, k, &parts, &nparts));
         }
-        GH_TRY(gh_launch_bomp_select(ctx, d, geo, parts, nparts, sel, mask, k, K, bws));
-        GH_TRY(gh_launch_bomp_corr(ctx, d, geo, Yd, k, K, bws));
+        GH_TRY(gh_launch_bomp_step(ctx, d, geo, parts, nparts, Yd, sel, mask, k, K, bws));
     }
     // results: selections, status word and the final amplitudes (double2 [K][Q]
     // at the start of the BOMP workspace)

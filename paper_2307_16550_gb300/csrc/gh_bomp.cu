@@ -97,6 +97,21 @@ __device__ __forceinline__ void better(float s, long long c, float& bs, long lon
 // best (score, cell) of iteration k; writes sel[k] and mask[k] and prepares
 // the new atom at every receiver: (r, u) in float64, its centring phase, row
 // k of the Gram matrices and the atom tables.
+// (r, u) of receiver q at a 4D cell (Eq. 1), float64.
+__device__ __forceinline__ void cell_ru(const GeoParams& g, long long cell, int q, double* r, double* u) {
+    const int nvy = g.n[3], nvx = g.n[2], ny = g.n[1];
+    const int ivy = (int)(cell % nvy);
+    cell /= nvy;
+    const int ivx = (int)(cell % nvx);
+    cell /= nvx;
+    const int iy = (int)(cell % ny);
+    const int ix = (int)(cell / ny);
+    double d, wx, wy;
+    gh_bistatic(g, q, gh_axis(g.lo[0], g.step[0], ix), gh_axis(g.lo[1], g.step[1], iy), &d, &wx, &wy);
+    *r = gh_range(g, d);
+    *u = gh_speed(g, wx, wy, gh_axis(g.lo[2], g.step[2], ivx), gh_axis(g.lo[3], g.step[3], ivy));
+}
+
 __device__ void bomp_select_body(float best, long long bestc, ArgResult* __restrict__ sel,
                                  int64_t* __restrict__ mask, int k, int K, const GeoParams& g, const BompPtrs& w) {
     __shared__ long long s_cell;
@@ -156,30 +171,6 @@ __device__ void bomp_select_body(float best, long long bestc, ArgResult* __restr
 
 
 // One CTA of 1024 threads.
-__global__ void __launch_bounds__(1024) bomp_select_kernel(const ArgPartial* __restrict__ parts, int nparts,
-                                                           ArgResult* __restrict__ sel, int64_t* __restrict__ mask,
-                                                           int k, int K, GeoParams g, BompPtrs w) {
-    __shared__ float s_bs[32];
-    __shared__ long long s_bc[32];
-    float best = -INFINITY;
-    long long bestc = 0x7fffffffffffffffLL;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) better(parts[i].score, parts[i].cell, best, bestc);
-    for (int off = 16; off > 0; off >>= 1) {
-        const float os = __shfl_down_sync(0xffffffffu, best, off);
-        const long long oc = __shfl_down_sync(0xffffffffu, bestc, off);
-        better(os, oc, best, bestc);
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        s_bs[warp] = best;
-        s_bc[warp] = bestc;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) better(s_bs[ww], s_bc[ww], best, bestc);
-    bomp_select_body(best, bestc, sel, mask, k, K, g, w);
-}
-
 // Batched selection: one CTA per listed frame, best cell from the frame's key.
 __global__ void __launch_bounds__(1024) bomp_select_batch_kernel(const BatchFrame* __restrict__ frames,
                                                                  const int* __restrict__ active, int k) {
@@ -314,9 +305,143 @@ __device__ void bomp_corr_body(const float2* __restrict__ Y, const GeoParams& g,
 }
 
 
-__global__ void __launch_bounds__(256) bomp_corr_kernel(const float2* __restrict__ Y, GeoParams g, int k, int K,
+// One BOMP iteration in one launch, grid (chunks, Q): every CTA reduces the
+// scorer's partials to the selected cell (all CTAs get the same cell), makes
+// its receiver's atom a(r_q) in shared memory (the CTAs of chunk 0 also store
+// it for the next maps' residual), correlates kCorrRows chirps with the atom
+// (storing their b(u_q) values), and the last CTA to finish writes the
+// selection, the new atom's phases and Gram rows, sums the correlations and
+// solves every receiver's least squares. Same arithmetic as a selection
+// followed by bomp_corr_body.
+__global__ void __launch_bounds__(256) bomp_step_kernel(const ArgPartial* __restrict__ parts, int nparts,
+                                                        const float2* __restrict__ Y, ArgResult* __restrict__ sel,
+                                                        int64_t* __restrict__ mask, int k, int K, GeoParams g,
                                                         BompPtrs w) {
-    bomp_corr_body(Y, g, k, K, w, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
+    extern __shared__ float2 s_at[];  // a(r_q), Ms values
+    __shared__ float s_bs[8];
+    __shared__ long long s_bc[8];
+    __shared__ long long s_best_cell;
+    __shared__ float s_best;
+    __shared__ unsigned long long s_rf, s_uf;
+    __shared__ double rx[kCorrRows], ry[kCorrRows];
+    __shared__ bool s_last;
+    __shared__ double s_r[GH_MAX_Q], s_u[GH_MAX_Q];
+    const int ch = blockIdx.x, q = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // selection (the same reduction in every CTA)
+    float best = -INFINITY;
+    long long bestc = 0x7fffffffffffffffLL;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) better(parts[i].score, parts[i].cell, best, bestc);
+    for (int off = 16; off > 0; off >>= 1) {
+        const float os = __shfl_down_sync(0xffffffffu, best, off);
+        const long long oc = __shfl_down_sync(0xffffffffu, bestc, off);
+        better(os, oc, best, bestc);
+    }
+    if (lane == 0) {
+        s_bs[warp] = best;
+        s_bc[warp] = bestc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) better(s_bs[ww], s_bc[ww], best, bestc);
+        s_best = best;
+        s_best_cell = bestc;
+        const long long cell = bestc != 0x7fffffffffffffffLL ? bestc : 0;
+        double r, u;
+        cell_ru(g, cell, q, &r, &u);
+        s_rf = gh_phase_fix(r);
+        s_uf = gh_phase_fix(u);
+        if (ch == 0) {  // the new atom's parameters at this receiver, for the last CTA
+            w.ru[(size_t)k * g.Q + q] = make_double2(r, u);
+            float sn, cs;
+            sincospif(mod2f(r * (g.Ms - 1) + u * (g.Mc - 1)), &sn, &cs);
+            w.phase[(size_t)k * g.Q + q] = make_double2(cs, sn);
+        }
+    }
+    __syncthreads();
+    float2* a_glob = w.atoms_a + ((size_t)k * g.Q + q) * g.Ms;
+    for (int m = threadIdx.x; m < g.Ms; m += blockDim.x) {
+        const float2 a = gh_cis_fix(s_rf * (unsigned long long)m);
+        s_at[m] = a;
+        if (ch == 0) a_glob[m] = a;
+    }
+    __syncthreads();
+    // correlation of kCorrRows chirps with b(u) (x) a(r)
+    const int mc = ch * kCorrRows + warp;
+    double sx = 0.0, sy = 0.0;
+    if (warp < kCorrRows && mc < g.Mc) {
+        const float2* row = Y + ((size_t)q * g.Mc + mc) * g.Ms;
+        float2 sm = make_float2(0.f, 0.f);
+        for (int m = lane; m < g.Ms; m += 32) {
+            const float2 y = row[m];
+            const float2 v = s_at[m];
+            sm.x += y.x * v.x + y.y * v.y;  // y * conj(a)
+            sm.y += y.y * v.x - y.x * v.y;
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            sm.x += __shfl_down_sync(0xffffffffu, sm.x, off);
+            sm.y += __shfl_down_sync(0xffffffffu, sm.y, off);
+        }
+        const float2 b = gh_cis_fix(s_uf * (unsigned long long)mc);
+        if (lane == 0) w.atoms_b[((size_t)k * g.Q + q) * g.Mc + mc] = b;
+        const double bx = b.x, by = b.y;  // s * conj(b)
+        sx = (double)sm.x * bx + (double)sm.y * by;
+        sy = (double)sm.y * bx - (double)sm.x * by;
+    }
+    if (lane == 0 && warp < kCorrRows) {
+        rx[warp] = sx;
+        ry[warp] = sy;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tx = 0, ty = 0;
+        for (int ww = 0; ww < kCorrRows; ++ww) {
+            tx += rx[ww];
+            ty += ry[ww];
+        }
+        w.corrp[((size_t)k * g.Q + q) * w.chunks + ch] = make_double2(tx, ty);
+        __threadfence();
+        s_last = atomicAdd(w.counter, 1u) == gridDim.x * gridDim.y - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        const bool valid = s_best_cell != 0x7fffffffffffffffLL;
+        sel[k].cell = s_best_cell;
+        sel[k].score = s_best;
+        sel[k].valid = valid;
+        mask[k] = s_best_cell;
+    }
+    // row k of the Gram matrix of every receiver, from the (r, u) the CTAs of chunk 0 stored
+    for (int i = threadIdx.x; i < g.Q; i += blockDim.x) {
+        const double2 ru = __ldcg(w.ru + (size_t)k * g.Q + i);
+        s_r[i] = ru.x;
+        s_u[i] = ru.y;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < g.Q * (k + 1); idx += blockDim.x) {
+        const int qg = idx / (k + 1), t = idx - qg * (k + 1);
+        const double2 rut = t == k ? make_double2(s_r[qg], s_u[qg]) : __ldcg(w.ru + (size_t)t * g.Q + qg);
+        const double v = dirichlet(s_r[qg] - rut.x, g.Ms) * dirichlet(s_u[qg] - rut.y, g.Mc);
+        double* G = w.gram + (size_t)qg * K * K;
+        G[k * K + t] = v;
+        G[t * K + k] = v;
+    }
+    const int qq = threadIdx.x;
+    if (qq < g.Q) {
+        double cx = 0.0, cy = 0.0;
+        const double2* pp = w.corrp + ((size_t)k * g.Q + qq) * w.chunks;
+        for (int c = 0; c < w.chunks; ++c) {
+            const double2 v = __ldcg(pp + c);
+            cx += v.x;
+            cy += v.y;
+        }
+        w.corr[(size_t)k * g.Q + qq] = make_double2(cx, cy);
+    }
+    __syncthreads();  // Gram row k of every receiver written
+    if (qq < g.Q) bomp_solve_q(qq, g.Q, g.Ms, g.Mc, k + 1, K, w.corr, w.phase, w.gram, w.alpha);
+    if (threadIdx.x == 0) *w.counter = 0u;  // ready for the next iteration
 }
 
 // Batched correlations: grid (max chunks, max Q, listed frames).
@@ -405,21 +530,16 @@ int gh_bomp_reset(gh_ctx* ctx, const Dims& d, int K, void* ws) {
     return GH_OK;
 }
 
-int gh_launch_bomp_select(gh_ctx* ctx, const Dims& d, const GeoParams& g, const ArgPartial* parts, int nparts,
-                          ArgResult* sel, int64_t* mask, int k, int K, void* ws) {
+int gh_launch_bomp_step(gh_ctx* ctx, const Dims& d, const GeoParams& g, const ArgPartial* parts, int nparts,
+                        const float2* Y, ArgResult* sel, int64_t* mask, int k, int K, void* ws) {
     const BompPtrs w = bomp_ptrs(ws, d, K);
-    cudaEvent_t ev;
-    gh_launch_begin(ctx, GH_K_ARGMAX, &ev);
-    bomp_select_kernel<<<1, 1024, 0, ctx->stream>>>(parts, nparts, sel, mask, k, K, g, w);
-    return gh_launch_end(ctx, GH_K_ARGMAX, ev, "bomp_select_kernel");
-}
-
-int gh_launch_bomp_corr(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y, int k, int K, void* ws) {
-    const BompPtrs w = bomp_ptrs(ws, d, K);
+    const size_t smem = (size_t)d.Ms * sizeof(float2);
+    GH_CUDA(cudaFuncSetAttribute(bomp_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_BOMP, &ev);
-    bomp_corr_kernel<<<dim3(w.chunks, d.Q), 32 * kCorrRows, 0, ctx->stream>>>(Y, g, k, K, w);
-    return gh_launch_end(ctx, GH_K_BOMP, ev, "bomp_corr_kernel");
+    bomp_step_kernel<<<dim3(w.chunks, d.Q), 32 * kCorrRows, smem, ctx->stream>>>(parts, nparts, Y, sel, mask, k, K,
+                                                                                  g, w);
+    return gh_launch_end(ctx, GH_K_BOMP, ev, "bomp_step_kernel");
 }
 
 int gh_launch_residual(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate& df, float2* R) {

@@ -436,14 +436,12 @@ int gh_launch_synth(gh_ctx* ctx, const Dims& d, const GeoParams& g, int T,
 int gh_launch_residual(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate& df, float2* R);
 
 // BOMP (workspace of gh_bomp_ws_bytes(d, K) bytes; the amplitudes, double2
-// [K][Q], sit at its start). Iteration k: gh_launch_bomp_select reduces the
-// scorer's partials into sel[k] (and mask[k]) and prepares the new atom;
-// gh_launch_bomp_corr correlates it with Y and solves the least squares of
-// atoms 0..k. gh_bomp_reset zeroes the workspace's completion counter.
+// [K][Q], sit at its start). Iteration k, one launch (gh_launch_bomp_step):
+// the scorer's partials -> sel[k] and mask[k], the new atom, its correlation
+// with Y and the least squares of atoms 0..k. gh_bomp_reset zeroes the
+// workspace's completion counter.
 size_t gh_bomp_ws_bytes(const Dims& d, int K);
 Deflate gh_bomp_deflate(void* bomp_ws, const Dims& d, int K, int n);
 int gh_bomp_reset(gh_ctx* ctx, const Dims& d, int K, void* bomp_ws);
-int gh_launch_bomp_select(gh_ctx* ctx, const Dims& d, const GeoParams& g, const ArgPartial* parts,
-                          int nparts, ArgResult* sel, int64_t* mask, int k, int K, void* bomp_ws);
-int gh_launch_bomp_corr(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y, int k, int K,
-                        void* bomp_ws);
+int gh_launch_bomp_step(gh_ctx* ctx, const Dims& d, const GeoParams& g, const ArgPartial* parts, int nparts,
+                        const float2* Y, ArgResult* sel, int64_t* mask, int k, int K, void* bomp_ws);

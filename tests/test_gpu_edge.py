@@ -105,8 +105,8 @@ def test_timing_and_launch_counts(ctx, torch_cuda):
     ctx.gh_set_timing(False)
     assert launches == 2 and ms > 0
     # per iteration: range FFT (residual applied on load), Doppler FFT, scorer,
-    # selection (argmax + new atom), correlation (+ least squares); plus the table once
-    assert n1 - n0 == 1 + 2 * 5
+    # BOMP step (selection, new atom, correlation, least squares); plus the table once
+    assert n1 - n0 == 1 + 2 * 4
 
 
 @pytest.mark.parametrize("Q,Ms,Mc,pad,n", [
