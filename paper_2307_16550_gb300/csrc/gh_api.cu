@@ -500,9 +500,14 @@ extern "C" int gh_make_maps(gh_ctx* ctx, const gh_radar* radar, int32_t Q, const
     return gh_launch_maps(ctx, d, (const float2*)Y_dev, nullptr, maps_dev, map_dtype);
 }
 
-static int build_table(gh_ctx* ctx, const Dims& d, const GeoParams& geo, void** table) {
-    GH_TRY(gh_ws(ctx, WS_TABLE, gh_hop_table_bytes(d), table));
-    return gh_launch_coord(ctx, d, geo, *table, nullptr, nullptr, nullptr, nullptr);
+// Coordinate table; with rowlim, also the per-receiver bounds of the map rows
+// it reads (stored after the table).
+static int build_table(gh_ctx* ctx, const Dims& d, const GeoParams& geo, void** table, int** rowlim = nullptr) {
+    const size_t tb = (gh_hop_table_bytes(d) + 255) & ~(size_t)255;
+    GH_TRY(gh_ws(ctx, WS_TABLE, tb + 2 * GH_MAX_Q * sizeof(int), table));
+    int* lim = rowlim ? (int*)((char*)*table + tb) : nullptr;
+    if (rowlim) *rowlim = lim;
+    return gh_launch_coord(ctx, d, geo, *table, nullptr, nullptr, nullptr, nullptr, lim);
 }
 
 extern "C" int gh_score_grid(gh_ctx* ctx, const gh_radar* radar, const double* tx_host, const double* rx_host,
@@ -588,7 +593,8 @@ static int detect_sequence(gh_ctx* ctx, int32_t method, const Dims& d, const Geo
     GH_TRY(gh_pinned(ctx, sel_bytes + alpha_bytes, &h));
     GH_TRY(gh_status_reset(ctx));
     GH_TRY(gh_bomp_reset(ctx, d, K, bws));
-    if (method == GH_HOP) GH_TRY(build_table(ctx, d, geo, &table));
+    int* rowlim = nullptr;  // map rows the scorer can read: the Doppler FFT skips the others
+    if (method == GH_HOP) GH_TRY(build_table(ctx, d, geo, &table, &rowlim));
     ArgResult* sel = (ArgResult*)res;  // sel[k] = selection of iteration k
     for (int k = 0; k < K; ++k) {
         // the residual of iteration k subtracts atoms 0..k-1 (amplitudes of the last solve)
@@ -596,7 +602,7 @@ static int detect_sequence(gh_ctx* ctx, int32_t method, const Dims& d, const Geo
         ArgPartial* parts;
         int nparts;
         if (method == GH_HOP) {
-            GH_TRY(gh_launch_maps(ctx, d, Yd, &df, maps, ctx->detect_maps));
+            GH_TRY(gh_launch_maps(ctx, d, Yd, &df, maps, ctx->detect_maps, rowlim));
             GH_TRY(gh_launch_hop_parts(ctx, d, geo, maps, ctx->detect_maps, table, nullptr, mask, k, &parts,
                                        &nparts));
         } else {

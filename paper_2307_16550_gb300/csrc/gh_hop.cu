@@ -120,12 +120,40 @@ __device__ __forceinline__ void coord_entry(const GeoParams& g, const CoordParam
     }
 }
 
+// rowlim (optional, device int[2Q]: Q minima preset large, then Q maxima
+// preset to -1): per receiver the smallest and largest map row any entry
+// reads (the map rows a detection's scorer can touch).
 __global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__ table, int32_t* diag_i,
-                             double* diag_tau, float* diag_c, double* diag_w) {
+                             double* diag_tau, float* diag_c, double* diag_w, int* __restrict__ rowlim) {
+    __shared__ int s_lim[2 * GH_MAX_Q];
     const long long nxy = (long long)g.n[0] * g.n[1];
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nxy * g.Q) return;
-    coord_entry(g, cp, idx, table, diag_i, diag_tau, diag_c, diag_w);
+    if (rowlim) {
+        for (int i = threadIdx.x; i < g.Q; i += blockDim.x) {
+            s_lim[i] = 0x7fffffff;
+            s_lim[g.Q + i] = -1;
+        }
+        __syncthreads();
+    }
+    if (idx < nxy * g.Q) {
+        coord_entry(g, cp, idx, table, diag_i, diag_tau, diag_c, diag_w);
+        if (rowlim) {
+            const int q = (int)(idx % g.Q);
+            const HopEntry& e = table[idx];
+            const int lo = min(e.row[0], min(e.row[1], e.row[2])), hi = max(e.row[0], max(e.row[1], e.row[2]));
+            atomicMin(&s_lim[q], lo);
+            atomicMax(&s_lim[g.Q + q], hi);
+        }
+    }
+    if (rowlim) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < g.Q; i += blockDim.x) {
+            if (s_lim[g.Q + i] >= 0) {
+                atomicMin(&rowlim[i], s_lim[i]);
+                atomicMax(&rowlim[g.Q + i], s_lim[g.Q + i]);
+            }
+        }
+    }
 }
 
 // Batched tables: item = (frame, first entry, count <= blockDim.x).
@@ -571,13 +599,17 @@ CoordParams coord_params(const Dims& d) {
 size_t gh_hop_table_bytes(const Dims& d) { return (size_t)d.nxy * d.Q * sizeof(HopEntry); }
 
 int gh_launch_coord(gh_ctx* ctx, const Dims& d, const GeoParams& g, void* table, int32_t* diag_i,
-                    double* diag_tau, float* diag_c, double* diag_w) {
+                    double* diag_tau, float* diag_c, double* diag_w, int* rowlim) {
     const CoordParams cp = coord_params(d);
     const long long n = d.nxy * d.Q;
+    if (rowlim) {  // minima 0x7f7f7f7f, maxima -1 (byte patterns)
+        GH_CUDA(cudaMemsetAsync(rowlim, 0x7f, (size_t)d.Q * sizeof(int), ctx->stream));
+        GH_CUDA(cudaMemsetAsync(rowlim + d.Q, 0xff, (size_t)d.Q * sizeof(int), ctx->stream));
+    }
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_COORD, &ev);
     coord_kernel<<<(unsigned)((n + 127) / 128), 128, 0, ctx->stream>>>(g, cp, (HopEntry*)table, diag_i, diag_tau,
-                                                                       diag_c, diag_w);
+                                                                       diag_c, diag_w, rowlim);
     return gh_launch_end(ctx, GH_K_COORD, ev, "coord_kernel");
 }
 
@@ -685,7 +717,8 @@ extern "C" int gh_score_grid_noalloc(void* stream_ptr, const gh_radar* radar, co
     gh_fill_geo(&g, radar, tx_host, rx_host, Q, grid);
     const CoordParams cp = coord_params(d);
     const long long n = d.nxy * d.Q;
-    coord_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(g, cp, table, nullptr, nullptr, nullptr, nullptr);
+    coord_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(g, cp, table, nullptr, nullptr, nullptr, nullptr,
+                                                                   nullptr);
     if (cudaGetLastError() != cudaSuccess) return GH_ECUDA;
     const HopParams hp = hop_params(d, g);
     long long nparts = 0;

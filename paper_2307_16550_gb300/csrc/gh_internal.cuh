@@ -372,7 +372,10 @@ struct BatchItem {
     long long count;
 };
 
-int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* df, void* maps, int map_dtype);
+// rowlim (optional): per receiver the row bounds from gh_launch_coord; rows
+// outside them are not computed (gh_detect's own maps only).
+int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* df, void* maps, int map_dtype,
+                   const int* rowlim = nullptr);
 // Zero-padded range FFT of every chirp alone: *zr = [Q][Mc][Nr] complex64 (context workspace).
 int gh_launch_range_rows(gh_ctx* ctx, const Dims& d, const float2* Y, void** zr);
 // exp(-j 2 pi t / N), t < 3N/4, rounded from float64 (the FFT twiddle table).
@@ -401,8 +404,8 @@ int gh_bomp_chunks(const Dims& d);
 int gh_launch_batch_reset(gh_ctx* ctx, const BatchFrame* frames, int nframes);
 // Packs every frame's selections and amplitudes into out (see gh_batch.cu).
 int gh_launch_batch_gather(gh_ctx* ctx, const BatchFrame* frames, int nframes, const long long* offsets, void* out);
-int gh_launch_coord(gh_ctx* ctx, const Dims& d, const GeoParams& g, void* table,
-                    int32_t* diag_i, double* diag_tau, float* diag_c, double* diag_w);
+int gh_launch_coord(gh_ctx* ctx, const Dims& d, const GeoParams& g, void* table, int32_t* diag_i,
+                    double* diag_tau, float* diag_c, double* diag_w, int* rowlim = nullptr);
 size_t gh_hop_table_bytes(const Dims& d);
 // Scorer: per-CTA argmax partials into the context workspace (*parts, *nparts);
 // gh_launch_hop also reduces them into *result.

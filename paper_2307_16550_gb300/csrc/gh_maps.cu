@@ -181,12 +181,17 @@ __device__ __forceinline__ void doppler_cols(const float2* __restrict__ Zr, void
     }
 }
 
+// rowlim (optional): Q minima then Q maxima of the rows to compute; CTAs
+// whose range bins all lie outside leave their rows untouched.
 template <int MT>
 __global__ void __launch_bounds__(256) doppler_fft_kernel(const float2* __restrict__ Zr, void* __restrict__ maps,
                                                           int Ms, int Mc, int logNr, int logNd, int IB,
-                                                          const float2* __restrict__ tw, float oscale) {
+                                                          const float2* __restrict__ tw, float oscale,
+                                                          const int* __restrict__ rowlim, int Q) {
     extern __shared__ float2 smem[];
-    doppler_cols<MT>(Zr, maps, Ms, Mc, logNr, logNd, IB, blockIdx.y, blockIdx.x * IB, tw, oscale, smem);
+    const int i0 = blockIdx.x * IB;
+    if (rowlim && (i0 + IB - 1 < rowlim[blockIdx.y] || i0 > rowlim[Q + blockIdx.y])) return;  // whole CTA
+    doppler_cols<MT>(Zr, maps, Ms, Mc, logNr, logNd, IB, blockIdx.y, i0, tw, oscale, smem);
 }
 
 // Batched maps of several frames: one work item (frame, first row / range
@@ -287,7 +292,8 @@ int gh_launch_range_rows(gh_ctx* ctx, const Dims& d, const float2* Y, void** zr)
     return range_fft(ctx, d, Y, nullptr, twr, zr);
 }
 
-int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* df, void* maps, int map_dtype) {
+int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* df, void* maps, int map_dtype,
+                   const int* rowlim) {
     const float2 *twr, *twd;
     GH_TRY(ensure_twiddles(ctx, d.Nr, d.Nd, &twr, &twd));
     void* zr;
@@ -306,7 +312,7 @@ int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* d
     GH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
     gh_launch_begin(ctx, GH_K_DOPPLER_FFT, &ev);
     kern<<<dim3(d.Nr / IB, d.Q), 256, smem2, ctx->stream>>>((const float2*)zr, maps, d.Ms, d.Mc, logNr, logNd, IB,
-                                                            twd, oscale);
+                                                            twd, oscale, rowlim, d.Q);
     return gh_launch_end(ctx, GH_K_DOPPLER_FFT, ev, "doppler_fft_kernel");
 }
 
