@@ -228,12 +228,14 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
         for (int r = 0; r < rows; r += rpc) {
             const int c = std::min(rpc, rows - r);
             range.push_back({f, 0, r, c});
-            P.smem_range = std::max(P.smem_range, ((size_t)2 * c * d.Nr + 3 * d.Nr / 4) * sizeof(float2));
+            P.smem_range =
+                std::max(P.smem_range, ((size_t)2 * c * gh_fft_ld(d.Nr) + 3 * d.Nr / 4) * sizeof(float2));
         }
         const int IB = std::min(std::min(std::max(1, 4096 / d.Nd), 16), d.Nr);
         for (int q = 0; q < d.Q; ++q)
             for (int i0 = 0; i0 < d.Nr; i0 += IB) dop.push_back({f, q, i0, IB});
-        P.smem_dop = std::max(P.smem_dop, ((size_t)2 * IB * (d.Nd + 1) + IB + 3 * d.Nd / 4) * sizeof(float2));
+        P.smem_dop = std::max(P.smem_dop,
+                              ((size_t)2 * IB * (gh_fft_ld(d.Nd) + 1) + IB + 3 * d.Nd / 4) * sizeof(float2));
         const int cls = class_of_bound[class_bound(d.Q * d.Nd)];
         P.classes[cls].max_q = std::max(P.classes[cls].max_q, d.Q);
         P.classes[cls].work += (double)d.ncells * d.Q * P.K[f];

@@ -378,6 +378,8 @@ int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* d
                    const int* rowlim = nullptr);
 // Zero-padded range FFT of every chirp alone: *zr = [Q][Mc][Nr] complex64 (context workspace).
 int gh_launch_range_rows(gh_ctx* ctx, const Dims& d, const float2* Y, void** zr);
+// Shared-memory column length of an N-point FFT (one float2 of padding per 16).
+__host__ __device__ inline int gh_fft_ld(int N) { return N + (N >> 4); }
 // exp(-j 2 pi t / N), t < 3N/4, rounded from float64 (the FFT twiddle table).
 void gh_twiddles(int N, float2* out);
 // Batched maps (iteration k's residual applied on load); items as built by gh_batch.cu.

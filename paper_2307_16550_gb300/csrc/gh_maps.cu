@@ -24,24 +24,42 @@ namespace {
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
-// Ping-pong Stockham FFT of `ncol` columns of length N = 2^logN stored at
-// x + c*ld: radix-4 passes, then one radix-2 pass when logN is odd.
+// Position of element i of a column in shared memory: one float2 of padding
+// after every 16, so that the strided stores of the early passes (runs of 4
+// consecutive outputs every 16) fall into different banks.
+__device__ __forceinline__ int p16(int i) { return i + (i >> 4); }
+
+// Ping-pong Stockham FFT of `ncol` columns of length N = 2^logN, element i of
+// column c at x[c * ld + p16(i)]: radix-4 passes, then one radix-2 pass when
+// logN is odd. When only the first nz <= N/4 inputs are nonzero (zero padding
+// by 4 or more), the first radix-4 pass reduces to replicating each input to
+// its four outputs and the other inputs are neither stored nor read.
 // tw[t] = exp(-j 2 pi t / N), t < 3N/4 (in shared memory). Returns the buffer
 // holding the transform (x or y).
-__device__ float2* fft_columns(float2* x, float2* y, int logN, int ncol, int ld, const float2* tw) {
+__device__ float2* fft_columns(float2* x, float2* y, int logN, int ncol, int ld, const float2* tw, int nz) {
     const int N = 1 << logN;
     int Ns = 1, rem = logN;
     while (rem >= 2) {
         const int lq = logN - 2, q4 = 1 << lq;
         const int total = ncol << lq;
         const int tstep = N / (4 * Ns);
+        const bool replicate = Ns == 1 && nz <= q4;
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             const int c = idx >> lq;
             const int j = idx & (q4 - 1);
             const int k = j & (Ns - 1);
             const float2* xc = x + c * ld;
             float2* yc = y + c * ld;
-            float2 v0 = xc[j], v1 = xc[j + q4], v2 = xc[j + 2 * q4], v3 = xc[j + 3 * q4];
+            const int o = ((j - k) << 2) + k;
+            if (replicate) {
+                const float2 v0 = j < nz ? xc[p16(j)] : make_float2(0.f, 0.f);
+                yc[p16(o)] = v0;
+                yc[p16(o + 1)] = v0;
+                yc[p16(o + 2)] = v0;
+                yc[p16(o + 3)] = v0;
+                continue;
+            }
+            float2 v0 = xc[p16(j)], v1 = xc[p16(j + q4)], v2 = xc[p16(j + 2 * q4)], v3 = xc[p16(j + 3 * q4)];
             if (Ns > 1) {
                 const int s = tstep * k;
                 v1 = cmul(v1, tw[s]);
@@ -51,11 +69,10 @@ __device__ float2* fft_columns(float2* x, float2* y, int logN, int ncol, int ld,
             const float2 a = f2add(v0, v2), b = f2sub(v0, v2), cc = f2add(v1, v3);
             const float2 dd = f2sub(v1, v3);
             const float2 d = make_float2(dd.y, -dd.x);  // (v1 - v3) * (-j)
-            const int o = ((j - k) << 2) + k;
-            yc[o] = f2add(a, cc);
-            yc[o + Ns] = f2add(b, d);
-            yc[o + 2 * Ns] = f2sub(a, cc);
-            yc[o + 3 * Ns] = f2sub(b, d);
+            yc[p16(o)] = f2add(a, cc);
+            yc[p16(o + Ns)] = f2add(b, d);
+            yc[p16(o + 2 * Ns)] = f2sub(a, cc);
+            yc[p16(o + 3 * Ns)] = f2sub(b, d);
         }
         __syncthreads();
         float2* t = x;
@@ -74,11 +91,17 @@ __device__ float2* fft_columns(float2* x, float2* y, int logN, int ncol, int ld,
             const int k = j & (Ns - 1);
             const float2* xc = x + c * ld;
             float2* yc = y + c * ld;
-            const float2 a = xc[j];
-            const float2 b = cmul(xc[j + half], tw[tstep * k]);
+            float2 a, b;
+            if (Ns == 1 && nz <= half) {  // N = 2: inputs beyond nz are zero
+                a = j < nz ? xc[p16(j)] : make_float2(0.f, 0.f);
+                b = make_float2(0.f, 0.f);
+            } else {
+                a = xc[p16(j)];
+                b = cmul(xc[p16(j + half)], tw[tstep * k]);
+            }
             const int o = ((j - k) << 1) + k;
-            yc[o] = f2add(a, b);
-            yc[o + Ns] = f2sub(a, b);
+            yc[p16(o)] = f2add(a, b);
+            yc[p16(o + Ns)] = f2sub(a, b);
         }
         __syncthreads();
         float2* t = x;
@@ -92,29 +115,37 @@ __device__ void load_twiddles(float2* dst, const float2* __restrict__ src, int n
     for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = __ldg(src + t);
 }
 
-// Range FFTs of rows r0 .. r0 + nrow - 1 (row = q * Mc + mc) of one frame.
+// Range FFTs of rows r0 .. r0 + nrow - 1 (row = q * Mc + mc) of one frame;
+// shared memory: 2 * rows_alloc * gh_fft_ld(Nr) + 3 Nr / 4 float2.
 __device__ __forceinline__ void range_rows(const float2* __restrict__ Y, float2* __restrict__ out, int Q, int Ms,
                                            int Mc, int logNr, int r0, int nrow, int rows_alloc, const Deflate& df,
                                            const float2* __restrict__ tw, float2* smem) {
     const int Nr = 1 << logNr;
+    const int ld = gh_fft_ld(Nr);
     float2* x = smem;
-    float2* y = smem + rows_alloc * Nr;
-    float2* twS = y + rows_alloc * Nr;
+    float2* y = smem + rows_alloc * ld;
+    float2* twS = y + rows_alloc * ld;
     load_twiddles(twS, tw, 3 * Nr / 4);
-    for (int idx = threadIdx.x; idx < nrow * Nr; idx += blockDim.x) {
-        const int c = idx >> logNr;
-        const int n = idx & (Nr - 1);
+    // only the Ms samples are stored when the first pass can skip the zero padding
+    const int nstore = Ms <= Nr / 4 ? Ms : Nr;
+    const int lst = Ms <= Nr / 4 ? 31 - __clz(Ms) : logNr;  // log2(nstore)
+    for (int idx = threadIdx.x; idx < nrow * nstore; idx += blockDim.x) {
+        const int c = idx >> lst;
+        const int n = idx & (nstore - 1);
         float2 v = make_float2(0.f, 0.f);
         if (n < Ms) {
             const int row = r0 + c;  // q * Mc + mc
             v = Y[(size_t)row * Ms + n];
             if (df.n > 0) v = gh_deflate(df, Q, Ms, Mc, row / Mc, row % Mc, n, v);
         }
-        x[idx] = v;
+        x[c * ld + p16(n)] = v;
     }
     __syncthreads();
-    float2* res = fft_columns(x, y, logNr, nrow, Nr, twS);
-    for (int idx = threadIdx.x; idx < nrow * Nr; idx += blockDim.x) out[(size_t)r0 * Nr + idx] = res[idx];
+    float2* res = fft_columns(x, y, logNr, nrow, ld, twS, Ms);
+    for (int idx = threadIdx.x; idx < nrow * Nr; idx += blockDim.x) {
+        const int c = idx >> logNr, n = idx & (Nr - 1);
+        out[(size_t)r0 * Nr + idx] = res[c * ld + p16(n)];
+    }
 }
 
 __global__ void __launch_bounds__(256) range_fft_kernel(const float2* __restrict__ Y, float2* __restrict__ out,
@@ -140,14 +171,15 @@ __device__ __forceinline__ void store_bin(void* maps, size_t idx, float2 v, floa
 }
 
 // Doppler FFTs of range bins i0 .. i0 + IB - 1 of receiver q of one frame,
-// times the range-centring factor, stored in type MT.
+// times the range-centring factor, stored in type MT. Shared memory:
+// 2 * IB * (gh_fft_ld(Nd) + 1) + IB + 3 Nd / 4 float2.
 template <int MT>
 __device__ __forceinline__ void doppler_cols(const float2* __restrict__ Zr, void* __restrict__ maps, int Ms, int Mc,
                                              int logNr, int logNd, int IB, int q, int i0,
                                              const float2* __restrict__ tw, float oscale, float2* smem) {
     const int Nr = 1 << logNr;
     const int Nd = 1 << logNd;
-    const int ld = Nd + 1;
+    const int ld = gh_fft_ld(Nd) + 1;  // odd column stride: the transposing loads spread over the banks
     float2* x = smem;
     float2* y = smem + IB * ld;
     float2* ramp = y + IB * ld;
@@ -157,13 +189,14 @@ __device__ __forceinline__ void doppler_cols(const float2* __restrict__ Zr, void
     for (int idx = threadIdx.x; idx < Mc * IB; idx += blockDim.x) {
         const int mc = idx / IB;
         const int c = idx - mc * IB;
-        x[c * ld + mc] = src[(size_t)mc * Nr + c];
+        x[c * ld + p16(mc)] = src[(size_t)mc * Nr + c];
     }
-    for (int idx = threadIdx.x; idx < (Nd - Mc) * IB; idx += blockDim.x) {
-        const int c = idx / (Nd - Mc);
-        const int n = Mc + (idx - c * (Nd - Mc));
-        x[c * ld + n] = make_float2(0.f, 0.f);
-    }
+    if (Mc > Nd / 4)  // the first pass reads the zero padding
+        for (int idx = threadIdx.x; idx < (Nd - Mc) * IB; idx += blockDim.x) {
+            const int c = idx / (Nd - Mc);
+            const int n = Mc + (idx - c * (Nd - Mc));
+            x[c * ld + p16(n)] = make_float2(0.f, 0.f);
+        }
     if (threadIdx.x < IB) {
         // exp(j pi (i/Nr)(Ms-1)) with the angle reduced exactly modulo 2 pi
         const long long t = ((long long)(i0 + threadIdx.x) * (Ms - 1)) % (2LL * Nr);
@@ -172,17 +205,15 @@ __device__ __forceinline__ void doppler_cols(const float2* __restrict__ Zr, void
         ramp[threadIdx.x] = make_float2(c, s);
     }
     __syncthreads();
-    float2* res = fft_columns(x, y, logNd, IB, ld, twS);
+    float2* res = fft_columns(x, y, logNd, IB, ld, twS, Mc);
     const size_t dst = ((size_t)q * Nr + i0) * Nd;
     for (int idx = threadIdx.x; idx < IB * Nd; idx += blockDim.x) {
         const int c = idx >> logNd;
         const int j = idx & (Nd - 1);
-        store_bin<MT>(maps, dst + idx, cmul(res[c * ld + j], ramp[c]), oscale);
+        store_bin<MT>(maps, dst + idx, cmul(res[c * ld + p16(j)], ramp[c]), oscale);
     }
 }
 
-// rowlim (optional): Q minima then Q maxima of the rows to compute; CTAs
-// whose range bins all lie outside leave their rows untouched.
 template <int MT>
 __global__ void __launch_bounds__(256) doppler_fft_kernel(const float2* __restrict__ Zr, void* __restrict__ maps,
                                                           int Ms, int Mc, int logNr, int logNd, int IB,
@@ -275,7 +306,7 @@ static int range_fft(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate*
     int rpc = 2048 / d.Nr;
     if (rpc < 1) rpc = 1;
     const int rows = d.Q * d.Mc;
-    size_t smem1 = ((size_t)2 * rpc * d.Nr + 3 * d.Nr / 4) * sizeof(float2);
+    size_t smem1 = ((size_t)2 * rpc * gh_fft_ld(d.Nr) + 3 * d.Nr / 4) * sizeof(float2);
     GH_CUDA(cudaFuncSetAttribute(range_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_RANGE_FFT, &ev);
@@ -305,7 +336,7 @@ int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* d
     if (IB < 1) IB = 1;
     if (IB > 16) IB = 16;
     if (IB > d.Nr) IB = d.Nr;
-    size_t smem2 = ((size_t)2 * IB * (d.Nd + 1) + IB + 3 * d.Nd / 4) * sizeof(float2);
+    size_t smem2 = ((size_t)2 * IB * (gh_fft_ld(d.Nd) + 1) + IB + 3 * d.Nd / 4) * sizeof(float2);
     const float oscale = ldexpf(1.0f, -gh_map_scale_log2(d, map_dtype));
     auto kern = map_dtype == GH_C16 ? doppler_fft_kernel<GH_C16>
               : map_dtype == GH_CBF16 ? doppler_fft_kernel<GH_CBF16> : doppler_fft_kernel<GH_C64>;
