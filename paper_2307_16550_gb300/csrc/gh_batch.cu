@@ -60,6 +60,7 @@ struct Plan {
     std::vector<int> n_active;               // per k
     int n_coord = 0, n_range = 0, n_dop = 0;
     size_t smem_range = 0, smem_dop = 0;
+    int thr_range = 32, thr_dop = 32;  // threads of the FFT kernels (enough for every item)
     unsigned long long* keys = nullptr;      // all frames' keys, contiguous
     size_t keys_bytes = 0;
     unsigned* counter = nullptr;
@@ -198,7 +199,7 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
         for (int N : {dims[f].Nr, dims[f].Nd})
             if (!tw_off.count(N)) {
                 tw_off[N] = ntw;
-                ntw += (size_t)(3 * N / 4 + 1);
+                ntw += (size_t)(N / 2);
             }
     std::vector<float2> tw(ntw);
     for (auto& kv : tw_off) gh_twiddles(kv.first, tw.data() + kv.second);
@@ -223,19 +224,19 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
         const Dims& d = dims[f];
         const long long ne = d.nxy * d.Q;
         for (long long s = 0; s < ne; s += 128) coord.push_back({f, 0, s, std::min(128LL, ne - s)});
-        const int rpc = std::max(1, 2048 / d.Nr);
+        const int rpc = gh_fft_rows_per_cta(d.Nr);
         const int rows = d.Q * d.Mc;
         for (int r = 0; r < rows; r += rpc) {
             const int c = std::min(rpc, rows - r);
             range.push_back({f, 0, r, c});
-            P.smem_range =
-                std::max(P.smem_range, ((size_t)2 * c * gh_fft_ld(d.Nr) + 3 * d.Nr / 4) * sizeof(float2));
+            P.smem_range = std::max(P.smem_range, gh_fft_smem_range(c, d.Nr));
+            P.thr_range = std::max(P.thr_range, gh_fft_threads(c * d.Nr));
         }
-        const int IB = std::min(std::min(std::max(1, 4096 / d.Nd), 16), d.Nr);
+        const int IB = gh_fft_bins_per_cta(d.Nr, d.Nd);
         for (int q = 0; q < d.Q; ++q)
             for (int i0 = 0; i0 < d.Nr; i0 += IB) dop.push_back({f, q, i0, IB});
-        P.smem_dop = std::max(P.smem_dop,
-                              ((size_t)2 * IB * (gh_fft_ld(d.Nd) + 1) + IB + 3 * d.Nd / 4) * sizeof(float2));
+        P.smem_dop = std::max(P.smem_dop, gh_fft_smem_dop(IB, d.Nd));
+        P.thr_dop = std::max(P.thr_dop, gh_fft_threads(IB * d.Nd));
         const int cls = class_of_bound[class_bound(d.Q * d.Nd)];
         P.classes[cls].max_q = std::max(P.classes[cls].max_q, d.Q);
         P.classes[cls].work += (double)d.ncells * d.Q * P.K[f];
@@ -349,8 +350,8 @@ int batch_sequence(gh_ctx* ctx, const Plan& P, const std::vector<Tuning>& t, voi
     GH_TRY(reset_frames(ctx, P));
     GH_TRY(gh_launch_coord_batch(ctx, P.frames, P.coord_items, P.n_coord));
     for (int k = 0; k < P.Kmax; ++k) {
-        GH_TRY(gh_launch_maps_batch(ctx, P.frames, P.range_items, P.n_range, 0, P.smem_range, P.dop_items, P.n_dop,
-                                    P.smem_dop, k));
+        GH_TRY(gh_launch_maps_batch(ctx, P.frames, P.range_items, P.n_range, P.thr_range, P.smem_range, P.dop_items,
+                                    P.n_dop, P.thr_dop, P.smem_dop, k));
         for (size_t c = 0; c < P.classes.size(); ++c) {
             const Plan::ScoreClass& C = P.classes[c];
             GH_TRY(gh_launch_hop_batch(ctx, P.frames, C.items[k], C.n[k], P.counter, k, t[c].ac, t[c].warps,
@@ -371,8 +372,8 @@ int batch_sequence(gh_ctx* ctx, const Plan& P, const std::vector<Tuning>& t, voi
 int autotune_prepare(gh_ctx* ctx, const Plan& P) {
     GH_TRY(reset_frames(ctx, P));
     GH_TRY(gh_launch_coord_batch(ctx, P.frames, P.coord_items, P.n_coord));
-    return gh_launch_maps_batch(ctx, P.frames, P.range_items, P.n_range, 0, P.smem_range, P.dop_items, P.n_dop,
-                                P.smem_dop, 0);
+    return gh_launch_maps_batch(ctx, P.frames, P.range_items, P.n_range, P.thr_range, P.smem_range, P.dop_items,
+                                P.n_dop, P.thr_dop, P.smem_dop, 0);
 }
 
 // Times every scorer configuration that fits in shared memory on the first

@@ -361,8 +361,8 @@ struct BatchFrame {
     int64_t* mask;              // [K] selected cells
     unsigned long long* key;    // [K] packed argmax: score bits << 32 | (2^32 - 1 - cell)
     ArgResult* sel;             // [K]
-    const float2* twr;          // exp(-j 2 pi t / Nr), t < 3 Nr / 4
-    const float2* twd;          // exp(-j 2 pi t / Nd), t < 3 Nd / 4
+    const float2* twr;          // exp(-j 2 pi t / Nr), t < Nr / 2
+    const float2* twd;          // exp(-j 2 pi t / Nd), t < Nd / 2
 };
 
 struct BatchItem {
@@ -380,12 +380,32 @@ int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* d
 int gh_launch_range_rows(gh_ctx* ctx, const Dims& d, const float2* Y, void** zr);
 // Shared-memory column length of an N-point FFT (one float2 of padding per 16).
 __host__ __device__ inline int gh_fft_ld(int N) { return N + (N >> 4); }
-// exp(-j 2 pi t / N), t < 3N/4, rounded from float64 (the FFT twiddle table).
+// Range FFT: rows of Nr points per CTA; Doppler FFT: range bins per CTA.
+inline int gh_fft_rows_per_cta(int Nr) { return Nr >= 2048 ? 1 : 2048 / Nr; }
+inline int gh_fft_bins_per_cta(int Nr, int Nd) {
+    const int IB = Nd >= 4096 ? 1 : 4096 / Nd;
+    return IB > 16 ? (Nr < 16 ? Nr : 16) : (IB > Nr ? Nr : IB);
+}
+// Shared memory of the two FFT kernels: the columns (+ the Doppler centring
+// factors) + the twiddle table of N/2 entries.
+inline size_t gh_fft_smem_range(int rows, int Nr) {
+    return ((size_t)rows * gh_fft_ld(Nr) + Nr / 2) * sizeof(float2);
+}
+inline size_t gh_fft_smem_dop(int IB, int Nd) {
+    return ((size_t)IB * (gh_fft_ld(Nd) + 2) + IB + Nd / 2) * sizeof(float2);
+}
+// Threads of an FFT CTA over `points` points: one per radix-16 butterfly
+// (the in-place passes need at least that many), in [32, 512].
+inline int gh_fft_threads(int points) {
+    const int t = points / 16;
+    return t < 32 ? 32 : t > 512 ? 512 : t;
+}
+// exp(-j 2 pi t / N), t < N/2, rounded from float64 (the FFT twiddle table).
 void gh_twiddles(int N, float2* out);
 // Batched maps (iteration k's residual applied on load); items as built by gh_batch.cu.
 int gh_launch_maps_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* range_items, int n_range,
-                         int rows_alloc, size_t smem_range, const BatchItem* dop_items, int n_dop, size_t smem_dop,
-                         int k);
+                         int thr_range, size_t smem_range, const BatchItem* dop_items, int n_dop, int thr_dop,
+                         size_t smem_dop, int k);
 // Scorer and coordinate-table parameters of one frame.
 void gh_hop_frame_params(const Dims& d, const GeoParams& g, HopParams* hp, CoordParams* cp);
 size_t gh_hop_batch_warp_bytes(int ac, int max_q_nd, int max_q);

@@ -25,136 +25,265 @@ __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2
 __device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
 // Position of element i of a column in shared memory: one float2 of padding
-// after every 16, so that the strided stores of the early passes (runs of 4
-// consecutive outputs every 16) fall into different banks.
+// after every 16, so that the strided stores of the first pass (runs of R
+// outputs every R) fall into different banks.
 __device__ __forceinline__ int p16(int i) { return i + (i >> 4); }
 
-// Ping-pong Stockham FFT of `ncol` columns of length N = 2^logN, element i of
-// column c at x[c * ld + p16(i)]: radix-4 passes, then one radix-2 pass when
-// logN is odd. When only the first nz <= N/4 inputs are nonzero (zero padding
-// by 4 or more), the first radix-4 pass reduces to replicating each input to
-// its four outputs and the other inputs are neither stored nor read.
-// tw[t] = exp(-j 2 pi t / N), t < 3N/4 (in shared memory). Returns the buffer
-// holding the transform (x or y).
-__device__ float2* fft_columns(float2* x, float2* y, int logN, int ncol, int ld, const float2* tw, int nz) {
-    const int N = 1 << logN;
-    int Ns = 1, rem = logN;
-    while (rem >= 2) {
-        const int lq = logN - 2, q4 = 1 << lq;
-        const int total = ncol << lq;
-        const int tstep = N / (4 * Ns);
-        const bool replicate = Ns == 1 && nz <= q4;
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int c = idx >> lq;
-            const int j = idx & (q4 - 1);
-            const int k = j & (Ns - 1);
-            const float2* xc = x + c * ld;
-            float2* yc = y + c * ld;
-            const int o = ((j - k) << 2) + k;
-            if (replicate) {
-                const float2 v0 = j < nz ? xc[p16(j)] : make_float2(0.f, 0.f);
-                yc[p16(o)] = v0;
-                yc[p16(o + 1)] = v0;
-                yc[p16(o + 2)] = v0;
-                yc[p16(o + 3)] = v0;
-                continue;
-            }
-            float2 v0 = xc[p16(j)], v1 = xc[p16(j + q4)], v2 = xc[p16(j + 2 * q4)], v3 = xc[p16(j + 3 * q4)];
-            if (Ns > 1) {
-                const int s = tstep * k;
-                v1 = cmul(v1, tw[s]);
-                v2 = cmul(v2, tw[2 * s]);
-                v3 = cmul(v3, tw[3 * s]);
-            }
-            const float2 a = f2add(v0, v2), b = f2sub(v0, v2), cc = f2add(v1, v3);
-            const float2 dd = f2sub(v1, v3);
-            const float2 d = make_float2(dd.y, -dd.x);  // (v1 - v3) * (-j)
-            yc[p16(o)] = f2add(a, cc);
-            yc[p16(o + Ns)] = f2add(b, d);
-            yc[p16(o + 2 * Ns)] = f2sub(a, cc);
-            yc[p16(o + 3 * Ns)] = f2sub(b, d);
+// exp(-j 2 pi t / 16) for t = 0 .. 9 (the in-register twiddles of a 16-point
+// DFT split 4 x 4): cos(pi/8), sin(pi/8) and sqrt(1/2).
+constexpr float kC8 = 0.92387953251128675613f, kS8 = 0.38268343236508977173f, kR2 = 0.70710678118654752440f;
+__host__ __device__ constexpr float cos16(int t) {
+    return t == 0 ? 1.f : t == 1 ? kC8 : t == 2 ? kR2 : t == 3 ? kS8 : t == 4 ? 0.f : t == 5 ? -kS8
+         : t == 6 ? -kR2 : t == 7 ? -kC8 : t == 8 ? -1.f : -kC8;
+}
+__host__ __device__ constexpr float sin16(int t) {
+    return t == 0 ? 0.f : t == 1 ? kS8 : t == 2 ? kR2 : t == 3 ? kC8 : t == 4 ? 1.f : t == 5 ? kC8
+         : t == 6 ? kR2 : t == 7 ? kS8 : t == 8 ? 0.f : -kS8;
+}
+
+// v * exp(-j 2 pi t / R), t and R compile-time after unrolling.
+template <int R>
+__device__ __forceinline__ float2 rot(float2 v, int t) {
+    const int u = t * (16 / R);
+    if (u == 0) return v;
+    if (u == 4) return make_float2(v.y, -v.x);
+    const float c = cos16(u), s = sin16(u);
+    return make_float2(v.x * c + v.y * s, v.y * c - v.x * s);
+}
+
+// In-register forward DFTs, natural order in and out.
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+    const float2 t = a;
+    a = f2add(t, b);
+    b = f2sub(t, b);
+}
+__device__ __forceinline__ void dft4(float2& a, float2& b, float2& c, float2& d) {
+    const float2 s0 = f2add(a, c), s1 = f2sub(a, c), s2 = f2add(b, d), t = f2sub(b, d);
+    const float2 s3 = make_float2(t.y, -t.x);  // (b - d) * (-j)
+    a = f2add(s0, s2);
+    b = f2add(s1, s3);
+    c = f2sub(s0, s2);
+    d = f2sub(s1, s3);
+}
+template <int R>
+__device__ __forceinline__ void dft(float2 (&v)[R]) {
+    if constexpr (R == 2) {
+        dft2(v[0], v[1]);
+    } else if constexpr (R == 4) {
+        dft4(v[0], v[1], v[2], v[3]);
+    } else {
+        // R = 4 x R2: n = R2 n1 + n2, k = k1 + 4 k2; 4-point DFTs over n1, the
+        // twiddles exp(-j 2 pi n2 k1 / R), then R2-point DFTs over n2
+        constexpr int R2 = R / 4;
+        float2 a[R];
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) {
+            float2 c0 = v[n2], c1 = v[R2 + n2], c2 = v[2 * R2 + n2], c3 = v[3 * R2 + n2];
+            dft4(c0, c1, c2, c3);
+            a[n2 * 4 + 0] = c0;
+            a[n2 * 4 + 1] = rot<R>(c1, n2);
+            a[n2 * 4 + 2] = rot<R>(c2, 2 * n2);
+            a[n2 * 4 + 3] = rot<R>(c3, 3 * n2);
         }
-        __syncthreads();
-        float2* t = x;
-        x = y;
-        y = t;
-        Ns <<= 2;
-        rem -= 2;
-    }
-    if (rem == 1) {
-        const int lh = logN - 1, half = 1 << lh;
-        const int total = ncol << lh;
-        const int tstep = N / (2 * Ns);
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int c = idx >> lh;
-            const int j = idx & (half - 1);
-            const int k = j & (Ns - 1);
-            const float2* xc = x + c * ld;
-            float2* yc = y + c * ld;
-            float2 a, b;
-            if (Ns == 1 && nz <= half) {  // N = 2: inputs beyond nz are zero
-                a = j < nz ? xc[p16(j)] : make_float2(0.f, 0.f);
-                b = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            if constexpr (R2 == 2) {
+                float2 b0 = a[k1], b1 = a[4 + k1];
+                dft2(b0, b1);
+                v[k1] = b0;
+                v[k1 + 4] = b1;
             } else {
-                a = xc[p16(j)];
-                b = cmul(xc[p16(j + half)], tw[tstep * k]);
+                float2 b0 = a[k1], b1 = a[4 + k1], b2 = a[8 + k1], b3 = a[12 + k1];
+                dft4(b0, b1, b2, b3);
+                v[k1] = b0;
+                v[k1 + 4] = b1;
+                v[k1 + 8] = b2;
+                v[k1 + 12] = b3;
             }
-            const int o = ((j - k) << 1) + k;
-            yc[p16(o)] = f2add(a, b);
-            yc[p16(o + Ns)] = f2sub(a, b);
         }
-        __syncthreads();
-        float2* t = x;
-        x = y;
-        y = t;
     }
-    return x;
+}
+
+// Where a Stockham pass reads its inputs and writes its outputs.
+enum { kGlobal = 0, kShared = 1 };
+
+// One radix-R Stockham pass over `ncol` columns of length N = 2^logN whose
+// sub-transforms of length Ns are done: item (c, j), k = j mod Ns, takes
+// x[j + m N/R] (m < R), multiplies it by exp(-j 2 pi m k / (R Ns)), takes the
+// R-point DFT and writes y[(j - k) R + k + r Ns] (r < R).
+//  * SRC kGlobal: the first pass (Ns = 1, no twiddles); inputs come from
+//    load(c, n), only for n < nz (the rest is the zero padding).
+//  * SRC kShared: inputs from buf[c * ld + p16(n)]; the twiddles come from
+//    tw[t] = exp(-j 2 pi t / N), t < N/2: the powers 1, 2, 4, 8 of
+//    exp(-j 2 pi k / (R Ns)) are read and the others are their products.
+//  * DST kShared: outputs to buf; with SRC kShared the pass is in place (one
+//    item per thread, all reads before a barrier, then all writes), which
+//    needs ncol N / R <= blockDim.x.
+//  * DST kGlobal: outputs to store(c, n, value).
+// CF: items numbered column-fastest (c = idx mod ncol), for loads that are
+// contiguous across columns; otherwise j-fastest.
+template <int R, int LR, int SRC, int DST, bool CF, class Load, class Store>
+__device__ __forceinline__ void fft_pass(float2* buf, int logN, int Ns, int ncol, int ld, const float2* tw, int nz,
+                                         const Load& load, const Store& store) {
+    const int lq = logN - LR, q = 1 << lq;
+    const int total = ncol << lq;
+    const int tstep = q / Ns;
+    auto item = [&](int idx, int& c, int& j, int& k, float2 (&v)[R]) {
+        if (CF) {
+            j = idx / ncol;
+            c = idx - j * ncol;
+        } else {
+            c = idx >> lq;
+            j = idx & (q - 1);
+        }
+        k = j & (Ns - 1);
+        if constexpr (SRC == kGlobal) {
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m] = j + m * q < nz ? load(c, j + m * q) : make_float2(0.f, 0.f);
+        } else {
+            const float2* xc = buf + c * ld;
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m] = xc[p16(j + m * q)];
+            if (Ns > 1) {
+                const int s = k * tstep;
+                float2 w[R];
+                w[1] = tw[s];
+                if constexpr (R >= 4) {
+                    w[2] = tw[2 * s];
+                    w[3] = cmul(w[1], w[2]);
+                }
+                if constexpr (R >= 8) {
+                    w[4] = tw[4 * s];
+#pragma unroll
+                    for (int m = 5; m < 8; ++m) w[m] = cmul(w[4], w[m - 4]);
+                }
+                if constexpr (R >= 16) {
+                    w[8] = tw[8 * s];
+#pragma unroll
+                    for (int m = 9; m < 16; ++m) w[m] = cmul(w[8], w[m - 8]);
+                }
+#pragma unroll
+                for (int m = 1; m < R; ++m) v[m] = cmul(v[m], w[m]);
+            }
+        }
+        dft<R>(v);
+    };
+    auto emit = [&](int c, int j, int k, const float2 (&v)[R]) {
+        const int o = ((j - k) << LR) + k;
+        if constexpr (DST == kShared) {
+            float2* yc = buf + c * ld;
+#pragma unroll
+            for (int r = 0; r < R; ++r) yc[p16(o + r * Ns)] = v[r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) store(c, o + r * Ns, v[r]);
+        }
+    };
+    if constexpr (SRC == kShared && DST == kShared) {
+        const bool has = (int)threadIdx.x < total;
+        int c = 0, j = 0, k = 0;
+        float2 v[R];
+        if (has) item(threadIdx.x, c, j, k, v);
+        __syncthreads();
+        if (has) emit(c, j, k, v);
+    } else {
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            int c, j, k;
+            float2 v[R];
+            item(idx, c, j, k, v);
+            emit(c, j, k, v);
+        }
+    }
+}
+
+// Last pass of an FFT: radix 2^LR with LR in [1, 4], shared memory to global.
+template <class Load, class Store>
+__device__ __forceinline__ void fft_last(float2* buf, int logN, int LR, int Ns, int ncol, int ld, const float2* tw,
+                                         int nz, const Load& load, const Store& store) {
+    switch (LR) {
+        case 1: fft_pass<2, 1, kShared, kGlobal, false>(buf, logN, Ns, ncol, ld, tw, nz, load, store); break;
+        case 2: fft_pass<4, 2, kShared, kGlobal, false>(buf, logN, Ns, ncol, ld, tw, nz, load, store); break;
+        case 3: fft_pass<8, 3, kShared, kGlobal, false>(buf, logN, Ns, ncol, ld, tw, nz, load, store); break;
+        default: fft_pass<16, 4, kShared, kGlobal, false>(buf, logN, Ns, ncol, ld, tw, nz, load, store); break;
+    }
+}
+
+// Stockham FFT of `ncol` columns of length N = 2^logN (N >= 4) from global
+// memory to global memory: input element n of column c is load(c, n) (only
+// n < nz is read: the rest is the zero padding), output bin n is passed to
+// store(c, n, value). Radix-16 passes and one last radix-2, -4, -8 or -16
+// pass; the first pass reads global memory, the last writes it, the others
+// work in place in buf (element n of column c at buf[c * ld + p16(n)],
+// ld >= N + N/16). tw: exp(-j 2 pi t / N), t < N/2, in shared memory and
+// complete before the first barrier. blockDim.x >= ncol N / 16 when N > 256.
+template <bool CF, class Load, class Store>
+__device__ __forceinline__ void fft_columns(float2* buf, int logN, int ncol, int ld, const float2* tw, int nz,
+                                            const Load& load, const Store& store) {
+    const int P = (logN + 3) >> 2;          // passes
+    const int LR = logN - 4 * (P - 1);      // log2 of the last pass's radix
+    if (P == 1) {
+        if (LR == 2) fft_pass<4, 2, kGlobal, kGlobal, CF>(buf, logN, 1, ncol, ld, tw, nz, load, store);
+        else if (LR == 3) fft_pass<8, 3, kGlobal, kGlobal, CF>(buf, logN, 1, ncol, ld, tw, nz, load, store);
+        else fft_pass<16, 4, kGlobal, kGlobal, CF>(buf, logN, 1, ncol, ld, tw, nz, load, store);
+        return;
+    }
+    fft_pass<16, 4, kGlobal, kShared, CF>(buf, logN, 1, ncol, ld, tw, nz, load, store);
+    __syncthreads();
+    int Ns = 16;
+    for (int p = 1; p < P - 1; ++p) {
+        fft_pass<16, 4, kShared, kShared, false>(buf, logN, Ns, ncol, ld, tw, nz, load, store);
+        __syncthreads();
+        Ns <<= 4;
+    }
+    fft_last(buf, logN, LR, Ns, ncol, ld, tw, nz, load, store);
 }
 
 __device__ void load_twiddles(float2* dst, const float2* __restrict__ src, int n) {
     for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = __ldg(src + t);
 }
 
+// Sample n of row `row` (= q * Mc + mc) minus the BOMP residual. Kept out of
+// line: the FFT's first pass inlines its loads once per radix, and the
+// deflation inlined at every one of them overflows the instruction cache.
+__device__ __noinline__ float2 range_deflate(Deflate df, int Q, int Ms, int Mc, int row, int n, float2 v) {
+    return gh_deflate(df, Q, Ms, Mc, row / Mc, row % Mc, n, v);
+}
+
+// Range FFT input: sample n of row r0 + c (row = q * Mc + mc), minus the
+// BOMP residual; output: bin n of that row, [Q][Mc][Nr].
+struct RangeIO {
+    const float2* __restrict__ Y;
+    float2* __restrict__ out;
+    Deflate df;
+    int Q, Ms, Mc, r0, logNr;
+    __device__ float2 operator()(int c, int n) const {
+        const int row = r0 + c;
+        const float2 v = Y[(size_t)row * Ms + n];
+        return df.n > 0 ? range_deflate(df, Q, Ms, Mc, row, n, v) : v;
+    }
+    __device__ void operator()(int c, int n, float2 v) const { out[((size_t)(r0 + c) << logNr) + n] = v; }
+};
+
 // Range FFTs of rows r0 .. r0 + nrow - 1 (row = q * Mc + mc) of one frame;
-// shared memory: 2 * rows_alloc * gh_fft_ld(Nr) + 3 Nr / 4 float2.
+// shared memory: gh_fft_smem_range(nrow, Nr) bytes.
 __device__ __forceinline__ void range_rows(const float2* __restrict__ Y, float2* __restrict__ out, int Q, int Ms,
-                                           int Mc, int logNr, int r0, int nrow, int rows_alloc, const Deflate& df,
+                                           int Mc, int logNr, int r0, int nrow, const Deflate& df,
                                            const float2* __restrict__ tw, float2* smem) {
     const int Nr = 1 << logNr;
     const int ld = gh_fft_ld(Nr);
-    float2* x = smem;
-    float2* y = smem + rows_alloc * ld;
-    float2* twS = y + rows_alloc * ld;
-    load_twiddles(twS, tw, 3 * Nr / 4);
-    // only the Ms samples are stored when the first pass can skip the zero padding
-    const int nstore = Ms <= Nr / 4 ? Ms : Nr;
-    const int lst = Ms <= Nr / 4 ? 31 - __clz(Ms) : logNr;  // log2(nstore)
-    for (int idx = threadIdx.x; idx < nrow * nstore; idx += blockDim.x) {
-        const int c = idx >> lst;
-        const int n = idx & (nstore - 1);
-        float2 v = make_float2(0.f, 0.f);
-        if (n < Ms) {
-            const int row = r0 + c;  // q * Mc + mc
-            v = Y[(size_t)row * Ms + n];
-            if (df.n > 0) v = gh_deflate(df, Q, Ms, Mc, row / Mc, row % Mc, n, v);
-        }
-        x[c * ld + p16(n)] = v;
-    }
-    __syncthreads();
-    float2* res = fft_columns(x, y, logNr, nrow, ld, twS, Ms);
-    for (int idx = threadIdx.x; idx < nrow * Nr; idx += blockDim.x) {
-        const int c = idx >> logNr, n = idx & (Nr - 1);
-        out[(size_t)r0 * Nr + idx] = res[c * ld + p16(n)];
-    }
+    float2* twS = smem + nrow * ld;
+    load_twiddles(twS, tw, Nr / 2);
+    const RangeIO io{Y, out, df, Q, Ms, Mc, r0, logNr};
+    fft_columns<false>(smem, logNr, nrow, ld, twS, Ms, io, io);
 }
 
-__global__ void __launch_bounds__(256) range_fft_kernel(const float2* __restrict__ Y, float2* __restrict__ out,
+__global__ void __launch_bounds__(512) range_fft_kernel(const float2* __restrict__ Y, float2* __restrict__ out,
                                                         int Q, int Ms, int Mc, int logNr, int rows,
                                                         int rows_per_cta, Deflate df,
                                                         const float2* __restrict__ tw) {
     extern __shared__ float2 smem[];
     const int r0 = blockIdx.x * rows_per_cta;
-    range_rows(Y, out, Q, Ms, Mc, logNr, r0, min(rows_per_cta, rows - r0), rows_per_cta, df, tw, smem);
+    range_rows(Y, out, Q, Ms, Mc, logNr, r0, min(rows_per_cta, rows - r0), df, tw, smem);
 }
 
 // One map bin in storage type MT (float32 pair, or 2^-s times the value
@@ -170,33 +299,38 @@ __device__ __forceinline__ void store_bin(void* maps, size_t idx, float2 v, floa
     }
 }
 
+// Doppler FFT input: chirp n of range bin i0 + c of receiver q ([Q][Mc][Nr]);
+// output: Doppler bin n of that range bin times the range-centring factor,
+// [Q][Nr][Nd] in storage type MT.
+template <int MT>
+struct DopplerIO {
+    const float2* __restrict__ src;  // Zr + q Mc Nr + i0
+    void* __restrict__ maps;
+    size_t dst;  // (q Nr + i0) Nd
+    const float2* ramp;
+    float oscale;
+    int Nr, logNd;
+    __device__ float2 operator()(int c, int n) const { return src[(size_t)n * Nr + c]; }
+    __device__ void operator()(int c, int n, float2 v) const {
+        store_bin<MT>(maps, dst + ((size_t)c << logNd) + n, cmul(v, ramp[c]), oscale);
+    }
+};
+
 // Doppler FFTs of range bins i0 .. i0 + IB - 1 of receiver q of one frame,
 // times the range-centring factor, stored in type MT. Shared memory:
-// 2 * IB * (gh_fft_ld(Nd) + 1) + IB + 3 Nd / 4 float2.
+// gh_fft_smem_dop(IB, Nd) bytes.
 template <int MT>
 __device__ __forceinline__ void doppler_cols(const float2* __restrict__ Zr, void* __restrict__ maps, int Ms, int Mc,
                                              int logNr, int logNd, int IB, int q, int i0,
                                              const float2* __restrict__ tw, float oscale, float2* smem) {
     const int Nr = 1 << logNr;
     const int Nd = 1 << logNd;
-    const int ld = gh_fft_ld(Nd) + 1;  // odd column stride: the transposing loads spread over the banks
-    float2* x = smem;
-    float2* y = smem + IB * ld;
-    float2* ramp = y + IB * ld;
+    // column stride = 2 mod 16 float2: the column-fastest first pass stores
+    // (8 columns x 2 items per half-warp) spread over the banks
+    const int ld = gh_fft_ld(Nd) + 2;
+    float2* ramp = smem + IB * ld;
     float2* twS = ramp + IB;
-    load_twiddles(twS, tw, 3 * Nd / 4);
-    const float2* src = Zr + (size_t)q * Mc * Nr + i0;
-    for (int idx = threadIdx.x; idx < Mc * IB; idx += blockDim.x) {
-        const int mc = idx / IB;
-        const int c = idx - mc * IB;
-        x[c * ld + p16(mc)] = src[(size_t)mc * Nr + c];
-    }
-    if (Mc > Nd / 4)  // the first pass reads the zero padding
-        for (int idx = threadIdx.x; idx < (Nd - Mc) * IB; idx += blockDim.x) {
-            const int c = idx / (Nd - Mc);
-            const int n = Mc + (idx - c * (Nd - Mc));
-            x[c * ld + p16(n)] = make_float2(0.f, 0.f);
-        }
+    load_twiddles(twS, tw, Nd / 2);
     if (threadIdx.x < IB) {
         // exp(j pi (i/Nr)(Ms-1)) with the angle reduced exactly modulo 2 pi
         const long long t = ((long long)(i0 + threadIdx.x) * (Ms - 1)) % (2LL * Nr);
@@ -204,18 +338,13 @@ __device__ __forceinline__ void doppler_cols(const float2* __restrict__ Zr, void
         sincospif((float)t / (float)Nr, &s, &c);
         ramp[threadIdx.x] = make_float2(c, s);
     }
-    __syncthreads();
-    float2* res = fft_columns(x, y, logNd, IB, ld, twS, Mc);
-    const size_t dst = ((size_t)q * Nr + i0) * Nd;
-    for (int idx = threadIdx.x; idx < IB * Nd; idx += blockDim.x) {
-        const int c = idx >> logNd;
-        const int j = idx & (Nd - 1);
-        store_bin<MT>(maps, dst + idx, cmul(res[c * ld + p16(j)], ramp[c]), oscale);
-    }
+    if (logNd <= 4) __syncthreads();  // one pass, no barrier before the stores read ramp
+    const DopplerIO<MT> io{Zr + (size_t)q * Mc * Nr + i0, maps, ((size_t)q * Nr + i0) * Nd, ramp, oscale, Nr, logNd};
+    fft_columns<true>(smem, logNd, IB, ld, twS, Mc, io, io);
 }
 
 template <int MT>
-__global__ void __launch_bounds__(256) doppler_fft_kernel(const float2* __restrict__ Zr, void* __restrict__ maps,
+__global__ void __launch_bounds__(512, 2) doppler_fft_kernel(const float2* __restrict__ Zr, void* __restrict__ maps,
                                                           int Ms, int Mc, int logNr, int logNd, int IB,
                                                           const float2* __restrict__ tw, float oscale,
                                                           const int* __restrict__ rowlim, int Q) {
@@ -227,9 +356,8 @@ __global__ void __launch_bounds__(256) doppler_fft_kernel(const float2* __restri
 
 // Batched maps of several frames: one work item (frame, first row / range
 // bin, count) per CTA; the residual of iteration k is applied on load.
-__global__ void __launch_bounds__(256) range_fft_batch_kernel(const BatchFrame* __restrict__ frames,
-                                                              const BatchItem* __restrict__ items, int k,
-                                                              int rows_alloc) {
+__global__ void __launch_bounds__(512) range_fft_batch_kernel(const BatchFrame* __restrict__ frames,
+                                                              const BatchItem* __restrict__ items, int k) {
     extern __shared__ float2 smem[];
     const BatchItem it = items[blockIdx.x];
     const BatchFrame& F = frames[it.frame];
@@ -237,12 +365,10 @@ __global__ void __launch_bounds__(256) range_fft_batch_kernel(const BatchFrame* 
     df.n = k;
     int logNr = 0;
     while ((1 << logNr) < F.d.Nr) ++logNr;
-    (void)rows_alloc;
-    range_rows(F.Y, F.zr, F.d.Q, F.d.Ms, F.d.Mc, logNr, (int)it.start, (int)it.count, (int)it.count, df, F.twr,
-               smem);
+    range_rows(F.Y, F.zr, F.d.Q, F.d.Ms, F.d.Mc, logNr, (int)it.start, (int)it.count, df, F.twr, smem);
 }
 
-__global__ void __launch_bounds__(256) doppler_fft_batch_kernel(const BatchFrame* __restrict__ frames,
+__global__ void __launch_bounds__(512, 2) doppler_fft_batch_kernel(const BatchFrame* __restrict__ frames,
                                                                 const BatchItem* __restrict__ items) {
     extern __shared__ float2 smem[];
     const BatchItem it = items[blockIdx.x];
@@ -258,7 +384,7 @@ __global__ void __launch_bounds__(256) doppler_fft_batch_kernel(const BatchFrame
 
 void gh_twiddles(int N, float2* out) {
     const double two_pi = 6.283185307179586476925286766559;
-    for (int t = 0; t < 3 * N / 4; ++t) {
+    for (int t = 0; t < N / 2; ++t) {
         const double a = -two_pi * (double)t / (double)N;
         out[t] = make_float2((float)cos(a), (float)sin(a));
     }
@@ -272,9 +398,9 @@ int ilog2(int v) {
     return l;
 }
 
-// Uploads exp(-j 2 pi t / N), t < 3N/4, for N = Nr then N = Nd (float64 -> float32).
+// Uploads exp(-j 2 pi t / N), t < N/2, for N = Nr then N = Nd (float64 -> float32).
 int ensure_twiddles(gh_ctx* ctx, int Nr, int Nd, const float2** twr, const float2** twd) {
-    const int nr = 3 * Nr / 4, nd = 3 * Nd / 4;
+    const int nr = Nr / 2, nd = Nd / 2;
     size_t bytes = (size_t)(nr + nd) * sizeof(float2);
     void* p;
     GH_TRY(gh_ws(ctx, WS_TWIDDLE, bytes, &p));
@@ -301,17 +427,18 @@ static int range_fft(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate*
     Deflate none = {nullptr, nullptr, nullptr, 0};
     void* zr;
     GH_TRY(gh_ws(ctx, WS_RANGE, (size_t)d.Q * d.Mc * d.Nr * sizeof(float2), &zr));
-    // rows of Nr points, as many rows per CTA as fit in ~32 KB
+    // rows of Nr points, 2048 points per CTA (one row when Nr > 2048), one
+    // thread per radix-16 butterfly
     const int logNr = ilog2(d.Nr);
-    int rpc = 2048 / d.Nr;
-    if (rpc < 1) rpc = 1;
+    const int rpc = gh_fft_rows_per_cta(d.Nr);
     const int rows = d.Q * d.Mc;
-    size_t smem1 = ((size_t)2 * rpc * gh_fft_ld(d.Nr) + 3 * d.Nr / 4) * sizeof(float2);
+    const size_t smem1 = gh_fft_smem_range(rpc, d.Nr);
+    const int threads = gh_fft_threads(rpc * d.Nr);
     GH_CUDA(cudaFuncSetAttribute(range_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_RANGE_FFT, &ev);
-    range_fft_kernel<<<(rows + rpc - 1) / rpc, 256, smem1, ctx->stream>>>(Y, (float2*)zr, d.Q, d.Ms, d.Mc, logNr,
-                                                                          rows, rpc, df ? *df : none, twr);
+    range_fft_kernel<<<(rows + rpc - 1) / rpc, threads, smem1, ctx->stream>>>(
+        Y, (float2*)zr, d.Q, d.Ms, d.Mc, logNr, rows, rpc, df ? *df : none, twr);
     GH_TRY(gh_launch_end(ctx, GH_K_RANGE_FFT, ev, "range_fft_kernel"));
     *zr_out = zr;
     return GH_OK;
@@ -332,30 +459,28 @@ int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* d
     const int logNr = ilog2(d.Nr), logNd = ilog2(d.Nd);
     cudaEvent_t ev;
     // Doppler FFT: IB range bins per CTA
-    int IB = 4096 / d.Nd;
-    if (IB < 1) IB = 1;
-    if (IB > 16) IB = 16;
-    if (IB > d.Nr) IB = d.Nr;
-    size_t smem2 = ((size_t)2 * IB * (gh_fft_ld(d.Nd) + 1) + IB + 3 * d.Nd / 4) * sizeof(float2);
+    const int IB = gh_fft_bins_per_cta(d.Nr, d.Nd);
+    const size_t smem2 = gh_fft_smem_dop(IB, d.Nd);
+    const int threads = gh_fft_threads(IB * d.Nd);
     const float oscale = ldexpf(1.0f, -gh_map_scale_log2(d, map_dtype));
     auto kern = map_dtype == GH_C16 ? doppler_fft_kernel<GH_C16>
               : map_dtype == GH_CBF16 ? doppler_fft_kernel<GH_CBF16> : doppler_fft_kernel<GH_C64>;
     GH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
     gh_launch_begin(ctx, GH_K_DOPPLER_FFT, &ev);
-    kern<<<dim3(d.Nr / IB, d.Q), 256, smem2, ctx->stream>>>((const float2*)zr, maps, d.Ms, d.Mc, logNr, logNd, IB,
+    kern<<<dim3(d.Nr / IB, d.Q), threads, smem2, ctx->stream>>>((const float2*)zr, maps, d.Ms, d.Mc, logNr, logNd, IB,
                                                             twd, oscale, rowlim, d.Q);
     return gh_launch_end(ctx, GH_K_DOPPLER_FFT, ev, "doppler_fft_kernel");
 }
 
 int gh_launch_maps_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* range_items, int n_range,
-                         int rows_alloc, size_t smem_range, const BatchItem* dop_items, int n_dop, size_t smem_dop,
-                         int k) {
+                         int thr_range, size_t smem_range, const BatchItem* dop_items, int n_dop, int thr_dop,
+                         size_t smem_dop, int k) {
     if (n_range > 0) {
         GH_CUDA(cudaFuncSetAttribute(range_fft_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem_range));
         cudaEvent_t ev;
         gh_launch_begin(ctx, GH_K_RANGE_FFT, &ev);
-        range_fft_batch_kernel<<<n_range, 256, smem_range, ctx->stream>>>(frames, range_items, k, rows_alloc);
+        range_fft_batch_kernel<<<n_range, thr_range, smem_range, ctx->stream>>>(frames, range_items, k);
         GH_TRY(gh_launch_end(ctx, GH_K_RANGE_FFT, ev, "range_fft_batch_kernel"));
     }
     if (n_dop > 0) {
@@ -363,7 +488,7 @@ int gh_launch_maps_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem*
                                      (int)smem_dop));
         cudaEvent_t ev;
         gh_launch_begin(ctx, GH_K_DOPPLER_FFT, &ev);
-        doppler_fft_batch_kernel<<<n_dop, 256, smem_dop, ctx->stream>>>(frames, dop_items);
+        doppler_fft_batch_kernel<<<n_dop, thr_dop, smem_dop, ctx->stream>>>(frames, dop_items);
         GH_TRY(gh_launch_end(ctx, GH_K_DOPPLER_FFT, ev, "doppler_fft_batch_kernel"));
     }
     return GH_OK;
