@@ -502,12 +502,19 @@ extern "C" int gh_make_maps(gh_ctx* ctx, const gh_radar* radar, int32_t Q, const
 
 // Coordinate table; with rowlim, also the per-receiver bounds of the map rows
 // it reads (stored after the table).
-static int build_table(gh_ctx* ctx, const Dims& d, const GeoParams& geo, void** table, int** rowlim = nullptr) {
+// Coordinate table; optionally also the map row bounds (rowlim) and the
+// float64 (r, wx, wy) of every entry (rw), after the table in WS_TABLE.
+static int build_table(gh_ctx* ctx, const Dims& d, const GeoParams& geo, void** table, int** rowlim = nullptr,
+                       double** rw = nullptr) {
     const size_t tb = (gh_hop_table_bytes(d) + 255) & ~(size_t)255;
-    GH_TRY(gh_ws(ctx, WS_TABLE, tb + 2 * GH_MAX_Q * sizeof(int), table));
+    const size_t lb = 2 * GH_MAX_Q * sizeof(int);
+    const size_t rb = rw ? (size_t)d.nxy * d.Q * 3 * sizeof(double) : 0;
+    GH_TRY(gh_ws(ctx, WS_TABLE, tb + lb + rb, table));
     int* lim = rowlim ? (int*)((char*)*table + tb) : nullptr;
     if (rowlim) *rowlim = lim;
-    return gh_launch_coord(ctx, d, geo, *table, nullptr, nullptr, nullptr, nullptr, lim);
+    double* r = rw ? (double*)((char*)*table + tb + lb) : nullptr;
+    if (rw) *rw = r;
+    return gh_launch_coord(ctx, d, geo, *table, nullptr, nullptr, nullptr, nullptr, lim, r);
 }
 
 extern "C" int gh_score_grid(gh_ctx* ctx, const gh_radar* radar, const double* tx_host, const double* rx_host,
@@ -594,7 +601,8 @@ static int detect_sequence(gh_ctx* ctx, int32_t method, const Dims& d, const Geo
     GH_TRY(gh_status_reset(ctx));
     GH_TRY(gh_bomp_reset(ctx, d, K, bws));
     int* rowlim = nullptr;  // map rows the scorer can read: the Doppler FFT skips the others
-    if (method == GH_HOP) GH_TRY(build_table(ctx, d, geo, &table, &rowlim));
+    double* rw = nullptr;   // (r, wx, wy) per coordinate entry, for the new atoms
+    if (method == GH_HOP) GH_TRY(build_table(ctx, d, geo, &table, &rowlim, &rw));
     ArgResult* sel = (ArgResult*)res;  // sel[k] = selection of iteration k
     for (int k = 0; k < K; ++k) {
         // the residual of iteration k subtracts atoms 0..k-1 (amplitudes of the last solve)
@@ -608,7 +616,7 @@ static int detect_sequence(gh_ctx* ctx, int32_t method, const Dims& d, const Geo
         } else {
             GH_TRY(gh_launch_exact_parts(ctx, d, geo, Yd, &df, nullptr, mask, k, &parts, &nparts));
         }
-        GH_TRY(gh_launch_bomp_step(ctx, d, geo, parts, nparts, Yd, sel, mask, k, K, bws));
+        GH_TRY(gh_launch_bomp_step(ctx, d, geo, parts, nparts, Yd, sel, mask, k, K, bws, rw));
     }
     // results: selections, status word and the final amplitudes (double2 [K][Q]
     // at the start of the BOMP workspace)

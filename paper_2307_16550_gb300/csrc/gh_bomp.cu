@@ -97,8 +97,12 @@ __device__ __forceinline__ void better(float s, long long c, float& bs, long lon
 // best (score, cell) of iteration k; writes sel[k] and mask[k] and prepares
 // the new atom at every receiver: (r, u) in float64, its centring phase, row
 // k of the Gram matrices and the atom tables.
-// (r, u) of receiver q at a 4D cell (Eq. 1), float64.
-__device__ __forceinline__ void cell_ru(const GeoParams& g, long long cell, int q, double* r, double* u) {
+// (r, u) of receiver q at a 4D cell (Eq. 1), float64. With rw (the
+// coordinate kernel's float64 (r, wx, wy) per (x, y, q)) the geometry is read
+// instead of recomputed: the same operations on the same values, so the same
+// (r, u).
+__device__ __forceinline__ void cell_ru(const GeoParams& g, long long cell, int q, const double* rw, double* r,
+                                        double* u) {
     const int nvy = g.n[3], nvx = g.n[2], ny = g.n[1];
     const int ivy = (int)(cell % nvy);
     cell /= nvy;
@@ -107,8 +111,15 @@ __device__ __forceinline__ void cell_ru(const GeoParams& g, long long cell, int 
     const int iy = (int)(cell % ny);
     const int ix = (int)(cell / ny);
     double d, wx, wy;
-    gh_bistatic(g, q, gh_axis(g.lo[0], g.step[0], ix), gh_axis(g.lo[1], g.step[1], iy), &d, &wx, &wy);
-    *r = gh_range(g, d);
+    if (rw) {
+        const double* e = rw + (((long long)ix * ny + iy) * g.Q + q) * 3;
+        *r = e[0];
+        wx = e[1];
+        wy = e[2];
+    } else {
+        gh_bistatic(g, q, gh_axis(g.lo[0], g.step[0], ix), gh_axis(g.lo[1], g.step[1], iy), &d, &wx, &wy);
+        *r = gh_range(g, d);
+    }
     *u = gh_speed(g, wx, wy, gh_axis(g.lo[2], g.step[2], ivx), gh_axis(g.lo[3], g.step[3], ivy));
 }
 
@@ -185,60 +196,202 @@ __global__ void __launch_bounds__(1024) bomp_select_batch_kernel(const BatchFram
     bomp_select_body(best, bestc, F.sel, F.mask, k, F.K, F.g, F.bw);
 }
 
-// Float64 normal equations of atoms 0..n-1 of receiver q (Cholesky, dependent
-// atoms dropped), amplitudes rotated back to the atoms of the signal model.
-__device__ void bomp_solve_q(int q, int Q, int Ms, int Mc, int n, int K, const double2* corr, const double2* phase,
-                             const double* gram, double2* alpha) {
-    double L[GH_MAX_K][GH_MAX_K];
-    double zr[GH_MAX_K], zi[GH_MAX_K];
-    bool dep[GH_MAX_K];
-    for (int t = 0; t < n; ++t) {
-        const double2 ph = phase[(size_t)t * Q + q];
-        const double2 ct = corr[(size_t)t * Q + q];
-        zr[t] = ph.x * ct.x - ph.y * ct.y;  // exp(+j pi ph) <Y, atom>
-        zi[t] = ph.x * ct.y + ph.y * ct.x;
+// 1 / sqrt(v) for a positive normal float64 v inside the float32 range:
+// Newton's iteration y <- y (3 - v y^2) / 2 from the float32 reciprocal
+// square root, whose relative error (about 2^-23) squares at every step:
+// two steps reach float64 rounding. (A Gram pivot lies between the
+// dependence floor 1e-9 Ms Mc and Ms Mc <= 2^26.)
+__device__ __forceinline__ double rsqrt_newton(double v) {
+    double y = (double)rsqrtf((float)v);
+    y = y * (1.5 - 0.5 * v * y * y);
+    y = y * (1.5 - 0.5 * v * y * y);
+    return y;
+}
+
+// Float64 normal equations of atoms 0..n-1 (n <= NM) of one receiver
+// (Cholesky, dependent atoms dropped), amplitudes rotated back to the atoms of
+// the signal model. G: the receiver's Gram matrix (row stride ldg); z:
+// exp(+j pi ph_t) <Y, atom_t> (stride sz); ph: the centring phases (stride
+// sp); alpha: output (stride sa). The factor is kept as rows scaled by the
+// reciprocal square roots of the pivots, so the solve has no division; the
+// loops unroll (small NM) and the factor stays in registers.
+template <int NM>
+__device__ __forceinline__ void bomp_solve_q(int Ms, int Mc, int n, const double* G, int ldg, const double2* z,
+                                             int sz, const double2* ph, int sp, double2* alpha, int sa) {
+    double L[NM][NM];
+    double zr[NM], zi[NM], rs[NM];  // rs[j] = 1 / L[j][j] (0 for a dependent atom)
+#pragma unroll
+    for (int t = 0; t < NM; ++t) {
+        if (t < n) {
+            const double2 v = z[(size_t)t * sz];
+            zr[t] = v.x;
+            zi[t] = v.y;
+        }
     }
-    const double* G = gram + (size_t)q * K * K;
     const double floor_v = 1e-9 * (double)Ms * (double)Mc;
-    for (int j = 0; j < n; ++j) {
-        for (int i = j; i < n; ++i) {
-            double v = G[i * K + j];
-            for (int t = 0; t < j; ++t) v -= L[i][t] * L[j][t];
-            if (i == j) {
-                dep[j] = !(v > floor_v);
-                L[j][j] = dep[j] ? 0.0 : sqrt(v);
-            } else {
-                L[i][j] = dep[j] ? 0.0 : v / L[j][j];
+#pragma unroll
+    for (int j = 0; j < NM; ++j) {
+        if (j < n) {
+            double v = G[j * ldg + j];
+#pragma unroll
+            for (int t = 0; t < j; ++t) v -= L[j][t] * L[j][t];
+            rs[j] = v > floor_v ? rsqrt_newton(v) : 0.0;
+#pragma unroll
+            for (int i = j + 1; i < NM; ++i) {
+                if (i < n) {
+                    double e = G[i * ldg + j];
+#pragma unroll
+                    for (int t = 0; t < j; ++t) e -= L[i][t] * L[j][t];
+                    L[i][j] = e * rs[j];
+                }
             }
         }
     }
-    for (int i = 0; i < n; ++i) {
-        if (dep[i]) {
-            zr[i] = zi[i] = 0.0;
-            continue;
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {  // L z' = z
+        if (i < n) {
+#pragma unroll
+            for (int t = 0; t < i; ++t) {
+                zr[i] -= L[i][t] * zr[t];
+                zi[i] -= L[i][t] * zi[t];
+            }
+            zr[i] *= rs[i];
+            zi[i] *= rs[i];
         }
+    }
+#pragma unroll
+    for (int i = NM - 1; i >= 0; --i) {  // L^T alpha~ = z'
+        if (i < n) {
+#pragma unroll
+            for (int t = i + 1; t < NM; ++t) {
+                if (t < n) {
+                    zr[i] -= L[t][i] * zr[t];
+                    zi[i] -= L[t][i] * zi[t];
+                }
+            }
+            zr[i] *= rs[i];
+            zi[i] *= rs[i];
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NM; ++t) {
+        if (t < n) {
+            const double2 p = ph[(size_t)t * sp];  // alpha = alpha~ exp(-j pi ph)
+            alpha[(size_t)t * sa] = make_double2(p.x * zr[t] + p.y * zi[t], p.x * zi[t] - p.y * zr[t]);
+        }
+    }
+}
+
+// The same solve for any n <= GH_MAX_K, loops not unrolled (the factor in
+// local memory).
+__device__ __noinline__ void bomp_solve_big(int Ms, int Mc, int n, const double* G, int ldg, const double2* z,
+                                            int sz, const double2* ph, int sp, double2* alpha, int sa) {
+    double L[GH_MAX_K][GH_MAX_K];
+    double zr[GH_MAX_K], zi[GH_MAX_K], rs[GH_MAX_K];
+    for (int t = 0; t < n; ++t) {
+        const double2 v = z[(size_t)t * sz];
+        zr[t] = v.x;
+        zi[t] = v.y;
+    }
+    const double floor_v = 1e-9 * (double)Ms * (double)Mc;
+    for (int j = 0; j < n; ++j) {
+        double v = G[j * ldg + j];
+        for (int t = 0; t < j; ++t) v -= L[j][t] * L[j][t];
+        rs[j] = v > floor_v ? rsqrt_newton(v) : 0.0;
+        for (int i = j + 1; i < n; ++i) {
+            double e = G[i * ldg + j];
+            for (int t = 0; t < j; ++t) e -= L[i][t] * L[j][t];
+            L[i][j] = e * rs[j];
+        }
+    }
+    for (int i = 0; i < n; ++i) {
         for (int t = 0; t < i; ++t) {
             zr[i] -= L[i][t] * zr[t];
             zi[i] -= L[i][t] * zi[t];
         }
-        zr[i] /= L[i][i];
-        zi[i] /= L[i][i];
+        zr[i] *= rs[i];
+        zi[i] *= rs[i];
     }
     for (int i = n - 1; i >= 0; --i) {
-        if (dep[i]) {
-            zr[i] = zi[i] = 0.0;
-            continue;
-        }
         for (int t = i + 1; t < n; ++t) {
             zr[i] -= L[t][i] * zr[t];
             zi[i] -= L[t][i] * zi[t];
         }
-        zr[i] /= L[i][i];
-        zi[i] /= L[i][i];
+        zr[i] *= rs[i];
+        zi[i] *= rs[i];
     }
     for (int t = 0; t < n; ++t) {
-        const double2 ph = phase[(size_t)t * Q + q];  // alpha = alpha~ exp(-j pi ph)
-        alpha[(size_t)t * Q + q] = make_double2(ph.x * zr[t] + ph.y * zi[t], ph.x * zi[t] - ph.y * zr[t]);
+        const double2 p = ph[(size_t)t * sp];
+        alpha[(size_t)t * sa] = make_double2(p.x * zr[t] + p.y * zi[t], p.x * zi[t] - p.y * zr[t]);
+    }
+}
+
+// The solve with the factor in registers for n <= 4, else in local memory.
+__device__ __forceinline__ void bomp_solve_any(int Ms, int Mc, int n, const double* G, int ldg, const double2* z,
+                                               int sz, const double2* ph, int sp, double2* alpha, int sa) {
+    if (n <= 4)
+        bomp_solve_q<4>(Ms, Mc, n, G, ldg, z, sz, ph, sp, alpha, sa);
+    else
+        bomp_solve_big(Ms, Mc, n, G, ldg, z, sz, ph, sp, alpha, sa);
+}
+
+constexpr int kSolveStage = 1024;  // doubles of shared memory for the staged solve
+
+// Last CTA of a BOMP iteration (all its threads): c_{k,q} = the sum of the
+// chunks' partial correlations (one warp per receiver, lanes over chunks,
+// then a fixed butterfly order), then every receiver's least squares. When
+// they fit, the Gram matrices, rotated correlations and phases are first
+// staged in shared memory by the whole CTA, so that the solves wait for one
+// round of loads instead of one per matrix entry.
+__device__ void bomp_sum_solve(const GeoParams& g, int k, int K, const BompPtrs& w) {
+    __shared__ double2 s_stage[kSolveStage / 2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int n = k + 1, Q = g.Q;
+    for (int qq = warp; qq < Q; qq += nw) {
+        const double2* pp = w.corrp + ((size_t)k * Q + qq) * w.chunks;
+        double cx = 0.0, cy = 0.0;
+        for (int c = lane; c < w.chunks; c += 32) {
+            const double2 v = __ldcg(pp + c);
+            cx += v.x;
+            cy += v.y;
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            cx += __shfl_xor_sync(0xffffffffu, cx, off);
+            cy += __shfl_xor_sync(0xffffffffu, cy, off);
+        }
+        if (lane == 0) w.corr[(size_t)k * Q + qq] = make_double2(cx, cy);
+    }
+    __syncthreads();
+    const int gsz = (Q * n * n + 1) & ~1;  // doubles of the Gram part, even: the double2 parts stay 16-byte aligned
+    const bool staged = (size_t)gsz + (size_t)4 * Q * n <= (size_t)kSolveStage;
+    if (staged) {
+        double* sG = (double*)s_stage;          // [Q][n][n]
+        double2* sz = s_stage + gsz / 2;        // [Q][n]
+        double2* sp = sz + Q * n;               // [Q][n]
+        for (int i = threadIdx.x; i < Q * n * n; i += blockDim.x) {
+            const int qq = i / (n * n), e = i - qq * n * n, r = e / n, c = e - r * n;
+            sG[i] = w.gram[((size_t)qq * K + r) * K + c];
+        }
+        for (int i = threadIdx.x; i < Q * n; i += blockDim.x) {
+            const int qq = i / n, t = i - qq * n;
+            const double2 p = w.phase[(size_t)t * Q + qq];
+            const double2 c = w.corr[(size_t)t * Q + qq];
+            sz[i] = make_double2(p.x * c.x - p.y * c.y, p.x * c.y + p.y * c.x);  // exp(+j pi ph) <Y, atom>
+            sp[i] = p;
+        }
+        __syncthreads();
+        for (int qq = threadIdx.x; qq < Q; qq += blockDim.x)
+            bomp_solve_any(g.Ms, g.Mc, n, sG + qq * n * n, n, sz + qq * n, 1, sp + qq * n, 1, w.alpha + qq, Q);
+    } else {
+        for (int qq = threadIdx.x; qq < Q; qq += blockDim.x) {
+            double2 z[GH_MAX_K];
+            for (int t = 0; t < n; ++t) {
+                const double2 p = w.phase[(size_t)t * Q + qq];
+                const double2 c = w.corr[(size_t)t * Q + qq];
+                z[t] = make_double2(p.x * c.x - p.y * c.y, p.x * c.y + p.y * c.x);
+            }
+            bomp_solve_any(g.Ms, g.Mc, n, w.gram + (size_t)qq * K * K, K, z, 1, w.phase + qq, Q, w.alpha + qq, Q);
+        }
     }
 }
 
@@ -289,18 +442,7 @@ __device__ void bomp_corr_body(const float2* __restrict__ Y, const GeoParams& g,
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    const int qq = threadIdx.x;
-    if (qq < g.Q) {
-        double cx = 0.0, cy = 0.0;
-        const double2* pp = w.corrp + ((size_t)k * g.Q + qq) * w.chunks;
-        for (int c = 0; c < w.chunks; ++c) {
-            const double2 v = __ldcg(pp + c);
-            cx += v.x;
-            cy += v.y;
-        }
-        w.corr[(size_t)k * g.Q + qq] = make_double2(cx, cy);
-        bomp_solve_q(qq, g.Q, g.Ms, g.Mc, k + 1, K, w.corr, w.phase, w.gram, w.alpha);
-    }
+    bomp_sum_solve(g, k, K, w);
     if (threadIdx.x == 0) *w.counter = 0u;  // ready for the next iteration
 }
 
@@ -316,7 +458,7 @@ __device__ void bomp_corr_body(const float2* __restrict__ Y, const GeoParams& g,
 __global__ void __launch_bounds__(256) bomp_step_kernel(const ArgPartial* __restrict__ parts, int nparts,
                                                         const float2* __restrict__ Y, ArgResult* __restrict__ sel,
                                                         int64_t* __restrict__ mask, int k, int K, GeoParams g,
-                                                        BompPtrs w) {
+                                                        BompPtrs w, const double* __restrict__ rw) {
     extern __shared__ float2 s_at[];  // a(r_q), Ms values
     __shared__ float s_bs[8];
     __shared__ long long s_bc[8];
@@ -348,7 +490,7 @@ __global__ void __launch_bounds__(256) bomp_step_kernel(const ArgPartial* __rest
         s_best_cell = bestc;
         const long long cell = bestc != 0x7fffffffffffffffLL ? bestc : 0;
         double r, u;
-        cell_ru(g, cell, q, &r, &u);
+        cell_ru(g, cell, q, rw, &r, &u);
         s_rf = gh_phase_fix(r);
         s_uf = gh_phase_fix(u);
         if (ch == 0) {  // the new atom's parameters at this receiver, for the last CTA
@@ -428,19 +570,8 @@ __global__ void __launch_bounds__(256) bomp_step_kernel(const ArgPartial* __rest
         G[k * K + t] = v;
         G[t * K + k] = v;
     }
-    const int qq = threadIdx.x;
-    if (qq < g.Q) {
-        double cx = 0.0, cy = 0.0;
-        const double2* pp = w.corrp + ((size_t)k * g.Q + qq) * w.chunks;
-        for (int c = 0; c < w.chunks; ++c) {
-            const double2 v = __ldcg(pp + c);
-            cx += v.x;
-            cy += v.y;
-        }
-        w.corr[(size_t)k * g.Q + qq] = make_double2(cx, cy);
-    }
     __syncthreads();  // Gram row k of every receiver written
-    if (qq < g.Q) bomp_solve_q(qq, g.Q, g.Ms, g.Mc, k + 1, K, w.corr, w.phase, w.gram, w.alpha);
+    bomp_sum_solve(g, k, K, w);
     if (threadIdx.x == 0) *w.counter = 0u;  // ready for the next iteration
 }
 
@@ -531,14 +662,14 @@ int gh_bomp_reset(gh_ctx* ctx, const Dims& d, int K, void* ws) {
 }
 
 int gh_launch_bomp_step(gh_ctx* ctx, const Dims& d, const GeoParams& g, const ArgPartial* parts, int nparts,
-                        const float2* Y, ArgResult* sel, int64_t* mask, int k, int K, void* ws) {
+                        const float2* Y, ArgResult* sel, int64_t* mask, int k, int K, void* ws, const double* rw) {
     const BompPtrs w = bomp_ptrs(ws, d, K);
     const size_t smem = (size_t)d.Ms * sizeof(float2);
     GH_CUDA(cudaFuncSetAttribute(bomp_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_BOMP, &ev);
     bomp_step_kernel<<<dim3(w.chunks, d.Q), 32 * kCorrRows, smem, ctx->stream>>>(parts, nparts, Y, sel, mask, k, K,
-                                                                                  g, w);
+                                                                                  g, w, rw);
     return gh_launch_end(ctx, GH_K_BOMP, ev, "bomp_step_kernel");
 }
 

@@ -52,7 +52,7 @@ inline uint32_t hop_tol(int nvx, int nvy) {
 // Entry idx = xy * Q + q of the coordinate table (diagnostics optional).
 __device__ __forceinline__ void coord_entry(const GeoParams& g, const CoordParams& cp, long long idx,
                                             HopEntry* __restrict__ table, int32_t* diag_i, double* diag_tau,
-                                            float* diag_c, double* diag_w) {
+                                            float* diag_c, double* diag_w, double* rw = nullptr) {
     const int q = (int)(idx % g.Q);
     const long long xy = idx / g.Q;
     const int ix = (int)(xy / g.n[1]);
@@ -110,6 +110,11 @@ __device__ __forceinline__ void coord_entry(const GeoParams& g, const CoordParam
     e.npair = wrap ? g.Nd / 2 : (int)((nu + 1) >> 1);
     e.wrap = wrap ? 1 : 0;
     table[idx] = e;
+    if (rw) {  // float64 (r, wx, wy) of the entry, for the BOMP atoms
+        rw[3 * idx] = r;
+        rw[3 * idx + 1] = wx;
+        rw[3 * idx + 2] = wy;
+    }
 
     if (diag_i) {
         diag_i[idx] = (int32_t)i;
@@ -122,9 +127,11 @@ __device__ __forceinline__ void coord_entry(const GeoParams& g, const CoordParam
 
 // rowlim (optional, device int[2Q]: Q minima preset large, then Q maxima
 // preset to -1): per receiver the smallest and largest map row any entry
-// reads (the map rows a detection's scorer can touch).
+// reads (the map rows a detection's scorer can touch). rw (optional, device
+// double[3][nxy Q]): every entry's float64 (r, wx, wy).
 __global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__ table, int32_t* diag_i,
-                             double* diag_tau, float* diag_c, double* diag_w, int* __restrict__ rowlim) {
+                             double* diag_tau, float* diag_c, double* diag_w, int* __restrict__ rowlim,
+                             double* __restrict__ rw) {
     __shared__ int s_lim[2 * GH_MAX_Q];
     const long long nxy = (long long)g.n[0] * g.n[1];
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -136,7 +143,7 @@ __global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__
         __syncthreads();
     }
     if (idx < nxy * g.Q) {
-        coord_entry(g, cp, idx, table, diag_i, diag_tau, diag_c, diag_w);
+        coord_entry(g, cp, idx, table, diag_i, diag_tau, diag_c, diag_w, rw);
         if (rowlim) {
             const int q = (int)(idx % g.Q);
             const HopEntry& e = table[idx];
@@ -599,7 +606,7 @@ CoordParams coord_params(const Dims& d) {
 size_t gh_hop_table_bytes(const Dims& d) { return (size_t)d.nxy * d.Q * sizeof(HopEntry); }
 
 int gh_launch_coord(gh_ctx* ctx, const Dims& d, const GeoParams& g, void* table, int32_t* diag_i,
-                    double* diag_tau, float* diag_c, double* diag_w, int* rowlim) {
+                    double* diag_tau, float* diag_c, double* diag_w, int* rowlim, double* rw) {
     const CoordParams cp = coord_params(d);
     const long long n = d.nxy * d.Q;
     if (rowlim) {  // minima 0x7f7f7f7f, maxima -1 (byte patterns)
@@ -609,7 +616,7 @@ int gh_launch_coord(gh_ctx* ctx, const Dims& d, const GeoParams& g, void* table,
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_COORD, &ev);
     coord_kernel<<<(unsigned)((n + 127) / 128), 128, 0, ctx->stream>>>(g, cp, (HopEntry*)table, diag_i, diag_tau,
-                                                                       diag_c, diag_w, rowlim);
+                                                                       diag_c, diag_w, rowlim, rw);
     return gh_launch_end(ctx, GH_K_COORD, ev, "coord_kernel");
 }
 
@@ -718,7 +725,7 @@ extern "C" int gh_score_grid_noalloc(void* stream_ptr, const gh_radar* radar, co
     const CoordParams cp = coord_params(d);
     const long long n = d.nxy * d.Q;
     coord_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(g, cp, table, nullptr, nullptr, nullptr, nullptr,
-                                                                   nullptr);
+                                                                   nullptr, nullptr);
     if (cudaGetLastError() != cudaSuccess) return GH_ECUDA;
     const HopParams hp = hop_params(d, g);
     long long nparts = 0;

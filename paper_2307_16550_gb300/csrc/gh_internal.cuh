@@ -426,8 +426,10 @@ int gh_bomp_chunks(const Dims& d);
 int gh_launch_batch_reset(gh_ctx* ctx, const BatchFrame* frames, int nframes);
 // Packs every frame's selections and amplitudes into out (see gh_batch.cu).
 int gh_launch_batch_gather(gh_ctx* ctx, const BatchFrame* frames, int nframes, const long long* offsets, void* out);
+// rowlim, rw: optional outputs, see coord_kernel.
 int gh_launch_coord(gh_ctx* ctx, const Dims& d, const GeoParams& g, void* table, int32_t* diag_i,
-                    double* diag_tau, float* diag_c, double* diag_w, int* rowlim = nullptr);
+                    double* diag_tau, float* diag_c, double* diag_w, int* rowlim = nullptr,
+                    double* rw = nullptr);
 size_t gh_hop_table_bytes(const Dims& d);
 // Scorer: per-CTA argmax partials into the context workspace (*parts, *nparts);
 // gh_launch_hop also reduces them into *result.
@@ -463,10 +465,13 @@ int gh_launch_residual(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflat
 // BOMP (workspace of gh_bomp_ws_bytes(d, K) bytes; the amplitudes, double2
 // [K][Q], sit at its start). Iteration k, one launch (gh_launch_bomp_step):
 // the scorer's partials -> sel[k] and mask[k], the new atom, its correlation
-// with Y and the least squares of atoms 0..k. gh_bomp_reset zeroes the
-// workspace's completion counter.
+// with Y and the least squares of atoms 0..k. rw (optional): the coordinate
+// kernel's float64 (r, wx, wy) per (x, y, q) entry, which saves recomputing
+// the new atom's geometry. gh_bomp_reset zeroes the workspace's completion
+// counter.
 size_t gh_bomp_ws_bytes(const Dims& d, int K);
 Deflate gh_bomp_deflate(void* bomp_ws, const Dims& d, int K, int n);
 int gh_bomp_reset(gh_ctx* ctx, const Dims& d, int K, void* bomp_ws);
 int gh_launch_bomp_step(gh_ctx* ctx, const Dims& d, const GeoParams& g, const ArgPartial* parts, int nparts,
-                        const float2* Y, ArgResult* sel, int64_t* mask, int k, int K, void* bomp_ws);
+                        const float2* Y, ArgResult* sel, int64_t* mask, int k, int K, void* bomp_ws,
+                        const double* rw = nullptr);
