@@ -76,6 +76,10 @@ struct gh_ctx {
     bool graphs = true;
     bool capturing = false;
     cudaStream_t capture_stream = nullptr;  // records graphs (the legacy stream cannot be captured)
+    // second stream for a branch that runs beside the main sequence (the
+    // coordinate table beside the first range FFT), forked and joined by events
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     std::vector<GraphEntry> graph_cache;
     std::vector<std::vector<unsigned char>> seen_keys;  // configurations met once
     uint64_t graph_tick = 0;
@@ -373,9 +377,11 @@ struct BatchItem {
 };
 
 // rowlim (optional): per receiver the row bounds from gh_launch_coord; rows
-// outside them are not computed (gh_detect's own maps only).
+// outside them are not computed (gh_detect's own maps only). before_doppler
+// (optional): an event the Doppler FFT waits for (the end of a branch that
+// writes rowlim beside the range FFT).
 int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* df, void* maps, int map_dtype,
-                   const int* rowlim = nullptr);
+                   const int* rowlim = nullptr, cudaEvent_t before_doppler = nullptr);
 // Zero-padded range FFT of every chirp alone: *zr = [Q][Mc][Nr] complex64 (context workspace).
 int gh_launch_range_rows(gh_ctx* ctx, const Dims& d, const float2* Y, void** zr);
 // Shared-memory column length of an N-point FFT (one float2 of padding per 16).
