@@ -166,17 +166,25 @@ __global__ void __launch_bounds__(1024) vel_kernel(const float2* __restrict__ Y,
             tw[t] = make_float2(c, s);
         }
     __syncthreads();
-    // g_q[mc] = sum_m Y[q][mc][m] conj(a_m(r_q))
-    for (int idx = threadIdx.x; idx < Q * Mc; idx += blockDim.x) {
-        const int q = idx / Mc, mc = idx - q * Mc;
-        const float2* row = Y + ((size_t)q * Mc + mc) * Ms;
-        float2 s = make_float2(0.f, 0.f);
-        for (int m = 0; m < Ms; ++m) {
-            const float2 v = __ldg(row + m), a = at[q * Ms + m];
-            s.x += v.x * a.x + v.y * a.y;
-            s.y += v.y * a.x - v.x * a.y;
+    // g_q[mc] = sum_m Y[q][mc][m] conj(a_m(r_q)): one warp per chirp, lanes
+    // over the samples (coalesced rows), then a butterfly sum
+    {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int idx = warp; idx < Q * Mc; idx += nw) {
+            const int q = idx / Mc;
+            const float2* row = Y + (size_t)idx * Ms;
+            float2 s = make_float2(0.f, 0.f);
+            for (int m = lane; m < Ms; m += 32) {
+                const float2 v = __ldg(row + m), a = at[q * Ms + m];
+                s.x += v.x * a.x + v.y * a.y;
+                s.y += v.y * a.x - v.x * a.y;
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
+                s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
+            }
+            if (lane == 0) gq[idx] = s;
         }
-        gq[idx] = s;
     }
     __syncthreads();
     if (hop) {
