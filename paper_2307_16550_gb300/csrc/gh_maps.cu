@@ -111,8 +111,9 @@ enum { kGlobal = 0, kShared = 1 };
 // sub-transforms of length Ns are done: item (c, j), k = j mod Ns, takes
 // x[j + m N/R] (m < R), multiplies it by exp(-j 2 pi m k / (R Ns)), takes the
 // R-point DFT and writes y[(j - k) R + k + r Ns] (r < R).
-//  * SRC kGlobal: the first pass (Ns = 1, no twiddles); inputs come from
-//    load(c, n), only for n < nz (the rest is the zero padding).
+//  * SRC kGlobal: the first pass (Ns = 1, no twiddles); the item's inputs
+//    n = j + m N/R come from load.load_item, only those with n < nz (the
+//    rest is the zero padding).
 //  * SRC kShared: inputs from buf[c * ld + p16(n)]; the twiddles come from
 //    tw[t] = exp(-j 2 pi t / N), t < N/2: the powers 1, 2, 4, 8 of
 //    exp(-j 2 pi k / (R Ns)) are read and the others are their products.
@@ -139,7 +140,7 @@ __device__ __forceinline__ void fft_pass(float2* buf, int logN, int Ns, int ncol
         k = j & (Ns - 1);
         if constexpr (SRC == kGlobal) {
 #pragma unroll
-            for (int m = 0; m < R; ++m) v[m] = j + m * q < nz ? load(c, j + m * q) : make_float2(0.f, 0.f);
+            load.template load_item<R>(c, j, q, nz, v);
         } else {
             const float2* xc = buf + c * ld;
 #pragma unroll
@@ -209,9 +210,9 @@ __device__ __forceinline__ void fft_last(float2* buf, int logN, int LR, int Ns, 
 }
 
 // Stockham FFT of `ncol` columns of length N = 2^logN (N >= 4) from global
-// memory to global memory: input element n of column c is load(c, n) (only
-// n < nz is read: the rest is the zero padding), output bin n is passed to
-// store(c, n, value). Radix-16 passes and one last radix-2, -4, -8 or -16
+// memory to global memory: load.load_item<R>(c, j, s, nz, v) reads the
+// inputs n = j + m s (m < R) of column c, only those with n < nz (the rest is
+// the zero padding); output bin n is passed to store(c, n, value). Radix-16 passes and one last radix-2, -4, -8 or -16
 // pass; the first pass reads global memory, the last writes it, the others
 // work in place in buf (element n of column c at buf[c * ld + p16(n)],
 // ld >= N + N/16). tw: exp(-j 2 pi t / N), t < N/2, in shared memory and
@@ -242,24 +243,39 @@ __device__ void load_twiddles(float2* dst, const float2* __restrict__ src, int n
     for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = __ldg(src + t);
 }
 
-// Sample n of row `row` (= q * Mc + mc) minus the BOMP residual. Kept out of
-// line: the FFT's first pass inlines its loads once per radix, and the
-// deflation inlined at every one of them overflows the instruction cache.
-__device__ __noinline__ float2 range_deflate(Deflate df, int Q, int Ms, int Mc, int row, int n, float2 v) {
-    return gh_deflate(df, Q, Ms, Mc, row / Mc, row % Mc, n, v);
-}
-
-// Range FFT input: sample n of row r0 + c (row = q * Mc + mc), minus the
-// BOMP residual; output: bin n of that row, [Q][Mc][Nr].
+// Range FFT input: samples n = j + m s (m < R, n < nz) of row r0 + c
+// (row = q * Mc + mc), minus the BOMP residual sum_t alpha_t b_t[mc] a_t[n]
+// (gh_deflate's arithmetic; the row's amplitude and b value are loaded once
+// per item); output: bin n of that row, [Q][Mc][Nr].
 struct RangeIO {
     const float2* __restrict__ Y;
     float2* __restrict__ out;
     Deflate df;
     int Q, Ms, Mc, r0, logNr;
-    __device__ float2 operator()(int c, int n) const {
+    template <int R>
+    __device__ __forceinline__ void load_item(int c, int j, int s, int nz, float2 (&v)[R]) const {
         const int row = r0 + c;
-        const float2 v = Y[(size_t)row * Ms + n];
-        return df.n > 0 ? range_deflate(df, Q, Ms, Mc, row, n, v) : v;
+        const float2* y = Y + (size_t)row * Ms;
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = j + m * s < nz ? y[j + m * s] : make_float2(0.f, 0.f);
+        if (df.n > 0) {
+            const int qq = row / Mc, mc = row - qq * Mc;
+            for (int t = 0; t < df.n; ++t) {
+                const double2 al = df.alpha[(size_t)t * Q + qq];
+                const float2 b = df.atoms_b[((size_t)t * Q + qq) * Mc + mc];
+                const float2* a = df.atoms_a + ((size_t)t * Q + qq) * Ms;
+                const float ax = (float)al.x, ay = (float)al.y;
+#pragma unroll
+                for (int m = 0; m < R; ++m) {
+                    if (j + m * s < nz) {
+                        const float2 av = a[j + m * s];
+                        const float2 ab = make_float2(av.x * b.x - av.y * b.y, av.x * b.y + av.y * b.x);
+                        v[m].x -= ax * ab.x - ay * ab.y;
+                        v[m].y -= ax * ab.y + ay * ab.x;
+                    }
+                }
+            }
+        }
     }
     __device__ void operator()(int c, int n, float2 v) const { out[((size_t)(r0 + c) << logNr) + n] = v; }
 };
@@ -310,7 +326,11 @@ struct DopplerIO {
     const float2* ramp;
     float oscale;
     int Nr, logNd;
-    __device__ float2 operator()(int c, int n) const { return src[(size_t)n * Nr + c]; }
+    template <int R>
+    __device__ __forceinline__ void load_item(int c, int j, int s, int nz, float2 (&v)[R]) const {
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = j + m * s < nz ? src[(size_t)(j + m * s) * Nr + c] : make_float2(0.f, 0.f);
+    }
     __device__ void operator()(int c, int n, float2 v) const {
         store_bin<MT>(maps, dst + ((size_t)c << logNd) + n, cmul(v, ramp[c]), oscale);
     }

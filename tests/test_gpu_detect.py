@@ -55,3 +55,35 @@ def test_mid_frame_exact_k3(ctx, torch_cuda):
     sc = scenes.custom_scene(5, radar, grid, Q=4, T=3, snr_db=10.0)
     Y32, Y = measurement64(sc)
     _check(ctx, torch_cuda, sc, Y32, Y, 3, "exact")
+
+
+def _many_targets(seed, Q, T):
+    radar = scenes.Radar(24e9, 250e6, 100e-6, 64, 32, 4)
+    grid = scenes.Grid.from_bounds((0, 0, -10, -10), (20, 20, 10, 10), (32, 32, 8, 8))
+    return scenes.custom_scene(seed, radar, grid, Q=Q, T=T, snr_db=None, on_grid=True)
+
+
+@pytest.mark.parametrize("method", ["hop", "exact"])
+@pytest.mark.parametrize("seed", [11, 12])
+def test_six_targets_least_squares_past_four_atoms(ctx, torch_cuda, method, seed):
+    """K = 6 noiseless on-grid targets, 3 receivers: the least squares of 5
+    and 6 atoms (the general solve, not the 4-atom register one), staged in
+    shared memory. Same cells, scores and amplitudes as the oracle, and the
+    true cells and amplitudes."""
+    sc = _many_targets(seed, 3, 6)
+    Y32, Y = measurement64(sc)
+    cells = _check(ctx, torch_cuda, sc, Y32, Y, 6, method)
+    assert sorted(cells.tolist()) == sorted(sc.target_cells.tolist())
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_ten_targets_eight_receivers_unstaged_solve(ctx, torch_cuda, seed):
+    """K = 10, Q = 8: the Gram matrices no longer fit the staging buffer
+    (Q (K^2 + 4K) > 1024 doubles), so the solve reads global memory."""
+    sc = _many_targets(seed, 8, 10)
+    Y32, Y = measurement64(sc)
+    cells = _check(ctx, torch_cuda, sc, Y32, Y, 10, "hop")
+    assert sorted(cells.tolist()) == sorted(sc.target_cells.tolist())
+    _, _, alpha = ctx.gh_detect(gh.GH_HOP, sc.radar, sc.tx, sc.rx, sc.Q, to_dev(torch_cuda, Y32), sc.grid, 10)
+    order = [list(sc.target_cells).index(c) for c in cells]
+    np.testing.assert_allclose(alpha, sc.alpha[order], atol=2e-4)
