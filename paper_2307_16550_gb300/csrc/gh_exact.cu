@@ -662,7 +662,10 @@ __global__ void __launch_bounds__(kThreadsWS, 1) exact_tc_ws_kernel(const float*
             if (ca < p.nvx) {
                 const long long cbase = xy * p.nv + (long long)ca * p.nvy;
                 bool hm = false;
-                for (int m = 0; m < nmask; ++m) hm |= (__ldg(&mask[m]) / p.nv == xy);
+                for (int m = 0; m < nmask; ++m) {  // a masked cell in this (x, y) cell's block?
+                    const long long mc = __ldg(&mask[m]);
+                    hm |= mc >= xy * p.nv && mc < (xy + 1) * p.nv;
+                }
                 float rb = -INFINITY;
                 int ri = -1;
 #pragma unroll

@@ -263,8 +263,15 @@ __device__ __forceinline__ void score_xy(const void* __restrict__ maps, const Ho
             }
         }
     }
+    // does a masked cell lie in this (x, y) cell's block [xy nv, (xy + 1) nv)?
     bool hm = false;
-    for (int m = 0; m < nmask; ++m) hm |= (__ldg(&mask[m]) / p.nv == xy);
+    {
+        const long long lo = xy * p.nv, hi = lo + p.nv;
+        for (int m = 0; m < nmask; ++m) {
+            const long long mc = __ldg(&mask[m]);
+            hm |= mc >= lo && mc < hi;
+        }
+    }
     __syncwarp();  // P rows complete
     if (!active) return;
     const long long cbase = xy * p.nv;
