@@ -329,35 +329,53 @@ __device__ __forceinline__ bool chol4_solve(double A[4][4], const double b[4], d
 // Damped Newton (Levenberg-Marquardt) ascent of every point for at most
 // `iters` iterations. The Hessian comes from central differences of the
 // analytic gradient (steps 1e-3 of the per-axis scales sc); a step solves
-// (-H + lambda D) d = g with D = diag(1 / sc^2); a step that raises S is
+// (-H + lambda diag(1/sc^2)) d = g (Cholesky); if it increases S the step is
 // taken and lambda shrinks by 3, otherwise lambda grows by 4 (at most 40
 // trials). The first lambda makes the step about `step` scale units long.
-// Every lane of the warp holds the same values (the sums over receivers are
-// butterfly reductions), so control flow stays warp-uniform.
+// One warp per point, split into 32/G groups of G lanes (G = the power of two
+// >= Q, at most 32; a group evaluates one point, receivers over its lanes).
+// The groups evaluate the 8 displaced gradients of the Hessian side by side,
+// and consecutive damping trials lambda, 4 lambda, 16 lambda, ... side by side
+// (the first improving one in that order is taken, as a sequential search
+// would). Every lane ends each stage with the same values, so control flow
+// stays warp-uniform.
 template <int MT>
 __global__ void __launch_bounds__(128) refine_kernel(const void* __restrict__ maps, PtParams p,
                                                     const double* __restrict__ rx, double* __restrict__ pts,
                                                     long long P, int iters, double sx, double sv, double step,
-                                                    float* __restrict__ S) {
+                                                    float* __restrict__ S, int G) {
     const long long pt = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (pt >= P) return;
+    const int lane = threadIdx.x & 31, gi = lane / G, NG = 32 / G;
     double* a = pts + 4 * pt;
     double x[4] = {a[0], a[1], a[2], a[3]};
     const double sc[4] = {sx, sx, sv, sv};
     double g[4];
-    double cur = point_grad<MT>(maps, p, rx, x[0], x[1], x[2], x[3], 0.f, nullptr, nullptr, g, 32);
+    double cur = point_grad<MT>(maps, p, rx, x[0], x[1], x[2], x[3], 0.f, nullptr, nullptr, g, G);
     double lam = -1.0;
     for (int it = 0; it < iters; ++it) {
+        // gradients at x +- del e_c, evaluation e = 2 c + (0: +, 1: -)
+        double gpm[8][4];
+        for (int e0 = 0; e0 < 8; e0 += NG) {
+            const int e = e0 + gi;
+            double xe[4] = {x[0], x[1], x[2], x[3]};
+            if (e < 8) {
+                const int c = e >> 1;
+                const double del = 1e-3 * sc[c];
+                if (e & 1)
+                    xe[c] -= del;
+                else
+                    xe[c] += del;
+            }
+            double ge[4];
+            point_grad<MT>(maps, p, rx, xe[0], xe[1], xe[2], xe[3], 0.f, nullptr, nullptr, ge, G);
+            for (int k = 0; k < NG && e0 + k < 8; ++k)
+                for (int r = 0; r < 4; ++r) gpm[e0 + k][r] = __shfl_sync(0xffffffffu, ge[r], k * G);
+        }
         double H[4][4];
         for (int c = 0; c < 4; ++c) {
             const double del = 1e-3 * sc[c];
-            double xp[4] = {x[0], x[1], x[2], x[3]}, xm[4] = {x[0], x[1], x[2], x[3]};
-            xp[c] += del;
-            xm[c] -= del;
-            double gp[4], gm[4];
-            point_grad<MT>(maps, p, rx, xp[0], xp[1], xp[2], xp[3], 0.f, nullptr, nullptr, gp, 32);
-            point_grad<MT>(maps, p, rx, xm[0], xm[1], xm[2], xm[3], 0.f, nullptr, nullptr, gm, 32);
-            for (int r = 0; r < 4; ++r) H[r][c] = (gp[r] - gm[r]) / (2.0 * del);
+            for (int r = 0; r < 4; ++r) H[r][c] = (gpm[2 * c][r] - gpm[2 * c + 1][r]) / (2.0 * del);
         }
         for (int r = 0; r < 4; ++r)
             for (int c = r + 1; c < 4; ++c) H[r][c] = H[c][r] = 0.5 * (H[r][c] + H[c][r]);
@@ -368,27 +386,30 @@ __global__ void __launch_bounds__(128) refine_kernel(const void* __restrict__ ma
             if (!(lam > 0.0)) break;  // zero gradient: nothing to do
         }
         bool moved = false;
-        for (int trial = 0; trial < 40 && !moved; ++trial) {
-            double A[4][4], d[4];
+        for (int t0 = 0; t0 < 40 && !moved; t0 += NG) {
+            double lt = lam;  // lambda of trial t0 + gi: lam 4^gi (exact: powers of two)
+            for (int i = 0; i < gi; ++i) lt *= 4.0;
+            double A[4][4], d[4] = {0.0, 0.0, 0.0, 0.0};
             for (int r = 0; r < 4; ++r)
-                for (int c = 0; c < 4; ++c) A[r][c] = -H[r][c] + (r == c ? lam / (sc[r] * sc[r]) : 0.0);
-            if (chol4_solve(A, g, d)) {
-                const double y0 = x[0] + d[0], y1 = x[1] + d[1], y2 = x[2] + d[2], y3 = x[3] + d[3];
-                double gy[4];
-                const double val = point_grad<MT>(maps, p, rx, y0, y1, y2, y3, 0.f, nullptr, nullptr, gy, 32);
-                if (val > cur) {
-                    x[0] = y0;
-                    x[1] = y1;
-                    x[2] = y2;
-                    x[3] = y3;
-                    for (int c = 0; c < 4; ++c) g[c] = gy[c];
-                    cur = val;
-                    lam /= 3.0;
-                    moved = true;
-                    break;
-                }
+                for (int c = 0; c < 4; ++c) A[r][c] = -H[r][c] + (r == c ? lt / (sc[r] * sc[r]) : 0.0);
+            const bool ok = t0 + gi < 40 && chol4_solve(A, g, d);
+            const double y0 = x[0] + d[0], y1 = x[1] + d[1], y2 = x[2] + d[2], y3 = x[3] + d[3];
+            double gy[4];
+            const double val = point_grad<MT>(maps, p, rx, y0, y1, y2, y3, 0.f, nullptr, nullptr, gy, G);
+            const unsigned win = __ballot_sync(0xffffffffu, ok && val > cur && (lane % G) == 0);
+            if (win) {
+                const int src = __ffs(win) - 1;  // the smallest improving lambda
+                x[0] = __shfl_sync(0xffffffffu, y0, src);
+                x[1] = __shfl_sync(0xffffffffu, y1, src);
+                x[2] = __shfl_sync(0xffffffffu, y2, src);
+                x[3] = __shfl_sync(0xffffffffu, y3, src);
+                for (int c = 0; c < 4; ++c) g[c] = __shfl_sync(0xffffffffu, gy[c], src);
+                cur = __shfl_sync(0xffffffffu, val, src);
+                lam = __shfl_sync(0xffffffffu, lt, src) / 3.0;
+                moved = true;
+            } else {
+                for (int i = 0; i < NG; ++i) lam *= 4.0;
             }
-            lam *= 4.0;
         }
         if (!moved) break;  // no improving step at any damping: converged
     }
@@ -481,13 +502,15 @@ int gh_launch_refine(gh_ctx* ctx, const Dims& d, const GeoParams& g, const void*
     if (P == 0) return GH_OK;
     const PtParams p = pt_params(d, g, map_dtype);
     const unsigned blocks = (unsigned)((P * 32 + 127) / 128);
+    const int G = group_width(d.Q);
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_POINTS, &ev);
     if (map_dtype == GH_C16)
-        refine_kernel<GH_C16><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, iters, sx, sv, step, S);
+        refine_kernel<GH_C16><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, iters, sx, sv, step, S, G);
     else if (map_dtype == GH_CBF16)
-        refine_kernel<GH_CBF16><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, iters, sx, sv, step, S);
+        refine_kernel<GH_CBF16><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, iters, sx, sv, step, S,
+                                                                 G);
     else
-        refine_kernel<GH_C64><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, iters, sx, sv, step, S);
+        refine_kernel<GH_C64><<<blocks, 128, 0, ctx->stream>>>(maps, p, rx_dev, pts, P, iters, sx, sv, step, S, G);
     return gh_launch_end(ctx, GH_K_POINTS, ev, "refine_kernel");
 }
