@@ -85,7 +85,8 @@ extern "C" {
 #define GH_K_EXACT_S2    7
 #define GH_K_SYNTH       8
 #define GH_K_POINTS      9   /* continuous-point scores, adjoint, refinement */
-#define GH_K_COUNT       10
+#define GH_K_DEFLATE     10  /* maps of a BOMP residual by linearity (atom maps subtracted) */
+#define GH_K_COUNT       11
 
 /* Size limits checked by every entry point (GH_EINVAL beyond them). */
 #define GH_MAX_Q        64

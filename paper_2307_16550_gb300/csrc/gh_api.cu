@@ -640,7 +640,11 @@ static int detect_sequence(gh_ctx* ctx, int32_t method, const Dims& d, const Geo
         ArgPartial* parts;
         int nparts;
         if (method == GH_HOP) {
-            GH_TRY(gh_launch_maps(ctx, d, Yd, &df, maps, ctx->detect_maps, rowlim, k == 0 ? ctx->join_ev : nullptr));
+            if (k > 0 && ctx->detect_maps == GH_C64)  // residual maps by linearity, in place
+                GH_TRY(gh_launch_maps_deflate(ctx, d, df, maps, rowlim));
+            else
+                GH_TRY(gh_launch_maps(ctx, d, Yd, &df, maps, ctx->detect_maps, rowlim,
+                                      k == 0 ? ctx->join_ev : nullptr));
             GH_TRY(gh_launch_hop_parts(ctx, d, geo, maps, ctx->detect_maps, table, nullptr, mask, k, &parts,
                                        &nparts));
         } else {

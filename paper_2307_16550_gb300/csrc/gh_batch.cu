@@ -3,7 +3,9 @@
 // size at once. Every step is one launch for the whole batch:
 //   coordinate tables         coord_batch_kernel       (once)
 //   per iteration k:
-//     maps of the residuals   range_fft_batch_kernel, doppler_fft_batch_kernel
+//     maps                    k = 0: range_fft_batch_kernel, doppler_fft_batch_kernel;
+//                             k > 0: maps_deflate_batch_kernel (the residual's
+//                             maps by linearity, as gh_detect does)
 //     scores + argmax         hop_batch_kernel (persistent; warps take work
 //                             items from a counter; per-frame packed argmax)
 //     selection, new atom     bomp_select_batch_kernel (one CTA per frame)
@@ -58,6 +60,8 @@ struct Plan {
     std::vector<ScoreClass> classes;
     std::vector<int*> active;                // per k
     std::vector<int> n_active;               // per k
+    std::vector<BatchItem*> defl_items;      // per k: residual maps by linearity (k >= 1, active frames)
+    std::vector<int> n_defl;                 // per k
     int n_coord = 0, n_range = 0, n_dop = 0;
     size_t smem_range = 0, smem_dop = 0;
     int thr_range = 32, thr_dop = 32;  // threads of the FFT kernels (enough for every item)
@@ -220,6 +224,7 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
     std::vector<std::vector<std::vector<BatchItem>>> score(P.classes.size(),
                                                           std::vector<std::vector<BatchItem>>(P.Kmax));
     std::vector<std::vector<int>> active(P.Kmax);
+    std::vector<std::vector<BatchItem>> defl(P.Kmax);
     for (int f = 0; f < nframes; ++f) {
         const Dims& d = dims[f];
         const long long ne = d.nxy * d.Q;
@@ -240,6 +245,9 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
         const int cls = class_of_bound[class_bound(d.Q * d.Nd)];
         P.classes[cls].max_q = std::max(P.classes[cls].max_q, d.Q);
         P.classes[cls].work += (double)d.ncells * d.Q * P.K[f];
+        for (int k = 1; k < P.K[f]; ++k)
+            for (int q = 0; q < d.Q; ++q)
+                for (int i0 = 0; i0 < d.Nr; i0 += IB) defl[k].push_back({f, q, i0, IB});
         for (int k = 0; k < P.K[f]; ++k) {
             active[k].push_back(f);
             for (long long s = 0; s < d.nxy; s += kBatchXyPerItem)
@@ -264,10 +272,11 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
     const size_t m_range = take(range.size() * sizeof(BatchItem));
     const size_t m_dop = take(dop.size() * sizeof(BatchItem));
     std::vector<std::vector<size_t>> m_score(P.classes.size(), std::vector<size_t>(P.Kmax));
-    std::vector<size_t> m_active(P.Kmax);
+    std::vector<size_t> m_active(P.Kmax), m_defl(P.Kmax);
     for (int k = 0; k < P.Kmax; ++k) {
         for (size_t c = 0; c < P.classes.size(); ++c) m_score[c][k] = take(score[c][k].size() * sizeof(BatchItem));
         m_active[k] = take(active[k].size() * sizeof(int));
+        m_defl[k] = take(defl[k].size() * sizeof(BatchItem));
     }
     const size_t m_tw = take(ntw * sizeof(float2));
     const size_t m_outoff = take(nframes * sizeof(long long));
@@ -314,6 +323,7 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
         for (size_t c = 0; c < P.classes.size(); ++c)
             put(m_score[c][k], score[c][k].data(), score[c][k].size() * sizeof(BatchItem));
         put(m_active[k], active[k].data(), active[k].size() * sizeof(int));
+        put(m_defl[k], defl[k].data(), defl[k].size() * sizeof(BatchItem));
     }
     put(m_tw, tw.data(), ntw * sizeof(float2));
     put(m_outoff, P.out_off.data(), nframes * sizeof(long long));
@@ -334,6 +344,8 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
         }
         P.active.push_back((int*)(M + m_active[k]));
         P.n_active.push_back((int)active[k].size());
+        P.defl_items.push_back((BatchItem*)(M + m_defl[k]));
+        P.n_defl.push_back((int)defl[k].size());
     }
     P.out_off_dev = (long long*)(M + m_outoff);
     P.out_dev = M + m_out;
@@ -350,8 +362,11 @@ int batch_sequence(gh_ctx* ctx, const Plan& P, const std::vector<Tuning>& t, voi
     GH_TRY(reset_frames(ctx, P));
     GH_TRY(gh_launch_coord_batch(ctx, P.frames, P.coord_items, P.n_coord));
     for (int k = 0; k < P.Kmax; ++k) {
-        GH_TRY(gh_launch_maps_batch(ctx, P.frames, P.range_items, P.n_range, P.thr_range, P.smem_range, P.dop_items,
-                                    P.n_dop, P.thr_dop, P.smem_dop, k));
+        if (k == 0)  // maps of the measurements
+            GH_TRY(gh_launch_maps_batch(ctx, P.frames, P.range_items, P.n_range, P.thr_range, P.smem_range,
+                                        P.dop_items, P.n_dop, P.thr_dop, P.smem_dop, 0));
+        else  // maps of the residuals by linearity, frames still iterating
+            GH_TRY(gh_launch_maps_deflate_batch(ctx, P.frames, P.defl_items[k], P.n_defl[k], k));
         for (size_t c = 0; c < P.classes.size(); ++c) {
             const Plan::ScoreClass& C = P.classes[c];
             GH_TRY(gh_launch_hop_batch(ctx, P.frames, C.items[k], C.n[k], P.counter, k, t[c].ac, t[c].warps,

@@ -28,7 +28,7 @@ namespace {
 constexpr int kCorrRows = 8;  // chirps per correlation CTA (one per warp)
 
 struct BompLayout {
-    size_t alpha, corr, ru, phase, gram, corrp, atoms_a, atoms_b, counter, total;
+    size_t alpha, corr, ru, phase, gram, corrp, atoms_a, atoms_b, alpha_prev, tab_a, tab_b, counter, total;
     int chunks;
 };
 
@@ -49,7 +49,10 @@ BompLayout bomp_layout(const Dims& d, int K) {
     L.corrp = take((size_t)K * d.Q * L.chunks * 2 * sizeof(double));  // double2 [K][Q][chunks]
     L.atoms_a = take((size_t)K * d.Q * d.Ms * sizeof(float2));
     L.atoms_b = take((size_t)K * d.Q * d.Mc * sizeof(float2));
-    L.counter = take(sizeof(unsigned int));
+    L.alpha_prev = take((size_t)K * d.Q * 2 * sizeof(double));  // double2 [K][Q]
+    L.tab_a = take((size_t)K * d.Q * d.Nr * sizeof(float2));      // [K][Q][Nr]
+    L.tab_b = take((size_t)K * d.Q * d.Nd * sizeof(float2));      // [K][Q][Nd]
+    L.counter = take((size_t)(1 + K * d.Q) * sizeof(unsigned int));  // completion counter, then [K][Q] table counters
     L.total = o;
     return L;
 }
@@ -67,7 +70,11 @@ BompPtrs bomp_ptrs(void* ws, const Dims& d, int K) {
     w.corrp = (double2*)(b + L.corrp);
     w.atoms_a = (float2*)(b + L.atoms_a);
     w.atoms_b = (float2*)(b + L.atoms_b);
+    w.alpha_prev = (double2*)(b + L.alpha_prev);
+    w.tab_a = (float2*)(b + L.tab_a);
+    w.tab_b = (float2*)(b + L.tab_b);
     w.counter = (unsigned int*)(b + L.counter);
+    w.tab_counter = w.counter + 1;
     w.chunks = L.chunks;
     return w;
 }
@@ -84,6 +91,79 @@ __device__ double dirichlet(double f, int M) {
         return ((n * (long long)(M - 1)) & 1) ? -(double)M : (double)M;
     }
     return (double)(sinpif(mod2f((double)M * f)) / s);
+}
+
+// sin(2 pi x 2^-64) with full relative precision: x is reduced to its distance
+// v <= 2^62 from the nearest multiple of half a cycle before the float
+// conversion.
+__device__ __forceinline__ float sin2pi_fix(uint64_t x) {
+    const uint64_t w = x & 0x7fffffffffffffffull;
+    const uint64_t v = w < (1ull << 62) ? w : (1ull << 63) - w;
+    const float s = sinpif((float)v * 1.08420217248550443e-19f);  // 2^-63
+    return (x >> 63) ? -s : s;
+}
+
+// F_M(f) = sum_{m < M} exp(j 2 pi f m) = exp(j pi f (M-1)) sin(pi M f) / sin(pi f)
+// for f = ph 2^-64 (a fixed-point phase; F is 1-periodic), M an even power of
+// two. The arguments are reduced exactly in integer arithmetic: M f mod 2 from
+// ph M/2 mod 2^64, the phase f (M-1)/2 mod 1 from the 128-bit product
+// ph (M-1), sin(pi f) from the distance of f to the nearest integer.
+__device__ __forceinline__ float2 dtft_fix(uint64_t ph, int M) {
+    const uint64_t h = ph < (1ull << 63) ? ph : (0ull - ph);
+    if (h == 0) return make_float2((float)M, 0.f);
+    const float sf = sinpif((float)h * 5.42101086242752217e-20f);  // sin(pi f) > 0, 2^-64
+    const float sm = sin2pi_fix(ph * (uint64_t)(M >> 1));           // sin(pi M f)
+    const uint64_t lo = ph * (uint64_t)(M - 1), hi = __umul64hi(ph, (uint64_t)(M - 1));
+    const float2 e = gh_cis_fix((lo >> 1) | (hi << 63));
+    const float d = sm / sf;
+    return make_float2(e.x * d, e.y * d);
+}
+
+// Maps of the signal-model atom b(u) (x) a(r) as the map maker computes them
+// (Sec. III; its bins are the inner products of Sec. IV): the 2D DFT of the
+// atom, times the range-centring factor, is A[i] B[j] with
+//   A[i] = exp(j pi i (Ms-1) / Nr) F_Ms(r - i/Nr),   B[j] = F_Mc(u - j/Nd),
+// from the fixed-point phases rf, uf of r and u (Nr, Nd powers of two, so
+// i/Nr and j/Nd are exact phase steps). Written by threads t0, t0 + nt, ...
+// of the calling group.
+// Entry e of the tables: A[e] for e < Nr, else B[e - Nr] (e < Nr + Nd).
+__device__ __forceinline__ void atom_map_entry(uint64_t rf, uint64_t uf, int Ms, int Mc, int Nr, int Nd,
+                                               float2* __restrict__ A, float2* __restrict__ B, int e) {
+    if (e < Nr) {
+        const uint64_t sr = 0ull - (~0ull / (uint64_t)Nr + 1ull);  // -2^64 / Nr (mod 2^64)
+        const float2 f = dtft_fix(rf + (uint64_t)e * sr, Ms);
+        // exp(j pi i (Ms-1) / Nr), the angle reduced exactly (as the Doppler FFT does)
+        const int t = (int)(((unsigned)e * (unsigned)(Ms - 1)) & (unsigned)(2 * Nr - 1));
+        float s, c;
+        sincospif((float)t / (float)Nr, &s, &c);
+        A[e] = make_float2(c * f.x - s * f.y, c * f.y + s * f.x);
+    } else {
+        const int j = e - Nr;
+        const uint64_t sd = 0ull - (~0ull / (uint64_t)Nd + 1ull);  // -2^64 / Nd
+        B[j] = dtft_fix(uf + (uint64_t)j * sd, Mc);
+    }
+}
+
+__device__ void atom_map_tables(uint64_t rf, uint64_t uf, int Ms, int Mc, int Nr, int Nd, float2* __restrict__ A,
+                                float2* __restrict__ B, int t0, int nt) {
+    for (int e = t0; e < Nr + Nd; e += nt) atom_map_entry(rf, uf, Ms, Mc, Nr, Nd, A, B, e);
+}
+
+// The tables of one atom and receiver, shared out in slices of blockDim.x
+// entries through a counter (zeroed before the detection) among the CTAs that
+// call this; every CTA of the group calls it, so every slice gets taken.
+__device__ void atom_map_tables_shared(uint64_t rf, uint64_t uf, int Ms, int Mc, int Nr, int Nd,
+                                       float2* __restrict__ A, float2* __restrict__ B, unsigned* counter) {
+    __shared__ unsigned s_base;
+    for (;;) {
+        if (threadIdx.x == 0) s_base = atomicAdd(counter, blockDim.x);
+        __syncthreads();
+        const unsigned base = s_base;
+        __syncthreads();
+        if (base >= (unsigned)(Nr + Nd)) break;
+        const unsigned e = base + threadIdx.x;
+        if (e < (unsigned)(Nr + Nd)) atom_map_entry(rf, uf, Ms, Mc, Nr, Nd, A, B, (int)e);
+    }
 }
 
 __device__ __forceinline__ void better(float s, long long c, float& bs, long long& bc) {
@@ -178,6 +258,9 @@ __device__ void bomp_select_body(float best, long long bestc, ArgResult* __restr
         const int qq = idx / g.Mc, m = idx - qq * g.Mc;
         w.atoms_b[((size_t)k * g.Q + qq) * g.Mc + m] = gh_cis_fix(s_uf[qq] * (unsigned long long)m);
     }
+    for (int qq = 0; qq < g.Q; ++qq)
+        atom_map_tables(s_rf[qq], s_uf[qq], g.Ms, g.Mc, g.Nr, g.Nd, w.tab_a + ((size_t)k * g.Q + qq) * g.Nr,
+                        w.tab_b + ((size_t)k * g.Q + qq) * g.Nd, threadIdx.x, blockDim.x);
 }
 
 
@@ -347,6 +430,10 @@ __device__ void bomp_sum_solve(const GeoParams& g, int k, int K, const BompPtrs&
     __shared__ double2 s_stage[kSolveStage / 2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int n = k + 1, Q = g.Q;
+    // the amplitudes the maps of this iteration's residual hold (atom k: none),
+    // kept before the solve replaces them
+    for (int i = threadIdx.x; i < n * Q; i += blockDim.x)
+        w.alpha_prev[i] = i < k * Q ? w.alpha[i] : make_double2(0.0, 0.0);
     for (int qq = warp; qq < Q; qq += nw) {
         const double2* pp = w.corrp + ((size_t)k * Q + qq) * w.chunks;
         double cx = 0.0, cy = 0.0;
@@ -546,7 +633,16 @@ __global__ void __launch_bounds__(256) bomp_step_kernel(const ArgPartial* __rest
         s_last = atomicAdd(w.counter, 1u) == gridDim.x * gridDim.y - 1;
     }
     __syncthreads();
-    if (!s_last) return;
+    // the new atom's maps at this receiver (for the next iteration's residual
+    // maps), shared out among this receiver's CTAs that are done, so that the
+    // last CTA's work does not wait for them; the last CTA takes what is left
+    float2* tab_a = w.tab_a + ((size_t)k * g.Q + q) * g.Nr;
+    float2* tab_b = w.tab_b + ((size_t)k * g.Q + q) * g.Nd;
+    unsigned* tab_cnt = w.tab_counter + (size_t)k * g.Q + q;
+    if (!s_last) {
+        atom_map_tables_shared(s_rf, s_uf, g.Ms, g.Mc, g.Nr, g.Nd, tab_a, tab_b, tab_cnt);
+        return;
+    }
     __threadfence();
     if (threadIdx.x == 0) {
         const bool valid = s_best_cell != 0x7fffffffffffffffLL;
@@ -573,6 +669,7 @@ __global__ void __launch_bounds__(256) bomp_step_kernel(const ArgPartial* __rest
     __syncthreads();  // Gram row k of every receiver written
     bomp_sum_solve(g, k, K, w);
     if (threadIdx.x == 0) *w.counter = 0u;  // ready for the next iteration
+    atom_map_tables_shared(s_rf, s_uf, g.Ms, g.Mc, g.Nr, g.Nd, tab_a, tab_b, tab_cnt);
 }
 
 // Batched correlations: grid (max chunks, max Q, listed frames).
@@ -652,12 +749,15 @@ Deflate gh_bomp_deflate(void* ws, const Dims& d, int K, int n) {
     f.atoms_a = w.atoms_a;
     f.atoms_b = w.atoms_b;
     f.n = n;
+    f.alpha_prev = w.alpha_prev;
+    f.tab_a = w.tab_a;
+    f.tab_b = w.tab_b;
     return f;
 }
 
 int gh_bomp_reset(gh_ctx* ctx, const Dims& d, int K, void* ws) {
     const BompPtrs w = bomp_ptrs(ws, d, K);
-    GH_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned int), ctx->stream));
+    GH_CUDA(cudaMemsetAsync(w.counter, 0, (size_t)(1 + K * d.Q) * sizeof(unsigned int), ctx->stream));
     return GH_OK;
 }
 

@@ -197,9 +197,12 @@ struct CoordParams {
 // BOMP workspace pointers (gh_bomp.cu).
 struct BompPtrs {
     double2 *alpha, *corr, *ru, *phase, *corrp;
+    double2* alpha_prev;     // the amplitudes the residual maps hold (see Deflate)
     double* gram;
     float2 *atoms_a, *atoms_b;
-    unsigned int* counter;
+    float2 *tab_a, *tab_b;   // maps of the atoms: range [K][Q][Nr], Doppler [K][Q][Nd]
+    unsigned int* counter;   // CTAs done with the current iteration
+    unsigned int* tab_counter;  // [K][Q] table entries handed out (zeroed with counter)
     int chunks;
 };
 
@@ -313,6 +316,12 @@ struct Deflate {
     const float2* atoms_a;   // [K][Q][Ms] a(r_t,q)
     const float2* atoms_b;   // [K][Q][Mc] b(u_t,q)
     int n;                   // atoms to subtract (0: Y unchanged)
+    // Maps of the residual by linearity (gh_launch_maps_deflate): the map of
+    // atom t at receiver q is tab_a[t][q][i] tab_b[t][q][j]; the maps hold the
+    // amplitudes alpha_prev, so alpha - alpha_prev is what is left to subtract.
+    const double2* alpha_prev;  // [K][Q]
+    const float2* tab_a;        // [K][Q][Nr]
+    const float2* tab_b;        // [K][Q][Nd]
 };
 
 __device__ __forceinline__ float2 gh_deflate(const Deflate& f, int Q, int Ms, int Mc, int q, int mc, int m,
@@ -408,6 +417,14 @@ inline int gh_fft_threads(int points) {
 }
 // exp(-j 2 pi t / N), t < N/2, rounded from float64 (the FFT twiddle table).
 void gh_twiddles(int N, float2* out);
+// Maps of the residual by linearity, in place (complex float32 maps): the
+// maps of the previous iteration's residual minus
+// sum_{t < df.n} (alpha_t - alpha_prev_t) tab_a_t[i] tab_b_t[j] per receiver;
+// rows outside rowlim (if given) are left as they are.
+int gh_launch_maps_deflate(gh_ctx* ctx, const Dims& d, const Deflate& df, void* maps, const int* rowlim);
+// The same for the frames listed in items (frame, receiver, first range bin,
+// count), iteration k.
+int gh_launch_maps_deflate_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* items, int n, int k);
 // Batched maps (iteration k's residual applied on load); items as built by gh_batch.cu.
 int gh_launch_maps_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* range_items, int n_range,
                          int thr_range, size_t smem_range, const BatchItem* dop_items, int n_dop, int thr_dop,

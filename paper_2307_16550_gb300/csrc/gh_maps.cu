@@ -374,6 +374,61 @@ __global__ void __launch_bounds__(512, 2) doppler_fft_kernel(const float2* __res
     doppler_cols<MT>(Zr, maps, Ms, Mc, logNr, logNd, IB, blockIdx.y, i0, tw, oscale, smem);
 }
 
+// Maps of the residual by linearity (complex float32 maps, in place): range
+// bins i0 .. i0 + IB - 1 of receiver q lose
+//   sum_{t < df.n} (alpha_t - alpha_prev_t) tab_a_t[i] tab_b_t[j],
+// the part of the atoms' maps (Sec. III) the maps do not yet hold; IB <= 16.
+__device__ __forceinline__ void deflate_rows(float2* __restrict__ maps, const Deflate& df, int Q, int Nr, int Nd,
+                                             int logNd, int q, int i0, int IB) {
+    __shared__ float2 s_c[GH_MAX_K * 16];  // (alpha_t - alpha_prev_t) tab_a_t[i], per atom and row
+    const int n = df.n;
+    for (int idx = threadIdx.x; idx < n * IB; idx += blockDim.x) {
+        const int t = idx / IB, ii = idx - t * IB;
+        const double2 al = df.alpha[(size_t)t * Q + q], ap = df.alpha_prev[(size_t)t * Q + q];
+        const float2 da = make_float2((float)(al.x - ap.x), (float)(al.y - ap.y));
+        s_c[idx] = cmul(da, df.tab_a[((size_t)t * Q + q) * Nr + i0 + ii]);
+    }
+    __syncthreads();
+    // two bins per 16-byte access, four accesses in flight per thread
+    float4* row = (float4*)(maps + ((size_t)q * Nr + i0) * Nd);
+    const int hp = Nd >> 1, lp = logNd - 1, npair = IB * hp;
+    for (int base = threadIdx.x; base < npair; base += 4 * blockDim.x) {
+        float4 v[4];
+        int ii[4], jp[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int pidx = base + u * blockDim.x;
+            ii[u] = pidx >> lp;
+            jp[u] = pidx & (hp - 1);
+            if (pidx < npair) v[u] = row[pidx];
+        }
+        for (int t = 0; t < n; ++t) {
+            const float4* tb = (const float4*)(df.tab_b + ((size_t)t * Q + q) * Nd);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (base + u * blockDim.x < npair) {
+                    const float4 b = __ldg(tb + jp[u]);
+                    const float2 c = s_c[t * IB + ii[u]];
+                    v[u].x -= c.x * b.x - c.y * b.y;
+                    v[u].y -= c.x * b.y + c.y * b.x;
+                    v[u].z -= c.x * b.z - c.y * b.w;
+                    v[u].w -= c.x * b.w + c.y * b.z;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (base + u * blockDim.x < npair) row[base + u * blockDim.x] = v[u];
+    }
+}
+
+__global__ void __launch_bounds__(256) maps_deflate_kernel(float2* __restrict__ maps, Deflate df, int Q, int Nr,
+                                                           int Nd, int logNd, int IB, const int* __restrict__ rowlim) {
+    const int i0 = blockIdx.x * IB;
+    if (rowlim && (i0 + IB - 1 < rowlim[blockIdx.y] || i0 > rowlim[Q + blockIdx.y])) return;  // whole CTA
+    deflate_rows(maps, df, Q, Nr, Nd, logNd, blockIdx.y, i0, IB);
+}
+
 // Batched maps of several frames: one work item (frame, first row / range
 // bin, count) per CTA; the residual of iteration k is applied on load.
 __global__ void __launch_bounds__(512) range_fft_batch_kernel(const BatchFrame* __restrict__ frames,
@@ -386,6 +441,19 @@ __global__ void __launch_bounds__(512) range_fft_batch_kernel(const BatchFrame* 
     int logNr = 0;
     while ((1 << logNr) < F.d.Nr) ++logNr;
     range_rows(F.Y, F.zr, F.d.Q, F.d.Ms, F.d.Mc, logNr, (int)it.start, (int)it.count, df, F.twr, smem);
+}
+
+// Batched residual maps by linearity: one item (frame, receiver, first range
+// bin, count) per CTA, iteration k (atoms 0 .. k-1).
+__global__ void __launch_bounds__(256) maps_deflate_batch_kernel(const BatchFrame* __restrict__ frames,
+                                                                 const BatchItem* __restrict__ items, int k) {
+    const BatchItem it = items[blockIdx.x];
+    const BatchFrame& F = frames[it.frame];
+    Deflate df = F.df;
+    df.n = k;
+    int logNd = 0;
+    while ((1 << logNd) < F.d.Nd) ++logNd;
+    deflate_rows(F.maps, df, F.d.Q, F.d.Nr, F.d.Nd, logNd, it.aux, (int)it.start, (int)it.count);
 }
 
 __global__ void __launch_bounds__(512, 2) doppler_fft_batch_kernel(const BatchFrame* __restrict__ frames,
@@ -491,6 +559,25 @@ int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* d
     kern<<<dim3(d.Nr / IB, d.Q), threads, smem2, ctx->stream>>>((const float2*)zr, maps, d.Ms, d.Mc, logNr, logNd, IB,
                                                             twd, oscale, rowlim, d.Q);
     return gh_launch_end(ctx, GH_K_DOPPLER_FFT, ev, "doppler_fft_kernel");
+}
+
+int gh_launch_maps_deflate(gh_ctx* ctx, const Dims& d, const Deflate& df, void* maps, const int* rowlim) {
+    if (df.n == 0) return GH_OK;
+    if (df.n > GH_MAX_K) return gh_fail(ctx, GH_EINVAL, "maps deflation of %d atoms", df.n);
+    const int IB = gh_fft_bins_per_cta(d.Nr, d.Nd);
+    cudaEvent_t ev;
+    gh_launch_begin(ctx, GH_K_DEFLATE, &ev);
+    maps_deflate_kernel<<<dim3(d.Nr / IB, d.Q), 256, 0, ctx->stream>>>((float2*)maps, df, d.Q, d.Nr, d.Nd,
+                                                                      ilog2(d.Nd), IB, rowlim);
+    return gh_launch_end(ctx, GH_K_DEFLATE, ev, "maps_deflate_kernel");
+}
+
+int gh_launch_maps_deflate_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* items, int n, int k) {
+    if (n == 0 || k == 0) return GH_OK;
+    cudaEvent_t ev;
+    gh_launch_begin(ctx, GH_K_DEFLATE, &ev);
+    maps_deflate_batch_kernel<<<n, 256, 0, ctx->stream>>>(frames, items, k);
+    return gh_launch_end(ctx, GH_K_DEFLATE, ev, "maps_deflate_batch_kernel");
 }
 
 int gh_launch_maps_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* range_items, int n_range,

@@ -22,9 +22,9 @@ GH_OK, GH_EINVAL, GH_ENOMEM, GH_ECUDA, GH_ETIMEOUT, GH_ENOTSUP = 0, -1, -2, -3, 
 GH_C64, GH_C16, GH_CBF16 = 0, 1, 2
 GH_HOP, GH_EXACT, GH_INDIRECT = 0, 1, 2
 (GH_K_RANGE_FFT, GH_K_DOPPLER_FFT, GH_K_COORD, GH_K_HOP_SCORE, GH_K_ARGMAX, GH_K_BOMP,
- GH_K_EXACT_S1, GH_K_EXACT_S2, GH_K_SYNTH, GH_K_POINTS) = range(10)
+ GH_K_EXACT_S1, GH_K_EXACT_S2, GH_K_SYNTH, GH_K_POINTS, GH_K_DEFLATE) = range(11)
 KERNEL_KINDS = {"range_fft": 0, "doppler_fft": 1, "coord": 2, "hop_score": 3, "argmax": 4,
-                "bomp": 5, "exact_s1": 6, "exact_s2": 7, "synth": 8, "points": 9}
+                "bomp": 5, "exact_s1": 6, "exact_s2": 7, "synth": 8, "points": 9, "deflate": 10}
 
 
 class GhRadar(ctypes.Structure):

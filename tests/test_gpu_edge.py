@@ -104,9 +104,12 @@ def test_timing_and_launch_counts(ctx, torch_cuda):
     ms, launches = ctx.gh_kernel_stats("hop_score")
     ctx.gh_set_timing(False)
     assert launches == 2 and ms > 0
-    # per iteration: range FFT (residual applied on load), Doppler FFT, scorer,
-    # BOMP step (selection, new atom, correlation, least squares); plus the table once
-    assert n1 - n0 == 1 + 2 * 4
+    # the table once; iteration 0: range FFT, Doppler FFT, scorer, BOMP step
+    # (selection, new atom, correlation, least squares); later iterations:
+    # the residual's maps by linearity, scorer, BOMP step
+    assert n1 - n0 == 1 + 4 + 3
+    ms_d, launches_d = ctx.gh_kernel_stats("deflate")
+    assert launches_d == 1 and ms_d > 0
 
 
 @pytest.mark.parametrize("Q,Ms,Mc,pad,n", [
