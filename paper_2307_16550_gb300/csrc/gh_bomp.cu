@@ -93,32 +93,6 @@ __device__ double dirichlet(double f, int M) {
     return (double)(sinpif(mod2f((double)M * f)) / s);
 }
 
-// sin(2 pi x 2^-64) with full relative precision: x is reduced to its distance
-// v <= 2^62 from the nearest multiple of half a cycle before the float
-// conversion.
-__device__ __forceinline__ float sin2pi_fix(uint64_t x) {
-    const uint64_t w = x & 0x7fffffffffffffffull;
-    const uint64_t v = w < (1ull << 62) ? w : (1ull << 63) - w;
-    const float s = sinpif((float)v * 1.08420217248550443e-19f);  // 2^-63
-    return (x >> 63) ? -s : s;
-}
-
-// F_M(f) = sum_{m < M} exp(j 2 pi f m) = exp(j pi f (M-1)) sin(pi M f) / sin(pi f)
-// for f = ph 2^-64 (a fixed-point phase; F is 1-periodic), M an even power of
-// two. The arguments are reduced exactly in integer arithmetic: M f mod 2 from
-// ph M/2 mod 2^64, the phase f (M-1)/2 mod 1 from the 128-bit product
-// ph (M-1), sin(pi f) from the distance of f to the nearest integer.
-__device__ __forceinline__ float2 dtft_fix(uint64_t ph, int M) {
-    const uint64_t h = ph < (1ull << 63) ? ph : (0ull - ph);
-    if (h == 0) return make_float2((float)M, 0.f);
-    const float sf = sinpif((float)h * 5.42101086242752217e-20f);  // sin(pi f) > 0, 2^-64
-    const float sm = sin2pi_fix(ph * (uint64_t)(M >> 1));           // sin(pi M f)
-    const uint64_t lo = ph * (uint64_t)(M - 1), hi = __umul64hi(ph, (uint64_t)(M - 1));
-    const float2 e = gh_cis_fix((lo >> 1) | (hi << 63));
-    const float d = sm / sf;
-    return make_float2(e.x * d, e.y * d);
-}
-
 // Maps of the signal-model atom b(u) (x) a(r) as the map maker computes them
 // (Sec. III; its bins are the inner products of Sec. IV): the 2D DFT of the
 // atom, times the range-centring factor, is A[i] B[j] with
@@ -131,7 +105,7 @@ __device__ __forceinline__ void atom_map_entry(uint64_t rf, uint64_t uf, int Ms,
                                                float2* __restrict__ A, float2* __restrict__ B, int e) {
     if (e < Nr) {
         const uint64_t sr = 0ull - (~0ull / (uint64_t)Nr + 1ull);  // -2^64 / Nr (mod 2^64)
-        const float2 f = dtft_fix(rf + (uint64_t)e * sr, Ms);
+        const float2 f = gh_dtft_fix(rf + (uint64_t)e * sr, Ms);
         // exp(j pi i (Ms-1) / Nr), the angle reduced exactly (as the Doppler FFT does)
         const int t = (int)(((unsigned)e * (unsigned)(Ms - 1)) & (unsigned)(2 * Nr - 1));
         float s, c;
@@ -140,7 +114,7 @@ __device__ __forceinline__ void atom_map_entry(uint64_t rf, uint64_t uf, int Ms,
     } else {
         const int j = e - Nr;
         const uint64_t sd = 0ull - (~0ull / (uint64_t)Nd + 1ull);  // -2^64 / Nd
-        B[j] = dtft_fix(uf + (uint64_t)j * sd, Mc);
+        B[j] = gh_dtft_fix(uf + (uint64_t)j * sd, Mc);
     }
 }
 
@@ -752,6 +726,7 @@ Deflate gh_bomp_deflate(void* ws, const Dims& d, int K, int n) {
     f.alpha_prev = w.alpha_prev;
     f.tab_a = w.tab_a;
     f.tab_b = w.tab_b;
+    f.ru = w.ru;
     return f;
 }
 

@@ -1004,6 +1004,79 @@ int launch_tc(gh_ctx* ctx, const Dims& d, const float* P, const ExEntry* tab, fl
 
 // Stage 1 (and the phase table the tensor-core kernels read): P planar
 // [Q][nxy][Re row | Im row][Mc]; *tab_out is NULL when no table was made.
+namespace {
+
+// Stage 1 of a BOMP residual by linearity (iterations k >= 1, in place): the
+// correlation of atom t with a(r) over the samples is
+// <b(u_t) (x) a(r_t), a(r)>_m = b(u_t)[mc] F_Ms(r_t - r) (Eq. 3's inner
+// products), so every (x, y, q) row loses
+// sum_t (alpha_t - alpha'_t) F_Ms(r_t - r_q(x)) b_t[mc], the part the rows do
+// not yet hold. F from fixed-point phases (exact argument reduction). One
+// warp per row (row = q nxy + xy), lanes over chirps.
+__global__ void __launch_bounds__(256) exact_p_deflate_kernel(float* __restrict__ P,
+                                                              const ExEntry* __restrict__ tab, Deflate df, int Q,
+                                                              long long nxy, int Ms, int Mc) {
+    __shared__ float2 s_ct[8][GH_MAX_K];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long row = (long long)blockIdx.x * 8 + warp;
+    if (row >= (long long)Q * nxy) return;  // whole warp
+    const int q = (int)(row / nxy);
+    const long long xy = row - (long long)q * nxy;
+    // the row's values first (4 chirps per 16-byte access, Mc <= 256), then
+    // the coefficients while those loads are in flight
+    float4* pr = (float4*)(P + (size_t)row * 2 * Mc);  // Re row, then Im row
+    const int n4 = Mc >> 2;
+    float4 re[2], im[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int v = lane + 32 * u;
+        if (v < n4) {
+            re[u] = pr[v];
+            im[u] = pr[n4 + v];
+        }
+    }
+    if (lane < df.n) {
+        const int t = lane;
+        const double2 al = df.alpha[(size_t)t * Q + q], ap = df.alpha_prev[(size_t)t * Q + q];
+        const uint64_t rf = gh_phase_fix(df.ru[(size_t)t * Q + q].x);
+        const float2 F = gh_dtft_fix(rf - tab[xy * Q + q].rfix, Ms);
+        s_ct[warp][t] = cmul(make_float2((float)(al.x - ap.x), (float)(al.y - ap.y)), F);
+    }
+    __syncwarp();
+    for (int t = 0; t < df.n; ++t) {
+        const float2 c = s_ct[warp][t];
+        const float4* bt = (const float4*)(df.atoms_b + ((size_t)t * Q + q) * Mc);  // 2 chirps per float4
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int v = lane + 32 * u;
+            if (v < n4) {
+                const float4 b0 = __ldg(bt + 2 * v), b1 = __ldg(bt + 2 * v + 1);  // chirps 4v .. 4v + 3
+                re[u].x -= c.x * b0.x - c.y * b0.y;
+                im[u].x -= c.x * b0.y + c.y * b0.x;
+                re[u].y -= c.x * b0.z - c.y * b0.w;
+                im[u].y -= c.x * b0.w + c.y * b0.z;
+                re[u].z -= c.x * b1.x - c.y * b1.y;
+                im[u].z -= c.x * b1.y + c.y * b1.x;
+                re[u].w -= c.x * b1.z - c.y * b1.w;
+                im[u].w -= c.x * b1.w + c.y * b1.z;
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int v = lane + 32 * u;
+        if (v < n4) {
+            pr[v] = re[u];
+            pr[n4 + v] = im[u];
+        }
+    }
+}
+
+}  // namespace
+
+// Stage 1 (P and, when needed, the coordinate table). With df.n > 0 and the
+// table of this detection already built (k >= 1), P of the residual is
+// updated in place by linearity instead of being recomputed.
 static int exact_stage1(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float2* Y, const Deflate& df,
                         bool need_tab, void** P_out, void** tab_out) {
     void* P;  // planar [Q][nxy][Re row | Im row][Mc]
@@ -1012,6 +1085,17 @@ static int exact_stage1(gh_ctx* ctx, const Dims& d, const GeoParams& g, const fl
     int* status = gh_status_dev(ctx);
     cudaEvent_t ev;
     void* tab = nullptr;
+    if (df.n > 0 && df.n <= GH_MAX_K && (tc1 || need_tab) && d.Mc <= 256) {  // residual of iteration k >= 1
+        GH_TRY(gh_ws(ctx, WS_EXACT_TAB, (size_t)d.nxy * d.Q * sizeof(ExEntry), &tab));
+        const long long rows = d.nxy * d.Q;
+        gh_launch_begin(ctx, GH_K_DEFLATE, &ev);
+        exact_p_deflate_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, ctx->stream>>>(
+            (float*)P, (const ExEntry*)tab, df, d.Q, d.nxy, d.Ms, d.Mc);
+        GH_TRY(gh_launch_end(ctx, GH_K_DEFLATE, ev, "exact_p_deflate_kernel"));
+        *P_out = P;
+        *tab_out = tab;
+        return GH_OK;
+    }
     if (tc1 || need_tab) {
         GH_TRY(gh_ws(ctx, WS_EXACT_TAB, (size_t)d.nxy * d.Q * sizeof(ExEntry), &tab));
         const long long n = d.nxy * d.Q;

@@ -300,6 +300,32 @@ __device__ __forceinline__ float2 gh_cis_fix(uint64_t ph) {
     return make_float2(c, s);
 }
 
+// sin(2 pi x 2^-64) with full relative precision: x is reduced to its distance
+// v <= 2^62 from the nearest multiple of half a cycle before the float
+// conversion.
+__device__ __forceinline__ float gh_sin2pi_fix(uint64_t x) {
+    const uint64_t w = x & 0x7fffffffffffffffull;
+    const uint64_t v = w < (1ull << 62) ? w : (1ull << 63) - w;
+    const float s = sinpif((float)v * 1.08420217248550443e-19f);  // 2^-63
+    return (x >> 63) ? -s : s;
+}
+
+// F_M(f) = sum_{m < M} exp(j 2 pi f m) = exp(j pi f (M-1)) sin(pi M f) / sin(pi f)
+// for f = ph 2^-64 (a fixed-point phase; F is 1-periodic), M an even power of
+// two. The arguments are reduced exactly in integer arithmetic: M f mod 2 from
+// ph M/2 mod 2^64, the phase f (M-1)/2 mod 1 from the 128-bit product
+// ph (M-1), sin(pi f) from the distance of f to the nearest integer.
+__device__ __forceinline__ float2 gh_dtft_fix(uint64_t ph, int M) {
+    const uint64_t h = ph < (1ull << 63) ? ph : (0ull - ph);
+    if (h == 0) return make_float2((float)M, 0.f);
+    const float sf = sinpif((float)h * 5.42101086242752217e-20f);  // sin(pi f) > 0, 2^-64
+    const float sm = gh_sin2pi_fix(ph * (uint64_t)(M >> 1));           // sin(pi M f)
+    const uint64_t lo = ph * (uint64_t)(M - 1), hi = __umul64hi(ph, (uint64_t)(M - 1));
+    const float2 e = gh_cis_fix((lo >> 1) | (hi << 63));
+    const float d = sm / sf;
+    return make_float2(e.x * d, e.y * d);
+}
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -322,7 +348,9 @@ struct Deflate {
     const double2* alpha_prev;  // [K][Q]
     const float2* tab_a;        // [K][Q][Nr]
     const float2* tab_b;        // [K][Q][Nd]
+    const double2* ru;          // [K][Q] (r, u) of the atoms (the exact path's stage-1 update)
 };
+
 
 __device__ __forceinline__ float2 gh_deflate(const Deflate& f, int Q, int Ms, int Mc, int q, int mc, int m,
                                              float2 y) {
