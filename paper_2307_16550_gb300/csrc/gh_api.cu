@@ -95,9 +95,6 @@ extern "C" void gh_destroy(gh_ctx* ctx) {
     gh_graph_invalidate(ctx);
     gh_batch_release(ctx);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
-    if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
-    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
-    if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
     for (auto& t : ctx->pending) {
         cudaEventDestroy(t.start);
         cudaEventDestroy(t.stop);
@@ -578,31 +575,6 @@ extern "C" int gh_direct_exact(gh_ctx* ctx, const gh_radar* radar, const double*
 
 // The gh_detect launch sequence (from the staged measurement to the results
 // copied into pinned host memory); recorded into a CUDA graph when capturing.
-// Runs launch(), which enqueues on ctx->stream, on the context's second stream
-// instead: the branch starts after the work already on ctx->stream (fork_ev)
-// and records join_ev at its end, which the main sequence must wait for
-// before it uses the branch's results (and before a graph capture ends).
-template <class F>
-static int on_aux_stream(gh_ctx* ctx, F launch) {
-    if (!ctx->aux_stream) {
-        if (ctx->capturing) return gh_fail(ctx, GH_ECUDA, "second stream created during graph capture");
-        GH_CUDA(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
-        GH_CUDA(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
-        GH_CUDA(cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming));
-    }
-    GH_CUDA(cudaEventRecord(ctx->fork_ev, ctx->stream));
-    GH_CUDA(cudaStreamWaitEvent(ctx->aux_stream, ctx->fork_ev, 0));
-    cudaStream_t main = ctx->stream;
-    ctx->stream = ctx->aux_stream;
-    const int st = launch();
-    ctx->stream = main;
-    // recorded even after a failure, so that a capture can still be joined
-    const cudaError_t e = cudaEventRecord(ctx->join_ev, ctx->aux_stream);
-    GH_TRY(st);
-    if (e != cudaSuccess) return gh_fail_cuda(ctx, e, "cudaEventRecord", __FILE__, __LINE__);
-    return GH_OK;
-}
-
 static int detect_sequence(gh_ctx* ctx, int32_t method, const Dims& d, const GeoParams& geo, const void* Y,
                            int Ydev, int K, void** host_out) {
     const float2* Yd;
@@ -630,9 +602,7 @@ static int detect_sequence(gh_ctx* ctx, int32_t method, const Dims& d, const Geo
     GH_TRY(gh_bomp_reset(ctx, d, K, bws));
     int* rowlim = nullptr;  // map rows the scorer can read: the Doppler FFT skips the others
     double* rw = nullptr;   // (r, wx, wy) per coordinate entry, for the new atoms
-    // the coordinate table (float64-bound) is built on the second stream beside
-    // the first range FFT; the first Doppler FFT waits for it
-    if (method == GH_HOP) GH_TRY(on_aux_stream(ctx, [&] { return build_table(ctx, d, geo, &table, &rowlim, &rw); }));
+    if (method == GH_HOP) GH_TRY(build_table(ctx, d, geo, &table, &rowlim, &rw));
     ArgResult* sel = (ArgResult*)res;  // sel[k] = selection of iteration k
     for (int k = 0; k < K; ++k) {
         // the residual of iteration k subtracts atoms 0..k-1 (amplitudes of the last solve)
@@ -643,8 +613,7 @@ static int detect_sequence(gh_ctx* ctx, int32_t method, const Dims& d, const Geo
             if (k > 0 && ctx->detect_maps == GH_C64)  // residual maps by linearity, in place
                 GH_TRY(gh_launch_maps_deflate(ctx, d, df, maps, rowlim));
             else
-                GH_TRY(gh_launch_maps(ctx, d, Yd, &df, maps, ctx->detect_maps, rowlim,
-                                      k == 0 ? ctx->join_ev : nullptr));
+                GH_TRY(gh_launch_maps(ctx, d, Yd, &df, maps, ctx->detect_maps, rowlim));
             GH_TRY(gh_launch_hop_parts(ctx, d, geo, maps, ctx->detect_maps, table, nullptr, mask, k, &parts,
                                        &nparts));
         } else {

@@ -49,18 +49,15 @@ inline uint32_t hop_tol(int nvx, int nvy) {
 
 
 
-// Entry idx = xy * Q + q of the coordinate table (diagnostics optional).
-__device__ __forceinline__ void coord_entry(const GeoParams& g, const CoordParams& cp, long long idx,
-                                            HopEntry* __restrict__ table, int32_t* diag_i, double* diag_tau,
-                                            float* diag_c, double* diag_w, double* rw = nullptr) {
+// Entry idx = xy * Q + q of the coordinate table (diagnostics optional), at
+// the point (x, y) whose transmitter distance and unit vector are given.
+__device__ __forceinline__ void coord_entry_at(const GeoParams& g, const CoordParams& cp, long long idx, double x,
+                                               double y, double n1, double ux1, double uy1,
+                                               HopEntry* __restrict__ table, int32_t* diag_i, double* diag_tau,
+                                               float* diag_c, double* diag_w, double* rw) {
     const int q = (int)(idx % g.Q);
-    const long long xy = idx / g.Q;
-    const int ix = (int)(xy / g.n[1]);
-    const int iy = (int)(xy - (long long)ix * g.n[1]);
-    const double x = gh_axis(g.lo[0], g.step[0], ix);
-    const double y = gh_axis(g.lo[1], g.step[1], iy);
     double d, wx, wy;
-    gh_bistatic(g, q, x, y, &d, &wx, &wy);
+    gh_bistatic_rx(g, q, x, y, n1, ux1, uy1, &d, &wx, &wy);
     const double r = gh_range(g, d);
     const double rho = __dmul_rn((double)g.Nr, r);
     const double fi = floor(__dadd_rn(rho, 0.5));
@@ -125,6 +122,23 @@ __device__ __forceinline__ void coord_entry(const GeoParams& g, const CoordParam
     }
 }
 
+// Entry idx = xy * Q + q of the coordinate table (diagnostics optional).
+__device__ __forceinline__ void coord_entry(const GeoParams& g, const CoordParams& cp, long long idx,
+                                            HopEntry* __restrict__ table, int32_t* diag_i, double* diag_tau,
+                                            float* diag_c, double* diag_w, double* rw = nullptr) {
+    const long long xy = idx / g.Q;
+    const int ix = (int)(xy / g.n[1]);
+    const int iy = (int)(xy - (long long)ix * g.n[1]);
+    const double x = gh_axis(g.lo[0], g.step[0], ix);
+    const double y = gh_axis(g.lo[1], g.step[1], iy);
+    double n1, ux1, uy1;
+    gh_unit(__dsub_rn(x, g.tx[0]), __dsub_rn(y, g.tx[1]), &n1, &ux1, &uy1);
+    coord_entry_at(g, cp, idx, x, y, n1, ux1, uy1, table, diag_i, diag_tau, diag_c, diag_w, rw);
+}
+
+// One thread per (x, y): the transmitter's distance and unit vector once,
+// then the Q receivers' entries (the float64 pipe is the limit: sharing the
+// transmitter half saves a third of its work at Q = 4).
 // rowlim (optional, device int[2Q]: Q minima preset large, then Q maxima
 // preset to -1): per receiver the smallest and largest map row any entry
 // reads (the map rows a detection's scorer can touch). rw (optional, device
@@ -134,7 +148,7 @@ __global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__
                              double* __restrict__ rw) {
     __shared__ int s_lim[2 * GH_MAX_Q];
     const long long nxy = (long long)g.n[0] * g.n[1];
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long xy = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (rowlim) {
         for (int i = threadIdx.x; i < g.Q; i += blockDim.x) {
             s_lim[i] = 0x7fffffff;
@@ -142,14 +156,23 @@ __global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__
         }
         __syncthreads();
     }
-    if (idx < nxy * g.Q) {
-        coord_entry(g, cp, idx, table, diag_i, diag_tau, diag_c, diag_w, rw);
-        if (rowlim) {
-            const int q = (int)(idx % g.Q);
-            const HopEntry& e = table[idx];
-            const int lo = min(e.row[0], min(e.row[1], e.row[2])), hi = max(e.row[0], max(e.row[1], e.row[2]));
-            atomicMin(&s_lim[q], lo);
-            atomicMax(&s_lim[g.Q + q], hi);
+    if (xy < nxy) {
+        const int ix = (int)(xy / g.n[1]);
+        const int iy = (int)(xy - (long long)ix * g.n[1]);
+        const double x = gh_axis(g.lo[0], g.step[0], ix);
+        const double y = gh_axis(g.lo[1], g.step[1], iy);
+        double n1, ux1, uy1;
+        gh_unit(__dsub_rn(x, g.tx[0]), __dsub_rn(y, g.tx[1]), &n1, &ux1, &uy1);
+        for (int q = 0; q < g.Q; ++q) {
+            const long long idx = xy * g.Q + q;
+            coord_entry_at(g, cp, idx, x, y, n1, ux1, uy1, table, diag_i, diag_tau, diag_c, diag_w, rw);
+            if (rowlim) {
+                const HopEntry& e = table[idx];
+                const int lo = min(e.row[0], min(e.row[1], e.row[2]));
+                const int hi = max(e.row[0], max(e.row[1], e.row[2]));
+                atomicMin(&s_lim[q], lo);
+                atomicMax(&s_lim[g.Q + q], hi);
+            }
         }
     }
     if (rowlim) {
@@ -615,15 +638,15 @@ size_t gh_hop_table_bytes(const Dims& d) { return (size_t)d.nxy * d.Q * sizeof(H
 int gh_launch_coord(gh_ctx* ctx, const Dims& d, const GeoParams& g, void* table, int32_t* diag_i,
                     double* diag_tau, float* diag_c, double* diag_w, int* rowlim, double* rw) {
     const CoordParams cp = coord_params(d);
-    const long long n = d.nxy * d.Q;
     if (rowlim) {  // minima 0x7f7f7f7f, maxima -1 (byte patterns)
         GH_CUDA(cudaMemsetAsync(rowlim, 0x7f, (size_t)d.Q * sizeof(int), ctx->stream));
         GH_CUDA(cudaMemsetAsync(rowlim + d.Q, 0xff, (size_t)d.Q * sizeof(int), ctx->stream));
     }
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_COORD, &ev);
-    coord_kernel<<<(unsigned)((n + 127) / 128), 128, 0, ctx->stream>>>(g, cp, (HopEntry*)table, diag_i, diag_tau,
-                                                                       diag_c, diag_w, rowlim, rw);
+    // one warp per CTA: the (x, y) cells spread over every SM's sub-partitions
+    coord_kernel<<<(unsigned)((d.nxy + 31) / 32), 32, 0, ctx->stream>>>(g, cp, (HopEntry*)table, diag_i, diag_tau,
+                                                                         diag_c, diag_w, rowlim, rw);
     return gh_launch_end(ctx, GH_K_COORD, ev, "coord_kernel");
 }
 
@@ -730,9 +753,8 @@ extern "C" int gh_score_grid_noalloc(void* stream_ptr, const gh_radar* radar, co
     GeoParams g;
     gh_fill_geo(&g, radar, tx_host, rx_host, Q, grid);
     const CoordParams cp = coord_params(d);
-    const long long n = d.nxy * d.Q;
-    coord_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(g, cp, table, nullptr, nullptr, nullptr, nullptr,
-                                                                   nullptr, nullptr);
+    coord_kernel<<<(unsigned)((d.nxy + 31) / 32), 32, 0, stream>>>(g, cp, table, nullptr, nullptr, nullptr, nullptr,
+                                                                    nullptr, nullptr);
     if (cudaGetLastError() != cudaSuccess) return GH_ECUDA;
     const HopParams hp = hop_params(d, g);
     long long nparts = 0;

@@ -76,10 +76,6 @@ struct gh_ctx {
     bool graphs = true;
     bool capturing = false;
     cudaStream_t capture_stream = nullptr;  // records graphs (the legacy stream cannot be captured)
-    // second stream for a branch that runs beside the main sequence (the
-    // coordinate table beside the first range FFT), forked and joined by events
-    cudaStream_t aux_stream = nullptr;
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     std::vector<GraphEntry> graph_cache;
     std::vector<std::vector<unsigned char>> seen_keys;  // configurations met once
     uint64_t graph_tick = 0;
@@ -262,14 +258,22 @@ __device__ __forceinline__ void gh_unit(double dx, double dy, double* n, double*
 }
 
 // Bistatic path d = |x - tx| + |x - rx| and gradient w (Eq. 1).
-__device__ __forceinline__ void gh_bistatic(const GeoParams& g, int q, double x, double y,
-                                            double* d, double* wx, double* wy) {
-    double n1, ux1, uy1, n2, ux2, uy2;
-    gh_unit(__dsub_rn(x, g.tx[0]), __dsub_rn(y, g.tx[1]), &n1, &ux1, &uy1);
+// The receiver half of gh_bistatic, given the transmitter's distance n1 and
+// unit vector (ux1, uy1) at the same point (shared by all receivers).
+__device__ __forceinline__ void gh_bistatic_rx(const GeoParams& g, int q, double x, double y, double n1, double ux1,
+                                               double uy1, double* d, double* wx, double* wy) {
+    double n2, ux2, uy2;
     gh_unit(__dsub_rn(x, g.rx[2 * q]), __dsub_rn(y, g.rx[2 * q + 1]), &n2, &ux2, &uy2);
     *d = __dadd_rn(n1, n2);
     *wx = __dadd_rn(ux1, ux2);
     *wy = __dadd_rn(uy1, uy2);
+}
+
+__device__ __forceinline__ void gh_bistatic(const GeoParams& g, int q, double x, double y,
+                                            double* d, double* wx, double* wy) {
+    double n1, ux1, uy1;
+    gh_unit(__dsub_rn(x, g.tx[0]), __dsub_rn(y, g.tx[1]), &n1, &ux1, &uy1);
+    gh_bistatic_rx(g, q, x, y, n1, ux1, uy1, d, wx, wy);
 }
 
 // r = (B*d)/(c*Ms), cycles per sample.
@@ -414,11 +418,9 @@ struct BatchItem {
 };
 
 // rowlim (optional): per receiver the row bounds from gh_launch_coord; rows
-// outside them are not computed (gh_detect's own maps only). before_doppler
-// (optional): an event the Doppler FFT waits for (the end of a branch that
-// writes rowlim beside the range FFT).
+// outside them are not computed (gh_detect's own maps only).
 int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* df, void* maps, int map_dtype,
-                   const int* rowlim = nullptr, cudaEvent_t before_doppler = nullptr);
+                   const int* rowlim = nullptr);
 // Zero-padded range FFT of every chirp alone: *zr = [Q][Mc][Nr] complex64 (context workspace).
 int gh_launch_range_rows(gh_ctx* ctx, const Dims& d, const float2* Y, void** zr);
 // Shared-memory column length of an N-point FFT (one float2 of padding per 16).

@@ -539,12 +539,11 @@ int gh_launch_range_rows(gh_ctx* ctx, const Dims& d, const float2* Y, void** zr)
 }
 
 int gh_launch_maps(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate* df, void* maps, int map_dtype,
-                   const int* rowlim, cudaEvent_t before_doppler) {
+                   const int* rowlim) {
     const float2 *twr, *twd;
     GH_TRY(ensure_twiddles(ctx, d.Nr, d.Nd, &twr, &twd));
     void* zr;
     GH_TRY(range_fft(ctx, d, Y, df, twr, &zr));
-    if (before_doppler) GH_CUDA(cudaStreamWaitEvent(ctx->stream, before_doppler, 0));
     const int logNr = ilog2(d.Nr), logNd = ilog2(d.Nd);
     cudaEvent_t ev;
     // Doppler FFT: IB range bins per CTA
