@@ -245,24 +245,29 @@ struct ExEntry {
     unsigned long long phy0, dphy;  // kappa wy vy_0 and kappa wy step_y
 };
 
+// One thread per (x, y): the transmitter's distance and unit vector once,
+// then its Q receivers' entries (float64-bound, like coord_kernel).
 __global__ void exact_coord_kernel(GeoParams g, ExEntry* __restrict__ tab) {
     const long long nxy = (long long)g.n[0] * g.n[1];
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nxy * g.Q) return;
-    const int q = (int)(idx % g.Q);
-    const long long xy = idx / g.Q;
+    const long long xy = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (xy >= nxy) return;
     const int ix = (int)(xy / g.n[1]);
     const int iy = (int)(xy - (long long)ix * g.n[1]);
-    double d, wx, wy;
-    gh_bistatic(g, q, gh_axis(g.lo[0], g.step[0], ix), gh_axis(g.lo[1], g.step[1], iy), &d, &wx, &wy);
-    ExEntry e;
-    e.rfix = gh_phase_fix(gh_range(g, d));
-    const double kx = g.kappa * wx, ky = g.kappa * wy;
-    e.phx0 = gh_phase_fix(kx * gh_axis(g.lo[2], g.step[2], 0));
-    e.dphx = gh_phase_fix(kx * g.step[2]);
-    e.phy0 = gh_phase_fix(ky * gh_axis(g.lo[3], g.step[3], 0));
-    e.dphy = gh_phase_fix(ky * g.step[3]);
-    tab[idx] = e;
+    const double x = gh_axis(g.lo[0], g.step[0], ix), y = gh_axis(g.lo[1], g.step[1], iy);
+    double n1, ux1, uy1;
+    gh_unit(__dsub_rn(x, g.tx[0]), __dsub_rn(y, g.tx[1]), &n1, &ux1, &uy1);
+    for (int q = 0; q < g.Q; ++q) {
+        double d, wx, wy;
+        gh_bistatic_rx(g, q, x, y, n1, ux1, uy1, &d, &wx, &wy);
+        ExEntry e;
+        e.rfix = gh_phase_fix(gh_range(g, d));
+        const double kx = g.kappa * wx, ky = g.kappa * wy;
+        e.phx0 = gh_phase_fix(kx * gh_axis(g.lo[2], g.step[2], 0));
+        e.dphx = gh_phase_fix(kx * g.step[2]);
+        e.phy0 = gh_phase_fix(ky * gh_axis(g.lo[3], g.step[3], 0));
+        e.dphy = gh_phase_fix(ky * g.step[3]);
+        tab[xy * g.Q + q] = e;
+    }
 }
 
 struct ExactTcParams {
@@ -1098,9 +1103,8 @@ static int exact_stage1(gh_ctx* ctx, const Dims& d, const GeoParams& g, const fl
     }
     if (tc1 || need_tab) {
         GH_TRY(gh_ws(ctx, WS_EXACT_TAB, (size_t)d.nxy * d.Q * sizeof(ExEntry), &tab));
-        const long long n = d.nxy * d.Q;
         gh_launch_begin(ctx, GH_K_EXACT_S1, &ev);
-        exact_coord_kernel<<<(unsigned)((n + 127) / 128), 128, 0, ctx->stream>>>(g, (ExEntry*)tab);
+        exact_coord_kernel<<<(unsigned)((d.nxy + 31) / 32), 32, 0, ctx->stream>>>(g, (ExEntry*)tab);
         GH_TRY(gh_launch_end(ctx, GH_K_EXACT_S1, ev, "exact_coord_kernel"));
     }
     if (tc1) {
