@@ -217,12 +217,20 @@ __global__ void __launch_bounds__(1024) vel_kernel(const float2* __restrict__ Y,
                 const float2 z = G[q * Nd + j];
                 acc += z.x * z.x + z.y * z.y;
             } else {
+                // b_mc(u) = exp(j 2 pi u mc): an exact value from the fixed-point
+                // phase every 32 chirps, the recurrence b_{mc+1} = b_mc w between
                 const unsigned long long uf = gh_phase_fix(u);
+                const float2 w = gh_cis_fix(uf);
                 float2 s = make_float2(0.f, 0.f);
-                for (int mc = 0; mc < Mc; ++mc) {
-                    const float2 bb = gh_cis_fix(uf * (unsigned long long)mc), z = gq[q * Mc + mc];
-                    s.x += z.x * bb.x + z.y * bb.y;  // z conj(b)
-                    s.y += z.y * bb.x - z.x * bb.y;
+                for (int mc0 = 0; mc0 < Mc; mc0 += 32) {
+                    float2 bb = gh_cis_fix(uf * (unsigned long long)mc0);
+                    const int m1 = min(mc0 + 32, Mc);
+                    for (int mc = mc0; mc < m1; ++mc) {
+                        const float2 z = gq[q * Mc + mc];
+                        s.x += z.x * bb.x + z.y * bb.y;  // z conj(b)
+                        s.y += z.y * bb.x - z.x * bb.y;
+                        bb = cmul(bb, w);
+                    }
                 }
                 acc += s.x * s.x + s.y * s.y;
             }
