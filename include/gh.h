@@ -205,6 +205,12 @@ GH_API int gh_direct_exact(gh_ctx* ctx, const gh_radar* radar, const double* tx_
  *                   atoms b(u) (x) a(r) of Sec. II, from the last solve (may be NULL)
  * All K iterations run on the device without host round trips; the stream is
  * synchronised once at the end. 1 <= K <= min(GH_MAX_K, ncells).
+ * The residual's maps (GH_HOP with complex float32 maps) and stage-1
+ * correlations (GH_EXACT) are reached by linearity after the first iteration:
+ * the previous ones minus the newly solved part of the atoms' own maps or
+ * correlations, which are known in closed form (equal to recomputing them
+ * from R_q up to float32 rounding). Reduced-precision maps are remade from
+ * R_q by FFT every iteration.
  */
 /*
  * gh_score_points - differentiable hopping score at P continuous points

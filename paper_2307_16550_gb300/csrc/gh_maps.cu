@@ -1,16 +1,19 @@
 // Range-Doppler maps (Sec. III: the 2D FFT of each Y_q; Sec. IV: the FFT bins
 // are correlations with the atoms on the FFT's frequency grid).
 //
-// Two kernels, both Stockham FFTs in shared memory (radix-4 passes, one
-// radix-2 pass for odd log2 sizes) with float32 data and a twiddle table
-// rounded from float64 and staged in shared memory:
+// Two FFT kernels, both Stockham (radix-16 register passes, a last radix-2,
+// -4, -8 or -16 pass; the first pass reads global memory, the last writes it,
+// the others work in place in shared memory) with float32 data and a twiddle
+// table rounded from float64 and staged in shared memory:
 //   range_fft   : per (q, mc) row, the Ms samples zero-padded to Nr = pad*Ms,
-//                 written [Q][Mc][Nr]; a BOMP residual is subtracted from the
-//                 samples as they are loaded;
+//                 written [Q][Mc][Nr]; a BOMP residual can be subtracted from
+//                 the samples as they are loaded;
 //   doppler_fft : per (q, block of IB range bins), the Mc chirps zero-padded to
 //                 Nd = pad*Mc, times the range-centring factor
 //                 exp(j pi (i/Nr)(Ms-1)), written [Q][Nr][Nd] so that one
 //                 range bin's Doppler row is contiguous for the scorer.
+// and maps_deflate, which takes complex float32 maps to those of a BOMP
+// residual by linearity (the atoms' maps in closed form, see Deflate).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
