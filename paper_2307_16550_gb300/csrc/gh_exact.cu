@@ -245,18 +245,21 @@ struct ExEntry {
     unsigned long long phy0, dphy;  // kappa wy vy_0 and kappa wy step_y
 };
 
-// One thread per (x, y): the transmitter's distance and unit vector once,
-// then its Q receivers' entries (float64-bound, like coord_kernel).
+// Two threads per (x, y), each taking every other receiver, the
+// transmitter's distance and unit vector once per thread (float64
+// latency-bound, like coord_kernel).
 __global__ void exact_coord_kernel(GeoParams g, ExEntry* __restrict__ tab) {
     const long long nxy = (long long)g.n[0] * g.n[1];
-    const long long xy = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long xy = t >> 1;
+    const int q0 = (int)(t & 1);
     if (xy >= nxy) return;
     const int ix = (int)(xy / g.n[1]);
     const int iy = (int)(xy - (long long)ix * g.n[1]);
     const double x = gh_axis(g.lo[0], g.step[0], ix), y = gh_axis(g.lo[1], g.step[1], iy);
     double n1, ux1, uy1;
     gh_unit(__dsub_rn(x, g.tx[0]), __dsub_rn(y, g.tx[1]), &n1, &ux1, &uy1);
-    for (int q = 0; q < g.Q; ++q) {
+    for (int q = q0; q < g.Q; q += 2) {
         double d, wx, wy;
         gh_bistatic_rx(g, q, x, y, n1, ux1, uy1, &d, &wx, &wy);
         ExEntry e;
@@ -1104,7 +1107,7 @@ static int exact_stage1(gh_ctx* ctx, const Dims& d, const GeoParams& g, const fl
     if (tc1 || need_tab) {
         GH_TRY(gh_ws(ctx, WS_EXACT_TAB, (size_t)d.nxy * d.Q * sizeof(ExEntry), &tab));
         gh_launch_begin(ctx, GH_K_EXACT_S1, &ev);
-        exact_coord_kernel<<<(unsigned)((d.nxy + 31) / 32), 32, 0, ctx->stream>>>(g, (ExEntry*)tab);
+        exact_coord_kernel<<<(unsigned)((2 * d.nxy + 31) / 32), 32, 0, ctx->stream>>>(g, (ExEntry*)tab);
         GH_TRY(gh_launch_end(ctx, GH_K_EXACT_S1, ev, "exact_coord_kernel"));
     }
     if (tc1) {
