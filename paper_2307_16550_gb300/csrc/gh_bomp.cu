@@ -531,6 +531,19 @@ __global__ void __launch_bounds__(256) bomp_step_kernel(const ArgPartial* __rest
     __shared__ double s_r[GH_MAX_Q], s_u[GH_MAX_Q];
     const int ch = blockIdx.x, q = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // this warp's chirp of Y, loaded now (Ms <= 256: eight samples per lane)
+    // so that the loads overlap the selection and the new atom's geometry
+    const int mc = ch * kCorrRows + warp;
+    const bool has_row = warp < kCorrRows && mc < g.Mc;
+    const float2* row = Y + ((size_t)q * g.Mc + (has_row ? mc : 0)) * g.Ms;
+    constexpr int kPre = 8;
+    const bool pre = g.Ms <= 32 * kPre;
+    float2 yv[kPre];
+#pragma unroll
+    for (int j = 0; j < kPre; ++j) {
+        const int m = lane + 32 * j;
+        yv[j] = (pre && has_row && m < g.Ms) ? row[m] : make_float2(0.f, 0.f);
+    }
     // selection (the same reduction in every CTA)
     float best = -INFINITY;
     long long bestc = 0x7fffffffffffffffLL;
@@ -570,16 +583,27 @@ __global__ void __launch_bounds__(256) bomp_step_kernel(const ArgPartial* __rest
     }
     __syncthreads();
     // correlation of kCorrRows chirps with b(u) (x) a(r)
-    const int mc = ch * kCorrRows + warp;
     double sx = 0.0, sy = 0.0;
-    if (warp < kCorrRows && mc < g.Mc) {
-        const float2* row = Y + ((size_t)q * g.Mc + mc) * g.Ms;
+    if (has_row) {
         float2 sm = make_float2(0.f, 0.f);
-        for (int m = lane; m < g.Ms; m += 32) {
-            const float2 y = row[m];
-            const float2 v = s_at[m];
-            sm.x += y.x * v.x + y.y * v.y;  // y * conj(a)
-            sm.y += y.y * v.x - y.x * v.y;
+        if (pre) {
+#pragma unroll
+            for (int j = 0; j < kPre; ++j) {
+                const int m = lane + 32 * j;
+                if (m < g.Ms) {
+                    const float2 y = yv[j];
+                    const float2 v = s_at[m];
+                    sm.x += y.x * v.x + y.y * v.y;  // y * conj(a)
+                    sm.y += y.y * v.x - y.x * v.y;
+                }
+            }
+        } else {
+            for (int m = lane; m < g.Ms; m += 32) {
+                const float2 y = row[m];
+                const float2 v = s_at[m];
+                sm.x += y.x * v.x + y.y * v.y;  // y * conj(a)
+                sm.y += y.y * v.x - y.x * v.y;
+            }
         }
         for (int off = 16; off > 0; off >>= 1) {
             sm.x += __shfl_down_sync(0xffffffffu, sm.x, off);

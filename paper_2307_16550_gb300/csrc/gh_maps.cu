@@ -385,6 +385,20 @@ __device__ __forceinline__ void deflate_rows(float2* __restrict__ maps, const De
                                              int logNd, int q, int i0, int IB) {
     __shared__ float2 s_c[GH_MAX_K * 16];  // (alpha_t - alpha_prev_t) tab_a_t[i], per atom and row
     const int n = df.n;
+    // two bins per 16-byte access, four accesses in flight per thread; the
+    // first four are issued before the coefficients are staged, so that the
+    // two rounds of loads overlap
+    float4* row = (float4*)(maps + ((size_t)q * Nr + i0) * Nd);
+    const int hp = Nd >> 1, lp = logNd - 1, npair = IB * hp;
+    float4 v[4];
+    auto load4 = [&](int base) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int pidx = base + u * blockDim.x;
+            if (pidx < npair) v[u] = row[pidx];
+        }
+    };
+    load4(threadIdx.x);
     for (int idx = threadIdx.x; idx < n * IB; idx += blockDim.x) {
         const int t = idx / IB, ii = idx - t * IB;
         const double2 al = df.alpha[(size_t)t * Q + q], ap = df.alpha_prev[(size_t)t * Q + q];
@@ -392,26 +406,16 @@ __device__ __forceinline__ void deflate_rows(float2* __restrict__ maps, const De
         s_c[idx] = cmul(da, df.tab_a[((size_t)t * Q + q) * Nr + i0 + ii]);
     }
     __syncthreads();
-    // two bins per 16-byte access, four accesses in flight per thread
-    float4* row = (float4*)(maps + ((size_t)q * Nr + i0) * Nd);
-    const int hp = Nd >> 1, lp = logNd - 1, npair = IB * hp;
     for (int base = threadIdx.x; base < npair; base += 4 * blockDim.x) {
-        float4 v[4];
-        int ii[4], jp[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int pidx = base + u * blockDim.x;
-            ii[u] = pidx >> lp;
-            jp[u] = pidx & (hp - 1);
-            if (pidx < npair) v[u] = row[pidx];
-        }
+        if (base != (int)threadIdx.x) load4(base);
         for (int t = 0; t < n; ++t) {
             const float4* tb = (const float4*)(df.tab_b + ((size_t)t * Q + q) * Nd);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                if (base + u * blockDim.x < npair) {
-                    const float4 b = __ldg(tb + jp[u]);
-                    const float2 c = s_c[t * IB + ii[u]];
+                const int pidx = base + u * blockDim.x;
+                if (pidx < npair) {
+                    const float4 b = __ldg(tb + (pidx & (hp - 1)));
+                    const float2 c = s_c[t * IB + (pidx >> lp)];
                     v[u].x -= c.x * b.x - c.y * b.y;
                     v[u].y -= c.x * b.y + c.y * b.x;
                     v[u].z -= c.x * b.z - c.y * b.w;
