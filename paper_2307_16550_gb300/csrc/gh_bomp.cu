@@ -4,21 +4,26 @@
 //
 // BOMP iteration k, after the scorer has written its per-CTA argmax partials
 // (no host round trip):
-//   bomp_select : reduces the partials to the selected cell sel[k] (ties: the
-//                 smallest index), appends it to the mask, and prepares the new
-//                 atom at every receiver q: (r, u) in float64, its centring
-//                 phase exp(j pi (r (Ms-1) + u (Mc-1))), row k of the real Gram
+//   selection   : the partials reduce to the selected cell sel[k] (ties: the
+//                 smallest index), appended to the mask; the new atom at every
+//                 receiver q: (r, u) in float64, its centring phase
+//                 exp(j pi (r (Ms-1) + u (Mc-1))), row k of the real Gram
 //                 matrix G[s][t] = D_Ms(r_t - r_s) D_Mc(u_t - u_s) with
 //                 D_M(f) = sin(pi M f) / sin(pi f), and the atoms a(r), b(u).
 //                 Trigonometric arguments are reduced exactly in float64 before
 //                 a float32 sincos.
-//   bomp_corr   : c_{k,q} = <Y_q, b(u) (x) a(r)> (float32 row sums added in
+//   correlation : c_{k,q} = <Y_q, b(u) (x) a(r)> (float32 row sums added in
 //                 float64); the last CTA to finish solves, per receiver, the
-//                 float64 normal equations of atoms 0..k (Cholesky, dependent
-//                 atoms dropped) and rotates the amplitudes back to the atoms of
-//                 the signal model (Sec. II).
-// The residual Y - sum_t alpha_t atom_t is never stored on the hopping path:
-// the next map-making pass subtracts it while loading Y (gh_deflate).
+//                 float64 normal equations of atoms 0..k (closed form for up
+//                 to three atoms, else Cholesky; dependent atoms dropped) and
+//                 rotates the amplitudes back to the atoms of the signal model
+//                 (Sec. II).
+// A single frame runs both in one launch (bomp_step_kernel); a batch of frames
+// runs them as two (bomp_select_batch_kernel, bomp_corr_batch_kernel). The
+// residual Y - sum_t alpha_t atom_t is never stored on the hopping path: the
+// next iteration's maps subtract the new atoms' maps (A_t (x) B_t, tabulated
+// here) by linearity, or the map-making pass subtracts the atoms while loading
+// Y (gh_deflate).
 #include <math.h>
 
 #include "gh_internal.cuh"
@@ -26,6 +31,7 @@
 namespace {
 
 constexpr int kCorrRows = 8;  // chirps per correlation CTA (one per warp)
+constexpr int kStepThreads = 32 * (kCorrRows + 1);  // BOMP step CTA: the correlation warps and a Gram warp
 
 struct BompLayout {
     size_t alpha, corr, ru, phase, gram, corrp, atoms_a, atoms_b, alpha_prev, tab_a, tab_b, counter, total;
@@ -140,6 +146,20 @@ __device__ void atom_map_tables_shared(uint64_t rf, uint64_t uf, int Ms, int Mc,
     }
 }
 
+// The same slices taken by one warp (32 entries at a time).
+__device__ void atom_map_tables_warp(uint64_t rf, uint64_t uf, int Ms, int Mc, int Nr, int Nd,
+                                     float2* __restrict__ A, float2* __restrict__ B, unsigned* counter) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned base = 0u;
+        if (lane == 0) base = atomicAdd(counter, 32u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= (unsigned)(Nr + Nd)) break;
+        const unsigned e = base + lane;
+        if (e < (unsigned)(Nr + Nd)) atom_map_entry(rf, uf, Ms, Mc, Nr, Nd, A, B, (int)e);
+    }
+}
+
 __device__ __forceinline__ void better(float s, long long c, float& bs, long long& bc) {
     if (s > bs || (s == bs && c < bc)) {
         bs = s;
@@ -158,12 +178,23 @@ __device__ __forceinline__ void better(float s, long long c, float& bs, long lon
 __device__ __forceinline__ void cell_ru(const GeoParams& g, long long cell, int q, const double* rw, double* r,
                                         double* u) {
     const int nvy = g.n[3], nvx = g.n[2], ny = g.n[1];
-    const int ivy = (int)(cell % nvy);
-    cell /= nvy;
-    const int ivx = (int)(cell % nvx);
-    cell /= nvx;
-    const int iy = (int)(cell % ny);
-    const int ix = (int)(cell / ny);
+    int ivy, ivx, iy, ix;
+    if (cell < (1ll << 32)) {  // 32-bit division: a shorter chain than the 64-bit one
+        unsigned c = (unsigned)cell;
+        ivy = (int)(c % (unsigned)nvy);
+        c /= (unsigned)nvy;
+        ivx = (int)(c % (unsigned)nvx);
+        c /= (unsigned)nvx;
+        iy = (int)(c % (unsigned)ny);
+        ix = (int)(c / (unsigned)ny);
+    } else {
+        ivy = (int)(cell % nvy);
+        cell /= nvy;
+        ivx = (int)(cell % nvx);
+        cell /= nvx;
+        iy = (int)(cell % ny);
+        ix = (int)(cell / ny);
+    }
     double d, wx, wy;
     if (rw) {
         const double* e = rw + (((long long)ix * ny + iy) * g.Q + q) * 3;
@@ -265,16 +296,19 @@ __device__ __forceinline__ double rsqrt_newton(double v) {
     return y;
 }
 
-// Float64 normal equations of atoms 0..n-1 (n <= NM) of one receiver
-// (Cholesky, dependent atoms dropped), amplitudes rotated back to the atoms of
-// the signal model. G: the receiver's Gram matrix (row stride ldg); z:
-// exp(+j pi ph_t) <Y, atom_t> (stride sz); ph: the centring phases (stride
-// sp); alpha: output (stride sa). The factor is kept as rows scaled by the
-// reciprocal square roots of the pivots, so the solve has no division; the
-// loops unroll (small NM) and the factor stays in registers.
-template <int NM>
-__device__ __forceinline__ void bomp_solve_q(int Ms, int Mc, int n, const double* G, int ldg, const double2* z,
-                                             int sz, const double2* ph, int sp, double2* alpha, int sa) {
+// Float64 normal equations of atoms 0..N-1 of one receiver (Cholesky,
+// dependent atoms dropped), amplitudes rotated back to the atoms of the signal
+// model. G: the receiver's Gram matrix (row stride ldg); z: exp(+j pi ph_t)
+// <Y, atom_t> (stride sz); ph: the centring phases (stride sp); alpha: output
+// (stride sa). The factor is kept as rows scaled by the reciprocal square
+// roots of the pivots, so the solve has no division; the loops unroll for the
+// exact size N (the float64 dependency chain is as long as N needs) and the
+// factor stays in registers.
+template <int N>
+__device__ __forceinline__ void bomp_solve_n(int Ms, int Mc, const double* G, int ldg, const double2* z, int sz,
+                                             const double2* ph, int sp, double2* alpha, int sa) {
+    constexpr int NM = N;
+    const int n = N;
     double L[NM][NM];
     double zr[NM], zi[NM], rs[NM];  // rs[j] = 1 / L[j][j] (0 for a dependent atom)
 #pragma unroll
@@ -383,68 +417,159 @@ __device__ __noinline__ void bomp_solve_big(int Ms, int Mc, int n, const double*
     }
 }
 
-// The solve with the factor in registers for n <= 4, else in local memory.
+// 1 / d for a positive normal float64 d inside the float32 range: one
+// third-order Newton step y <- y (1 + e + e^2), e = 1 - d y, from the float32
+// reciprocal (relative error about 2^-23, cubed by the step).
+__device__ __forceinline__ double rcp_newton(double d) {
+    const double y = (double)__frcp_rn((float)d);
+    const double e = fma(-d, y, 1.0);
+    return fma(y, fma(e, e, e), y);
+}
+
+// The same normal equations for N <= 3 atoms in closed form (cofactors over
+// the determinant, Cramer's rule): a float64 dependency chain about a third
+// as long as the factorisation's. Used when every Cholesky pivot clears twice
+// the dependence floor (pivot j = det G_{0..j} / det G_{0..j-1}); otherwise
+// the factorisation decides which atoms to drop.
+template <int N>
+__device__ __forceinline__ void bomp_solve_cramer(int Ms, int Mc, const double* G, int ldg, const double2* z, int sz,
+                                                  const double2* ph, int sp, double2* alpha, int sa) {
+    const double floor2 = 2e-9 * (double)Ms * (double)Mc;
+    double C[N][N], det;
+    bool ok;
+    if constexpr (N == 1) {
+        det = G[0];
+        C[0][0] = 1.0;
+        ok = det > floor2;
+    } else if constexpr (N == 2) {
+        const double g00 = G[0], g01 = G[1], g11 = G[ldg + 1];
+        det = fma(g00, g11, -g01 * g01);
+        C[0][0] = g11;
+        C[0][1] = C[1][0] = -g01;
+        C[1][1] = g00;
+        ok = g00 > floor2 && det > floor2 * g00;
+    } else {
+        const double g00 = G[0], g01 = G[1], g02 = G[2];
+        const double g11 = G[ldg + 1], g12 = G[ldg + 2], g22 = G[2 * ldg + 2];
+        C[0][0] = fma(g11, g22, -g12 * g12);
+        C[0][1] = C[1][0] = fma(g02, g12, -g01 * g22);
+        C[0][2] = C[2][0] = fma(g01, g12, -g02 * g11);
+        C[1][1] = fma(g00, g22, -g02 * g02);
+        C[1][2] = C[2][1] = fma(g01, g02, -g00 * g12);
+        C[2][2] = fma(g00, g11, -g01 * g01);
+        det = fma(g02, C[0][2], fma(g01, C[0][1], g00 * C[0][0]));
+        ok = g00 > floor2 && C[2][2] > floor2 * g00 && det > floor2 * C[2][2];
+    }
+    if (!ok) {
+        bomp_solve_n<N>(Ms, Mc, G, ldg, z, sz, ph, sp, alpha, sa);
+        return;
+    }
+    const double inv = rcp_newton(det);
+    double zr[N], zi[N];
+#pragma unroll
+    for (int t = 0; t < N; ++t) {
+        const double2 v = z[(size_t)t * sz];
+        zr[t] = v.x;
+        zi[t] = v.y;
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        double ar = C[i][0] * zr[0], ai = C[i][0] * zi[0];
+#pragma unroll
+        for (int t = 1; t < N; ++t) {
+            ar = fma(C[i][t], zr[t], ar);
+            ai = fma(C[i][t], zi[t], ai);
+        }
+        ar *= inv;
+        ai *= inv;
+        const double2 p = ph[(size_t)i * sp];  // alpha = alpha~ exp(-j pi ph)
+        alpha[(size_t)i * sa] = make_double2(p.x * ar + p.y * ai, p.x * ai - p.y * ar);
+    }
+}
+
+// The solve in closed form for n <= 3, with the factor in registers for
+// n = 4, else in local memory.
 __device__ __forceinline__ void bomp_solve_any(int Ms, int Mc, int n, const double* G, int ldg, const double2* z,
                                                int sz, const double2* ph, int sp, double2* alpha, int sa) {
-    if (n <= 4)
-        bomp_solve_q<4>(Ms, Mc, n, G, ldg, z, sz, ph, sp, alpha, sa);
-    else
-        bomp_solve_big(Ms, Mc, n, G, ldg, z, sz, ph, sp, alpha, sa);
+    switch (n) {
+        case 1: bomp_solve_cramer<1>(Ms, Mc, G, ldg, z, sz, ph, sp, alpha, sa); break;
+        case 2: bomp_solve_cramer<2>(Ms, Mc, G, ldg, z, sz, ph, sp, alpha, sa); break;
+        case 3: bomp_solve_cramer<3>(Ms, Mc, G, ldg, z, sz, ph, sp, alpha, sa); break;
+        case 4: bomp_solve_n<4>(Ms, Mc, G, ldg, z, sz, ph, sp, alpha, sa); break;
+        default: bomp_solve_big(Ms, Mc, n, G, ldg, z, sz, ph, sp, alpha, sa);
+    }
 }
 
 constexpr int kSolveStage = 1024;  // doubles of shared memory for the staged solve
 
-// Last CTA of a BOMP iteration (all its threads): c_{k,q} = the sum of the
+// The smallest power of two >= min(n, 32).
+__device__ __forceinline__ int lane_span(int n) {
+    const int m = n < 32 ? n : 32;
+    return m <= 1 ? 1 : 1 << (32 - __clz(m - 1));
+}
+
+// Last CTA of a BOMP iteration (its first nthr threads, a multiple of 32;
+// they synchronise on named barrier 1): c_{k,q} = the sum of the
 // chunks' partial correlations (one warp per receiver, lanes over chunks,
 // then a fixed butterfly order), then every receiver's least squares. When
-// they fit, the Gram matrices, rotated correlations and phases are first
-// staged in shared memory by the whole CTA, so that the solves wait for one
-// round of loads instead of one per matrix entry.
-__device__ void bomp_sum_solve(const GeoParams& g, int k, int K, const BompPtrs& w) {
+// they fit, the Gram matrices, rotated correlations and phases are staged in
+// shared memory by the whole CTA in the same round of loads as the partial
+// correlations, so that the solves wait for one round of loads in all.
+__device__ void bomp_sum_solve(const GeoParams& g, int k, int K, const BompPtrs& w, int nthr) {
     __shared__ double2 s_stage[kSolveStage / 2];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = nthr >> 5;
     const int n = k + 1, Q = g.Q;
     // the amplitudes the maps of this iteration's residual hold (atom k: none),
     // kept before the solve replaces them
-    for (int i = threadIdx.x; i < n * Q; i += blockDim.x)
+    for (int i = threadIdx.x; i < n * Q; i += nthr)
         w.alpha_prev[i] = i < k * Q ? w.alpha[i] : make_double2(0.0, 0.0);
+    const int gsz = (Q * n * n + 1) & ~1;  // doubles of the Gram part, even: the double2 parts stay 16-byte aligned
+    const bool staged = (size_t)gsz + (size_t)4 * Q * n <= (size_t)kSolveStage;
+    double* sG = (double*)s_stage;    // [Q][n][n]
+    double2* sz = s_stage + gsz / 2;  // [Q][n]
+    double2* sp = sz + Q * n;         // [Q][n]
+    if (staged) {
+        for (int i = threadIdx.x; i < Q * n * n; i += nthr) {
+            const int qq = i / (n * n), e = i - qq * n * n, r = e / n, c = e - r * n;
+            sG[i] = __ldcg(w.gram + ((size_t)qq * K + r) * K + c);
+        }
+        for (int i = threadIdx.x; i < Q * n; i += nthr) {
+            const int qq = i / n, t = i - qq * n;
+            const double2 p = __ldcg(w.phase + (size_t)t * Q + qq);
+            sp[i] = p;
+            if (t < k) {
+                const double2 c = w.corr[(size_t)t * Q + qq];
+                sz[i] = make_double2(p.x * c.x - p.y * c.y, p.x * c.y + p.y * c.x);  // exp(+j pi ph) <Y, atom>
+            }
+        }
+    }
     for (int qq = warp; qq < Q; qq += nw) {
         const double2* pp = w.corrp + ((size_t)k * Q + qq) * w.chunks;
+        double2 p = make_double2(0.0, 0.0);
+        if (staged && lane == 0) p = __ldcg(w.phase + (size_t)k * Q + qq);
         double cx = 0.0, cy = 0.0;
         for (int c = lane; c < w.chunks; c += 32) {
             const double2 v = __ldcg(pp + c);
             cx += v.x;
             cy += v.y;
         }
-        for (int off = 16; off > 0; off >>= 1) {
+        // lanes at or above min(chunks, 32) hold zeros: the butterfly starts
+        // at half the next power of two
+        for (int off = lane_span(w.chunks) >> 1; off > 0; off >>= 1) {
             cx += __shfl_xor_sync(0xffffffffu, cx, off);
             cy += __shfl_xor_sync(0xffffffffu, cy, off);
         }
-        if (lane == 0) w.corr[(size_t)k * Q + qq] = make_double2(cx, cy);
+        if (lane == 0) {
+            w.corr[(size_t)k * Q + qq] = make_double2(cx, cy);
+            if (staged) sz[qq * n + k] = make_double2(p.x * cx - p.y * cy, p.x * cy + p.y * cx);
+        }
     }
-    __syncthreads();
-    const int gsz = (Q * n * n + 1) & ~1;  // doubles of the Gram part, even: the double2 parts stay 16-byte aligned
-    const bool staged = (size_t)gsz + (size_t)4 * Q * n <= (size_t)kSolveStage;
+    asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
     if (staged) {
-        double* sG = (double*)s_stage;          // [Q][n][n]
-        double2* sz = s_stage + gsz / 2;        // [Q][n]
-        double2* sp = sz + Q * n;               // [Q][n]
-        for (int i = threadIdx.x; i < Q * n * n; i += blockDim.x) {
-            const int qq = i / (n * n), e = i - qq * n * n, r = e / n, c = e - r * n;
-            sG[i] = w.gram[((size_t)qq * K + r) * K + c];
-        }
-        for (int i = threadIdx.x; i < Q * n; i += blockDim.x) {
-            const int qq = i / n, t = i - qq * n;
-            const double2 p = w.phase[(size_t)t * Q + qq];
-            const double2 c = w.corr[(size_t)t * Q + qq];
-            sz[i] = make_double2(p.x * c.x - p.y * c.y, p.x * c.y + p.y * c.x);  // exp(+j pi ph) <Y, atom>
-            sp[i] = p;
-        }
-        __syncthreads();
-        for (int qq = threadIdx.x; qq < Q; qq += blockDim.x)
+        for (int qq = threadIdx.x; qq < Q; qq += nthr)
             bomp_solve_any(g.Ms, g.Mc, n, sG + qq * n * n, n, sz + qq * n, 1, sp + qq * n, 1, w.alpha + qq, Q);
     } else {
-        for (int qq = threadIdx.x; qq < Q; qq += blockDim.x) {
+        for (int qq = threadIdx.x; qq < Q; qq += nthr) {
             double2 z[GH_MAX_K];
             for (int t = 0; t < n; ++t) {
                 const double2 p = w.phase[(size_t)t * Q + qq];
@@ -454,6 +579,13 @@ __device__ void bomp_sum_solve(const GeoParams& g, int k, int K, const BompPtrs&
             bomp_solve_any(g.Ms, g.Mc, n, w.gram + (size_t)qq * K * K, K, z, 1, w.phase + qq, Q, w.alpha + qq, Q);
         }
     }
+}
+
+// Sum of the kCorrRows chirp correlations of a CTA, in a pairwise tree (a
+// float64 dependency chain of log2(kCorrRows) additions).
+__device__ __forceinline__ double sum_rows(const double* r) {
+    static_assert(kCorrRows == 8, "pairwise tree of eight");
+    return ((r[0] + r[1]) + (r[2] + r[3])) + ((r[4] + r[5]) + (r[6] + r[7]));
 }
 
 // CTA (chunk, q): partial <Y_q, b(u) (x) a(r)> over kCorrRows chirps. The last
@@ -491,11 +623,7 @@ __device__ void bomp_corr_body(const float2* __restrict__ Y, const GeoParams& g,
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double tx = 0, ty = 0;
-        for (int ww = 0; ww < kCorrRows; ++ww) {
-            tx += rx[ww];
-            ty += ry[ww];
-        }
+        const double tx = sum_rows(rx), ty = sum_rows(ry);
         w.corrp[((size_t)k * g.Q + q) * w.chunks + ch] = make_double2(tx, ty);
         __threadfence();
         s_last = atomicAdd(w.counter, 1u) == total - 1;
@@ -503,32 +631,34 @@ __device__ void bomp_corr_body(const float2* __restrict__ Y, const GeoParams& g,
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    bomp_sum_solve(g, k, K, w);
+    bomp_sum_solve(g, k, K, w, blockDim.x);
     if (threadIdx.x == 0) *w.counter = 0u;  // ready for the next iteration
 }
 
 
-// One BOMP iteration in one launch, grid (chunks, Q): every CTA reduces the
-// scorer's partials to the selected cell (all CTAs get the same cell), makes
-// its receiver's atom a(r_q) in shared memory (the CTAs of chunk 0 also store
-// it for the next maps' residual), correlates kCorrRows chirps with the atom
-// (storing their b(u_q) values), and the last CTA to finish writes the
-// selection, the new atom's phases and Gram rows, sums the correlations and
-// solves every receiver's least squares. Same arithmetic as a selection
-// followed by bomp_corr_body.
-__global__ void __launch_bounds__(256) bomp_step_kernel(const ArgPartial* __restrict__ parts, int nparts,
+// One BOMP iteration in one launch, grid (chunks, Q), kStepThreads threads:
+// every CTA reduces the scorer's partials to the selected cell (all CTAs get
+// the same cell) and takes the new atom's (r, u) at its receiver; then its
+// first kCorrRows warps make the atom a(r_q) in shared memory (the CTAs of
+// chunk 0 also store it for the next maps' residual) and correlate kCorrRows
+// chirps with the atom (storing their b(u_q) values), while its last warp
+// writes the CTA's share of row k of the receiver's Gram matrix (entries
+// t = chunk, chunk + chunks, ...). The last CTA to finish writes the
+// selection, sums the correlations and solves every receiver's least
+// squares. Same arithmetic as a selection followed by bomp_corr_body.
+__global__ void __launch_bounds__(kStepThreads) bomp_step_kernel(const ArgPartial* __restrict__ parts, int nparts,
                                                         const float2* __restrict__ Y, ArgResult* __restrict__ sel,
                                                         int64_t* __restrict__ mask, int k, int K, GeoParams g,
                                                         BompPtrs w, const double* __restrict__ rw) {
     extern __shared__ float2 s_at[];  // a(r_q), Ms values
-    __shared__ float s_bs[8];
-    __shared__ long long s_bc[8];
+    __shared__ float s_bs[kStepThreads / 32];
+    __shared__ long long s_bc[kStepThreads / 32];
     __shared__ long long s_best_cell;
     __shared__ float s_best;
     __shared__ unsigned long long s_rf, s_uf;
     __shared__ double rx[kCorrRows], ry[kCorrRows];
     __shared__ bool s_last;
-    __shared__ double s_r[GH_MAX_Q], s_u[GH_MAX_Q];
+    __shared__ double s_rk, s_uk;  // the new atom at this CTA's receiver
     const int ch = blockIdx.x, q = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // this warp's chirp of Y, loaded now (Ms <= 256: eight samples per lane)
@@ -567,6 +697,8 @@ __global__ void __launch_bounds__(256) bomp_step_kernel(const ArgPartial* __rest
         cell_ru(g, cell, q, rw, &r, &u);
         s_rf = gh_phase_fix(r);
         s_uf = gh_phase_fix(u);
+        s_rk = r;
+        s_uk = u;
         if (ch == 0) {  // the new atom's parameters at this receiver, for the last CTA
             w.ru[(size_t)k * g.Q + q] = make_double2(r, u);
             float sn, cs;
@@ -575,45 +707,58 @@ __global__ void __launch_bounds__(256) bomp_step_kernel(const ArgPartial* __rest
         }
     }
     __syncthreads();
-    float2* a_glob = w.atoms_a + ((size_t)k * g.Q + q) * g.Ms;
-    for (int m = threadIdx.x; m < g.Ms; m += blockDim.x) {
-        const float2 a = gh_cis_fix(s_rf * (unsigned long long)m);
-        s_at[m] = a;
-        if (ch == 0) a_glob[m] = a;
-    }
-    __syncthreads();
-    // correlation of kCorrRows chirps with b(u) (x) a(r)
     double sx = 0.0, sy = 0.0;
-    if (has_row) {
-        float2 sm = make_float2(0.f, 0.f);
-        if (pre) {
+    if (warp == kCorrRows) {
+        // this CTA's entries of row k of the receiver's Gram matrix
+        double* G = w.gram + (size_t)q * K * K;
+        for (int t = ch + lane * (int)gridDim.x; t <= k; t += 32 * (int)gridDim.x) {
+            const double2 rut = t == k ? make_double2(s_rk, s_uk) : __ldcg(w.ru + (size_t)t * g.Q + q);
+            const double v = dirichlet(s_rk - rut.x, g.Ms) * dirichlet(s_uk - rut.y, g.Mc);
+            G[k * K + t] = v;
+            G[t * K + k] = v;
+        }
+        __threadfence();
+    } else {
+        float2* a_glob = w.atoms_a + ((size_t)k * g.Q + q) * g.Ms;
+        for (int m = threadIdx.x; m < g.Ms; m += 32 * kCorrRows) {
+            const float2 a = gh_cis_fix(s_rf * (unsigned long long)m);
+            s_at[m] = a;
+            if (ch == 0) a_glob[m] = a;
+        }
+        // the correlation warps only (the Gram warp does not wait for the atom)
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * kCorrRows) : "memory");
+        // correlation of kCorrRows chirps with b(u) (x) a(r)
+        if (has_row) {
+            float2 sm = make_float2(0.f, 0.f);
+            if (pre) {
 #pragma unroll
-            for (int j = 0; j < kPre; ++j) {
-                const int m = lane + 32 * j;
-                if (m < g.Ms) {
-                    const float2 y = yv[j];
+                for (int j = 0; j < kPre; ++j) {
+                    const int m = lane + 32 * j;
+                    if (m < g.Ms) {
+                        const float2 y = yv[j];
+                        const float2 v = s_at[m];
+                        sm.x += y.x * v.x + y.y * v.y;  // y * conj(a)
+                        sm.y += y.y * v.x - y.x * v.y;
+                    }
+                }
+            } else {
+                for (int m = lane; m < g.Ms; m += 32) {
+                    const float2 y = row[m];
                     const float2 v = s_at[m];
                     sm.x += y.x * v.x + y.y * v.y;  // y * conj(a)
                     sm.y += y.y * v.x - y.x * v.y;
                 }
             }
-        } else {
-            for (int m = lane; m < g.Ms; m += 32) {
-                const float2 y = row[m];
-                const float2 v = s_at[m];
-                sm.x += y.x * v.x + y.y * v.y;  // y * conj(a)
-                sm.y += y.y * v.x - y.x * v.y;
+            for (int off = 16; off > 0; off >>= 1) {
+                sm.x += __shfl_down_sync(0xffffffffu, sm.x, off);
+                sm.y += __shfl_down_sync(0xffffffffu, sm.y, off);
             }
+            const float2 b = gh_cis_fix(s_uf * (unsigned long long)mc);
+            if (lane == 0) w.atoms_b[((size_t)k * g.Q + q) * g.Mc + mc] = b;
+            const double bx = b.x, by = b.y;  // s * conj(b)
+            sx = (double)sm.x * bx + (double)sm.y * by;
+            sy = (double)sm.y * bx - (double)sm.x * by;
         }
-        for (int off = 16; off > 0; off >>= 1) {
-            sm.x += __shfl_down_sync(0xffffffffu, sm.x, off);
-            sm.y += __shfl_down_sync(0xffffffffu, sm.y, off);
-        }
-        const float2 b = gh_cis_fix(s_uf * (unsigned long long)mc);
-        if (lane == 0) w.atoms_b[((size_t)k * g.Q + q) * g.Mc + mc] = b;
-        const double bx = b.x, by = b.y;  // s * conj(b)
-        sx = (double)sm.x * bx + (double)sm.y * by;
-        sy = (double)sm.y * bx - (double)sm.x * by;
     }
     if (lane == 0 && warp < kCorrRows) {
         rx[warp] = sx;
@@ -621,11 +766,7 @@ __global__ void __launch_bounds__(256) bomp_step_kernel(const ArgPartial* __rest
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double tx = 0, ty = 0;
-        for (int ww = 0; ww < kCorrRows; ++ww) {
-            tx += rx[ww];
-            ty += ry[ww];
-        }
+        const double tx = sum_rows(rx), ty = sum_rows(ry);
         w.corrp[((size_t)k * g.Q + q) * w.chunks + ch] = make_double2(tx, ty);
         __threadfence();
         s_last = atomicAdd(w.counter, 1u) == gridDim.x * gridDim.y - 1;
@@ -642,6 +783,11 @@ __global__ void __launch_bounds__(256) bomp_step_kernel(const ArgPartial* __rest
         return;
     }
     __threadfence();
+    if (warp == kCorrRows) {
+        // the Gram warp takes what is left of the tables while the others solve
+        atom_map_tables_warp(s_rf, s_uf, g.Ms, g.Mc, g.Nr, g.Nd, tab_a, tab_b, tab_cnt);
+        return;
+    }
     if (threadIdx.x == 0) {
         const bool valid = s_best_cell != 0x7fffffffffffffffLL;
         sel[k].cell = s_best_cell;
@@ -649,25 +795,8 @@ __global__ void __launch_bounds__(256) bomp_step_kernel(const ArgPartial* __rest
         sel[k].valid = valid;
         mask[k] = s_best_cell;
     }
-    // row k of the Gram matrix of every receiver, from the (r, u) the CTAs of chunk 0 stored
-    for (int i = threadIdx.x; i < g.Q; i += blockDim.x) {
-        const double2 ru = __ldcg(w.ru + (size_t)k * g.Q + i);
-        s_r[i] = ru.x;
-        s_u[i] = ru.y;
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < g.Q * (k + 1); idx += blockDim.x) {
-        const int qg = idx / (k + 1), t = idx - qg * (k + 1);
-        const double2 rut = t == k ? make_double2(s_r[qg], s_u[qg]) : __ldcg(w.ru + (size_t)t * g.Q + qg);
-        const double v = dirichlet(s_r[qg] - rut.x, g.Ms) * dirichlet(s_u[qg] - rut.y, g.Mc);
-        double* G = w.gram + (size_t)qg * K * K;
-        G[k * K + t] = v;
-        G[t * K + k] = v;
-    }
-    __syncthreads();  // Gram row k of every receiver written
-    bomp_sum_solve(g, k, K, w);
+    bomp_sum_solve(g, k, K, w, 32 * kCorrRows);
     if (threadIdx.x == 0) *w.counter = 0u;  // ready for the next iteration
-    atom_map_tables_shared(s_rf, s_uf, g.Ms, g.Mc, g.Nr, g.Nd, tab_a, tab_b, tab_cnt);
 }
 
 // Batched correlations: grid (max chunks, max Q, listed frames).
@@ -767,7 +896,7 @@ int gh_launch_bomp_step(gh_ctx* ctx, const Dims& d, const GeoParams& g, const Ar
     GH_CUDA(cudaFuncSetAttribute(bomp_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_BOMP, &ev);
-    bomp_step_kernel<<<dim3(w.chunks, d.Q), 32 * kCorrRows, smem, ctx->stream>>>(parts, nparts, Y, sel, mask, k, K,
+    bomp_step_kernel<<<dim3(w.chunks, d.Q), kStepThreads, smem, ctx->stream>>>(parts, nparts, Y, sel, mask, k, K,
                                                                                   g, w, rw);
     return gh_launch_end(ctx, GH_K_BOMP, ev, "bomp_step_kernel");
 }
