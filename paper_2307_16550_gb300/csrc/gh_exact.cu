@@ -1019,64 +1019,79 @@ namespace {
 // <b(u_t) (x) a(r_t), a(r)>_m = b(u_t)[mc] F_Ms(r_t - r) (Eq. 3's inner
 // products), so every (x, y, q) row loses
 // sum_t (alpha_t - alpha'_t) F_Ms(r_t - r_q(x)) b_t[mc], the part the rows do
-// not yet hold. F from fixed-point phases (exact argument reduction). One
-// warp per row (row = q nxy + xy), lanes over chirps.
+// not yet hold. F from fixed-point phases (exact argument reduction). Grid
+// (row blocks of kDeflRows, Q): the float64 parts (alpha_t - alpha'_t and the
+// fixed-point phase of r_t) depend on (t, q) only and are taken once per CTA
+// (float64 issues one warp instruction per 64 cycles per SM sub-partition);
+// then one warp per row (row = q nxy + xy), lanes over chirps.
+constexpr int kDeflRows = 64;  // (x, y) rows per CTA, 8 per warp
+
 __global__ void __launch_bounds__(256) exact_p_deflate_kernel(float* __restrict__ P,
                                                               const ExEntry* __restrict__ tab, Deflate df, int Q,
                                                               long long nxy, int Ms, int Mc) {
+    __shared__ float2 s_da[GH_MAX_K];              // alpha_t - alpha'_t, this CTA's receiver
+    __shared__ unsigned long long s_rf[GH_MAX_K];  // fixed-point phase of r_t
     __shared__ float2 s_ct[8][GH_MAX_K];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long row = (long long)blockIdx.x * 8 + warp;
-    if (row >= (long long)Q * nxy) return;  // whole warp
-    const int q = (int)(row / nxy);
-    const long long xy = row - (long long)q * nxy;
-    // the row's values first (4 chirps per 16-byte access, Mc <= 256), then
-    // the coefficients while those loads are in flight
-    float4* pr = (float4*)(P + (size_t)row * 2 * Mc);  // Re row, then Im row
-    const int n4 = Mc >> 2;
-    float4 re[2], im[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const int v = lane + 32 * u;
-        if (v < n4) {
-            re[u] = pr[v];
-            im[u] = pr[n4 + v];
-        }
-    }
-    if (lane < df.n) {
-        const int t = lane;
+    const int q = blockIdx.y;
+    if (threadIdx.x < df.n) {
+        const int t = threadIdx.x;
         const double2 al = df.alpha[(size_t)t * Q + q], ap = df.alpha_prev[(size_t)t * Q + q];
-        const uint64_t rf = gh_phase_fix(df.ru[(size_t)t * Q + q].x);
-        const float2 F = gh_dtft_fix(rf - tab[xy * Q + q].rfix, Ms);
-        s_ct[warp][t] = cmul(make_float2((float)(al.x - ap.x), (float)(al.y - ap.y)), F);
+        s_da[t] = make_float2((float)(al.x - ap.x), (float)(al.y - ap.y));
+        s_rf[t] = gh_phase_fix(df.ru[(size_t)t * Q + q].x);
     }
-    __syncwarp();
-    for (int t = 0; t < df.n; ++t) {
-        const float2 c = s_ct[warp][t];
-        const float4* bt = (const float4*)(df.atoms_b + ((size_t)t * Q + q) * Mc);  // 2 chirps per float4
+    __syncthreads();
+    const long long xy0 = (long long)blockIdx.x * kDeflRows;
+    const long long xy1 = xy0 + kDeflRows < nxy ? xy0 + kDeflRows : nxy;
+    const int n4 = Mc >> 2;
+    for (long long xy = xy0 + warp; xy < xy1; xy += 8) {
+        const long long row = (long long)q * nxy + xy;
+        // the row's values first (4 chirps per 16-byte access, Mc <= 256), then
+        // the coefficients while those loads are in flight
+        float4* pr = (float4*)(P + (size_t)row * 2 * Mc);  // Re row, then Im row
+        float4 re[2], im[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const int v = lane + 32 * u;
             if (v < n4) {
-                const float4 b0 = __ldg(bt + 2 * v), b1 = __ldg(bt + 2 * v + 1);  // chirps 4v .. 4v + 3
-                re[u].x -= c.x * b0.x - c.y * b0.y;
-                im[u].x -= c.x * b0.y + c.y * b0.x;
-                re[u].y -= c.x * b0.z - c.y * b0.w;
-                im[u].y -= c.x * b0.w + c.y * b0.z;
-                re[u].z -= c.x * b1.x - c.y * b1.y;
-                im[u].z -= c.x * b1.y + c.y * b1.x;
-                re[u].w -= c.x * b1.z - c.y * b1.w;
-                im[u].w -= c.x * b1.w + c.y * b1.z;
+                re[u] = pr[v];
+                im[u] = pr[n4 + v];
             }
         }
-    }
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const int v = lane + 32 * u;
-        if (v < n4) {
-            pr[v] = re[u];
-            pr[n4 + v] = im[u];
+        if (lane < df.n) {
+            const int t = lane;
+            const float2 F = gh_dtft_fix(s_rf[t] - tab[xy * Q + q].rfix, Ms);
+            s_ct[warp][t] = cmul(s_da[t], F);
         }
+        __syncwarp();
+        for (int t = 0; t < df.n; ++t) {
+            const float2 c = s_ct[warp][t];
+            const float4* bt = (const float4*)(df.atoms_b + ((size_t)t * Q + q) * Mc);  // 2 chirps per float4
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int v = lane + 32 * u;
+                if (v < n4) {
+                    const float4 b0 = __ldg(bt + 2 * v), b1 = __ldg(bt + 2 * v + 1);  // chirps 4v .. 4v + 3
+                    re[u].x -= c.x * b0.x - c.y * b0.y;
+                    im[u].x -= c.x * b0.y + c.y * b0.x;
+                    re[u].y -= c.x * b0.z - c.y * b0.w;
+                    im[u].y -= c.x * b0.w + c.y * b0.z;
+                    re[u].z -= c.x * b1.x - c.y * b1.y;
+                    im[u].z -= c.x * b1.y + c.y * b1.x;
+                    re[u].w -= c.x * b1.z - c.y * b1.w;
+                    im[u].w -= c.x * b1.w + c.y * b1.z;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int v = lane + 32 * u;
+            if (v < n4) {
+                pr[v] = re[u];
+                pr[n4 + v] = im[u];
+            }
+        }
+        __syncwarp();  // this row's coefficients read before the next row's
     }
 }
 
@@ -1095,9 +1110,8 @@ static int exact_stage1(gh_ctx* ctx, const Dims& d, const GeoParams& g, const fl
     void* tab = nullptr;
     if (df.n > 0 && df.n <= GH_MAX_K && (tc1 || need_tab) && d.Mc <= 256) {  // residual of iteration k >= 1
         GH_TRY(gh_ws(ctx, WS_EXACT_TAB, (size_t)d.nxy * d.Q * sizeof(ExEntry), &tab));
-        const long long rows = d.nxy * d.Q;
         gh_launch_begin(ctx, GH_K_DEFLATE, &ev);
-        exact_p_deflate_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, ctx->stream>>>(
+        exact_p_deflate_kernel<<<dim3((unsigned)((d.nxy + kDeflRows - 1) / kDeflRows), d.Q), 256, 0, ctx->stream>>>(
             (float*)P, (const ExEntry*)tab, df, d.Q, d.nxy, d.Ms, d.Mc);
         GH_TRY(gh_launch_end(ctx, GH_K_DEFLATE, ev, "exact_p_deflate_kernel"));
         *P_out = P;
