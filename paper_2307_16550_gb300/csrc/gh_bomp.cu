@@ -175,29 +175,35 @@ __device__ __forceinline__ void better(float s, long long c, float& bs, long lon
 // coordinate kernel's float64 (r, wx, wy) per (x, y, q)) the geometry is read
 // instead of recomputed: the same operations on the same values, so the same
 // (r, u).
-__device__ __forceinline__ void cell_ru(const GeoParams& g, long long cell, int q, const double* rw, double* r,
-                                        double* u) {
+// Grid indices (ix, iy, ivx, ivy) of a 4D cell.
+__device__ __forceinline__ void cell_decode(const GeoParams& g, long long cell, int* ix, int* iy, int* ivx,
+                                            int* ivy) {
     const int nvy = g.n[3], nvx = g.n[2], ny = g.n[1];
-    int ivy, ivx, iy, ix;
     if (cell < (1ll << 32)) {  // 32-bit division: a shorter chain than the 64-bit one
         unsigned c = (unsigned)cell;
-        ivy = (int)(c % (unsigned)nvy);
+        *ivy = (int)(c % (unsigned)nvy);
         c /= (unsigned)nvy;
-        ivx = (int)(c % (unsigned)nvx);
+        *ivx = (int)(c % (unsigned)nvx);
         c /= (unsigned)nvx;
-        iy = (int)(c % (unsigned)ny);
-        ix = (int)(c / (unsigned)ny);
+        *iy = (int)(c % (unsigned)ny);
+        *ix = (int)(c / (unsigned)ny);
     } else {
-        ivy = (int)(cell % nvy);
+        *ivy = (int)(cell % nvy);
         cell /= nvy;
-        ivx = (int)(cell % nvx);
+        *ivx = (int)(cell % nvx);
         cell /= nvx;
-        iy = (int)(cell % ny);
-        ix = (int)(cell / ny);
+        *iy = (int)(cell % ny);
+        *ix = (int)(cell / ny);
     }
+}
+
+__device__ __forceinline__ void cell_ru(const GeoParams& g, long long cell, int q, const double* rw, double* r,
+                                        double* u) {
+    int ix, iy, ivx, ivy;
+    cell_decode(g, cell, &ix, &iy, &ivx, &ivy);
     double d, wx, wy;
     if (rw) {
-        const double* e = rw + (((long long)ix * ny + iy) * g.Q + q) * 3;
+        const double* e = rw + (((long long)ix * g.n[1] + iy) * g.Q + q) * 3;
         *r = e[0];
         wx = e[1];
         wy = e[2];
@@ -548,16 +554,30 @@ __device__ void bomp_sum_solve(const GeoParams& g, int k, int K, const BompPtrs&
         double2 p = make_double2(0.0, 0.0);
         if (staged && lane == 0) p = __ldcg(w.phase + (size_t)k * Q + qq);
         double cx = 0.0, cy = 0.0;
-        for (int c = lane; c < w.chunks; c += 32) {
-            const double2 v = __ldcg(pp + c);
-            cx += v.x;
-            cy += v.y;
-        }
         // lanes at or above min(chunks, 32) hold zeros: the butterfly starts
         // at half the next power of two
-        for (int off = lane_span(w.chunks) >> 1; off > 0; off >>= 1) {
-            cx += __shfl_xor_sync(0xffffffffu, cx, off);
-            cy += __shfl_xor_sync(0xffffffffu, cy, off);
+        if (w.chunks <= 16) {
+            // real parts on lanes 0-15, imaginary parts on lanes 16-31: one
+            // butterfly (within each half) for both, the same additions
+            double a = 0.0;
+            const int c = lane & 15;
+            if (c < w.chunks) {
+                const double2 v = __ldcg(pp + c);
+                a += lane < 16 ? v.x : v.y;
+            }
+            for (int off = lane_span(w.chunks) >> 1; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+            cx = __shfl_sync(0xffffffffu, a, 0);
+            cy = __shfl_sync(0xffffffffu, a, 16);
+        } else {
+            for (int c = lane; c < w.chunks; c += 32) {
+                const double2 v = __ldcg(pp + c);
+                cx += v.x;
+                cy += v.y;
+            }
+            for (int off = lane_span(w.chunks) >> 1; off > 0; off >>= 1) {
+                cx += __shfl_xor_sync(0xffffffffu, cx, off);
+                cy += __shfl_xor_sync(0xffffffffu, cy, off);
+            }
         }
         if (lane == 0) {
             w.corr[(size_t)k * Q + qq] = make_double2(cx, cy);
@@ -586,6 +606,14 @@ __device__ void bomp_sum_solve(const GeoParams& g, int k, int K, const BompPtrs&
 __device__ __forceinline__ double sum_rows(const double* r) {
     static_assert(kCorrRows == 8, "pairwise tree of eight");
     return ((r[0] + r[1]) + (r[2] + r[3])) + ((r[4] + r[5]) + (r[6] + r[7]));
+}
+
+// Both sums (real parts rx, imaginary parts ry) by one warp, lanes 0 and 1
+// side by side (float64 issues per warp instruction, so two lanes cost what
+// one does); every lane of the warp gets the pair.
+__device__ __forceinline__ double2 sum_rows_xy(const double* rx, const double* ry, int lane) {
+    const double s = lane < 2 ? sum_rows(lane == 0 ? rx : ry) : 0.0;
+    return make_double2(__shfl_sync(0xffffffffu, s, 0), __shfl_sync(0xffffffffu, s, 1));
 }
 
 // CTA (chunk, q): partial <Y_q, b(u) (x) a(r)> over kCorrRows chirps. The last
@@ -622,11 +650,13 @@ __device__ void bomp_corr_body(const float2* __restrict__ Y, const GeoParams& g,
         ry[warp] = sy;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const double tx = sum_rows(rx), ty = sum_rows(ry);
-        w.corrp[((size_t)k * g.Q + q) * w.chunks + ch] = make_double2(tx, ty);
-        __threadfence();
-        s_last = atomicAdd(w.counter, 1u) == total - 1;
+    if (warp == 0) {
+        const double2 t = sum_rows_xy(rx, ry, lane);
+        if (lane == 0) {
+            w.corrp[((size_t)k * g.Q + q) * w.chunks + ch] = t;
+            __threadfence();
+            s_last = atomicAdd(w.counter, 1u) == total - 1;
+        }
     }
     __syncthreads();
     if (!s_last) return;
@@ -688,18 +718,46 @@ __global__ void __launch_bounds__(kStepThreads) bomp_step_kernel(const ArgPartia
         s_bc[warp] = bestc;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) better(s_bs[ww], s_bc[ww], best, bestc);
-        s_best = best;
-        s_best_cell = bestc;
-        const long long cell = bestc != 0x7fffffffffffffffLL ? bestc : 0;
-        double r, u;
-        cell_ru(g, cell, q, rw, &r, &u);
-        s_rf = gh_phase_fix(r);
-        s_uf = gh_phase_fix(u);
-        s_rk = r;
-        s_uk = u;
-        if (ch == 0) {  // the new atom's parameters at this receiver, for the last CTA
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) better(s_bs[ww], s_bc[ww], best, bestc);
+            s_best = best;
+            s_best_cell = bestc;
+        }
+        long long cell = __shfl_sync(0xffffffffu, bestc, 0);
+        if (cell == 0x7fffffffffffffffLL) cell = 0;
+        double r = 0.0, u = 0.0;
+        if (rw) {
+            // the new atom's (r, u) and fixed-point phases, lanes 0 and 1 side
+            // by side (vx | vy, then r | u): float64 issues per warp
+            // instruction, so the second lane comes free; the same operations
+            // on the same values as cell_ru
+            if (lane < 2) {
+                int ix, iy, ivx, ivy;
+                cell_decode(g, cell, &ix, &iy, &ivx, &ivy);
+                const double* e = rw + (((long long)ix * g.n[1] + iy) * g.Q + q) * 3;
+                r = e[0];
+                const double wx = e[1], wy = e[2];
+                const double v = lane == 0 ? gh_axis(g.lo[2], g.step[2], ivx) : gh_axis(g.lo[3], g.step[3], ivy);
+                const double vo = __shfl_sync(0x3u, v, lane ^ 1);
+                u = gh_speed(g, wx, wy, lane == 0 ? v : vo, lane == 0 ? vo : v);
+                const uint64_t f = gh_phase_fix(lane == 0 ? r : u);
+                if (lane == 0) {
+                    s_rf = f;
+                    s_rk = r;
+                } else {
+                    s_uf = f;
+                    s_uk = u;
+                }
+            }
+        } else if (lane == 0) {
+            cell_ru(g, cell, q, rw, &r, &u);
+            s_rf = gh_phase_fix(r);
+            s_uf = gh_phase_fix(u);
+            s_rk = r;
+            s_uk = u;
+        }
+        if (ch == 0 && lane == 0) {  // the new atom's parameters at this receiver, for the last CTA
             w.ru[(size_t)k * g.Q + q] = make_double2(r, u);
             float sn, cs;
             sincospif(mod2f(r * (g.Ms - 1) + u * (g.Mc - 1)), &sn, &cs);
@@ -765,11 +823,13 @@ __global__ void __launch_bounds__(kStepThreads) bomp_step_kernel(const ArgPartia
         ry[warp] = sy;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const double tx = sum_rows(rx), ty = sum_rows(ry);
-        w.corrp[((size_t)k * g.Q + q) * w.chunks + ch] = make_double2(tx, ty);
-        __threadfence();
-        s_last = atomicAdd(w.counter, 1u) == gridDim.x * gridDim.y - 1;
+    if (warp == 0) {
+        const double2 t = sum_rows_xy(rx, ry, lane);
+        if (lane == 0) {
+            w.corrp[((size_t)k * g.Q + q) * w.chunks + ch] = t;
+            __threadfence();
+            s_last = atomicAdd(w.counter, 1u) == gridDim.x * gridDim.y - 1;
+        }
     }
     __syncthreads();
     // the new atom's maps at this receiver (for the next iteration's residual

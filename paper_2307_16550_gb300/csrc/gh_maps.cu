@@ -385,20 +385,22 @@ __device__ __forceinline__ void deflate_rows(float2* __restrict__ maps, const De
                                              int logNd, int q, int i0, int IB) {
     __shared__ float2 s_c[GH_MAX_K * 16];  // (alpha_t - alpha_prev_t) tab_a_t[i], per atom and row
     const int n = df.n;
-    // two bins per 16-byte access, four accesses in flight per thread; the
-    // first four are issued before the coefficients are staged, so that the
-    // two rounds of loads overlap
+    // two bins per 16-byte access, eight accesses in flight per thread (the
+    // whole share of a CTA of eight 512-bin rows); the first eight are issued
+    // before the coefficients are staged, so that the two rounds of loads
+    // overlap
+    constexpr int U = 8;
     float4* row = (float4*)(maps + ((size_t)q * Nr + i0) * Nd);
     const int hp = Nd >> 1, lp = logNd - 1, npair = IB * hp;
-    float4 v[4];
-    auto load4 = [&](int base) {
+    float4 v[U];
+    auto load_u = [&](int base) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int pidx = base + u * blockDim.x;
             if (pidx < npair) v[u] = row[pidx];
         }
     };
-    load4(threadIdx.x);
+    load_u(threadIdx.x);
     for (int idx = threadIdx.x; idx < n * IB; idx += blockDim.x) {
         const int t = idx / IB, ii = idx - t * IB;
         const double2 al = df.alpha[(size_t)t * Q + q], ap = df.alpha_prev[(size_t)t * Q + q];
@@ -406,12 +408,12 @@ __device__ __forceinline__ void deflate_rows(float2* __restrict__ maps, const De
         s_c[idx] = cmul(da, df.tab_a[((size_t)t * Q + q) * Nr + i0 + ii]);
     }
     __syncthreads();
-    for (int base = threadIdx.x; base < npair; base += 4 * blockDim.x) {
-        if (base != (int)threadIdx.x) load4(base);
+    for (int base = threadIdx.x; base < npair; base += U * blockDim.x) {
+        if (base != (int)threadIdx.x) load_u(base);
         for (int t = 0; t < n; ++t) {
             const float4* tb = (const float4*)(df.tab_b + ((size_t)t * Q + q) * Nd);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const int pidx = base + u * blockDim.x;
                 if (pidx < npair) {
                     const float4 b = __ldg(tb + (pidx & (hp - 1)));
@@ -424,7 +426,7 @@ __device__ __forceinline__ void deflate_rows(float2* __restrict__ maps, const De
             }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < U; ++u)
             if (base + u * blockDim.x < npair) row[base + u * blockDim.x] = v[u];
     }
 }
