@@ -188,31 +188,6 @@ GH_API int gh_direct_exact(gh_ctx* ctx, const gh_radar* radar, const double* tx_
                     float* best_score);
 
 /*
- * gh_detect - K iterations of block orthogonal matching pursuit (BOMP, named
- * in the paper's acronym list; multi-target iterative direct detection is its
- * stated future work, Sec. VI). A block is the Q per-receiver atoms of one grid
- * cell with independent amplitudes. Iteration k:
- *   1. score the residual on the grid (method GH_HOP: maps + gh_score_grid;
- *      GH_EXACT: gh_direct_exact), cells already selected excluded;
- *   2. append the argmax cell;
- *   3. per receiver, solve the float64 least-squares problem for the
- *      amplitudes of all selected atoms (at their exact r, u) against Y;
- *   4. residual R_q = Y_q - sum_t alpha_{t,q} b(u_{t,q}) (x) a(r_{t,q}).
- *   Y_host_or_dev : complex float32 [Q][Mc][Ms], host or device
- *   cells_host    : host int64[K], selected cells in order
- *   scores_host   : host float[K], residual score at each selected cell (may be NULL)
- *   alpha_host    : host double[K][Q][2] (re, im) amplitudes multiplying the
- *                   atoms b(u) (x) a(r) of Sec. II, from the last solve (may be NULL)
- * All K iterations run on the device without host round trips; the stream is
- * synchronised once at the end. 1 <= K <= min(GH_MAX_K, ncells).
- * The residual's maps (GH_HOP with complex float32 maps) and stage-1
- * correlations (GH_EXACT) are reached by linearity after the first iteration:
- * the previous ones minus the newly solved part of the atoms' own maps or
- * correlations, which are known in closed form (equal to recomputing them
- * from R_q up to float32 rounding). Reduced-precision maps are remade from
- * R_q by FFT every iteration.
- */
-/*
  * gh_score_points - differentiable hopping score at P continuous points
  * (x, y, vx, vy), for off-grid refinement of detections and calibration of
  * receiver positions (Sec. VI names refined estimation as future work). Both
@@ -343,6 +318,31 @@ GH_API int gh_factorized(gh_ctx* ctx, int32_t method, const gh_radar* radar, con
  */
 GH_API int gh_set_detect_maps(gh_ctx* ctx, int32_t map_dtype);
 
+/*
+ * gh_detect - K iterations of block orthogonal matching pursuit (BOMP, named
+ * in the paper's acronym list; multi-target iterative direct detection is its
+ * stated future work, Sec. VI). A block is the Q per-receiver atoms of one grid
+ * cell with independent amplitudes. Iteration k:
+ *   1. score the residual on the grid (method GH_HOP: maps + gh_score_grid;
+ *      GH_EXACT: gh_direct_exact), cells already selected excluded;
+ *   2. append the argmax cell;
+ *   3. per receiver, solve the float64 least-squares problem for the
+ *      amplitudes of all selected atoms (at their exact r, u) against Y;
+ *   4. residual R_q = Y_q - sum_t alpha_{t,q} b(u_{t,q}) (x) a(r_{t,q}).
+ *   Y_host_or_dev : complex float32 [Q][Mc][Ms], host or device
+ *   cells_host    : host int64[K], selected cells in order
+ *   scores_host   : host float[K], residual score at each selected cell (may be NULL)
+ *   alpha_host    : host double[K][Q][2] (re, im) amplitudes multiplying the
+ *                   atoms b(u) (x) a(r) of Sec. II, from the last solve (may be NULL)
+ * All K iterations run on the device without host round trips; the stream is
+ * synchronised once at the end. 1 <= K <= min(GH_MAX_K, ncells).
+ * The residual's maps (GH_HOP with complex float32 maps) and stage-1
+ * correlations (GH_EXACT) are reached by linearity after the first iteration:
+ * the previous ones minus the newly solved part of the atoms' own maps or
+ * correlations, which are known in closed form (equal to recomputing them
+ * from R_q up to float32 rounding). Reduced-precision maps are remade from
+ * R_q by FFT every iteration.
+ */
 GH_API int gh_detect(gh_ctx* ctx, int32_t method, const gh_radar* radar,
               const double* tx_host, const double* rx_host, int32_t Q,
               const void* Y_host_or_dev, const gh_grid* grid, int32_t K,
@@ -401,9 +401,15 @@ GH_API int gh_coord_table(gh_ctx* ctx, const gh_radar* radar, const double* tx_h
  *   scores_dev   : device float[ncells] or NULL
  *   best_cell, best_score: host, may be NULL; when either is given the call
  *                  copies the result with cudaMemcpyAsync and synchronises the stream
+ * The address is cached per device ordinal for the life of the process:
+ * resetting a device (cudaDeviceReset) after its first call here is not
+ * supported, since later calls would pass the old address.
  * Errors: GH_EINVAL for bad arguments or a problem beyond the scratch size,
- * GH_ENOTSUP when shared memory is too small, GH_ECUDA for CUDA failures (no
- * error text is kept: there is no context).
+ * GH_ENOTSUP when shared memory is too small or the current device's ordinal
+ * is 64 or more, GH_ECUDA for CUDA failures (no error text is kept: there is
+ * no context). Launch failures are read from each launch's own status: a CUDA
+ * error that other code left pending in the calling thread is neither
+ * reported nor cleared.
  */
 #define GH_NOALLOC_MAX_XYQ 98304   /* max nx * ny * Q of gh_score_grid_noalloc */
 GH_API int gh_score_grid_noalloc(void* stream, const gh_radar* radar,

@@ -62,12 +62,14 @@ def range_rows(Y, pad):
     return R * centring_phase(np.arange(Nr), Nr, Ms)[None, None, :]
 
 
-def location_scores_hop(Y, radar, tx, rx, grid):
+def location_scores_hop(Y, radar, tx, rx, grid, table=None):
     """Grid-hopping Eq. 3: sum_q sum_mc |sum_k c_k R~_q,mc[i_q + k]|^2 with
-    the polar coefficients and wrapped reads of the 4D scorer."""
+    the polar coefficients and wrapped reads of the 4D scorer. ``table``
+    (a ``hopping.coord_table`` dict, default: the grid's own) supplies the
+    bins i_q and coefficients c_k."""
     R = range_rows(Y, radar.pad)
     Q, Mc, Nr = R.shape
-    t = coord_table(radar, tx, rx, grid)
+    t = coord_table(radar, tx, rx, grid) if table is None else table
     nx, ny = grid.n[0], grid.n[1]
     out = np.zeros((nx, ny))
     for q in range(Q):

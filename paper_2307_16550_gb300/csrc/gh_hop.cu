@@ -499,9 +499,20 @@ int hop_launch_t(cudaStream_t stream, const Dims& d, HopParams hp, const void* m
     if (ctas > d.nxy) ctas = d.nxy;
     hp.xy_per_cta = (d.nxy + ctas - 1) / ctas;
     ctas = (d.nxy + hp.xy_per_cta - 1) / hp.xy_per_cta;
-    hop_score_kernel<AC, MT><<<(unsigned)ctas, 32 * W, smem, stream>>>(maps, table, hp, scores, mask, nmask, parts);
+    // the launch's own status (cudaLaunchKernelEx returns it), so that an error
+    // another caller left pending in the thread is neither reported nor cleared
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ctas);
+    cfg.blockDim = dim3(32 * W);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
     *nparts = ctas;
-    return cudaGetLastError() == cudaSuccess ? GH_OK : GH_ECUDA;
+    if (cudaLaunchKernelEx(&cfg, hop_score_kernel<AC, MT>, maps, table, hp, scores, mask, nmask, parts) !=
+        cudaSuccess) {
+        (void)cudaGetLastError();  // consume this launch's own error
+        return GH_ECUDA;
+    }
+    return GH_OK;
 }
 
 template <int MT>
@@ -735,6 +746,21 @@ int noalloc_scratch(int dev, unsigned char** p) {
     return GH_OK;
 }
 
+// Launches kernel<<<grid, block, 0, stream>>>(args...) and returns GH_ECUDA
+// if that launch itself failed (its error is consumed), GH_OK otherwise.
+template <typename... P, typename... A>
+int noalloc_launch(void (*kernel)(P...), dim3 grid, dim3 block, cudaStream_t stream, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.stream = stream;
+    if (cudaLaunchKernelEx(&cfg, kernel, args...) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return GH_ECUDA;
+    }
+    return GH_OK;
+}
+
 }  // namespace
 
 extern "C" int gh_score_grid_noalloc(void* stream_ptr, const gh_radar* radar, const double* tx_host,
@@ -761,16 +787,18 @@ extern "C" int gh_score_grid_noalloc(void* stream_ptr, const gh_radar* radar, co
     GeoParams g;
     gh_fill_geo(&g, radar, tx_host, rx_host, Q, grid);
     const CoordParams cp = coord_params(d);
-    coord_kernel<<<(unsigned)((2 * d.nxy + 31) / 32), 32, 0, stream>>>(g, cp, table, nullptr, nullptr, nullptr,
-                                                                        nullptr, nullptr, nullptr);
-    if (cudaGetLastError() != cudaSuccess) return GH_ECUDA;
+    // launches checked by their own return status (noalloc_launch): an error
+    // left pending by other code in this thread is neither reported nor cleared
+    GH_TRY(noalloc_launch(coord_kernel, dim3((unsigned)((2 * d.nxy + 31) / 32)), dim3(32), stream, g, cp, table,
+                          (int32_t*)nullptr, (double*)nullptr, (float*)nullptr, (double*)nullptr, (int*)nullptr,
+                          (double*)nullptr));
     const HopParams hp = hop_params(d, g);
     long long nparts = 0;
     int st = hop_launch(stream, d, hp, maps_dev, GH_C64, table, scores_dev, nullptr, 0, parts,
                         kNoAllocMaxCtas, num_sms, (size_t)smem_optin, &nparts);
     if (st != GH_OK) return st;
-    argmax_finalize_kernel<<<1, 1024, 0, stream>>>(parts, (int)nparts, result);
-    if (cudaGetLastError() != cudaSuccess) return GH_ECUDA;
+    GH_TRY(noalloc_launch(argmax_finalize_kernel, dim3(1), dim3(1024), stream, (const ArgPartial*)parts,
+                          (int)nparts, result));
     if (best_cell || best_score) {
         ArgResult h;
         if (cudaMemcpyAsync(&h, result, sizeof(h), cudaMemcpyDeviceToHost, stream) != cudaSuccess) return GH_ECUDA;

@@ -87,3 +87,13 @@ def test_ten_targets_eight_receivers_unstaged_solve(ctx, torch_cuda, seed):
     _, _, alpha = ctx.gh_detect(gh.GH_HOP, sc.radar, sc.tx, sc.rx, sc.Q, to_dev(torch_cuda, Y32), sc.grid, 10)
     order = [list(sc.target_cells).index(c) for c in cells]
     np.testing.assert_allclose(alpha, sc.alpha[order], atol=2e-4)
+
+
+def test_paper_frame_exact_k3(ctx, torch_cuda):
+    """The benchmark's exact workload: paper-shaped frame, exact direct
+    decision function (tensor-core stages, stage-1 correlations of the
+    residual by linearity), K = 3, measurement in device memory."""
+    sc = scenes.paper_frame(1)
+    Y32, Y = measurement64(sc)
+    cells = _check(ctx, torch_cuda, sc, Y32, Y, 3, "exact")
+    assert len(set(cells.tolist())) == 3

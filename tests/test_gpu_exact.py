@@ -60,3 +60,21 @@ def test_exact_on_grid_noiseless_peak_value(ctx, torch_cuda):
     assert cell == sc.target_cells[0]
     peak = (sc.radar.Ms * sc.radar.Mc) ** 2 * np.sum(np.abs(sc.alpha[0]) ** 2)
     assert score == pytest.approx(peak, rel=1e-4)
+
+
+def test_paper_frame_full_grid(ctx, torch_cuda):
+    """Every exact score of the paper-shaped frame (128 x 128 (x, y) cells x
+    32 x 32 velocities, Q = 4, Ms = 256, Mc = 128: the tensor-core stage 1 and
+    stage 2 the benchmark times) against the oracle's factored evaluation,
+    element by element, and the argmax."""
+    sc = scenes.paper_frame(1)
+    Y32, Y = measurement64(sc)
+    got, cell, score = ctx.exact_scores(sc.radar, sc.tx, sc.rx, to_dev(torch_cuda, Y32), sc.grid)
+    got = got.cpu().numpy()
+    ref = direct.scores_full(Y, sc.radar, sc.tx, sc.rx, sc.grid)
+    err = rel_err(got, ref)
+    print(f"paper-shaped frame, exact: max |S_gpu - S| / max S = {err:.2e}")
+    assert err < TOL
+    assert top2_margin(ref) > 10 * TOL
+    assert cell == hopping.argmax_cell(ref)
+    assert score == pytest.approx(ref.max(), rel=TOL)

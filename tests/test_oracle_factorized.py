@@ -83,3 +83,63 @@ def test_multilateration_recovers_a_cell_from_its_exact_values(monkeypatch):
     cell, lc, vc = fz.indirect(None, sc.radar, sc.tx, sc.rx, sc.grid)
     assert cell == sc.grid.cell_index(ix, iy, ivx, ivy)
     assert lc < 1e-20 and vc < 1e-20
+
+
+def _loc_brute(Y, radar, table, ix, iy, coeffs=None):
+    """sum_q sum_mc |sum_k c_k <Y_q[mc], a~(n_k / Nr)>|^2 at (ix, iy), with the
+    centred atom a~_m(f) = exp(j 2 pi f (m - (Ms-1)/2)) taken at the unwrapped
+    bin n_k = i_q + k (no FFT, no folding of n into [0, Nr))."""
+    Q = Y.shape[0]
+    Ms = radar.Ms
+    Nr = radar.pad * Ms
+    m = np.arange(Ms) - (Ms - 1) / 2.0
+    c_all = table["c"] if coeffs is None else coeffs
+    tot = 0.0
+    for q in range(Q):
+        s = np.zeros(Y.shape[1], np.complex128)
+        for kk, k in enumerate((-1, 0, 1)):
+            n = int(table["i"][ix, iy, q]) + k
+            s += c_all[ix, iy, q, kk] * (Y[q] @ np.conj(np.exp(2j * np.pi * (n / Nr) * m)))
+        tot += np.sum(np.abs(s) ** 2)
+    return tot
+
+
+def test_hop_location_wrapped_reads_forced_bins():
+    """Bins forced to i = 0 and i = Nr - 1 make the stencil read n = -1 and
+    n = Nr; with unit coefficients each read, and with pairs of unit
+    coefficients the sum of a wrapped and an unwrapped read (where the
+    centring sign of the wrap shows in |.|^2), must equal the chirps'
+    correlations with the centred atoms at the unwrapped bins."""
+    from oracle import hopping
+    sc = _scene(seed=5, snr=10.0)
+    Y = model.measurement(sc)
+    table = hopping.coord_table(sc.radar, sc.tx, sc.rx, sc.grid)
+    Nr = sc.radar.pad * sc.radar.Ms
+    table["i"][0, 0, :] = 0
+    table["i"][0, 1, :] = Nr - 1
+    table["i"][3, 2, 1] = 2 * Nr - 1  # two periods up
+    for pick in ((1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (0, 1, 1), (1, -0.5, 1)):
+        coeffs = np.zeros_like(table["c"])
+        coeffs[...] = pick
+        t = dict(table, c=coeffs)
+        L = fz.location_scores_hop(Y, sc.radar, sc.tx, sc.rx, sc.grid, table=t)
+        for ix, iy in [(0, 0), (0, 1), (3, 2), (7, 9)]:
+            ref = _loc_brute(Y, sc.radar, t, ix, iy)
+            assert abs(L[ix, iy] - ref) < 1e-9 * ref
+
+
+def test_hop_location_aliased_ranges_against_brute_force():
+    """Ms = 8 makes every bistatic range wrap around the map several times:
+    the whole location grid with the polar coefficients against the brute
+    force at the unwrapped bins."""
+    from oracle import hopping
+    for Ms in (8, 16):
+        radar = scenes.Radar(24e9, 250e6, 128e-6, Ms, 16, 2)
+        grid = scenes.Grid.from_bounds((0, 0, -10, -10), (30, 30, 10, 10), (12, 10, 4, 4))
+        sc = scenes.custom_scene(4, radar, grid, Q=3, T=2, snr_db=10.0)
+        Y = model.measurement(sc)
+        table = hopping.coord_table(sc.radar, sc.tx, sc.rx, sc.grid)
+        assert table["i"].max() > 2 * radar.pad * Ms  # really wraps
+        L = fz.location_scores_hop(Y, sc.radar, sc.tx, sc.rx, sc.grid)
+        ref = np.array([[_loc_brute(Y, radar, table, ix, iy) for iy in range(10)] for ix in range(12)])
+        np.testing.assert_allclose(L, ref, rtol=1e-10)

@@ -40,3 +40,23 @@ def test_noalloc_rejects_problems_beyond_its_scratch(ctx, torch_cuda):
     with pytest.raises(gh.GhError) as e:
         gh.gh_score_grid_noalloc(None, sc.radar, sc.tx, sc.rx, 3, maps, big, None)
     assert e.value.status == gh.GH_EINVAL
+
+
+def test_warm_noalloc_call_leaves_free_device_memory_unchanged(ctx, torch_cuda):
+    """After a first call (which may load the kernels' code on the device),
+    further calls take no device memory: the device's free memory is the same
+    before and after them."""
+    stream = torch_cuda.cuda.current_stream()
+    sc = scenes.paper_frame(2)
+    Y32, _ = measurement64(sc)
+    maps = ctx.maps(sc.radar, to_dev(torch_cuda, Y32))
+    out = torch_cuda.empty(tuple(sc.grid.n), dtype=torch_cuda.float32, device="cuda:0")
+    first = gh.gh_score_grid_noalloc(stream, sc.radar, sc.tx, sc.rx, sc.Q, maps, sc.grid, out)
+    torch_cuda.cuda.synchronize()
+    free0, _ = torch_cuda.cuda.mem_get_info()
+    for _ in range(3):
+        assert gh.gh_score_grid_noalloc(stream, sc.radar, sc.tx, sc.rx, sc.Q, maps, sc.grid, out) == first
+        assert gh.gh_score_grid_noalloc(stream, sc.radar, sc.tx, sc.rx, sc.Q, maps, sc.grid, None) == first
+    torch_cuda.cuda.synchronize()
+    free1, _ = torch_cuda.cuda.mem_get_info()
+    assert free1 == free0
