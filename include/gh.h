@@ -429,6 +429,28 @@ GH_API int gh_selftest_tcgen05(gh_ctx* ctx, const float* A_host, const float* B_
                                float* D_host, int32_t N, int32_t K);
 
 /*
+ * gh_selftest_tcgen05_ex - gh_selftest_tcgen05 with a choice of operand
+ * layout and of the wait limit (diagnostic; no counterpart in the paper):
+ *   layout     : GH_TC_NOSWIZZLE (the canonical K-major layout of 8 x 16-byte
+ *                core matrices) or GH_TC_SW128 (K-major, 128-byte swizzle;
+ *                K a multiple of 64)
+ *   flags      : 0, or GH_TC_SKIP_MMA: no MMA and no commit are issued, so
+ *                nothing arrives on the completion barrier; the kernel's
+ *                bounded wait gives up after wait_polls polls, the kernel frees
+ *                its tensor memory, and the call returns GH_ETIMEOUT with the
+ *                context still usable (the test of that failure path)
+ *   wait_polls : polls of the completion barrier before giving up (0: the
+ *                library's default, 2^22)
+ * D_host is written only when the wait succeeds.
+ */
+#define GH_TC_NOSWIZZLE 0
+#define GH_TC_SW128     1
+#define GH_TC_SKIP_MMA  1
+GH_API int gh_selftest_tcgen05_ex(gh_ctx* ctx, const float* A_host, const float* B_host,
+                                  float* D_host, int32_t N, int32_t K, int32_t layout,
+                                  int32_t flags, int32_t wait_polls);
+
+/*
  * gh_probe_read_bandwidth - diagnostic read-bandwidth probe (no counterpart in
  * the paper): streams 16-byte loads over a device buffer of `bytes` bytes
  * (1 MiB .. 64 GiB), `reps` times (1 .. 1000), and returns GB/s in *gbs. A

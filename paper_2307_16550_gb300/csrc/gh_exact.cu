@@ -230,14 +230,22 @@ int launch_s2(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float* P, fl
 //
 // Per (x, y, q) the Doppler correlation F[a][b] = sum_mc Ex[a][mc] G[b][mc],
 // Ex[a][mc] = exp(-j 2 pi phx_a mc), G[b][mc] = P[mc] exp(-j 2 pi phy_b mc), is
-// a complex (nvx x Mc) x (Mc x nvy) product. It is written as one real GEMM
-// D = A B^T: row 2a of A holds [Re Ex | -Im Ex], row 2a+1 holds [Im Ex | Re Ex],
-// row b of B holds [Re G | Im G] (K = 2 Mc), so D[2a][b] = Re F, D[2a+1][b] = Im F.
-// Two receivers' problems share one M = 128 MMA (rows 0-63 and 64-127, their B
-// rows side by side in N = 2 * nvy_pad; the cross blocks are discarded).
-// Operands are split into BF16 high and low parts and three MMAs per K step
-// (hi*hi + hi*lo + lo*hi) accumulate in FP32 in tensor memory.
-// The K loop runs over stages of 32 chirps (K = 64 per stage).
+// a complex (nvx x Mc) x (Mc x nvy) product, written as the four real
+// products of its parts (Re Ex Re G, Re Ex Im G, Im Ex Re G, Im Ex Im G) in
+// one real GEMM D = A B^T with K = Mc:
+//   A rows (M = 128): Re Ex and Im Ex of every velocity row a, each split into
+//     BF16 high and low parts (x = hi + lo to about 16 significant bits);
+//   B rows (N = 4 nvy_pad): Re G and Im G of every velocity column b, split
+//     the same way.
+// Every block of D is used: Re F = sum (ReA ReB - ImA ImB), Im F = sum (ReA ImB
+// + ImA ReB) over the four (A part, B part) split combinations, so one MMA
+// per 16 chirps gives the split-BF16 product of one receiver (FP32 products
+// of BF16 values are exact; the accumulation is FP32 in tensor memory).
+// Row and column orders are chosen so that a 16x256b tensor-memory load
+// hands each epilogue thread all sixteen partial products of its cells:
+//   A row 32 (a / 8) + 8 s + a % 8, s = (Re hi, Re lo, Im hi, Im lo);
+//   B row 32 (b / 8) + 8 t + b % 8, t = (Re hi, Im hi, Re lo, Im lo).
+// The K loop runs over stages of 32 chirps (two MMAs of K = 16 per stage).
 // ---------------------------------------------------------------------------
 struct ExEntry {
     unsigned long long rfix;        // r_q(x): cycles per sample, 2^64 fixed point
@@ -286,19 +294,19 @@ __device__ __forceinline__ void st16(unsigned char* p, const uint32_t* w, uint32
 
 // ---------------------------------------------------------------------------
 // Stage 2 kernel, warp-specialised: the warps of a CTA (one per SM,
-// persistent over the items (x, y, receiver pair)) have fixed roles and meet
-// only at mbarriers:
-//   warp 0       : TMEM owner; its lane 0 issues the MMAs of each stage and
-//                  the commits that free a stage slot (empty) and publish an
-//                  accumulator (accfull)
-//   warps 1..16  : producers; generate a stage's split-BF16 A and B operands
-//                  into a ring of shared-memory slots (full, count 16 warps):
-//                  8 warps per operand, (receiver of the pair, chirp quarter)
-//   warps 17..20 : epilogue, one per TMEM lane quarter; square their Re or
-//                  Im F rows, hand the accumulator back (accempty, count 4),
-//                  sum the four quarters in a fixed order through shared
-//                  memory and keep each cell's sum over receiver pairs; after
-//                  the last pair of a cell (x, y): scores, mask and argmax
+// persistent over the items (x, y, q), receivers fastest) have fixed roles
+// and meet only at mbarriers:
+//   warp 0       : TMEM owner; its lane 0 issues the two MMAs of each stage
+//                  and the commits that free a stage slot (empty) and publish
+//                  an accumulator (accfull)
+//   warps 1..16  : producers, two groups of 8 taking alternate items; in a
+//                  group 4 warps generate A and 4 warps B, one 8-chirp chunk
+//                  of the stage each (full, count 8 warps per stage)
+//   warps 17..20 : epilogue, one per TMEM lane quarter (8 velocity rows a);
+//                  combine the sixteen partial products of each cell into
+//                  |F|^2, hand the accumulator back (accempty, count 4) and
+//                  keep each cell's sum over receivers; after the last
+//                  receiver of a cell (x, y): scores, mask and argmax
 // Two accumulators in TMEM let the MMAs of one item run while the epilogue
 // reads the previous one. Every wait is bounded; a wait that gives up sets a
 // shared abort flag that ends every role's loop, and the kernel reports
@@ -309,15 +317,14 @@ constexpr int kEpiWarps = 4;
 constexpr int kThreadsWS = 32 * (1 + kProdWarps + kEpiWarps);
 
 template <int NV32>
-struct WsCfg {
-    static constexpr int NVP = 32 * NV32;
-    static constexpr int N = 2 * NVP;
-    static constexpr int STAGES = NV32 == 1 ? 4 : 3;
-    static constexpr uint32_t A_BYTES = 128 * 64 * 2, B_BYTES = N * 64 * 2;
-    static constexpr uint32_t SLOT = 2 * A_BYTES + 2 * B_BYTES;
-    static constexpr uint32_t XFER = kEpiWarps * 32 * (NVP + 1) * 4;  // rows padded by one word
-    static constexpr uint32_t SMEM = STAGES * SLOT + XFER;
-    static constexpr uint32_t TM_COLS = 2 * N <= 128 ? 128 : 256;
+struct S2Cfg {
+    static constexpr int NVP = 32 * NV32;  // velocity columns b, padded
+    static constexpr int N = 4 * NVP;      // B rows: (Re, Im) x (hi, lo) per column b
+    static constexpr int STAGES = NV32 == 1 ? 8 : 6;  // two rings of STAGES / 2, one per producer group
+    static constexpr uint32_t A_BYTES = 128 * 32 * 2, B_BYTES = N * 32 * 2;
+    static constexpr uint32_t SLOT = A_BYTES + B_BYTES;
+    static constexpr uint32_t SMEM = STAGES * SLOT;
+    static constexpr uint32_t TM_COLS = 2 * N;  // two accumulators: 256 or 512 columns
 };
 
 // Bounded wait of one thread, sleeping in the wait instruction (up to 20 us
@@ -336,8 +343,6 @@ __device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(gh_tc::smem_u32(bar)) : "memory");
 }
-
-__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 // Barrier of the 128 epilogue threads that also ANDs their predicates, so that
 // the four warps take the same decision after their bounded waits.
@@ -392,34 +397,48 @@ __device__ __forceinline__ void split8(const float2* z, uint32_t* reH, uint32_t*
     }
 }
 
+// 16 consecutive-chunk TMEM values of the 16x256b shape (x4: four 8-column
+// chunks): thread t gets lane (base + t/4) in v[4c + 0, 1] and lane
+// (base + t/4 + 8) in v[4c + 2, 3], columns 8c + 2 (t % 4) + {0, 1}.
+__device__ __forceinline__ void tmem_ld_16x256b_x4(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x4.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 template <int NV32>
-__global__ void __launch_bounds__(kThreadsWS, 1) exact_tc_ws_kernel(const float* __restrict__ P,
+__global__ void __launch_bounds__(kThreadsWS, 1) exact_s2_tc_kernel(const float* __restrict__ P,
                                                                     const ExEntry* __restrict__ tab, ExactTcParams p,
                                                                     float* __restrict__ scores,
                                                                     const int64_t* __restrict__ mask, int nmask,
                                                                     ArgPartial* __restrict__ parts,
                                                                     int* __restrict__ status) {
-    using C = WsCfg<NV32>;
-    constexpr int NVP = C::NVP, N = C::N, S = C::STAGES;
+    using C = S2Cfg<NV32>;
+    constexpr int NVP = C::NVP, N = C::N, S = C::STAGES, SG = S / 2;
     constexpr uint32_t SBO = 128, LBO_A = 16 * 128, LBO_B = (N / 8) * 128;
-    constexpr uint32_t FLIP = 0x80008000u;  // sign bits of a BF16 pair
-    constexpr int CPT = NVP / 4;            // epilogue cells per thread and pair row
+    constexpr int NBLK = NVP / 8;  // 8-column blocks of b
     extern __shared__ __align__(1024) unsigned char smem[];
-    float* xfer = (float*)(smem + S * C::SLOT);  // [4 quarters][32 lanes][NVP + 1]
-    constexpr int XS = NVP + 1;                  // row stride of xfer (bank-conflict free)
     __shared__ uint64_t full[S], empty[S], accfull[2], accempty[2];
     __shared__ uint32_t tmem_holder;
     __shared__ int s_abort;
-    __shared__ int s_issued;  // stages issued by the MMA thread (for the abort drain)
+    __shared__ int s_last_slot, s_last_par;  // last stage the MMA thread committed (abort drain)
     __shared__ float s_bs[kEpiWarps];
     __shared__ long long s_bc[kEpiWarps];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int npairs = (p.Q + 1) >> 1;
+    const long long nitems_cta =
+        (blockIdx.x < p.nxy ? (p.nxy - 1 - blockIdx.x) / gridDim.x + 1 : 0) * (long long)p.Q;
     volatile int* abort_flag = &s_abort;
     if (tid == 0) {
         for (int i = 0; i < S; ++i) {
-            gh_tc::mbar_init(&full[i], kProdWarps);
+            gh_tc::mbar_init(&full[i], kProdWarps / 2);
             gh_tc::mbar_init(&empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -427,7 +446,8 @@ __global__ void __launch_bounds__(kThreadsWS, 1) exact_tc_ws_kernel(const float*
             gh_tc::mbar_init(&accempty[i], kEpiWarps);
         }
         s_abort = 0;
-        s_issued = 0;
+        s_last_slot = -1;
+        s_last_par = 0;
         gh_tc::mbar_fence_init();
     }
     if (warp == 0) gh_tc::tmem_alloc(&tmem_holder, C::TM_COLS);
@@ -443,63 +463,72 @@ __global__ void __launch_bounds__(kThreadsWS, 1) exact_tc_ws_kernel(const float*
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             const uint32_t idesc = gh_tc::idesc_bf16_f32(128, N);
-            uint32_t g = 0, it = 0;
             bool ok = true;
-            for (long long xy = blockIdx.x; xy < p.nxy && ok; xy += gridDim.x)
-                for (int pp = 0; pp < npairs && ok; ++pp, ++it) {
-                    const uint32_t buf = it & 1;
-                    if (!ws_wait(&accempty[buf], ((it >> 1) & 1) ^ 1, abort_flag)) {
+            for (long long it = 0; it < nitems_cta && ok; ++it) {
+                const uint32_t buf = (uint32_t)it & 1;
+                if (!ws_wait(&accempty[buf], ((uint32_t)(it >> 1) & 1) ^ 1, abort_flag)) break;
+                gh_tc::fence_after_sync();
+                const uint32_t dcol = buf * N;
+                uint32_t j = (uint32_t)((it >> 1) * p.nstages);  // stage count of the producing group's ring
+                for (int s = 0; s < p.nstages; ++s, ++j) {
+                    const uint32_t slot = (uint32_t)(it & 1) * SG + j % SG;
+                    if (!ws_wait(&full[slot], (j / SG) & 1, abort_flag)) {
                         ok = false;
                         break;
                     }
                     gh_tc::fence_after_sync();
-                    const uint32_t dcol = buf * N;
-                    for (int s = 0; s < p.nstages; ++s, ++g) {
-                        const uint32_t slot = g % S;
-                        if (!ws_wait(&full[slot], (g / S) & 1, abort_flag)) {
-                            ok = false;
-                            break;
-                        }
-                        gh_tc::fence_after_sync();
-                        unsigned char* Ah = smem + slot * C::SLOT;
-                        const uint32_t ah = gh_tc::smem_u32(Ah), al = ah + C::A_BYTES;
-                        const uint32_t bh = al + C::A_BYTES, bl = bh + C::B_BYTES;
+                    const uint32_t a0 = gh_tc::smem_u32(smem + slot * C::SLOT), b0 = a0 + C::A_BYTES;
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            const uint64_t dah = gh_tc::smem_desc(ah + 2 * kk * LBO_A, LBO_A, SBO);
-                            const uint64_t dal = gh_tc::smem_desc(al + 2 * kk * LBO_A, LBO_A, SBO);
-                            const uint64_t dbh = gh_tc::smem_desc(bh + 2 * kk * LBO_B, LBO_B, SBO);
-                            const uint64_t dbl = gh_tc::smem_desc(bl + 2 * kk * LBO_B, LBO_B, SBO);
-                            gh_tc::mma_bf16(tmem + dcol, dah, dbh, idesc, (s > 0 || kk > 0) ? 1u : 0u);
-                            gh_tc::mma_bf16(tmem + dcol, dah, dbl, idesc, 1u);
-                            gh_tc::mma_bf16(tmem + dcol, dal, dbh, idesc, 1u);
-                        }
-                        gh_tc::mma_commit(&empty[slot]);  // the slot is free once these MMAs are done
-                        s_issued = (int)(g + 1);
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint64_t da = gh_tc::smem_desc(a0 + 2 * kk * LBO_A, LBO_A, SBO);
+                        const uint64_t db = gh_tc::smem_desc(b0 + 2 * kk * LBO_B, LBO_B, SBO);
+                        gh_tc::mma_bf16(tmem + dcol, da, db, idesc, (s > 0 || kk > 0) ? 1u : 0u);
                     }
-                    if (!ok) break;
-                    gh_tc::mma_commit(&accfull[buf]);  // the item's accumulator is complete
+                    gh_tc::mma_commit(&empty[slot]);  // the slot is free once these MMAs are done
+                    s_last_slot = (int)slot;
+                    s_last_par = (int)((j / SG) & 1);
                 }
+                if (!ok) break;
+                gh_tc::mma_commit(&accfull[buf]);  // the item's accumulator is complete
+            }
         }
     } else if (warp <= kProdWarps) {
         // ---------------- producers ----------------
-        // The inputs of an item (its phase entry and, for B warps, its row of
-        // P) are loaded while the previous item is generated, so that no
-        // stage waits on a global load. P values depend on the chirp only:
+        // Group grp takes items it = grp, grp + 2, ... and fills its own ring
+        // of SG slots (grp * SG ..), stage j of the group at slot j % SG, so
+        // that every ring has one producer that fills its slots in order
+        // (with one shared ring, a group could get a full lap ahead of the
+        // MMAs on a slot the other group filled, where the phase parity of
+        // the slot's barrier can no longer tell the laps apart). The inputs of a group's next item
+        // (its phase entry and, for B warps, its row of P) are loaded while
+        // the current one is generated. P values depend on the chirp only:
         // lane l of a B warp holds chirps 32 (l / 8 + 4 u) + 8 kq + l % 8,
         // u = 0, 1, and a stage takes its 8 values by shuffles.
         const int pw = warp - 1;
-        const bool a_role = pw < 8;
-        const int h = (pw & 7) >> 2;  // receiver of the pair
-        const int kq = pw & 3;        // chirp quarter of a stage (8 chirps)
-        const uint32_t offA_re = gh_tc::kmajor_off((uint32_t)(h * 64 + lane), 0, LBO_A, SBO);
-        const uint32_t offA_im = gh_tc::kmajor_off((uint32_t)(h * 64 + 32 + lane), 0, LBO_A, SBO);
-        auto fetch = [&](long long fxy, int fpp, unsigned long long& f0, unsigned long long& f1, float* fre,
-                         float* fim) {
-            const int fq = 2 * fpp + h;
+        const int grp = pw >> 3;
+        const bool a_role = (pw & 7) < 4;
+        const int kq = pw & 3;  // chirp chunk of a stage (8 chirps)
+        // A: lane = velocity row a; rows 32 (a / 8) + 8 s + a % 8 (s = Re hi, Re lo, Im hi, Im lo)
+        const uint32_t offA = gh_tc::kmajor_off((uint32_t)(32 * (lane >> 3) + (lane & 7)), 0, LBO_A, SBO) +
+                              (uint32_t)kq * LBO_A;
+        // (x, y, q) of the group's items, advanced by counting (no division)
+        long long fxy = blockIdx.x;
+        int fq = grp;
+        auto advance = [&]() {  // to the group's next item: q += 2, carried into xy
+            fq += 2;
+            while (fq >= p.Q) {
+                fq -= p.Q;
+                fxy += gridDim.x;
+            }
+        };
+        while (fq >= p.Q) {  // the group's first item (Q = 1: item 1 is (x, y) number 1)
+            fq -= p.Q;
+            fxy += gridDim.x;
+        }
+        auto fetch = [&](long long it, unsigned long long& f0, unsigned long long& f1, float* fre, float* fim) {
             f0 = f1 = 0ull;
             fre[0] = fre[1] = fim[0] = fim[1] = 0.f;
-            if (fxy >= p.nxy || fq >= p.Q) return;
+            if (it >= nitems_cta) return;
             const ExEntry& e = tab[fxy * p.Q + fq];
             if (a_role) {
                 f0 = e.phx0;
@@ -518,193 +547,169 @@ __global__ void __launch_bounds__(kThreadsWS, 1) exact_tc_ws_kernel(const float*
                 }
             }
         };
-        uint32_t g = 0;
         bool ok = true;
         unsigned long long n0, n1;
         float nre[2], nim[2];
-        fetch(blockIdx.x, 0, n0, n1, nre, nim);
-        for (long long xy = blockIdx.x; xy < p.nxy && ok; xy += gridDim.x)
-            for (int pp = 0; pp < npairs && ok; ++pp) {
-                const int q = 2 * pp + h;
-                const bool vq = q < p.Q;
-                const unsigned long long c0e = n0, c1e = n1;
-                const float cre[2] = {nre[0], nre[1]}, cim[2] = {nim[0], nim[1]};
-                {
-                    long long nxy = xy;
-                    int npp = pp + 1;
-                    if (npp == npairs) {
-                        npp = 0;
-                        nxy += gridDim.x;
-                    }
-                    fetch(nxy, npp, n0, n1, nre, nim);  // next item's inputs, in flight during this item
+        fetch(grp, n0, n1, nre, nim);
+        for (long long it = grp; it < nitems_cta && ok; it += 2) {
+            const unsigned long long c0e = n0, c1e = n1;
+            const float cre[2] = {nre[0], nre[1]}, cim[2] = {nim[0], nim[1]};
+            advance();
+            fetch(it + 2, n0, n1, nre, nim);  // this group's next item, in flight during this one
+            AtomRow ar[NV32];
+            bool vrow[NV32];
+            if (a_role) {
+                vrow[0] = lane < p.nvx;
+                if (vrow[0]) ar[0] = atom_row(c0e + (unsigned long long)lane * c1e, 8 * kq);
+            } else {
+#pragma unroll
+                for (int gg = 0; gg < NV32; ++gg) {
+                    const int b = lane + 32 * gg;
+                    vrow[gg] = b < p.nvy;
+                    if (vrow[gg]) ar[gg] = atom_row(c0e + (unsigned long long)b * c1e, 8 * kq);
                 }
-                AtomRow ar[NV32];
-                bool vrow[NV32];
+            }
+            uint32_t j = (uint32_t)((it >> 1) * p.nstages);
+            for (int s = 0; s < p.nstages; ++s, ++j) {
+                const uint32_t slot = (uint32_t)grp * SG + j % SG;
+                float2 pv[8];
+                if (!a_role) {
+                    const int src = ((s & 3) << 3);
+                    const float sre = (s < 4) ? cre[0] : cre[1];
+                    const float sim = (s < 4) ? cim[0] : cim[1];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        pv[k] = make_float2(__shfl_sync(0xffffffffu, sre, src + k),
+                                            __shfl_sync(0xffffffffu, sim, src + k));
+                }
+                const bool w_ok = ws_wait(&empty[slot], ((j / SG) & 1) ^ 1, abort_flag);
+                if (!__all_sync(0xffffffffu, w_ok)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char* As = smem + slot * C::SLOT;
+                unsigned char* Bs = As + C::A_BYTES;
                 if (a_role) {
-                    vrow[0] = vq && lane < p.nvx;
-                    if (vrow[0]) ar[0] = atom_row(c0e + (unsigned long long)lane * c1e, 8 * kq);
+                    float2 z[8];
+                    if (vrow[0]) {
+                        atoms8_next(ar[0], z);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) z[k] = make_float2(0.f, 0.f);
+                    }
+                    uint32_t reH[4], reL[4], imH[4], imL[4];
+                    split8(z, reH, reL, imH, imL);
+                    st16(As + offA, reH, 0u);
+                    st16(As + offA + 8 * 16, reL, 0u);
+                    st16(As + offA + 16 * 16, imH, 0u);
+                    st16(As + offA + 24 * 16, imL, 0u);
                 } else {
 #pragma unroll
                     for (int gg = 0; gg < NV32; ++gg) {
-                        const int b = lane + 32 * gg;
-                        vrow[gg] = vq && b < p.nvy;
-                        if (vrow[gg]) ar[gg] = atom_row(c0e + (unsigned long long)b * c1e, 8 * kq);
-                    }
-                }
-                for (int s = 0; s < p.nstages; ++s, ++g) {
-                    const uint32_t slot = g % S;
-                    // chirps 32 s + 8 kq .. + 7: K chunk kq (real parts) and 4 + kq (imaginary parts)
-                    float2 pv[8];
-                    if (!a_role) {
-                        const int src = ((s & 3) << 3);
-                        const float sre = (s < 4) ? cre[0] : cre[1];
-                        const float sim = (s < 4) ? cim[0] : cim[1];
-#pragma unroll
-                        for (int k = 0; k < 8; ++k)
-                            pv[k] = make_float2(__shfl_sync(0xffffffffu, sre, src + k),
-                                                __shfl_sync(0xffffffffu, sim, src + k));
-                    }
-                    const bool w_ok = ws_wait(&empty[slot], ((g / S) & 1) ^ 1, abort_flag);
-                    if (!__all_sync(0xffffffffu, w_ok)) {
-                        ok = false;
-                        break;
-                    }
-                    unsigned char* Ah = smem + slot * C::SLOT;
-                    unsigned char* Al = Ah + C::A_BYTES;
-                    unsigned char* Bh = Al + C::A_BYTES;
-                    unsigned char* Bl = Bh + C::B_BYTES;
-                    const uint32_t c0 = kq, c1 = 4 + kq;
-                    if (a_role) {
                         float2 z[8];
-                        if (vrow[0]) {
-                            atoms8_next(ar[0], z);
+                        if (vrow[gg]) {
+                            atoms8_next(ar[gg], z);
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) z[k] = cmul(pv[k], z[k]);
                         } else {
 #pragma unroll
                             for (int k = 0; k < 8; ++k) z[k] = make_float2(0.f, 0.f);
                         }
                         uint32_t reH[4], reL[4], imH[4], imL[4];
                         split8(z, reH, reL, imH, imL);
-                        // Re F row: [Re z | -Im z]; Im F row: [Im z | Re z]
-                        st16(Ah + offA_re + c0 * LBO_A, reH, 0u);
-                        st16(Al + offA_re + c0 * LBO_A, reL, 0u);
-                        st16(Ah + offA_re + c1 * LBO_A, imH, FLIP);
-                        st16(Al + offA_re + c1 * LBO_A, imL, FLIP);
-                        st16(Ah + offA_im + c0 * LBO_A, imH, 0u);
-                        st16(Al + offA_im + c0 * LBO_A, imL, 0u);
-                        st16(Ah + offA_im + c1 * LBO_A, reH, 0u);
-                        st16(Al + offA_im + c1 * LBO_A, reL, 0u);
-                    } else {
-#pragma unroll
-                        for (int gg = 0; gg < NV32; ++gg) {
-                            float2 z[8];
-                            if (vrow[gg]) {
-                                atoms8_next(ar[gg], z);
-#pragma unroll
-                                for (int k = 0; k < 8; ++k) z[k] = cmul(pv[k], z[k]);
-                            } else {
-#pragma unroll
-                                for (int k = 0; k < 8; ++k) z[k] = make_float2(0.f, 0.f);
-                            }
-                            uint32_t reH[4], reL[4], imH[4], imL[4];
-                            split8(z, reH, reL, imH, imL);
-                            const uint32_t offB =
-                                gh_tc::kmajor_off((uint32_t)(h * NVP + lane + 32 * gg), 0, LBO_B, SBO);
-                            st16(Bh + offB + c0 * LBO_B, reH, 0u);
-                            st16(Bl + offB + c0 * LBO_B, reL, 0u);
-                            st16(Bh + offB + c1 * LBO_B, imH, 0u);
-                            st16(Bl + offB + c1 * LBO_B, imL, 0u);
-                        }
+                        // B row 32 (b / 8) + 8 t + b % 8, t = (Re hi, Im hi, Re lo, Im lo)
+                        const int b = lane + 32 * gg;
+                        const uint32_t offB =
+                            gh_tc::kmajor_off((uint32_t)(32 * (b >> 3) + (b & 7)), 0, LBO_B, SBO) +
+                            (uint32_t)kq * LBO_B;
+                        st16(Bs + offB, reH, 0u);
+                        st16(Bs + offB + 8 * 16, imH, 0u);
+                        st16(Bs + offB + 16 * 16, reL, 0u);
+                        st16(Bs + offB + 24 * 16, imL, 0u);
                     }
-                    gh_tc::fence_smem_to_async();  // generic stores -> tensor core
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&full[slot]);
                 }
+                gh_tc::fence_smem_to_async();  // generic stores -> tensor core
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[slot]);
             }
+        }
     } else {
         // ---------------- epilogue ----------------
-        const int e = warp & 3;               // TMEM lane quarter this warp may access (warp % 4)
-        const int eh = e >> 1;                // receiver of the pair
-        const int et = tid - 32 * (1 + kProdWarps);  // 0..127
-        const int ca = et >> 2;               // cell row a of this thread
-        const int cb0 = (et & 3) * CPT;       // first column b
-        float sacc[CPT];
+        // Warp of TMEM lane quarter e: velocity rows a = 8 e + lane / 4; per
+        // 8-column block of b, columns b = 8 blk + 2 (lane % 4) + {0, 1}.
+        const int e = warp & 3;
+        const int a = 8 * e + (lane >> 2);
+        const int bq = 2 * (lane & 3);
+        float sacc[2 * NBLK];
 #pragma unroll
-        for (int i = 0; i < CPT; ++i) sacc[i] = 0.f;
-        uint32_t it = 0;
+        for (int i = 0; i < 2 * NBLK; ++i) sacc[i] = 0.f;
         bool ok = true;
-        for (long long xy = blockIdx.x; xy < p.nxy && ok; xy += gridDim.x) {
-            for (int pp = 0; pp < npairs; ++pp, ++it) {
-                const uint32_t buf = it & 1;
-                const bool w_ok = ws_wait(&accfull[buf], (it >> 1) & 1, abort_flag);
-                if (!epi_all(w_ok)) {  // same decision in all four epilogue warps
-                    ok = false;
-                    break;
-                }
-                gh_tc::fence_after_sync();
-                float* dst = xfer + ((size_t)e * 32 + lane) * XS;
-#pragma unroll
-                for (int c = 0; c < NVP / 16; ++c) {
-                    float v[16];
-                    gh_tc::tmem_ld16(tmem + ((uint32_t)(32 * e) << 16) + buf * N + (uint32_t)(eh * NVP + 16 * c), v);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) dst[16 * c + i] = v[i] * v[i];
-                }
-                gh_tc::fence_before_sync();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&accempty[buf]);
-                epi_barrier();  // the four quarters' squares are in xfer
-                // |F|^2 = (Re F)^2 + (Im F)^2 for both receivers, in a fixed order
-#pragma unroll
-                for (int i = 0; i < CPT; ++i) {
-                    const int b = cb0 + i;
-                    const float r0 = xfer[((size_t)0 * 32 + ca) * XS + b];
-                    const float i0 = xfer[((size_t)1 * 32 + ca) * XS + b];
-                    const float r1 = xfer[((size_t)2 * 32 + ca) * XS + b];
-                    const float i1 = xfer[((size_t)3 * 32 + ca) * XS + b];
-                    sacc[i] += (r0 + i0) + (r1 + i1);
-                }
-                epi_barrier();  // xfer is free for the next item
+        long long xy = blockIdx.x;
+        int q = 0;
+        for (long long it = 0; it < nitems_cta && ok; ++it) {
+            const uint32_t buf = (uint32_t)it & 1;
+            const bool w_ok = ws_wait(&accfull[buf], (uint32_t)(it >> 1) & 1, abort_flag);
+            if (!epi_all(w_ok)) {  // same decision in all four epilogue warps
+                ok = false;
+                break;
             }
-            if (!ok) break;
+            gh_tc::fence_after_sync();
+            const uint32_t t0 = tmem + ((uint32_t)(32 * e) << 16) + buf * N;
+#pragma unroll
+            for (int blk = 0; blk < NBLK; ++blk) {
+                float re[16], im[16];  // [t][r][e]: B part t, A hi/lo r, column e
+                tmem_ld_16x256b_x4(t0 + 32 * blk, re);                 // A rows Re hi, Re lo
+                tmem_ld_16x256b_x4(t0 + (16u << 16) + 32 * blk, im);   // A rows Im hi, Im lo
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    // B parts t: 0 Re hi, 1 Im hi, 2 Re lo, 3 Im lo; index 4 t + 2 r + c
+                    const float rr = (re[0 + c] + re[2 + c]) + (re[8 + c] + re[10 + c]);   // Re A . Re G
+                    const float ri = (re[4 + c] + re[6 + c]) + (re[12 + c] + re[14 + c]);  // Re A . Im G
+                    const float ir = (im[0 + c] + im[2 + c]) + (im[8 + c] + im[10 + c]);   // Im A . Re G
+                    const float ii = (im[4 + c] + im[6 + c]) + (im[12 + c] + im[14 + c]);  // Im A . Im G
+                    const float fr = rr - ii, fi = ri + ir;
+                    sacc[2 * blk + c] += fr * fr + fi * fi;
+                }
+            }
+            gh_tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accempty[buf]);
+            if (++q < p.Q) continue;
             // cell (x, y) complete: scores, mask, argmax
-            if (ca < p.nvx) {
-                const long long cbase = xy * p.nv + (long long)ca * p.nvy;
+            q = 0;
+            if (a < p.nvx) {
+                const long long cbase = xy * p.nv + (long long)a * p.nvy;
                 bool hm = false;
                 for (int m = 0; m < nmask; ++m) {  // a masked cell in this (x, y) cell's block?
                     const long long mc = __ldg(&mask[m]);
                     hm |= mc >= xy * p.nv && mc < (xy + 1) * p.nv;
                 }
-                float rb = -INFINITY;
-                int ri = -1;
 #pragma unroll
-                for (int i = 0; i < CPT; ++i) {
-                    const int b = cb0 + i;
+                for (int i = 0; i < 2 * NBLK; ++i) {
+                    const int b = 8 * (i >> 1) + bq + (i & 1);
                     if (b < p.nvy) {
                         if (scores) scores[cbase + b] = sacc[i];
                         bool masked = false;
                         if (hm)
                             for (int m = 0; m < nmask; ++m) masked |= (__ldg(&mask[m]) == cbase + b);
-                        if (!masked && sacc[i] > rb) {
-                            rb = sacc[i];
-                            ri = b;
-                        }
+                        if (!masked) better(sacc[i], cbase + b, best, bestc);
                     }
                 }
-                if (ri >= 0) better(rb, cbase + ri, best, bestc);
             }
 #pragma unroll
-            for (int i = 0; i < CPT; ++i) sacc[i] = 0.f;
+            for (int i = 0; i < 2 * NBLK; ++i) sacc[i] = 0.f;
+            xy += gridDim.x;
         }
     }
 
     __syncthreads();
     if (*abort_flag) {
         if (tid == 0) atomicExch(status, GH_ETIMEOUT);
-        // give issued tensor-core work a bounded chance to drain before freeing TMEM
-        if (tid == 0 && s_issued > 0) {
-            const uint32_t last = (uint32_t)s_issued - 1;
-            gh_tc::mbar_wait_bounded(&empty[last % S], (last / S) & 1, kTcWaitIters);
-        }
+        // give issued tensor-core work a bounded chance to drain before freeing
+        // TMEM (tcgen05 work completes in issue order: the last commit suffices)
+        if (tid == 0 && s_last_slot >= 0)
+            gh_tc::mbar_wait_bounded(&empty[s_last_slot], (uint32_t)s_last_par, kTcWaitIters);
     }
     gh_tc::fence_before_sync();
     __syncthreads();
@@ -984,11 +989,11 @@ int launch_s1_tc(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate& df,
 template <int NV32>
 int launch_tc(gh_ctx* ctx, const Dims& d, const float* P, const ExEntry* tab, float* scores, const int64_t* mask,
               int nmask, ArgPartial* parts, int* status, long long* nparts) {
-    using C = WsCfg<NV32>;
+    using C = S2Cfg<NV32>;
     if (d.Mc > 256) return gh_fail(ctx, GH_ENOTSUP, "exact tensor-core stage 2 supports Mc <= 256");
     const size_t smem = C::SMEM;
     if (smem > ctx->smem_optin) return gh_fail(ctx, GH_ENOTSUP, "exact tensor-core path needs %zu B", smem);
-    GH_CUDA(cudaFuncSetAttribute(exact_tc_ws_kernel<NV32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GH_CUDA(cudaFuncSetAttribute(exact_s2_tc_kernel<NV32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     long long ctas = ctx->num_sms;  // one persistent CTA per SM
     if (ctas > d.nxy) ctas = d.nxy;
     ExactTcParams p;
@@ -1001,9 +1006,9 @@ int launch_tc(gh_ctx* ctx, const Dims& d, const float* P, const ExEntry* tab, fl
     p.nv = d.nv;
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_EXACT_S2, &ev);
-    exact_tc_ws_kernel<NV32><<<(unsigned)ctas, kThreadsWS, smem, ctx->stream>>>(P, tab, p, scores, mask, nmask, parts,
+    exact_s2_tc_kernel<NV32><<<(unsigned)ctas, kThreadsWS, smem, ctx->stream>>>(P, tab, p, scores, mask, nmask, parts,
                                                                                 status);
-    GH_TRY(gh_launch_end(ctx, GH_K_EXACT_S2, ev, "exact_tc_ws_kernel"));
+    GH_TRY(gh_launch_end(ctx, GH_K_EXACT_S2, ev, "exact_s2_tc_kernel"));
     *nparts = ctas;
     return GH_OK;
 }

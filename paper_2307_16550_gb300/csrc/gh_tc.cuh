@@ -111,6 +111,29 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;                // base offset 0, layout type 0 (no swizzle)
 }
 
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte
+// swizzled layout (sm_100 family, version 1, layout type 2): rows of 64 BF16
+// (128 bytes), 8-row groups of 1024 bytes (SBO), the 16-byte chunks of row r
+// permuted by XOR with r % 8. The tile must start on a 1024-byte boundary;
+// the K = 16 steps inside a row advance the start address by 32 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;             // leading byte offset (unused for this layout), 16 B
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;             // descriptor version
+    d |= (uint64_t)2 << 61;             // layout type: 128-byte swizzle
+    return d;
+}
+
+// Byte offset of element (row, k) in a K-major 128-byte-swizzled tile of
+// `rows` rows (a multiple of 8): K blocks of 64 elements lie `rows` x 128
+// bytes apart; in a block, row r occupies bytes r * 128 .. + 127 with its
+// 16-byte chunk c at position c ^ (r % 8).
+__host__ __device__ __forceinline__ uint32_t sw128_off(uint32_t row, uint32_t k, uint32_t rows) {
+    return (k >> 6) * rows * 128 + row * 128 + ((((k >> 3) & 7) ^ (row & 7)) << 4) + (k & 7) * 2;
+}
+
 // Instruction descriptor of kind::f16: BF16 x BF16 -> FP32, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(uint32_t M, uint32_t N) {
     return (1u << 4)                // D format: FP32

@@ -1,29 +1,45 @@
 // Self-test of the tensor-core plumbing used by the exact direct path:
-// D = A * B^T for M = 128, one CTA, BF16 operands in shared memory (no-swizzle
-// K-major layout), FP32 accumulation in tensor memory, mbarrier completion.
+// D = A * B^T for M = 128, one CTA, BF16 operands in shared memory (K-major,
+// no-swizzle or 128-byte-swizzled layout), FP32 accumulation in tensor memory,
+// mbarrier completion, and the bounded wait that gives up with GH_ETIMEOUT.
 #include "gh_internal.cuh"
 #include "gh_tc.cuh"
 
 namespace {
 
 constexpr uint32_t kWaitIters = 1u << 22;
+constexpr size_t kSw128Margin = 32 << 10;  // zeroed bytes after the swizzled tiles
 
+// layout 0: no swizzle; 1: 128-byte swizzle. skip_mma: no MMA and no commit
+// are issued, so nothing ever arrives on the barrier and the bounded wait
+// (wait_iters polls) runs out; the kernel then reports GH_ETIMEOUT and frees
+// its tensor memory like every tensor-core kernel of the library.
 __global__ void __launch_bounds__(128) tc_selftest_kernel(const float* __restrict__ A, const float* __restrict__ B,
-                                                          float* __restrict__ D, int N, int K, int* status) {
-    extern __shared__ __align__(128) unsigned char smem[];
+                                                          float* __restrict__ D, int N, int K, int layout,
+                                                          int skip_mma, uint32_t wait_iters, int* status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t bar;
     __shared__ uint32_t tmem_holder;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lboA = (128 / 8) * 128, lboB = (uint32_t)(N / 8) * 128, sbo = 128;
+    const size_t tileA = (size_t)128 * K * 2, tileB = (size_t)N * K * 2;
     unsigned char* sA = smem;
-    unsigned char* sB = smem + (size_t)128 * K * 2;
+    unsigned char* sB = smem + tileA;
+    auto offA = [&](int r, int k) {
+        return layout == 1 ? gh_tc::sw128_off(r, k, 128) : gh_tc::kmajor_off(r, k, lboA, sbo);
+    };
+    auto offB = [&](int r, int k) {
+        return layout == 1 ? gh_tc::sw128_off(r, k, (uint32_t)N) : gh_tc::kmajor_off(r, k, lboB, sbo);
+    };
+    if (layout == 1)
+        for (size_t i = tileA + tileB + tid; i < tileA + tileB + kSw128Margin; i += blockDim.x) smem[i] = 0;
     for (int idx = tid; idx < 128 * K; idx += blockDim.x) {
         const int r = idx / K, k = idx % K;
-        *(__nv_bfloat16*)(sA + gh_tc::kmajor_off(r, k, lboA, sbo)) = __float2bfloat16_rn(A[idx]);
+        *(__nv_bfloat16*)(sA + offA(r, k)) = __float2bfloat16_rn(A[idx]);
     }
     for (int idx = tid; idx < N * K; idx += blockDim.x) {
         const int r = idx / K, k = idx % K;
-        *(__nv_bfloat16*)(sB + gh_tc::kmajor_off(r, k, lboB, sbo)) = __float2bfloat16_rn(B[idx]);
+        *(__nv_bfloat16*)(sB + offB(r, k)) = __float2bfloat16_rn(B[idx]);
     }
     gh_tc::fence_smem_to_async();
     if (tid == 0) {
@@ -35,17 +51,24 @@ __global__ void __launch_bounds__(128) tc_selftest_kernel(const float* __restric
     __syncthreads();
     gh_tc::fence_after_sync();
     const uint32_t tmem = tmem_holder;
-    if (tid == 0) {
+    if (tid == 0 && !skip_mma) {
         const uint32_t idesc = gh_tc::idesc_bf16_f32(128, (uint32_t)N);
         const uint32_t a0 = gh_tc::smem_u32(sA), b0 = gh_tc::smem_u32(sB);
         for (int kk = 0; kk < K / 16; ++kk) {
-            const uint64_t ad = gh_tc::smem_desc(a0 + 2 * kk * lboA, lboA, sbo);
-            const uint64_t bd = gh_tc::smem_desc(b0 + 2 * kk * lboB, lboB, sbo);
+            uint64_t ad, bd;
+            if (layout == 1) {
+                // K block kk / 4 of the tile, 32 bytes per K = 16 step inside a row
+                ad = gh_tc::smem_desc_sw128(a0 + (uint32_t)(kk >> 2) * 128 * 128 + (uint32_t)(kk & 3) * 32);
+                bd = gh_tc::smem_desc_sw128(b0 + (uint32_t)(kk >> 2) * (uint32_t)N * 128 + (uint32_t)(kk & 3) * 32);
+            } else {
+                ad = gh_tc::smem_desc(a0 + 2 * kk * lboA, lboA, sbo);
+                bd = gh_tc::smem_desc(b0 + 2 * kk * lboB, lboB, sbo);
+            }
             gh_tc::mma_bf16(tmem, ad, bd, idesc, kk > 0);
         }
         gh_tc::mma_commit(&bar);
     }
-    const bool ok = gh_tc::mbar_wait_bounded(&bar, 0, kWaitIters);
+    const bool ok = gh_tc::mbar_wait_bounded(&bar, 0, wait_iters);
     if (!ok && lane == 0) atomicExch(status, GH_ETIMEOUT);
     gh_tc::fence_after_sync();
     if (ok) {
@@ -63,14 +86,20 @@ __global__ void __launch_bounds__(128) tc_selftest_kernel(const float* __restric
 
 }  // namespace
 
-extern "C" int gh_selftest_tcgen05(gh_ctx* ctx, const float* A_host, const float* B_host, float* D_host, int32_t N,
-                                   int32_t K) {
+extern "C" int gh_selftest_tcgen05_ex(gh_ctx* ctx, const float* A_host, const float* B_host, float* D_host,
+                                      int32_t N, int32_t K, int32_t layout, int32_t flags, int32_t wait_polls) {
     if (!ctx) return GH_EINVAL;
     if (!A_host || !B_host || !D_host) return gh_fail(ctx, GH_EINVAL, "NULL argument");
     if (N < 32 || N > 256 || N % 32 != 0 || K < 16 || K > 256 || K % 16 != 0)
         return gh_fail(ctx, GH_EINVAL, "N must be a multiple of 32 in [32, 256], K a multiple of 16 in [16, 256]");
+    if (layout != GH_TC_NOSWIZZLE && layout != GH_TC_SW128) return gh_fail(ctx, GH_EINVAL, "unknown layout %d", layout);
+    if (layout == GH_TC_SW128 && K % 64 != 0)
+        return gh_fail(ctx, GH_EINVAL, "the 128-byte swizzled layout needs K a multiple of 64");
+    if ((flags & ~GH_TC_SKIP_MMA) != 0 || wait_polls < 0) return gh_fail(ctx, GH_EINVAL, "bad flags or wait limit");
     cudaSetDevice(ctx->device);
     const size_t a = (size_t)128 * K, b = (size_t)N * K, dsz = (size_t)128 * N;
+    const size_t smem = (a + b) * 2 + (layout == GH_TC_SW128 ? kSw128Margin : 0);
+    if (smem > ctx->smem_optin) return gh_fail(ctx, GH_ENOTSUP, "self-test needs %zu B of shared memory", smem);
     void* buf;
     GH_TRY(gh_ws(ctx, WS_DIAG, (a + b + dsz) * sizeof(float) + 256, &buf));
     float* dA = (float*)buf;
@@ -81,11 +110,11 @@ extern "C" int gh_selftest_tcgen05(gh_ctx* ctx, const float* A_host, const float
     GH_CUDA(cudaMemcpyAsync(dB, B_host, b * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     GH_CUDA(cudaMemsetAsync(status, 0, sizeof(int), ctx->stream));
     GH_CUDA(cudaMemsetAsync(dD, 0, dsz * sizeof(float), ctx->stream));
-    const size_t smem = (a + b) * 2;
     GH_CUDA(cudaFuncSetAttribute(tc_selftest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_EXACT_S2, &ev);
-    tc_selftest_kernel<<<1, 128, smem, ctx->stream>>>(dA, dB, dD, N, K, status);
+    tc_selftest_kernel<<<1, 128, smem, ctx->stream>>>(dA, dB, dD, N, K, layout, flags & GH_TC_SKIP_MMA,
+                                                      wait_polls > 0 ? (uint32_t)wait_polls : kWaitIters, status);
     GH_TRY(gh_launch_end(ctx, GH_K_EXACT_S2, ev, "tc_selftest_kernel"));
     int st = 0;
     GH_CUDA(cudaMemcpyAsync(D_host, dD, dsz * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
@@ -93,6 +122,11 @@ extern "C" int gh_selftest_tcgen05(gh_ctx* ctx, const float* A_host, const float
     GH_CUDA(cudaStreamSynchronize(ctx->stream));
     if (st != 0) return gh_fail(ctx, GH_ETIMEOUT, "tensor-core self-test: mbarrier wait timed out");
     return GH_OK;
+}
+
+extern "C" int gh_selftest_tcgen05(gh_ctx* ctx, const float* A_host, const float* B_host, float* D_host, int32_t N,
+                                   int32_t K) {
+    return gh_selftest_tcgen05_ex(ctx, A_host, B_host, D_host, N, K, GH_TC_NOSWIZZLE, 0, 0);
 }
 
 // ---------------------------------------------------------------------------

@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_HERE, "lib", "libgh.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "gh.h")
 
 GH_OK, GH_EINVAL, GH_ENOMEM, GH_ECUDA, GH_ETIMEOUT, GH_ENOTSUP = 0, -1, -2, -3, -4, -5
+GH_TC_NOSWIZZLE, GH_TC_SW128 = 0, 1
+GH_TC_SKIP_MMA = 1
 GH_C64, GH_C16, GH_CBF16 = 0, 1, 2
 GH_HOP, GH_EXACT, GH_INDIRECT = 0, 1, 2
 (GH_K_RANGE_FFT, GH_K_DOPPLER_FFT, GH_K_COORD, GH_K_HOP_SCORE, GH_K_ARGMAX, GH_K_BOMP,
@@ -69,6 +71,7 @@ _SIGNATURES = {
     "gh_score_grid_noalloc": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, ctypes.POINTER(GhGrid),
                                      _P, _P, _P]),
     "gh_selftest_tcgen05": (_I32, [_P, _P, _P, _P, _I32, _I32]),
+    "gh_selftest_tcgen05_ex": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _I32]),
     "gh_probe_read_bandwidth": (_I32, [_P, ctypes.c_int64, _I32, _PD]),
     "gh_set_timing": (_I32, [_P, _I32]),
     "gh_set_graphs": (_I32, [_P, _I32]),
@@ -272,6 +275,17 @@ class Context:
         D = np.zeros((128, N), np.float32)
         self._check("gh_selftest_tcgen05", self._lib.gh_selftest_tcgen05(self.handle, _ptr(A), _ptr(B), _ptr(D),
                                                                          int(N), int(K)))
+        return D
+
+    def gh_selftest_tcgen05_ex(self, A, B, layout=GH_TC_NOSWIZZLE, flags=0, wait_polls=0):
+        """As gh_selftest_tcgen05, with the operand layout, flags and wait limit
+        of include/gh.h."""
+        A = np.ascontiguousarray(A, dtype=np.float32)
+        B = np.ascontiguousarray(B, dtype=np.float32)
+        N, K = B.shape
+        D = np.zeros((128, N), np.float32)
+        self._check("gh_selftest_tcgen05_ex", self._lib.gh_selftest_tcgen05_ex(
+            self.handle, _ptr(A), _ptr(B), _ptr(D), int(N), int(K), int(layout), int(flags), int(wait_polls)))
         return D
 
     def gh_probe_read_bandwidth(self, nbytes, reps=20):

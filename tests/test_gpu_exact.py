@@ -78,3 +78,23 @@ def test_paper_frame_full_grid(ctx, torch_cuda):
     assert top2_margin(ref) > 10 * TOL
     assert cell == hopping.argmax_cell(ref)
     assert score == pytest.approx(ref.max(), rel=TOL)
+
+
+@pytest.mark.parametrize("Ms,Mc,n", [
+    (64, 128, (6, 5, 32, 64)),    # 64 velocity columns: two 32-column halves of B
+    (32, 32, (7, 6, 17, 45)),     # ragged velocity grid, one 32-chirp stage
+    (32, 256, (5, 4, 32, 33)),    # eight stages, one column past 32
+    (64, 16, (4, 5, 9, 3)),       # fewer chirps than a stage
+])
+def test_tensor_core_shapes(ctx, torch_cuda, Ms, Mc, n):
+    """The tensor-core stage 2 over its shape range (velocity rows <= 32,
+    columns <= 64, Mc <= 256): every score against the oracle."""
+    radar = scenes.Radar(24e9, 250e6, 128e-6, Ms, Mc, 4)
+    grid = scenes.Grid.from_bounds((3, 2, -14, -13), (31, 29, 12, 15), n)
+    sc = scenes.custom_scene(6, radar, grid, Q=3, T=2, snr_db=5.0)
+    Y32, Y = measurement64(sc)
+    ref = direct.scores_full(Y, sc.radar, sc.tx, sc.rx, sc.grid)
+    got, cell, _ = ctx.exact_scores(sc.radar, sc.tx, sc.rx, to_dev(torch_cuda, Y32), sc.grid)
+    assert rel_err(got.cpu().numpy(), ref) < TOL
+    if top2_margin(ref) > 10 * TOL:
+        assert cell == hopping.argmax_cell(ref)
