@@ -238,14 +238,15 @@ int launch_s2(gh_ctx* ctx, const Dims& d, const GeoParams& g, const float* P, fl
 //   B rows (N = 4 nvy_pad): Re G and Im G of every velocity column b, split
 //     the same way.
 // Every block of D is used: Re F = sum (ReA ReB - ImA ImB), Im F = sum (ReA ImB
-// + ImA ReB) over the four (A part, B part) split combinations, so one MMA
-// per 16 chirps gives the split-BF16 product of one receiver (FP32 products
-// of BF16 values are exact; the accumulation is FP32 in tensor memory).
-// Row and column orders are chosen so that a 16x256b tensor-memory load
-// hands each epilogue thread all sixteen partial products of its cells:
+// + ImA ReB) over the four (A part, B part) split combinations, so four MMAs
+// per 64 chirps give the split-BF16 product of one receiver (FP32 products of
+// BF16 values are exact; the accumulation is FP32 in tensor memory).
+// Operands are K-major in the 128-byte swizzled layout, one 128-byte row of 64
+// chirps per operand row and stage. Row orders are chosen so that a 16x256b
+// tensor-memory load hands each epilogue thread all sixteen partial products
+// of its cells:
 //   A row 32 (a / 8) + 8 s + a % 8, s = (Re hi, Re lo, Im hi, Im lo);
 //   B row 32 (b / 8) + 8 t + b % 8, t = (Re hi, Im hi, Re lo, Im lo).
-// The K loop runs over stages of 32 chirps (two MMAs of K = 16 per stage).
 // ---------------------------------------------------------------------------
 struct ExEntry {
     unsigned long long rfix;        // r_q(x): cycles per sample, 2^64 fixed point
@@ -295,36 +296,40 @@ __device__ __forceinline__ void st16(unsigned char* p, const uint32_t* w, uint32
 // ---------------------------------------------------------------------------
 // Stage 2 kernel, warp-specialised: the warps of a CTA (one per SM,
 // persistent over the items (x, y, q), receivers fastest) have fixed roles
-// and meet only at mbarriers:
-//   warp 0       : TMEM owner; its lane 0 issues the two MMAs of each stage
+// and meet only at mbarriers. Sixteen warps, so that each SM sub-partition
+// (warp % 4) runs one epilogue warp, one A and one B producer:
+//   warp 0       : TMEM owner; its lane 0 issues the four MMAs of each stage
 //                  and the commits that free a stage slot (empty) and publish
-//                  an accumulator (accfull)
-//   warps 1..16  : producers, two groups of 8 taking alternate items; in a
-//                  group 4 warps generate A and 4 warps B, one 8-chirp chunk
-//                  of the stage each (full, count 8 warps per stage)
-//   warps 17..20 : epilogue, one per TMEM lane quarter (8 velocity rows a);
+//                  an accumulator (accfull); warps 1..3 have no role
+//   warps 4..7   : epilogue, one per TMEM lane quarter (8 velocity rows a);
 //                  combine the sixteen partial products of each cell into
 //                  |F|^2, hand the accumulator back (accempty, count 4) and
 //                  keep each cell's sum over receivers; after the last
 //                  receiver of a cell (x, y): scores, mask and argmax
+//   warps 8..11  : A producers, warps 12..15: B producers; warp j of each
+//                  operand makes chirp chunks 2j and 2j + 1 (8 chirps each)
+//                  of every stage (64 chirps) into a ring of shared-memory
+//                  slots (full, count 8)
 // Two accumulators in TMEM let the MMAs of one item run while the epilogue
 // reads the previous one. Every wait is bounded; a wait that gives up sets a
 // shared abort flag that ends every role's loop, and the kernel reports
 // GH_ETIMEOUT through the status word after freeing its tensor memory.
 // ---------------------------------------------------------------------------
-constexpr int kProdWarps = 16;
+constexpr int kProdWarps = 8;
 constexpr int kEpiWarps = 4;
-constexpr int kThreadsWS = 32 * (1 + kProdWarps + kEpiWarps);
+constexpr int kThreadsWS = 32 * 16;
+constexpr int kEpiWarp0 = 4, kProdWarp0 = 8;
+constexpr int kStageChirps = 64;  // one 128-byte swizzled row of BF16 per operand row
 
 template <int NV32>
 struct S2Cfg {
     static constexpr int NVP = 32 * NV32;  // velocity columns b, padded
     static constexpr int N = 4 * NVP;      // B rows: (Re, Im) x (hi, lo) per column b
-    static constexpr int STAGES = NV32 == 1 ? 8 : 6;  // two rings of STAGES / 2, one per producer group
-    static constexpr uint32_t A_BYTES = 128 * 32 * 2, B_BYTES = N * 32 * 2;
+    static constexpr int STAGES = NV32 == 1 ? 6 : 4;
+    static constexpr uint32_t A_BYTES = 128 * 128, B_BYTES = N * 128;
     static constexpr uint32_t SLOT = A_BYTES + B_BYTES;
-    static constexpr uint32_t SMEM = STAGES * SLOT;
-    static constexpr uint32_t TM_COLS = 2 * N;  // two accumulators: 256 or 512 columns
+    static constexpr uint32_t SMEM = STAGES * SLOT + 1024;  // + alignment of the slots to 1024 B
+    static constexpr uint32_t TM_COLS = 2 * N;              // two accumulators: 256 or 512 columns
 };
 
 // Bounded wait of one thread, sleeping in the wait instruction (up to 20 us
@@ -359,42 +364,50 @@ __device__ __forceinline__ bool epi_all(bool v) {
     return r != 0;
 }
 
-// Atoms of one row for the 8 chirps m0 .. m0 + 7 of every stage (m0 = 32 s +
-// 8 kq): z[k] = exp(-j 2 pi ph (m0 + k)). The seed of stage 0 and the steps
-// w = exp(-j 2 pi ph), w^2, w^32 are exact (fixed-point phase, float32
-// sincos); within a stage two interleaved recurrences z[k + 2] = z[k] w^2,
-// and the next stage's seed is this seed times w^32.
+// Atoms of one row for the two 8-chirp chunks (2j, 2j + 1) a producer warp
+// makes in every stage: z[k] = exp(-j 2 pi ph (m0 + k)), m0 = 64 s + 16 j
+// (+ 8 for the second chunk). The step w = exp(-j 2 pi ph) and the first
+// chunk's start are exact to float32 rounding (fixed-point phases,
+// polynomial sincos); w^8 and w^64 come from w by squaring. Inside a chunk
+// the three-term recurrence z[k + 1] = 2 cos(2 pi ph) z[k] - z[k - 1]
+// (|w| = 1); the second chunk starts at the first one's start times w^8 and
+// the next stage's start is the first one's start times w^64.
 struct AtomRow {
-    float2 seed, w, w2, w32;
+    float2 seed, w, w8, w64;
 };
 
 __device__ __forceinline__ AtomRow atom_row(unsigned long long ph, int m0) {
     AtomRow r;
-    r.w = gh_cis_fix(0ull - ph);
-    r.w2 = cmul(r.w, r.w);
-    float2 t = cmul(r.w2, r.w2);  // w^4
-    t = cmul(t, t);               // w^8
-    t = cmul(t, t);               // w^16
-    r.w32 = cmul(t, t);
-    r.seed = gh_cis_fix(0ull - ph * (unsigned long long)m0);
+    r.w = gh_cis_fix_poly(0ull - ph);
+    float2 t = cmul(r.w, r.w);  // w^2
+    t = cmul(t, t);             // w^4
+    r.w8 = cmul(t, t);
+    t = cmul(r.w8, r.w8);  // w^16
+    t = cmul(t, t);        // w^32
+    r.w64 = cmul(t, t);
+    r.seed = gh_cis_fix_poly(0ull - ph * (unsigned long long)m0);
     return r;
 }
 
-__device__ __forceinline__ void atoms8_next(AtomRow& r, float2* z) {
-    z[0] = r.seed;
-    z[1] = cmul(z[0], r.w);
+// z[0..7] from a chunk start z0: z[1] = z0 w, then the three-term recurrence.
+__device__ __forceinline__ void atoms8(float2 z0, float2 w, float* zr, float* zi) {
+    const float c2 = 2.f * w.x;
+    const float2 z1 = cmul(z0, w);
+    zr[0] = z0.x;
+    zi[0] = z0.y;
+    zr[1] = z1.x;
+    zi[1] = z1.y;
 #pragma unroll
-    for (int i = 2; i < 8; ++i) z[i] = cmul(z[i - 2], r.w2);
-    r.seed = cmul(r.seed, r.w32);
+    for (int i = 2; i < 8; ++i) {
+        zr[i] = fmaf(c2, zr[i - 1], -zr[i - 2]);
+        zi[i] = fmaf(c2, zi[i - 1], -zi[i - 2]);
+    }
 }
 
-__device__ __forceinline__ void split8(const float2* z, uint32_t* reH, uint32_t* reL, uint32_t* imH,
-                                       uint32_t* imL) {
+// Splits 8 values into BF16 high and low parts, packed in pairs.
+__device__ __forceinline__ void split8v(const float* v, uint32_t* H, uint32_t* L) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        gh_tc::split_bf16x2(z[2 * i].x, z[2 * i + 1].x, &reH[i], &reL[i]);
-        gh_tc::split_bf16x2(z[2 * i].y, z[2 * i + 1].y, &imH[i], &imL[i]);
-    }
+    for (int i = 0; i < 4; ++i) gh_tc::split_bf16x2(v[2 * i], v[2 * i + 1], &H[i], &L[i]);
 }
 
 // 16 consecutive-chunk TMEM values of the 16x256b shape (x4: four 8-column
@@ -421,16 +434,17 @@ __global__ void __launch_bounds__(kThreadsWS, 1) exact_s2_tc_kernel(const float*
                                                                     ArgPartial* __restrict__ parts,
                                                                     int* __restrict__ status) {
     using C = S2Cfg<NV32>;
-    constexpr int NVP = C::NVP, N = C::N, S = C::STAGES, SG = S / 2;
-    constexpr uint32_t SBO = 128, LBO_A = 16 * 128, LBO_B = (N / 8) * 128;
+    constexpr int NVP = C::NVP, N = C::N, S = C::STAGES;
     constexpr int NBLK = NVP / 8;  // 8-column blocks of b
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t full[S], empty[S], accfull[2], accempty[2];
     __shared__ uint32_t tmem_holder;
     __shared__ int s_abort;
     __shared__ int s_last_slot, s_last_par;  // last stage the MMA thread committed (abort drain)
     __shared__ float s_bs[kEpiWarps];
     __shared__ long long s_bc[kEpiWarps];
+    // the swizzled tiles need 1024-byte aligned slots
+    unsigned char* smem = smem_raw + ((1024u - (gh_tc::smem_u32(smem_raw) & 1023u)) & 1023u);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long nitems_cta =
@@ -438,7 +452,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) exact_s2_tc_kernel(const float*
     volatile int* abort_flag = &s_abort;
     if (tid == 0) {
         for (int i = 0; i < S; ++i) {
-            gh_tc::mbar_init(&full[i], kProdWarps / 2);
+            gh_tc::mbar_init(&full[i], kProdWarps);
             gh_tc::mbar_init(&empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -463,71 +477,55 @@ __global__ void __launch_bounds__(kThreadsWS, 1) exact_s2_tc_kernel(const float*
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             const uint32_t idesc = gh_tc::idesc_bf16_f32(128, N);
+            const uint32_t base = gh_tc::smem_u32(smem);
+            const uint64_t dA0 = gh_tc::smem_desc_sw128(base), dB0 = gh_tc::smem_desc_sw128(base + C::A_BYTES);
+            uint32_t g = 0;
             bool ok = true;
             for (long long it = 0; it < nitems_cta && ok; ++it) {
                 const uint32_t buf = (uint32_t)it & 1;
                 if (!ws_wait(&accempty[buf], ((uint32_t)(it >> 1) & 1) ^ 1, abort_flag)) break;
                 gh_tc::fence_after_sync();
-                const uint32_t dcol = buf * N;
-                uint32_t j = (uint32_t)((it >> 1) * p.nstages);  // stage count of the producing group's ring
-                for (int s = 0; s < p.nstages; ++s, ++j) {
-                    const uint32_t slot = (uint32_t)(it & 1) * SG + j % SG;
-                    if (!ws_wait(&full[slot], (j / SG) & 1, abort_flag)) {
+                const uint32_t dcol = tmem + buf * N;
+                for (int s = 0; s < p.nstages; ++s, ++g) {
+                    const uint32_t slot = g % S;
+                    if (!ws_wait(&full[slot], (g / S) & 1, abort_flag)) {
                         ok = false;
                         break;
                     }
                     gh_tc::fence_after_sync();
-                    const uint32_t a0 = gh_tc::smem_u32(smem + slot * C::SLOT), b0 = a0 + C::A_BYTES;
+                    const uint64_t so = (uint64_t)((slot * C::SLOT) >> 4);
 #pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const uint64_t da = gh_tc::smem_desc(a0 + 2 * kk * LBO_A, LBO_A, SBO);
-                        const uint64_t db = gh_tc::smem_desc(b0 + 2 * kk * LBO_B, LBO_B, SBO);
-                        gh_tc::mma_bf16(tmem + dcol, da, db, idesc, (s > 0 || kk > 0) ? 1u : 0u);
-                    }
+                    for (int kk = 0; kk < 4; ++kk)  // K = 16 steps: 32 bytes along the swizzled row
+                        gh_tc::mma_bf16(dcol, dA0 + so + 2 * kk, dB0 + so + 2 * kk, idesc, (s > 0 || kk > 0) ? 1u : 0u);
                     gh_tc::mma_commit(&empty[slot]);  // the slot is free once these MMAs are done
                     s_last_slot = (int)slot;
-                    s_last_par = (int)((j / SG) & 1);
+                    s_last_par = (int)((g / S) & 1);
                 }
                 if (!ok) break;
                 gh_tc::mma_commit(&accfull[buf]);  // the item's accumulator is complete
             }
         }
-    } else if (warp <= kProdWarps) {
+    } else if (warp >= kProdWarp0) {
         // ---------------- producers ----------------
-        // Group grp takes items it = grp, grp + 2, ... and fills its own ring
-        // of SG slots (grp * SG ..), stage j of the group at slot j % SG, so
-        // that every ring has one producer that fills its slots in order
-        // (with one shared ring, a group could get a full lap ahead of the
-        // MMAs on a slot the other group filled, where the phase parity of
-        // the slot's barrier can no longer tell the laps apart). The inputs of a group's next item
-        // (its phase entry and, for B warps, its row of P) are loaded while
-        // the current one is generated. P values depend on the chirp only:
-        // lane l of a B warp holds chirps 32 (l / 8 + 4 u) + 8 kq + l % 8,
-        // u = 0, 1, and a stage takes its 8 values by shuffles.
-        const int pw = warp - 1;
-        const int grp = pw >> 3;
-        const bool a_role = (pw & 7) < 4;
-        const int kq = pw & 3;  // chirp chunk of a stage (8 chirps)
-        // A: lane = velocity row a; rows 32 (a / 8) + 8 s + a % 8 (s = Re hi, Re lo, Im hi, Im lo)
-        const uint32_t offA = gh_tc::kmajor_off((uint32_t)(32 * (lane >> 3) + (lane & 7)), 0, LBO_A, SBO) +
-                              (uint32_t)kq * LBO_A;
-        // (x, y, q) of the group's items, advanced by counting (no division)
-        long long fxy = blockIdx.x;
-        int fq = grp;
-        auto advance = [&]() {  // to the group's next item: q += 2, carried into xy
-            fq += 2;
-            while (fq >= p.Q) {
-                fq -= p.Q;
-                fxy += gridDim.x;
-            }
+        // Warp j of an operand makes chirp chunks 2j and 2j + 1 of every stage
+        // (chirps 64 s + 16 j .. + 15); lane = operand row (a, or b and
+        // b + 32). The inputs of the next item (its phase entry and, for B
+        // warps, its row of P) are loaded while the current one is generated.
+        // P values depend on the chirp only: lane l of a B warp holds chirps
+        // 64 (l / 8) + 16 j + l % 8 and + 8, and a stage takes its 16 values
+        // by shuffles.
+        const int pw = warp - kProdWarp0;
+        const bool a_role = pw < 4;
+        const int j = pw & 3;
+        // chunk c of row r sits at 16 (c ^ (r % 8)) in the row's 128 bytes
+        auto row_off = [&](int r, int c) {
+            return (uint32_t)(32 * (r >> 3) + (r & 7)) * 128u + (uint32_t)((c ^ (r & 7)) << 4);
         };
-        while (fq >= p.Q) {  // the group's first item (Q = 1: item 1 is (x, y) number 1)
-            fq -= p.Q;
-            fxy += gridDim.x;
-        }
-        auto fetch = [&](long long it, unsigned long long& f0, unsigned long long& f1, float* fre, float* fim) {
+        long long fxy = blockIdx.x;
+        int fq = 0;
+        auto fetch = [&](long long it, unsigned long long& f0, unsigned long long& f1, float4& fp) {
             f0 = f1 = 0ull;
-            fre[0] = fre[1] = fim[0] = fim[1] = 0.f;
+            fp = make_float4(0.f, 0.f, 0.f, 0.f);
             if (it >= nitems_cta) return;
             const ExEntry& e = tab[fxy * p.Q + fq];
             if (a_role) {
@@ -536,104 +534,104 @@ __global__ void __launch_bounds__(kThreadsWS, 1) exact_s2_tc_kernel(const float*
             } else {
                 f0 = e.phy0;
                 f1 = e.dphy;
+                const int mc = 64 * (lane >> 3) + 16 * j + (lane & 7);
                 const float* Pq = P + ((size_t)fq * p.nxy + fxy) * 2 * p.Mc;
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int mc = 32 * ((lane >> 3) + 4 * u) + 8 * kq + (lane & 7);
-                    if (mc < p.Mc) {
-                        fre[u] = __ldg(Pq + mc);
-                        fim[u] = __ldg(Pq + p.Mc + mc);
-                    }
+                if (mc < p.Mc) {
+                    fp.x = __ldg(Pq + mc);
+                    fp.y = __ldg(Pq + p.Mc + mc);
+                }
+                if (mc + 8 < p.Mc) {
+                    fp.z = __ldg(Pq + mc + 8);
+                    fp.w = __ldg(Pq + p.Mc + mc + 8);
                 }
             }
         };
         bool ok = true;
         unsigned long long n0, n1;
-        float nre[2], nim[2];
-        fetch(grp, n0, n1, nre, nim);
-        for (long long it = grp; it < nitems_cta && ok; it += 2) {
+        float4 np_;
+        fetch(0, n0, n1, np_);
+        uint32_t g = 0;
+        for (long long it = 0; it < nitems_cta && ok; ++it) {
             const unsigned long long c0e = n0, c1e = n1;
-            const float cre[2] = {nre[0], nre[1]}, cim[2] = {nim[0], nim[1]};
-            advance();
-            fetch(it + 2, n0, n1, nre, nim);  // this group's next item, in flight during this one
+            const float4 cp = np_;
+            if (++fq == p.Q) {  // the next item's (x, y, q), by counting
+                fq = 0;
+                fxy += gridDim.x;
+            }
+            fetch(it + 1, n0, n1, np_);  // in flight during this item
             AtomRow ar[NV32];
             bool vrow[NV32];
-            if (a_role) {
-                vrow[0] = lane < p.nvx;
-                if (vrow[0]) ar[0] = atom_row(c0e + (unsigned long long)lane * c1e, 8 * kq);
-            } else {
 #pragma unroll
-                for (int gg = 0; gg < NV32; ++gg) {
-                    const int b = lane + 32 * gg;
-                    vrow[gg] = b < p.nvy;
-                    if (vrow[gg]) ar[gg] = atom_row(c0e + (unsigned long long)b * c1e, 8 * kq);
-                }
+            for (int gg = 0; gg < NV32; ++gg) {
+                const int r = lane + 32 * gg;
+                vrow[gg] = a_role ? (gg == 0 && r < p.nvx) : r < p.nvy;
+                if (vrow[gg]) ar[gg] = atom_row(c0e + (unsigned long long)r * c1e, 16 * j);
             }
-            uint32_t j = (uint32_t)((it >> 1) * p.nstages);
-            for (int s = 0; s < p.nstages; ++s, ++j) {
-                const uint32_t slot = (uint32_t)grp * SG + j % SG;
-                float2 pv[8];
+            for (int s = 0; s < p.nstages; ++s, ++g) {
+                const uint32_t slot = g % S;
+                float pr[16], pi[16];  // P of the stage's 16 chirps of this warp
                 if (!a_role) {
-                    const int src = ((s & 3) << 3);
-                    const float sre = (s < 4) ? cre[0] : cre[1];
-                    const float sim = (s < 4) ? cim[0] : cim[1];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        pv[k] = make_float2(__shfl_sync(0xffffffffu, sre, src + k),
-                                            __shfl_sync(0xffffffffu, sim, src + k));
+                    for (int k = 0; k < 8; ++k) {
+                        pr[k] = __shfl_sync(0xffffffffu, cp.x, 8 * s + k);
+                        pi[k] = __shfl_sync(0xffffffffu, cp.y, 8 * s + k);
+                        pr[8 + k] = __shfl_sync(0xffffffffu, cp.z, 8 * s + k);
+                        pi[8 + k] = __shfl_sync(0xffffffffu, cp.w, 8 * s + k);
+                    }
                 }
-                const bool w_ok = ws_wait(&empty[slot], ((j / SG) & 1) ^ 1, abort_flag);
+                const bool w_ok = ws_wait(&empty[slot], ((g / S) & 1) ^ 1, abort_flag);
                 if (!__all_sync(0xffffffffu, w_ok)) {
                     ok = false;
                     break;
                 }
                 unsigned char* As = smem + slot * C::SLOT;
-                unsigned char* Bs = As + C::A_BYTES;
-                if (a_role) {
-                    float2 z[8];
-                    if (vrow[0]) {
-                        atoms8_next(ar[0], z);
-                    } else {
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) z[k] = make_float2(0.f, 0.f);
-                    }
-                    uint32_t reH[4], reL[4], imH[4], imL[4];
-                    split8(z, reH, reL, imH, imL);
-                    st16(As + offA, reH, 0u);
-                    st16(As + offA + 8 * 16, reL, 0u);
-                    st16(As + offA + 16 * 16, imH, 0u);
-                    st16(As + offA + 24 * 16, imL, 0u);
-                } else {
+                for (int gg = 0; gg < (a_role ? 1 : NV32); ++gg) {
+                    const int r = lane + 32 * gg;
 #pragma unroll
-                    for (int gg = 0; gg < NV32; ++gg) {
-                        float2 z[8];
+                    for (int h = 0; h < 2; ++h) {  // chunk 2j + h
+                        float zr[8], zi[8];
                         if (vrow[gg]) {
-                            atoms8_next(ar[gg], z);
+                            const float2 z0 = h == 0 ? ar[gg].seed : cmul(ar[gg].seed, ar[gg].w8);
+                            atoms8(z0, ar[gg].w, zr, zi);
+                            if (!a_role) {
 #pragma unroll
-                            for (int k = 0; k < 8; ++k) z[k] = cmul(pv[k], z[k]);
+                                for (int k = 0; k < 8; ++k) {  // G = P conj(Ey)
+                                    const float a = pr[8 * h + k], b = pi[8 * h + k];
+                                    const float x = zr[k], y = zi[k];
+                                    zr[k] = a * x - b * y;
+                                    zi[k] = a * y + b * x;
+                                }
+                            }
                         } else {
 #pragma unroll
-                            for (int k = 0; k < 8; ++k) z[k] = make_float2(0.f, 0.f);
+                            for (int k = 0; k < 8; ++k) zr[k] = zi[k] = 0.f;
                         }
                         uint32_t reH[4], reL[4], imH[4], imL[4];
-                        split8(z, reH, reL, imH, imL);
-                        // B row 32 (b / 8) + 8 t + b % 8, t = (Re hi, Im hi, Re lo, Im lo)
-                        const int b = lane + 32 * gg;
-                        const uint32_t offB =
-                            gh_tc::kmajor_off((uint32_t)(32 * (b >> 3) + (b & 7)), 0, LBO_B, SBO) +
-                            (uint32_t)kq * LBO_B;
-                        st16(Bs + offB, reH, 0u);
-                        st16(Bs + offB + 8 * 16, imH, 0u);
-                        st16(Bs + offB + 16 * 16, reL, 0u);
-                        st16(Bs + offB + 24 * 16, imL, 0u);
+                        split8v(zr, reH, reL);
+                        split8v(zi, imH, imL);
+                        if (a_role) {  // A rows: Re hi, Re lo, Im hi, Im lo
+                            unsigned char* d = As + row_off(r, 2 * j + h);
+                            st16(d, reH, 0u);
+                            st16(d + 8 * 128, reL, 0u);
+                            st16(d + 16 * 128, imH, 0u);
+                            st16(d + 24 * 128, imL, 0u);
+                        } else {  // B rows: Re hi, Im hi, Re lo, Im lo
+                            unsigned char* d = As + C::A_BYTES + row_off(r, 2 * j + h);
+                            st16(d, reH, 0u);
+                            st16(d + 8 * 128, imH, 0u);
+                            st16(d + 16 * 128, reL, 0u);
+                            st16(d + 24 * 128, imL, 0u);
+                        }
                     }
+                    if (vrow[gg]) ar[gg].seed = cmul(ar[gg].seed, ar[gg].w64);  // next stage
                 }
                 gh_tc::fence_smem_to_async();  // generic stores -> tensor core
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&full[slot]);
             }
         }
-    } else {
+    } else if (warp >= kEpiWarp0) {
         // ---------------- epilogue ----------------
         // Warp of TMEM lane quarter e: velocity rows a = 8 e + lane / 4; per
         // 8-column block of b, columns b = 8 blk + 2 (lane % 4) + {0, 1}.
@@ -657,7 +655,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) exact_s2_tc_kernel(const float*
             const uint32_t t0 = tmem + ((uint32_t)(32 * e) << 16) + buf * N;
 #pragma unroll
             for (int blk = 0; blk < NBLK; ++blk) {
-                float re[16], im[16];  // [t][r][e]: B part t, A hi/lo r, column e
+                float re[16], im[16];  // [t][r][c]: B part t, A hi/lo r, column c
                 tmem_ld_16x256b_x4(t0 + 32 * blk, re);                 // A rows Re hi, Re lo
                 tmem_ld_16x256b_x4(t0 + (16u << 16) + 32 * blk, im);   // A rows Im hi, Im lo
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -719,15 +717,15 @@ __global__ void __launch_bounds__(kThreadsWS, 1) exact_s2_tc_kernel(const float*
     }
 
     // argmax over the epilogue warps
-    if (warp > kProdWarps) {
+    if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kEpiWarps) {
         for (int off = 16; off > 0; off >>= 1) {
             const float os = __shfl_down_sync(0xffffffffu, best, off);
             const long long oc = __shfl_down_sync(0xffffffffu, bestc, off);
             better(os, oc, best, bestc);
         }
         if (lane == 0) {
-            s_bs[warp - 1 - kProdWarps] = best;
-            s_bc[warp - 1 - kProdWarps] = bestc;
+            s_bs[warp - kEpiWarp0] = best;
+            s_bc[warp - kEpiWarp0] = bestc;
         }
     }
     __syncthreads();
@@ -1001,7 +999,7 @@ int launch_tc(gh_ctx* ctx, const Dims& d, const float* P, const ExEntry* tab, fl
     p.Mc = d.Mc;
     p.nvx = d.nvx;
     p.nvy = d.nvy;
-    p.nstages = (d.Mc + 31) / 32;
+    p.nstages = (d.Mc + kStageChirps - 1) / kStageChirps;
     p.nxy = d.nxy;
     p.nv = d.nv;
     cudaEvent_t ev;

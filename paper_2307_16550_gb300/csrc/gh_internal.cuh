@@ -304,6 +304,30 @@ __device__ __forceinline__ float2 gh_cis_fix(uint64_t ph) {
     return make_float2(c, s);
 }
 
+// cos and sin of 2*pi*phase for a fixed-point phase (top 32 bits used), by
+// reduction to the nearest quarter turn (exact, in integer arithmetic) and the
+// Taylor series of sin and cos on |x| <= pi/4 to the x^9 and x^10 terms (the
+// remainders, below x^11/11! and x^12/12!, are under 2e-9), then the exact
+// rotation by that many quarter turns. Float32; about 1e-7 absolute error.
+__device__ __forceinline__ float2 gh_cis_fix_poly(uint64_t ph) {
+    const uint32_t u = (uint32_t)(ph >> 32);
+    const uint32_t qi = (u + (1u << 29)) >> 30;        // nearest quarter turn, mod 4
+    const int32_t r = (int32_t)(u - (qi << 30));       // in [-2^29, 2^29)
+    const float x = (float)r * 1.46291807926715968e-9f;  // 2 pi / 2^32
+    const float x2 = x * x;
+    float sp = fmaf(x2, 2.75573192239858907e-6f, -1.98412698412698413e-4f);  // 1/9!, -1/7!
+    sp = fmaf(x2, sp, 8.33333333333333333e-3f);                               // 1/5!
+    sp = fmaf(x2, sp, -1.66666666666666667e-1f);                              // -1/3!
+    const float sn = fmaf(x * x2, sp, x);
+    float cp = fmaf(x2, -2.75573192239858907e-7f, 2.48015873015873016e-5f);   // -1/10!, 1/8!
+    cp = fmaf(x2, cp, -1.38888888888888889e-3f);                              // -1/6!
+    cp = fmaf(x2, cp, 4.16666666666666667e-2f);                               // 1/4!
+    cp = fmaf(x2, cp, -0.5f);                                                 // -1/2!
+    const float cs = fmaf(x2, cp, 1.0f);
+    const float c = (qi & 1) ? -sn : cs, sv = (qi & 1) ? cs : sn;  // times i^qi
+    return (qi & 2) ? make_float2(-c, -sv) : make_float2(c, sv);
+}
+
 // sin(2 pi x 2^-64) with full relative precision: x is reduced to its distance
 // v <= 2^62 from the nearest multiple of half a cycle before the float
 // conversion.

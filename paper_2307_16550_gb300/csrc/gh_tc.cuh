@@ -201,13 +201,16 @@ __host__ __device__ __forceinline__ uint32_t kmajor_off(uint32_t row, uint32_t k
 }
 
 // Splits two floats into BF16 high parts and BF16 residuals (x = hi + lo to
-// about 16 significant bits), packed in pairs.
+// about 16 significant bits), packed in pairs (x0 in the low half): hi is x
+// rounded to nearest-even BF16, lo is the FP32 remainder x - hi (exact)
+// rounded the same way.
 __device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t* hi, uint32_t* lo) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-    float2 hf = __bfloat1622float2(h);
-    __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
-    *hi = *reinterpret_cast<uint32_t*>(&h);
-    *lo = *reinterpret_cast<uint32_t*>(&l);
+    uint32_t h, l;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(x1), "f"(x0));
+    const float h0 = __uint_as_float(h << 16), h1 = __uint_as_float(h & 0xFFFF0000u);
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(x1 - h1), "f"(x0 - h0));
+    *hi = h;
+    *lo = l;
 }
 
 }  // namespace gh_tc
