@@ -471,6 +471,9 @@ def run_ours(args):
     if rank == 0:
         build.build()
     _barrier(world)
+    build_id = gh.gh_build_id()
+    if build_id != build.source_hash():
+        raise RuntimeError(f"loaded libgh.so ({build_id}) was not built from this tree ({build.source_hash()})")
     stream = torch.cuda.Stream(device)
     torch.cuda.set_stream(stream)
     ctx = gh.Context(local, stream)
@@ -608,7 +611,8 @@ def run_ours(args):
                                  "exact_ms_per_step_with_timers": ex_ms_timed / args.steps},
                "roofline": roof, "cpu_baseline": cpu, "precision": prec,
                "differentiation": diff, "batching": batch, "factorized": fact, "clocks": clk,
-               "wall_s_timed_region": wall}
+               "wall_s_timed_region": wall,
+               "build_id": build_id}
         print(json.dumps(out), flush=True)
     ctx.close()
     if world > 1:

@@ -122,6 +122,10 @@ typedef struct gh_ctx gh_ctx;
 GH_API int gh_create(gh_ctx** ctx, int32_t device, void* stream);
 /* Free the context, its workspace and (if owned) its stream. NULL is a no-op. */
 GH_API void gh_destroy(gh_ctx* ctx);
+/* Build id of the library: the first 16 hex digits of the SHA-256 of its
+ * CUDA sources and this header, fixed at compile time (no counterpart in the
+ * paper; it tells which sources a loaded library was built from). */
+GH_API const char* gh_build_id(void);
 /* Static text for a status code. */
 GH_API const char* gh_status_str(int32_t status);
 /* Text of the last error recorded in the context ("" if none). */
@@ -459,6 +463,24 @@ GH_API int gh_selftest_tcgen05_ex(gh_ctx* ctx, const float* A_host, const float*
  * (a growth drops the context's recorded gh_detect graphs).
  */
 GH_API int gh_probe_read_bandwidth(gh_ctx* ctx, int64_t bytes, int32_t reps, double* gbs);
+
+/*
+ * gh_inject_fault - host-side fault injection for testing the failure paths
+ * (no counterpart in the paper; nothing faults on the GPU). Arms one fault
+ * of `status` on the context: the (after + 1)-th site of that kind reached
+ * by later calls reports it, then the fault is disarmed.
+ *   GH_ENOMEM   : a workspace or pinned-buffer acquisition fails
+ *   GH_ECUDA    : a kernel-launch check reports a failure (the kernel itself
+ *                 was launched and runs)
+ *   GH_ETIMEOUT : the device status word read after a synchronising call
+ *                 reports a bounded wait that gave up (gh_make_maps has no
+ *                 such read)
+ *   GH_OK       : disarms an armed fault
+ * The call that meets the fault returns its status with the message in
+ * gh_last_error; the context stays usable (no partial state survives into
+ * the next call). after >= 0.
+ */
+GH_API int gh_inject_fault(gh_ctx* ctx, int32_t status, int32_t after);
 
 /*
  * Instrumentation. gh_set_timing(ctx, mask) brackets every launch of the

@@ -5,6 +5,11 @@ into paper_2307_16550_gb300/lib/libgh.so with the static CUDA runtime. Host
 code is compiled with -ffp-contract=off so that float64 expressions evaluate
 with the documented rounding on every host architecture.
 
+The library carries the build id of its sources (source_hash(): SHA-256 of
+every csrc/*.cu, csrc/*.cuh and include/gh.h, first 16 hex digits), returned
+by gh_build_id(); lib/libgh.so.id records it beside the library, and a
+library whose id differs from the sources' is rebuilt.
+
     python -m paper_2307_16550_gb300.build [--force]
 """
 from __future__ import annotations
@@ -44,9 +49,27 @@ def _deps():
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "gh.h")]
 
 
+def source_hash() -> str:
+    """Build id of the library sources (file names and contents)."""
+    import hashlib
+    h = hashlib.sha256()
+    for p in sorted(_deps()):
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _id_path(lib: str) -> str:
+    return lib + ".id"
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(_id_path(LIB)):
         return False
+    with open(_id_path(LIB)) as f:
+        if f.read().strip() != source_hash():
+            return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
@@ -63,7 +86,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None, out=None
     os.makedirs(objdir, exist_ok=True)
     os.makedirs(os.path.dirname(lib), exist_ok=True)
     cc = nvcc()
-    flags = list(NVCC_FLAGS) + list(extra_flags or [])
+    bid = source_hash()
+    flags = list(NVCC_FLAGS) + [f'-DGH_BUILD_ID="{bid}"'] + list(extra_flags or [])
 
     def compile_one(src):
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
@@ -84,6 +108,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None, out=None
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, lib)
+    with open(_id_path(lib), "w") as f:
+        f.write(bid + "\n")
     return lib
 
 

@@ -27,6 +27,11 @@ int gh_fail_cuda(gh_ctx* ctx, cudaError_t e, const char* what, const char* file,
     return e == cudaErrorMemoryAllocation ? GH_ENOMEM : GH_ECUDA;
 }
 
+#ifndef GH_BUILD_ID
+#define GH_BUILD_ID "unknown"
+#endif
+extern "C" const char* gh_build_id(void) { return GH_BUILD_ID; }
+
 extern "C" const char* gh_status_str(int32_t status) {
     switch (status) {
         case GH_OK: return "ok";
@@ -40,6 +45,32 @@ extern "C" const char* gh_status_str(int32_t status) {
 }
 
 extern "C" const char* gh_last_error(const gh_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+// ---------------------------------------------------------------------------
+// Host-side fault injection: the failure paths of the entry points are
+// exercised without a GPU fault. Sites: workspace and pinned-buffer
+// acquisitions (GH_ENOMEM), kernel-launch checks (GH_ECUDA) and the read of
+// the device status word (GH_ETIMEOUT).
+// ---------------------------------------------------------------------------
+bool gh_fault_hit(gh_ctx* ctx, int status) {
+    if (!ctx || ctx->fault_status == 0 || ctx->fault_status != status) return false;
+    if (ctx->fault_after > 0) {
+        --ctx->fault_after;
+        return false;
+    }
+    ctx->fault_status = 0;
+    return true;
+}
+
+extern "C" int gh_inject_fault(gh_ctx* ctx, int32_t status, int32_t after) {
+    if (!ctx) return GH_EINVAL;
+    if (status != GH_OK && status != GH_ENOMEM && status != GH_ECUDA && status != GH_ETIMEOUT)
+        return gh_fail(ctx, GH_EINVAL, "cannot inject status %d", status);
+    if (after < 0) return gh_fail(ctx, GH_EINVAL, "after must be >= 0");
+    ctx->fault_status = status;
+    ctx->fault_after = after;
+    return GH_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Device guard: makes the context's device current for the duration of a call.
@@ -124,6 +155,7 @@ void gh_graph_invalidate(gh_ctx* ctx) {
 }
 
 int gh_ws(gh_ctx* ctx, WsSlot slot, size_t bytes, void** p) {
+    if (gh_fault_hit(ctx, GH_ENOMEM)) return gh_fail(ctx, GH_ENOMEM, "injected fault: workspace acquisition refused");
     if (bytes == 0) bytes = 256;
     if (ctx->ws_bytes[slot] < bytes) {
         if (ctx->capturing) return gh_fail(ctx, GH_ECUDA, "workspace growth during graph capture");
@@ -144,6 +176,7 @@ int gh_ws(gh_ctx* ctx, WsSlot slot, size_t bytes, void** p) {
 }
 
 int gh_pinned(gh_ctx* ctx, size_t bytes, void** p) {
+    if (gh_fault_hit(ctx, GH_ENOMEM)) return gh_fail(ctx, GH_ENOMEM, "injected fault: pinned buffer refused");
     if (ctx->pinned_bytes < bytes) {
         if (ctx->capturing) return gh_fail(ctx, GH_ECUDA, "pinned buffer growth during graph capture");
         gh_graph_invalidate(ctx);
@@ -190,6 +223,11 @@ void gh_launch_begin(gh_ctx* ctx, int kind, cudaEvent_t* start) {
 
 int gh_launch_end(gh_ctx* ctx, int kind, cudaEvent_t start, const char* name) {
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && gh_fault_hit(ctx, GH_ECUDA)) {
+        if (start) ctx->event_pool.push_back(start);
+        ctx->launches++;  // the kernel did launch
+        return gh_fail(ctx, GH_ECUDA, "injected fault: launch of %s reported as failed", name);
+    }
     if (e != cudaSuccess) {
         if (start) ctx->event_pool.push_back(start);
         return gh_fail_cuda(ctx, e, name, __FILE__, __LINE__);
@@ -462,7 +500,8 @@ int gh_status_reset(gh_ctx* ctx) {
 }
 
 static int check_status(gh_ctx* ctx, const ArgResult* host_slots) {
-    const int st = *(const int*)(host_slots + (kResultSlots - 1));
+    int st = *(const int*)(host_slots + (kResultSlots - 1));
+    if (st == 0 && gh_fault_hit(ctx, GH_ETIMEOUT)) st = GH_ETIMEOUT;
     if (st != 0) return gh_fail(ctx, st, "a device-side wait gave up (status %d)", st);
     return GH_OK;
 }

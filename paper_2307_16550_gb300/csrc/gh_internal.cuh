@@ -84,7 +84,15 @@ struct gh_ctx {
     double ms[GH_K_COUNT] = {0};
     int64_t nlaunch[GH_K_COUNT] = {0};
     int64_t launches = 0;
+
+    // host-side fault injection (gh_inject_fault): the status to report and
+    // how many of its sites still pass before it fires
+    int fault_status = 0;
+    int fault_after = 0;
 };
+
+// True (and disarmed) when an injected fault of this status fires at this site.
+bool gh_fault_hit(gh_ctx* ctx, int status);
 
 // Records a failed CUDA call in the context and returns GH_ECUDA.
 int gh_fail_cuda(gh_ctx* ctx, cudaError_t e, const char* what, const char* file, int line);

@@ -59,6 +59,7 @@ _SIGNATURES = {
     "gh_create": (_I32, [ctypes.POINTER(_P), _I32, _P]),
     "gh_destroy": (None, [_P]),
     "gh_status_str": (ctypes.c_char_p, [_I32]),
+    "gh_build_id": (ctypes.c_char_p, []),
     "gh_last_error": (ctypes.c_char_p, [_P]),
     "gh_make_maps": (_I32, [_P, ctypes.POINTER(GhRadar), _I32, _P, _P, _I32]),
     "gh_score_grid": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, _I32, ctypes.POINTER(GhGrid),
@@ -74,6 +75,7 @@ _SIGNATURES = {
     "gh_selftest_tcgen05_ex": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _I32]),
     "gh_probe_read_bandwidth": (_I32, [_P, ctypes.c_int64, _I32, _PD]),
     "gh_set_timing": (_I32, [_P, _I32]),
+    "gh_inject_fault": (_I32, [_P, _I32, _I32]),
     "gh_set_graphs": (_I32, [_P, _I32]),
     "gh_set_detect_maps": (_I32, [_P, _I32]),
     "gh_detect_batch": (_I32, [_P, _I32, _P, _P, _P, _P]),
@@ -117,6 +119,11 @@ def header_functions(path: str = HEADER):
 
 def gh_status_str(status: int) -> str:
     return load().gh_status_str(status).decode()
+
+
+def gh_build_id() -> str:
+    """Build id compiled into the loaded library (see include/gh.h)."""
+    return load().gh_build_id().decode()
 
 
 def _ptr(x):
@@ -387,6 +394,10 @@ class Context:
     def gh_set_detect_maps(self, map_dtype):
         """Storage type of the maps gh_detect makes for GH_HOP (GH_C64, GH_C16, GH_CBF16)."""
         self._check("gh_set_detect_maps", self._lib.gh_set_detect_maps(self.handle, int(map_dtype)))
+
+    def gh_inject_fault(self, status, after=0):
+        """Arms one host-side fault (see include/gh.h); GH_OK disarms."""
+        self._check("gh_inject_fault", self._lib.gh_inject_fault(self.handle, int(status), int(after)))
 
     def gh_set_graphs(self, enable: bool):
         self._check("gh_set_graphs", self._lib.gh_set_graphs(self.handle, int(bool(enable))))

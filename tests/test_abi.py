@@ -45,6 +45,7 @@ def test_null_context_is_rejected(lib):
     assert lib.gh_detect_batch(None, 1, None, None, None, None) == gh.GH_EINVAL
     assert lib.gh_score_points(None, r, None, None, 1, None, 0, None, 0, None) == gh.GH_EINVAL
     assert lib.gh_set_batch_tuning(None, 8, 4) == gh.GH_EINVAL
+    assert lib.gh_inject_fault(None, gh.GH_ECUDA, 0) == gh.GH_EINVAL
     lib.gh_destroy(None)
     assert lib.gh_create(None, 0, None) == gh.GH_EINVAL
 
@@ -71,3 +72,12 @@ def test_struct_sizes_agree_with_the_c_compiler(tmp_path):
     subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     assert [int(v) for v in out] == [ctypes.sizeof(gh.GhRadar), ctypes.sizeof(gh.GhGrid), ctypes.sizeof(gh.GhFrame)]
+
+
+def test_loaded_library_was_built_from_these_sources(lib):
+    """gh_build_id() of the loaded library equals the hash of the sources in
+    the tree (and the id file written beside it)."""
+    bid = gh.gh_build_id()
+    assert len(bid) == 16 and bid == build.source_hash()
+    with open(build.LIB + ".id") as f:
+        assert f.read().strip() == bid
