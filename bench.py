@@ -202,6 +202,48 @@ def oracle_exact_sample(sc, Y, nxy):
     return nxy * sc.grid.n[2] * sc.grid.n[3] * sc.Q, dt
 
 
+_POOL_FRAME = None
+
+
+def _oracle_pool_init(frame):
+    global _POOL_FRAME
+    _POOL_FRAME = frame
+
+
+def _oracle_rows_worker(rows):
+    """Oracle hopping scores of some x rows (a worker of the all-cores
+    baseline; the frame's maps were handed to the worker at start-up)."""
+    from oracle import hopping
+    Z, radar, tx, rx, grid = _POOL_FRAME
+    if rows:
+        hopping.hop_scores(Z, radar, tx, rx, grid, xy_rows=rows)
+    return len(rows)
+
+
+def oracle_hop_all_cores(sc, Y, rows, procs):
+    """The same oracle loops over x rows on `procs` host processes (one
+    numerical thread each; a spawn pool, safe after CUDA use). Timed: the
+    frame's maps (once, in this process) and the scores of `rows` x rows
+    split over the workers; the workers receive the maps when the pool
+    starts, outside the timed region. Returns (evals, seconds)."""
+    import multiprocessing as mp
+    from oracle import maps
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"  # inherited by the spawned workers
+    Z0 = maps.rd_maps(Y, sc.radar.pad)
+    chunks = [list(range(r, rows, procs)) for r in range(procs)]
+    with mp.get_context("spawn").Pool(procs, initializer=_oracle_pool_init,
+                                       initargs=((Z0, sc.radar, sc.tx, sc.rx, sc.grid),)) as pool:
+        pool.map(_oracle_rows_worker, [[]] * procs)  # workers up
+        t0 = time.perf_counter()
+        Z = maps.rd_maps(Y, sc.radar.pad)
+        done = sum(pool.map(_oracle_rows_worker, chunks, chunksize=1))
+        dt = time.perf_counter() - t0
+    assert done == rows and np.array_equal(Z, Z0)
+    nx, ny, nvx, nvy = sc.grid.n
+    return rows * ny * nvx * nvy * sc.Q, dt
+
+
 def _oracle_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -215,11 +257,29 @@ def cpu_baseline(sc, Y):
     rows = 128
     ev, dt = oracle_hop_sample(sc, Y, rows)
     ex_ev, ex_dt = oracle_exact_sample(sc, Y, 1024)
+    procs = os.cpu_count() or 1
+    ev_n, dt_n = oracle_hop_all_cores(sc, Y, rows, procs)
     return {"value": ev / dt, "unit": UNIT, "cores": _oracle_threads(), "kind": "oracle",
             "sample": f"FP64 NumPy oracle: maps of the frame + hopping scores of {rows} of 128 x rows "
                       f"({ev} cell-RX evals) in {dt:.2f} s; exact direct (factored) on 1024 (x,y) cells: "
                       f"{ex_ev / ex_dt:.3e} evals/s",
-            "exact_value": ex_ev / ex_dt, "host_cpus": os.cpu_count()}
+            "exact_value": ex_ev / ex_dt, "host_cpus": os.cpu_count(),
+            "all_cores": {"value": ev_n / dt_n, "unit": UNIT, "cores": procs, "kind": "oracle",
+                          "sample": f"the same maps (one process) + {rows} x rows split over {procs} processes "
+                                    f"(one numerical thread each): {dt_n:.2f} s",
+                          "cpu_model": _cpu_model()}}
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
 
 
 def run_reference(args):
@@ -253,7 +313,87 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def precision_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args):
+ACCURACY_SEEDS = 8
+HIT_TAUS = (0.3125, 0.625, 1.25)  # m: one grid step, the paper's 60 cm resolution, two resolutions
+
+
+def accuracy_leg(ctx, torch, gh, scenes, device, rank, args):
+    """Detection accuracy of grid hopping and of the exact direct method (the
+    benchmark's K = 3 detections) on ACCURACY_SEEDS paper-shaped frames,
+    against the frames' true targets. A target is hit at threshold tau when
+    the (x, y) centre of one of the K detected cells lies within tau metres
+    of its position (the paper's hit ratio against a distance threshold,
+    Sec. V, Fig. 3); `hit_cell` asks for its own (nearest) 4D cell and
+    `hit_4d` for a detection within one grid step of it on all four axes.
+    `identical` counts the frames where both methods detect the same cells."""
+    per = {m: {"hit": {str(t): 0 for t in HIT_TAUS}, "hit_cell": 0, "hit_4d": 0} for m in ("hop", "exact")}
+    identical, ntargets = 0, 0
+    for i in range(ACCURACY_SEEDS):
+        sc = scenes.paper_frame(1000 * (rank + 1) + i)
+        g = sc.grid
+        noise = torch.from_numpy(sc.noise.astype(np.complex64)).to(device)
+        Y = ctx.synth(sc.radar, sc.tx, sc.rx, sc.targets, sc.alpha, noise)
+        found = {}
+        for name, m in (("hop", gh.GH_HOP), ("exact", gh.GH_EXACT)):
+            cells, _, _ = ctx.gh_detect(m, sc.radar, sc.tx, sc.rx, sc.Q, Y, g, K_DETECT)
+            found[name] = [int(c) for c in cells]
+        identical += int(sorted(found["hop"]) == sorted(found["exact"]))
+        lo, step, n = np.array(g.lo), np.array(g.step), np.array(g.n)
+        for t in sc.targets:
+            ntargets += 1
+            own = np.clip(np.floor((t - lo) / step).astype(np.int64), 0, n - 1)
+            for name, cells in found.items():
+                idx = np.array([g.unravel(c) for c in cells])
+                centres = lo + (idx + 0.5) * step
+                dpos = np.hypot(centres[:, 0] - t[0], centres[:, 1] - t[1])
+                for tau in HIT_TAUS:
+                    per[name]["hit"][str(tau)] += int(dpos.min() <= tau + 1e-12)
+                per[name]["hit_cell"] += int(any((idx == own).all(axis=1)))
+                per[name]["hit_4d"] += int(any((np.abs(idx - own) <= 1).all(axis=1)))
+    out = {"frames": ACCURACY_SEEDS, "targets": ntargets, "K": K_DETECT,
+           "seeds": f"paper_frame({1000 * (rank + 1)} .. {1000 * (rank + 1) + ACCURACY_SEEDS - 1})",
+           "identical_cells_frames": identical}
+    for name in per:
+        out[name] = {"hit_ratio": {tau: v / ntargets for tau, v in per[name]["hit"].items()},
+                     "hit_cell_ratio": per[name]["hit_cell"] / ntargets,
+                     "hit_4d_ratio": per[name]["hit_4d"] / ntargets}
+    return out
+
+
+def precision_oracle_check(sc, Y, cells, scores_by_format, K):
+    """FP64 oracle check of the precision-at-scale detections (cheap: no full
+    grid). For the detected cells c_0..c_{K-1}: the oracle's residual before
+    iteration k (least squares of c_0..c_{k-1} against Y, the BOMP reading)
+    and its maps; the oracle's hopping scores over c_k's whole x row; the
+    error of each format's score at c_k relative to the row's maximum, and
+    whether c_k is the row's argmax (cells already selected excluded)."""
+    from oracle import bomp as obomp, hopping, maps as omaps
+    g = sc.grid
+    nv = g.n[2] * g.n[3]
+    rows = []
+    for k, c in enumerate(cells):
+        R = np.array(Y, copy=True)
+        if k > 0:
+            for q in range(sc.Q):
+                A = obomp.atom_matrix(sc.radar, sc.tx, sc.rx[q], g, cells[:k])
+                sol, *_ = np.linalg.lstsq(A, Y[q].reshape(-1), rcond=None)
+                R[q] = Y[q] - (A @ sol).reshape(Y[q].shape)
+        ix, iy, ivx, ivy = g.unravel(c)
+        row = hopping.hop_scores(omaps.rd_maps(R, sc.radar.pad), sc.radar, sc.tx, sc.rx, g,
+                                 xy_rows=[ix])[0].reshape(-1)
+        base = ix * g.n[1] * nv
+        for prev in cells[:k]:
+            if base <= prev < base + g.n[1] * nv:
+                row[prev - base] = -np.inf
+        ref = row[c - base]
+        rows.append({"k": k, "cell": int(c), "oracle_score": float(ref),
+                     "row_argmax": bool(int(np.argmax(row)) + base == c),
+                     "row_top2_margin": float((np.sort(row)[-1] - np.sort(row)[-2]) / np.max(row)),
+                     "rel_err": {f: float(abs(float(v[k]) - ref) / np.max(row)) for f, v in scores_by_format.items()}})
+    return rows
+
+
+def precision_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args, l2_gbs=None):
     """Precision-at-scale frame (Q = 8, Ms = 512 x Mc = 256, five targets at
     SNR 5 dB, grid 256 x 256 x 64 x 64 = 268M cells, K = 5): hopping detection
     with float32, float16 and bfloat16 maps, and the exact direct scores of a
@@ -292,9 +432,25 @@ def precision_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args):
         ctx.gh_set_timing(False)
         if cells64 is None:
             cells64 = cells
+        launch_s = hs_ms * 1e-3 / max(hs_n, 1)
+        units = sc.grid.ncells * sc.Q
+        bpe = 24 if mt == gh.GH_C64 else 12  # three map values per cell-RX eval
+        achieved = bpe * units / launch_s / 1e9
+        maps_bytes = sc.Q * sc.radar.pad ** 2 * sc.radar.Ms * sc.radar.Mc * (8 if mt == gh.GH_C64 else 4)
+        peaks, peak_src = _peaks()
         res["maps"][name] = {"value": evals / (ms * 1e-3), "ms_per_step": ms,
-                             "hop_score_ms": hs_ms / max(hs_n, 1), "cells": cells.tolist(),
-                             "cells_equal_c64": bool(np.array_equal(cells, cells64))}
+                             "hop_score_ms": launch_s * 1e3, "cells": cells.tolist(),
+                             "scores": [float(v) for v in scores],
+                             "cells_equal_c64": bool(np.array_equal(cells, cells64)),
+                             "roofline": {"bound": "l2", "achieved": achieved, "peak": l2_gbs, "unit": "GB/s",
+                                          "frac": achieved / l2_gbs if l2_gbs else None, "traffic": None,
+                                          "kernel": "hop_score_kernel", "bytes_per_unit": bpe,
+                                          "units_per_launch": units,
+                                          "peak_source": "L2-resident read probe of this run",
+                                          "hbm": {"achieved": (maps_bytes + sc.grid.n[0] * sc.grid.n[1] * sc.Q * 80)
+                                                  / launch_s / 1e9, "peak": peaks["hbm_gbs"],
+                                                  "peak_source": peak_src,
+                                                  "note": "compulsory bytes: maps + coordinate table"}}}
     ctx.gh_set_detect_maps(gh.GH_C64)
     t = sc.targets[0]
     sub = scenes.Grid.from_bounds((t[0] - 6.4, t[1] - 6.4, -15.0, -15.0), (t[0] + 6.4, t[1] + 6.4, 15.0, 15.0),
@@ -305,7 +461,15 @@ def precision_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args):
     ms, _ = timed(ex, args.steps)
     res["exact_subgrid"] = {"value": sub.ncells * sc.Q / (ms * 1e-3), "ms_per_step": ms,
                             "grid": list(sub.n)}
-    res["error_vs_oracle"] = "tests/test_gpu_precision.py (per score and per detected cell, printed with -s)"
+    t0 = time.perf_counter()
+    Yh = Y.cpu().numpy().astype(np.complex128)
+    res["oracle_check"] = {
+        "how": "FP64 oracle (residual by least squares of the earlier detections, its maps, hopping scores of "
+               "the detected cell's x row) at the c64 detections; rel_err = |score - oracle| / row max",
+        "cells": precision_oracle_check(sc, Yh, [int(c) for c in cells64], {
+            n: v["scores"] for n, v in res["maps"].items() if v["cells_equal_c64"]}, K)}
+    res["oracle_check"]["seconds"] = time.perf_counter() - t0
+    res["error_vs_oracle"] = "per score and per detected cell: oracle_check here, tests/test_gpu_precision.py"
     return res
 
 
@@ -539,7 +703,9 @@ def run_ours(args):
     torch.cuda.synchronize(device)
     _barrier(world)
     wall = time.perf_counter() - t_wall
-    prec = None if args.no_precision else precision_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args)
+    prec = None if args.no_precision else precision_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args,
+                                                           l2_gbs)
+    acc = accuracy_leg(ctx, torch, gh, scenes, device, rank, args)
     diff = diff_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args)
     fact = factorized_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args)
     batch = None if args.no_batch else batch_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args)
@@ -595,6 +761,7 @@ def run_ours(args):
                "config": workload_config(sc),
                "exact_direct": {"value": ex_value, "unit": UNIT, "ms_per_step": ex_ms / args.steps,
                                 "speedup_hop_vs_exact": value / ex_value,
+                                "accuracy": acc,
                                 "roofline": {"bound": "tensor", "achieved": ex_achieved, "peak": tc_peak,
                                              "unit": "TFLOP/s", "frac": ex_achieved / tc_peak, "traffic": None,
                                              "kernel": "exact_s1_tc_kernel + exact_tc_ws_kernel",
