@@ -49,9 +49,10 @@ GATHER_BYTES_PER_EVAL = 24  # three complex64 map values per cell-RX eval
 L2_PROBE_SIZES = (32, 64)  # MiB, well inside the 129 MB L2
 L2_PROBE_MIB = "32/64"
 L2_PROBE_REPS = 200
-# DRAM bytes (read + write) of one hop_score_kernel launch on this workload,
-# from an ncu capture, valid while the scorer's sources hash to the key.
-HOP_TRAFFIC = {"c52708b4ab4d7dc1": 10251264}  # ncu capture summarised under profiles/
+# One hop_score_kernel launch on this workload, from an ncu capture (summarised
+# under profiles/), valid while the scorer's sources hash to the key: DRAM
+# bytes (read + write), warp instructions issued, and L2-to-SM read bytes.
+HOP_NCU = {}
 
 
 def _hop_source_hash():
@@ -63,8 +64,8 @@ def _hop_source_hash():
     return h.hexdigest()[:16]
 
 
-def hop_traffic():
-    return HOP_TRAFFIC.get(_hop_source_hash())
+def hop_ncu():
+    return HOP_NCU.get(_hop_source_hash(), {})
 
 
 def _peaks():
@@ -676,6 +677,8 @@ def run_ours(args):
     # L2 read peak of this GPU for the scorer's roofline (before the warm-up:
     # the probe's buffer grows the workspace, which drops recorded graphs)
     l2_gbs = max(ctx.gh_probe_read_bandwidth(mib << 20, L2_PROBE_REPS) for mib in L2_PROBE_SIZES)
+    smem_gbs = max(ctx.gh_probe_smem_bandwidth() for _ in range(2))
+    issue_rate = max(ctx.gh_probe_issue_rate() for _ in range(2))
     torch.cuda.synchronize(device)
 
     # warm-up of each timed configuration (the library records a CUDA graph of
@@ -730,8 +733,21 @@ def run_ours(args):
     comp_bytes = maps_bytes + table_bytes
     achieved = gather_bytes / hs_avg_s / 1e9
     hbm_achieved = comp_bytes / hs_avg_s / 1e9
+    nc = hop_ncu()
+    algo = {"how": "the kernel's own counters (ncu capture of this source, stored in bench.py) against the "
+                   "limits measured in this run: warp instructions / issue-rate probe, L2-to-SM bytes / L2 read "
+                   "probe; frac = that bound's time / measured time",
+            "issue_rate_warp_inst_per_s": issue_rate, "smem_gbs": smem_gbs}
+    if nc:
+        t_issue = nc["inst"] / issue_rate
+        t_l2 = nc["l2_to_sm"] / (l2_gbs * 1e9)
+        algo.update({"warp_inst_per_launch": nc["inst"], "inst_per_eval": nc["inst"] * 32.0 / units,
+                     "issue_bound_ms": t_issue * 1e3, "issue_frac": t_issue / hs_avg_s,
+                     "l2_to_sm_bytes_per_launch": nc["l2_to_sm"], "l2_bound_ms": t_l2 * 1e3,
+                     "l2_frac": t_l2 / hs_avg_s})
     roof = {"bound": "l2", "achieved": achieved, "peak": l2_gbs, "unit": "GB/s", "frac": achieved / l2_gbs,
-            "traffic": hop_traffic(), "kernel": "hop_score_kernel", "kernel_ms": hs_avg_s * 1e3,
+            "traffic": nc.get("dram"), "kernel": "hop_score_kernel", "kernel_ms": hs_avg_s * 1e3,
+            "algorithmic": algo,
             "bytes_per_unit": GATHER_BYTES_PER_EVAL, "units_per_launch": units, "bytes_per_launch": gather_bytes,
             "peak_source": f"measured in this run: L2-resident read probe ({L2_PROBE_MIB} MiB x "
                            f"{L2_PROBE_REPS} reads, best of {len(L2_PROBE_SIZES)} sizes)",

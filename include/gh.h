@@ -465,6 +465,17 @@ GH_API int gh_selftest_tcgen05_ex(gh_ctx* ctx, const float* A_host, const float*
 GH_API int gh_probe_read_bandwidth(gh_ctx* ctx, int64_t bytes, int32_t reps, double* gbs);
 
 /*
+ * gh_probe_smem_bandwidth - diagnostic (no counterpart in the paper): shared-
+ * memory load bandwidth of the GPU in GB/s (conflict-free 16-byte loads, 64
+ * warps per SM, every SM).
+ * gh_probe_issue_rate - diagnostic: warp instructions issued per second by
+ * the whole GPU for a stream of independent FP32 FMAs (the issue limit that
+ * bounds an instruction-bound kernel).
+ */
+GH_API int gh_probe_smem_bandwidth(gh_ctx* ctx, double* gbs);
+GH_API int gh_probe_issue_rate(gh_ctx* ctx, double* warp_inst_per_s);
+
+/*
  * gh_inject_fault - host-side fault injection for testing the failure paths
  * (no counterpart in the paper; nothing faults on the GPU). Arms one fault
  * of `status` on the context: the (after + 1)-th site of that kind reached

@@ -184,3 +184,101 @@ extern "C" int gh_probe_read_bandwidth(gh_ctx* ctx, int64_t bytes, int32_t reps,
     *gbs = (double)(n4 * 16) * reps / (ms * 1e-3) / 1e9;
     return GH_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Shared-memory load bandwidth and instruction issue rate probes (the limits
+// of the hopping scorer's power-row reads and of its instruction stream).
+// ---------------------------------------------------------------------------
+namespace {
+// Every warp reads its own 1 KiB of shared memory with conflict-free 16-byte
+// loads (512 contiguous bytes per instruction), `iters` times.
+__global__ void __launch_bounds__(1024) probe_smem_kernel(int iters, float* __restrict__ sink) {
+    __shared__ __align__(16) float4 buf[32 * 64];  // 32 warps x 1 KiB
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* w = buf + warp * 64;
+    for (int i = lane; i < 64; i += 32) w[i] = make_float4(i, lane, warp, 1.f);
+    __syncwarp();
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float4 v = w[(j * 8 + lane + it) & 63];  // eight distinct blocks per iteration
+            acc.x += v.x;
+            acc.y += v.y;
+            acc.z += v.z;
+            acc.w += v.w;
+        }
+    }
+    if (acc.x == 1.234567e-30f) sink[0] = acc.x + acc.y + acc.z + acc.w;
+}
+
+// Eight independent FMA chains per thread: the instruction stream never
+// waits on a result, so the SM issues at its maximum rate.
+__global__ void __launch_bounds__(1024) probe_issue_kernel(int iters, float* __restrict__ sink) {
+    float a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = threadIdx.x * 1e-3f + j;
+    const float m = 0.999f, c = 1e-4f;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = fmaf(a[j], m, c);
+    }
+    float t = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t += a[j];
+    if (t == 1.234567e-30f) sink[0] = t;
+}
+}  // namespace
+
+static int probe_time(gh_ctx* ctx, void (*launch)(gh_ctx*, int, float*), int iters, float* sink, double* ms_out) {
+    launch(ctx, 16, sink);  // warm
+    GH_CUDA(cudaGetLastError());
+    cudaEvent_t a, b;
+    GH_CUDA(cudaEventCreate(&a));
+    GH_CUDA(cudaEventCreate(&b));
+    GH_CUDA(cudaEventRecord(a, ctx->stream));
+    launch(ctx, iters, sink);
+    GH_CUDA(cudaGetLastError());
+    GH_CUDA(cudaEventRecord(b, ctx->stream));
+    GH_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    GH_CUDA(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->launches += 2;
+    *ms_out = ms;
+    return GH_OK;
+}
+
+extern "C" int gh_probe_smem_bandwidth(gh_ctx* ctx, double* gbs) {
+    if (!ctx || !gbs) return GH_EINVAL;
+    DeviceGuard g(ctx->device);
+    void* buf;
+    GH_TRY(gh_ws(ctx, WS_DIAG, 256, &buf));
+    const int iters = 4096;
+    auto launch = [](gh_ctx* c, int it, float* sink) {
+        probe_smem_kernel<<<(unsigned)c->num_sms * 2, 1024, 0, c->stream>>>(it, sink);
+    };
+    double ms;
+    GH_TRY(probe_time(ctx, launch, iters, (float*)buf, &ms));
+    const double bytes = (double)ctx->num_sms * 2 * 1024 * 16.0 * 8 * iters;
+    *gbs = bytes / (ms * 1e-3) / 1e9;
+    return GH_OK;
+}
+
+extern "C" int gh_probe_issue_rate(gh_ctx* ctx, double* warp_inst_per_s) {
+    if (!ctx || !warp_inst_per_s) return GH_EINVAL;
+    DeviceGuard g(ctx->device);
+    void* buf;
+    GH_TRY(gh_ws(ctx, WS_DIAG, 256, &buf));
+    const int iters = 16384;
+    auto launch = [](gh_ctx* c, int it, float* sink) {
+        probe_issue_kernel<<<(unsigned)c->num_sms * 2, 1024, 0, c->stream>>>(it, sink);
+    };
+    double ms;
+    GH_TRY(probe_time(ctx, launch, iters, (float*)buf, &ms));
+    // FMAs only (the loop's own instructions are a small extra, not counted)
+    const double warp_inst = (double)ctx->num_sms * 2 * (1024 / 32) * 8.0 * iters;
+    *warp_inst_per_s = warp_inst / (ms * 1e-3);
+    return GH_OK;
+}

@@ -74,6 +74,8 @@ _SIGNATURES = {
     "gh_selftest_tcgen05": (_I32, [_P, _P, _P, _P, _I32, _I32]),
     "gh_selftest_tcgen05_ex": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _I32]),
     "gh_probe_read_bandwidth": (_I32, [_P, ctypes.c_int64, _I32, _PD]),
+    "gh_probe_smem_bandwidth": (_I32, [_P, _PD]),
+    "gh_probe_issue_rate": (_I32, [_P, _PD]),
     "gh_set_timing": (_I32, [_P, _I32]),
     "gh_inject_fault": (_I32, [_P, _I32, _I32]),
     "gh_set_graphs": (_I32, [_P, _I32]),
@@ -301,6 +303,18 @@ class Context:
         self._check("gh_probe_read_bandwidth",
                     self._lib.gh_probe_read_bandwidth(self.handle, int(nbytes), int(reps), ctypes.byref(g)))
         return g.value
+
+    def gh_probe_smem_bandwidth(self):
+        """Shared-memory load bandwidth of the GPU, GB/s."""
+        v = ctypes.c_double(0.0)
+        self._check("gh_probe_smem_bandwidth", self._lib.gh_probe_smem_bandwidth(self.handle, ctypes.byref(v)))
+        return v.value
+
+    def gh_probe_issue_rate(self):
+        """Warp instructions per second the GPU issues (independent FP32 FMAs)."""
+        v = ctypes.c_double(0.0)
+        self._check("gh_probe_issue_rate", self._lib.gh_probe_issue_rate(self.handle, ctypes.byref(v)))
+        return v.value
 
     def gh_set_timing(self, enable):
         """True: time every kernel class; False: none; a kind name, an int mask
