@@ -743,9 +743,11 @@ __global__ void __launch_bounds__(kThreadsWS, 1) exact_s2_tc_kernel(const float*
 // Real form per receiver: A rows [Re ca | -Im ca] and [Im ca | Re ca] with
 // ca_m = exp(-j 2 pi r m) for a tile of 64 (x, y) cells (M = 128), B rows
 // [Re Y | Im Y] of the Mc chirps (N = Mc), K = 2 Ms in stages of 32 samples.
-// Y is split into BF16 high/low tiles once per call, already in the canonical
-// shared-memory layout, and each stage's B tiles arrive with one bulk copy
-// (TMA) that completes on an mbarrier. Split-BF16, three MMAs per K step.
+// Y is split into BF16 high/low tiles once per call, already in the 128-byte
+// swizzled K-major layout the MMAs read (one 128-byte row of 32 samples x
+// Re/Im per operand row and stage), and each stage's B tiles arrive with one
+// bulk copy (TMA) that completes on an mbarrier. Split-BF16, three MMAs per
+// K step.
 // ---------------------------------------------------------------------------
 // Splits 8 floats into BF16 high/low parts and stores one 16-byte chunk of each.
 __device__ __forceinline__ void store_chunk(unsigned char* hi, unsigned char* lo, uint32_t off, const float* v) {
@@ -758,7 +760,8 @@ __device__ __forceinline__ void store_chunk(unsigned char* hi, unsigned char* lo
     *(uint4*)(lo + off) = b;
 }
 
-// Y -> per (q, stage) B tiles [hi | lo], rows mc, K = [Re Y[mc][32s..] | Im Y[mc][32s..]].
+// Y -> per (q, stage) B tiles [hi | lo], rows mc, K = [Re Y[mc][32s..] | Im Y[mc][32s..]],
+// K-major in the 128-byte swizzled layout (one 128-byte row per chirp).
 __global__ void y_split_kernel(const float2* __restrict__ Y, int Q, int Ms, int Mc, Deflate df,
                                unsigned char* __restrict__ out) {
     const int nst = Ms / 32;
@@ -771,7 +774,7 @@ __global__ void y_split_kernel(const float2* __restrict__ Y, int Q, int Ms, int 
     t /= Mc;
     const int s = (int)(t % nst);
     const int q = (int)(t / nst);
-    const uint32_t tile = (uint32_t)Mc * 64 * 2, lbo = (uint32_t)(Mc / 8) * 128;
+    const uint32_t tile = (uint32_t)Mc * 64 * 2;
     unsigned char* hi = out + ((size_t)(q * nst + s) * 2) * tile;
     unsigned char* lo = hi + tile;
     const int m0 = 32 * s + 8 * (c & 3);
@@ -783,7 +786,7 @@ __global__ void y_split_kernel(const float2* __restrict__ Y, int Q, int Ms, int 
         if (df.n > 0) y = gh_deflate(df, Q, Ms, Mc, q, mc, m0 + i, y);
         v[i] = c < 4 ? y.x : y.y;
     }
-    const uint32_t off = gh_tc::kmajor_off((uint32_t)mc, (uint32_t)(8 * c), lbo, 128);
+    const uint32_t off = gh_tc::sw128_off((uint32_t)mc, (uint32_t)(8 * c), (uint32_t)Mc);
     store_chunk(hi, lo, off, v);
 }
 
@@ -809,15 +812,16 @@ __global__ void __launch_bounds__(256, 1) exact_s1_tc_kernel(const unsigned char
                                                              const ExEntry* __restrict__ tab, S1Params p,
                                                              float* __restrict__ Pout, int* __restrict__ status) {
     constexpr int N = NMC;
-    constexpr uint32_t SBO = 128, LBO_A = 16 * 128, LBO_B = (N / 8) * 128;
     constexpr uint32_t A_BYTES = 128 * 64 * 2, B_BYTES = N * 64 * 2;
     constexpr uint32_t BUF_BYTES = 2 * A_BYTES + 2 * B_BYTES;
     constexpr uint32_t TM_COLS = 2 * N <= 64 ? 64 : (2 * N <= 128 ? 128 : (2 * N <= 256 ? 256 : 512));
     constexpr uint32_t FLIP = 0x80008000u;
     constexpr int CH = N / 2;  // columns per epilogue warp
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ unsigned char smem_raw1[];
     __shared__ uint64_t mbar[2], tbar[2];
     __shared__ uint32_t tmem_holder;
+    // the swizzled tiles need 1024-byte aligned buffers
+    unsigned char* smem = smem_raw1 + ((1024u - (gh_tc::smem_u32(smem_raw1) & 1023u)) & 1023u);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int h = warp >> 2;        // xy half of the tile (generation)
@@ -837,8 +841,10 @@ __global__ void __launch_bounds__(256, 1) exact_s1_tc_kernel(const unsigned char
     gh_tc::fence_after_sync();
     const uint32_t tmem = tmem_holder;
     const uint32_t idesc = gh_tc::idesc_bf16_f32(128, N);
-    const uint32_t offA_re = gh_tc::kmajor_off((uint32_t)(h * 64 + lane), 0, LBO_A, SBO);
-    const uint32_t offA_im = gh_tc::kmajor_off((uint32_t)(h * 64 + 32 + lane), 0, LBO_A, SBO);
+    // A rows h*64 + lane (Re row: [Re ca | -Im ca]) and h*64 + 32 + lane (Im row:
+    // [Im ca | Re ca]), 128-byte swizzled: K chunk c of row r at 16 (c ^ (r % 8))
+    const int rre = h * 64 + lane, rim = h * 64 + 32 + lane;
+    auto offA = [](int r, int c) { return (uint32_t)r * 128u + (uint32_t)(((c ^ (r & 7)) & 7) << 4); };
 
     uint32_t gs = 0;
     int tile_ctr = 0;
@@ -882,14 +888,14 @@ __global__ void __launch_bounds__(256, 1) exact_s1_tc_kernel(const unsigned char
                     gh_tc::split_bf16x2(z[2 * i].y, z[2 * i + 1].y, &imH[i], &imL[i]);
                 }
                 // Re row: [Re ca | -Im ca]; Im row: [Im ca | Re ca]
-                st16(Ah + offA_re + kq * LBO_A, reH, 0u);
-                st16(Al + offA_re + kq * LBO_A, reL, 0u);
-                st16(Ah + offA_re + (4 + kq) * LBO_A, imH, FLIP);
-                st16(Al + offA_re + (4 + kq) * LBO_A, imL, FLIP);
-                st16(Ah + offA_im + kq * LBO_A, imH, 0u);
-                st16(Al + offA_im + kq * LBO_A, imL, 0u);
-                st16(Ah + offA_im + (4 + kq) * LBO_A, reH, 0u);
-                st16(Al + offA_im + (4 + kq) * LBO_A, reL, 0u);
+                st16(Ah + offA(rre, kq), reH, 0u);
+                st16(Al + offA(rre, kq), reL, 0u);
+                st16(Ah + offA(rre, 4 + kq), imH, FLIP);
+                st16(Al + offA(rre, 4 + kq), imL, FLIP);
+                st16(Ah + offA(rim, kq), imH, 0u);
+                st16(Al + offA(rim, kq), imL, 0u);
+                st16(Ah + offA(rim, 4 + kq), reH, 0u);
+                st16(Al + offA(rim, 4 + kq), reL, 0u);
             }
             gh_tc::fence_smem_to_async();
             const bool tok = gh_tc::mbar_wait_bounded(&tbar[buf], (gs >> 1) & 1, kTcWaitIters);
@@ -903,11 +909,11 @@ __global__ void __launch_bounds__(256, 1) exact_s1_tc_kernel(const unsigned char
                 const uint32_t ah = gh_tc::smem_u32(Ah), al = gh_tc::smem_u32(Al);
                 const uint32_t bh = gh_tc::smem_u32(Bh), bl = bh + B_BYTES;
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const uint64_t dah = gh_tc::smem_desc(ah + 2 * kk * LBO_A, LBO_A, SBO);
-                    const uint64_t dal = gh_tc::smem_desc(al + 2 * kk * LBO_A, LBO_A, SBO);
-                    const uint64_t dbh = gh_tc::smem_desc(bh + 2 * kk * LBO_B, LBO_B, SBO);
-                    const uint64_t dbl = gh_tc::smem_desc(bl + 2 * kk * LBO_B, LBO_B, SBO);
+                for (int kk = 0; kk < 4; ++kk) {  // K = 16 steps: 32 bytes along the swizzled rows
+                    const uint64_t dah = gh_tc::smem_desc_sw128(ah + 32 * kk);
+                    const uint64_t dal = gh_tc::smem_desc_sw128(al + 32 * kk);
+                    const uint64_t dbh = gh_tc::smem_desc_sw128(bh + 32 * kk);
+                    const uint64_t dbl = gh_tc::smem_desc_sw128(bl + 32 * kk);
                     gh_tc::mma_bf16(tmem + dcol, dah, dbh, idesc, (s > 0 || kk > 0) ? 1u : 0u);
                     gh_tc::mma_bf16(tmem + dcol, dah, dbl, idesc, 1u);
                     gh_tc::mma_bf16(tmem + dcol, dal, dbh, idesc, 1u);
@@ -956,7 +962,7 @@ template <int NMC>
 int launch_s1_tc(gh_ctx* ctx, const Dims& d, const float2* Y, const Deflate& df, const ExEntry* tab, float* P,
                  int* status) {
     constexpr uint32_t B_BYTES = NMC * 64 * 2;
-    const size_t smem = (size_t)2 * (2 * 128 * 64 * 2 + 2 * B_BYTES);
+    const size_t smem = (size_t)2 * (2 * 128 * 64 * 2 + 2 * B_BYTES) + 1024;  // + alignment
     if (smem > ctx->smem_optin) return gh_fail(ctx, GH_ENOTSUP, "stage-1 tensor-core path needs %zu B", smem);
     const int nst = d.Ms / 32;
     void* bt;
