@@ -52,7 +52,7 @@ L2_PROBE_REPS = 200
 # One hop_score_kernel launch on this workload, from an ncu capture (summarised
 # under profiles/), valid while the scorer's sources hash to the key: DRAM
 # bytes (read + write), warp instructions issued, and L2-to-SM read bytes.
-HOP_NCU = {}
+HOP_NCU = {"d7ef01bb7e2bda81": {"dram": 10251264, "inst": 49200001, "l2_to_sm": 448023072}}
 
 
 def _hop_source_hash():
