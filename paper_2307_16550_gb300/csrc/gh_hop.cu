@@ -96,7 +96,7 @@ __device__ __forceinline__ void coord_entry_at(const GeoParams& g, const CoordPa
     const double emax = eta00 + fmax(0.0, ex) + fmax(0.0, ey);
     const long long j_lo = (long long)floor(emin + 0.5) - 1;
     const long long j_hi = (long long)floor(emax + 0.5) + 1;
-    const long long j_ref = j_lo & ~1LL;  // even, <= j_lo
+    const long long j_ref = j_lo & ~3LL;  // a multiple of 4 (16-bit maps build groups of four bins), <= j_lo
     const long long nu = j_hi - j_ref + 1;
     const bool wrap = nu > g.Nd;
     const double two32 = 4294967296.0;
@@ -106,7 +106,7 @@ __device__ __forceinline__ void coord_entry_at(const GeoParams& g, const CoordPa
     e.wx = wx;
     e.wy = wy;
     e.j_ref = (int)j_ref;
-    e.npair = wrap ? g.Nd / 2 : (int)((nu + 1) >> 1);
+    e.npair = wrap ? g.Nd / 2 : (int)((nu + 1) >> 1);  // at most Nd / 2 (nu <= Nd)
     e.wrap = wrap ? 1 : 0;
     table[idx] = e;
     if (rw) {  // float64 (r, wx, wy) of the entry, for the BOMP atoms
@@ -237,6 +237,16 @@ __device__ __forceinline__ float4 load_pair(const void* row, int jh) {
     }
 }
 
+// One bin (re, im) of a 16-bit map as float32.
+template <int MT>
+__device__ __forceinline__ float2 unpack_bin(uint32_t w) {
+    if constexpr (MT == GH_C16) {
+        return __half22float2(*reinterpret_cast<const __half2*>(&w));
+    } else {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+    }
+}
+
 // Scores every velocity cell of the (x, y) cell `xy` with one warp: builds the
 // Doppler power rows P_q of the receivers in the warp's shared memory, then
 // each lane sums the rows at its cells' Doppler bins; merges the best unmasked
@@ -267,27 +277,67 @@ __device__ __forceinline__ void score_xy(const void* __restrict__ maps, const Ho
         const char* r2 = (const char*)maps + (qb + eq.row[2]) * p.Nd * BB;
         float* Pq = P + (size_t)q * p.Nd;
         constexpr int U = GH_HOP_U;  // row loads in flight per lane
-        for (int pp0 = 0; pp0 < npair; pp0 += 32 * U) {
-            float4 z0[U], z1[U], z2[U];
+        if constexpr (MT == GH_C64) {
+            // pairs of bins: one 16-byte load per row and pair
+            for (int pp0 = 0; pp0 < npair; pp0 += 32 * U) {
+                float4 z0[U], z1[U], z2[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int pp = pp0 + lane + 32 * u;
-                if (pp < npair) {
-                    const int jh = ((j_ref + 2 * pp) & ndm) >> 1;  // pair of absolute bins
-                    z0[u] = load_pair<MT>(r0, jh);
-                    z1[u] = load_pair<MT>(r1, jh);
-                    z2[u] = load_pair<MT>(r2, jh);
+                for (int u = 0; u < U; ++u) {
+                    const int pp = pp0 + lane + 32 * u;
+                    if (pp < npair) {
+                        const int jh = ((j_ref + 2 * pp) & ndm) >> 1;  // pair of absolute bins
+                        z0[u] = load_pair<MT>(r0, jh);
+                        z1[u] = load_pair<MT>(r1, jh);
+                        z2[u] = load_pair<MT>(r2, jh);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int pp = pp0 + lane + 32 * u;
+                    if (pp < npair) {
+                        const float re0 = c0 * z0[u].x + c1 * z1[u].x + c2 * z2[u].x;
+                        const float im0 = c0 * z0[u].y + c1 * z1[u].y + c2 * z2[u].y;
+                        const float re1 = c0 * z0[u].z + c1 * z1[u].z + c2 * z2[u].z;
+                        const float im1 = c0 * z0[u].w + c1 * z1[u].w + c2 * z2[u].w;
+                        *(float2*)(Pq + 2 * pp) = make_float2(re0 * re0 + im0 * im0, re1 * re1 + im1 * im1);
+                    }
                 }
             }
+        } else {
+            // 16-bit maps: groups of four bins (j_ref is a multiple of 4), one
+            // 16-byte load per row and group, lanes on consecutive groups; the
+            // same registers in flight cover twice the bins of the pair loop
+            const int nquad = (npair + 1) >> 1;
+            for (int g0 = 0; g0 < nquad; g0 += 32 * U) {
+                uint4 z0[U], z1[U], z2[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int pp = pp0 + lane + 32 * u;
-                if (pp < npair) {
-                    const float re0 = c0 * z0[u].x + c1 * z1[u].x + c2 * z2[u].x;
-                    const float im0 = c0 * z0[u].y + c1 * z1[u].y + c2 * z2[u].y;
-                    const float re1 = c0 * z0[u].z + c1 * z1[u].z + c2 * z2[u].z;
-                    const float im1 = c0 * z0[u].w + c1 * z1[u].w + c2 * z2[u].w;
-                    *(float2*)(Pq + 2 * pp) = make_float2(re0 * re0 + im0 * im0, re1 * re1 + im1 * im1);
+                for (int u = 0; u < U; ++u) {
+                    const int g = g0 + lane + 32 * u;
+                    if (g < nquad) {
+                        const int jq = ((j_ref + 4 * g) & ndm) >> 2;  // group of four absolute bins
+                        z0[u] = __ldg((const uint4*)r0 + jq);
+                        z1[u] = __ldg((const uint4*)r1 + jq);
+                        z2[u] = __ldg((const uint4*)r2 + jq);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int g = g0 + lane + 32 * u;
+                    if (g < nquad) {
+                        const uint32_t* w0 = &z0[u].x;
+                        const uint32_t* w1 = &z1[u].x;
+                        const uint32_t* w2 = &z2[u].x;
+                        float pw[4];
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const float2 a0 = unpack_bin<MT>(w0[b]), a1 = unpack_bin<MT>(w1[b]),
+                                         a2 = unpack_bin<MT>(w2[b]);
+                            const float re = c0 * a0.x + c1 * a1.x + c2 * a2.x;
+                            const float im = c0 * a0.y + c1 * a1.y + c2 * a2.y;
+                            pw[b] = re * re + im * im;
+                        }
+                        *(float4*)(Pq + 4 * g) = make_float4(pw[0], pw[1], pw[2], pw[3]);
+                    }
                 }
             }
         }

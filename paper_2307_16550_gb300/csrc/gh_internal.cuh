@@ -172,7 +172,7 @@ struct __align__(16) HopEntry {
     double wx, wy;   // bistatic gradient (float64 bin decisions)
     int row[3];      // map rows (i + k) mod Nr, k = -1, 0, 1
     float cs[3];     // polar coefficients times the wrap sign
-    int j_ref;       // even Doppler bin of power-row entry 0 (entry u is bin (j_ref + u) mod Nd)
+    int j_ref;       // Doppler bin of power-row entry 0, a multiple of 4 (entry u is bin (j_ref + u) mod Nd)
     int npair;       // power-row entries to build, in pairs
     int wrap;        // 1 if the velocity grid reaches more than Nd - 1 bins (entries wrap mod Nd)
 };
