@@ -568,6 +568,7 @@ def batch_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args):
         batched()
     ms_batch = timed(batched, args.steps)
     tuning = ctx.gh_batch_tuning()
+    tile = ctx.gh_batch_tile()
 
     def one_by_one():
         for (radar, tx, rx, Q, Y, grid, K) in dev:
@@ -582,7 +583,8 @@ def batch_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args):
                         "160^2x40^2, 1..5 targets at SNR 0..20 dB, K = targets",
             "value": units / (ms_batch * 1e-3), "unit": UNIT, "ms_per_step": ms_batch,
             "evals_per_step": units, "maps_gb": maps_gb,
-            "tuning": {"cells_per_lane": tuning[0], "warps_per_cta": tuning[1]},
+            "tuning": {"cells_per_lane": tuning[0], "warps_per_cta": tuning[1], "xy_cells_per_item": tile,
+                       "of": "the scorer group with the most work"},
             "one_by_one": {"value": units / (ms_seq * 1e-3), "ms_per_step": ms_seq,
                            "how": "256 gh_detect calls (each a replayed graph)"}}
 

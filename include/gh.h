@@ -276,9 +276,10 @@ typedef struct {
  *   cells_host  : host int64[sum K]
  *   scores_host : host float[sum K] (may be NULL)
  *   alpha_host  : host double[sum K*Q][2] (may be NULL), per frame [K][Q][2]
- * Each scorer group's cells per lane and warps per CTA are chosen by timing
- * the candidates on the first iteration of a batch shape (cached in the
- * context), unless fixed with gh_set_batch_tuning. From the second call with an
+ * Each scorer group's cells per lane, warps per CTA and (x, y) cells per work
+ * item are chosen by timing the candidates on the first iteration of a batch
+ * shape (cached in the context), unless fixed with gh_set_batch_tuning and
+ * gh_set_batch_tile. From the second call with an
  * unchanged batch on, the whole sequence is a replayed CUDA graph.
  */
 GH_API int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* frames, int64_t* cells_host,
@@ -289,6 +290,16 @@ GH_API int gh_set_batch_tuning(gh_ctx* ctx, int32_t cells_per_lane, int32_t warp
 /* The configuration the last gh_detect_batch call used for its scorer group
  * with the most work. */
 GH_API int gh_batch_tuning(gh_ctx* ctx, int32_t* cells_per_lane, int32_t* warps);
+/* Fixes the number of consecutive (x, y) cells in one work item of the
+ * batched scorer: 4, 8, 16 or 32; 0 returns to tuning (the default: after the
+ * cells per lane and warps, the autotuner times the four item sizes; a
+ * configuration fixed with gh_set_batch_tuning uses 8 unless an item size is
+ * fixed here). Larger items keep a warp on neighbouring cells (map rows
+ * shared in L1), smaller ones balance the last items of a launch. */
+GH_API int gh_set_batch_tile(gh_ctx* ctx, int32_t cells_per_item);
+/* The item size the last gh_detect_batch call used for its scorer group with
+ * the most work (0 before the first call). */
+GH_API int gh_batch_tile(gh_ctx* ctx, int32_t* cells_per_item);
 
 /*
  * gh_factorized - the paper's factorised single-target estimators: location

@@ -33,7 +33,10 @@
 
 namespace {
 
-constexpr int kBatchXyPerItem = 8;      // (x, y) cells per scorer work item
+// (x, y) cells per scorer work item: the tile sizes the autotuner tries
+constexpr int kTiles[] = {4, 8, 16, 32};
+constexpr int kNumTiles = 4;
+constexpr int kDefaultTile = 1;  // 8 cells
 constexpr int kBatchMaxFrames = 65536;
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -54,8 +57,11 @@ struct Plan {
     struct ScoreClass {
         int bound = 0, max_q = 0;
         double work = 0.0;                    // cell * receiver * iteration evals
-        std::vector<BatchItem*> items;        // per k
-        std::vector<int> n;                   // per k
+        // per tile size: the class's items, frames in decreasing K (so the
+        // items of the frames still iterating at k are a prefix), and per k
+        // that prefix's length
+        BatchItem* items[kNumTiles] = {};
+        std::vector<int> n[kNumTiles];
     };
     std::vector<ScoreClass> classes;
     std::vector<int*> active;                // per k
@@ -73,7 +79,7 @@ struct Plan {
 };
 
 struct Tuning {
-    int ac = 0, warps = 0;
+    int ac = 0, warps = 0, tile = kDefaultTile;  // tile: index into kTiles
 };
 
 int class_bound(int q_nd) {
@@ -87,6 +93,7 @@ struct BatchState {
     Plan plan;
     bool plan_valid = false;
     int force_ac = 0, force_warps = 0;
+    int force_tile = -1;  // index into kTiles, -1: tuned
     Tuning last;                                         // of the class with the most work
     std::map<std::vector<unsigned char>, Tuning> tuned;  // per batch shape and class
 };
@@ -221,8 +228,7 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
         c.bound = kv.first;
         P.classes.push_back(c);
     }
-    std::vector<std::vector<std::vector<BatchItem>>> score(P.classes.size(),
-                                                          std::vector<std::vector<BatchItem>>(P.Kmax));
+    std::vector<std::vector<int>> class_frames(P.classes.size());
     std::vector<std::vector<int>> active(P.Kmax);
     std::vector<std::vector<BatchItem>> defl(P.Kmax);
     for (int f = 0; f < nframes; ++f) {
@@ -248,10 +254,25 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
         for (int k = 1; k < P.K[f]; ++k)
             for (int q = 0; q < d.Q; ++q)
                 for (int i0 = 0; i0 < d.Nr; i0 += IB) defl[k].push_back({f, q, i0, IB});
-        for (int k = 0; k < P.K[f]; ++k) {
-            active[k].push_back(f);
-            for (long long s = 0; s < d.nxy; s += kBatchXyPerItem)
-                score[cls][k].push_back({f, 0, s, std::min((long long)kBatchXyPerItem, d.nxy - s)});
+        for (int k = 0; k < P.K[f]; ++k) active[k].push_back(f);
+        class_frames[cls].push_back(f);
+    }
+    // scorer items per class and tile size: frames in decreasing K (ties in
+    // frame order), runs of `tile` consecutive (x, y) cells; n[t][k] = items
+    // of the frames with K > k (a prefix)
+    std::vector<std::vector<std::vector<BatchItem>>> score(P.classes.size(),
+                                                          std::vector<std::vector<BatchItem>>(kNumTiles));
+    for (size_t c = 0; c < P.classes.size(); ++c) {
+        std::vector<int>& cf = class_frames[c];
+        std::stable_sort(cf.begin(), cf.end(), [&](int a, int b) { return P.K[a] > P.K[b]; });
+        for (int t = 0; t < kNumTiles; ++t) {
+            const long long T = kTiles[t];
+            P.classes[c].n[t].assign(P.Kmax, 0);
+            for (int f : cf) {
+                for (long long s = 0; s < dims[f].nxy; s += T)
+                    score[c][t].push_back({f, 0, s, std::min(T, dims[f].nxy - s)});
+                for (int k = 0; k < P.K[f]; ++k) P.classes[c].n[t][k] = (int)score[c][t].size();
+            }
         }
     }
     // packed results: per frame ArgResult[K] then double2[K][Q]
@@ -271,10 +292,11 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
     const size_t m_coord = take(coord.size() * sizeof(BatchItem));
     const size_t m_range = take(range.size() * sizeof(BatchItem));
     const size_t m_dop = take(dop.size() * sizeof(BatchItem));
-    std::vector<std::vector<size_t>> m_score(P.classes.size(), std::vector<size_t>(P.Kmax));
+    std::vector<std::vector<size_t>> m_score(P.classes.size(), std::vector<size_t>(kNumTiles));
+    for (size_t c = 0; c < P.classes.size(); ++c)
+        for (int t = 0; t < kNumTiles; ++t) m_score[c][t] = take(score[c][t].size() * sizeof(BatchItem));
     std::vector<size_t> m_active(P.Kmax), m_defl(P.Kmax);
     for (int k = 0; k < P.Kmax; ++k) {
-        for (size_t c = 0; c < P.classes.size(); ++c) m_score[c][k] = take(score[c][k].size() * sizeof(BatchItem));
         m_active[k] = take(active[k].size() * sizeof(int));
         m_defl[k] = take(defl[k].size() * sizeof(BatchItem));
     }
@@ -320,11 +342,12 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
     put(m_range, range.data(), range.size() * sizeof(BatchItem));
     put(m_dop, dop.data(), dop.size() * sizeof(BatchItem));
     for (int k = 0; k < P.Kmax; ++k) {
-        for (size_t c = 0; c < P.classes.size(); ++c)
-            put(m_score[c][k], score[c][k].data(), score[c][k].size() * sizeof(BatchItem));
         put(m_active[k], active[k].data(), active[k].size() * sizeof(int));
         put(m_defl[k], defl[k].data(), defl[k].size() * sizeof(BatchItem));
     }
+    for (size_t c = 0; c < P.classes.size(); ++c)
+        for (int t = 0; t < kNumTiles; ++t)
+            put(m_score[c][t], score[c][t].data(), score[c][t].size() * sizeof(BatchItem));
     put(m_tw, tw.data(), ntw * sizeof(float2));
     put(m_outoff, P.out_off.data(), nframes * sizeof(long long));
     GH_CUDA(cudaMemcpyAsync(meta, host.data(), m, cudaMemcpyHostToDevice, ctx->stream));
@@ -338,15 +361,13 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
     P.n_range = (int)range.size();
     P.n_dop = (int)dop.size();
     for (int k = 0; k < P.Kmax; ++k) {
-        for (size_t c = 0; c < P.classes.size(); ++c) {
-            P.classes[c].items.push_back((BatchItem*)(M + m_score[c][k]));
-            P.classes[c].n.push_back((int)score[c][k].size());
-        }
         P.active.push_back((int*)(M + m_active[k]));
         P.n_active.push_back((int)active[k].size());
         P.defl_items.push_back((BatchItem*)(M + m_defl[k]));
         P.n_defl.push_back((int)defl[k].size());
     }
+    for (size_t c = 0; c < P.classes.size(); ++c)
+        for (int t = 0; t < kNumTiles; ++t) P.classes[c].items[t] = (BatchItem*)(M + m_score[c][t]);
     P.out_off_dev = (long long*)(M + m_outoff);
     P.out_dev = M + m_out;
     return GH_OK;
@@ -369,7 +390,8 @@ int batch_sequence(gh_ctx* ctx, const Plan& P, const std::vector<Tuning>& t, voi
             GH_TRY(gh_launch_maps_deflate_batch(ctx, P.frames, P.defl_items[k], P.n_defl[k], k));
         for (size_t c = 0; c < P.classes.size(); ++c) {
             const Plan::ScoreClass& C = P.classes[c];
-            GH_TRY(gh_launch_hop_batch(ctx, P.frames, C.items[k], C.n[k], P.counter, k, t[c].ac, t[c].warps,
+            GH_TRY(gh_launch_hop_batch(ctx, P.frames, C.items[t[c].tile], C.n[t[c].tile][k], P.counter, k,
+                                       t[c].ac, t[c].warps,
                                        C.bound, C.max_q));
         }
         GH_TRY(gh_launch_bomp_select_batch(ctx, P.frames, P.active[k], P.n_active[k], k));
@@ -391,39 +413,49 @@ int autotune_prepare(gh_ctx* ctx, const Plan& P) {
                                 P.n_dop, P.thr_dop, P.smem_dop, 0);
 }
 
-// Times every scorer configuration that fits in shared memory on the first
-// iteration of one class and returns the fastest.
-int autotune(gh_ctx* ctx, const Plan& P, const Plan::ScoreClass& C, Tuning* best) {
+// Times the scorer on the first iteration of one class and returns the
+// fastest configuration: cells per lane (8, 16, 32) x warps per CTA (8, 4, 2,
+// as shared memory allows) with 8-cell items, then, for that configuration,
+// items of 4, 8, 16 and 32 (x, y) cells (`tile` >= 0 fixes the item size).
+int autotune(gh_ctx* ctx, const Plan& P, const Plan::ScoreClass& C, int tile, Tuning* best) {
     cudaEvent_t a, b;
     GH_CUDA(cudaEventCreate(&a));
     GH_CUDA(cudaEventCreate(&b));
     float best_ms = 1e30f;
     *best = Tuning();
     int st = GH_OK;
-    for (int ac : {8, 16, 32})
-        for (int warps : {8, 4, 2}) {
-            if (gh_hop_batch_warp_bytes(ac, C.bound, C.max_q) * warps > ctx->smem_optin) continue;
-            for (int rep = 0; rep < 2 && st == GH_OK; ++rep) {  // first launch warms up
-                cudaEventRecord(a, ctx->stream);
-                st = gh_launch_hop_batch(ctx, P.frames, C.items[0], C.n[0], P.counter, 0, ac, warps, C.bound,
-                                         C.max_q);
-                cudaEventRecord(b, ctx->stream);
-            }
-            if (st != GH_OK) break;
-            float ms = 0.f;
-            if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
-                st = gh_fail(ctx, GH_ECUDA, "autotune timing failed");
-                break;
-            }
-            if (ms < best_ms) {
-                best_ms = ms;
-                best->ac = ac;
-                best->warps = warps;
-            }
+    auto time_one = [&](const Tuning& c) {
+        for (int rep = 0; rep < 2 && st == GH_OK; ++rep) {  // first launch warms up
+            cudaEventRecord(a, ctx->stream);
+            st = gh_launch_hop_batch(ctx, P.frames, C.items[c.tile], C.n[c.tile][0], P.counter, 0, c.ac, c.warps,
+                                     C.bound, C.max_q);
+            cudaEventRecord(b, ctx->stream);
         }
+        if (st != GH_OK) return;
+        float ms = 0.f;
+        if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+            st = gh_fail(ctx, GH_ECUDA, "autotune timing failed");
+            return;
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            *best = c;
+        }
+    };
+    const int t0 = tile >= 0 ? tile : kDefaultTile;
+    for (int ac : {8, 16, 32})
+        for (int warps : {8, 4, 2})
+            if (st == GH_OK && gh_hop_batch_warp_bytes(ac, C.bound, C.max_q) * warps <= ctx->smem_optin)
+                time_one({ac, warps, t0});
+    if (st == GH_OK && best->ac == 0)
+        st = gh_fail(ctx, GH_ENOTSUP, "batched scorer: frames too large for shared memory");
+    if (tile < 0) {
+        const Tuning cfg = *best;
+        for (int t = 0; t < kNumTiles && st == GH_OK; ++t)
+            if (t != t0) time_one({cfg.ac, cfg.warps, t});
+    }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    if (st == GH_OK && best->ac == 0) st = gh_fail(ctx, GH_ENOTSUP, "batched scorer: frames too large for shared memory");
     return st;
 }
 
@@ -463,10 +495,12 @@ extern "C" int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* fra
         if (S->force_ac) {
             t[c].ac = S->force_ac;
             t[c].warps = S->force_warps;
+            t[c].tile = S->force_tile >= 0 ? S->force_tile : kDefaultTile;
             continue;
         }
         std::vector<unsigned char> tkey = P.shape;
         append(tkey, P.classes[c].bound);
+        append(tkey, S->force_tile);
         auto it = S->tuned.find(tkey);
         if (it != S->tuned.end()) {
             t[c] = it->second;
@@ -476,7 +510,7 @@ extern "C" int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* fra
             GH_TRY(autotune_prepare(ctx, P));
             prepared = true;
         }
-        GH_TRY(autotune(ctx, P, P.classes[c], &t[c]));
+        GH_TRY(autotune(ctx, P, P.classes[c], S->force_tile, &t[c]));
         S->tuned[tkey] = t[c];
     }
     S->last = t[heaviest];
@@ -485,6 +519,7 @@ extern "C" int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* fra
     for (const Tuning& tc : t) {
         append(gkey, tc.ac);
         append(gkey, tc.warps);
+        append(gkey, tc.tile);
     }
     append(gkey, ctx->timing);
     const char tag[] = "batch";
@@ -531,6 +566,23 @@ extern "C" int gh_batch_tuning(gh_ctx* ctx, int32_t* cells_per_lane, int32_t* wa
     const BatchState* S = state_of(ctx);
     *cells_per_lane = S->last.ac;
     *warps = S->last.warps;
+    return GH_OK;
+}
+
+extern "C" int gh_set_batch_tile(gh_ctx* ctx, int32_t cells_per_item) {
+    if (!ctx) return GH_EINVAL;
+    int idx = -1;
+    for (int t = 0; t < kNumTiles; ++t)
+        if (kTiles[t] == cells_per_item) idx = t;
+    if (cells_per_item != 0 && idx < 0)
+        return gh_fail(ctx, GH_EINVAL, "cells per item %d: 0 (tuned) or one of 4, 8, 16, 32", cells_per_item);
+    state_of(ctx)->force_tile = idx;
+    return GH_OK;
+}
+
+extern "C" int gh_batch_tile(gh_ctx* ctx, int32_t* cells_per_item) {
+    if (!ctx || !cells_per_item) return GH_EINVAL;
+    *cells_per_item = state_of(ctx)->last.ac ? kTiles[state_of(ctx)->last.tile] : 0;
     return GH_OK;
 }
 

@@ -85,6 +85,8 @@ _SIGNATURES = {
                              _P]),
     "gh_set_batch_tuning": (_I32, [_P, _I32, _I32]),
     "gh_batch_tuning": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "gh_set_batch_tile": (_I32, [_P, _I32]),
+    "gh_batch_tile": (_I32, [_P, ctypes.POINTER(_I32)]),
     "gh_score_points": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, _I32, _P, ctypes.c_int64, _P]),
     "gh_score_points_adjoint": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, _I32, _P, ctypes.c_int64,
                                        _P, _P, _P, _P]),
@@ -404,6 +406,14 @@ class Context:
         a, w = _I32(0), _I32(0)
         self._check("gh_batch_tuning", self._lib.gh_batch_tuning(self.handle, ctypes.byref(a), ctypes.byref(w)))
         return a.value, w.value
+
+    def gh_set_batch_tile(self, cells_per_item=0):
+        self._check("gh_set_batch_tile", self._lib.gh_set_batch_tile(self.handle, int(cells_per_item)))
+
+    def gh_batch_tile(self):
+        t = _I32(0)
+        self._check("gh_batch_tile", self._lib.gh_batch_tile(self.handle, ctypes.byref(t)))
+        return t.value
 
     def gh_set_detect_maps(self, map_dtype):
         """Storage type of the maps gh_detect makes for GH_HOP (GH_C64, GH_C16, GH_CBF16)."""

@@ -69,6 +69,22 @@ def test_batch_equals_single_frame_detect(ctx, torch_cuda, tuning):
         _same(r, _single(ctx, f))
 
 
+@pytest.mark.parametrize("tile", [4, 16, 32])
+def test_item_sizes_give_single_frame_results(ctx, torch_cuda, tile):
+    """Work items of 4, 16 and 32 (x, y) cells (the tuned default is tried
+    among them): the same results as gh_detect, bit for bit."""
+    frames = scenes.batch_scenes(5, 8, small=True) + [scenes.tiny_scene(2)]
+    dev, _ = _device_frames(torch_cuda, frames)
+    ctx.gh_set_batch_tile(tile)
+    try:
+        res = ctx.gh_detect_batch(dev)
+        assert ctx.gh_batch_tile() == tile
+    finally:
+        ctx.gh_set_batch_tile(0)
+    for f, r in zip(dev, res):
+        _same(r, _single(ctx, f))
+
+
 def test_batch_graph_replay_follows_data(ctx, torch_cuda):
     frames = scenes.batch_scenes(4, 5, small=True)
     dev, _ = _device_frames(torch_cuda, frames)
@@ -97,6 +113,9 @@ def test_batch_rejects_bad_frames(ctx, torch_cuda):
         ctx.gh_detect_batch([(sc.radar, sc.tx, sc.rx, sc.Q, to_dev(torch_cuda, Y32), sc.grid, 0)])
     with pytest.raises(gh.GhError):
         ctx.gh_set_batch_tuning(12, 4)
+    with pytest.raises(gh.GhError) as e:
+        ctx.gh_set_batch_tile(12)
+    assert e.value.status == gh.GH_EINVAL
 
 
 def test_uneven_256_frame_workload_sampled(ctx, torch_cuda):
