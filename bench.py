@@ -569,6 +569,7 @@ def batch_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args):
     ms_batch = timed(batched, args.steps)
     tuning = ctx.gh_batch_tuning()
     tile = ctx.gh_batch_tile()
+    row_mode = ctx.gh_batch_row_mode()
 
     def one_by_one():
         for (radar, tx, rx, Q, Y, grid, K) in dev:
@@ -584,6 +585,7 @@ def batch_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args):
             "value": units / (ms_batch * 1e-3), "unit": UNIT, "ms_per_step": ms_batch,
             "evals_per_step": units, "maps_gb": maps_gb,
             "tuning": {"cells_per_lane": tuning[0], "warps_per_cta": tuning[1], "xy_cells_per_item": tile,
+                       "power_rows": "one receiver at a time" if row_mode else "all receivers",
                        "of": "the scorer group with the most work"},
             "one_by_one": {"value": units / (ms_seq * 1e-3), "ms_per_step": ms_seq,
                            "how": "256 gh_detect calls (each a replayed graph)"}}

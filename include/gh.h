@@ -300,6 +300,13 @@ GH_API int gh_set_batch_tile(gh_ctx* ctx, int32_t cells_per_item);
 /* The item size the last gh_detect_batch call used for its scorer group with
  * the most work (0 before the first call). */
 GH_API int gh_batch_tile(gh_ctx* ctx, int32_t* cells_per_item);
+/* Whether the last gh_detect_batch call's scorer group with the most work
+ * built one receiver's Doppler power row at a time (1) or the rows of all its
+ * receivers at once (0). One row at a time needs a warp's velocity cells per
+ * lane to fit one run (nvy <= 32), and leaves room for more warps per SM when
+ * Q * Nd is large; the autotuner times both where both apply (a
+ * configuration fixed with gh_set_batch_tuning builds all rows at once). */
+GH_API int gh_batch_row_mode(gh_ctx* ctx, int32_t* per_receiver);
 
 /*
  * gh_factorized - the paper's factorised single-target estimators: location

@@ -55,7 +55,11 @@ struct Plan {
     // rounded up to a power of two, at least 1024 floats): one scorer launch
     // per class and iteration, each sized and tuned for its class
     struct ScoreClass {
-        int bound = 0, max_q = 0;
+        int bound = 0, max_q = 0, max_nd = 0;
+        // cells per lane of the frame with the most (one run per lane), or a
+        // large value when a frame has nvy > 32: the per-receiver scorer
+        // needs ac >= pr_need
+        int pr_need = 0;
         double work = 0.0;                    // cell * receiver * iteration evals
         // per tile size: the class's items, frames in decreasing K (so the
         // items of the frames still iterating at k are a prefix), and per k
@@ -80,6 +84,7 @@ struct Plan {
 
 struct Tuning {
     int ac = 0, warps = 0, tile = kDefaultTile;  // tile: index into kTiles
+    bool per_rx = false;                         // one receiver's power row at a time
 };
 
 int class_bound(int q_nd) {
@@ -217,15 +222,19 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
 
     // work items
     std::vector<BatchItem> coord, range, dop;
-    std::map<int, int> class_of_bound;
-    for (int f = 0; f < nframes; ++f) {
-        const int b = class_bound(dims[f].Q * dims[f].Nd);
-        if (!class_of_bound.count(b)) class_of_bound[b] = 0;
-    }
-    for (auto& kv : class_of_bound) {
+    // classes: (shared-memory bound, whether every lane's cells form one run,
+    // which the per-receiver scorer needs)
+    auto class_key = [&](const Dims& d) {
+        const int NB = d.nvy < 32 ? d.nvy : 32, SA = 32 / NB;
+        const bool one_run = d.nvy <= 32 && (d.nvx + SA - 1) / SA <= 32;
+        return std::make_pair(class_bound(d.Q * d.Nd), one_run ? 1 : 0);
+    };
+    std::map<std::pair<int, int>, int> class_of_key;
+    for (int f = 0; f < nframes; ++f) class_of_key[class_key(dims[f])] = 0;
+    for (auto& kv : class_of_key) {
         kv.second = (int)P.classes.size();
         Plan::ScoreClass c;
-        c.bound = kv.first;
+        c.bound = kv.first.first;
         P.classes.push_back(c);
     }
     std::vector<std::vector<int>> class_frames(P.classes.size());
@@ -248,8 +257,14 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
             for (int i0 = 0; i0 < d.Nr; i0 += IB) dop.push_back({f, q, i0, IB});
         P.smem_dop = std::max(P.smem_dop, gh_fft_smem_dop(IB, d.Nd));
         P.thr_dop = std::max(P.thr_dop, gh_fft_threads(IB * d.Nd));
-        const int cls = class_of_bound[class_bound(d.Q * d.Nd)];
+        const int cls = class_of_key[class_key(d)];
         P.classes[cls].max_q = std::max(P.classes[cls].max_q, d.Q);
+        P.classes[cls].max_nd = std::max(P.classes[cls].max_nd, d.Nd);
+        {
+            const int NB = d.nvy < 32 ? d.nvy : 32, SA = 32 / NB;
+            const int cells = d.nvy <= 32 ? (d.nvx + SA - 1) / SA : (1 << 20);
+            P.classes[cls].pr_need = std::max(P.classes[cls].pr_need, cells);
+        }
         P.classes[cls].work += (double)d.ncells * d.Q * P.K[f];
         for (int k = 1; k < P.K[f]; ++k)
             for (int q = 0; q < d.Q; ++q)
@@ -391,8 +406,7 @@ int batch_sequence(gh_ctx* ctx, const Plan& P, const std::vector<Tuning>& t, voi
         for (size_t c = 0; c < P.classes.size(); ++c) {
             const Plan::ScoreClass& C = P.classes[c];
             GH_TRY(gh_launch_hop_batch(ctx, P.frames, C.items[t[c].tile], C.n[t[c].tile][k], P.counter, k,
-                                       t[c].ac, t[c].warps,
-                                       C.bound, C.max_q));
+                                       t[c].ac, t[c].warps, t[c].per_rx, C.max_nd, C.bound, C.max_q));
         }
         GH_TRY(gh_launch_bomp_select_batch(ctx, P.frames, P.active[k], P.n_active[k], k));
         GH_TRY(gh_launch_bomp_corr_batch(ctx, P.frames, P.active[k], P.n_active[k], k, P.max_chunks, P.max_q));
@@ -415,8 +429,10 @@ int autotune_prepare(gh_ctx* ctx, const Plan& P) {
 
 // Times the scorer on the first iteration of one class and returns the
 // fastest configuration: cells per lane (8, 16, 32) x warps per CTA (8, 4, 2,
-// as shared memory allows) with 8-cell items, then, for that configuration,
-// items of 4, 8, 16 and 32 (x, y) cells (`tile` >= 0 fixes the item size).
+// as shared memory allows) x power rows of all receivers or of one receiver
+// at a time (where every frame's cells of a lane form one run), with 8-cell
+// items, then, for that configuration, items of 4, 8, 16 and 32 (x, y) cells
+// (`tile` >= 0 fixes the item size).
 int autotune(gh_ctx* ctx, const Plan& P, const Plan::ScoreClass& C, int tile, Tuning* best) {
     cudaEvent_t a, b;
     GH_CUDA(cudaEventCreate(&a));
@@ -428,7 +444,7 @@ int autotune(gh_ctx* ctx, const Plan& P, const Plan::ScoreClass& C, int tile, Tu
         for (int rep = 0; rep < 2 && st == GH_OK; ++rep) {  // first launch warms up
             cudaEventRecord(a, ctx->stream);
             st = gh_launch_hop_batch(ctx, P.frames, C.items[c.tile], C.n[c.tile][0], P.counter, 0, c.ac, c.warps,
-                                     C.bound, C.max_q);
+                                     c.per_rx, C.max_nd, C.bound, C.max_q);
             cudaEventRecord(b, ctx->stream);
         }
         if (st != GH_OK) return;
@@ -444,15 +460,19 @@ int autotune(gh_ctx* ctx, const Plan& P, const Plan::ScoreClass& C, int tile, Tu
     };
     const int t0 = tile >= 0 ? tile : kDefaultTile;
     for (int ac : {8, 16, 32})
-        for (int warps : {8, 4, 2})
+        for (int warps : {8, 4, 2}) {
             if (st == GH_OK && gh_hop_batch_warp_bytes(ac, C.bound, C.max_q) * warps <= ctx->smem_optin)
-                time_one({ac, warps, t0});
+                time_one({ac, warps, t0, false});
+            if (st == GH_OK && ac >= C.pr_need &&
+                gh_hop_batch_warp_bytes(ac, C.max_nd, C.max_q) * warps <= ctx->smem_optin)
+                time_one({ac, warps, t0, true});
+        }
     if (st == GH_OK && best->ac == 0)
         st = gh_fail(ctx, GH_ENOTSUP, "batched scorer: frames too large for shared memory");
     if (tile < 0) {
         const Tuning cfg = *best;
         for (int t = 0; t < kNumTiles && st == GH_OK; ++t)
-            if (t != t0) time_one({cfg.ac, cfg.warps, t});
+            if (t != t0) time_one({cfg.ac, cfg.warps, t, cfg.per_rx});
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -500,6 +520,7 @@ extern "C" int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* fra
         }
         std::vector<unsigned char> tkey = P.shape;
         append(tkey, P.classes[c].bound);
+        append(tkey, P.classes[c].pr_need);
         append(tkey, S->force_tile);
         auto it = S->tuned.find(tkey);
         if (it != S->tuned.end()) {
@@ -520,6 +541,7 @@ extern "C" int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* fra
         append(gkey, tc.ac);
         append(gkey, tc.warps);
         append(gkey, tc.tile);
+        append(gkey, tc.per_rx);
     }
     append(gkey, ctx->timing);
     const char tag[] = "batch";
@@ -577,6 +599,12 @@ extern "C" int gh_set_batch_tile(gh_ctx* ctx, int32_t cells_per_item) {
     if (cells_per_item != 0 && idx < 0)
         return gh_fail(ctx, GH_EINVAL, "cells per item %d: 0 (tuned) or one of 4, 8, 16, 32", cells_per_item);
     state_of(ctx)->force_tile = idx;
+    return GH_OK;
+}
+
+extern "C" int gh_batch_row_mode(gh_ctx* ctx, int32_t* per_receiver) {
+    if (!ctx || !per_receiver) return GH_EINVAL;
+    *per_receiver = state_of(ctx)->last.per_rx ? 1 : 0;
     return GH_OK;
 }
 

@@ -247,17 +247,174 @@ __device__ __forceinline__ float2 unpack_bin(uint32_t w) {
     }
 }
 
+// Power row P_q[u] = |T_q[u]|^2 (u relative to j_ref) of receiver q, with
+// staged entry eq, into Pq: one warp.
+template <int MT>
+__device__ __forceinline__ void build_row(const void* __restrict__ maps, const HopParams& p, const HopEntry& eq,
+                                          int q, float* Pq, int lane) {
+    const int ndm = p.Nd - 1;
+    const int j_ref = eq.j_ref, npair = eq.npair;
+    const float c0 = eq.cs[0] * p.cscale, c1 = eq.cs[1] * p.cscale, c2 = eq.cs[2] * p.cscale;
+    const size_t qb = (size_t)q * p.Nr;
+    constexpr size_t BB = MT == GH_C64 ? 8 : 4;  // bytes per bin
+    const char* r0 = (const char*)maps + (qb + eq.row[0]) * p.Nd * BB;
+    const char* r1 = (const char*)maps + (qb + eq.row[1]) * p.Nd * BB;
+    const char* r2 = (const char*)maps + (qb + eq.row[2]) * p.Nd * BB;
+    constexpr int U = GH_HOP_U;  // row loads in flight per lane
+    if constexpr (MT == GH_C64) {
+        // pairs of bins: one 16-byte load per row and pair
+        for (int pp0 = 0; pp0 < npair; pp0 += 32 * U) {
+            float4 z0[U], z1[U], z2[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int pp = pp0 + lane + 32 * u;
+                if (pp < npair) {
+                    const int jh = ((j_ref + 2 * pp) & ndm) >> 1;  // pair of absolute bins
+                    z0[u] = load_pair<MT>(r0, jh);
+                    z1[u] = load_pair<MT>(r1, jh);
+                    z2[u] = load_pair<MT>(r2, jh);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int pp = pp0 + lane + 32 * u;
+                if (pp < npair) {
+                    const float re0 = c0 * z0[u].x + c1 * z1[u].x + c2 * z2[u].x;
+                    const float im0 = c0 * z0[u].y + c1 * z1[u].y + c2 * z2[u].y;
+                    const float re1 = c0 * z0[u].z + c1 * z1[u].z + c2 * z2[u].z;
+                    const float im1 = c0 * z0[u].w + c1 * z1[u].w + c2 * z2[u].w;
+                    *(float2*)(Pq + 2 * pp) = make_float2(re0 * re0 + im0 * im0, re1 * re1 + im1 * im1);
+                }
+            }
+        }
+    } else {
+        // 16-bit maps: groups of four bins (j_ref is a multiple of 4), one
+        // 16-byte load per row and group, lanes on consecutive groups; the
+        // same registers in flight cover twice the bins of the pair loop
+        const int nquad = (npair + 1) >> 1;
+        for (int g0 = 0; g0 < nquad; g0 += 32 * U) {
+            uint4 z0[U], z1[U], z2[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int g = g0 + lane + 32 * u;
+                if (g < nquad) {
+                    const int jq = ((j_ref + 4 * g) & ndm) >> 2;  // group of four absolute bins
+                    z0[u] = __ldg((const uint4*)r0 + jq);
+                    z1[u] = __ldg((const uint4*)r1 + jq);
+                    z2[u] = __ldg((const uint4*)r2 + jq);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int g = g0 + lane + 32 * u;
+                if (g < nquad) {
+                    const uint32_t* w0 = &z0[u].x;
+                    const uint32_t* w1 = &z1[u].x;
+                    const uint32_t* w2 = &z2[u].x;
+                    float pw[4];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const float2 a0 = unpack_bin<MT>(w0[b]), a1 = unpack_bin<MT>(w1[b]),
+                                     a2 = unpack_bin<MT>(w2[b]);
+                        const float re = c0 * a0.x + c1 * a1.x + c2 * a2.x;
+                        const float im = c0 * a0.y + c1 * a1.y + c2 * a2.y;
+                        pw[b] = re * re + im * im;
+                    }
+                    *(float4*)(Pq + 4 * g) = make_float4(pw[0], pw[1], pw[2], pw[3]);
+                }
+            }
+        }
+    }
+}
+
+// Adds receiver q's power-row values at the Doppler bins of the run of AC
+// cells (a0 + i SA, b) to acc. Entries of cells on the grid lie in [0, Nd)
+// (wrapping mod Nd only when the grid reaches Nd or more bins); cells of a
+// partial run past the grid's edge are read and discarded, and the mask keeps
+// those reads inside the row as well.
+template <int AC>
+__device__ __forceinline__ void score_run_q(const HopParams& p, const HopEntry& eq, const float* Pq, int a0, int b,
+                                            float (&acc)[AC], float* fix) {
+    const int ndm = p.Nd - 1;
+    const long long t0 = eq.base + (long long)b * eq.by + (long long)a0 * eq.ax;
+    const long long st = (long long)p.SA * eq.ax;
+    const int imask = ndm;
+    long long t = t0;
+    bool amb = false;
+    {
+#pragma unroll
+        for (int i = 0; i < AC; ++i) {
+            amb |= (uint32_t)t < p.tol2;
+            acc[i] += Pq[(int)(t >> 32) & imask];
+            t += st;
+        }
+    }
+    if (amb) {
+        // rare: a bin decision within tol of a rounding boundary;
+        // replace the fast bin by the float64 one for those cells
+        // (corrections go through shared memory so that the
+        // float64 path keeps the accumulators in registers)
+        t = t0;
+#pragma unroll 1
+        for (int i = 0; i < AC; ++i) {
+            float dlt = 0.f;
+            if ((uint32_t)t < p.tol2) {
+                const int fast = (int)(t >> 32) & imask;
+                const long long j = slow_bin(eq.wx, eq.wy, a0 + i * p.SA, b, p.lo2, p.step2, p.lo3,
+                                             p.step3, p.kappa, p.Nd);
+                const int exact = (int)(j - eq.j_ref) & imask;
+                if (exact != fast) dlt = Pq[exact] - Pq[fast];
+            }
+            fix[i] = dlt;
+            t += st;
+        }
+#pragma unroll
+        for (int i = 0; i < AC; ++i) acc[i] += fix[i];
+    }
+}
+
+// Best unmasked cell of a run (cells in increasing index order) merged into
+// (best, bestc); scores written when asked for.
+template <int AC>
+__device__ __forceinline__ void finish_run(const HopParams& p, const float (&acc)[AC], long long cbase, int a0, int b,
+                                           float* __restrict__ scores, const int64_t* __restrict__ mask, int nmask,
+                                           bool hm, float& best, long long& bestc) {
+    // best of this run (cells in increasing index order), then merge
+    float rb = -INFINITY;
+    int ri = -1;
+    const bool full = a0 + (AC - 1) * p.SA < p.nvx;
+#pragma unroll
+    for (int i = 0; i < AC; ++i) {
+        if (full || a0 + i * p.SA < p.nvx) {
+            const long long cell = cbase + (long long)(a0 + i * p.SA) * p.nvy + b;
+            if (scores) scores[cell] = acc[i];
+            bool masked = false;
+            if (hm)
+                for (int m = 0; m < nmask; ++m) masked |= (__ldg(&mask[m]) == cell);
+            if (!masked && acc[i] > rb) {
+                rb = acc[i];
+                ri = i;
+            }
+        }
+    }
+    if (ri >= 0) better(rb, cbase + (long long)(a0 + ri * p.SA) * p.nvy + b, best, bestc);
+}
+
 // Scores every velocity cell of the (x, y) cell `xy` with one warp: builds the
 // Doppler power rows P_q of the receivers in the warp's shared memory, then
 // each lane sums the rows at its cells' Doppler bins; merges the best unmasked
 // cell into (best, bestc). P, E and fix are the warp's shared-memory areas.
-template <int AC, int MT>
+// PR = false: the rows of all Q receivers are built first (P holds Q Nd
+// floats), then each run of a lane's cells is scored. PR = true (the lane's
+// cells form one run: nvy <= 32 and nvx <= SA AC): one receiver's row at a
+// time (P holds Nd floats) added into the run's accumulators, so that frames
+// with large Q Nd keep many warps per SM. Same arithmetic in the same order.
+template <int AC, int MT, bool PR>
 __device__ __forceinline__ void score_xy(const void* __restrict__ maps, const HopEntry* __restrict__ table,
                                          const HopParams& p, float* __restrict__ scores,
                                          const int64_t* __restrict__ mask, int nmask, long long xy, float* P,
                                          HopEntry* E, float* fix, int lane, int tb, int ta, bool active, float& best,
                                          long long& bestc) {
-    const int ndm = p.Nd - 1;
     const int ewords = p.Q * (int)(sizeof(HopEntry) / 8);
     __syncwarp();  // the previous cell's reads of P and E are done
     {
@@ -266,181 +423,65 @@ __device__ __forceinline__ void score_xy(const void* __restrict__ maps, const Ho
         for (int w = lane; w < ewords; w += 32) dst[w] = __ldg(src + w);
     }
     __syncwarp();
-    for (int q = 0; q < p.Q; ++q) {
-        const HopEntry& eq = E[q];
-        const int j_ref = eq.j_ref, npair = eq.npair;
-        const float c0 = eq.cs[0] * p.cscale, c1 = eq.cs[1] * p.cscale, c2 = eq.cs[2] * p.cscale;
-        const size_t qb = (size_t)q * p.Nr;
-        constexpr size_t BB = MT == GH_C64 ? 8 : 4;  // bytes per bin
-        const char* r0 = (const char*)maps + (qb + eq.row[0]) * p.Nd * BB;
-        const char* r1 = (const char*)maps + (qb + eq.row[1]) * p.Nd * BB;
-        const char* r2 = (const char*)maps + (qb + eq.row[2]) * p.Nd * BB;
-        float* Pq = P + (size_t)q * p.Nd;
-        constexpr int U = GH_HOP_U;  // row loads in flight per lane
-        if constexpr (MT == GH_C64) {
-            // pairs of bins: one 16-byte load per row and pair
-            for (int pp0 = 0; pp0 < npair; pp0 += 32 * U) {
-                float4 z0[U], z1[U], z2[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int pp = pp0 + lane + 32 * u;
-                    if (pp < npair) {
-                        const int jh = ((j_ref + 2 * pp) & ndm) >> 1;  // pair of absolute bins
-                        z0[u] = load_pair<MT>(r0, jh);
-                        z1[u] = load_pair<MT>(r1, jh);
-                        z2[u] = load_pair<MT>(r2, jh);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int pp = pp0 + lane + 32 * u;
-                    if (pp < npair) {
-                        const float re0 = c0 * z0[u].x + c1 * z1[u].x + c2 * z2[u].x;
-                        const float im0 = c0 * z0[u].y + c1 * z1[u].y + c2 * z2[u].y;
-                        const float re1 = c0 * z0[u].z + c1 * z1[u].z + c2 * z2[u].z;
-                        const float im1 = c0 * z0[u].w + c1 * z1[u].w + c2 * z2[u].w;
-                        *(float2*)(Pq + 2 * pp) = make_float2(re0 * re0 + im0 * im0, re1 * re1 + im1 * im1);
-                    }
-                }
-            }
-        } else {
-            // 16-bit maps: groups of four bins (j_ref is a multiple of 4), one
-            // 16-byte load per row and group, lanes on consecutive groups; the
-            // same registers in flight cover twice the bins of the pair loop
-            const int nquad = (npair + 1) >> 1;
-            for (int g0 = 0; g0 < nquad; g0 += 32 * U) {
-                uint4 z0[U], z1[U], z2[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int g = g0 + lane + 32 * u;
-                    if (g < nquad) {
-                        const int jq = ((j_ref + 4 * g) & ndm) >> 2;  // group of four absolute bins
-                        z0[u] = __ldg((const uint4*)r0 + jq);
-                        z1[u] = __ldg((const uint4*)r1 + jq);
-                        z2[u] = __ldg((const uint4*)r2 + jq);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int g = g0 + lane + 32 * u;
-                    if (g < nquad) {
-                        const uint32_t* w0 = &z0[u].x;
-                        const uint32_t* w1 = &z1[u].x;
-                        const uint32_t* w2 = &z2[u].x;
-                        float pw[4];
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            const float2 a0 = unpack_bin<MT>(w0[b]), a1 = unpack_bin<MT>(w1[b]),
-                                         a2 = unpack_bin<MT>(w2[b]);
-                            const float re = c0 * a0.x + c1 * a1.x + c2 * a2.x;
-                            const float im = c0 * a0.y + c1 * a1.y + c2 * a2.y;
-                            pw[b] = re * re + im * im;
-                        }
-                        *(float4*)(Pq + 4 * g) = make_float4(pw[0], pw[1], pw[2], pw[3]);
-                    }
-                }
-            }
-        }
-    }
     // does a masked cell lie in this (x, y) cell's block [xy nv, (xy + 1) nv)?
-    bool hm = false;
-    {
+    auto has_mask = [&]() {
+        bool hm = false;
         const long long lo = xy * p.nv, hi = lo + p.nv;
         for (int m = 0; m < nmask; ++m) {
             const long long mc = __ldg(&mask[m]);
             hm |= mc >= lo && mc < hi;
         }
-    }
-    __syncwarp();  // P rows complete
-    if (!active) return;
-    const long long cbase = xy * p.nv;
-    for (int b = tb; b < p.nvy; b += p.NB) {
-        for (int a0 = ta; a0 < p.nvx; a0 += p.SA * AC) {
-            float acc[AC];
+        return hm;
+    };
+    if constexpr (PR) {
+        float acc[AC];
 #pragma unroll
-            for (int i = 0; i < AC; ++i) acc[i] = 0.f;
-            for (int q = 0; q < p.Q; ++q) {
-                const HopEntry& eq = E[q];
-                const long long t0 = eq.base + (long long)b * eq.by + (long long)a0 * eq.ax;
-                const long long st = (long long)p.SA * eq.ax;
-                const float* Pq = P + (size_t)q * p.Nd;
-                // Entries of cells on the grid lie in [0, Nd) (wrapping mod Nd only
-                // when the grid reaches Nd or more bins). Cells of a partial run
-                // past the grid's edge are read and discarded; the mask keeps
-                // those reads inside the receiver's row as well.
-                const int imask = ndm;
-                long long t = t0;
-                bool amb = false;
-                {
+        for (int i = 0; i < AC; ++i) acc[i] = 0.f;
+        for (int q = 0; q < p.Q; ++q) {
+            build_row<MT>(maps, p, E[q], q, P, lane);
+            __syncwarp();  // row q complete
+            if (active) score_run_q<AC>(p, E[q], P, ta, tb, acc, fix);
+            __syncwarp();  // reads of row q done
+        }
+        const bool hm = has_mask();
+        if (active) finish_run<AC>(p, acc, xy * p.nv, ta, tb, scores, mask, nmask, hm, best, bestc);
+    } else {
+        for (int q = 0; q < p.Q; ++q) build_row<MT>(maps, p, E[q], q, P + (size_t)q * p.Nd, lane);
+        const bool hm = has_mask();
+        __syncwarp();  // P rows complete
+        if (!active) return;
+        const long long cbase = xy * p.nv;
+        for (int b = tb; b < p.nvy; b += p.NB) {
+            for (int a0 = ta; a0 < p.nvx; a0 += p.SA * AC) {
+                float acc[AC];
 #pragma unroll
-                    for (int i = 0; i < AC; ++i) {
-                        amb |= (uint32_t)t < p.tol2;
-                        acc[i] += Pq[(int)(t >> 32) & imask];
-                        t += st;
-                    }
-                }
-                if (amb) {
-                    // rare: a bin decision within tol of a rounding boundary;
-                    // replace the fast bin by the float64 one for those cells
-                    // (corrections go through shared memory so that the
-                    // float64 path keeps the accumulators in registers)
-                    t = t0;
-#pragma unroll 1
-                    for (int i = 0; i < AC; ++i) {
-                        float dlt = 0.f;
-                        if ((uint32_t)t < p.tol2) {
-                            const int fast = (int)(t >> 32) & imask;
-                            const long long j = slow_bin(eq.wx, eq.wy, a0 + i * p.SA, b, p.lo2, p.step2, p.lo3,
-                                                         p.step3, p.kappa, p.Nd);
-                            const int exact = (int)(j - eq.j_ref) & imask;
-                            if (exact != fast) dlt = Pq[exact] - Pq[fast];
-                        }
-                        fix[i] = dlt;
-                        t += st;
-                    }
-#pragma unroll
-                    for (int i = 0; i < AC; ++i) acc[i] += fix[i];
-                }
+                for (int i = 0; i < AC; ++i) acc[i] = 0.f;
+                for (int q = 0; q < p.Q; ++q) score_run_q<AC>(p, E[q], P + (size_t)q * p.Nd, a0, b, acc, fix);
+                finish_run<AC>(p, acc, cbase, a0, b, scores, mask, nmask, hm, best, bestc);
             }
-            // best of this run (cells in increasing index order), then merge
-            float rb = -INFINITY;
-            int ri = -1;
-            const bool full = a0 + (AC - 1) * p.SA < p.nvx;
-#pragma unroll
-            for (int i = 0; i < AC; ++i) {
-                if (full || a0 + i * p.SA < p.nvx) {
-                    const long long cell = cbase + (long long)(a0 + i * p.SA) * p.nvy + b;
-                    if (scores) scores[cell] = acc[i];
-                    bool masked = false;
-                    if (hm)
-                        for (int m = 0; m < nmask; ++m) masked |= (__ldg(&mask[m]) == cell);
-                    if (!masked && acc[i] > rb) {
-                        rb = acc[i];
-                        ri = i;
-                    }
-                }
-            }
-            if (ri >= 0) better(rb, cbase + (long long)(a0 + ri * p.SA) * p.nvy + b, best, bestc);
         }
     }
 }
 
-// AC: velocity cells per lane per pass (along vx, stride SA); MT: map storage type.
-template <int AC, int MT>
+// AC: velocity cells per lane per pass (along vx, stride SA); MT: map storage
+// type; PR: one receiver's power row at a time (see score_xy).
+template <int AC, int MT, bool PR>
 __global__ void __launch_bounds__(256, GH_HOP_MINB) hop_score_kernel(const void* __restrict__ maps,
                                                            const HopEntry* __restrict__ table, HopParams p,
                                                            float* __restrict__ scores,
                                                            const int64_t* __restrict__ mask, int nmask,
                                                            ArgPartial* __restrict__ parts) {
-    extern __shared__ __align__(16) unsigned char smem_hop[];  // [warps] x ([Q][Nd] floats + [Q] entries)
+    // [warps] x ([Q][Nd] floats, or [Nd] with PR, + [Q] entries + corrections)
+    extern __shared__ __align__(16) unsigned char smem_hop[];
     __shared__ float s_bs[8];
     __shared__ long long s_bc[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int W = blockDim.x >> 5;
+    const size_t pfloats = PR ? (size_t)p.Nd : (size_t)p.Q * p.Nd;
     const size_t warp_bytes =
-        (size_t)p.Q * p.Nd * sizeof(float) + (size_t)p.Q * sizeof(HopEntry) + (size_t)32 * AC * sizeof(float);
+        pfloats * sizeof(float) + (size_t)p.Q * sizeof(HopEntry) + (size_t)32 * AC * sizeof(float);
     float* P = (float*)(smem_hop + warp * warp_bytes);
-    HopEntry* E = (HopEntry*)(P + (size_t)p.Q * p.Nd);
+    HopEntry* E = (HopEntry*)(P + pfloats);
     float* fix = (float*)(E + p.Q) + lane * AC;  // per-lane corrections of the float64 path
     const int tb = lane % p.NB, ta = lane / p.NB;
     const bool active = ta < p.SA;
@@ -451,7 +492,7 @@ __global__ void __launch_bounds__(256, GH_HOP_MINB) hop_score_kernel(const void*
     long long xy1 = xy0 + p.xy_per_cta;
     if (xy1 > p.nxy) xy1 = p.nxy;
     for (long long xy = xy0 + warp; xy < xy1; xy += W) {
-        score_xy<AC, MT>(maps, table, p, scores, mask, nmask, xy, P, E, fix, lane, tb, ta, active, best, bestc);
+        score_xy<AC, MT, PR>(maps, table, p, scores, mask, nmask, xy, P, E, fix, lane, tb, ta, active, best, bestc);
     }
 
 
@@ -522,27 +563,32 @@ HopParams hop_params(const Dims& d, const GeoParams& g) {
 
 CoordParams coord_params(const Dims& d);
 
+// Shared memory of one scorer warp: power rows (all receivers', or one with
+// PR), entries, float64-path corrections.
+inline size_t hop_warp_bytes(const Dims& d, int ac, bool pr) {
+    return (size_t)(pr ? 1 : d.Q) * d.Nd * sizeof(float) + (size_t)d.Q * sizeof(HopEntry) +
+           (size_t)32 * ac * sizeof(float);
+}
+
 // Launch of the scorer (shared by the context path and the allocation-free
 // entry point). Returns the number of CTAs (partials) in *nparts.
-template <int AC, int MT>
+template <int AC, int MT, bool PR>
 int hop_launch_t(cudaStream_t stream, const Dims& d, HopParams hp, const void* maps, const HopEntry* table,
                  float* scores, const int64_t* mask, int nmask, ArgPartial* parts, long long max_ctas, int num_sms,
                  size_t smem_optin, long long* nparts) {
-    const size_t per_warp =
-        (size_t)d.Q * d.Nd * sizeof(float) + (size_t)d.Q * sizeof(HopEntry) + (size_t)32 * AC * sizeof(float);
+    const size_t per_warp = hop_warp_bytes(d, AC, PR);
     if (per_warp > smem_optin) return GH_ENOTSUP;
     int W = (int)((size_t)(100 << 10) / per_warp);
     if (W > 8) W = 8;
     if (W < 1) W = 1;
     const size_t smem = per_warp * W;
-    if (cudaFuncSetAttribute(hop_score_kernel<AC, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(hop_score_kernel<AC, MT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    auto kern = hop_score_kernel<AC, MT, PR>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
         return GH_ECUDA;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_score_kernel<AC, MT>, 32 * W, smem) != cudaSuccess)
-        return GH_ECUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * W, smem) != cudaSuccess) return GH_ECUDA;
     if (per_sm < 1) per_sm = 1;
     long long ctas = (long long)num_sms * per_sm;
     if (ctas > max_ctas) ctas = max_ctas;
@@ -557,8 +603,7 @@ int hop_launch_t(cudaStream_t stream, const Dims& d, HopParams hp, const void* m
     cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
     *nparts = ctas;
-    if (cudaLaunchKernelEx(&cfg, hop_score_kernel<AC, MT>, maps, table, hp, scores, mask, nmask, parts) !=
-        cudaSuccess) {
+    if (cudaLaunchKernelEx(&cfg, kern, maps, table, hp, scores, mask, nmask, parts) != cudaSuccess) {
         (void)cudaGetLastError();  // consume this launch's own error
         return GH_ECUDA;
     }
@@ -572,18 +617,25 @@ int hop_launch_mt(cudaStream_t stream, const Dims& d, const HopParams& hp, const
     // cells per lane and run: at most 16 (a lane takes several runs when the
     // velocity axis is longer); measured faster than 32 on the paper-shaped
     // frame (82 against 86 us per launch) at the same occupancy
-    const int need = std::min((d.nvx + hp.SA - 1) / hp.SA, 16);
-#define GH_HOP_CASE(N)                                                                                           \
-    if (need <= N)                                                                                               \
-        return hop_launch_t<N, MT>(stream, d, hp, maps, table, scores, mask, nmask, parts, max_ctas, num_sms, \
-                                   smem_optin, nparts);
+    const int full = (d.nvx + hp.SA - 1) / hp.SA;
+    const int need = std::min(full, 16);
+    // one receiver's row at a time when the lane's cells form one run and the
+    // rows of all receivers would leave fewer than eight warps per CTA
+    const int ac = need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : 16;
+    const bool pr = d.nvy <= 32 && full <= 16 && hop_warp_bytes(d, ac, false) * 8 > (100 << 10);
+#define GH_HOP_CASE(N)                                                                                             \
+    if (need <= N)                                                                                                 \
+        return pr ? hop_launch_t<N, MT, true>(stream, d, hp, maps, table, scores, mask, nmask, parts, max_ctas,  \
+                                              num_sms, smem_optin, nparts)                                         \
+                  : hop_launch_t<N, MT, false>(stream, d, hp, maps, table, scores, mask, nmask, parts, max_ctas, \
+                                               num_sms, smem_optin, nparts);
     GH_HOP_CASE(1)
     GH_HOP_CASE(2)
     GH_HOP_CASE(4)
     GH_HOP_CASE(8)
+    GH_HOP_CASE(16)
 #undef GH_HOP_CASE
-    return hop_launch_t<16, MT>(stream, d, hp, maps, table, scores, mask, nmask, parts, max_ctas, num_sms,
-                                smem_optin, nparts);
+    return GH_ENOTSUP;
 }
 
 int hop_launch(cudaStream_t stream, const Dims& d, HopParams hp, const void* maps, int map_dtype,
@@ -606,7 +658,7 @@ int hop_launch(cudaStream_t stream, const Dims& d, HopParams hp, const void* map
 // the frame's key[k] = score bits << 32 | (2^32 - 1 - cell) (largest key: best
 // score, then smallest cell). The warp's shared-memory area holds a copy of
 // the frame's scorer parameters, its power rows, entries and corrections.
-template <int AC>
+template <int AC, bool PR>
 __global__ void __launch_bounds__(256, GH_HOP_MINB) hop_batch_kernel(const BatchFrame* __restrict__ frames,
                                                           const BatchItem* __restrict__ items, int nitems,
                                                           unsigned* __restrict__ counter, int k,
@@ -631,15 +683,15 @@ __global__ void __launch_bounds__(256, GH_HOP_MINB) hop_batch_kernel(const Batch
         }
         __syncwarp();
         float* P = (float*)(base + kParamBytes);
-        HopEntry* E = (HopEntry*)(P + (size_t)p.Q * p.Nd);
+        HopEntry* E = (HopEntry*)(P + (PR ? (size_t)p.Nd : (size_t)p.Q * p.Nd));
         float* fix = (float*)(E + p.Q) + lane * AC;
         const int tb = lane % p.NB, ta = lane / p.NB;
         const bool active = ta < p.SA;
         float best = -INFINITY;
         long long bestc = 0x7fffffffffffffffLL;
         for (long long xy = item.start; xy < item.start + item.count; ++xy)
-            score_xy<AC, GH_C64>(F.maps, (const HopEntry*)F.table, p, nullptr, F.mask, k, xy, P, E, fix, lane, tb, ta,
-                                 active, best, bestc);
+            score_xy<AC, GH_C64, PR>(F.maps, (const HopEntry*)F.table, p, nullptr, F.mask, k, xy, P, E, fix, lane,
+                                     tb, ta, active, best, bestc);
         for (int off = 16; off > 0; off >>= 1) {
             const float os = __shfl_down_sync(0xffffffffu, best, off);
             const long long oc = __shfl_down_sync(0xffffffffu, bestc, off);
@@ -653,30 +705,31 @@ __global__ void __launch_bounds__(256, GH_HOP_MINB) hop_batch_kernel(const Batch
     }
 }
 
-// Shared memory of one batched-scorer warp for frames with Q * Nd <= max_q_nd.
-size_t hop_batch_warp_bytes(int ac, int max_q_nd, int max_q) {
-    const size_t b = ((sizeof(HopParams) + 15) & ~(size_t)15) + (size_t)max_q_nd * sizeof(float) +
+// Shared memory of one batched-scorer warp for frames with power rows of at
+// most `row_floats` floats (Q * Nd, or Nd with one receiver's row at a time).
+size_t hop_batch_warp_bytes(int ac, int row_floats, int max_q) {
+    const size_t b = ((sizeof(HopParams) + 15) & ~(size_t)15) + (size_t)row_floats * sizeof(float) +
                      (size_t)max_q * sizeof(HopEntry) + (size_t)32 * ac * sizeof(float);
     return (b + 15) & ~(size_t)15;
 }
 
-template <int AC>
+template <int AC, bool PR>
 int hop_batch_launch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* items, int n, unsigned* counter, int k,
-                     int warps, int max_q_nd, int max_q) {
-    const size_t per_warp = hop_batch_warp_bytes(AC, max_q_nd, max_q);
+                     int warps, int max_nd, int max_q_nd, int max_q) {
+    const size_t per_warp = hop_batch_warp_bytes(AC, PR ? max_nd : max_q_nd, max_q);
     const size_t smem = per_warp * warps;
     if (smem > ctx->smem_optin) return gh_fail(ctx, GH_ENOTSUP, "batched scorer: %zu bytes of shared memory", smem);
-    GH_CUDA(cudaFuncSetAttribute(hop_batch_kernel<AC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    GH_CUDA(cudaFuncSetAttribute(hop_batch_kernel<AC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    auto kern = hop_batch_kernel<AC, PR>;
+    GH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared));
     int per_sm = 0;
-    GH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hop_batch_kernel<AC>, 32 * warps, smem));
+    GH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, smem));
     if (per_sm < 1) per_sm = 1;
     GH_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), ctx->stream));
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_HOP_SCORE, &ev);
-    hop_batch_kernel<AC><<<ctx->num_sms * per_sm, 32 * warps, smem, ctx->stream>>>(frames, items, n, counter, k,
-                                                                                  (int)per_warp);
+    kern<<<ctx->num_sms * per_sm, 32 * warps, smem, ctx->stream>>>(frames, items, n, counter, k, (int)per_warp);
     return gh_launch_end(ctx, GH_K_HOP_SCORE, ev, "hop_batch_kernel");
 }
 
@@ -873,12 +926,17 @@ int gh_launch_coord_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem
 }
 
 int gh_launch_hop_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* items, int n, unsigned* counter,
-                        int k, int ac, int warps, int max_q_nd, int max_q) {
+                        int k, int ac, int warps, bool per_rx, int max_nd, int max_q_nd, int max_q) {
     if (n == 0) return GH_OK;
-    if (ac == 8) return hop_batch_launch<8>(ctx, frames, items, n, counter, k, warps, max_q_nd, max_q);
-    if (ac == 16) return hop_batch_launch<16>(ctx, frames, items, n, counter, k, warps, max_q_nd, max_q);
-    if (ac == 32) return hop_batch_launch<32>(ctx, frames, items, n, counter, k, warps, max_q_nd, max_q);
+#define GH_BATCH_CASE(N)                                                                                            \
+    if (ac == N)                                                                                                    \
+        return per_rx ? hop_batch_launch<N, true>(ctx, frames, items, n, counter, k, warps, max_nd, max_q_nd, max_q) \
+                      : hop_batch_launch<N, false>(ctx, frames, items, n, counter, k, warps, max_nd, max_q_nd, max_q);
+    GH_BATCH_CASE(8)
+    GH_BATCH_CASE(16)
+    GH_BATCH_CASE(32)
+#undef GH_BATCH_CASE
     return gh_fail(ctx, GH_EINVAL, "batched scorer: cells per lane %d not in {8, 16, 32}", ac);
 }
 
-size_t gh_hop_batch_warp_bytes(int ac, int max_q_nd, int max_q) { return hop_batch_warp_bytes(ac, max_q_nd, max_q); }
+size_t gh_hop_batch_warp_bytes(int ac, int row_floats, int max_q) { return hop_batch_warp_bytes(ac, row_floats, max_q); }

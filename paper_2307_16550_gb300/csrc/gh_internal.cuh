@@ -493,13 +493,19 @@ int gh_launch_maps_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem*
                          size_t smem_dop, int k);
 // Scorer and coordinate-table parameters of one frame.
 void gh_hop_frame_params(const Dims& d, const GeoParams& g, HopParams* hp, CoordParams* cp);
-size_t gh_hop_batch_warp_bytes(int ac, int max_q_nd, int max_q);
+// Shared memory of one batched-scorer warp whose power rows hold at most
+// row_floats floats (Q * Nd, or Nd with one receiver's row at a time).
+size_t gh_hop_batch_warp_bytes(int ac, int row_floats, int max_q);
 // Batched coordinate tables (items: frame, first (x, y, q) entry, count <= 128).
 int gh_launch_coord_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* items, int n);
 // Persistent batched scorer: warps take items (frame, first (x, y) cell, count)
-// from *counter (zeroed here) and fold each frame's best cell into key[k].
+// from *counter (zeroed here) and fold each frame's best cell into key[k];
+// ac cells per lane (8, 16, 32), warps per CTA; per_rx: one receiver's power
+// row at a time (every frame's cells of a lane form one run: nvy <= 32 and
+// nvx <= SA ac). max_nd, max_q_nd, max_q: largest Nd, Q * Nd and Q of the
+// frames the items name.
 int gh_launch_hop_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* items, int n, unsigned* counter,
-                        int k, int ac, int warps, int max_q_nd, int max_q);
+                        int k, int ac, int warps, bool per_rx, int max_nd, int max_q_nd, int max_q);
 // Batched BOMP selection and correlation of iteration k for the listed frames.
 int gh_launch_bomp_select_batch(gh_ctx* ctx, const BatchFrame* frames, const int* active, int n, int k);
 int gh_launch_bomp_corr_batch(gh_ctx* ctx, const BatchFrame* frames, const int* active, int n, int k, int max_chunks,

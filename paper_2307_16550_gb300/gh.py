@@ -87,6 +87,7 @@ _SIGNATURES = {
     "gh_batch_tuning": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "gh_set_batch_tile": (_I32, [_P, _I32]),
     "gh_batch_tile": (_I32, [_P, ctypes.POINTER(_I32)]),
+    "gh_batch_row_mode": (_I32, [_P, ctypes.POINTER(_I32)]),
     "gh_score_points": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, _I32, _P, ctypes.c_int64, _P]),
     "gh_score_points_adjoint": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, _I32, _P, ctypes.c_int64,
                                        _P, _P, _P, _P]),
@@ -409,6 +410,12 @@ class Context:
 
     def gh_set_batch_tile(self, cells_per_item=0):
         self._check("gh_set_batch_tile", self._lib.gh_set_batch_tile(self.handle, int(cells_per_item)))
+
+    def gh_batch_row_mode(self):
+        """1: the heaviest scorer group built one receiver's power row at a time; 0: all at once."""
+        m = _I32(0)
+        self._check("gh_batch_row_mode", self._lib.gh_batch_row_mode(self.handle, ctypes.byref(m)))
+        return m.value
 
     def gh_batch_tile(self):
         t = _I32(0)

@@ -107,3 +107,35 @@ def test_aliased_ranges_wrap_with_centring_sign(ctx, torch_cuda):
     assert table["i"].max() > 2 * 16  # really wraps
     got, _, _ = ctx.scores(sc.radar, sc.tx, sc.rx, ctx.maps(sc.radar, to_dev(torch_cuda, Y32)), sc.grid)
     assert rel_err(got.cpu().numpy(), ref) < TOL
+
+
+def _rows_scene(nv):
+    """Q = 8, Nd = 1024: the power rows of all receivers take 32 KiB per warp.
+    With 16 x 16 velocity cells a lane's cells form one run and the scorer
+    builds one receiver's row at a time; with 16 x 40 (nvy > 32) it builds
+    all of them."""
+    radar = scenes.Radar(24e9, 250e6, 128e-6, 32, 256, 4)
+    grid = scenes.Grid((0.0, 0.0, -15.0, -15.0), (5.0, 4.4, 1.875, 1.875), (8, 9) + nv)
+    return scenes.custom_scene(31, radar, grid, Q=8, T=2, snr_db=10.0)
+
+
+def test_one_receiver_row_at_a_time_matches_oracle(ctx, torch_cuda):
+    sc = _rows_scene((16, 16))
+    Y32, Y = measurement64(sc)
+    ref = hopping.hop_scores(omaps.rd_maps(Y, 4), sc.radar, sc.tx, sc.rx, sc.grid)
+    got, cell, _ = ctx.scores(sc.radar, sc.tx, sc.rx, ctx.maps(sc.radar, to_dev(torch_cuda, Y32)), sc.grid)
+    assert rel_err(got.cpu().numpy(), ref) < TOL
+    if top2_margin(ref) > 10 * TOL:
+        assert cell == hopping.argmax_cell(ref)
+
+
+def test_one_row_at_a_time_and_all_rows_agree_bit_for_bit(ctx, torch_cuda):
+    """The 16 x 16 velocity cells are the first cells of the 16 x 40 grid with
+    the same origin and steps (same bins): the scores of the two row modes
+    are equal bit for bit."""
+    small, big = _rows_scene((16, 16)), _rows_scene((16, 40))
+    Y32, _ = measurement64(small)
+    maps = ctx.maps(small.radar, to_dev(torch_cuda, Y32))
+    s_small, _, _ = ctx.scores(small.radar, small.tx, small.rx, maps, small.grid)
+    s_big, _, _ = ctx.scores(big.radar, big.tx, big.rx, maps, big.grid)
+    np.testing.assert_array_equal(s_small.cpu().numpy(), s_big.cpu().numpy()[:, :, :, :16])
