@@ -10,10 +10,11 @@
 //   s_q = sum_{k,l} c_k(tau_q) d_l(sigma_q) V_q(i_q + k, j_q + l),  S = sum_q |s_q|^2,
 //   V_q(n, m) = maps[q][n mod Nr][m mod Nd] (-1)^((Ms-1) floor(n/Nr)) exp(j pi m (Mc-1)/Nd)
 // with rho = Nr r_q, i = floor(rho + 1/2), tau = rho - i, eta = Nd u_q,
-// j = floor(eta + 1/2), sigma = eta - j, all in float64 (Eq. 1; one
-// reciprocal per distance, so bin choices may differ from a division-based
-// evaluation within a few ulps of a bin edge, where the score is continuous
-// to the interpolation error); derivatives in float32.
+// j = floor(eta + 1/2), sigma = eta - j, all in float64 (Eq. 1; each
+// distance and its reciprocal from one reciprocal square root, so bin choices
+// may differ from a square-root-and-division evaluation within a few ulps of a
+// bin edge, where the score is continuous to the interpolation error);
+// derivatives in float32.
 //
 // Adjoint (i, j fixed between bin switches): dS/drho_q = 2 Re(conj(s) sum c_k' d_l V),
 // dS/deta_q = 2 Re(conj(s) sum c_k d_l' V), chained through
@@ -36,6 +37,7 @@ struct PtParams {
     double gr, ge;     // Nr B / (c Ms) and Nd kappa
     float grf, gef;    // the same in float32 (derivative factors)
     int Q, Ms, Mc, Nr, Nd;
+    int lgNr;          // log2 of Nr (a power of two, as Nd)
     float thr, thd;    // polar half-angles (range, Doppler)
     float mscale;      // 2^s of reduced-precision maps
 };
@@ -87,12 +89,18 @@ struct PtGeo {
     float tau, sig;
 };
 
-// Unit vector from p to x and 1/|x - p| in float64 with one division
-// (zero below 1e-9 m, as Eq. 1's gradient of a point on p).
+// Unit vector from p to x, |x - p| and 1/|x - p| in float64 from one
+// reciprocal square root (zero below 1e-9 m, as Eq. 1's gradient of a point
+// on p).
 __device__ __forceinline__ void unit_recip(double dx, double dy, double* n, double* ux, double* uy, double* r) {
-    const double nn = sqrt(dx * dx + dy * dy);
-    *n = nn;
-    *r = nn < 1e-9 ? 0.0 : 1.0 / nn;
+    const double d2 = dx * dx + dy * dy;
+    if (d2 < 1e-18) {
+        *n = sqrt(d2);
+        *r = 0.0;
+    } else {
+        *r = rsqrt(d2);
+        *n = d2 * *r;
+    }
     *ux = dx * *r;
     *uy = dy * *r;
 }
@@ -125,11 +133,6 @@ __device__ __forceinline__ PtGeo pt_geo(const PtParams& p, double x, double y, d
     return g;
 }
 
-__device__ __forceinline__ long long floor_div(long long a, long long b) {
-    long long q = a / b;
-    if (a < 0 && q * b != a) --q;
-    return q;
-}
 
 // Stencil values V(i+k, j+l) of receiver q (range sign and Doppler centring applied).
 template <int MT>
@@ -139,19 +142,18 @@ __device__ __forceinline__ void stencil(const void* maps, const PtParams& p, int
     long long mm[3];
     for (int l = 0; l < 3; ++l) {
         const long long m = j + (l - 1);
-        const long long w = floor_div(m, p.Nd);
-        mm[l] = m - w * p.Nd;
+        mm[l] = m & (long long)(p.Nd - 1);  // m mod Nd (Nd a power of two)
         // exp(j pi m (Mc-1)/Nd), angle reduced exactly modulo 2 pi
-        long long t = (m % (2LL * p.Nd)) * (long long)(p.Mc - 1) % (2LL * p.Nd);
-        if (t < 0) t += 2LL * p.Nd;
+        const long long t2 = 2LL * p.Nd - 1;
+        const long long t = ((m & t2) * (long long)(p.Mc - 1)) & t2;
         float s, c;
         sincospif((float)t / (float)p.Nd, &s, &c);
         ph[l] = make_float2(c, s);
     }
     for (int k = 0; k < 3; ++k) {
         const long long n = i + (k - 1);
-        const long long w = floor_div(n, p.Nr);
-        const long long nr = n - w * p.Nr;
+        const long long w = n >> p.lgNr;  // floor(n / Nr)
+        const long long nr = n & (long long)(p.Nr - 1);
         const float sg = (((p.Ms - 1) & 1) && (w & 1)) ? -p.mscale : p.mscale;
         for (int l = 0; l < 3; ++l) {
             idx[k][l] = ((size_t)q * p.Nr + (size_t)nr) * p.Nd + (size_t)mm[l];
@@ -209,6 +211,10 @@ __device__ double point_grad(const void* maps, const PtParams& p, const double* 
     const int sub = threadIdx.x & (G - 1);
     double acc = 0.0;
     float gx = 0.f, gy = 0.f, gvx = 0.f, gvy = 0.f;
+    // receiver gradient of this lane's receiver (Q <= G: at most one per
+    // lane), summed over the warp's point groups before the atomics
+    const bool one_rx = p.Q <= G;
+    float rgx = 0.f, rgy = 0.f;
     for (int q = sub; q < p.Q; q += G) {
         const PtGeo g = pt_geo(p, x, y, vx, vy, rx[2 * q], rx[2 * q + 1]);
         const Coef cr = polar(p.thr, g.tau), cd = polar(p.thd, g.sig);
@@ -232,8 +238,13 @@ __device__ double point_grad(const void* maps, const PtParams& p, const double* 
         gvx += fe * g.wx;
         gvy += fe * g.wy;
         if (drx && live) {
-            atomicAdd(&drx[2 * q], (double)(gs * (-fr * g.ux2 - fe * j2x)));
-            atomicAdd(&drx[2 * q + 1], (double)(gs * (-fr * g.uy2 - fe * j2y)));
+            if (one_rx) {
+                rgx = gs * (-fr * g.ux2 - fe * j2x);
+                rgy = gs * (-fr * g.uy2 - fe * j2y);
+            } else {
+                atomicAdd(&drx[2 * q], (double)(gs * (-fr * g.ux2 - fe * j2x)));
+                atomicAdd(&drx[2 * q + 1], (double)(gs * (-fr * g.uy2 - fe * j2y)));
+            }
         }
         if (dmaps && live) {
             // d|s|^2 / d(stored bin) = 2 s conj(c_k d_l wph) (stored bins are 2^-s times the values)
@@ -244,6 +255,17 @@ __device__ double point_grad(const void* maps, const PtParams& p, const double* 
                     atomicAdd(&dmaps[idx[k][l]].x, w * t.x);
                     atomicAdd(&dmaps[idx[k][l]].y, w * t.y);
                 }
+        }
+    }
+    if (drx && one_rx) {  // every lane takes part (drx is the same for the whole warp)
+        double sx = rgx, sy = rgy;
+        for (int o = G; o < 32; o <<= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        }
+        if ((threadIdx.x & 31) < G && sub < p.Q) {
+            atomicAdd(&drx[2 * sub], sx);
+            atomicAdd(&drx[2 * sub + 1], sy);
         }
     }
     grad[0] = group_sum((double)gx, G);
@@ -445,6 +467,8 @@ PtParams pt_params(const Dims& d, const GeoParams& g, int map_dtype) {
     p.Mc = d.Mc;
     p.Nr = d.Nr;
     p.Nd = d.Nd;
+    p.lgNr = 0;
+    while ((1 << p.lgNr) < d.Nr) ++p.lgNr;
     p.thr = (float)half_angle(d.Ms, d.Nr);
     p.thd = (float)half_angle(d.Mc, d.Nd);
     p.mscale = ldexpf(1.0f, gh_map_scale_log2(d, map_dtype));
