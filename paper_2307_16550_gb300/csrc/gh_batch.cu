@@ -242,8 +242,7 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
     std::vector<std::vector<BatchItem>> defl(P.Kmax);
     for (int f = 0; f < nframes; ++f) {
         const Dims& d = dims[f];
-        const long long ne = d.nxy * d.Q;
-        for (long long s = 0; s < ne; s += 128) coord.push_back({f, 0, s, std::min(128LL, ne - s)});
+        for (long long s = 0; s < d.nxy; s += 16) coord.push_back({f, 0, s, std::min(16LL, d.nxy - s)});
         const int rpc = gh_fft_rows_per_cta(d.Nr);
         const int rows = d.Q * d.Mc;
         for (int r = 0; r < rows; r += rpc) {

@@ -53,11 +53,10 @@ inline uint32_t hop_tol(int nvx, int nvy) {
 
 // Entry idx = xy * Q + q of the coordinate table (diagnostics optional), at
 // the point (x, y) whose transmitter distance and unit vector are given.
-__device__ __forceinline__ void coord_entry_at(const GeoParams& g, const CoordParams& cp, long long idx, double x,
-                                               double y, double n1, double ux1, double uy1,
+__device__ __forceinline__ void coord_entry_at(const GeoParams& g, const CoordParams& cp, long long idx, int q,
+                                               double x, double y, double n1, double ux1, double uy1,
                                                HopEntry* __restrict__ table, int32_t* diag_i, double* diag_tau,
                                                float* diag_c, double* diag_w, double* rw) {
-    const int q = (int)(idx % g.Q);
     double d, wx, wy;
     gh_bistatic_rx(g, q, x, y, n1, ux1, uy1, &d, &wx, &wy);
     const double r = gh_range(g, d);
@@ -76,11 +75,11 @@ __device__ __forceinline__ void coord_entry_at(const GeoParams& g, const CoordPa
     const float c[3] = {0.5f * (kap - sig), 1.0f - kap, 0.5f * (kap + sig)};
 
     HopEntry e;
+    const int lgNr = __ffs(g.Nr) - 1;  // Nr is a power of two
     for (int k = 0; k < 3; ++k) {
         const long long n = i + (k - 1);
-        long long w = n / g.Nr;
-        if (n < 0 && w * g.Nr != n) --w;  // floor division
-        e.row[k] = (int)(n - w * g.Nr);
+        const long long w = n >> lgNr;  // floor(n / Nr)
+        e.row[k] = (int)(n & (long long)(g.Nr - 1));
         const bool flip = cp.Ms_odd_sign && (w & 1);
         e.cs[k] = flip ? -c[k] : c[k];
     }
@@ -124,20 +123,6 @@ __device__ __forceinline__ void coord_entry_at(const GeoParams& g, const CoordPa
     }
 }
 
-// Entry idx = xy * Q + q of the coordinate table (diagnostics optional).
-__device__ __forceinline__ void coord_entry(const GeoParams& g, const CoordParams& cp, long long idx,
-                                            HopEntry* __restrict__ table, int32_t* diag_i, double* diag_tau,
-                                            float* diag_c, double* diag_w, double* rw = nullptr) {
-    const long long xy = idx / g.Q;
-    const int ix = (int)(xy / g.n[1]);
-    const int iy = (int)(xy - (long long)ix * g.n[1]);
-    const double x = gh_axis(g.lo[0], g.step[0], ix);
-    const double y = gh_axis(g.lo[1], g.step[1], iy);
-    double n1, ux1, uy1;
-    gh_unit(__dsub_rn(x, g.tx[0]), __dsub_rn(y, g.tx[1]), &n1, &ux1, &uy1);
-    coord_entry_at(g, cp, idx, x, y, n1, ux1, uy1, table, diag_i, diag_tau, diag_c, diag_w, rw);
-}
-
 // Two threads per (x, y), each taking every other receiver: the
 // transmitter's distance and unit vector once per thread, then its receivers'
 // entries. Float64 latency is the limit: sharing the transmitter half saves
@@ -171,7 +156,7 @@ __global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__
         gh_unit(__dsub_rn(x, g.tx[0]), __dsub_rn(y, g.tx[1]), &n1, &ux1, &uy1);
         for (int q = q0; q < g.Q; q += 2) {
             const long long idx = xy * g.Q + q;
-            coord_entry_at(g, cp, idx, x, y, n1, ux1, uy1, table, diag_i, diag_tau, diag_c, diag_w, rw);
+            coord_entry_at(g, cp, idx, q, x, y, n1, ux1, uy1, table, diag_i, diag_tau, diag_c, diag_w, rw);
             if (rowlim) {
                 const HopEntry& e = table[idx];
                 const int lo = min(e.row[0], min(e.row[1], e.row[2]));
@@ -192,12 +177,25 @@ __global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__
     }
 }
 
-// Batched tables: item = (frame, first entry, count <= blockDim.x).
+// Batched tables: item = (frame, first (x, y) cell, count <= 16), one warp;
+// two threads per cell, each taking every other receiver after the
+// transmitter's distance and unit vector (as coord_kernel).
 __global__ void coord_batch_kernel(const BatchFrame* __restrict__ frames, const BatchItem* __restrict__ items) {
     const BatchItem it = items[blockIdx.x];
-    if (threadIdx.x >= it.count) return;
+    const int c = threadIdx.x >> 1, q0 = threadIdx.x & 1;
+    if (c >= it.count) return;
     const BatchFrame& F = frames[it.frame];
-    coord_entry(F.g, F.cp, it.start + threadIdx.x, (HopEntry*)F.table, nullptr, nullptr, nullptr, nullptr);
+    const GeoParams& g = F.g;
+    const long long xy = it.start + c;
+    const int ix = (int)(xy / g.n[1]);
+    const int iy = (int)(xy - (long long)ix * g.n[1]);
+    const double x = gh_axis(g.lo[0], g.step[0], ix);
+    const double y = gh_axis(g.lo[1], g.step[1], iy);
+    double n1, ux1, uy1;
+    gh_unit(__dsub_rn(x, g.tx[0]), __dsub_rn(y, g.tx[1]), &n1, &ux1, &uy1);
+    for (int q = q0; q < g.Q; q += 2)
+        coord_entry_at(g, F.cp, xy * g.Q + q, q, x, y, n1, ux1, uy1, (HopEntry*)F.table, nullptr, nullptr, nullptr,
+                       nullptr, nullptr);
 }
 
 
@@ -921,7 +919,7 @@ int gh_launch_coord_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem
     if (n == 0) return GH_OK;
     cudaEvent_t ev;
     gh_launch_begin(ctx, GH_K_COORD, &ev);
-    coord_batch_kernel<<<n, 128, 0, ctx->stream>>>(frames, items);
+    coord_batch_kernel<<<n, 32, 0, ctx->stream>>>(frames, items);
     return gh_launch_end(ctx, GH_K_COORD, ev, "coord_batch_kernel");
 }
 

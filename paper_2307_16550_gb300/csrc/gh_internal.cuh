@@ -496,7 +496,7 @@ void gh_hop_frame_params(const Dims& d, const GeoParams& g, HopParams* hp, Coord
 // Shared memory of one batched-scorer warp whose power rows hold at most
 // row_floats floats (Q * Nd, or Nd with one receiver's row at a time).
 size_t gh_hop_batch_warp_bytes(int ac, int row_floats, int max_q);
-// Batched coordinate tables (items: frame, first (x, y, q) entry, count <= 128).
+// Batched coordinate tables (items: frame, first (x, y) cell, count <= 16).
 int gh_launch_coord_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* items, int n);
 // Persistent batched scorer: warps take items (frame, first (x, y) cell, count)
 // from *counter (zeroed here) and fold each frame's best cell into key[k];
