@@ -177,7 +177,7 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
     }
     // per-frame device buffers
     std::vector<size_t> off_zr(nframes), off_maps(nframes), off_tab(nframes), off_bomp(nframes), off_mask(nframes),
-        off_sel(nframes), off_key(nframes);
+        off_sel(nframes), off_key(nframes), off_lim(nframes);
     size_t o = 0, okeys = 0;
     for (int f = 0; f < nframes; ++f) {
         const Dims& d = dims[f];
@@ -194,6 +194,8 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
         o += align256((size_t)K * sizeof(int64_t));
         off_sel[f] = o;
         o += align256((size_t)K * sizeof(ArgResult));
+        off_lim[f] = o;
+        o += align256((size_t)2 * d.Q * sizeof(int));
         off_key[f] = okeys;
         okeys += (size_t)K * sizeof(unsigned long long);
     }
@@ -345,6 +347,7 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
         F.zr = (float2*)(B + off_zr[f]);
         F.maps = (float2*)(B + off_maps[f]);
         F.table = B + off_tab[f];
+        F.rowlim = (int*)(B + off_lim[f]);
         F.mask = (int64_t*)(B + off_mask[f]);
         F.key = (unsigned long long*)((char*)P.keys + off_key[f]);
         F.sel = (ArgResult*)(B + off_sel[f]);

@@ -868,7 +868,12 @@ __global__ void __launch_bounds__(256) bomp_corr_batch_kernel(const BatchFrame* 
 }
 
 __global__ void batch_reset_kernel(const BatchFrame* __restrict__ frames) {
-    if (threadIdx.x == 0) *frames[blockIdx.x].bw.counter = 0u;
+    const BatchFrame& F = frames[blockIdx.x];
+    if (threadIdx.x == 0) *F.bw.counter = 0u;
+    for (int i = threadIdx.x; i < F.d.Q; i += blockDim.x) {  // row limits, filled by the coordinate tables
+        F.rowlim[i] = 0x7fffffff;
+        F.rowlim[F.d.Q + i] = -1;
+    }
 }
 
 // Packs frame f's selections (ArgResult [K]) and amplitudes (double2 [K][Q])

@@ -179,23 +179,43 @@ __global__ void coord_kernel(GeoParams g, CoordParams cp, HopEntry* __restrict__
 
 // Batched tables: item = (frame, first (x, y) cell, count <= 16), one warp;
 // two threads per cell, each taking every other receiver after the
-// transmitter's distance and unit vector (as coord_kernel).
+// transmitter's distance and unit vector (as coord_kernel); the frame's row
+// limits (reset to empty by batch_reset_kernel) take the rows the entries read.
 __global__ void coord_batch_kernel(const BatchFrame* __restrict__ frames, const BatchItem* __restrict__ items) {
+    __shared__ int s_lim[2 * GH_MAX_Q];
     const BatchItem it = items[blockIdx.x];
     const int c = threadIdx.x >> 1, q0 = threadIdx.x & 1;
-    if (c >= it.count) return;
     const BatchFrame& F = frames[it.frame];
     const GeoParams& g = F.g;
-    const long long xy = it.start + c;
-    const int ix = (int)(xy / g.n[1]);
-    const int iy = (int)(xy - (long long)ix * g.n[1]);
-    const double x = gh_axis(g.lo[0], g.step[0], ix);
-    const double y = gh_axis(g.lo[1], g.step[1], iy);
-    double n1, ux1, uy1;
-    gh_unit(__dsub_rn(x, g.tx[0]), __dsub_rn(y, g.tx[1]), &n1, &ux1, &uy1);
-    for (int q = q0; q < g.Q; q += 2)
-        coord_entry_at(g, F.cp, xy * g.Q + q, q, x, y, n1, ux1, uy1, (HopEntry*)F.table, nullptr, nullptr, nullptr,
-                       nullptr, nullptr);
+    for (int i = threadIdx.x; i < g.Q; i += blockDim.x) {
+        s_lim[i] = 0x7fffffff;
+        s_lim[g.Q + i] = -1;
+    }
+    __syncwarp();
+    if (c < it.count) {
+        const long long xy = it.start + c;
+        const int ix = (int)(xy / g.n[1]);
+        const int iy = (int)(xy - (long long)ix * g.n[1]);
+        const double x = gh_axis(g.lo[0], g.step[0], ix);
+        const double y = gh_axis(g.lo[1], g.step[1], iy);
+        double n1, ux1, uy1;
+        gh_unit(__dsub_rn(x, g.tx[0]), __dsub_rn(y, g.tx[1]), &n1, &ux1, &uy1);
+        HopEntry* table = (HopEntry*)F.table;
+        for (int q = q0; q < g.Q; q += 2) {
+            const long long idx = xy * g.Q + q;
+            coord_entry_at(g, F.cp, idx, q, x, y, n1, ux1, uy1, table, nullptr, nullptr, nullptr, nullptr, nullptr);
+            const HopEntry& e = table[idx];
+            atomicMin(&s_lim[q], min(e.row[0], min(e.row[1], e.row[2])));
+            atomicMax(&s_lim[g.Q + q], max(e.row[0], max(e.row[1], e.row[2])));
+        }
+    }
+    __syncwarp();
+    for (int i = threadIdx.x; i < g.Q; i += blockDim.x) {
+        if (s_lim[g.Q + i] >= 0) {
+            atomicMin(&F.rowlim[i], s_lim[i]);
+            atomicMax(&F.rowlim[g.Q + i], s_lim[g.Q + i]);
+        }
+    }
 }
 
 

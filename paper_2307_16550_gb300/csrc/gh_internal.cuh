@@ -435,6 +435,7 @@ struct BatchFrame {
     float2* zr;                 // range-FFT intermediate [Q][Mc][Nr]
     float2* maps;               // [Q][Nr][Nd]
     void* table;                // hopping coordinate table [nxy][Q]
+    int* rowlim;                // [2Q]: per receiver the smallest, then the largest map row the table reads
     int64_t* mask;              // [K] selected cells
     unsigned long long* key;    // [K] packed argmax: score bits << 32 | (2^32 - 1 - cell)
     ArgResult* sel;             // [K]

@@ -453,16 +453,19 @@ __global__ void __launch_bounds__(512) range_fft_batch_kernel(const BatchFrame* 
 }
 
 // Batched residual maps by linearity: one item (frame, receiver, first range
-// bin, count) per CTA, iteration k (atoms 0 .. k-1).
+// bin, count) per CTA, iteration k (atoms 0 .. k-1); items outside the frame's
+// row limits (rows no coordinate entry reads) do nothing, as in gh_detect.
 __global__ void __launch_bounds__(256) maps_deflate_batch_kernel(const BatchFrame* __restrict__ frames,
                                                                  const BatchItem* __restrict__ items, int k) {
     const BatchItem it = items[blockIdx.x];
     const BatchFrame& F = frames[it.frame];
+    const int i0 = (int)it.start, q = it.aux;
+    if (i0 + (int)it.count - 1 < F.rowlim[q] || i0 > F.rowlim[F.d.Q + q]) return;  // rows the scorer never reads
     Deflate df = F.df;
     df.n = k;
     int logNd = 0;
     while ((1 << logNd) < F.d.Nd) ++logNd;
-    deflate_rows(F.maps, df, F.d.Q, F.d.Nr, F.d.Nd, logNd, it.aux, (int)it.start, (int)it.count);
+    deflate_rows(F.maps, df, F.d.Q, F.d.Nr, F.d.Nd, logNd, q, i0, (int)it.count);
 }
 
 __global__ void __launch_bounds__(512, 2) doppler_fft_batch_kernel(const BatchFrame* __restrict__ frames,
@@ -470,11 +473,12 @@ __global__ void __launch_bounds__(512, 2) doppler_fft_batch_kernel(const BatchFr
     extern __shared__ float2 smem[];
     const BatchItem it = items[blockIdx.x];
     const BatchFrame& F = frames[it.frame];
+    const int i0 = (int)it.start, q = it.aux;
+    if (i0 + (int)it.count - 1 < F.rowlim[q] || i0 > F.rowlim[F.d.Q + q]) return;  // rows the scorer never reads
     int logNr = 0, logNd = 0;
     while ((1 << logNr) < F.d.Nr) ++logNr;
     while ((1 << logNd) < F.d.Nd) ++logNd;
-    doppler_cols<GH_C64>(F.zr, F.maps, F.d.Ms, F.d.Mc, logNr, logNd, (int)it.count, it.aux, (int)it.start, F.twd,
-                         1.0f, smem);
+    doppler_cols<GH_C64>(F.zr, F.maps, F.d.Ms, F.d.Mc, logNr, logNd, (int)it.count, q, i0, F.twd, 1.0f, smem);
 }
 
 }  // namespace
