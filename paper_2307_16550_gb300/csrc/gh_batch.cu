@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <vector>
 
@@ -60,6 +61,7 @@ struct Plan {
         // large value when a frame has nvy > 32: the per-receiver scorer
         // needs ac >= pr_need
         int pr_need = 0;
+        int layout_ac = 0;  // 6 or 10: the 8 x 4 lane layout fits the class's frames best
         double work = 0.0;                    // cell * receiver * iteration evals
         // per tile size: the class's items, frames in decreasing K (so the
         // items of the frames still iterating at k are a prefix), and per k
@@ -86,6 +88,29 @@ struct Tuning {
     int ac = 0, warps = 0, tile = kDefaultTile;  // tile: index into kTiles
     bool per_rx = false;                         // one receiver's power row at a time
 };
+
+// Scoring slots per lane (cells, partial runs included) of frame d with AC
+// cells per run: lanes b = lane % NB, a = lane / NB; NB = min(nvy, 32) for
+// AC = 8, 16, 32 and NB = 8 (SA = 4) for AC = 6, 10 (the scorer's layouts).
+int lane_slots(const Dims& d, int ac) {
+    const int NB = (ac == 6 || ac == 10) ? 8 : (d.nvy < 32 ? d.nvy : 32), SA = 32 / NB;
+    const int rows = (d.nvy + NB - 1) / NB, cells = (d.nvx + SA - 1) / SA;
+    return rows * ((cells + ac - 1) / ac) * ac;
+}
+
+// 6 or 10 when the 8 x 4 layout with that many cells per run needs fewer
+// slots than every standard configuration, else 0.
+int lane_layout_ac(const Dims& d) {
+    int best = 0, best_slots = 1 << 30;
+    for (int ac : {8, 16, 32, 6, 10}) {
+        const int sl = lane_slots(d, ac);
+        if (sl < best_slots) {
+            best_slots = sl;
+            best = ac;
+        }
+    }
+    return (best == 6 || best == 10) ? best : 0;
+}
 
 int class_bound(int q_nd) {
     int b = 1024;
@@ -225,18 +250,20 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
     // work items
     std::vector<BatchItem> coord, range, dop;
     // classes: (shared-memory bound, whether every lane's cells form one run,
-    // which the per-receiver scorer needs)
+    // which the per-receiver scorer needs, and the 8 x 4 lane layout's cells
+    // per run when that layout fills the runs best: 6 or 10, else 0)
     auto class_key = [&](const Dims& d) {
         const int NB = d.nvy < 32 ? d.nvy : 32, SA = 32 / NB;
         const bool one_run = d.nvy <= 32 && (d.nvx + SA - 1) / SA <= 32;
-        return std::make_pair(class_bound(d.Q * d.Nd), one_run ? 1 : 0);
+        return std::make_tuple(class_bound(d.Q * d.Nd), one_run ? 1 : 0, lane_layout_ac(d));
     };
-    std::map<std::pair<int, int>, int> class_of_key;
+    std::map<std::tuple<int, int, int>, int> class_of_key;
     for (int f = 0; f < nframes; ++f) class_of_key[class_key(dims[f])] = 0;
     for (auto& kv : class_of_key) {
         kv.second = (int)P.classes.size();
         Plan::ScoreClass c;
-        c.bound = kv.first.first;
+        c.bound = std::get<0>(kv.first);
+        c.layout_ac = std::get<2>(kv.first);
         P.classes.push_back(c);
     }
     std::vector<std::vector<int>> class_frames(P.classes.size());
@@ -430,9 +457,10 @@ int autotune_prepare(gh_ctx* ctx, const Plan& P) {
 }
 
 // Times the scorer on the first iteration of one class and returns the
-// fastest configuration: cells per lane (8, 16, 32) x warps per CTA (8, 4, 2,
-// as shared memory allows) x power rows of all receivers or of one receiver
-// at a time (where every frame's cells of a lane form one run), with 8-cell
+// fastest configuration: cells per lane (8, 16, 32, and 6 or 10 in the 8 x 4
+// lane layout for classes it fits) x warps per CTA (8, 4, 2, as shared memory
+// allows) x power rows of all receivers or of one receiver at a time (where
+// every frame's cells of a lane form one run), with 8-cell
 // items, then, for that configuration, items of 4, 8, 16 and 32 (x, y) cells
 // (`tile` >= 0 fixes the item size).
 int autotune(gh_ctx* ctx, const Plan& P, const Plan::ScoreClass& C, int tile, Tuning* best) {
@@ -461,14 +489,16 @@ int autotune(gh_ctx* ctx, const Plan& P, const Plan::ScoreClass& C, int tile, Tu
         }
     };
     const int t0 = tile >= 0 ? tile : kDefaultTile;
-    for (int ac : {8, 16, 32})
+    for (int ac : {8, 16, 32, 6, 10}) {
+        if ((ac == 6 || ac == 10) && ac != C.layout_ac) continue;
         for (int warps : {8, 4, 2}) {
             if (st == GH_OK && gh_hop_batch_warp_bytes(ac, C.bound, C.max_q) * warps <= ctx->smem_optin)
                 time_one({ac, warps, t0, false});
-            if (st == GH_OK && ac >= C.pr_need &&
+            if (st == GH_OK && ac >= 8 && ac >= C.pr_need &&
                 gh_hop_batch_warp_bytes(ac, C.max_nd, C.max_q) * warps <= ctx->smem_optin)
                 time_one({ac, warps, t0, true});
         }
+    }
     if (st == GH_OK && best->ac == 0)
         st = gh_fail(ctx, GH_ENOTSUP, "batched scorer: frames too large for shared memory");
     if (tile < 0) {
@@ -523,6 +553,7 @@ extern "C" int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* fra
         std::vector<unsigned char> tkey = P.shape;
         append(tkey, P.classes[c].bound);
         append(tkey, P.classes[c].pr_need);
+        append(tkey, P.classes[c].layout_ac);
         append(tkey, S->force_tile);
         auto it = S->tuned.find(tkey);
         if (it != S->tuned.end()) {

@@ -670,6 +670,9 @@ int hop_launch(cudaStream_t stream, const Dims& d, HopParams hp, const void* map
                                  smem_optin, nparts);
 }
 
+// Lane layout: b = lane % NB, a = lane / NB with the frame's NB = min(nvy, 32)
+// for AC = 8, 16, 32, and NB = 8, SA = 4 for AC = 6 and 10 (a lane's cells
+// of a 24 x 24 or 40 x 40 velocity grid then fill its runs exactly).
 // Persistent batched scorer (complex float32 maps): each warp takes work items
 // (frame, first (x, y) cell, count) from *counter until none is left, scores
 // the item's cells with score_xy and folds the item's best unmasked cell into
@@ -700,6 +703,13 @@ __global__ void __launch_bounds__(256, GH_HOP_MINB) hop_batch_kernel(const Batch
             for (int w = lane; w < (int)(sizeof(HopParams) / 4); w += 32) dst[w] = src[w];
         }
         __syncwarp();
+        if constexpr (AC == 6 || AC == 10) {  // lanes 8 (vy) x 4 (vx): grids of 24 or 40 velocities per axis
+            if (lane == 0) {
+                p.NB = 8;
+                p.SA = 4;
+            }
+            __syncwarp();
+        }
         float* P = (float*)(base + kParamBytes);
         HopEntry* E = (HopEntry*)(P + (PR ? (size_t)p.Nd : (size_t)p.Q * p.Nd));
         float* fix = (float*)(E + p.Q) + lane * AC;
@@ -954,7 +964,12 @@ int gh_launch_hop_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* 
     GH_BATCH_CASE(16)
     GH_BATCH_CASE(32)
 #undef GH_BATCH_CASE
-    return gh_fail(ctx, GH_EINVAL, "batched scorer: cells per lane %d not in {8, 16, 32}", ac);
+    if (!per_rx && ac == 6)
+        return hop_batch_launch<6, false>(ctx, frames, items, n, counter, k, warps, max_nd, max_q_nd, max_q);
+    if (!per_rx && ac == 10)
+        return hop_batch_launch<10, false>(ctx, frames, items, n, counter, k, warps, max_nd, max_q_nd, max_q);
+    return gh_fail(ctx, GH_EINVAL, "batched scorer: cells per lane %d not in {8, 16, 32} (or 6, 10 with all rows)",
+                   ac);
 }
 
 size_t gh_hop_batch_warp_bytes(int ac, int row_floats, int max_q) { return hop_batch_warp_bytes(ac, row_floats, max_q); }
