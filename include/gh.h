@@ -307,6 +307,11 @@ GH_API int gh_batch_tile(gh_ctx* ctx, int32_t* cells_per_item);
  * Q * Nd is large; the autotuner times both where both apply (a
  * configuration fixed with gh_set_batch_tuning builds all rows at once). */
 GH_API int gh_batch_row_mode(gh_ctx* ctx, int32_t* per_receiver);
+/* Keeps the autotuner to one power-row mode: 0 all receivers' rows, 1 one
+ * receiver's row at a time (for the scorer groups where it applies; all rows
+ * elsewhere); -1 (the default) lets it time both. Results do not depend on
+ * the mode. */
+GH_API int gh_set_batch_row_mode(gh_ctx* ctx, int32_t row_mode);
 
 /*
  * gh_factorized - the paper's factorised single-target estimators: location

@@ -124,6 +124,7 @@ struct BatchState {
     bool plan_valid = false;
     int force_ac = 0, force_warps = 0;
     int force_tile = -1;  // index into kTiles, -1: tuned
+    int force_rm = -1;    // row mode the autotuner keeps to (0 all rows, 1 one row at a time), -1: either
     Tuning last;                                         // of the class with the most work
     std::map<std::vector<unsigned char>, Tuning> tuned;  // per batch shape and class
 };
@@ -463,7 +464,7 @@ int autotune_prepare(gh_ctx* ctx, const Plan& P) {
 // every frame's cells of a lane form one run), with 8-cell
 // items, then, for that configuration, items of 4, 8, 16 and 32 (x, y) cells
 // (`tile` >= 0 fixes the item size).
-int autotune(gh_ctx* ctx, const Plan& P, const Plan::ScoreClass& C, int tile, Tuning* best) {
+int autotune(gh_ctx* ctx, const Plan& P, const Plan::ScoreClass& C, int tile, int rm, Tuning* best) {
     cudaEvent_t a, b;
     GH_CUDA(cudaEventCreate(&a));
     GH_CUDA(cudaEventCreate(&b));
@@ -489,12 +490,16 @@ int autotune(gh_ctx* ctx, const Plan& P, const Plan::ScoreClass& C, int tile, Tu
         }
     };
     const int t0 = tile >= 0 ? tile : kDefaultTile;
+    // one row at a time where it applies and is wanted; all rows otherwise
+    // (also when one row at a time is asked for but applies to no configuration)
+    const bool pr_any = rm != 0 && C.pr_need <= 32;
     for (int ac : {8, 16, 32, 6, 10}) {
         if ((ac == 6 || ac == 10) && ac != C.layout_ac) continue;
         for (int warps : {8, 4, 2}) {
-            if (st == GH_OK && gh_hop_batch_warp_bytes(ac, C.bound, C.max_q) * warps <= ctx->smem_optin)
+            if (st == GH_OK && (rm != 1 || !pr_any) &&
+                gh_hop_batch_warp_bytes(ac, C.bound, C.max_q) * warps <= ctx->smem_optin)
                 time_one({ac, warps, t0, false});
-            if (st == GH_OK && ac >= 8 && ac >= C.pr_need &&
+            if (st == GH_OK && rm != 0 && ac >= 8 && ac >= C.pr_need &&
                 gh_hop_batch_warp_bytes(ac, C.max_nd, C.max_q) * warps <= ctx->smem_optin)
                 time_one({ac, warps, t0, true});
         }
@@ -555,6 +560,7 @@ extern "C" int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* fra
         append(tkey, P.classes[c].pr_need);
         append(tkey, P.classes[c].layout_ac);
         append(tkey, S->force_tile);
+        append(tkey, S->force_rm);
         auto it = S->tuned.find(tkey);
         if (it != S->tuned.end()) {
             t[c] = it->second;
@@ -564,7 +570,7 @@ extern "C" int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* fra
             GH_TRY(autotune_prepare(ctx, P));
             prepared = true;
         }
-        GH_TRY(autotune(ctx, P, P.classes[c], S->force_tile, &t[c]));
+        GH_TRY(autotune(ctx, P, P.classes[c], S->force_tile, S->force_rm, &t[c]));
         S->tuned[tkey] = t[c];
     }
     S->last = t[heaviest];
@@ -632,6 +638,13 @@ extern "C" int gh_set_batch_tile(gh_ctx* ctx, int32_t cells_per_item) {
     if (cells_per_item != 0 && idx < 0)
         return gh_fail(ctx, GH_EINVAL, "cells per item %d: 0 (tuned) or one of 4, 8, 16, 32", cells_per_item);
     state_of(ctx)->force_tile = idx;
+    return GH_OK;
+}
+
+extern "C" int gh_set_batch_row_mode(gh_ctx* ctx, int32_t row_mode) {
+    if (!ctx) return GH_EINVAL;
+    if (row_mode < -1 || row_mode > 1) return gh_fail(ctx, GH_EINVAL, "row mode %d: -1 (tuned), 0 or 1", row_mode);
+    state_of(ctx)->force_rm = row_mode;
     return GH_OK;
 }
 

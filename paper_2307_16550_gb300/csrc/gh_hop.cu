@@ -748,7 +748,14 @@ int hop_batch_launch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* ite
     const size_t smem = per_warp * warps;
     if (smem > ctx->smem_optin) return gh_fail(ctx, GH_ENOTSUP, "batched scorer: %zu bytes of shared memory", smem);
     auto kern = hop_batch_kernel<AC, PR>;
-    GH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // The classes of one batch launch the same kernel with different shared
+    // memory; the function's limit is set to the device's largest, so that
+    // every launch (also a graph node launched on its own) stays within it
+    // whatever class set it last.
+    cudaFuncAttributes fa;
+    GH_CUDA(cudaFuncGetAttributes(&fa, kern));
+    GH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(ctx->smem_optin - fa.sharedSizeBytes)));
     GH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared));
     int per_sm = 0;

@@ -88,6 +88,7 @@ _SIGNATURES = {
     "gh_set_batch_tile": (_I32, [_P, _I32]),
     "gh_batch_tile": (_I32, [_P, ctypes.POINTER(_I32)]),
     "gh_batch_row_mode": (_I32, [_P, ctypes.POINTER(_I32)]),
+    "gh_set_batch_row_mode": (_I32, [_P, _I32]),
     "gh_score_points": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, _I32, _P, ctypes.c_int64, _P]),
     "gh_score_points_adjoint": (_I32, [_P, ctypes.POINTER(GhRadar), _P, _P, _I32, _P, _I32, _P, ctypes.c_int64,
                                        _P, _P, _P, _P]),
@@ -416,6 +417,9 @@ class Context:
         m = _I32(0)
         self._check("gh_batch_row_mode", self._lib.gh_batch_row_mode(self.handle, ctypes.byref(m)))
         return m.value
+
+    def gh_set_batch_row_mode(self, row_mode=-1):
+        self._check("gh_set_batch_row_mode", self._lib.gh_set_batch_row_mode(self.handle, int(row_mode)))
 
     def gh_batch_tile(self):
         t = _I32(0)

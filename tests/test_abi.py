@@ -48,6 +48,7 @@ def test_null_context_is_rejected(lib):
     assert lib.gh_set_batch_tile(None, 8) == gh.GH_EINVAL
     assert lib.gh_batch_tile(None, None) == gh.GH_EINVAL
     assert lib.gh_batch_row_mode(None, None) == gh.GH_EINVAL
+    assert lib.gh_set_batch_row_mode(None, 0) == gh.GH_EINVAL
     assert lib.gh_inject_fault(None, gh.GH_ECUDA, 0) == gh.GH_EINVAL
     lib.gh_destroy(None)
     assert lib.gh_create(None, 0, None) == gh.GH_EINVAL

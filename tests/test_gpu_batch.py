@@ -85,6 +85,25 @@ def test_item_sizes_give_single_frame_results(ctx, torch_cuda, tile):
         _same(r, _single(ctx, f))
 
 
+@pytest.mark.parametrize("row_mode", [0, 1])
+def test_power_row_modes_give_single_frame_results(ctx, torch_cuda, row_mode):
+    """The batched scorer kept to one power-row mode (all receivers' rows, or
+    one receiver's row at a time where a lane's cells form one run): the same
+    results as gh_detect, bit for bit, on frames with 16..40 velocities per
+    axis."""
+    frames = scenes.batch_scenes(7, 12) + [scenes.tiny_scene(3)]
+    dev, _ = _device_frames(torch_cuda, frames, synth_ctx=ctx)
+    ctx.gh_set_batch_row_mode(row_mode)
+    try:
+        res = ctx.gh_detect_batch(dev)
+        if row_mode == 0:
+            assert ctx.gh_batch_row_mode() == 0
+    finally:
+        ctx.gh_set_batch_row_mode(-1)
+    for f, r in zip(dev, res):
+        _same(r, _single(ctx, f))
+
+
 def test_batch_graph_replay_follows_data(ctx, torch_cuda):
     frames = scenes.batch_scenes(4, 5, small=True)
     dev, _ = _device_frames(torch_cuda, frames)
@@ -116,6 +135,8 @@ def test_batch_rejects_bad_frames(ctx, torch_cuda):
     with pytest.raises(gh.GhError) as e:
         ctx.gh_set_batch_tile(12)
     assert e.value.status == gh.GH_EINVAL
+    with pytest.raises(gh.GhError):
+        ctx.gh_set_batch_row_mode(2)
 
 
 def test_uneven_256_frame_workload_sampled(ctx, torch_cuda):
