@@ -118,8 +118,22 @@ int class_bound(int q_nd) {
     return b;
 }
 
+constexpr int kMaxClasses = 256;  // scorer classes of a batch (shared-memory bound x run x lane layout: far fewer)
+constexpr int kSideStreams = 4;  // streams the scorer classes of one iteration run on side by side
+
 // Context-side state of the batch path (one per context).
 struct BatchState {
+    // side streams and events of the scorer classes' fork and join (created on
+    // first use, released with the state)
+    cudaStream_t side[kSideStreams] = {};
+    cudaEvent_t fork = nullptr, join[kSideStreams] = {};
+    ~BatchState() {
+        for (int i = 0; i < kSideStreams; ++i) {
+            if (side[i]) cudaStreamDestroy(side[i]);
+            if (join[i]) cudaEventDestroy(join[i]);
+        }
+        if (fork) cudaEventDestroy(fork);
+    }
     Plan plan;
     bool plan_valid = false;
     int force_ac = 0, force_warps = 0;
@@ -228,7 +242,7 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
     const size_t keys_off = o;
     o += align256(okeys);
     const size_t counter_off = o;
-    o += 256;
+    o += kMaxClasses * sizeof(unsigned);  // work counters, one per scorer class
     void* big;
     GH_TRY(gh_ws(ctx, WS_BATCH, o, &big));
     char* B = (char*)big;
@@ -267,6 +281,8 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
         c.layout_ac = std::get<2>(kv.first);
         P.classes.push_back(c);
     }
+    if ((int)P.classes.size() > kMaxClasses)
+        return gh_fail(ctx, GH_ENOTSUP, "batch: %zu scorer classes, at most %d", P.classes.size(), kMaxClasses);
     std::vector<std::vector<int>> class_frames(P.classes.size());
     std::vector<std::vector<int>> active(P.Kmax);
     std::vector<std::vector<BatchItem>> defl(P.Kmax);
@@ -424,7 +440,53 @@ int reset_frames(gh_ctx* ctx, const Plan& P) {
     return gh_launch_batch_reset(ctx, P.frames, P.nframes);
 }
 
-int batch_sequence(gh_ctx* ctx, const Plan& P, const std::vector<Tuning>& t, void** h) {
+int side_streams(gh_ctx* ctx, BatchState* S) {
+    for (int i = 0; i < kSideStreams; ++i) {
+        if (!S->side[i]) GH_CUDA(cudaStreamCreateWithFlags(&S->side[i], cudaStreamNonBlocking));
+        if (!S->join[i]) GH_CUDA(cudaEventCreateWithFlags(&S->join[i], cudaEventDisableTiming));
+    }
+    if (!S->fork) GH_CUDA(cudaEventCreateWithFlags(&S->fork, cudaEventDisableTiming));
+    return GH_OK;
+}
+
+// The scorer launches of iteration k, one per class, each with its own work
+// counter. Without kernel timers they run on side streams after a fork from
+// the context's stream and are joined back (graph branches when captured):
+// the classes score disjoint frames, and a class's first CTAs fill the SMs
+// the previous class's last items leave idle.
+int score_classes(gh_ctx* ctx, BatchState* S, const Plan& P, const std::vector<Tuning>& t, int k) {
+    const int nc = (int)P.classes.size();
+    auto launch = [&](int c) {
+        const Plan::ScoreClass& C = P.classes[c];
+        return gh_launch_hop_batch(ctx, P.frames, C.items[t[c].tile], C.n[t[c].tile][k], P.counter + c, k, t[c].ac,
+                                   t[c].warps, t[c].per_rx, C.max_nd, C.bound, C.max_q);
+    };
+    if (ctx->timing != 0 || nc < 2) {
+        for (int c = 0; c < nc; ++c) GH_TRY(launch(c));
+        return GH_OK;
+    }
+    GH_TRY(side_streams(ctx, S));
+    cudaStream_t main = ctx->stream;
+    GH_CUDA(cudaEventRecord(S->fork, main));
+    int st = GH_OK;
+    for (int c = 0; c < nc && st == GH_OK; ++c) {
+        cudaStream_t s = S->side[c % kSideStreams];
+        if (c < kSideStreams && cudaStreamWaitEvent(s, S->fork, 0) != cudaSuccess) {
+            st = gh_fail(ctx, GH_ECUDA, "fork of the scorer classes failed");
+            break;
+        }
+        ctx->stream = s;
+        st = launch(c);
+        ctx->stream = main;
+    }
+    for (int i = 0; i < kSideStreams && i < nc; ++i) {  // join (also after a failed launch)
+        GH_CUDA(cudaEventRecord(S->join[i], S->side[i]));
+        GH_CUDA(cudaStreamWaitEvent(main, S->join[i], 0));
+    }
+    return st;
+}
+
+int batch_sequence(gh_ctx* ctx, BatchState* S, const Plan& P, const std::vector<Tuning>& t, void** h) {
     GH_TRY(reset_frames(ctx, P));
     GH_TRY(gh_launch_coord_batch(ctx, P.frames, P.coord_items, P.n_coord));
     for (int k = 0; k < P.Kmax; ++k) {
@@ -433,11 +495,7 @@ int batch_sequence(gh_ctx* ctx, const Plan& P, const std::vector<Tuning>& t, voi
                                         P.dop_items, P.n_dop, P.thr_dop, P.smem_dop, 0));
         else  // maps of the residuals by linearity, frames still iterating
             GH_TRY(gh_launch_maps_deflate_batch(ctx, P.frames, P.defl_items[k], P.n_defl[k], k));
-        for (size_t c = 0; c < P.classes.size(); ++c) {
-            const Plan::ScoreClass& C = P.classes[c];
-            GH_TRY(gh_launch_hop_batch(ctx, P.frames, C.items[t[c].tile], C.n[t[c].tile][k], P.counter, k,
-                                       t[c].ac, t[c].warps, t[c].per_rx, C.max_nd, C.bound, C.max_q));
-        }
+        GH_TRY(score_classes(ctx, S, P, t, k));
         GH_TRY(gh_launch_bomp_select_batch(ctx, P.frames, P.active[k], P.n_active[k], k));
         GH_TRY(gh_launch_bomp_corr_batch(ctx, P.frames, P.active[k], P.n_active[k], k, P.max_chunks, P.max_q));
     }
@@ -586,7 +644,7 @@ extern "C" int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* fra
     const char tag[] = "batch";
     gkey.insert(gkey.begin(), tag, tag + sizeof(tag));
     void* h = nullptr;
-    const GhSequence seq = [&](void** out) { return batch_sequence(ctx, P, t, out); };
+    const GhSequence seq = [&](void** out) { return batch_sequence(ctx, S, P, t, out); };
     GH_TRY(gh_run_sequence(ctx, ctx->graphs ? &gkey : nullptr, seq, &h));
     // unpack: per frame ArgResult[K] then double2[K][Q]
     size_t oc = 0, oa = 0;
