@@ -62,6 +62,7 @@ struct Plan {
         // needs ac >= pr_need
         int pr_need = 0;
         int layout_ac = 0;  // 6 or 10: the 8 x 4 lane layout fits the class's frames best
+        int layout_run = 0;  // largest ceil(nvx / 4): cells per vy row and lane in the 8 x 4 layout
         double work = 0.0;                    // cell * receiver * iteration evals
         // per tile size: the class's items, frames in decreasing K (so the
         // items of the frames still iterating at k are a prefix), and per k
@@ -305,6 +306,7 @@ int build_plan(gh_ctx* ctx, int nframes, const gh_frame* frames, Plan& P) {
         const int cls = class_of_key[class_key(d)];
         P.classes[cls].max_q = std::max(P.classes[cls].max_q, d.Q);
         P.classes[cls].max_nd = std::max(P.classes[cls].max_nd, d.Nd);
+        P.classes[cls].layout_run = std::max(P.classes[cls].layout_run, (d.nvx + 3) / 4);
         {
             const int NB = d.nvy < 32 ? d.nvy : 32, SA = 32 / NB;
             const int cells = d.nvy <= 32 ? (d.nvx + SA - 1) / SA : (1 << 20);
@@ -550,14 +552,16 @@ int autotune(gh_ctx* ctx, const Plan& P, const Plan::ScoreClass& C, int tile, in
     const int t0 = tile >= 0 ? tile : kDefaultTile;
     // one row at a time where it applies and is wanted; all rows otherwise
     // (also when one row at a time is asked for but applies to no configuration)
-    const bool pr_any = rm != 0 && C.pr_need <= 32;
+    const bool pr_any = rm != 0 && (C.pr_need <= 32 || (C.layout_ac && C.layout_run <= C.layout_ac));
     for (int ac : {8, 16, 32, 6, 10}) {
         if ((ac == 6 || ac == 10) && ac != C.layout_ac) continue;
         for (int warps : {8, 4, 2}) {
             if (st == GH_OK && (rm != 1 || !pr_any) &&
                 gh_hop_batch_warp_bytes(ac, C.bound, C.max_q) * warps <= ctx->smem_optin)
                 time_one({ac, warps, t0, false});
-            if (st == GH_OK && rm != 0 && ac >= 8 && ac >= C.pr_need &&
+            // one row at a time: one run per lane (standard layout) or per vy row (8 x 4 layout)
+            const bool pr_ok = (ac == 6 || ac == 10) ? C.layout_run <= ac : ac >= C.pr_need;
+            if (st == GH_OK && rm != 0 && pr_ok &&
                 gh_hop_batch_warp_bytes(ac, C.max_nd, C.max_q) * warps <= ctx->smem_optin)
                 time_one({ac, warps, t0, true});
         }

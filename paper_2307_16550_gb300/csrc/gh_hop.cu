@@ -452,17 +452,37 @@ __device__ __forceinline__ void score_xy(const void* __restrict__ maps, const Ho
         return hm;
     };
     if constexpr (PR) {
-        float acc[AC];
-#pragma unroll
-        for (int i = 0; i < AC; ++i) acc[i] = 0.f;
-        for (int q = 0; q < p.Q; ++q) {
-            build_row<MT>(maps, p, E[q], q, P, lane);
-            __syncwarp();  // row q complete
-            if (active) score_run_q<AC>(p, E[q], P, ta, tb, acc, fix);
-            __syncwarp();  // reads of row q done
-        }
+        // the 8 x 4 lane layout (AC = 6, 10) gives a lane one run per vy row
+        // it takes; G rows' runs per pass (the rows are rebuilt per pass)
+        constexpr int G = (AC == 6 || AC == 10) ? 3 : 1;
+        const int nrows = (p.nvy + p.NB - 1) / p.NB;
         const bool hm = has_mask();
-        if (active) finish_run<AC>(p, acc, xy * p.nv, ta, tb, scores, mask, nmask, hm, best, bestc);
+        for (int r0 = 0; r0 < nrows; r0 += G) {
+            float acc[G][AC];
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int i = 0; i < AC; ++i) acc[g][i] = 0.f;
+            for (int q = 0; q < p.Q; ++q) {
+                build_row<MT>(maps, p, E[q], q, P, lane);
+                __syncwarp();  // row q complete
+                if (active) {
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        const int b = tb + p.NB * (r0 + g);
+                        if (b < p.nvy) score_run_q<AC>(p, E[q], P, ta, b, acc[g], fix);
+                    }
+                }
+                __syncwarp();  // reads of row q done
+            }
+            if (active) {
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const int b = tb + p.NB * (r0 + g);
+                    if (b < p.nvy) finish_run<AC>(p, acc[g], xy * p.nv, ta, b, scores, mask, nmask, hm, best, bestc);
+                }
+            }
+        }
     } else {
         for (int q = 0; q < p.Q; ++q) build_row<MT>(maps, p, E[q], q, P + (size_t)q * p.Nd, lane);
         const bool hm = has_mask();
@@ -970,13 +990,10 @@ int gh_launch_hop_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* 
     GH_BATCH_CASE(8)
     GH_BATCH_CASE(16)
     GH_BATCH_CASE(32)
+    GH_BATCH_CASE(6)
+    GH_BATCH_CASE(10)
 #undef GH_BATCH_CASE
-    if (!per_rx && ac == 6)
-        return hop_batch_launch<6, false>(ctx, frames, items, n, counter, k, warps, max_nd, max_q_nd, max_q);
-    if (!per_rx && ac == 10)
-        return hop_batch_launch<10, false>(ctx, frames, items, n, counter, k, warps, max_nd, max_q_nd, max_q);
-    return gh_fail(ctx, GH_EINVAL, "batched scorer: cells per lane %d not in {8, 16, 32} (or 6, 10 with all rows)",
-                   ac);
+    return gh_fail(ctx, GH_EINVAL, "batched scorer: cells per lane %d not in {6, 8, 10, 16, 32}", ac);
 }
 
 size_t gh_hop_batch_warp_bytes(int ac, int row_floats, int max_q) { return hop_batch_warp_bytes(ac, row_floats, max_q); }
