@@ -104,6 +104,27 @@ def test_power_row_modes_give_single_frame_results(ctx, torch_cuda, row_mode):
         _same(r, _single(ctx, f))
 
 
+@pytest.mark.parametrize("row_mode", [-1, 0, 1])
+def test_uneven_velocity_axes_give_single_frame_results(ctx, torch_cuda, row_mode):
+    """Velocity grids with unequal and odd axes (partial runs in the 8 x 4
+    lane layout, a lane's vy rows over several one-row passes, runs past the
+    vx edge): the same results as gh_detect, bit for bit, in every row mode."""
+    shapes = [(22, 24), (40, 37), (24, 7), (37, 40), (13, 40), (40, 9), (6, 24), (31, 17)]
+    frames = []
+    for i, (nvx, nvy) in enumerate(shapes):
+        radar = scenes.Radar(24e9, 250e6, 128e-6, 64 << (i % 3), 32 << (i % 2), 4)
+        grid = scenes.Grid.from_bounds((0, 0, -15, -15), (40, 40, 15, 15), (12 + i, 10 + 2 * i, nvx, nvy))
+        frames.append(scenes.custom_scene(60 + i, radar, grid, Q=3 + i % 6, T=1 + i % 3, snr_db=10.0))
+    dev, _ = _device_frames(torch_cuda, frames, synth_ctx=ctx)
+    ctx.gh_set_batch_row_mode(row_mode)
+    try:
+        res = ctx.gh_detect_batch(dev)
+    finally:
+        ctx.gh_set_batch_row_mode(-1)
+    for f, r in zip(dev, res):
+        _same(r, _single(ctx, f))
+
+
 def test_batch_graph_replay_follows_data(ctx, torch_cuda):
     frames = scenes.batch_scenes(4, 5, small=True)
     dev, _ = _device_frames(torch_cuda, frames)
