@@ -90,29 +90,6 @@ struct Tuning {
     bool per_rx = false;                         // one receiver's power row at a time
 };
 
-// Scoring slots per lane (cells, partial runs included) of frame d with AC
-// cells per run: lanes b = lane % NB, a = lane / NB; NB = min(nvy, 32) for
-// AC = 8, 16, 32 and NB = 8 (SA = 4) for AC = 6, 10 (the scorer's layouts).
-int lane_slots(const Dims& d, int ac) {
-    const int NB = (ac == 6 || ac == 10) ? 8 : (d.nvy < 32 ? d.nvy : 32), SA = 32 / NB;
-    const int rows = (d.nvy + NB - 1) / NB, cells = (d.nvx + SA - 1) / SA;
-    return rows * ((cells + ac - 1) / ac) * ac;
-}
-
-// 6 or 10 when the 8 x 4 layout with that many cells per run needs fewer
-// slots than every standard configuration, else 0.
-int lane_layout_ac(const Dims& d) {
-    int best = 0, best_slots = 1 << 30;
-    for (int ac : {8, 16, 32, 6, 10}) {
-        const int sl = lane_slots(d, ac);
-        if (sl < best_slots) {
-            best_slots = sl;
-            best = ac;
-        }
-    }
-    return (best == 6 || best == 10) ? best : 0;
-}
-
 int class_bound(int q_nd) {
     int b = 1024;
     while (b < q_nd) b <<= 1;

@@ -655,6 +655,25 @@ int hop_launch_mt(cudaStream_t stream, const Dims& d, const HopParams& hp, const
     // cells per lane and run: at most 16 (a lane takes several runs when the
     // velocity axis is longer); measured faster than 32 on the paper-shaped
     // frame (82 against 86 us per launch) at the same occupancy
+    // lanes 8 (vy) x 4 (vx) with 6 or 10 cells per run where that fills the
+    // runs best (velocity axes of 24 or 40 cells); one receiver's row at a
+    // time when the rows of all receivers would leave fewer than eight warps
+    // per CTA and each vy row of a lane is one run
+    const int lay = lane_layout_ac(d);
+    if (lay) {
+        HopParams h8 = hp;
+        h8.NB = 8;
+        h8.SA = 4;
+        const bool pr8 = (d.nvx + 3) / 4 <= lay && hop_warp_bytes(d, lay, false) * 8 > (100 << 10);
+#define GH_HOP_LAYOUT(N)                                                                                          \
+    return pr8 ? hop_launch_t<N, MT, true>(stream, d, h8, maps, table, scores, mask, nmask, parts, max_ctas,      \
+                                           num_sms, smem_optin, nparts)                                          \
+               : hop_launch_t<N, MT, false>(stream, d, h8, maps, table, scores, mask, nmask, parts, max_ctas,     \
+                                            num_sms, smem_optin, nparts);
+        if (lay == 6) GH_HOP_LAYOUT(6)
+        GH_HOP_LAYOUT(10)
+#undef GH_HOP_LAYOUT
+    }
     const int full = (d.nvx + hp.SA - 1) / hp.SA;
     const int need = std::min(full, 16);
     // one receiver's row at a time when the lane's cells form one run and the

@@ -494,6 +494,29 @@ int gh_launch_maps_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem*
                          size_t smem_dop, int k);
 // Scorer and coordinate-table parameters of one frame.
 void gh_hop_frame_params(const Dims& d, const GeoParams& g, HopParams* hp, CoordParams* cp);
+// Scoring slots per lane (cells, partial runs included) of frame d with AC
+// cells per run: lanes b = lane % NB, a = lane / NB; NB = min(nvy, 32) for
+// AC = 8, 16, 32 and NB = 8 (SA = 4) for AC = 6, 10 (the scorer's layouts).
+inline int lane_slots(const Dims& d, int ac) {
+    const int NB = (ac == 6 || ac == 10) ? 8 : (d.nvy < 32 ? d.nvy : 32), SA = 32 / NB;
+    const int rows = (d.nvy + NB - 1) / NB, cells = (d.nvx + SA - 1) / SA;
+    return rows * ((cells + ac - 1) / ac) * ac;
+}
+
+// 6 or 10 when the 8 x 4 layout with that many cells per run needs fewer
+// slots than every standard configuration, else 0.
+inline int lane_layout_ac(const Dims& d) {
+    int best = 0, best_slots = 1 << 30;
+    for (int ac : {8, 16, 32, 6, 10}) {
+        const int sl = lane_slots(d, ac);
+        if (sl < best_slots) {
+            best_slots = sl;
+            best = ac;
+        }
+    }
+    return (best == 6 || best == 10) ? best : 0;
+}
+
 // Shared memory of one batched-scorer warp whose power rows hold at most
 // row_floats floats (Q * Nd, or Nd with one receiver's row at a time).
 size_t gh_hop_batch_warp_bytes(int ac, int row_floats, int max_q);

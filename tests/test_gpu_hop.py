@@ -139,3 +139,34 @@ def test_one_row_at_a_time_and_all_rows_agree_bit_for_bit(ctx, torch_cuda):
     s_small, _, _ = ctx.scores(small.radar, small.tx, small.rx, maps, small.grid)
     s_big, _, _ = ctx.scores(big.radar, big.tx, big.rx, maps, big.grid)
     np.testing.assert_array_equal(s_small.cpu().numpy(), s_big.cpu().numpy()[:, :, :, :16])
+
+
+@pytest.mark.parametrize("Q,Mc,nv", [(4, 64, (40, 37)), (3, 64, (24, 24)), (8, 256, (40, 40)), (8, 256, (22, 24))])
+def test_wide_velocity_axes_match_oracle(ctx, torch_cuda, Q, Mc, nv):
+    """Velocity axes of 22..40 cells take the 8 x 4 lane layout (6 or 10 cells
+    per run); with Q = 8, Nd = 1024 the scorer also builds one receiver's row
+    at a time. Every score against the oracle."""
+    radar = scenes.Radar(24e9, 250e6, 128e-6, 32, Mc, 4)
+    grid = scenes.Grid.from_bounds((2, 3, -15, -15), (38, 36, 15, 15), (5, 4) + nv)
+    sc = scenes.custom_scene(41 + Q, radar, grid, Q=Q, T=2, snr_db=10.0)
+    Y32, Y = measurement64(sc)
+    ref = hopping.hop_scores(omaps.rd_maps(Y, 4), sc.radar, sc.tx, sc.rx, sc.grid)
+    got, cell, _ = ctx.scores(sc.radar, sc.tx, sc.rx, ctx.maps(sc.radar, to_dev(torch_cuda, Y32)), sc.grid)
+    assert rel_err(got.cpu().numpy(), ref) < TOL
+    if top2_margin(ref) > 10 * TOL:
+        assert cell == hopping.argmax_cell(ref)
+
+
+def test_lane_layouts_agree_bit_for_bit(ctx, torch_cuda):
+    """A 24 x 24 velocity grid (8 x 4 lane layout, 6 cells per run) and the
+    24 x 32 grid with the same origin and steps (standard layout): equal
+    scores on the shared cells, bit for bit."""
+    radar = scenes.Radar(24e9, 250e6, 128e-6, 32, 64, 4)
+    mk = lambda nvy: scenes.Grid((0.0, 0.0, -15.0, -15.0), (5.0, 4.0, 1.25, 1.25), (6, 7, 24, nvy))
+    small = scenes.custom_scene(51, radar, mk(24), Q=4, T=2, snr_db=10.0)
+    big = scenes.custom_scene(51, radar, mk(32), Q=4, T=2, snr_db=10.0)
+    Y32, _ = measurement64(small)
+    maps = ctx.maps(radar, to_dev(torch_cuda, Y32))
+    s_small, _, _ = ctx.scores(radar, small.tx, small.rx, maps, small.grid)
+    s_big, _, _ = ctx.scores(radar, big.tx, big.rx, maps, big.grid)
+    np.testing.assert_array_equal(s_small.cpu().numpy(), s_big.cpu().numpy()[:, :, :, :24])
