@@ -267,20 +267,24 @@ typedef struct {
 /*
  * gh_detect_batch - gh_detect with grid hopping (GH_HOP, complex float32
  * maps) for nframes independent frames of any sizes, each step launched once
- * for the whole batch (coordinate tables, maps, persistent scorers whose
- * warps take (frame, cells) work items from a shared counter, one per group
- * of frames with the same shared-memory need, BOMP selection and
- * correlation); frames whose K is reached drop out of later iterations.
+ * for the whole batch (coordinate tables, maps of the rows the tables read,
+ * persistent scorers whose warps take (frame, cells) work items from a
+ * counter, one per group of frames with the same shared-memory need, lane
+ * layout and run shape, the groups of an iteration side by side, BOMP
+ * selection and correlation); frames whose K is reached drop out of later
+ * iterations.
  * Each frame's results equal those of gh_detect on that frame. Outputs are
  * concatenated in frame order:
  *   cells_host  : host int64[sum K]
  *   scores_host : host float[sum K] (may be NULL)
  *   alpha_host  : host double[sum K*Q][2] (may be NULL), per frame [K][Q][2]
- * Each scorer group's cells per lane, warps per CTA and (x, y) cells per work
- * item are chosen by timing the candidates on the first iteration of a batch
- * shape (cached in the context), unless fixed with gh_set_batch_tuning and
- * gh_set_batch_tile. From the second call with an
- * unchanged batch on, the whole sequence is a replayed CUDA graph.
+ * Each scorer group's cells per lane (8, 16, 32, or 6 and 10 in the 8 x 4
+ * lane layout for velocity axes of about 24 and 40 cells), warps per CTA,
+ * power-row mode and (x, y) cells per work item are chosen by timing the
+ * candidates on the first iteration of a batch shape (cached in the context),
+ * unless fixed with gh_set_batch_tuning, gh_set_batch_row_mode and
+ * gh_set_batch_tile. From the second call with an unchanged batch on, the
+ * whole sequence is a replayed CUDA graph.
  */
 GH_API int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* frames, int64_t* cells_host,
                     float* scores_host, double* alpha_host);
@@ -288,7 +292,7 @@ GH_API int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* frames,
  * warps per CTA in {2, 4, 8}; (0, 0) returns to autotuning (the default). */
 GH_API int gh_set_batch_tuning(gh_ctx* ctx, int32_t cells_per_lane, int32_t warps);
 /* The configuration the last gh_detect_batch call used for its scorer group
- * with the most work. */
+ * with the most work (cells per lane 6 and 10: the 8 x 4 lane layout). */
 GH_API int gh_batch_tuning(gh_ctx* ctx, int32_t* cells_per_lane, int32_t* warps);
 /* Fixes the number of consecutive (x, y) cells in one work item of the
  * batched scorer: 4, 8, 16 or 32; 0 returns to tuning (the default: after the
@@ -302,10 +306,11 @@ GH_API int gh_set_batch_tile(gh_ctx* ctx, int32_t cells_per_item);
 GH_API int gh_batch_tile(gh_ctx* ctx, int32_t* cells_per_item);
 /* Whether the last gh_detect_batch call's scorer group with the most work
  * built one receiver's Doppler power row at a time (1) or the rows of all its
- * receivers at once (0). One row at a time needs a warp's velocity cells per
- * lane to fit one run (nvy <= 32), and leaves room for more warps per SM when
- * Q * Nd is large; the autotuner times both where both apply (a
- * configuration fixed with gh_set_batch_tuning builds all rows at once). */
+ * receivers at once (0). One row at a time needs a lane's velocity cells to
+ * fit one run per vy row it takes (nvy <= 32, or the 8 x 4 layout), and
+ * leaves room for more warps per SM when Q * Nd is large; the autotuner times
+ * both where both apply (a configuration fixed with gh_set_batch_tuning
+ * builds all rows at once). */
 GH_API int gh_batch_row_mode(gh_ctx* ctx, int32_t* per_receiver);
 /* Keeps the autotuner to one power-row mode: 0 all receivers' rows, 1 one
  * receiver's row at a time (for the scorer groups where it applies; all rows
