@@ -1,7 +1,7 @@
 // Grid-hopping score (Sec. IV, Eq. 5) over the 4D grid, its argmax, and the
 // coordinate mapping it needs (Eq. 1).
 //
-// coord_kernel (one thread per (x, y, q), float64):
+// coord_kernel (two threads per (x, y), each every other receiver, float64):
 //   rho = Nr * r_q(x), i = floor(rho + 1/2), tau = rho - i, the three polar
 //   coefficients c_k(tau) on rows (i + k) mod Nr (signed by the centring phase
 //   of a wrapped index), and the Doppler bin position as 64-bit fixed point:
@@ -13,9 +13,14 @@
 //   For a fixed (x, y, q) the hopping value at Doppler bin j is
 //   T_q[j] = sum_k c_k Z~_q[i+k][j], and the cell's contribution is |T_q[j_q]|^2.
 //   The warp first evaluates P_q[j] = |T_q[j]|^2 into its own shared-memory
-//   rows (indexed by absolute Doppler bin) for the bins the velocity grid
-//   reaches, reading the three map rows with 16-byte loads; then each lane
-//   scores up to 32 velocity cells, one shared-memory read per receiver.
+//   rows (indexed relative to j_ref) for the bins the velocity grid reaches,
+//   reading the three map rows with 16-byte loads (a pair of float32 bins, or
+//   four 16-bit bins, per load); then each lane scores its velocity cells in
+//   runs of AC, one shared-memory read per cell and receiver. Row modes: the
+//   rows of all receivers first, or (large Q Nd, one run per vy row of a
+//   lane) one receiver's row at a time added into register sums. Lane
+//   layouts: b = lane mod min(nvy, 32), or 8 (vy) x 4 (vx) lanes with 6 or 10
+//   cells per run for velocity axes of about 24 or 40 cells.
 //   The bin j_q = floor(eta + 1/2) is the high word of the fixed-point value;
 //   when its fraction lies within `tol` of a rounding boundary the bin is
 //   recomputed with the float64 expression floor(Nd * (kappa * (wx*vx + wy*vy)) + 1/2),
