@@ -1,13 +1,16 @@
 // gh_detect_batch: the grid-hopping detect-and-deflate loop of gh_detect
 // (Sec. IV scores, BOMP iterations) over many independent frames of uneven
 // size at once. Every step is one launch for the whole batch:
-//   coordinate tables         coord_batch_kernel       (once)
+//   coordinate tables         coord_batch_kernel       (once; also each frame's
+//                             map row limits)
 //   per iteration k:
 //     maps                    k = 0: range_fft_batch_kernel, doppler_fft_batch_kernel;
 //                             k > 0: maps_deflate_batch_kernel (the residual's
-//                             maps by linearity, as gh_detect does)
-//     scores + argmax         hop_batch_kernel (persistent; warps take work
-//                             items from a counter; per-frame packed argmax)
+//                             maps by linearity, as gh_detect does); rows
+//                             outside the row limits are skipped
+//     scores + argmax         hop_batch_kernel, one launch per scorer class
+//                             (persistent; warps take work items from the
+//                             class's counter; per-frame packed argmax)
 //     selection, new atom     bomp_select_batch_kernel (one CTA per frame)
 //     correlation + solve     bomp_corr_batch_kernel
 //   results                   batch_gather_kernel + one copy to the host
@@ -15,12 +18,16 @@
 // the kernels of the single-frame path on the same data in the same order, so
 // its results are those of gh_detect bit for bit.
 //
-// Frames are grouped by the shared memory a scorer warp needs (Q * Nd rounded
-// up to a power of two); each group has its own scorer launch per iteration,
-// whose cells per lane and warps per CTA are picked by timing the candidates
-// on the group's first iteration (once per batch shape, cached in the
-// context) unless set with gh_set_batch_tuning. The whole sequence is a
-// CUDA graph from the second call with an unchanged batch on (gh_run_sequence).
+// Frames are classed by the shared memory a scorer warp needs (Q * Nd rounded
+// up to a power of two), by whether a lane's velocity cells form one run (the
+// one-receiver-row mode's condition) and by the lane layout that fits their
+// velocity axes best; each class has its own scorer launch per iteration
+// (the classes of an iteration on side streams), whose cells per lane, warps
+// per CTA, row mode and cells per work item are picked by timing the
+// candidates on the class's first iteration (once per batch shape, cached in
+// the context) unless fixed with gh_set_batch_tuning, gh_set_batch_row_mode
+// and gh_set_batch_tile. The whole sequence is a CUDA graph from the second
+// call with an unchanged batch on (gh_run_sequence).
 #include <string.h>
 
 #include <algorithm>
