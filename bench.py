@@ -52,7 +52,7 @@ L2_PROBE_REPS = 200
 # One hop_score_kernel launch on this workload, from an ncu capture (summarised
 # under profiles/), valid while the scorer's sources hash to the key: DRAM
 # bytes (read + write), warp instructions issued, and L2-to-SM read bytes.
-HOP_NCU = {"20b19e75f2f548ad": {"dram": 10251947, "inst": 49124666, "l2_to_sm": 443536064}}
+HOP_NCU = {"eff03bd6c416a529": {"dram": 10253483, "inst": 49124666, "l2_to_sm": 442942944}}
 
 
 def _hop_source_hash():
@@ -585,7 +585,8 @@ def batch_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args):
             "value": units / (ms_batch * 1e-3), "unit": UNIT, "ms_per_step": ms_batch,
             "evals_per_step": units, "maps_gb": maps_gb,
             "tuning": {"cells_per_lane": tuning[0], "warps_per_cta": tuning[1], "xy_cells_per_item": tile,
-                       "power_rows": "one receiver at a time" if row_mode else "all receivers",
+                       "power_rows": ("all receivers", "one receiver at a time",
+                                      "all receivers, two warps per (x, y) cell")[row_mode],
                        "of": "the scorer group with the most work"},
             "one_by_one": {"value": units / (ms_seq * 1e-3), "ms_per_step": ms_seq,
                            "how": "256 gh_detect calls (each a replayed graph)"}}

@@ -8,7 +8,7 @@
 //                             k > 0: maps_deflate_batch_kernel (the residual's
 //                             maps by linearity, as gh_detect does); rows
 //                             outside the row limits are skipped
-//     scores + argmax         hop_batch_kernel, one launch per scorer class
+//     scores + argmax         hop_batch_kernel or hop_pair_kernel, one launch per class
 //                             (persistent; warps take work items from the
 //                             class's counter; per-frame packed argmax)
 //     selection, new atom     bomp_select_batch_kernel (one CTA per frame)
@@ -23,7 +23,9 @@
 // one-receiver-row mode's condition) and by the lane layout that fits their
 // velocity axes best; each class has its own scorer launch per iteration
 // (the classes of an iteration on side streams), whose cells per lane, warps
-// per CTA, row mode and cells per work item are picked by timing the
+// per CTA, row mode (all receivers' rows, one receiver's row at a time, or
+// all rows shared by two warps per (x, y) cell: hop_pair_kernel) and cells
+// per work item are picked by timing the
 // candidates on the class's first iteration (once per batch shape, cached in
 // the context) unless fixed with gh_set_batch_tuning, gh_set_batch_row_mode
 // and gh_set_batch_tile. The whole sequence is a CUDA graph from the second
@@ -123,7 +125,7 @@ struct BatchState {
     bool plan_valid = false;
     int force_ac = 0, force_warps = 0;
     int force_tile = -1;  // index into kTiles, -1: tuned
-    int force_rm = -1;    // row mode the autotuner keeps to (0 all rows, 1 one row at a time), -1: either
+    int force_rm = -1;    // row mode the autotuner keeps to (0 all rows, 1 one row at a time, 2 paired), -1: any
     Tuning last;                                         // of the class with the most work
     std::map<std::vector<unsigned char>, Tuning> tuned;  // per batch shape and class
 };
@@ -505,9 +507,11 @@ int autotune_prepare(gh_ctx* ctx, const Plan& P) {
 // fastest configuration: cells per lane (8, 16, 32, and 6 or 10 in the 8 x 4
 // lane layout for classes it fits) x warps per CTA (8, 4, 2, as shared memory
 // allows) x power rows of all receivers or of one receiver at a time (where
-// every frame's cells of a lane form one run), with 8-cell
-// items, then, for that configuration, items of 4, 8, 16 and 32 (x, y) cells
-// (`tile` >= 0 fixes the item size).
+// every frame's cells of a lane form one run), and, for the 8 x 4 layout's
+// classes, the paired scorer (two warps per (x, y) cell, 3 or 5 cells per
+// lane), with 8-cell items, then, for that configuration, items of 4, 8, 16
+// and 32 (x, y) cells (`tile` >= 0 fixes the item size). rm: the row mode
+// kept to (-1 any, 0 all rows, 1 one row at a time, 2 paired).
 int autotune(gh_ctx* ctx, const Plan& P, const Plan::ScoreClass& C, int tile, int rm, Tuning* best) {
     cudaEvent_t a, b;
     GH_CUDA(cudaEventCreate(&a));
@@ -534,10 +538,17 @@ int autotune(gh_ctx* ctx, const Plan& P, const Plan::ScoreClass& C, int tile, in
         }
     };
     const int t0 = tile >= 0 ? tile : kDefaultTile;
+    // two warps per (x, y) cell: classes in the 8 x 4 layout whose rows fit
+    // one CTA; where it is asked for but does not apply, all rows
+    const bool pair_ok =
+        C.layout_ac != 0 && gh_hop_pair_bytes(C.layout_ac / 2, C.bound, C.max_q) <= ctx->smem_optin;
+    if (rm == 2 && !pair_ok) rm = 0;
+    if (st == GH_OK && pair_ok && (rm == -1 || rm == 2)) time_one({C.layout_ac / 2, 2, t0, false});
     // one row at a time where it applies and is wanted; all rows otherwise
     // (also when one row at a time is asked for but applies to no configuration)
     const bool pr_any = rm != 0 && (C.pr_need <= 32 || (C.layout_ac && C.layout_run <= C.layout_ac));
     for (int ac : {8, 16, 32, 6, 10}) {
+        if (rm == 2) break;
         if ((ac == 6 || ac == 10) && ac != C.layout_ac) continue;
         for (int warps : {8, 4, 2}) {
             if (st == GH_OK && (rm != 1 || !pr_any) &&
@@ -689,14 +700,16 @@ extern "C" int gh_set_batch_tile(gh_ctx* ctx, int32_t cells_per_item) {
 
 extern "C" int gh_set_batch_row_mode(gh_ctx* ctx, int32_t row_mode) {
     if (!ctx) return GH_EINVAL;
-    if (row_mode < -1 || row_mode > 1) return gh_fail(ctx, GH_EINVAL, "row mode %d: -1 (tuned), 0 or 1", row_mode);
+    if (row_mode < -1 || row_mode > 2)
+        return gh_fail(ctx, GH_EINVAL, "row mode %d: -1 (tuned), 0, 1 or 2", row_mode);
     state_of(ctx)->force_rm = row_mode;
     return GH_OK;
 }
 
 extern "C" int gh_batch_row_mode(gh_ctx* ctx, int32_t* per_receiver) {
     if (!ctx || !per_receiver) return GH_EINVAL;
-    *per_receiver = state_of(ctx)->last.per_rx ? 1 : 0;
+    const Tuning& t = state_of(ctx)->last;
+    *per_receiver = t.per_rx ? 1 : (t.ac == 3 || t.ac == 5) ? 2 : 0;
     return GH_OK;
 }
 

@@ -271,8 +271,9 @@ __device__ __forceinline__ float2 unpack_bin(uint32_t w) {
 }
 
 // Power row P_q[u] = |T_q[u]|^2 (u relative to j_ref) of receiver q, with
-// staged entry eq, into Pq: one warp.
-template <int MT>
+// staged entry eq, into Pq: NL lanes (one warp, or the two warps of a pair;
+// `lane` in [0, NL)).
+template <int MT, int NL = 32>
 __device__ __forceinline__ void build_row(const void* __restrict__ maps, const HopParams& p, const HopEntry& eq,
                                           int q, float* Pq, int lane) {
     const int ndm = p.Nd - 1;
@@ -286,11 +287,11 @@ __device__ __forceinline__ void build_row(const void* __restrict__ maps, const H
     constexpr int U = GH_HOP_U;  // row loads in flight per lane
     if constexpr (MT == GH_C64) {
         // pairs of bins: one 16-byte load per row and pair
-        for (int pp0 = 0; pp0 < npair; pp0 += 32 * U) {
+        for (int pp0 = 0; pp0 < npair; pp0 += NL * U) {
             float4 z0[U], z1[U], z2[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int pp = pp0 + lane + 32 * u;
+                const int pp = pp0 + lane + NL * u;
                 if (pp < npair) {
                     const int jh = ((j_ref + 2 * pp) & ndm) >> 1;  // pair of absolute bins
                     z0[u] = load_pair<MT>(r0, jh);
@@ -300,7 +301,7 @@ __device__ __forceinline__ void build_row(const void* __restrict__ maps, const H
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int pp = pp0 + lane + 32 * u;
+                const int pp = pp0 + lane + NL * u;
                 if (pp < npair) {
                     const float re0 = c0 * z0[u].x + c1 * z1[u].x + c2 * z2[u].x;
                     const float im0 = c0 * z0[u].y + c1 * z1[u].y + c2 * z2[u].y;
@@ -315,11 +316,11 @@ __device__ __forceinline__ void build_row(const void* __restrict__ maps, const H
         // 16-byte load per row and group, lanes on consecutive groups; the
         // same registers in flight cover twice the bins of the pair loop
         const int nquad = (npair + 1) >> 1;
-        for (int g0 = 0; g0 < nquad; g0 += 32 * U) {
+        for (int g0 = 0; g0 < nquad; g0 += NL * U) {
             uint4 z0[U], z1[U], z2[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int g = g0 + lane + 32 * u;
+                const int g = g0 + lane + NL * u;
                 if (g < nquad) {
                     const int jq = ((j_ref + 4 * g) & ndm) >> 2;  // group of four absolute bins
                     z0[u] = __ldg((const uint4*)r0 + jq);
@@ -329,7 +330,7 @@ __device__ __forceinline__ void build_row(const void* __restrict__ maps, const H
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int g = g0 + lane + 32 * u;
+                const int g = g0 + lane + NL * u;
                 if (g < nquad) {
                     const uint32_t* w0 = &z0[u].x;
                     const uint32_t* w1 = &z1[u].x;
@@ -777,6 +778,135 @@ __global__ void __launch_bounds__(256, GH_HOP_MINB) hop_batch_kernel(const Batch
     }
 }
 
+// Paired scorer: the two warps of a 64-thread CTA score each (x, y) cell
+// together, so that one set of power rows (all receivers', Q Nd floats) serves
+// 64 lanes and frames with large Q Nd keep twice the warps per SM. The pair's
+// 64 lanes v take b = v % 8 (stride 8) and a = v / 8 (stride 8) with runs of
+// AC = 3 or 5 cells along vx: the 8 x 4 layout's 6- and 10-cell runs split in
+// two. Every cell's sum takes the same terms in the same order as score_xy.
+// Both warps pass every __syncthreads below: the loop bounds they depend on
+// (item, cells, Q) come from shared memory, and no barrier sits in lane- or
+// warp-dependent code.
+template <int AC>
+__device__ __forceinline__ void score_xy_pair(const void* __restrict__ maps, const HopEntry* __restrict__ table,
+                                              const HopParams& p, const int64_t* __restrict__ mask, int nmask,
+                                              long long xy, float* P, HopEntry* E, float* fix, int v, int tb,
+                                              int ta, float& best, long long& bestc) {
+    const int ewords = p.Q * (int)(sizeof(HopEntry) / 8);
+    __syncthreads();  // the previous cell's reads of P and E are done
+    {
+        const long long* src = (const long long*)(table + xy * p.Q);
+        long long* dst = (long long*)E;
+        for (int w = v; w < ewords; w += 64) dst[w] = __ldg(src + w);
+    }
+    __syncthreads();
+    for (int q = 0; q < p.Q; ++q) build_row<GH_C64, 64>(maps, p, E[q], q, P + (size_t)q * p.Nd, v);
+    bool hm = false;
+    {
+        const long long lo = xy * p.nv, hi = lo + p.nv;
+        for (int m = 0; m < nmask; ++m) {
+            const long long mc = __ldg(&mask[m]);
+            hm |= mc >= lo && mc < hi;
+        }
+    }
+    __syncthreads();  // P rows complete
+    const long long cbase = xy * p.nv;
+    for (int b = tb; b < p.nvy; b += p.NB) {
+        for (int a0 = ta; a0 < p.nvx; a0 += p.SA * AC) {
+            float acc[AC];
+#pragma unroll
+            for (int i = 0; i < AC; ++i) acc[i] = 0.f;
+            for (int q = 0; q < p.Q; ++q) score_run_q<AC>(p, E[q], P + (size_t)q * p.Nd, a0, b, acc, fix);
+            finish_run<AC>(p, acc, cbase, a0, b, nullptr, mask, nmask, hm, best, bestc);
+        }
+    }
+}
+
+// Persistent paired batched scorer (complex float32 maps, all receivers'
+// rows): each CTA of two warps takes work items from *counter as
+// hop_batch_kernel's warps do and scores their cells with score_xy_pair;
+// each warp folds its own best cell into the frame's key. Shared memory: the
+// frame's scorer parameters (NB = SA = 8), power rows, entries and the 64
+// lanes' corrections.
+template <int AC>
+__global__ void __launch_bounds__(64, 8) hop_pair_kernel(const BatchFrame* __restrict__ frames,
+                                                         const BatchItem* __restrict__ items, int nitems,
+                                                         unsigned* __restrict__ counter, int k) {
+    extern __shared__ __align__(16) unsigned char smem_hop[];
+    __shared__ int s_item;
+    const int v = threadIdx.x, lane = v & 31;
+    HopParams& p = *(HopParams*)smem_hop;
+    constexpr int kParamBytes = (int)((sizeof(HopParams) + 15) & ~(size_t)15);
+    const int tb = v % 8, ta = v / 8;
+    for (;;) {
+        if (v == 0) s_item = (int)atomicAdd(counter, 1u);
+        __syncthreads();  // s_item set; the previous item's reads of p are done
+        const int it = s_item;
+        if (it >= nitems) break;  // the same for both warps
+        const BatchItem item = items[it];
+        const BatchFrame& F = frames[item.frame];
+        {
+            const int* src = (const int*)&F.hp;
+            int* dst = (int*)&p;
+            for (int w = v; w < (int)(sizeof(HopParams) / 4); w += 64) dst[w] = src[w];
+        }
+        __syncthreads();  // p copied; both warps have read s_item
+        if (v == 0) {
+            p.NB = 8;
+            p.SA = 8;
+        }
+        __syncthreads();
+        float* P = (float*)(smem_hop + kParamBytes);
+        HopEntry* E = (HopEntry*)(P + (size_t)p.Q * p.Nd);
+        float* fix = (float*)(E + p.Q) + v * AC;
+        float best = -INFINITY;
+        long long bestc = 0x7fffffffffffffffLL;
+        for (long long xy = item.start; xy < item.start + item.count; ++xy)
+            score_xy_pair<AC>(F.maps, (const HopEntry*)F.table, p, F.mask, k, xy, P, E, fix, v, tb, ta, best,
+                              bestc);
+        for (int off = 16; off > 0; off >>= 1) {
+            const float os = __shfl_down_sync(0xffffffffu, best, off);
+            const long long oc = __shfl_down_sync(0xffffffffu, bestc, off);
+            better(os, oc, best, bestc);
+        }
+        if (lane == 0 && bestc != 0x7fffffffffffffffLL) {
+            const unsigned long long key =
+                ((unsigned long long)__float_as_uint(best) << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)bestc);
+            atomicMax(&F.key[k], key);
+        }
+    }
+}
+
+// Shared memory of one paired-scorer CTA for frames with Q Nd <= row_floats.
+size_t hop_pair_bytes(int ac, int row_floats, int max_q) {
+    const size_t b = ((sizeof(HopParams) + 15) & ~(size_t)15) + (size_t)row_floats * sizeof(float) +
+                     (size_t)max_q * sizeof(HopEntry) + (size_t)64 * ac * sizeof(float);
+    return (b + 15) & ~(size_t)15;
+}
+
+template <int AC>
+int hop_pair_launch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* items, int n, unsigned* counter, int k,
+                    int max_q_nd, int max_q) {
+    const size_t smem = hop_pair_bytes(AC, max_q_nd, max_q);
+    if (smem > ctx->smem_optin) return gh_fail(ctx, GH_ENOTSUP, "paired scorer: %zu bytes of shared memory", smem);
+    auto kern = hop_pair_kernel<AC>;
+    // the function's limit: the device's largest (see hop_batch_launch)
+    cudaFuncAttributes fa;
+    GH_CUDA(cudaFuncGetAttributes(&fa, kern));
+    GH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(ctx->smem_optin - fa.sharedSizeBytes)));
+    GH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
+    int per_sm = 0;
+    GH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 64, smem));
+    if (per_sm < 1) per_sm = 1;
+    GH_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), ctx->stream));
+    cudaEvent_t ev;
+    gh_launch_begin(ctx, GH_K_HOP_SCORE, &ev);
+    kern<<<ctx->num_sms * per_sm, 64, smem, ctx->stream>>>(frames, items, n, counter, k);
+    return gh_launch_end(ctx, GH_K_HOP_SCORE, ev, "hop_pair_kernel");
+}
+
 // Shared memory of one batched-scorer warp for frames with power rows of at
 // most `row_floats` floats (Q * Nd, or Nd with one receiver's row at a time).
 size_t hop_batch_warp_bytes(int ac, int row_floats, int max_q) {
@@ -1017,7 +1147,12 @@ int gh_launch_hop_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* 
     GH_BATCH_CASE(6)
     GH_BATCH_CASE(10)
 #undef GH_BATCH_CASE
-    return gh_fail(ctx, GH_EINVAL, "batched scorer: cells per lane %d not in {6, 8, 10, 16, 32}", ac);
+    // two warps per (x, y) cell: the 8 x 4 layout's runs split between them
+    if ((ac == 3 || ac == 5) && warps == 2 && !per_rx)
+        return ac == 3 ? hop_pair_launch<3>(ctx, frames, items, n, counter, k, max_q_nd, max_q)
+                       : hop_pair_launch<5>(ctx, frames, items, n, counter, k, max_q_nd, max_q);
+    return gh_fail(ctx, GH_EINVAL, "batched scorer: cells per lane %d not in {3, 5, 6, 8, 10, 16, 32}", ac);
 }
 
 size_t gh_hop_batch_warp_bytes(int ac, int row_floats, int max_q) { return hop_batch_warp_bytes(ac, row_floats, max_q); }
+size_t gh_hop_pair_bytes(int ac, int row_floats, int max_q) { return hop_pair_bytes(ac, row_floats, max_q); }

@@ -520,11 +520,16 @@ inline int lane_layout_ac(const Dims& d) {
 // Shared memory of one batched-scorer warp whose power rows hold at most
 // row_floats floats (Q * Nd, or Nd with one receiver's row at a time).
 size_t gh_hop_batch_warp_bytes(int ac, int row_floats, int max_q);
+// Shared memory of one paired-scorer CTA (two warps per (x, y) cell, all
+// receivers' rows: row_floats >= Q * Nd).
+size_t gh_hop_pair_bytes(int ac, int row_floats, int max_q);
 // Batched coordinate tables (items: frame, first (x, y) cell, count <= 16).
 int gh_launch_coord_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* items, int n);
 // Persistent batched scorer: warps take items (frame, first (x, y) cell, count)
 // from *counter (zeroed here) and fold each frame's best cell into key[k];
-// ac cells per lane (8, 16, 32), warps per CTA; per_rx: one receiver's power
+// ac cells per lane (8, 16, 32; 6, 10 in the 8 x 4 lane layout; 3, 5 with
+// warps = 2 and !per_rx: the paired scorer, two warps per (x, y) cell sharing
+// one set of power rows), warps per CTA; per_rx: one receiver's power
 // row at a time (every frame's cells of a lane form one run: nvy <= 32 and
 // nvx <= SA ac). max_nd, max_q_nd, max_q: largest Nd, Q * Nd and Q of the
 // frames the items name.

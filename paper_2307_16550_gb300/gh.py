@@ -413,7 +413,8 @@ class Context:
         self._check("gh_set_batch_tile", self._lib.gh_set_batch_tile(self.handle, int(cells_per_item)))
 
     def gh_batch_row_mode(self):
-        """1: the heaviest scorer group built one receiver's power row at a time; 0: all at once."""
+        """1: the heaviest scorer group built one receiver's power row at a time; 0: all at once;
+        2: all at once, shared by two warps per (x, y) cell."""
         m = _I32(0)
         self._check("gh_batch_row_mode", self._lib.gh_batch_row_mode(self.handle, ctypes.byref(m)))
         return m.value

@@ -64,7 +64,7 @@ def test_batch_equals_single_frame_detect(ctx, torch_cuda, tuning):
     if tuning != (0, 0):
         assert used == tuning
     else:
-        assert used[0] in (6, 8, 10, 16, 32) and used[1] in (2, 4, 8)
+        assert used[0] in (3, 5, 6, 8, 10, 16, 32) and used[1] in (2, 4, 8)
     for f, r in zip(dev, res):
         _same(r, _single(ctx, f))
 
@@ -85,12 +85,13 @@ def test_item_sizes_give_single_frame_results(ctx, torch_cuda, tile):
         _same(r, _single(ctx, f))
 
 
-@pytest.mark.parametrize("row_mode", [0, 1])
+@pytest.mark.parametrize("row_mode", [0, 1, 2])
 def test_power_row_modes_give_single_frame_results(ctx, torch_cuda, row_mode):
-    """The batched scorer kept to one power-row mode (all receivers' rows, or
-    one receiver's row at a time where a lane's cells form one run): the same
-    results as gh_detect, bit for bit, on frames with 16..40 velocities per
-    axis."""
+    """The batched scorer kept to one power-row mode (all receivers' rows, one
+    receiver's row at a time where a lane's cells form one run, or all rows
+    shared by two warps per (x, y) cell in the 8 x 4 layout's classes): the
+    same results as gh_detect, bit for bit, on frames with 16..40 velocities
+    per axis."""
     frames = scenes.batch_scenes(7, 12) + [scenes.tiny_scene(3)]
     dev, _ = _device_frames(torch_cuda, frames, synth_ctx=ctx)
     ctx.gh_set_batch_row_mode(row_mode)
@@ -98,13 +99,15 @@ def test_power_row_modes_give_single_frame_results(ctx, torch_cuda, row_mode):
         res = ctx.gh_detect_batch(dev)
         if row_mode == 0:
             assert ctx.gh_batch_row_mode() == 0
+        if row_mode == 2:
+            assert ctx.gh_batch_row_mode() in (0, 2)
     finally:
         ctx.gh_set_batch_row_mode(-1)
     for f, r in zip(dev, res):
         _same(r, _single(ctx, f))
 
 
-@pytest.mark.parametrize("row_mode", [-1, 0, 1])
+@pytest.mark.parametrize("row_mode", [-1, 0, 1, 2])
 def test_uneven_velocity_axes_give_single_frame_results(ctx, torch_cuda, row_mode):
     """Velocity grids with unequal and odd axes (partial runs in the 8 x 4
     lane layout, a lane's vy rows over several one-row passes, runs past the
@@ -119,6 +122,28 @@ def test_uneven_velocity_axes_give_single_frame_results(ctx, torch_cuda, row_mod
     ctx.gh_set_batch_row_mode(row_mode)
     try:
         res = ctx.gh_detect_batch(dev)
+    finally:
+        ctx.gh_set_batch_row_mode(-1)
+    for f, r in zip(dev, res):
+        _same(r, _single(ctx, f))
+
+
+def test_paired_scorer_gives_single_frame_results(ctx, torch_cuda):
+    """Two warps per (x, y) cell sharing one set of power rows (the 8 x 4
+    layout's 24 x 24 and 40 x 40 velocity grids, odd and even Q, several Nd,
+    K up to 3 so that masked cells are skipped): the same results as
+    gh_detect, bit for bit, and the paired scorer is the one that ran."""
+    frames = []
+    for i, nv in enumerate((24, 40, 40, 24, 40)):
+        radar = scenes.Radar(24e9, 250e6, 128e-6, 64 << (i % 3), 64 << (i % 2), 4)
+        grid = scenes.Grid.from_bounds((0, 0, -15, -15), (40, 40, 15, 15), (10 + 2 * i, 12 + i, nv, nv))
+        frames.append(scenes.custom_scene(90 + i, radar, grid, Q=3 + i, T=1 + i % 3, snr_db=12.0))
+    dev, _ = _device_frames(torch_cuda, frames, synth_ctx=ctx)
+    ctx.gh_set_batch_row_mode(2)
+    try:
+        res = ctx.gh_detect_batch(dev)
+        assert ctx.gh_batch_row_mode() == 2
+        assert ctx.gh_batch_tuning() in ((3, 2), (5, 2))
     finally:
         ctx.gh_set_batch_row_mode(-1)
     for f, r in zip(dev, res):
@@ -157,7 +182,7 @@ def test_batch_rejects_bad_frames(ctx, torch_cuda):
         ctx.gh_set_batch_tile(12)
     assert e.value.status == gh.GH_EINVAL
     with pytest.raises(gh.GhError):
-        ctx.gh_set_batch_row_mode(2)
+        ctx.gh_set_batch_row_mode(3)
 
 
 def test_uneven_256_frame_workload_sampled(ctx, torch_cuda):
