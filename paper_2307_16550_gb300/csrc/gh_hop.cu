@@ -29,6 +29,11 @@
 //   map rows overlap in L1. Scores (optional) are written coalesced; the best
 //   (score, cell) is reduced per lane, then with warp shuffles and once per
 //   CTA (ties: smallest cell index).
+//
+// hop_pair_score_kernel, hop_pair_kernel (batched): where all receivers' rows
+//   leave few warps per SM (large Q Nd, cells that do not fit one register
+//   run), the two warps of a 64-thread CTA score each (x, y) cell together
+//   from one set of rows, with the lanes' velocity cells split between them.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
@@ -507,6 +512,96 @@ __device__ __forceinline__ void score_xy(const void* __restrict__ maps, const Ho
     }
 }
 
+// Paired scoring: the two warps of a 64-thread CTA score each (x, y) cell
+// together, so that one set of power rows (all receivers', Q Nd floats) serves
+// 64 lanes and frames with large Q Nd keep twice the warps per SM. The pair's
+// lanes v in [0, 64) take b = v % NB (stride NB) and a = v / NB (stride SA)
+// with the pair's NB and SA: NB = min(nvy, 32) and SA = 64 / NB, or, in the
+// 8 x 4 layout, NB = SA = 8 with runs of 3 or 5 cells (the 6- and 10-cell
+// runs split in two). Every cell's sum takes the same terms in the same order
+// as score_xy. Both warps pass every __syncthreads below: the loop bounds
+// they depend on (cells, Q) are the same for both, and no barrier sits in
+// lane- or warp-dependent code.
+template <int AC, int MT>
+__device__ __forceinline__ void score_xy_pair(const void* __restrict__ maps, const HopEntry* __restrict__ table,
+                                              const HopParams& p, float* __restrict__ scores,
+                                              const int64_t* __restrict__ mask, int nmask, long long xy, float* P,
+                                              HopEntry* E, float* fix, int v, int tb, int ta, bool active,
+                                              float& best, long long& bestc) {
+    const int ewords = p.Q * (int)(sizeof(HopEntry) / 8);
+    __syncthreads();  // the previous cell's reads of P and E are done
+    {
+        const long long* src = (const long long*)(table + xy * p.Q);
+        long long* dst = (long long*)E;
+        for (int w = v; w < ewords; w += 64) dst[w] = __ldg(src + w);
+    }
+    __syncthreads();
+    for (int q = 0; q < p.Q; ++q) build_row<MT, 64>(maps, p, E[q], q, P + (size_t)q * p.Nd, v);
+    bool hm = false;
+    {
+        const long long lo = xy * p.nv, hi = lo + p.nv;
+        for (int m = 0; m < nmask; ++m) {
+            const long long mc = __ldg(&mask[m]);
+            hm |= mc >= lo && mc < hi;
+        }
+    }
+    __syncthreads();  // P rows complete
+    if (!active) return;
+    const long long cbase = xy * p.nv;
+    for (int b = tb; b < p.nvy; b += p.NB) {
+        for (int a0 = ta; a0 < p.nvx; a0 += p.SA * AC) {
+            float acc[AC];
+#pragma unroll
+            for (int i = 0; i < AC; ++i) acc[i] = 0.f;
+            for (int q = 0; q < p.Q; ++q) score_run_q<AC>(p, E[q], P + (size_t)q * p.Nd, a0, b, acc, fix);
+            finish_run<AC>(p, acc, cbase, a0, b, scores, mask, nmask, hm, best, bestc);
+        }
+    }
+}
+
+// Paired single-frame scorer: CTA = one pair of warps walking its (x, y)
+// cells with score_xy_pair (p.NB, p.SA: the pair's layout), then one argmax
+// partial per CTA. Shared memory: all receivers' rows, entries, the 64
+// lanes' corrections.
+template <int AC, int MT>
+__global__ void __launch_bounds__(64, 8) hop_pair_score_kernel(const void* __restrict__ maps,
+                                                               const HopEntry* __restrict__ table, HopParams p,
+                                                               float* __restrict__ scores,
+                                                               const int64_t* __restrict__ mask, int nmask,
+                                                               ArgPartial* __restrict__ parts) {
+    extern __shared__ __align__(16) unsigned char smem_hop[];
+    __shared__ float s_bs[2];
+    __shared__ long long s_bc[2];
+    const int v = threadIdx.x, warp = v >> 5, lane = v & 31;
+    float* P = (float*)smem_hop;
+    HopEntry* E = (HopEntry*)(P + (size_t)p.Q * p.Nd);
+    float* fix = (float*)(E + p.Q) + v * AC;
+    const int tb = v % p.NB, ta = v / p.NB;
+    const bool active = ta < p.SA;
+    float best = -INFINITY;
+    long long bestc = 0x7fffffffffffffffLL;
+    const long long xy0 = (long long)blockIdx.x * p.xy_per_cta;
+    long long xy1 = xy0 + p.xy_per_cta;
+    if (xy1 > p.nxy) xy1 = p.nxy;
+    for (long long xy = xy0; xy < xy1; ++xy)
+        score_xy_pair<AC, MT>(maps, table, p, scores, mask, nmask, xy, P, E, fix, v, tb, ta, active, best, bestc);
+    for (int off = 16; off > 0; off >>= 1) {
+        const float os = __shfl_down_sync(0xffffffffu, best, off);
+        const long long oc = __shfl_down_sync(0xffffffffu, bestc, off);
+        better(os, oc, best, bestc);
+    }
+    if (lane == 0) {
+        s_bs[warp] = best;
+        s_bc[warp] = bestc;
+    }
+    __syncthreads();
+    if (v == 0) {
+        better(s_bs[1], s_bc[1], best, bestc);
+        parts[blockIdx.x].score = best;
+        parts[blockIdx.x].cell = bestc;
+    }
+}
+
 // AC: velocity cells per lane per pass (along vx, stride SA); MT: map storage
 // type; PR: one receiver's power row at a time (see score_xy).
 template <int AC, int MT, bool PR>
@@ -654,6 +749,65 @@ int hop_launch_t(cudaStream_t stream, const Dims& d, HopParams hp, const void* m
     return GH_OK;
 }
 
+// Shared memory of one paired scorer CTA: all receivers' rows, entries, the
+// 64 lanes' corrections.
+inline size_t hop_pair_frame_bytes(const Dims& d, int ac) {
+    const size_t b = (size_t)d.Q * d.Nd * sizeof(float) + (size_t)d.Q * sizeof(HopEntry) +
+                     (size_t)64 * ac * sizeof(float);
+    return (b + 15) & ~(size_t)15;
+}
+
+// Whether the paired scorer (pair_bytes per 64-thread CTA) keeps more warps
+// per SM than one warp per cell (per_warp bytes, W warps per CTA as
+// hop_launch_t picks them), from the 128-register budget of both and the
+// SM's shared memory (1 KiB reserved per CTA).
+inline bool pair_keeps_more_warps(size_t per_warp, size_t pair_bytes, size_t smem_optin) {
+    const size_t sm = smem_optin + 1024;
+    int W = (int)((size_t)(100 << 10) / per_warp);
+    if (W > 8) W = 8;
+    if (W < 1) W = 1;
+    const size_t by_regs = (size_t)(16 / W), by_smem = sm / (W * per_warp + 1024);
+    const size_t one = (size_t)W * std::min(by_regs, by_smem);
+    const size_t two = 2 * std::min((size_t)8, sm / (pair_bytes + 1024));
+    return two > one;
+}
+
+// Launch of the paired scorer; hp carries the pair's NB and SA.
+template <int AC, int MT>
+int hop_pair_launch_t(cudaStream_t stream, const Dims& d, HopParams hp, const void* maps, const HopEntry* table,
+                      float* scores, const int64_t* mask, int nmask, ArgPartial* parts, long long max_ctas,
+                      int num_sms, size_t smem_optin, long long* nparts) {
+    const size_t smem = hop_pair_frame_bytes(d, AC);
+    if (smem > smem_optin) return GH_ENOTSUP;
+    auto kern = hop_pair_score_kernel<AC, MT>;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(smem_optin - fa.sharedSizeBytes)) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+        return GH_ECUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 64, smem) != cudaSuccess) return GH_ECUDA;
+    if (per_sm < 1) per_sm = 1;
+    long long ctas = (long long)num_sms * per_sm;
+    if (ctas > max_ctas) ctas = max_ctas;
+    if (ctas > d.nxy) ctas = d.nxy;
+    hp.xy_per_cta = (d.nxy + ctas - 1) / ctas;
+    ctas = (d.nxy + hp.xy_per_cta - 1) / hp.xy_per_cta;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ctas);
+    cfg.blockDim = dim3(64);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    *nparts = ctas;
+    if (cudaLaunchKernelEx(&cfg, kern, maps, table, hp, scores, mask, nmask, parts) != cudaSuccess) {
+        (void)cudaGetLastError();  // consume this launch's own error
+        return GH_ECUDA;
+    }
+    return GH_OK;
+}
+
 template <int MT>
 int hop_launch_mt(cudaStream_t stream, const Dims& d, const HopParams& hp, const void* maps, const HopEntry* table,
                   float* scores, const int64_t* mask, int nmask, ArgPartial* parts, long long max_ctas, int num_sms,
@@ -671,6 +825,17 @@ int hop_launch_mt(cudaStream_t stream, const Dims& d, const HopParams& hp, const
         h8.NB = 8;
         h8.SA = 4;
         const bool pr8 = (d.nvx + 3) / 4 <= lay && hop_warp_bytes(d, lay, false) * 8 > (100 << 10);
+        // all rows: two warps per (x, y) cell where that keeps more warps per SM
+        if (!pr8 && pair_keeps_more_warps(hop_warp_bytes(d, lay, false), hop_pair_frame_bytes(d, lay / 2),
+                                          smem_optin)) {
+            HopParams h2 = hp;
+            h2.NB = 8;
+            h2.SA = 8;
+            return lay == 6 ? hop_pair_launch_t<3, MT>(stream, d, h2, maps, table, scores, mask, nmask, parts,
+                                                       max_ctas, num_sms, smem_optin, nparts)
+                            : hop_pair_launch_t<5, MT>(stream, d, h2, maps, table, scores, mask, nmask, parts,
+                                                       max_ctas, num_sms, smem_optin, nparts);
+        }
 #define GH_HOP_LAYOUT(N)                                                                                          \
     return pr8 ? hop_launch_t<N, MT, true>(stream, d, h8, maps, table, scores, mask, nmask, parts, max_ctas,      \
                                            num_sms, smem_optin, nparts)                                          \
@@ -686,6 +851,18 @@ int hop_launch_mt(cudaStream_t stream, const Dims& d, const HopParams& hp, const
     // rows of all receivers would leave fewer than eight warps per CTA
     const int ac = need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : 16;
     const bool pr = d.nvy <= 32 && full <= 16 && hop_warp_bytes(d, ac, false) * 8 > (100 << 10);
+    if (!pr) {
+        // all rows: two warps per (x, y) cell (SA doubled) where that keeps
+        // more warps per SM
+        HopParams h2 = hp;
+        h2.SA = 64 / hp.NB;
+        const int pac = (d.nvx + h2.SA - 1) / h2.SA <= 8 ? 8 : 16;
+        if (pair_keeps_more_warps(hop_warp_bytes(d, ac, false), hop_pair_frame_bytes(d, pac), smem_optin))
+            return pac == 8 ? hop_pair_launch_t<8, MT>(stream, d, h2, maps, table, scores, mask, nmask, parts,
+                                                       max_ctas, num_sms, smem_optin, nparts)
+                            : hop_pair_launch_t<16, MT>(stream, d, h2, maps, table, scores, mask, nmask, parts,
+                                                        max_ctas, num_sms, smem_optin, nparts);
+    }
 #define GH_HOP_CASE(N)                                                                                             \
     if (need <= N)                                                                                                 \
         return pr ? hop_launch_t<N, MT, true>(stream, d, hp, maps, table, scores, mask, nmask, parts, max_ctas,  \
@@ -778,53 +955,11 @@ __global__ void __launch_bounds__(256, GH_HOP_MINB) hop_batch_kernel(const Batch
     }
 }
 
-// Paired scorer: the two warps of a 64-thread CTA score each (x, y) cell
-// together, so that one set of power rows (all receivers', Q Nd floats) serves
-// 64 lanes and frames with large Q Nd keep twice the warps per SM. The pair's
-// 64 lanes v take b = v % 8 (stride 8) and a = v / 8 (stride 8) with runs of
-// AC = 3 or 5 cells along vx: the 8 x 4 layout's 6- and 10-cell runs split in
-// two. Every cell's sum takes the same terms in the same order as score_xy.
-// Both warps pass every __syncthreads below: the loop bounds they depend on
-// (item, cells, Q) come from shared memory, and no barrier sits in lane- or
-// warp-dependent code.
-template <int AC>
-__device__ __forceinline__ void score_xy_pair(const void* __restrict__ maps, const HopEntry* __restrict__ table,
-                                              const HopParams& p, const int64_t* __restrict__ mask, int nmask,
-                                              long long xy, float* P, HopEntry* E, float* fix, int v, int tb,
-                                              int ta, float& best, long long& bestc) {
-    const int ewords = p.Q * (int)(sizeof(HopEntry) / 8);
-    __syncthreads();  // the previous cell's reads of P and E are done
-    {
-        const long long* src = (const long long*)(table + xy * p.Q);
-        long long* dst = (long long*)E;
-        for (int w = v; w < ewords; w += 64) dst[w] = __ldg(src + w);
-    }
-    __syncthreads();
-    for (int q = 0; q < p.Q; ++q) build_row<GH_C64, 64>(maps, p, E[q], q, P + (size_t)q * p.Nd, v);
-    bool hm = false;
-    {
-        const long long lo = xy * p.nv, hi = lo + p.nv;
-        for (int m = 0; m < nmask; ++m) {
-            const long long mc = __ldg(&mask[m]);
-            hm |= mc >= lo && mc < hi;
-        }
-    }
-    __syncthreads();  // P rows complete
-    const long long cbase = xy * p.nv;
-    for (int b = tb; b < p.nvy; b += p.NB) {
-        for (int a0 = ta; a0 < p.nvx; a0 += p.SA * AC) {
-            float acc[AC];
-#pragma unroll
-            for (int i = 0; i < AC; ++i) acc[i] = 0.f;
-            for (int q = 0; q < p.Q; ++q) score_run_q<AC>(p, E[q], P + (size_t)q * p.Nd, a0, b, acc, fix);
-            finish_run<AC>(p, acc, cbase, a0, b, nullptr, mask, nmask, hm, best, bestc);
-        }
-    }
-}
-
 // Persistent paired batched scorer (complex float32 maps, all receivers'
-// rows): each CTA of two warps takes work items from *counter as
-// hop_batch_kernel's warps do and scores their cells with score_xy_pair;
+// rows, the 8 x 4 layout's runs split in two): each CTA of two warps takes
+// work items from *counter as hop_batch_kernel's warps do and scores their
+// cells with score_xy_pair (the loop bounds come from shared memory, so both
+// warps pass the same barriers);
 // each warp folds its own best cell into the frame's key. Shared memory: the
 // frame's scorer parameters (NB = SA = 8), power rows, entries and the 64
 // lanes' corrections.
@@ -862,8 +997,8 @@ __global__ void __launch_bounds__(64, 8) hop_pair_kernel(const BatchFrame* __res
         float best = -INFINITY;
         long long bestc = 0x7fffffffffffffffLL;
         for (long long xy = item.start; xy < item.start + item.count; ++xy)
-            score_xy_pair<AC>(F.maps, (const HopEntry*)F.table, p, F.mask, k, xy, P, E, fix, v, tb, ta, best,
-                              bestc);
+            score_xy_pair<AC, GH_C64>(F.maps, (const HopEntry*)F.table, p, nullptr, F.mask, k, xy, P, E, fix, v,
+                                      tb, ta, true, best, bestc);
         for (int off = 16; off > 0; off >>= 1) {
             const float os = __shfl_down_sync(0xffffffffu, best, off);
             const long long oc = __shfl_down_sync(0xffffffffu, bestc, off);

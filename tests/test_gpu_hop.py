@@ -170,3 +170,44 @@ def test_lane_layouts_agree_bit_for_bit(ctx, torch_cuda):
     s_small, _, _ = ctx.scores(radar, small.tx, small.rx, maps, small.grid)
     s_big, _, _ = ctx.scores(radar, big.tx, big.rx, maps, big.grid)
     np.testing.assert_array_equal(s_small.cpu().numpy(), s_big.cpu().numpy()[:, :, :, :24])
+
+
+@pytest.mark.parametrize("nv", [(64, 64), (44, 40), (76, 40), (20, 24)])
+def test_paired_scorer_matches_oracle(ctx, torch_cuda, nv):
+    """Q = 8, Nd = 1024 with velocity grids whose cells do not fit one
+    register run per lane (64 x 64 standard layout, 44 x 40 and 76 x 40 in
+    the 8 x 4 layout): all receivers' rows would leave 6 warps per SM, so two
+    warps score each (x, y) cell together. 20 x 24 (one run per lane: one
+    receiver's row at a time) for contrast. Every score against the oracle."""
+    radar = scenes.Radar(24e9, 250e6, 128e-6, 32, 256, 4)
+    grid = scenes.Grid.from_bounds((2, 3, -15, -15), (38, 36, 15, 15), (3, 2) + nv)
+    sc = scenes.custom_scene(71, radar, grid, Q=8, T=2, snr_db=10.0)
+    Y32, Y = measurement64(sc)
+    ref = hopping.hop_scores(omaps.rd_maps(Y, 4), sc.radar, sc.tx, sc.rx, sc.grid)
+    got, cell, _ = ctx.scores(sc.radar, sc.tx, sc.rx, ctx.maps(sc.radar, to_dev(torch_cuda, Y32)), sc.grid)
+    assert rel_err(got.cpu().numpy(), ref) < TOL
+    if top2_margin(ref) > 10 * TOL:
+        assert cell == hopping.argmax_cell(ref)
+
+
+def test_paired_and_single_warp_scores_agree_bit_for_bit(ctx, torch_cuda):
+    """The 32 x 32 velocity cells of a Q = 8, Nd = 1024 frame are scored by
+    two warps per (x, y) cell in gh_score_grid and by one warp per cell in the
+    batched scorer kept to all receivers' rows (the batch's argmax at that
+    frame's best cell): the single-frame scores' argmax cell and score equal
+    the batch's bit for bit."""
+    radar = scenes.Radar(24e9, 250e6, 128e-6, 64, 256, 4)
+    grid = scenes.Grid.from_bounds((2, 3, -15, -15), (38, 36, 15, 15), (6, 5, 32, 32))
+    sc = scenes.custom_scene(72, radar, grid, Q=8, T=1, snr_db=15.0)
+    Y32, _ = measurement64(sc)
+    Yd = to_dev(torch_cuda, Y32)
+    got, cell, best = ctx.scores(sc.radar, sc.tx, sc.rx, ctx.maps(sc.radar, Yd), sc.grid)
+    ctx.gh_set_batch_row_mode(0)
+    try:
+        (bcells, bscores, _), = ctx.gh_detect_batch([(sc.radar, sc.tx, sc.rx, sc.Q, Yd, sc.grid, 1)])
+    finally:
+        ctx.gh_set_batch_row_mode(-1)
+    assert int(bcells[0]) == cell
+    assert np.float32(bscores[0]) == np.float32(best)
+    assert np.float32(got.cpu().numpy().reshape(-1)[cell]) == np.float32(best)
+
