@@ -279,8 +279,9 @@ typedef struct {
  *   scores_host : host float[sum K] (may be NULL)
  *   alpha_host  : host double[sum K*Q][2] (may be NULL), per frame [K][Q][2]
  * Each scorer group's cells per lane (8, 16, 32, or 6 and 10 in the 8 x 4
- * lane layout for velocity axes of about 24 and 40 cells, or 3 and 5 when
- * two warps share each (x, y) cell's power rows), warps per CTA,
+ * lane layout for velocity axes of about 24 and 40 cells; with two warps
+ * sharing each (x, y) cell's power rows, 3 and 5 in that layout and 8 and 16
+ * in the standard one), warps per CTA,
  * power-row mode and (x, y) cells per work item are chosen by timing the
  * candidates on the first iteration of a batch shape (cached in the context),
  * unless fixed with gh_set_batch_tuning, gh_set_batch_row_mode and
@@ -293,8 +294,8 @@ GH_API int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* frames,
  * warps per CTA in {2, 4, 8}; (0, 0) returns to autotuning (the default). */
 GH_API int gh_set_batch_tuning(gh_ctx* ctx, int32_t cells_per_lane, int32_t warps);
 /* The configuration the last gh_detect_batch call used for its scorer group
- * with the most work (cells per lane 6 and 10: the 8 x 4 lane layout; 3 and
- * 5 with 2 warps: the paired scorer, row mode 2). */
+ * with the most work (cells per lane 6 and 10: the 8 x 4 lane layout; with
+ * row mode 2 the paired scorer, 2 warps per CTA). */
 GH_API int gh_batch_tuning(gh_ctx* ctx, int32_t* cells_per_lane, int32_t* warps);
 /* Fixes the number of consecutive (x, y) cells in one work item of the
  * batched scorer: 4, 8, 16 or 32; 0 returns to tuning (the default: after the
@@ -311,14 +312,15 @@ GH_API int gh_batch_tile(gh_ctx* ctx, int32_t* cells_per_item);
  * all its receivers at once, 2 the rows of all receivers shared by the two
  * warps of a CTA that score each (x, y) cell together. One row at a time
  * needs a lane's velocity cells to fit one run per vy row it takes (nvy <=
- * 32, or the 8 x 4 layout); it and the paired mode (groups in the 8 x 4
- * layout) leave room for more warps per SM when Q * Nd is large; the
+ * 32, or the 8 x 4 layout); it and the paired mode leave room for more
+ * warps per SM when Q * Nd is large; the
  * autotuner times every mode that applies (a configuration fixed with
  * gh_set_batch_tuning builds all rows at once, one warp per cell). */
 GH_API int gh_batch_row_mode(gh_ctx* ctx, int32_t* per_receiver);
 /* Keeps the autotuner to one power-row mode: 0 all receivers' rows, 1 one
  * receiver's row at a time, 2 paired (1 and 2 for the scorer groups where
- * they apply; all rows elsewhere); -1 (the default) lets it time every mode.
+ * they apply, 2 wherever a group's rows fit one CTA; all rows elsewhere); -1
+ * (the default) lets it time every mode.
  * Results do not depend on the mode. Other values: GH_EINVAL. */
 GH_API int gh_set_batch_row_mode(gh_ctx* ctx, int32_t row_mode);
 

@@ -97,6 +97,7 @@ struct Plan {
 struct Tuning {
     int ac = 0, warps = 0, tile = kDefaultTile;  // tile: index into kTiles
     bool per_rx = false;                         // one receiver's power row at a time
+    bool pair = false;                           // two warps per (x, y) cell (warps = 2, all rows)
 };
 
 int class_bound(int q_nd) {
@@ -447,7 +448,7 @@ int score_classes(gh_ctx* ctx, BatchState* S, const Plan& P, const std::vector<T
     auto launch = [&](int c) {
         const Plan::ScoreClass& C = P.classes[c];
         return gh_launch_hop_batch(ctx, P.frames, C.items[t[c].tile], C.n[t[c].tile][k], P.counter + c, k, t[c].ac,
-                                   t[c].warps, t[c].per_rx, C.max_nd, C.bound, C.max_q);
+                                   t[c].warps, t[c].per_rx, t[c].pair, C.max_nd, C.bound, C.max_q);
     };
     if (ctx->timing != 0 || nc < 2) {
         for (int c = 0; c < nc; ++c) GH_TRY(launch(c));
@@ -507,11 +508,11 @@ int autotune_prepare(gh_ctx* ctx, const Plan& P) {
 // fastest configuration: cells per lane (8, 16, 32, and 6 or 10 in the 8 x 4
 // lane layout for classes it fits) x warps per CTA (8, 4, 2, as shared memory
 // allows) x power rows of all receivers or of one receiver at a time (where
-// every frame's cells of a lane form one run), and, for the 8 x 4 layout's
-// classes, the paired scorer (two warps per (x, y) cell, 3 or 5 cells per
-// lane), with 8-cell items, then, for that configuration, items of 4, 8, 16
-// and 32 (x, y) cells (`tile` >= 0 fixes the item size). rm: the row mode
-// kept to (-1 any, 0 all rows, 1 one row at a time, 2 paired).
+// every frame's cells of a lane form one run), and the paired scorer (two
+// warps per (x, y) cell: 3 or 5 cells per run in the 8 x 4 layout, 8 or 16 in
+// the standard one), with 8-cell items, then, for that configuration, items
+// of 4, 8, 16 and 32 (x, y) cells (`tile` >= 0 fixes the item size). rm: the
+// row mode kept to (-1 any, 0 all rows, 1 one row at a time, 2 paired).
 int autotune(gh_ctx* ctx, const Plan& P, const Plan::ScoreClass& C, int tile, int rm, Tuning* best) {
     cudaEvent_t a, b;
     GH_CUDA(cudaEventCreate(&a));
@@ -523,7 +524,7 @@ int autotune(gh_ctx* ctx, const Plan& P, const Plan::ScoreClass& C, int tile, in
         for (int rep = 0; rep < 2 && st == GH_OK; ++rep) {  // first launch warms up
             cudaEventRecord(a, ctx->stream);
             st = gh_launch_hop_batch(ctx, P.frames, C.items[c.tile], C.n[c.tile][0], P.counter, 0, c.ac, c.warps,
-                                     c.per_rx, C.max_nd, C.bound, C.max_q);
+                                     c.per_rx, c.pair, C.max_nd, C.bound, C.max_q);
             cudaEventRecord(b, ctx->stream);
         }
         if (st != GH_OK) return;
@@ -538,12 +539,20 @@ int autotune(gh_ctx* ctx, const Plan& P, const Plan::ScoreClass& C, int tile, in
         }
     };
     const int t0 = tile >= 0 ? tile : kDefaultTile;
-    // two warps per (x, y) cell: classes in the 8 x 4 layout whose rows fit
-    // one CTA; where it is asked for but does not apply, all rows
+    // two warps per (x, y) cell, where the class's rows fit one CTA: runs of
+    // 3 or 5 in the 8 x 4 layout, of 8 or 16 in the standard one; where it is
+    // asked for but does not apply, all rows
     const bool pair_ok =
-        C.layout_ac != 0 && gh_hop_pair_bytes(C.layout_ac / 2, C.bound, C.max_q) <= ctx->smem_optin;
+        gh_hop_pair_bytes(C.layout_ac ? C.layout_ac / 2 : 16, C.bound, C.max_q) <= ctx->smem_optin;
     if (rm == 2 && !pair_ok) rm = 0;
-    if (st == GH_OK && pair_ok && (rm == -1 || rm == 2)) time_one({C.layout_ac / 2, 2, t0, false});
+    if (pair_ok && (rm == -1 || rm == 2)) {
+        if (C.layout_ac) {
+            if (st == GH_OK) time_one({C.layout_ac / 2, 2, t0, false, true});
+        } else {
+            for (int ac : {8, 16})
+                if (st == GH_OK) time_one({ac, 2, t0, false, true});
+        }
+    }
     // one row at a time where it applies and is wanted; all rows otherwise
     // (also when one row at a time is asked for but applies to no configuration)
     const bool pr_any = rm != 0 && (C.pr_need <= 32 || (C.layout_ac && C.layout_run <= C.layout_ac));
@@ -566,7 +575,7 @@ int autotune(gh_ctx* ctx, const Plan& P, const Plan::ScoreClass& C, int tile, in
     if (tile < 0) {
         const Tuning cfg = *best;
         for (int t = 0; t < kNumTiles && st == GH_OK; ++t)
-            if (t != t0) time_one({cfg.ac, cfg.warps, t, cfg.per_rx});
+            if (t != t0) time_one({cfg.ac, cfg.warps, t, cfg.per_rx, cfg.pair});
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -638,6 +647,7 @@ extern "C" int gh_detect_batch(gh_ctx* ctx, int32_t nframes, const gh_frame* fra
         append(gkey, tc.warps);
         append(gkey, tc.tile);
         append(gkey, tc.per_rx);
+        append(gkey, tc.pair);
     }
     append(gkey, ctx->timing);
     const char tag[] = "batch";
@@ -709,7 +719,7 @@ extern "C" int gh_set_batch_row_mode(gh_ctx* ctx, int32_t row_mode) {
 extern "C" int gh_batch_row_mode(gh_ctx* ctx, int32_t* per_receiver) {
     if (!ctx || !per_receiver) return GH_EINVAL;
     const Tuning& t = state_of(ctx)->last;
-    *per_receiver = t.per_rx ? 1 : (t.ac == 3 || t.ac == 5) ? 2 : 0;
+    *per_receiver = t.per_rx ? 1 : t.pair ? 2 : 0;
     return GH_OK;
 }
 

@@ -956,14 +956,15 @@ __global__ void __launch_bounds__(256, GH_HOP_MINB) hop_batch_kernel(const Batch
 }
 
 // Persistent paired batched scorer (complex float32 maps, all receivers'
-// rows, the 8 x 4 layout's runs split in two): each CTA of two warps takes
-// work items from *counter as hop_batch_kernel's warps do and scores their
-// cells with score_xy_pair (the loop bounds come from shared memory, so both
-// warps pass the same barriers);
-// each warp folds its own best cell into the frame's key. Shared memory: the
-// frame's scorer parameters (NB = SA = 8), power rows, entries and the 64
+// rows): each CTA of two warps takes work items from *counter as
+// hop_batch_kernel's warps do and scores their cells with score_xy_pair (the
+// loop bounds come from shared memory, so both warps pass the same barriers);
+// each warp folds its own best cell into the frame's key. L8: the 8 x 4
+// layout's runs split in two (NB = SA = 8, AC = 3 or 5), else the standard
+// layout with SA doubled (SA = 64 / NB). Shared memory: the frame's scorer
+// parameters (with the pair's NB and SA), power rows, entries and the 64
 // lanes' corrections.
-template <int AC>
+template <int AC, bool L8>
 __global__ void __launch_bounds__(64, 8) hop_pair_kernel(const BatchFrame* __restrict__ frames,
                                                          const BatchItem* __restrict__ items, int nitems,
                                                          unsigned* __restrict__ counter, int k) {
@@ -972,7 +973,6 @@ __global__ void __launch_bounds__(64, 8) hop_pair_kernel(const BatchFrame* __res
     const int v = threadIdx.x, lane = v & 31;
     HopParams& p = *(HopParams*)smem_hop;
     constexpr int kParamBytes = (int)((sizeof(HopParams) + 15) & ~(size_t)15);
-    const int tb = v % 8, ta = v / 8;
     for (;;) {
         if (v == 0) s_item = (int)atomicAdd(counter, 1u);
         __syncthreads();  // s_item set; the previous item's reads of p are done
@@ -987,10 +987,16 @@ __global__ void __launch_bounds__(64, 8) hop_pair_kernel(const BatchFrame* __res
         }
         __syncthreads();  // p copied; both warps have read s_item
         if (v == 0) {
-            p.NB = 8;
-            p.SA = 8;
+            if (L8) {
+                p.NB = 8;
+                p.SA = 8;
+            } else {
+                p.SA = 64 / p.NB;  // NB = min(nvy, 32)
+            }
         }
         __syncthreads();
+        const int tb = v % p.NB, ta = v / p.NB;
+        const bool active = ta < p.SA;
         float* P = (float*)(smem_hop + kParamBytes);
         HopEntry* E = (HopEntry*)(P + (size_t)p.Q * p.Nd);
         float* fix = (float*)(E + p.Q) + v * AC;
@@ -998,7 +1004,7 @@ __global__ void __launch_bounds__(64, 8) hop_pair_kernel(const BatchFrame* __res
         long long bestc = 0x7fffffffffffffffLL;
         for (long long xy = item.start; xy < item.start + item.count; ++xy)
             score_xy_pair<AC, GH_C64>(F.maps, (const HopEntry*)F.table, p, nullptr, F.mask, k, xy, P, E, fix, v,
-                                      tb, ta, true, best, bestc);
+                                      tb, ta, active, best, bestc);
         for (int off = 16; off > 0; off >>= 1) {
             const float os = __shfl_down_sync(0xffffffffu, best, off);
             const long long oc = __shfl_down_sync(0xffffffffu, bestc, off);
@@ -1019,12 +1025,12 @@ size_t hop_pair_bytes(int ac, int row_floats, int max_q) {
     return (b + 15) & ~(size_t)15;
 }
 
-template <int AC>
+template <int AC, bool L8>
 int hop_pair_launch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* items, int n, unsigned* counter, int k,
                     int max_q_nd, int max_q) {
     const size_t smem = hop_pair_bytes(AC, max_q_nd, max_q);
     if (smem > ctx->smem_optin) return gh_fail(ctx, GH_ENOTSUP, "paired scorer: %zu bytes of shared memory", smem);
-    auto kern = hop_pair_kernel<AC>;
+    auto kern = hop_pair_kernel<AC, L8>;
     // the function's limit: the device's largest (see hop_batch_launch)
     cudaFuncAttributes fa;
     GH_CUDA(cudaFuncGetAttributes(&fa, kern));
@@ -1270,8 +1276,16 @@ int gh_launch_coord_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem
 }
 
 int gh_launch_hop_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* items, int n, unsigned* counter,
-                        int k, int ac, int warps, bool per_rx, int max_nd, int max_q_nd, int max_q) {
+                        int k, int ac, int warps, bool per_rx, bool pair, int max_nd, int max_q_nd, int max_q) {
     if (n == 0) return GH_OK;
+    if (pair) {  // two warps per (x, y) cell
+        if (warps != 2 || per_rx) return gh_fail(ctx, GH_EINVAL, "paired scorer: 2 warps, all rows");
+        if (ac == 3) return hop_pair_launch<3, true>(ctx, frames, items, n, counter, k, max_q_nd, max_q);
+        if (ac == 5) return hop_pair_launch<5, true>(ctx, frames, items, n, counter, k, max_q_nd, max_q);
+        if (ac == 8) return hop_pair_launch<8, false>(ctx, frames, items, n, counter, k, max_q_nd, max_q);
+        if (ac == 16) return hop_pair_launch<16, false>(ctx, frames, items, n, counter, k, max_q_nd, max_q);
+        return gh_fail(ctx, GH_EINVAL, "paired scorer: cells per lane %d not in {3, 5, 8, 16}", ac);
+    }
 #define GH_BATCH_CASE(N)                                                                                            \
     if (ac == N)                                                                                                    \
         return per_rx ? hop_batch_launch<N, true>(ctx, frames, items, n, counter, k, warps, max_nd, max_q_nd, max_q) \
@@ -1282,11 +1296,7 @@ int gh_launch_hop_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* 
     GH_BATCH_CASE(6)
     GH_BATCH_CASE(10)
 #undef GH_BATCH_CASE
-    // two warps per (x, y) cell: the 8 x 4 layout's runs split between them
-    if ((ac == 3 || ac == 5) && warps == 2 && !per_rx)
-        return ac == 3 ? hop_pair_launch<3>(ctx, frames, items, n, counter, k, max_q_nd, max_q)
-                       : hop_pair_launch<5>(ctx, frames, items, n, counter, k, max_q_nd, max_q);
-    return gh_fail(ctx, GH_EINVAL, "batched scorer: cells per lane %d not in {3, 5, 6, 8, 10, 16, 32}", ac);
+    return gh_fail(ctx, GH_EINVAL, "batched scorer: cells per lane %d not in {6, 8, 10, 16, 32}", ac);
 }
 
 size_t gh_hop_batch_warp_bytes(int ac, int row_floats, int max_q) { return hop_batch_warp_bytes(ac, row_floats, max_q); }

@@ -527,14 +527,15 @@ size_t gh_hop_pair_bytes(int ac, int row_floats, int max_q);
 int gh_launch_coord_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* items, int n);
 // Persistent batched scorer: warps take items (frame, first (x, y) cell, count)
 // from *counter (zeroed here) and fold each frame's best cell into key[k];
-// ac cells per lane (8, 16, 32; 6, 10 in the 8 x 4 lane layout; 3, 5 with
-// warps = 2 and !per_rx: the paired scorer, two warps per (x, y) cell sharing
-// one set of power rows), warps per CTA; per_rx: one receiver's power
-// row at a time (every frame's cells of a lane form one run: nvy <= 32 and
-// nvx <= SA ac). max_nd, max_q_nd, max_q: largest Nd, Q * Nd and Q of the
-// frames the items name.
+// ac cells per lane (8, 16, 32; 6, 10 in the 8 x 4 lane layout), warps per
+// CTA; per_rx: one receiver's power row at a time (every frame's cells of a
+// lane form one run: nvy <= 32 and nvx <= SA ac); pair: the paired scorer
+// (two warps per (x, y) cell sharing one set of power rows; warps = 2,
+// !per_rx; ac 3 or 5 in the 8 x 4 layout, 8 or 16 in the standard one).
+// max_nd, max_q_nd, max_q: largest Nd, Q * Nd and Q of the frames the items
+// name.
 int gh_launch_hop_batch(gh_ctx* ctx, const BatchFrame* frames, const BatchItem* items, int n, unsigned* counter,
-                        int k, int ac, int warps, bool per_rx, int max_nd, int max_q_nd, int max_q);
+                        int k, int ac, int warps, bool per_rx, bool pair, int max_nd, int max_q_nd, int max_q);
 // Batched BOMP selection and correlation of iteration k for the listed frames.
 int gh_launch_bomp_select_batch(gh_ctx* ctx, const BatchFrame* frames, const int* active, int n, int k);
 int gh_launch_bomp_corr_batch(gh_ctx* ctx, const BatchFrame* frames, const int* active, int n, int k, int max_chunks,

@@ -100,7 +100,7 @@ def test_power_row_modes_give_single_frame_results(ctx, torch_cuda, row_mode):
         if row_mode == 0:
             assert ctx.gh_batch_row_mode() == 0
         if row_mode == 2:
-            assert ctx.gh_batch_row_mode() in (0, 2)
+            assert ctx.gh_batch_row_mode() == 2
     finally:
         ctx.gh_set_batch_row_mode(-1)
     for f, r in zip(dev, res):
@@ -130,20 +130,22 @@ def test_uneven_velocity_axes_give_single_frame_results(ctx, torch_cuda, row_mod
 
 def test_paired_scorer_gives_single_frame_results(ctx, torch_cuda):
     """Two warps per (x, y) cell sharing one set of power rows (the 8 x 4
-    layout's 24 x 24 and 40 x 40 velocity grids, odd and even Q, several Nd,
-    K up to 3 so that masked cells are skipped): the same results as
-    gh_detect, bit for bit, and the paired scorer is the one that ran."""
+    layout's 24 x 24 and 40 x 40 velocity grids and the standard layout's
+    16 x 16, 32 x 32 and 12 x 20, odd and even Q, several Nd, K up to 3 so
+    that masked cells are skipped): the same results as gh_detect, bit for
+    bit, and the paired scorer is the one that ran."""
     frames = []
-    for i, nv in enumerate((24, 40, 40, 24, 40)):
+    for i, nv in enumerate((24, 40, 40, 24, 40, 16, 32, (12, 20))):
+        nv = nv if isinstance(nv, tuple) else (nv, nv)
         radar = scenes.Radar(24e9, 250e6, 128e-6, 64 << (i % 3), 64 << (i % 2), 4)
-        grid = scenes.Grid.from_bounds((0, 0, -15, -15), (40, 40, 15, 15), (10 + 2 * i, 12 + i, nv, nv))
-        frames.append(scenes.custom_scene(90 + i, radar, grid, Q=3 + i, T=1 + i % 3, snr_db=12.0))
+        grid = scenes.Grid.from_bounds((0, 0, -15, -15), (40, 40, 15, 15), (10 + 2 * i, 12 + i) + nv)
+        frames.append(scenes.custom_scene(90 + i, radar, grid, Q=3 + i % 6, T=1 + i % 3, snr_db=12.0))
     dev, _ = _device_frames(torch_cuda, frames, synth_ctx=ctx)
     ctx.gh_set_batch_row_mode(2)
     try:
         res = ctx.gh_detect_batch(dev)
         assert ctx.gh_batch_row_mode() == 2
-        assert ctx.gh_batch_tuning() in ((3, 2), (5, 2))
+        assert ctx.gh_batch_tuning() in ((3, 2), (5, 2), (8, 2), (16, 2))
     finally:
         ctx.gh_set_batch_row_mode(-1)
     for f, r in zip(dev, res):
