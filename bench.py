@@ -445,7 +445,9 @@ def precision_leg(ctx, torch, gh, scenes, device, stream, flush, rank, args, l2_
                              "cells_equal_c64": bool(np.array_equal(cells, cells64)),
                              "roofline": {"bound": "l2", "achieved": achieved, "peak": l2_gbs, "unit": "GB/s",
                                           "frac": achieved / l2_gbs if l2_gbs else None, "traffic": None,
-                                          "kernel": "hop_score_kernel", "bytes_per_unit": bpe,
+                                          # this frame's rows of all receivers fill shared memory:
+                                          # two warps score each (x, y) cell
+                                          "kernel": "hop_pair_score_kernel", "bytes_per_unit": bpe,
                                           "units_per_launch": units,
                                           "peak_source": "L2-resident read probe of this run",
                                           "hbm": {"achieved": (maps_bytes + sc.grid.n[0] * sc.grid.n[1] * sc.Q * 80)
